@@ -1,0 +1,578 @@
+"""Pins of the CPU oracle against what arXiv 1302.6303 and the mathematics fix.
+
+Each test checks the oracle against something other than itself: closed forms
+from the model of Sec. 3.1 written in a different algebraic form, invariants
+of the finite-volume discretisation (Sec. 3.2: conservation with flux
+matching, zero flux at equilibrium), exactness of linear coarse-fine
+interpolation (Sec. 3.2.1), brute-force Jacobians, eigenvalues of the
+textbook 7-point operator, convergence of FAC (Algorithm 1) to a direct solve,
+and second-order convergence on a manufactured solution.
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import Oracle, JV_ANALYTIC, JV_FD, LIM_PAPER_LITERAL, LIM_WILSON
+from paper_1302_6303_gb300 import workloads as W
+
+
+def vols(h):
+    L, _, _, _ = h.cell_ijk()
+    return np.array([1.0 / np.prod(h.level_n(l)) for l in range(h.nlevels)])[L]
+
+
+def leaf_sum(o, h, x):
+    m = o.leaf_mask()
+    V = vols(h)
+    return float(np.sum((V * x)[m]))
+
+
+# ------------------------------------------------------------- equilibrium
+def test_equilibrium_exact_zero_single_level():
+    """Sec. 3.1: uniform E = T^4 gives zero flux and zero coupling."""
+    h = W.all_neumann(W.uniform(6))
+    z = W.material_from_cubes(h, [((1, 1, 1), 2, 10.0)])
+    o = Oracle(h, z)
+    N = h.ncells
+    u = np.concatenate([np.full(N, 0.0625), np.full(N, 0.5)])  # T^4 == E exactly
+    F = o.residual(u, u.copy(), 1.0, 1e-2)
+    assert np.all(F == 0.0)
+
+
+@pytest.mark.parametrize("three", [False, True])
+def test_equilibrium_amr(three):
+    h = W.all_neumann(W.tiny_amr(8, three_levels=three))
+    o = Oracle(h, W.material_from_cubes(h, [((2, 2, 2), 3, 10.0)]))
+    N = h.ncells
+    u = np.concatenate([np.full(N, 0.0625), np.full(N, 0.5)])
+    F = o.residual(u, u.copy(), 1.0, 1e-2)
+    S = o.residual_scale(u, u.copy(), 1.0, 1e-2)
+    assert np.all(np.abs(F) <= 1e-14 * S)
+
+
+def test_robin_equilibrium():
+    """Robin data R = E/4 is satisfied by a uniform E: no boundary flux."""
+    h = W.uniform(5, bc_type=[1, 1, 0, 0, 0, 0], bc_R=[0.0625 / 4, 0.0625 / 4, 0, 0, 0, 0])
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    N = h.ncells
+    u = np.concatenate([np.full(N, 0.0625), np.full(N, 0.5)])
+    F = o.residual(u, u.copy(), 1.0, 1e-2)
+    assert np.abs(F).max() <= 1e-17
+
+
+# ------------------------------------------------------------ conservation
+HIERS = {
+    "single": lambda: W.uniform(6),
+    "tiny2": lambda: W.tiny_amr(8),
+    "tiny3": lambda: W.tiny_amr(8, three_levels=True),
+    "boundary": lambda: W.boundary_amr(8),
+}
+
+
+@pytest.mark.parametrize("name", list(HIERS))
+def test_conservation_neumann(name):
+    """Sum over leaf cells of V (F_E + F_T) equals sum of V (a0 u - b): the
+    coupling cancels, interior fluxes telescope and coarse-fine fluxes match
+    (Sec. 3.2.1 flux matching)."""
+    h = W.all_neumann(HIERS[name]())
+    z = W.material_from_cubes(h, [((1, 2, 3), 3, 10.0), ((5, 0, 4), 2, 10.0)])
+    o = Oracle(h, z)
+    N = h.ncells
+    u = W.front_state(h, seed=4)
+    rng = np.random.default_rng(5)
+    b = u * (1 + 0.1 * rng.uniform(-1, 1, 2 * N))
+    a0, dt = 1.5, 0.05
+    F = o.residual(u, b, a0, dt)
+    lhs = leaf_sum(o, h, F[:N] + F[N:])
+    rhs = leaf_sum(o, h, a0 * (u[:N] + u[N:]) - b[:N] - b[N:])
+    S = o.residual_scale(u, b, a0, dt)
+    tol = 1e-13 * leaf_sum(o, h, S[:N] + S[N:])
+    assert abs(lhs - rhs) <= tol
+    # the identity is not vacuous: diffusion terms are large here
+    assert leaf_sum(o, h, np.abs(F[:N] - (a0 * u[:N] - b[:N]))) > 1e3 * tol
+
+
+@pytest.mark.parametrize("name", ["single", "boundary"])
+def test_conservation_with_robin(name):
+    """With a Robin face at x = 0 the imbalance equals dt times the boundary
+    flux D_b (E_0 - E_g)/h_x through that face, D_b = 1/(3 sigma_a(T_0))
+    unlimited (Sec. 3.1, boundary conditions not flux limited)."""
+    h = HIERS[name]()
+    z = W.material_from_cubes(h, [((0, 2, 3), 3, 10.0)])
+    o = Oracle(h, z)
+    N = h.ncells
+    u = W.front_state(h, seed=7)
+    b = u.copy()
+    a0, dt = 1.0, 0.02
+    F = o.residual(u, b, a0, dt)
+    imb = leaf_sum(o, h, F[:N] + F[N:]) - leaf_sum(o, h, a0 * (u[:N] + u[N:]) - b[:N] - b[N:])
+    gE, _, _ = o.ghosts(u)
+    # boundary flux from the ghost layer of x- faces of leaf cells at i = 0
+    expect = 0.0
+    gi = 0
+    leaf = o.leaf_mask()
+    L, I, J, K = h.cell_ijk()
+    index = {}
+    for c in range(N):
+        index[(L[c], I[c], J[c], K[c])] = c
+    for (l, lo, hi, off) in h.patches():
+        n = [hi[d] - lo[d] + 1 for d in range(3)]
+        nx = h.level_n(l)
+        hx, hy, hz = 1.0 / nx[0], 1.0 / nx[1], 1.0 / nx[2]
+        # face 0 (x-) is the first block of this patch's ghosts
+        for kk in range(n[2]):
+            for jj in range(n[1]):
+                if lo[0] == 0:
+                    c = index[(l, 0, lo[1] + jj, lo[2] + kk)]
+                    if leaf[c]:
+                        sigma = float(z[c]) ** 3 / u[N + c] ** 3
+                        Db = 1.0 / (3.0 * sigma)
+                        Eg = gE[gi + jj + n[1] * kk]
+                        expect += dt * hy * hz * Db * (u[c] - Eg) / hx
+        gi += 2 * (n[1] * n[2] + n[0] * n[2] + n[0] * n[1])
+    assert expect != 0.0
+    assert abs(imb - expect) <= 1e-12 * abs(expect)
+
+
+def test_robin_ghost_relation_and_neumann_copy():
+    """The Robin ghost satisfies (1/2) D_b dE/dn + E_face/4 = R at the face;
+    Neumann ghosts equal the interior cell (zero normal derivative)."""
+    h = W.uniform((4, 3, 2), bc_type=[1, 1, 0, 0, 0, 0], bc_R=[1.0, 0.3, 0, 0, 0, 0])
+    z = W.material_from_cubes(h, [((0, 0, 0), 1, 10.0)])
+    o = Oracle(h, z)
+    N = h.ncells
+    u = W.front_state(h, seed=2)
+    gE, gT, gz = o.ghosts(u)
+    n = (4, 3, 2)
+    hx = 1.0 / 4
+    sizes = [n[1] * n[2]] * 2 + [n[0] * n[2]] * 2 + [n[0] * n[1]] * 2
+    starts = np.cumsum([0] + sizes)
+    for face, R in ((0, 1.0), (1, 0.3)):
+        i = 0 if face == 0 else n[0] - 1
+        for kk in range(n[2]):
+            for jj in range(n[1]):
+                c = i + n[0] * (jj + n[1] * kk)
+                E0, T0 = u[c], u[N + c]
+                Db = 1.0 / (3.0 * (float(z[c]) ** 3 / T0 ** 3))
+                Eg = gE[starts[face] + jj + n[1] * kk]
+                dEdn = (Eg - E0) / hx            # outward normal derivative
+                lhs = 0.5 * Db * dEdn + 0.25 * 0.5 * (Eg + E0)
+                assert abs(lhs - R) <= 1e-13 * max(1.0, abs(R))
+                assert gT[starts[face] + jj + n[1] * kk] == T0
+    # Neumann y faces: ghost = interior
+    for kk in range(n[2]):
+        for ii in range(n[0]):
+            c = ii + n[0] * (0 + n[1] * kk)
+            assert gE[starts[2] + kk + n[2] * ii] == u[c]  # y face: z fastest, then x
+
+
+# ------------------------------------------------ closed forms of the model
+def _two_cell(limiter, za, zb):
+    h = W.all_neumann(W.uniform((2, 1, 1)))
+    z = np.array([za, zb], np.float32)
+    o = Oracle(h, z, limiter=limiter)
+    u = np.array([0.3, 0.05, 0.7, 0.45])  # E_a, E_b, T_a, T_b
+    b = np.array([0.1, 0.2, 0.3, 0.4])
+    a0, dt = 1.3, 0.07
+    return o.residual(u, b, a0, dt), u, b, a0, dt
+
+
+@pytest.mark.parametrize("limiter", [LIM_WILSON, LIM_PAPER_LITERAL])
+@pytest.mark.parametrize("zz", [(1.0, 1.0), (1.0, 10.0)])
+def test_two_cell_closed_form(limiter, zz):
+    """Face D_E from Sec. 3.1: the Wilson coefficient 1/(3 sigma + |grad E|/E)
+    with sigma taken as the harmonic combination of the two cells at the face
+    temperature, |grad E| = |dE|/h and E the face average; D_T = k T_f^(5/2);
+    coupling sigma_a (T^4 - E) with sigma_a = z^3/T^3 per cell."""
+    za, zb = zz
+    F, u, b, a0, dt = _two_cell(limiter, za, zb)
+    Ea, Eb, Ta, Tb = u
+    h = 0.5
+    Tf = 0.5 * (Ta + Tb)
+    # harmonic mean of the two cells' unlimited D = 1/(3 sigma) at T_f
+    Da, Db_ = 1.0 / (3 * za ** 3 / Tf ** 3), 1.0 / (3 * zb ** 3 / Tf ** 3)
+    Dharm = 2 * Da * Db_ / (Da + Db_)
+    grad_over_E = abs(Eb - Ea) / h / (0.5 * (Ea + Eb))
+    if limiter == LIM_WILSON:
+        DE = 1.0 / (1.0 / Dharm + grad_over_E)
+    else:  # the printed form runs the limiter at half strength
+        DE = 1.0 / (1.0 / Dharm + 0.5 * grad_over_E)
+    DT = 0.01 * Tf ** 2.5
+    flux_E = DE * (Eb - Ea) / h
+    flux_T = DT * (Tb - Ta) / h
+    cpl_a = za ** 3 / Ta ** 3 * (Ta ** 4 - Ea)
+    cpl_b = zb ** 3 / Tb ** 3 * (Tb ** 4 - Eb)
+    fEa, fEb = flux_E / h + cpl_a, -flux_E / h + cpl_b
+    fTa, fTb = flux_T / h - cpl_a, -flux_T / h - cpl_b
+    expect = np.array([a0 * Ea - b[0] - dt * fEa, a0 * Eb - b[1] - dt * fEb,
+                       a0 * Ta - b[2] - dt * fTa, a0 * Tb - b[3] - dt * fTb])
+    np.testing.assert_allclose(F, expect, rtol=1e-13, atol=1e-15)
+
+
+def test_single_cell_ode_and_newton():
+    """One cell, Neumann: the residual reduces to the coupling ODE; the Newton
+    solution conserves E + T and matches scipy's fsolve of the same 2x2
+    backward-Euler system written from Eqs. E_td, T_td."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    h = W.all_neumann(W.uniform(1))
+    z = np.array([3.0], np.float32)
+    o = Oracle(h, z)
+    o.set_solver(nmg=1, coarse_sweeps=1, rtol=1e-12)
+    un = np.array([0.9, 0.2])
+    dt = 0.05
+
+    def be(x):
+        E, T = x
+        s = 27.0 / T ** 3
+        return [E - un[0] - dt * s * (T ** 4 - E), T - un[1] + dt * s * (T ** 4 - E)]
+
+    F = o.residual(un, un.copy(), 1.0, dt)
+    np.testing.assert_allclose(F, be(un), rtol=1e-14)
+    u, st = o.newton(un.copy(), un.copy(), 1.0, dt)
+    assert st["status"] == 0
+    ref = scipy_opt.fsolve(be, un, xtol=1e-14)
+    np.testing.assert_allclose(u, ref, rtol=1e-10)
+    assert abs(u.sum() - un.sum()) <= 1e-14
+
+
+# ---------------------------------------------------------------- Jacobian
+@pytest.mark.parametrize("name", ["single4", "tiny2"])
+def test_dense_jacobian_vs_central_fd(name):
+    """Analytic Jv columns equal brute-force central differences of F."""
+    if name == "single4":
+        h = W.uniform(4)
+        cols = None
+    else:
+        h = W.tiny_amr(8)
+        cols = 60
+    z = W.material_from_cubes(h, [((1, 1, 1), 2, 10.0)])
+    o = Oracle(h, z)
+    N = h.ncells
+    u = W.front_state(h, seed=11, noise=0.2)
+    b = u.copy()
+    a0, dt = 1.0, 0.01
+    rng = np.random.default_rng(3)
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    idx = np.arange(2 * N)[leaf]
+    if cols is not None:
+        idx = rng.choice(idx, cols, replace=False)
+    for j in idx:
+        e = np.zeros(2 * N)
+        e[j] = 1.0
+        Ja = o.jv_analytic(u, e, a0, dt)
+        step = 1e-6 * abs(u[j])
+        up, um = u.copy(), u.copy()
+        up[j] += step
+        um[j] -= step
+        Jc = (o.residual(up, b, a0, dt) - o.residual(um, b, a0, dt)) / (2 * step)
+        scale = np.abs(Ja).max()
+        assert np.abs(Ja - Jc).max() <= 2e-6 * scale, (j, np.abs(Ja - Jc).max(), scale)
+
+
+@pytest.mark.parametrize("name", ["single", "tiny3"])
+def test_fd_jv_close_to_analytic(name):
+    h = HIERS[name]()
+    o = Oracle(h, W.material_from_cubes(h, [((1, 1, 1), 2, 10.0)]))
+    u = W.front_state(h, seed=2)
+    v = W.random_direction(h, seed=3)
+    v /= np.sqrt(o.dot(v, v))
+    Ja = o.jv_analytic(u, v, 1.0, 1e-3)
+    Jf, eps = o.jv_fd(u, v, u.copy(), 1.0, 1e-3)
+    assert 1e-10 < abs(eps) < 1e-6
+    assert np.abs(Ja - Jf).max() <= 1e-5 * np.abs(Ja).max()
+
+
+def test_fd_eps_properties():
+    """Sec. 4.1 differencing parameter: ~sqrt(eps_mach) <u,v>/||v||^2,
+    scales as 1/c under v -> c v (both branches), keeps u + eps v > 0."""
+    h = W.uniform(4)
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    u = W.front_state(h, seed=1)
+    rng = np.random.default_rng(0)
+    v = rng.uniform(0.1, 1.0, u.size)             # <u,v> > u_min ||v||_1 branch
+    e1 = o.fd_eps(u, v)
+    assert abs(o.fd_eps(u, 4.0 * v) - e1 / 4.0) <= 1e-15 * abs(e1)
+    assert 1e-9 < e1 < 1e-6
+    # second branch: <u,v> ~ 0
+    v2 = rng.standard_normal(u.size)
+    v2 -= o.dot(u, v2) / o.dot(u, u) * u
+    e2 = o.fd_eps(u, v2)
+    assert abs(o.fd_eps(u, 8.0 * v2) - e2 / 8.0) <= 1e-12 * abs(e2)
+    assert abs(e2) < 1e-8 * 1e-3 * 10
+    # positivity halving: one huge negative component
+    v3 = v.copy()
+    v3[5] = -1e9
+    e3 = o.fd_eps(u, v3)
+    assert np.all(u + e3 * v3 > 0)
+
+
+# --------------------------------------------------------- P1 operators
+def _setup_pc(h, seed=4, a0=1.0, dt=0.05, nmg=2, **kw):
+    z = W.material_from_cubes(h, [((1, 2, 1), 2, 10.0)])
+    o = Oracle(h, z)
+    o.set_solver(nmg=nmg, **kw)
+    u = W.front_state(h, seed=seed, noise=0.1)
+    o.pc_setup(u, a0, dt)
+    return o, u
+
+
+@pytest.mark.parametrize("fld", [0, 1])
+def test_linop_symmetry_single_level(fld):
+    """The frozen diffusion block I - beta div D grad is symmetric in the
+    volume-weighted inner product on a single level (Robin included)."""
+    h = W.uniform(6)
+    o, _ = _setup_pc(h)
+    rng = np.random.default_rng(1)
+    x, y = rng.standard_normal(h.ncells), rng.standard_normal(h.ncells)
+    a = np.dot(x, o.comp_apply(fld, y))
+    b = np.dot(o.comp_apply(fld, x), y)
+    assert abs(a - b) <= 1e-13 * np.sqrt(np.dot(x, x) * np.dot(y, y)) * 50
+
+
+@pytest.mark.parametrize("fld", [0, 1])
+def test_linop_fourier_eigenvalues(fld):
+    """Uniform state, all Neumann: D is constant and the block is the
+    textbook 7-point operator; Neumann cosine modes are eigenvectors with
+    eigenvalue 1 + beta D sum_d (4/h_d^2) sin^2(pi m_d / (2 n_d))."""
+    n = (6, 4, 5)
+    h = W.all_neumann(W.uniform(n))
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    N = h.ncells
+    T = 0.6
+    u = np.concatenate([np.full(N, T ** 4), np.full(N, T)])
+    dt = 0.03
+    o.pc_setup(u, 1.0, dt)
+    D = (T ** 3 / 3.0) if fld == 0 else 0.01 * T ** 2.5
+    _, I, J, K = h.cell_ijk()
+    for m in [(1, 0, 0), (2, 3, 1), (5, 1, 4)]:
+        x = (np.cos(np.pi * m[0] * (I + 0.5) / n[0]) * np.cos(np.pi * m[1] * (J + 0.5) / n[1])
+             * np.cos(np.pi * m[2] * (K + 0.5) / n[2]))
+        lam = 1.0 + dt * D * sum(4.0 * n[d] ** 2 * np.sin(np.pi * m[d] / (2 * n[d])) ** 2
+                                 for d in range(3))
+        np.testing.assert_allclose(o.comp_apply(fld, x), lam * x, rtol=0, atol=1e-12 * lam)
+
+
+@pytest.mark.parametrize("fld", [0, 1])
+def test_linop_constant_on_amr(fld):
+    """All Neumann: diffusion of a constant is zero across coarse-fine faces."""
+    h = W.all_neumann(W.tiny_amr(8, three_levels=True))
+    o, _ = _setup_pc(h, nmg=3)
+    y = o.comp_apply(fld, np.ones(h.ncells))
+    leaf = o.leaf_mask()
+    assert np.abs(y[leaf] - 1.0).max() <= 1e-12
+
+
+def test_cf_ghost_linear_exact():
+    """Linear coarse-fine interpolation (Sec. 3.2.1) reproduces linear fields
+    exactly at fine ghost centres; sibling ghosts are exact cell values."""
+    h = W.tiny_amr(8, three_levels=True)
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    L, x, y, zc = h.cell_centres()
+    lin = lambda X, Y, Z: 1.0 + 0.1 * X + 0.2 * Y + 0.3 * Z
+    E = lin(x, y, zc)
+    u = np.concatenate([E, np.full(h.ncells, 0.5)])
+    u[: h.ncells] = o.average_down(u[: h.ncells].copy())  # covered = mean of children
+    gE, _, _ = o.ghosts(u)
+    gi = 0
+    checked = 0
+    for (l, lo, hi, off) in h.patches():
+        if l == 0:
+            gi += 6 * 64
+            continue
+        nl = h.level_n(l)
+        n = [hi[d] - lo[d] + 1 for d in range(3)]
+        for face in range(6):
+            d, s = face // 2, (1 if face % 2 else -1)
+            t1, t2 = (d + 1) % 3, (d + 2) % 3
+            for b2 in range(lo[t2], hi[t2] + 1):
+                for b1 in range(lo[t1], hi[t1] + 1):
+                    c = [0, 0, 0]
+                    c[d] = (lo[d] - 1) if s < 0 else (hi[d] + 1)
+                    c[t1], c[t2] = b1, b2
+                    X = [(c[a] + 0.5) / nl[a] for a in range(3)]
+                    assert abs(gE[gi] - lin(*X)) <= 1e-14, (l, face, c)
+                    gi += 1
+                    checked += 1
+    assert checked > 0
+
+
+def test_gmg_textbook_convergence():
+    """One V(2,2) cycle of the GMG on a constant-coefficient Neumann problem
+    contracts the error by a textbook factor (< 0.15) when the coarsest grid
+    (one cell, where the operator is the identity) is solved exactly."""
+    h = W.all_neumann(W.uniform(16))
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    o.set_solver(nmg=5, nu1=2, nu2=2)
+    N = h.ncells
+    T = 0.9
+    u = np.concatenate([np.full(N, T ** 4), np.full(N, T)])
+    o.pc_setup(u, 1.0, 5.0)  # strongly diffusion dominated
+    rng = np.random.default_rng(0)
+    f = rng.standard_normal(N)
+    x = np.zeros(N)
+    rn = []
+    for _ in range(6):
+        r = f - o.comp_apply(0, x)
+        rn.append(np.linalg.norm(r))
+        x += o.gmg(0, r)
+    rates = np.array(rn[1:]) / np.array(rn[:-1])
+    assert rates[-1] < 0.15, rates
+
+
+def test_fac_single_level_equals_gmg():
+    h = W.uniform(8)
+    o, _ = _setup_pc(h, nmg=3)
+    rng = np.random.default_rng(2)
+    f = rng.standard_normal(h.ncells)
+    for fld in (0, 1):
+        np.testing.assert_array_equal(o.fac(fld, f), o.gmg(fld, f))
+
+
+@pytest.mark.parametrize("three", [False, True])
+@pytest.mark.parametrize("fld", [0, 1])
+def test_fac_converges_to_direct_solve(three, fld):
+    """Iterating FAC V-cycles (Algorithm 1) converges, at a multigrid rate,
+    to the dense direct solution of the composite operator L^c."""
+    h = W.tiny_amr(8, three_levels=three)
+    o, _ = _setup_pc(h, nmg=3, dt=0.2)
+    leaf = o.leaf_mask()
+    idx = np.nonzero(leaf)[0]
+    N = h.ncells
+    A = np.zeros((idx.size, idx.size))
+    for jj, j in enumerate(idx):
+        e = np.zeros(N)
+        e[j] = 1.0
+        A[:, jj] = o.comp_apply(fld, e)[idx]
+    rng = np.random.default_rng(7)
+    f = np.zeros(N)
+    f[idx] = rng.standard_normal(idx.size)
+    xd = np.linalg.solve(A, f[idx])
+    x = np.zeros(N)
+    errs = []
+    for _ in range(12):
+        r = f - o.comp_apply(fld, x)
+        r[~leaf] = 0.0
+        x += o.fac(fld, r)
+        errs.append(np.abs(x[idx] - xd).max())
+    assert errs[-1] <= 1e-10 * np.abs(xd).max()
+    assert errs[3] / errs[2] < 0.5
+
+
+def test_p2_solve_matches_printed_matrix():
+    """y = P^{-1} w = P2^{-1} P1^{-1} w with P2 as printed in Sec. 4.2."""
+    h = W.uniform(4)
+    o, u = _setup_pc(h, nmg=2, dt=0.1)
+    N = h.ncells
+    rng = np.random.default_rng(9)
+    w = rng.standard_normal(2 * N)
+    y = o.pc_apply(w)
+    zE, zT = o.fac(0, w[:N]), o.fac(1, w[N:])
+    T = u[N:]
+    zc = W.material_from_cubes(h, [((1, 2, 1), 2, 10.0)]).astype(np.float64)
+    sig = zc ** 3 / T ** 3
+    beta = 0.1
+    yE, yT = y[:N], y[N:]
+    r1 = (1 + sig * beta) * yE - sig * beta * T ** 3 * yT
+    r2 = -sig * beta * yE + (1 + sig * beta * T ** 3) * yT
+    np.testing.assert_allclose(r1, zE, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(r2, zT, rtol=1e-12, atol=1e-14)
+
+
+# ------------------------------------------------------------------ Newton
+@pytest.mark.parametrize("name", ["single", "tiny2"])
+def test_newton_solution_independent_of_solver_settings(name):
+    h = {"single": lambda: W.uniform(8), "tiny2": lambda: W.tiny_amr(8)}[name]()
+    z = W.material_from_cubes(h, [((1, 2, 1), 3, 10.0)])
+    u0 = W.front_state(h, seed=5, noise=0.02)
+    sols = []
+    for kw in [dict(nu1=2, nu2=2, nmg=3, jv_mode=JV_FD),
+               dict(nu1=1, nu2=0, nmg=1, jv_mode=JV_FD),
+               dict(nu1=2, nu2=2, nmg=3, jv_mode=JV_ANALYTIC)]:
+        o = Oracle(h, z)
+        o.set_solver(rtol=1e-10, **kw)
+        u, st = o.newton(u0.copy(), u0.copy(), 1.0, 2e-3)
+        assert st["status"] == 0 and st["fnorm"] <= 1e-10 * st["fnorm0"]
+        leaf = np.concatenate([o.leaf_mask()] * 2)
+        sols.append(u[leaf])
+    for s in sols[1:]:
+        np.testing.assert_allclose(s, sols[0], rtol=1e-8)
+
+
+# ------------------------------------------------- manufactured solution
+def _mms_funcs():
+    sp = pytest.importorskip("sympy")
+    x = sp.symbols("x", real=True)
+    E = sp.Rational(1, 2) + sp.Rational(1, 4) * sp.cos(sp.pi * x)
+    T = sp.Rational(4, 5) + sp.Rational(1, 10) * sp.cos(sp.pi * x)
+    sigma = 1 / T ** 3                                   # z = 1
+    dE = sp.diff(E, x)
+    # Wilson limiter D_E = 1/(3 sigma + |grad E|/E) with |grad E| = |E_x|
+    DE = 1 / (3 * sigma + sp.Abs(dE) / E)
+    DT = sp.Rational(1, 100) * T ** sp.Rational(5, 2)
+    cpl = sigma * (T ** 4 - E)
+    fE = sp.diff(DE * dE, x) + cpl
+    fT = sp.diff(DT * sp.diff(T, x), x) - cpl
+    lam = lambda ex: sp.lambdify(x, ex, "numpy")
+    return lam(E), lam(T), lam(fE), lam(fT)
+
+
+def _mms_error(h, funcs, dt=0.05):
+    Ef, Tf, fEf, fTf = funcs
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    o.set_solver(rtol=1e-11, nmg=1, nu1=2, nu2=2, coarse_sweeps=4, jv_mode=JV_ANALYTIC)
+    L, x, y, z = h.cell_centres()
+    us = np.concatenate([Ef(x), Tf(x)])
+    fs = np.concatenate([fEf(x), fTf(x)])
+    b = us - dt * fs                       # makes u* the exact semi-discrete step
+    u, st = o.newton(1.05 * us, b, 1.0, dt)
+    assert st["status"] == 0
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    return np.abs(u - us)[leaf].max()
+
+
+def test_mms_second_order_uniform():
+    """Second-order spatial accuracy (Sec. 6 accuracy study) on a smooth
+    manufactured 1D profile with Neumann walls."""
+    funcs = _mms_funcs()
+    errs = [_mms_error(W.all_neumann(W.uniform((n, 1, 1))), funcs) for n in (16, 32, 64)]
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), (errs, rates)
+
+
+def test_mms_amr_second_order():
+    """With a refined patch (linear coarse-fine interpolation plus flux
+    matching) the solution error still converges at second order, the claim
+    of Sec. 3.2.1; a wrong interpolation weight drops this to first order."""
+    funcs = _mms_funcs()
+    errs = []
+    for n in (16, 32, 64):
+        lv1 = [((n // 2, 0, 0), (n + n // 2 - 1, 1, 1))]
+        h = W.all_neumann(W.Hierarchy((n, 1, 1), [[((0, 0, 0), (n - 1, 0, 0))], lv1]))
+        errs.append(_mms_error(h, funcs))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 1.8), (errs, rates)
+
+
+# -------------------------------------------------------------- tagging
+def test_tag_linear_field():
+    """Sec. 5 indicators on E linear in x: curvature indicator 0 away from the
+    boundary, gradient indicator h |E_x| / (0.1 max E) exactly."""
+    h = W.all_neumann(W.uniform(8))
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    L, x, y, z = h.cell_centres()
+    E = 0.2 + 0.5 * x
+    u = np.concatenate([E, np.full(h.ncells, 0.5)])
+    emax = E.max()
+    tg = (1.0 / 8) * 0.5 / (0.1 * emax)
+    _, I, J, K = h.cell_ijk()
+    inner = (I > 0) & (I < 7)
+    t = o.tag(u, thr_g=tg * (1 - 1e-9))
+    assert np.all((t[inner] & 2) == 2)
+    t = o.tag(u, thr_g=tg * (1 + 1e-9))
+    assert np.all((t[inner] & 2) == 0)
+    t = o.tag(u, thr_c=1e-9)
+    assert np.all((t[inner] & 1) == 0)
+    rel = np.sqrt((0.5 / 8) ** 2) / E
+    t = o.tag(u, thr_r=0.0)
+    assert np.all(t[inner] & 4)
+    tr = o.tag(u, thr_r=float(rel[inner].max()) * (1 + 1e-9))
+    assert np.all((tr[inner] & 4) == 0)
