@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the implicit radiation-diffusion hot path on one GB300.
+
+Workload: 2-level AMR, base 64^3, refinement ratio 2, fine patches of
+16^3-32^3 cells tiling the Marshak band x < 1/8, z = 10 in 20 seeded cubes of
+side 4-12 base cells on z = 1, E0 = 1e-5, T0 = E0^(1/4), Robin R = 1 at x = 0;
+BDF2 steps (first backward Euler) with dt = 5e-4, Newton rtol 1e-8.
+
+One benchmark step = one implicit time step through the public API (nrd_step:
+ghost fill, residual, Jv, GMRES, preconditioner set-up and V-cycles, P2,
+Newton updates) followed by the refinement indicators (nrd_tag).
+
+metric: Mcell/s of Jv + V-cycle = leaf cells x Krylov iterations (each one Jv
+plus one P^{-1} application) / total implicit-step time.  Reported for the
+production form (analytic Jv, FP32 V-cycle) with the plain form (FD Jv, FP64
+V-cycle) measured on the same workload beside it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
+# FP64 FMA throughput of this GB300 measured with an FMA-chain microbenchmark
+# (1.20 TFLOP/s); used as the ALU peak of the FP64 stencil kernels.
+FP64_PEAK_TFLOPS = 1.20
+DT = 5e-4
+WORKLOAD = "amr2_base64_marshak_band"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1302_6303_gb300 import workloads as W
+    h, z = W.config_amr2(64, seed=0)
+    return h, z, W.initial_state(h)
+
+
+def peaks():
+    if os.path.exists(MEASURED):
+        d = json.load(open(MEASURED))
+        return float(d.get("hbm_gbs", FALLBACK_HBM)), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_ctx(nrd, h, z, torch, production):
+    if production:
+        p = dict(jv_mode=nrd.JV_ANALYTIC, pc_precision=nrd.PC_F32)
+    else:
+        p = dict(jv_mode=nrd.JV_FD, pc_precision=nrd.PC_F64)
+    ctx = nrd.Context(nu1=2, nu2=2, nmg=4, coarse_sweeps=4, restart=30, rtol=1e-8, **p)
+    ctx.set_hierarchy_from(h)
+    ctx.set_material(torch.from_numpy(z).cuda())
+    return ctx
+
+
+def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
+    """Integrate warmup + nsteps BDF2 steps (first BE); time the last nsteps
+    with CUDA events per step (L2 flushed between steps, outside the events)."""
+    dev = torch.device("cuda")
+    un = torch.from_numpy(u0).to(dev)
+    unm1 = None
+    u = un.clone()
+    tags = None
+    times, kry, newt = [], 0, 0
+    for s in range(warmup + nsteps):
+        timed = s >= warmup
+        if timed and s == warmup:
+            torch.cuda.synchronize()
+            if timing:
+                ctx.timing_enable(True)
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        u.copy_(un)
+        ev0.record()
+        st = ctx.step(u, un, unm1, DT, DT if unm1 is not None else 0.0)
+        tags = ctx.tag(u, thr_r=0.1)
+        ev1.record()
+        torch.cuda.synchronize()
+        if timed:
+            times.append(ev0.elapsed_time(ev1))
+            kry += st["krylov_its"]
+            newt += st["newton_its"]
+        unm1 = un
+        un = u
+        u = torch.empty_like(un)
+    kt = ctx.timing_read() if timing else None
+    if timing:
+        ctx.timing_enable(False)
+    return dict(ms=times, krylov=kry, newton=newt, kernel=kt, u=un, tags=tags)
+
+
+def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
+    """Same metric through the public API with host buffers: each step copies
+    u_n, u_{n-1} from pinned host memory, steps, tags, and reads u_{n+1} and
+    the tags back."""
+    N2 = u0.size
+    hn = torch.from_numpy(u0.copy()).pin_memory()
+    hnm1 = None
+    hout = torch.empty(N2, dtype=torch.float64).pin_memory()
+    htag = torch.empty(N2 // 2, dtype=torch.uint8).pin_memory()
+    d_n = torch.empty(N2, dtype=torch.float64, device="cuda")
+    d_nm1 = torch.empty_like(d_n)
+    d_u = torch.empty_like(d_n)
+    total, kry = 0.0, 0
+    h2d = d2h = 0
+    for s in range(warmup + nsteps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        d_n.copy_(hn, non_blocking=True)
+        b_in = N2 * 8
+        if hnm1 is not None:
+            d_nm1.copy_(hnm1, non_blocking=True)
+            b_in += N2 * 8
+        d_u.copy_(d_n)
+        st = ctx.step(d_u, d_n, d_nm1 if hnm1 is not None else None, DT,
+                      DT if hnm1 is not None else 0.0)
+        t = ctx.tag(d_u, thr_r=0.1)
+        hout.copy_(d_u, non_blocking=True)
+        htag.copy_(t, non_blocking=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        if s >= warmup:
+            total += ev0.elapsed_time(ev1)
+            kry += st["krylov_its"]
+            h2d, d2h = b_in, N2 * 8 + N2 // 2
+        hnm1 = hn.clone()
+        hn = hout.clone()
+    return total, kry, h2d, d2h
+
+
+def cpu_baseline(h, z, u0, leaf):
+    """The oracle as it stands, on the host: preconditioner set-up plus two
+    Krylov iterations' worth of P^{-1} and Jv on the full workload."""
+    from oracle.oracle import Oracle, JV_ANALYTIC
+    o = Oracle(h, z)
+    o.set_solver(jv_mode=JV_ANALYTIC, nu1=2, nu2=2, nmg=4, coarse_sweeps=4)
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal(u0.size)
+    o.pc_setup(u0, 1.0, DT)
+    t0 = time.perf_counter()
+    its = 2
+    for _ in range(its):
+        y = o.pc_apply(w)
+        w = o.jv_analytic(u0, y, 1.0, DT)
+        w /= np.sqrt(max(o.dot(w, w), 1e-300))
+    dt = time.perf_counter() - t0
+    return {"value": leaf * its / dt / 1e6, "unit": "Mcell/s", "cores": 1, "kind": "oracle",
+            "sample": "%d Krylov iterations (P^-1 FAC/GMG apply + analytic Jv) of the FP64 "
+                      "oracle on the full workload (%d leaf cells), single thread" % (its, leaf),
+            "seconds": dt}
+
+
+def reference_arm(args):
+    """The oracle timed as the reference arm: each step = one Krylov iteration
+    (P^{-1} + Jv) of the oracle on the full workload, host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    h, z, u0 = workload()
+    from oracle.oracle import Oracle, JV_ANALYTIC
+    o = Oracle(h, z)
+    o.set_solver(jv_mode=JV_ANALYTIC, nu1=2, nu2=2, nmg=4, coarse_sweeps=4)
+    leaf = int(o.leaf_mask().sum())
+    o.pc_setup(u0, 1.0, DT)
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal(u0.size)
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        y = o.pc_apply(w)
+        w = o.jv_analytic(u0, y, 1.0, DT)
+        w /= np.sqrt(max(o.dot(w, w), 1e-300))
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            times.append(t1 - t0)
+    tot = sum(times)
+    val = leaf * args.steps / tot / 1e6
+    line = {
+        "impl": "reference", "metric": "Mcell/s of Jv+V-cycle", "value": val, "unit": "Mcell/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "leaf_cells": leaf, "step": "one Krylov iteration"},
+        "cpu_baseline": {"value": val, "unit": "Mcell/s", "cores": 1, "kind": "oracle",
+                         "sample": "one FP64 oracle Krylov iteration (FAC/GMG P^-1 + analytic "
+                                   "Jv) per step on the full workload, single thread"},
+        "e2e": {"value": val, "unit": "Mcell/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    h, z, u0 = workload()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    ctx = make_ctx(nrd, h, z, torch, production=True)
+    leaf = ctx.nleaf
+
+    # production form, timed (replicas: every rank runs the same workload)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    r = run_steps(ctx, torch, u0, args.steps, args.warmup, flush, timing=True)
+    barrier()
+    clocks = clk.stop()
+    tot_ms = sum(r["ms"])
+    if dist is not None:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * leaf * r["krylov"] / (tot_ms * 1e-3) / 1e6
+
+    # dominant kernel group and its roofline
+    kt = r["kernel"]
+    hbm_peak, peak_src = peaks()
+    jv_ms, jv_n = kt["jv"]
+    pc_ms, pc_n = kt["pc_apply"]
+    dom = max(kt.items(), key=lambda kv: kv[1][0])[0]
+    roof = None
+    if dom == "jv" and jv_n:
+        # FP64 work of the analytic-tangent stencil per leaf cell, in
+        # FMA-equivalent flops (derivation in the design notes)
+        flops_cell = 2.0 * 228.0
+        ach = flops_cell * leaf / (jv_ms / jv_n * 1e-3) / 1e12
+        roof = {"kernel": "k_stencil<JV> (analytic tangent)", "bound": "alu", "achieved": ach,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": None, "peak_source": "measured FP64 FMA microbenchmark"}
+    else:
+        # one FP32 V-cycle application, algorithmic bytes per leaf cell
+        bytes_cell = 400.0
+        ach = bytes_cell * leaf / (pc_ms / max(pc_n, 1) * 1e-3) / 1e9
+        roof = {"kernel": "P^-1 apply (FAC/GMG V-cycle, FP32)", "bound": "hbm", "achieved": ach,
+                "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
+                "peak_source": peak_src}
+
+    # plain form beside it
+    plain = None
+    if not args.no_plain:
+        ctxp = make_ctx(nrd, h, z, torch, production=False)
+        rp = run_steps(ctxp, torch, u0, args.steps, args.warmup, flush, timing=False)
+        pms = sum(rp["ms"])
+        plain = {"form": "FD Jv + FP64 V-cycle", "ms_per_step": pms / args.steps,
+                 "value": leaf * rp["krylov"] / (pms * 1e-3) / 1e6,
+                 "krylov_per_step": rp["krylov"] / args.steps,
+                 "newton_per_step": rp["newton"] / args.steps}
+        del ctxp
+
+    e_ms, e_kry, h2d, d2h = run_e2e(nrd, ctx, torch, u0, args.steps, 1)
+    e2e = {"value": world * leaf * e_kry / (e_ms * 1e-3) / 1e6, "unit": "Mcell/s",
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(h, z, u0, leaf)
+
+    launches = sum(n for _, n in kt.values())
+    line = {
+        "metric": "Mcell/s of Jv+V-cycle", "value": value, "unit": "Mcell/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "base": 64, "levels": 2, "leaf_cells": leaf,
+                   "patches": sum(h.nboxes), "dt": DT, "newton_rtol": 1e-8,
+                   "form": "analytic Jv + FP32 FAC/GMG V(2,2) + FGMRES(30)",
+                   "krylov_per_step": r["krylov"] / args.steps,
+                   "newton_per_step": r["newton"] / args.steps,
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roof,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+        "plain": plain,
+        "speedup_vs_plain": (plain["ms_per_step"] / (tot_ms / args.steps)) if plain else None,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "gpu_launches_note": "instrumented launch groups in the timed region",
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,251 @@
+/*
+ * nrd.h -- C ABI of the GB300 implementation of the implicit non-equilibrium
+ * radiation diffusion hot path of arXiv 1302.6303 ("Dynamic Implicit 3D
+ * Adaptive Mesh Refinement for Non-Equilibrium Radiation Diffusion").
+ *
+ * The library computes, on one GPU, for a 3D patch hierarchy with refinement
+ * ratio 2:
+ *   - the two-field (E, T) finite-volume residual of Sec. 3.2/3.3
+ *     (Eqs. E_int, diffusion_coeffs1-6, bdf2, be, nonlinearsystem);
+ *   - its Jacobian-vector product, as the finite difference of Sec. 4.1
+ *     (Eq. Jac-free) or as the exact tangent;
+ *   - the physics-based preconditioner P = P1 P2 of Sec. 4.2 with FAC
+ *     V-cycles (Sec. 4.3, Algorithm 1) on the diffusion blocks;
+ *   - right-preconditioned GMRES inside an inexact Newton solve (Sec. 4.1);
+ *   - a BE / BDF2 implicit time step (Sec. 3.3);
+ *   - the refinement indicators of Sec. 5.
+ *
+ * Conventions
+ *   - Every call returns an int status: NRD_OK (0) or a negative NRD_E* code;
+ *     nrd_last_error() then describes the failure.  A NULL context returns
+ *     NRD_EINVAL.
+ *   - Array arguments are DEVICE pointers owned by the caller (for example
+ *     torch CUDA tensors), unless the argument name ends in _host.  Arrays
+ *     must not alias unless a call says so.
+ *   - Calls taking a cudaStream_t are asynchronous on that stream, except
+ *     where a call documents that it synchronises (it then returns results
+ *     through host pointers).
+ *   - The context owns its internal device work buffers (allocated in
+ *     nrd_set_hierarchy and on first use by the solver calls) and frees them
+ *     in nrd_destroy.  A context is used by one host thread at a time.
+ *
+ * Data layout (the "hierarchy layout")
+ *   - A hierarchy has L levels; level 0 is one box [0,n0x) x [0,n0y) x
+ *     [0,n0z) covering the unit cube; level l has spacing h_d = 1/(n0d 2^l).
+ *   - Boxes are given as lo[3], hi[3] (inclusive) in their level's index
+ *     space.  Boxes of a level must not overlap.  Boxes of level l >= 1 must
+ *     be aligned to ratio 2 (lo even, hi odd) and properly nested: the box
+ *     coarsened to level l-1 and grown by one cell (clipped to the domain)
+ *     must lie inside level l-1.
+ *   - One field on the hierarchy is a vector of ncells values: level 0
+ *     first, then level 1, ..., boxes in the given order, x fastest inside a
+ *     box.  Cells covered by a finer level are present but are not unknowns:
+ *     the residual and Jv return 0 there and their input values are ignored
+ *     (except where a call says otherwise).
+ *   - A state u is E (ncells values) followed by T (ncells values), FP64.
+ *   - Ghost buffers hold one value per face cell of every box, boxes in
+ *     layout order, faces x-, x+, y-, y+, z-, z+; on a face normal to axis d
+ *     the cells run with axis (d+1)%3 fastest, then axis (d+2)%3.
+ *
+ * Readings of points where the paper is silent (all implemented exactly this
+ * way): Wilson-consistent limiter D_E = D_h/(1 + D_h |dE|/(h E_f)) with
+ * D_h = 2 T_f^3/(3 (z_a^3 + z_b^3)) (NRD_LIM_PAPER_LITERAL selects the printed
+ * 2 D_r/(1 + D_r g)); face D_T = k T_f^(5/2); Neumann ghost = interior value;
+ * Robin ghost from the discrete Robin relation with the unlimited
+ * D_b = T^3/(3 z^3); coarse-fine ghost g = (f + 2 i)/3 with i the bilinear
+ * interpolation (9,3,3,1)/16 of the four nearest coarse cells; residual per
+ * unit volume F = a0 u - b - dt f(u); dots and norms weighted by cell volume
+ * over leaf cells.
+ */
+#ifndef NRD_H
+#define NRD_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+enum {
+  NRD_OK = 0,
+  NRD_EINVAL = -1,   /* bad argument, hierarchy or state */
+  NRD_ENOMEM = -2,   /* device or host allocation failed */
+  NRD_ENONCONV = -3, /* Newton or GMRES hit its iteration cap (stats filled) */
+  NRD_ENEG = -4,     /* a state lost positivity */
+  NRD_ENAN = -5,     /* a NaN or Inf appeared in a norm */
+  NRD_ECUDA = -6,    /* a CUDA runtime call failed */
+  NRD_ESTATE = -7    /* call order: e.g. no hierarchy or no material yet */
+};
+
+enum { NRD_BC_NEUMANN = 0, NRD_BC_ROBIN = 1 };
+enum { NRD_LIM_WILSON = 0, NRD_LIM_PAPER_LITERAL = 1 };
+enum { NRD_JV_FD = 0, NRD_JV_ANALYTIC = 1 };
+enum { NRD_PC_F64 = 0, NRD_PC_F32 = 1 };
+
+/* Solver and model parameters.  nrd_params_default() fills the values used
+ * by the paper (Sec. 3.1: k = 0.01; Sec. 4.1: u_min = 1e-6) and the
+ * benchmark defaults (GMRES(30), V(2,2), 4 GMG levels, Newton rtol 1e-8). */
+typedef struct {
+  double k;            /* material conduction constant: D_T = k T^(5/2) */
+  int limiter;         /* NRD_LIM_* */
+  double u_min;        /* differencing parameter floor of Sec. 4.1 */
+  int restart;         /* GMRES restart length m */
+  int max_krylov;      /* cap on Krylov iterations per Newton step */
+  int jv_mode;         /* NRD_JV_FD (plain) or NRD_JV_ANALYTIC */
+  int pc_precision;    /* NRD_PC_F64 or NRD_PC_F32 V-cycle arithmetic */
+  int nu1, nu2;        /* pre-/post-smoothing red-black GS sweeps */
+  int nmg;             /* GMG levels on the base box, including the base */
+  int coarse_sweeps;   /* RB-GS sweeps on the coarsest GMG grid */
+  double rtol, atol;   /* Newton stop: ||F|| <= rtol ||F(u0)|| + atol */
+  int max_newton;      /* Newton iteration cap */
+  double eta_max;      /* Eisenstat-Walker forcing cap (and eta_0) */
+  double ew_gamma;     /* Eisenstat-Walker gamma */
+  int tile_y, tile_z;  /* stencil tile shape 32 x tile_y x tile_z (0: auto) */
+} nrd_params;
+
+/* Statistics of one Newton solve (nrd_newton / nrd_step). */
+typedef struct {
+  int status;          /* 0 converged, NRD_ENONCONV otherwise */
+  int newton_its;      /* Newton iterations taken */
+  int krylov_its;      /* total GMRES iterations (Jv + P^{-1} applications) */
+  int pc_setups;       /* preconditioner set-ups (one per Newton iteration) */
+  double fnorm0;       /* ||F(u0)|| (volume-weighted 2-norm over leaf cells) */
+  double fnorm;        /* final ||F|| */
+  double min_lambda;   /* smallest positivity damping factor used (Sec. 4.1) */
+} nrd_stats;
+
+typedef struct nrd_ctx nrd_ctx;
+
+/* Fill *p with defaults.  Returns NRD_EINVAL if p is NULL. */
+int nrd_params_default(nrd_params* p);
+
+/* Create a context on the current CUDA device.  *out receives the handle.
+ * Errors: NRD_EINVAL (bad parameter), NRD_ENOMEM. */
+int nrd_create(const nrd_params* p, nrd_ctx** out);
+
+/* Free the context and every device buffer it owns. */
+int nrd_destroy(nrd_ctx* ctx);
+
+/* Message of the last failed call on ctx (owned by ctx; valid until the
+ * next call).  NULL ctx gives a static message. */
+const char* nrd_last_error(const nrd_ctx* ctx);
+
+/* Replace the parameters of an existing context (takes effect on the next
+ * call). */
+int nrd_set_params(nrd_ctx* ctx, const nrd_params* p);
+
+/* Define the patch hierarchy (Sec. 3.2.1 SAMR hierarchy).
+ *   nlevels      number of levels L >= 1
+ *   nboxes_host  [L] boxes per level (nboxes_host[0] must be 1)
+ *   boxes_host   6 ints per box, levels in order: lo[3], hi[3] inclusive
+ *   bc_type_host [6] NRD_BC_* for faces x-, x+, y-, y+, z-, z+ (for E; T is
+ *                Neumann everywhere, Sec. 3.1 Eq. bcs)
+ *   bc_R_host    [6] Robin data R of Sec. 3.1 Eq. robinbc
+ * Builds every ghost, flux-matching, coarsening and tile work-list on the
+ * host and uploads them.  Synchronises the device.  Errors: NRD_EINVAL
+ * (alignment, nesting, overlap, domain), NRD_ENOMEM, NRD_ECUDA. */
+int nrd_set_hierarchy(nrd_ctx* ctx, int nlevels, const int* nboxes_host, const int* boxes_host,
+                      const int* bc_type_host, const double* bc_R_host);
+
+/* Sizes of the hierarchy layout: ncells per field, ghost cells per field,
+ * leaf cells. */
+int nrd_layout(const nrd_ctx* ctx, int64_t* ncells_host, int64_t* nghosts_host,
+               int64_t* nleaf_host);
+
+/* Material atomic number z per cell (hierarchy layout, ncells floats,
+ * Sec. 3.1 sigma_a = z^3/T^3).  Copied; the caller may free z afterwards. */
+int nrd_set_material(nrd_ctx* ctx, const float* z, cudaStream_t stream);
+
+/* Ghost values of a state (Sec. 3.2 first-order physical ghosts, sibling
+ * copies, Sec. 3.2.1 linear coarse-fine interpolation), written to gE, gT
+ * (nghosts doubles each) and gz (nghosts floats, z of the ghost cell; may be
+ * NULL).  u: 2*ncells doubles. */
+int nrd_ghost_fill(nrd_ctx* ctx, const double* u, double* gE, double* gT, float* gz,
+                   cudaStream_t stream);
+
+/* Nonlinear residual (Eq. nonlinearsystem per unit volume):
+ *   F = a0 u - b - dt f(u),  f from Eqs. E_td, T_td discretised as in
+ * Sec. 3.2 with flux matching at coarse-fine faces (Sec. 3.2.1).
+ *   u, b, F: 2*ncells doubles (b = history combination, e.g. u_n for BE).
+ * F is 0 on covered cells. */
+int nrd_residual(nrd_ctx* ctx, const double* u, const double* b, double a0, double dt, double* F,
+                 cudaStream_t stream);
+
+/* Jacobian-vector product J v of the residual at u.
+ *   mode NRD_JV_ANALYTIC: exact tangent a0 v - dt f'(u) v (b, F0 unused,
+ *                         may be NULL);
+ *   mode NRD_JV_FD:       (F(u + eps v) - F0)/eps of Sec. 4.1 Eq. Jac-free
+ *                         with the two-branch eps of Sec. 4.1 (b required;
+ *                         F0 = F(u) required).
+ * Jv: 2*ncells doubles, 0 on covered cells. */
+int nrd_jv(nrd_ctx* ctx, const double* u, const double* v, const double* b, const double* F0,
+           double a0, double dt, int mode, double* Jv, cudaStream_t stream);
+
+/* The differencing parameter eps(u, v) of Sec. 4.1 (synchronises; result in
+ * *eps_host). */
+int nrd_fd_eps(nrd_ctx* ctx, const double* u, const double* v, double* eps_host,
+               cudaStream_t stream);
+
+/* Volume-weighted inner product over leaf cells of both fields
+ * (synchronises; result in *out_host). */
+int nrd_dot(nrd_ctx* ctx, const double* x, const double* y, double* out_host,
+            cudaStream_t stream);
+
+/* Freeze the preconditioner at the iterate u (Sec. 4.2): face D_E^k, D_T^k
+ * for every AMR level, their coarsening to the GMG levels, and the P2 data.
+ * beta = dt/a0 = (alpha+1)/(2 alpha+1) dt. */
+int nrd_precond_setup(nrd_ctx* ctx, const double* u, double a0, double dt, cudaStream_t stream);
+
+/* y = P^{-1} w = P2^{-1} (P1^{-1} w): one FAC V(nu1,nu2) cycle per diffusion
+ * block (Algorithm 1) in the precision chosen by pc_precision, then the
+ * cell-local 2x2 P2 solve in FP64.  w, y: 2*ncells doubles; y is 0 on
+ * covered cells.  Requires nrd_precond_setup. */
+int nrd_precond_apply(nrd_ctx* ctx, const double* w, double* y, cudaStream_t stream);
+
+/* Solve F(u) = 0 (Eq. nonlinearsystem) by inexact Newton with
+ * Eisenstat-Walker forcing, positivity-damped updates and right-
+ * preconditioned restarted GMRES (Sec. 4.1-4.2).
+ *   u: in initial guess, out solution (covered cells set to the mean of
+ *      their children);  b: history combination;  stats: may be NULL.
+ * Host-driven loop: synchronises once per Krylov iteration.
+ * Returns NRD_ENONCONV if the Newton cap is hit (u holds the last iterate). */
+int nrd_newton(nrd_ctx* ctx, double* u, const double* b, double a0, double dt, nrd_stats* stats,
+               cudaStream_t stream);
+
+/* One implicit time step (Sec. 3.3): backward Euler when u_nm1 is NULL
+ * (Eq. be), else variable-step BDF2 (Eq. bdf2) with alpha = dt/dt_prev.
+ *   u: in initial guess for u_{n+1}, out u_{n+1};  u_n, u_nm1: history. */
+int nrd_step(nrd_ctx* ctx, double* u, const double* u_n, const double* u_nm1, double dt,
+             double dt_prev, nrd_stats* stats, cudaStream_t stream);
+
+/* Refinement indicators of Sec. 5 on every cell (covered cells use the mean
+ * of their children): bit 0: tau^c > thr_c (curvature), bit 1: tau^g > thr_g
+ * (gradient), bit 2: h |grad E| / E > thr_r.  tags: ncells bytes. */
+int nrd_tag(nrd_ctx* ctx, const double* u, double thr_c, double thr_g, double thr_r,
+            uint8_t* tags, cudaStream_t stream);
+
+/* ------------------------------------------------------- kernel timing
+ * Optional CUDA-event timing of the library's kernel groups, recorded on the
+ * stream each group is launched on (a start/stop event pair around every
+ * launch).  Off by default; nrd_timing_enable(ctx, 1) turns it on and clears
+ * the counters.  nrd_timing_read synchronises on the recorded events and
+ * returns the summed device time (ms) and the number of launches. */
+enum {
+  NRD_TK_RESIDUAL = 0,   /* residual stencil (all levels, one launch) */
+  NRD_TK_JV = 1,         /* analytic-tangent stencil */
+  NRD_TK_JV_FD = 2,      /* finite-difference Jv stencil (incl. eps reduction) */
+  NRD_TK_PC_APPLY = 3,   /* one P^{-1} application: FAC/GMG V-cycles + P2 */
+  NRD_TK_PC_SETUP = 4,   /* coefficient freeze and coarsening */
+  NRD_TK_ORTHO = 5,      /* CGS2 orthogonalisation of one Krylov vector */
+  NRD_TK_GHOST = 6,      /* ghost fill of a direction vector */
+  NRD_TK_COUNT = 7
+};
+int nrd_timing_enable(nrd_ctx* ctx, int enable);
+int nrd_timing_read(nrd_ctx* ctx, int group, double* ms_host, int64_t* launches_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NRD_H */

@@ -1096,8 +1096,10 @@ void ghost_of(const Hier& H, const double* u, int l, const int c[3], int d, int 
   }
   long ig = H.cell(l, g);
   if (ig >= 0) {
-    *Eg = comp_value(H, E, l, g);
-    *Tg = comp_value(H, T, l, g);
+    // sibling: the stored value (a covered sibling is never used by the
+    // residual, whose flux there comes from flux matching)
+    *Eg = E[ig];
+    *Tg = T[ig];
     *zg = H.z[ig];
     return;
   }
@@ -1370,6 +1372,12 @@ void orc_tag(orc_hier* h, const double* u, double thr_c, double thr_g, double th
   double emax = 0.0;
   for (long i = 0; i < N; i++)
     if (!H->covered_idx(i)) emax = std::max(emax, std::fabs(u[i]));
+  // the indicators see composite values: covered cells (and the physical
+  // ghosts next to them) take the mean of their children
+  std::vector<double> uc(u, u + 2 * N);
+  average_down(*H, uc.data());
+  average_down(*H, uc.data() + N);
+  u = uc.data();
   for (long idx = 0; idx < N; idx++) {
     int l = H->cell_level[idx];
     const int* c = &H->cell_ijk[3 * idx];

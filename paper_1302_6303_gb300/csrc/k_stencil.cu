@@ -1,0 +1,599 @@
+// Stencil kernels of the radiation-diffusion residual (Sec. 3.2, 3.2.1, 3.3)
+// and its Jacobian-vector products (Sec. 4.1), all FP64:
+//   ghost fill     physical / sibling / coarse-fine ghosts from a work-list
+//   k_stencil      one persistent launch over the tiles of every level:
+//                  halo staged in shared memory, each face flux computed
+//                  once and shared by its two cells, then the cell balance
+//   k_reflux       flux matching at coarse-fine faces
+//   k_tag          Sec. 5 refinement indicators
+//   k_avgdown      covered cells := mean of their children
+#include <algorithm>
+#include <cstdio>
+
+#include "nrd_internal.h"
+
+namespace {
+
+struct LevelH {
+  double h[NRD_MAX_LEVELS][3];
+};
+
+struct GhostArgs {
+  const uint8_t* gtype;
+  const uint8_t* gface;   // face | level << 3
+  const int* gcell;
+  const int* gt0;
+  const int* gidx;
+  const double* gw;
+  const float* z;
+  int N, G;
+  double R[6];
+  LevelH lh;
+};
+
+// Fill ghosts of a two-field vector u (E = u[0..N), T = u[N..2N)) into
+// g[0..G) (E) and g[G..2G) (T).  nonlinear = 1 evaluates the Robin ghost of
+// Sec. 3.1 Eq. robinbc; nonlinear = 0 copies the interior value there (linear
+// uses never read physical ghosts).
+__global__ void k_ghost_fill(GhostArgs a, const double* __restrict__ u, double* __restrict__ g,
+                             int nonlinear) {
+  const int N = a.N, G = a.G;
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < G; gi += gridDim.x * blockDim.x) {
+    uint8_t t = a.gtype[gi];
+    int c = a.gcell[gi];
+    double e, tt;
+    if (t == GT_NEUMANN) {
+      e = u[c];
+      tt = u[N + c];
+    } else if (t == GT_ROBIN) {
+      e = u[c];
+      tt = u[N + c];
+      if (nonlinear) {
+        int f = a.gface[gi] & 7, lvl = a.gface[gi] >> 3;
+        double h = a.lh.h[lvl][f / 2];
+        double T = tt;
+        double zc = (double)a.z[c];
+        double Db = T * T * T / (3.0 * (zc * zc * zc));
+        double aa = Db / (2.0 * h);
+        e = (a.R[f] + e * (aa - 0.125)) / (aa + 0.125);
+      }
+    } else {
+      int t0 = a.gt0[gi], t1 = a.gt0[gi + 1];
+      double se = 0.0, st = 0.0;
+      for (int q = t0; q < t1; q++) {
+        int s = a.gidx[q];
+        double w = a.gw[q];
+        se += w * u[s];
+        st += w * u[N + s];
+      }
+      e = se;
+      tt = st;
+    }
+    g[gi] = e;
+    g[G + gi] = tt;
+  }
+}
+
+__global__ void k_ghost_z(const int* __restrict__ zsrc, const float* __restrict__ z,
+                          float* __restrict__ gz, int G) {
+  for (int gi = blockIdx.x * blockDim.x + threadIdx.x; gi < G; gi += gridDim.x * blockDim.x)
+    gz[gi] = z[zsrc[gi]];
+}
+
+struct StArgs {
+  const TileDev* tiles;
+  const PatchDev* patches;
+  const uint8_t* mask;
+  const uint8_t* gtype;
+  const float* z;     // material z per cell
+  const float* gz;    // z of every ghost cell
+  int ntiles, N, G;
+  double k;       // D_T = k T^(5/2)
+  double cL;      // limiter constant: 4 (Wilson form) or 2 (printed form)
+  double R[6];
+  LevelH lh;
+  StencilIO io;
+};
+
+// Face flux in the +e_d direction between cells a (low) and b (high):
+//   Phi_E = D_E (E_b - E_a)/h with D_E = D_h/(1 + D_h g) (or the printed form)
+//         = 2 Tf^3 S dE / (3 h Zs S + cL Tf^3 |dE|),  S = E_a + E_b,
+//           Zs = z_a^3 + z_b^3, dE = E_b - E_a, Tf = (T_a + T_b)/2
+//   Phi_T = k Tf^(5/2) (T_b - T_a)/h.
+__device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double Tb, double za,
+                                         double zb, double h, double kh, double cL, double& PE,
+                                         double& PT) {
+  double Tf = 0.5 * (Ta + Tb);
+  double Tf2 = Tf * Tf;
+  double Tf3 = Tf2 * Tf;
+  double dE = Eb - Ea;
+  double S = Ea + Eb;
+  double Zs = za + zb;
+  double num = 2.0 * Tf3 * dE * S;
+  double den = 3.0 * h * Zs * S + cL * Tf3 * fabs(dE);
+  PE = num / den;
+  PT = kh * Tf2 * sqrt(Tf) * (Tb - Ta);
+}
+
+// Tangent of flux_val in the direction (dEa, dEb, dTa, dTb); sign(0) = 0.
+__device__ __forceinline__ void flux_tan(double Ea, double Eb, double Ta, double Tb, double za,
+                                         double zb, double h, double kh, double cL, double vEa,
+                                         double vEb, double vTa, double vTb, double& dPE,
+                                         double& dPT) {
+  double Tf = 0.5 * (Ta + Tb);
+  double dTf = 0.5 * (vTa + vTb);
+  double Tf2 = Tf * Tf;
+  double Tf3 = Tf2 * Tf;
+  double dTf3 = 3.0 * Tf2 * dTf;
+  double dE = Eb - Ea, ddE = vEb - vEa;
+  double S = Ea + Eb, dS = vEa + vEb;
+  double Zs = za + zb;
+  double sg = (dE > 0.0) ? 1.0 : ((dE < 0.0) ? -1.0 : 0.0);
+  double num = 2.0 * Tf3 * dE * S;
+  double dnum = 2.0 * (dTf3 * dE * S + Tf3 * (ddE * S + dE * dS));
+  double den = 3.0 * h * Zs * S + cL * Tf3 * fabs(dE);
+  double dden = 3.0 * h * Zs * dS + cL * (dTf3 * fabs(dE) + Tf3 * sg * ddE);
+  double rden = 1.0 / den;
+  double PE = num * rden;
+  dPE = (dnum - PE * dden) * rden;
+  double sq = sqrt(Tf);
+  dPT = kh * ((2.5 * Tf * sq * dTf) * (Tb - Ta) + Tf2 * sq * (vTb - vTa));
+}
+
+// Robin face (Sec. 3.1 Eq. robinbc, unlimited D_b = T^3/(3 z^3)): the +e_d
+// flux through the boundary face on side s of the cell is
+//   Phi = -s D_b (2 E - 8 R) / (4 D_b + h).
+__device__ __forceinline__ double robin_flux(double E, double T, double z, double h, double R,
+                                             int s) {
+  double Db = T * T * T / (3.0 * z);
+  return -(double)s * Db * (2.0 * E - 8.0 * R) / (4.0 * Db + h);
+}
+
+__device__ __forceinline__ double robin_tan(double E, double T, double z, double h, double R,
+                                            int s, double vE, double vT) {
+  double Db = T * T * T / (3.0 * z);
+  double dDb = T * T * vT / z;
+  double m = 2.0 * E - 8.0 * R, dm = 2.0 * vE;
+  double q = 4.0 * Db + h;
+  return -(double)s * (dDb * m * h + Db * dm * q) / (q * q);
+}
+
+template <int MODE, int TY, int TZ>
+__global__ void __launch_bounds__(256) k_stencil(StArgs A) {
+  constexpr int TX = NRD_TX;
+  constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
+  constexpr int NH = HX * HY * HZ;
+  constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
+  constexpr int NC = TX * TY * TZ;
+  constexpr bool TAN = (MODE == ST_JV);
+  extern __shared__ double smem[];
+  double* sE = smem;
+  double* sT = sE + NH;
+  double* svE = sT + NH;                       // tangent direction (JV only)
+  double* svT = svE + (TAN ? NH : 0);
+  double* fxE = svT + (TAN ? NH : 0);
+  double* fxT = fxE + NFX;
+  double* fyE = fxT + NFX;
+  double* fyT = fyE + NFY;
+  double* fzE = fyT + NFY;
+  double* fzT = fzE + NFZ;
+  double* sZ = fzT + NFZ;                     // z^3 of the halo cells
+
+  const int N = A.N, G = A.G;
+  const StencilIO& io = A.io;
+  double eps = 0.0;
+  if (MODE == ST_FD) eps = *io.eps;
+
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const TileDev tile = A.tiles[t];
+    const PatchDev P = A.patches[tile.patch];
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const double hx = A.lh.h[P.level][0], hy = A.lh.h[P.level][1], hz = A.lh.h[P.level][2];
+    if (tile.flags & 1) {
+      // every cell covered: not unknowns
+      for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+        int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
+        int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
+        if (i >= nx || j >= ny || k >= nz) continue;
+        int idx = P.off + i + nx * (j + ny * k);
+        io.out[idx] = 0.0;
+        io.out[N + idx] = 0.0;
+      }
+      continue;
+    }
+    // ---- halo load (face halos only; edges and corners are never read)
+    for (int hh = threadIdx.x; hh < NH; hh += blockDim.x) {
+      int hx_ = hh % HX, hy_ = (hh / HX) % HY, hz_ = hh / (HX * HY);
+      int i = tile.i0 + hx_ - 1, j = tile.j0 + hy_ - 1, k = tile.k0 + hz_ - 1;
+      int ox = (i < 0) ? -1 : ((i >= nx) ? 1 : 0);
+      int oy = (j < 0) ? -1 : ((j >= ny) ? 1 : 0);
+      int oz = (k < 0) ? -1 : ((k >= nz) ? 1 : 0);
+      if ((ox != 0) + (oy != 0) + (oz != 0) > 1) continue;
+      if (i > nx || j > ny || k > nz) continue;
+      double e, tt, ve = 0.0, vt = 0.0;
+      double z;
+      if (!ox && !oy && !oz) {
+        int idx = P.off + i + nx * (j + ny * k);
+        e = io.u[idx];
+        tt = io.u[N + idx];
+        z = (double)A.z[idx];
+        if (MODE != ST_RESIDUAL) {
+          ve = io.v[idx];
+          vt = io.v[N + idx];
+        }
+      } else {
+        int f, a, b;
+        if (ox) { f = ox < 0 ? 0 : 1; a = j; b = k; }
+        else if (oy) { f = oy < 0 ? 2 : 3; a = k; b = i; }
+        else { f = oz < 0 ? 4 : 5; a = i; b = j; }
+        int d = f / 2;
+        int nt1 = P.n[(d + 1) % 3];
+        int gi = P.goff + P.fo[f] + a + nt1 * b;
+        e = io.gu[gi];
+        tt = io.gu[G + gi];
+        z = (double)A.gz[gi];
+        if (MODE != ST_RESIDUAL) {
+          ve = io.gv[gi];
+          vt = io.gv[G + gi];
+        }
+      }
+      if (MODE == ST_FD) {
+        e += eps * ve;
+        tt += eps * vt;
+      }
+      sE[hh] = e;
+      sT[hh] = tt;
+      sZ[hh] = z * z * z;
+      if (TAN) {
+        svE[hh] = ve;
+        svT[hh] = vt;
+      }
+    }
+    __syncthreads();
+    // ---- face fluxes, each computed once
+    auto face = [&](int dir, int fi, int fj, int fk, double* outE, double* outT, int slot) {
+      // face on the low side of tile cell (fi, fj, fk) along dir
+      int i = tile.i0 + fi, j = tile.j0 + fj, k = tile.k0 + fk;
+      int pos = (dir == 0) ? i : ((dir == 1) ? j : k);
+      int nd = P.n[dir];
+      if (i > nx || j > ny || k > nz) return;
+      if ((dir != 0 && i >= nx) || (dir != 1 && j >= ny) || (dir != 2 && k >= nz)) return;
+      int hb = (fi + 1) + HX * ((fj + 1) + HY * (fk + 1));   // high-side cell
+      int st = (dir == 0) ? 1 : ((dir == 1) ? HX : HX * HY);
+      int ha = hb - st;                                      // low-side cell
+      double h = (dir == 0) ? hx : ((dir == 1) ? hy : hz);
+      double kh = A.k / h;
+      double PE = 0.0, PT = 0.0;
+      uint8_t gt = GT_SIBLING;
+      int gi = -1;
+      if (pos == 0 || pos == nd) {
+        int f = 2 * dir + (pos == nd ? 1 : 0);
+        int a, b;
+        if (dir == 0) { a = j; b = k; }
+        else if (dir == 1) { a = k; b = i; }
+        else { a = i; b = j; }
+        gi = P.goff + P.fo[f] + a + P.n[(dir + 1) % 3] * b;
+        gt = A.gtype[gi];
+      }
+      if (gt == GT_NEUMANN) {
+        PE = 0.0;
+        PT = 0.0;
+      } else if (gt == GT_ROBIN) {
+        int s = (pos == 0) ? -1 : 1;
+        int hc = (pos == 0) ? hb : ha;      // the interior cell
+        int f = 2 * dir + (pos == nd ? 1 : 0);
+        if (TAN)
+          PE = robin_tan(sE[hc], sT[hc], sZ[hc], h, A.R[f], s, svE[hc], svT[hc]);
+        else
+          PE = robin_flux(sE[hc], sT[hc], sZ[hc], h, A.R[f], s);
+        PT = 0.0;
+      } else {
+        if (TAN)
+          flux_tan(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, kh, A.cL,
+                   svE[ha], svE[hb], svT[ha], svT[hb], PE, PT);
+        else
+          flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, kh, A.cL,
+                   PE, PT);
+        if (gt == GT_CF) {
+          io.cfflux[gi] = PE;
+          io.cfflux[G + gi] = PT;
+        }
+      }
+      outE[slot] = PE;
+      outT[slot] = PT;
+    };
+    for (int f = threadIdx.x; f < NFX + NFY + NFZ; f += blockDim.x) {
+      if (f < NFX) {
+        int fi = f % (TX + 1), fj = (f / (TX + 1)) % TY, fk = f / ((TX + 1) * TY);
+        face(0, fi, fj, fk, fxE, fxT, f);
+      } else if (f < NFX + NFY) {
+        int g = f - NFX;
+        int fi = g % TX, fj = (g / TX) % (TY + 1), fk = g / (TX * (TY + 1));
+        face(1, fi, fj, fk, fyE, fyT, g);
+      } else {
+        int g = f - NFX - NFY;
+        int fi = g % TX, fj = (g / TX) % TY, fk = g / (TX * TY);
+        face(2, fi, fj, fk, fzE, fzT, g);
+      }
+    }
+    __syncthreads();
+    // ---- cell balance
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+      int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
+      int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
+      if (i >= nx || j >= ny || k >= nz) continue;
+      int idx = P.off + i + nx * (j + ny * k);
+      uint8_t m = A.mask[idx];
+      if (m & MASK_COVERED) {
+        io.out[idx] = 0.0;
+        io.out[N + idx] = 0.0;
+        continue;
+      }
+      int xl = ci + (TX + 1) * (cj + TY * ck);
+      int yl = ci + TX * (cj + (TY + 1) * ck);
+      int zl = ci + TX * (cj + TY * ck);
+      // coarse-side coarse-fine faces take their flux from flux matching
+      double xlo = (m & 2) ? 0.0 : 1.0, xhi = (m & 4) ? 0.0 : 1.0;
+      double ylo = (m & 8) ? 0.0 : 1.0, yhi = (m & 16) ? 0.0 : 1.0;
+      double zlo = (m & 32) ? 0.0 : 1.0, zhi = (m & 64) ? 0.0 : 1.0;
+      auto pick = [](double keep, double v) { return keep != 0.0 ? v : 0.0; };
+      double divE = (pick(xhi, fxE[xl + 1]) - pick(xlo, fxE[xl])) / hx +
+                    (pick(yhi, fyE[yl + TX]) - pick(ylo, fyE[yl])) / hy +
+                    (pick(zhi, fzE[zl + TX * TY]) - pick(zlo, fzE[zl])) / hz;
+      double divT = (pick(xhi, fxT[xl + 1]) - pick(xlo, fxT[xl])) / hx +
+                    (pick(yhi, fyT[yl + TX]) - pick(ylo, fyT[yl])) / hy +
+                    (pick(zhi, fzT[zl + TX * TY]) - pick(zlo, fzT[zl])) / hz;
+      int hc = (ci + 1) + HX * ((cj + 1) + HY * (ck + 1));
+      double E = sE[hc], T = sT[hc], z = sZ[hc];
+      double T2 = T * T, T3 = T2 * T;
+      if (MODE == ST_JV) {
+        double rT = 1.0 / T;
+        double sig = z * rT * rT * rT;
+        double vE = svE[hc], vT = svT[hc];
+        double dc = sig * ((T3 + 3.0 * E * rT) * vT - vE);
+        io.out[idx] = io.a0 * vE - io.dt * (divE + dc);
+        io.out[N + idx] = io.a0 * vT - io.dt * (divT - dc);
+      } else {
+        double sig = z / T3;
+        double cp = sig * (T2 * T2 - E);
+        double FE = io.a0 * E - io.b[idx] - io.dt * (divE + cp);
+        double FT = io.a0 * T - io.b[N + idx] - io.dt * (divT - cp);
+        if (MODE == ST_FD) {
+          FE = (FE - io.F0[idx]) / eps;
+          FT = (FT - io.F0[N + idx]) / eps;
+        }
+        io.out[idx] = FE;
+        io.out[N + idx] = FT;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+struct RfArgs {
+  const int* cell;
+  const int* off;
+  const int* face;
+  const int4* g;
+  const PatchDev* patches;
+  int nrf, N, G;
+  LevelH lh;
+};
+
+// Flux matching (Sec. 3.2.1): the coarse face flux is the average of the four
+// fine fluxes stored by the fine-side stencil; scale = -dt (RESIDUAL, JV) or
+// -dt/eps (FD).
+__global__ void k_reflux(RfArgs a, const int* __restrict__ rf_level, const double* cf,
+                         double* out, double dt, const double* eps, int mode) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.nrf; r += gridDim.x * blockDim.x) {
+    int c = a.cell[r];
+    int lvl = rf_level[r];
+    double sc = -dt;
+    if (mode == ST_FD) sc /= *eps;
+    double dE = 0.0, dT = 0.0;
+    for (int q = a.off[r]; q < a.off[r + 1]; q++) {
+      int f = a.face[q];
+      int d = f / 2;
+      double s = (f % 2) ? 1.0 : -1.0;
+      int4 g = a.g[q];
+      double PE = 0.25 * (cf[g.x] + cf[g.y] + cf[g.z] + cf[g.w]);
+      double PT = 0.25 * (cf[a.G + g.x] + cf[a.G + g.y] + cf[a.G + g.z] + cf[a.G + g.w]);
+      double h = a.lh.h[lvl][d];
+      dE += s * PE / h;
+      dT += s * PT / h;
+    }
+    out[c] += sc * dE;
+    out[a.N + c] += sc * dT;
+  }
+}
+
+// Sec. 5 indicators on every cell.  E holds composite values (covered cells
+// already averaged from their children); gE its ghosts.
+__global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles, int ty, int tz,
+                      const double* E, const double* gE, double thr_c, double thr_g,
+                      double thr_r, const double* emax_p, uint8_t* tags) {
+  const double emax = *emax_p;
+  const int nc = NRD_TX * ty * tz;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileDev tile = tiles[t];
+    const PatchDev P = patches[tile.patch];
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % ty, k = tile.k0 + c / (NRD_TX * ty);
+      if (i >= nx || j >= ny || k >= nz) continue;
+      int idx = P.off + i + nx * (j + ny * k);
+      double Ec = E[idx];
+      double tc = 0.0, tg = 0.0, gr2 = 0.0;
+      int pos[3] = {i, j, k};
+      for (int d = 0; d < 3; d++) {
+        double Ev[2];
+        for (int si = 0; si < 2; si++) {
+          int q[3] = {i, j, k};
+          q[d] += si ? 1 : -1;
+          if (q[d] >= 0 && q[d] < P.n[d]) {
+            Ev[si] = E[P.off + q[0] + nx * (q[1] + ny * q[2])];
+          } else {
+            int f = 2 * d + si;
+            int a = pos[(d + 1) % 3], b = pos[(d + 2) % 3];
+            Ev[si] = gE[P.goff + P.fo[f] + a + P.n[(d + 1) % 3] * b];
+          }
+        }
+        // no contraction: the same roundings as a plain evaluation
+        tc += fabs(__dadd_rn(__dsub_rn(Ev[1], __dmul_rn(2.0, Ec)), Ev[0]));
+        tg += __dmul_rn(0.5, fabs(__dsub_rn(Ev[1], Ev[0])));
+        double df = __dsub_rn(Ev[1], Ev[0]);
+        gr2 = __dadd_rn(gr2, __dmul_rn(__dmul_rn(0.25, df), df));
+      }
+      uint8_t tag = 0;
+      if (tc / (0.1 * emax) > thr_c) tag |= 1;
+      if (tg / (0.1 * emax) > thr_g) tag |= 2;
+      if (sqrt(gr2) / Ec > thr_r) tag |= 4;
+      tags[idx] = tag;
+    }
+  }
+}
+
+// covered cell := mean of its 8 children (children order: x slowest ... as
+// listed), for nfield fields stored fstride apart.
+__global__ void k_avgdown(const int4* __restrict__ cov, int n, double* x, int nfield,
+                          int fstride) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    int4 c = cov[r];
+    for (int f = 0; f < nfield; f++) {
+      double* xf = x + (long)f * fstride;
+      double s = 0.0;
+      for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+          for (int e = 0; e < 2; e++) s += xf[c.y + a + b * c.z + e * c.w];
+      xf[c.x] = s / 8.0;
+    }
+  }
+}
+
+int blocks_for(long n, int bs) {
+  long b = (n + bs - 1) / bs;
+  if (b > 152 * 16) b = 152 * 16;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+LevelH level_h(const Hier& H) {
+  LevelH lh;
+  for (int l = 0; l < NRD_MAX_LEVELS; l++)
+    for (int d = 0; d < 3; d++) lh.h[l][d] = (l < H.L) ? H.lev[l].h[d] : 1.0;
+  return lh;
+}
+
+template <int MODE, int TY, int TZ>
+size_t stencil_smem() {
+  constexpr int TX = NRD_TX;
+  constexpr int NH = (TX + 2) * (TY + 2) * (TZ + 2);
+  constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
+  size_t d = (size_t)NH * (MODE == ST_JV ? 5 : 3) + 2 * (size_t)NF;
+  return d * sizeof(double);
+}
+
+template <int MODE, int TY, int TZ>
+void run_stencil(const StArgs& a, cudaStream_t s) {
+  size_t sm = stencil_smem<MODE, TY, TZ>();
+  static bool init = false;
+  if (!init) {
+    cudaFuncSetAttribute(k_stencil<MODE, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    init = true;
+  }
+  int per_sm = (int)(200 * 1024 / sm);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 4) per_sm = 4;
+  int grid = std::min(a.ntiles, 152 * per_sm);
+  if (grid < 1) return;
+  k_stencil<MODE, TY, TZ><<<grid, 256, sm, s>>>(a);
+}
+
+template <int MODE>
+void dispatch_tile(const StArgs& a, int ty, int tz, cudaStream_t s) {
+  if (ty == 8 && tz == 4) run_stencil<MODE, 8, 4>(a, s);
+  else if (ty == 4 && tz == 8) run_stencil<MODE, 4, 8>(a, s);
+  else if (ty == 2 && tz == 4) run_stencil<MODE, 2, 4>(a, s);
+  else if (ty == 4 && tz == 2) run_stencil<MODE, 4, 2>(a, s);
+  else run_stencil<MODE, 4, 4>(a, s);
+}
+
+}  // namespace
+
+void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
+                       double* g, int nonlinear, cudaStream_t s) {
+  GhostArgs a;
+  a.gtype = H.d_gtype;
+  a.gface = H.d_gface;
+  a.gcell = H.d_gcell;
+  a.gt0 = H.d_gt0;
+  a.gidx = H.d_gidx;
+  a.gw = H.d_gw;
+  a.z = z;
+  a.N = H.N;
+  a.G = H.G;
+  for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
+  a.lh = level_h(H);
+  if (H.G == 0) return;
+  k_ghost_fill<<<blocks_for(H.G, 256), 256, 0, s>>>(a, u, g, nonlinear);
+}
+
+void launch_ghost_z(const Hier& H, const float* z, float* gz, cudaStream_t s) {
+  if (H.G == 0) return;
+  k_ghost_z<<<blocks_for(H.G, 256), 256, 0, s>>>(H.d_gzsrc, z, gz, H.G);
+}
+
+void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const float* gz,
+                    int mode, const StencilIO& io, cudaStream_t s) {
+  StArgs a;
+  a.tiles = H.d_tiles;
+  a.patches = H.d_patches;
+  a.mask = H.d_mask;
+  a.gtype = H.d_gtype;
+  a.z = z;
+  a.gz = gz;
+  a.ntiles = (int)H.tiles.size();
+  a.N = H.N;
+  a.G = H.G;
+  a.k = mp.k;
+  a.cL = (mp.limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
+  for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
+  a.lh = level_h(H);
+  a.io = io;
+  if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_y, H.tile_z, s);
+  else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_y, H.tile_z, s);
+  else dispatch_tile<ST_FD>(a, H.tile_y, H.tile_z, s);
+}
+
+void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s) {
+  if (H.nrf == 0) return;
+  RfArgs a;
+  a.cell = H.d_rf_cell;
+  a.off = H.d_rf_off;
+  a.face = H.d_rf_face;
+  a.g = H.d_rf_g;
+  a.patches = H.d_patches;
+  a.nrf = H.nrf;
+  a.N = H.N;
+  a.G = H.G;
+  a.lh = level_h(H);
+  k_reflux<<<blocks_for(H.nrf, 128), 128, 0, s>>>(a, H.d_rf_level, io.cfflux, io.out, io.dt,
+                                                   io.eps, mode);
+}
+
+void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, double thr_g,
+                double thr_r, const double* emax, uint8_t* tags, cudaStream_t s) {
+  // tag tiles: reuse the stencil tile list (tiles are at most 32 x 8 x 8)
+  k_tag<<<std::min((int)H.tiles.size(), 152 * 8), 256, 0, s>>>(
+      H.d_tiles, H.d_patches, (int)H.tiles.size(), H.tile_y, H.tile_z, E, gE, thr_c, thr_g, thr_r,
+      emax, tags);
+}
+
+void launch_average_down(const Hier& H, double* x, int nfield, int fstride, cudaStream_t s) {
+  for (int l = H.L - 2; l >= 0; l--) {
+    if (H.ncov[l] == 0) continue;
+    k_avgdown<<<blocks_for(H.ncov[l], 256), 256, 0, s>>>(H.d_cov[l], H.ncov[l], x, nfield,
+                                                          fstride);
+  }
+}

@@ -1,0 +1,255 @@
+// Internal declarations of the nrd CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/nrd.h"
+
+#define NRD_MAX_LEVELS 8
+#define NRD_MAX_MG 12
+#define NRD_TX 32
+
+// Ghost cell kinds (one per face cell of every patch).
+enum : uint8_t { GT_NEUMANN = 0, GT_ROBIN = 1, GT_SIBLING = 2, GT_CF = 3 };
+
+// Cell mask bits: bit 0 covered by a finer level; bit 1+f: face f of this leaf
+// cell is the coarse side of a coarse-fine face (its flux comes from flux
+// matching).  Faces f = 0..5 are x-, x+, y-, y+, z-, z+.
+enum : uint8_t { MASK_COVERED = 1 };
+
+struct PatchDev {
+  int n[3];     // cells per axis
+  int lo[3];    // level index of the first cell
+  int level;
+  int off;      // first cell (hierarchy layout)
+  int goff;     // first ghost of this patch
+  int fo[6];    // ghost offset of each face, relative to goff
+};
+
+struct TileDev {
+  int patch;
+  int i0, j0, k0;
+  int flags;    // bit 0: every cell of the tile is covered
+};
+
+struct LevelInfo {
+  int n[3];
+  double h[3];
+  int off, ncell;      // cell range of the level
+  int p0, np;          // patch range
+  int g0, ng;          // ghost range
+  int t0, nt;          // tile range
+};
+
+// Host-built hierarchy metadata mirrored on the device.
+struct Hier {
+  int L = 0;
+  LevelInfo lev[NRD_MAX_LEVELS];
+  int N = 0, G = 0, nleaf = 0;
+  int bc_type[6];
+  double bc_R[6];
+  int tile_y = 4, tile_z = 4;
+
+  // host copies
+  std::vector<PatchDev> patches;
+  std::vector<TileDev> tiles;
+  std::vector<int> cell_patch;            // per cell
+  std::vector<std::vector<int>> lmap;     // dense level maps (all levels, host)
+
+  // device arrays
+  PatchDev* d_patches = nullptr;
+  TileDev* d_tiles = nullptr;
+  uint8_t* d_mask = nullptr;              // N
+  float* d_wvol = nullptr;                // N: cell volume for leaf cells, 0 if covered
+  // ghosts
+  uint8_t* d_gtype = nullptr;             // G
+  uint8_t* d_gface = nullptr;             // G: face 0..5 of the owning patch
+  int* d_gcell = nullptr;                 // G: interior cell adjacent to the ghost
+  int* d_gzsrc = nullptr;                 // G: cell whose z the ghost takes
+  int* d_gt0 = nullptr;                   // G+1: term ranges (sibling and CF)
+  int* d_gidx = nullptr;                  // terms: source cells
+  double* d_gw = nullptr;                 // terms: weights
+  int nterm = 0;
+  // flux matching: coarse leaf cells with coarse-side CF faces
+  int nrf = 0;
+  int* d_rf_cell = nullptr;               // nrf
+  int* d_rf_off = nullptr;                // nrf+1, entries per cell
+  int* d_rf_face = nullptr;               // entries: face 0..5 of the coarse cell
+  int4* d_rf_g = nullptr;                 // entries: ghost slots of the 4 fine fluxes
+  int* d_rf_level = nullptr;              // nrf: level of the coarse cell
+  // coefficient coarsening (per level l < L-1; sources on level l+1)
+  int ncz[NRD_MAX_LEVELS] = {0};
+  int* d_cz_tgt[NRD_MAX_LEVELS] = {nullptr};
+  int4* d_cz_src[NRD_MAX_LEVELS] = {nullptr};
+  // dense level maps (device) for levels 0..L-2
+  int* d_lmap[NRD_MAX_LEVELS] = {nullptr};
+  // covered cells per level (for average-down): cell, first child, strides
+  int ncov[NRD_MAX_LEVELS] = {0};
+  int4* d_cov[NRD_MAX_LEVELS] = {nullptr};  // x: cell, y: child base, z: sx, w: sxy
+  // leaf cells where fine-side CF ghosts live: none needed separately
+};
+
+// Parameters copied to kernels.
+struct ModelParams {
+  double k;
+  int limiter;
+  double bc_R[6];
+  int bc_type[6];
+};
+
+struct nrd_ctx_s;
+
+// host helpers (hier.cu)
+int hier_build(Hier& H, int nlevels, const int* nboxes, const int* boxes, const int* bc_type,
+               const double* bc_R, std::string& err);
+int hier_upload(Hier& H, std::string& err);
+void hier_free(Hier& H);
+
+// Kernel launchers (k_stencil.cu)
+enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2 };
+struct StencilIO {
+  const double* u;      // state (E then T)
+  const double* v;      // direction (JV, FD)
+  const double* gu;     // ghosts of u: [2][G]
+  const double* gv;     // ghosts of v: [2][G]
+  const double* b;      // history (RESIDUAL, FD)
+  const double* F0;     // F(u) (FD)
+  const double* eps;    // device scalar (FD)
+  double a0, dt;
+  double* out;          // F or Jv
+  double* cfflux;       // [2][G] fine-side coarse-fine fluxes
+};
+void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
+                       double* g, int nonlinear, cudaStream_t s);
+void launch_ghost_z(const Hier& H, const float* z, float* gz, cudaStream_t s);
+void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const float* gz,
+                    int mode, const StencilIO& io, cudaStream_t s);
+void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s);
+void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, double thr_g,
+                double thr_r, const double* emax, uint8_t* tags, cudaStream_t s);
+void launch_average_down(const Hier& H, double* x, int nfield, int fstride, cudaStream_t s);
+
+// BLAS / reductions (k_blas.cu)
+struct Reducer {
+  int nblk = 0;
+  double* d_part = nullptr;   // partials [nblk * 8]
+  double* d_res = nullptr;    // results [64]
+  double* h_res = nullptr;    // pinned host mirror [64]
+};
+int reducer_init(Reducer& R, int N);
+void reducer_free(Reducer& R);
+// res[slot] = sum over leaf cells of both fields of wvol * x * y
+void launch_wdot(const Hier& H, Reducer& R, const double* x, const double* y, int slot,
+                 cudaStream_t s);
+// eps of Sec. 4.1 into R.d_res[slot]
+void launch_fd_eps(const Hier& H, Reducer& R, const double* u, const double* v, double u_min,
+                   int slot, cudaStream_t s);
+// max |E| over leaf cells into R.d_res[slot]
+void launch_emax(const Hier& H, Reducer& R, const double* E, int slot, cudaStream_t s);
+// multi-dot: res[slot + i] = <w, V_i> for i < nv (V given as base + i*stride)
+void launch_mdot(const Hier& H, Reducer& R, const double* w, const double* V, long stride, int nv,
+                 int slot, cudaStream_t s);
+// w -= sum_i h[i] V_i  (h device)
+void launch_mupdate(int n2, double* w, const double* V, long stride, int nv, const double* h,
+                    cudaStream_t s);
+void launch_axpy(int n, double a, const double* x, double* y, cudaStream_t s);
+void launch_scale_dev(int n, const double* num, const double* den_sq, double* x, cudaStream_t s);
+void launch_lincomb_dev(int n, double* x, const double* Z, long stride, int nv, const double* y,
+                        cudaStream_t s);
+void launch_zero_covered(const Hier& H, double* x, cudaStream_t s);
+void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v, int slot,
+                    cudaStream_t s);
+
+// Preconditioner (k_pc.cu)
+struct PcState;
+int pc_alloc(PcState** ps, const Hier& H, const nrd_params& p, std::string& err);
+void pc_free(PcState* ps);
+int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u, const double* gu,
+             const float* z, const float* gz, double a0, double dt, cudaStream_t s);
+int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s);
+
+#define CUDA_TRY(x)                                         \
+  do {                                                      \
+    cudaError_t e_ = (x);                                   \
+    if (e_ != cudaSuccess) {                                \
+      err = std::string(#x) + ": " + cudaGetErrorString(e_); \
+      return NRD_ECUDA;                                     \
+    }                                                       \
+  } while (0)
+
+// CUDA-event timing of kernel groups (off unless enabled).
+struct Timer {
+  bool on = false;
+  std::vector<cudaEvent_t> ev[NRD_TK_COUNT];   // start/stop pairs
+  size_t used[NRD_TK_COUNT] = {0};
+  void begin(int k, cudaStream_t s) {
+    if (!on) return;
+    if (used[k] + 2 > ev[k].size()) {
+      for (int i = 0; i < 64; i++) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        ev[k].push_back(e);
+      }
+    }
+    cudaEventRecord(ev[k][used[k]], s);
+  }
+  void end(int k, cudaStream_t s) {
+    if (!on) return;
+    cudaEventRecord(ev[k][used[k] + 1], s);
+    used[k] += 2;
+  }
+  void reset() {
+    for (int k = 0; k < NRD_TK_COUNT; k++) used[k] = 0;
+  }
+  void destroy() {
+    for (int k = 0; k < NRD_TK_COUNT; k++) {
+      for (auto e : ev[k]) cudaEventDestroy(e);
+      ev[k].clear();
+      used[k] = 0;
+    }
+  }
+};
+
+// The context behind the opaque nrd_ctx handle.
+struct nrd_ctx {
+  Timer timer;
+  nrd_params p;
+  ModelParams mp;
+  Hier H;
+  bool have_hier = false, have_mat = false;
+  float* d_z = nullptr;        // N: material z
+  float* d_gz = nullptr;       // G: z of ghost cells
+  double* d_gu = nullptr;      // 2G: ghosts of the state
+  double* d_gv = nullptr;      // 2G: ghosts of a direction
+  double* d_cf = nullptr;      // 2G: fine-side coarse-fine fluxes
+  double* d_tmp = nullptr;     // 2N scratch
+  Reducer R;
+  PcState* pc = nullptr;
+  bool pc_ready = false;
+  // Krylov / Newton work space (allocated on first solver call)
+  int kry_m = 0;
+  double* d_V = nullptr;       // (m+1) x 2N
+  double* d_Z = nullptr;       // m x 2N
+  double* d_F = nullptr;       // 2N
+  double* d_dx = nullptr;      // 2N
+  double* d_w = nullptr;       // 2N
+  double* d_r = nullptr;       // 2N
+  double* d_b = nullptr;       // 2N
+  double* d_small = nullptr;   // Hessenberg, rotations, g, y
+  std::string err;
+};
+
+// solver.cu
+int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
+                  cudaStream_t s);
+int solver_alloc(nrd_ctx* c);
+void solver_free(nrd_ctx* c);
+// capi.cu helpers used by the solver
+int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
+                 bool fill_ghosts, cudaStream_t s);
+int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const double* F0,
+           double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s);

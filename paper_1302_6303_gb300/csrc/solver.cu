@@ -1,0 +1,289 @@
+// Inexact Newton with Eisenstat-Walker forcing and right-preconditioned
+// restarted GMRES (Sec. 4.1, 4.2).  All vectors stay on the device; the
+// Hessenberg column, Givens rotations and the residual estimate are updated
+// by a one-thread kernel, and the host reads back one scalar per Krylov
+// iteration to decide convergence.  Orthogonalisation is classical
+// Gram-Schmidt applied twice (CGS2), each pass one multi-dot and one update.
+// The preconditioned directions z_j = P^{-1} v_j are kept (flexible form), so
+// the update is x = sum_j y_j z_j; for a fixed preconditioner this is
+// right-preconditioned GMRES, and it stays valid for the FP32 V-cycle.
+#include <cmath>
+#include <cstdio>
+
+#include "nrd_internal.h"
+
+namespace {
+
+enum {
+  SL_EPS = 0, SL_DOT = 1, SL_NRM = 2, SL_G = 3, SL_F = 4, SL_CAP = 5, SL_R = 6,
+  SL_H1 = 8, SL_H2 = 48
+};
+
+struct Small {
+  double* Hm;   // (m+1) x m, column-major by j: Hm[i + (m+1) j]
+  double* cs;
+  double* sn;
+  double* g;    // m+1
+  double* y;    // m
+};
+
+Small small_of(nrd_ctx* c) {
+  int m = c->kry_m;
+  Small S;
+  S.Hm = c->d_small;
+  S.cs = S.Hm + (m + 1) * m;
+  S.sn = S.cs + m;
+  S.g = S.sn + m;
+  S.y = S.g + m + 1;
+  return S;
+}
+
+// Column j of the Hessenberg matrix from the two CGS passes, then the Givens
+// update of the least-squares problem; res[SL_G] = |g_{j+1}|.
+__global__ void k_arnoldi(Small S, int m, int j, double* res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double* col = S.Hm + (size_t)(m + 1) * j;
+  for (int i = 0; i <= j; i++) col[i] = res[SL_H1 + i] + res[SL_H2 + i];
+  double hn = sqrt(res[SL_NRM]);
+  col[j + 1] = hn;
+  for (int i = 0; i < j; i++) {
+    double a = col[i], b = col[i + 1];
+    col[i] = S.cs[i] * a + S.sn[i] * b;
+    col[i + 1] = -S.sn[i] * a + S.cs[i] * b;
+  }
+  double a = col[j], b = col[j + 1];
+  double den = sqrt(a * a + b * b);
+  double cs = (den > 0.0) ? a / den : 1.0;
+  double sn = (den > 0.0) ? b / den : 0.0;
+  S.cs[j] = cs;
+  S.sn[j] = sn;
+  col[j] = den;
+  col[j + 1] = 0.0;
+  double gj = S.g[j];
+  S.g[j + 1] = -sn * gj;
+  S.g[j] = cs * gj;
+  res[SL_G] = fabs(S.g[j + 1]);
+}
+
+__global__ void k_ginit(Small S, int m, const double* nrm2, double* res) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = 0; i <= m; i++) S.g[i] = 0.0;
+  S.g[0] = sqrt(*nrm2);
+}
+
+__global__ void k_backsub(Small S, int m, int k) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = k - 1; i >= 0; i--) {
+    double s = S.g[i];
+    for (int t = i + 1; t < k; t++) s -= S.Hm[i + (size_t)(m + 1) * t] * S.y[t];
+    S.y[i] = s / S.Hm[i + (size_t)(m + 1) * i];
+  }
+}
+
+// v0 = sign * r / sqrt(nrm2)
+__global__ void k_normalize(int n, const double* r, double* v, const double* nrm2, double sign) {
+  double d = sqrt(*nrm2);
+  double sc = (d > 0.0) ? sign / d : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    v[i] = sc * r[i];
+}
+
+// r = rhs_sign * F - Jx   (rhs = -F)
+__global__ void k_resid(int n, const double* F, const double* Jx, double* r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    r[i] = -F[i] - Jx[i];
+}
+
+int grid1(long n) {
+  long b = (n + 255) / 256;
+  return (int)std::max(1L, std::min(b, 152L * 8));
+}
+
+double read_slot(nrd_ctx* c, int slot, cudaStream_t s) {
+  cudaMemcpyAsync(c->R.h_res + slot, c->R.d_res + slot, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  return c->R.h_res[slot];
+}
+
+}  // namespace
+
+int solver_alloc(nrd_ctx* c) {
+  int m = c->p.restart;
+  if (c->d_V && c->kry_m == m) return NRD_OK;
+  solver_free(c);
+  size_t n2 = 2 * (size_t)c->H.N;
+  bool ok = cudaMalloc(&c->d_V, (m + 1) * n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_Z, m * n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_F, n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_dx, n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_w, n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_r, n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_b, n2 * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_small, ((m + 1) * m + 5 * m + 8) * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    solver_free(c);
+    c->err = "solver work-space allocation failed";
+    return NRD_ENOMEM;
+  }
+  c->kry_m = m;
+  return NRD_OK;
+}
+
+void solver_free(nrd_ctx* c) {
+  auto F = [](void* p) { if (p) cudaFree(p); };
+  F(c->d_V); F(c->d_Z); F(c->d_F); F(c->d_dx); F(c->d_w); F(c->d_r); F(c->d_b); F(c->d_small);
+  c->d_V = c->d_Z = c->d_F = c->d_dx = c->d_w = c->d_r = c->d_b = c->d_small = nullptr;
+  c->kry_m = 0;
+}
+
+// GMRES for J dx = -F to ||-F - J dx|| <= tol.  Returns iterations in *its.
+static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double fn,
+                 double tol, int* its, cudaStream_t s) {
+  Hier& H = c->H;
+  const int n2 = 2 * H.N;
+  const long stride = n2;
+  const int m = c->kry_m;
+  Small S = small_of(c);
+  const int mode = c->p.jv_mode;
+  cudaMemsetAsync(c->d_dx, 0, n2 * sizeof(double), s);
+  // r0 = -F
+  double rn2 = fn * fn;
+  const double* r0 = c->d_F;
+  double sign = -1.0;
+  int total = 0;
+  *its = 0;
+  if (fn <= tol) return NRD_OK;
+  bool first = true;
+  while (total < c->p.max_krylov) {
+    // V0 = r / ||r||
+    cudaMemcpyAsync(c->R.d_res + SL_R, &rn2, sizeof(double), cudaMemcpyHostToDevice, s);
+    k_normalize<<<grid1(n2), 256, 0, s>>>(n2, r0, c->d_V, c->R.d_res + SL_R, sign);
+    k_ginit<<<1, 1, 0, s>>>(S, m, c->R.d_res + SL_R, c->R.d_res);
+    int j = 0;
+    bool conv = false;
+    for (; j < m && total < c->p.max_krylov; j++) {
+      double* Vj = c->d_V + (size_t)j * stride;
+      double* Zj = c->d_Z + (size_t)j * stride;
+      c->timer.begin(NRD_TK_PC_APPLY, s);
+      int rc = pc_apply(c->pc, H, Vj, Zj, s);
+      c->timer.end(NRD_TK_PC_APPLY, s);
+      if (rc != NRD_OK) return rc;
+      rc = ctx_jv(c, u, Zj, b, c->d_F, a0, dt, mode, c->d_w, false, s);
+      if (rc != NRD_OK) return rc;
+      total++;
+      // CGS2
+      c->timer.begin(NRD_TK_ORTHO, s);
+      launch_mdot(H, c->R, c->d_w, c->d_V, stride, j + 1, SL_H1, s);
+      launch_mupdate(n2, c->d_w, c->d_V, stride, j + 1, c->R.d_res + SL_H1, s);
+      launch_mdot(H, c->R, c->d_w, c->d_V, stride, j + 1, SL_H2, s);
+      launch_mupdate(n2, c->d_w, c->d_V, stride, j + 1, c->R.d_res + SL_H2, s);
+      launch_wdot(H, c->R, c->d_w, c->d_w, SL_NRM, s);
+      k_normalize<<<grid1(n2), 256, 0, s>>>(n2, c->d_w, c->d_V + (size_t)(j + 1) * stride,
+                                             c->R.d_res + SL_NRM, 1.0);
+      c->timer.end(NRD_TK_ORTHO, s);
+      k_arnoldi<<<1, 1, 0, s>>>(S, m, j, c->R.d_res);
+      double gres = read_slot(c, SL_G, s);
+      double hn2 = c->R.h_res[SL_NRM];
+      (void)hn2;
+      if (!std::isfinite(gres)) {
+        c->err = "non-finite GMRES residual";
+        return NRD_ENAN;
+      }
+      if (gres <= tol) {
+        j++;
+        conv = true;
+        break;
+      }
+    }
+    k_backsub<<<1, 1, 0, s>>>(S, m, j);
+    launch_lincomb_dev(n2, c->d_dx, c->d_Z, stride, j, S.y, s);
+    if (conv) break;
+    if (total >= c->p.max_krylov) break;
+    // restart from the true residual r = -F - J dx
+    int rc = ctx_jv(c, u, c->d_dx, b, c->d_F, a0, dt, mode, c->d_w, false, s);
+    if (rc != NRD_OK) return rc;
+    k_resid<<<grid1(n2), 256, 0, s>>>(n2, c->d_F, c->d_w, c->d_r);
+    launch_wdot(H, c->R, c->d_r, c->d_r, SL_R, s);
+    rn2 = read_slot(c, SL_R, s);
+    r0 = c->d_r;
+    sign = 1.0;
+    first = false;
+    if (std::sqrt(rn2) <= tol) break;
+  }
+  (void)first;
+  *its = total;
+  return (cudaGetLastError() == cudaSuccess) ? NRD_OK : NRD_ECUDA;
+}
+
+int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
+                  cudaStream_t s) {
+  int rc = solver_alloc(c);
+  if (rc != NRD_OK) return rc;
+  Hier& H = c->H;
+  const int n2 = 2 * H.N;
+  nrd_stats loc{};
+  loc.min_lambda = 1.0;
+  rc = ctx_residual(c, u, b, a0, dt, c->d_F, true, s);
+  if (rc != NRD_OK) return rc;
+  launch_wdot(H, c->R, c->d_F, c->d_F, SL_F, s);
+  double fn = std::sqrt(read_slot(c, SL_F, s));
+  if (!std::isfinite(fn)) {
+    c->err = "non-finite initial residual";
+    return NRD_ENAN;
+  }
+  loc.fnorm0 = fn;
+  const double stop = c->p.rtol * fn + c->p.atol;
+  double eta = c->p.eta_max;
+  int it = 0;
+  while (fn > stop && it < c->p.max_newton) {
+    c->timer.begin(NRD_TK_PC_SETUP, s);
+    rc = pc_setup(c->pc, H, c->mp, u, c->d_gu, c->d_z, c->d_gz, a0, dt, s);
+    c->timer.end(NRD_TK_PC_SETUP, s);
+    if (rc != NRD_OK) { c->err = "preconditioner set-up failed"; return rc; }
+    c->pc_ready = true;
+    loc.pc_setups++;
+    int its = 0;
+    rc = gmres(c, u, b, a0, dt, fn, eta * fn, &its, s);
+    if (rc != NRD_OK) return rc;
+    loc.krylov_its += its;
+    // positivity-constrained update (Sec. 4.1 remark, reading R7)
+    launch_pos_cap(H, c->R, u, c->d_dx, SL_CAP, s);
+    double m = read_slot(c, SL_CAP, s);
+    double lam = std::min(1.0, 0.9 * m);
+    if (!(lam > 0.0)) {
+      c->err = "positivity cap vanished";
+      return NRD_ENEG;
+    }
+    loc.min_lambda = std::min(loc.min_lambda, lam);
+    launch_axpy(n2, lam, c->d_dx, u, s);
+    rc = ctx_residual(c, u, b, a0, dt, c->d_F, true, s);
+    if (rc != NRD_OK) return rc;
+    launch_wdot(H, c->R, c->d_F, c->d_F, SL_F, s);
+    double fold = fn;
+    fn = std::sqrt(read_slot(c, SL_F, s));
+    if (!std::isfinite(fn)) {
+      c->err = "non-finite residual";
+      return NRD_ENAN;
+    }
+    // Eisenstat-Walker forcing term (Kelley's safeguarded choice)
+    double rat = fn / fold;
+    double g = c->p.ew_gamma;
+    double etaA = g * rat * rat;
+    double etaN;
+    if (g * eta * eta <= 0.1) etaN = std::min(c->p.eta_max, etaA);
+    else etaN = std::min(c->p.eta_max, std::max(etaA, g * eta * eta));
+    eta = std::min(c->p.eta_max, std::max(etaN, 0.5 * stop / fn));
+    it++;
+  }
+  launch_average_down(H, u, 2, H.N, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    c->err = "synchronisation failed";
+    return NRD_ECUDA;
+  }
+  loc.newton_its = it;
+  loc.fnorm = fn;
+  loc.status = (fn > stop) ? NRD_ENONCONV : NRD_OK;
+  if (st) *st = loc;
+  if (loc.status != NRD_OK) c->err = "Newton did not converge within max_newton";
+  return loc.status;
+}

@@ -1,0 +1,254 @@
+"""Thin Python binding of the nrd C ABI (include/nrd.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library ``libnrd.so``.  Tensors are torch CUDA tensors (device memory and the
+current stream come from torch); nothing here falls back to a CPU path, and
+loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libnrd.so")
+
+OK, EINVAL, ENOMEM, ENONCONV, ENEG, ENAN, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+BC_NEUMANN, BC_ROBIN = 0, 1
+LIM_WILSON, LIM_PAPER_LITERAL = 0, 1
+JV_FD, JV_ANALYTIC = 0, 1
+PC_F64, PC_F32 = 0, 1
+
+EXPORTED = [
+    "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
+    "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
+    "nrd_jv", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
+    "nrd_step", "nrd_tag", "nrd_timing_enable", "nrd_timing_read",
+]
+TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST = range(7)
+TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_double), ("limiter", ctypes.c_int), ("u_min", ctypes.c_double),
+        ("restart", ctypes.c_int), ("max_krylov", ctypes.c_int), ("jv_mode", ctypes.c_int),
+        ("pc_precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+        ("nmg", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("rtol", ctypes.c_double),
+        ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("eta_max", ctypes.c_double),
+        ("ew_gamma", ctypes.c_double), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("newton_its", ctypes.c_int), ("krylov_its", ctypes.c_int),
+        ("pc_setups", ctypes.c_int), ("fnorm0", ctypes.c_double), ("fnorm", ctypes.c_double),
+        ("min_lambda", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class NrdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("nrd error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = _LIBPATH):
+    """Load libnrd.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libnrd.so not built: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp, fp = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
+    c_int, c_dbl = ctypes.c_int, ctypes.c_double
+    P = ctypes.POINTER
+    sig = {
+        "nrd_params_default": (c_int, [P(Params)]),
+        "nrd_create": (c_int, [P(Params), P(vp)]),
+        "nrd_destroy": (c_int, [vp]),
+        "nrd_last_error": (ctypes.c_char_p, [vp]),
+        "nrd_set_params": (c_int, [vp, P(Params)]),
+        "nrd_set_hierarchy": (c_int, [vp, c_int, P(c_int), P(c_int), P(c_int), P(c_dbl)]),
+        "nrd_layout": (c_int, [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]),
+        "nrd_set_material": (c_int, [vp, fp, vp]),
+        "nrd_ghost_fill": (c_int, [vp, dp, dp, dp, fp, vp]),
+        "nrd_residual": (c_int, [vp, dp, dp, c_dbl, c_dbl, dp, vp]),
+        "nrd_jv": (c_int, [vp, dp, dp, dp, dp, c_dbl, c_dbl, c_int, dp, vp]),
+        "nrd_fd_eps": (c_int, [vp, dp, dp, P(c_dbl), vp]),
+        "nrd_dot": (c_int, [vp, dp, dp, P(c_dbl), vp]),
+        "nrd_precond_setup": (c_int, [vp, dp, c_dbl, c_dbl, vp]),
+        "nrd_precond_apply": (c_int, [vp, dp, dp, vp]),
+        "nrd_newton": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
+        "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
+        "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
+        "nrd_timing_enable": (c_int, [vp, c_int]),
+        "nrd_timing_read": (c_int, [vp, c_int, P(c_dbl), P(ctypes.c_int64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_params(**kw) -> Params:
+    lib = load()
+    p = Params()
+    lib.nrd_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t, dtype):
+    if t is None:
+        return None
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == dtype):
+        raise ValueError("expected a contiguous CUDA tensor of dtype %s" % dtype)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """One nrd context: a hierarchy, a material field and solver state."""
+
+    def __init__(self, params: Params | None = None, **kw):
+        self.lib = load()
+        self.params = params if params is not None else default_params(**kw)
+        h = ctypes.c_void_p()
+        rc = self.lib.nrd_create(ctypes.byref(self.params), ctypes.byref(h))
+        if rc != OK:
+            raise NrdError(rc, "nrd_create failed (bad parameters?)")
+        self._h = h
+        self.N = self.G = self.nleaf = 0
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self.lib.nrd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != OK:
+            msg = self.lib.nrd_last_error(self._h)
+            raise NrdError(rc, msg.decode() if msg else "")
+        return rc
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            setattr(self.params, k, v)
+        self._check(self.lib.nrd_set_params(self._h, ctypes.byref(self.params)))
+
+    def set_hierarchy(self, nboxes, boxes, bc_type, bc_R):
+        nb = (ctypes.c_int * len(nboxes))(*nboxes)
+        bx = (ctypes.c_int * len(boxes))(*boxes)
+        bt = (ctypes.c_int * 6)(*bc_type)
+        br = (ctypes.c_double * 6)(*bc_R)
+        self._check(self.lib.nrd_set_hierarchy(self._h, len(nboxes), nb, bx, bt, br))
+        n, g, lf = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.nrd_layout(self._h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(lf)))
+        self.N, self.G, self.nleaf = n.value, g.value, lf.value
+
+    def set_hierarchy_from(self, hier):
+        self.set_hierarchy(hier.nboxes, hier.boxes_flat(), hier.bc_type, hier.bc_R)
+
+    def set_material(self, z):
+        self._check(self.lib.nrd_set_material(self._h, _ptr(z, torch.float32), _stream()))
+
+    def ghost_fill(self, u):
+        gE = torch.empty(self.G, dtype=torch.float64, device=u.device)
+        gT = torch.empty_like(gE)
+        gz = torch.empty(self.G, dtype=torch.float32, device=u.device)
+        self._check(self.lib.nrd_ghost_fill(self._h, _ptr(u, torch.float64), _ptr(gE, torch.float64),
+                                            _ptr(gT, torch.float64), _ptr(gz, torch.float32),
+                                            _stream()))
+        return gE, gT, gz
+
+    def residual(self, u, b, a0, dt, out=None):
+        out = torch.empty_like(u) if out is None else out
+        self._check(self.lib.nrd_residual(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
+                                          a0, dt, _ptr(out, torch.float64), _stream()))
+        return out
+
+    def jv(self, u, v, a0, dt, mode=JV_ANALYTIC, b=None, F0=None, out=None):
+        out = torch.empty_like(u) if out is None else out
+        self._check(self.lib.nrd_jv(self._h, _ptr(u, torch.float64), _ptr(v, torch.float64),
+                                    _ptr(b, torch.float64), _ptr(F0, torch.float64), a0, dt, mode,
+                                    _ptr(out, torch.float64), _stream()))
+        return out
+
+    def fd_eps(self, u, v):
+        e = ctypes.c_double()
+        self._check(self.lib.nrd_fd_eps(self._h, _ptr(u, torch.float64), _ptr(v, torch.float64),
+                                        ctypes.byref(e), _stream()))
+        return e.value
+
+    def dot(self, x, y):
+        d = ctypes.c_double()
+        self._check(self.lib.nrd_dot(self._h, _ptr(x, torch.float64), _ptr(y, torch.float64),
+                                     ctypes.byref(d), _stream()))
+        return d.value
+
+    def precond_setup(self, u, a0, dt):
+        self._check(self.lib.nrd_precond_setup(self._h, _ptr(u, torch.float64), a0, dt, _stream()))
+
+    def precond_apply(self, w, out=None):
+        out = torch.empty_like(w) if out is None else out
+        self._check(self.lib.nrd_precond_apply(self._h, _ptr(w, torch.float64),
+                                               _ptr(out, torch.float64), _stream()))
+        return out
+
+    def newton(self, u, b, a0, dt, check=True):
+        st = Stats()
+        rc = self.lib.nrd_newton(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64), a0, dt,
+                                 ctypes.byref(st), _stream())
+        if check and rc not in (OK,):
+            self._check(rc)
+        return st.as_dict()
+
+    def step(self, u, u_n, u_nm1, dt, dt_prev=0.0, check=True):
+        st = Stats()
+        rc = self.lib.nrd_step(self._h, _ptr(u, torch.float64), _ptr(u_n, torch.float64),
+                               _ptr(u_nm1, torch.float64), dt, dt_prev, ctypes.byref(st), _stream())
+        if check and rc != OK:
+            self._check(rc)
+        return st.as_dict()
+
+    def timing_enable(self, on=True):
+        self._check(self.lib.nrd_timing_enable(self._h, 1 if on else 0))
+
+    def timing_read(self):
+        out = {}
+        for k, name in enumerate(TK_NAMES):
+            ms, n = ctypes.c_double(), ctypes.c_int64()
+            self._check(self.lib.nrd_timing_read(self._h, k, ctypes.byref(ms), ctypes.byref(n)))
+            out[name] = (ms.value, n.value)
+        return out
+
+    def tag(self, u, thr_c=float("inf"), thr_g=float("inf"), thr_r=float("inf")):
+        t = torch.empty(self.N, dtype=torch.uint8, device=u.device)
+        self._check(self.lib.nrd_tag(self._h, _ptr(u, torch.float64), thr_c, thr_g, thr_r,
+                                     _ptr(t, torch.uint8), _stream()))
+        return t

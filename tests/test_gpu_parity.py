@@ -1,0 +1,255 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (each derived from the arithmetic, see the design notes):
+  ghosts                 1e-14 relative (same formulas, different summation order)
+  residual, analytic Jv  |gpu - oracle| <= 1e-12 * S_cell, S_cell the sum of
+                         absolute values of the cell's terms (oracle-computed)
+  FD Jv                  8 eps_mach S_cell / |eps| (rounding of F(u + eps v)
+                         amplified by 1/eps) + 1e-12 S_jv
+  FP64 V-cycle           1e-11 of max |y| (same algorithm, different rounding)
+  FP32 V-cycle           2e-4 of max |y|
+  converged step         1e-8 relative to max |u| (Newton rtol 1e-10 on both)
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from oracle.oracle import Oracle, JV_ANALYTIC as O_AN, JV_FD as O_FD, LIM_PAPER_LITERAL  # noqa: E402
+from paper_1302_6303_gb300 import workloads as W  # noqa: E402
+
+EPS = 2.0 ** -52
+
+
+@pytest.fixture(scope="session")
+def nrd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd as m
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def auto_nmg(h, cap=4):
+    m = 1
+    while m < cap and all(n % (1 << m) == 0 for n in h.n0):
+        m += 1
+    return m
+
+
+def make(nrd, h, z, limiter=0, **kw):
+    kw.setdefault("nmg", auto_nmg(h))
+    ctx = nrd.Context(limiter=limiter, **kw)
+    ctx.set_hierarchy_from(h)
+    ctx.set_material(dev(z.astype(np.float32)))
+    o = Oracle(h, z, limiter=limiter)
+    return ctx, o
+
+
+CASES = {
+    "single32": lambda: W.config_single_level(32, seed=1, cube_side=8),
+    "ragged": lambda: (W.uniform((20, 12, 7)),
+                       W.material_from_cubes(W.uniform((20, 12, 7)), [((3, 2, 1), 4, 10.0)])),
+    "one_cell": lambda: (W.uniform(1), np.array([3.0], np.float32)),
+    "tiny2": lambda: (W.tiny_amr(8), W.material_from_cubes(W.tiny_amr(8), [((2, 2, 2), 3, 10.0)])),
+    "tiny3": lambda: (W.tiny_amr(8, True),
+                      W.material_from_cubes(W.tiny_amr(8, True), [((3, 3, 3), 3, 10.0)])),
+    "boundary": lambda: (W.boundary_amr(8),
+                         W.material_from_cubes(W.boundary_amr(8), [((0, 1, 1), 2, 10.0)])),
+    "amr2_16": lambda: W.config_amr2(16, seed=3, band=4, ncubes=4),
+}
+
+
+def _state(h, seed=2):
+    return W.front_state(h, seed=seed, noise=0.1)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_ghosts(nrd, name):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z)
+    u = _state(h)
+    gE, gT, gz = ctx.ghost_fill(dev(u))
+    oE, oT, oz = o.ghosts(u)
+    np.testing.assert_allclose(gE.cpu().numpy(), oE, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(gT.cpu().numpy(), oT, rtol=1e-14, atol=0)
+    np.testing.assert_array_equal(gz.cpu().numpy(), oz)
+
+
+@pytest.mark.parametrize("limiter", [0, LIM_PAPER_LITERAL])
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual(nrd, name, limiter):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z, limiter=limiter)
+    u = _state(h)
+    rng = np.random.default_rng(4)
+    b = u * (1 + 0.05 * rng.uniform(-1, 1, u.size))
+    a0, dt = 1.5, 3e-3
+    F = ctx.residual(dev(u), dev(b), a0, dt).cpu().numpy()
+    Fo = o.residual(u, b, a0, dt)
+    S = o.residual_scale(u, b, a0, dt)
+    err = np.abs(F - Fo)
+    assert np.all(err <= 1e-12 * S + 1e-300), (err / np.maximum(S, 1e-300)).max()
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    assert np.all(F[~leaf] == 0.0)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jv_analytic(nrd, name):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z)
+    u = _state(h)
+    v = W.random_direction(h, 7)
+    a0, dt = 1.0, 2e-3
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_ANALYTIC).cpu().numpy()
+    Jo = o.jv_analytic(u, v, a0, dt)
+    S = o.jv_scale(u, v, a0, dt)
+    err = np.abs(J - Jo)
+    assert np.all(err <= 1e-12 * S + 1e-300), (err / np.maximum(S, 1e-300)).max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_jv_fd_and_eps(nrd, name):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z)
+    u = _state(h)
+    v = W.random_direction(h, 8)
+    a0, dt = 1.0, 2e-3
+    b = u.copy()
+    F0 = o.residual(u, b, a0, dt)
+    eps_g = ctx.fd_eps(dev(u), dev(v))
+    eps_o = o.fd_eps(u, v)
+    assert abs(eps_g - eps_o) <= 1e-13 * abs(eps_o)
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_FD, b=dev(b), F0=dev(F0)).cpu().numpy()
+    Jo, eps = o.jv_fd(u, v, b, a0, dt, F0=F0)
+    up = u + eps * v
+    S = o.residual_scale(up, b, a0, dt)
+    Sj = o.jv_scale(u, v, a0, dt)
+    tol = 8 * EPS * S / abs(eps) + 1e-12 * Sj
+    assert np.all(np.abs(J - Jo) <= tol), (np.abs(J - Jo) / tol).max()
+
+
+@pytest.mark.parametrize("name", ["single32", "tiny3", "amr2_16"])
+def test_dot(nrd, name):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z)
+    x = W.random_direction(h, 1)
+    y = W.random_direction(h, 2)
+    d = ctx.dot(dev(x), dev(y))
+    do = o.dot(x, y)
+    scale = o.dot(np.abs(x), np.abs(y))
+    assert abs(d - do) <= 1e-14 * scale
+
+
+@pytest.mark.parametrize("name", ["single32", "tiny3", "boundary", "amr2_16"])
+def test_tag(nrd, name):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z)
+    u = _state(h)
+    for thr in [(0.5, np.inf, np.inf), (np.inf, 0.3, np.inf), (np.inf, np.inf, 0.1)]:
+        t = ctx.tag(dev(u), *thr).cpu().numpy()
+        to = o.tag(u, *thr)
+        assert np.mean(t == to) > 0.999
+        # any disagreement must sit on the threshold within rounding
+        assert np.sum(t != to) <= 2
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+@pytest.mark.parametrize("name", ["single32", "tiny2", "tiny3", "boundary", "amr2_16"])
+def test_precond_apply(nrd, name, prec, tol):
+    h, z = CASES[name]()
+    nmg = 3 if h.n0[0] >= 16 else 2
+    ctx, o = make(nrd, h, z, pc_precision=prec, nmg=nmg, nu1=2, nu2=2, coarse_sweeps=4)
+    o.set_solver(nmg=nmg, nu1=2, nu2=2, coarse_sweeps=4)
+    u = _state(h)
+    a0, dt = 1.2, 5e-3
+    ctx.precond_setup(dev(u), a0, dt)
+    o.pc_setup(u, a0, dt)
+    w = W.random_direction(h, 5)
+    y = ctx.precond_apply(dev(w)).cpu().numpy()
+    yo = o.pc_apply(w)
+    assert np.abs(y - yo).max() <= tol * np.abs(yo).max(), np.abs(y - yo).max() / np.abs(yo).max()
+
+
+@pytest.mark.parametrize("jv", ["fd", "analytic"])
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["single32", "tiny2", "amr2_16"])
+def test_newton_step(nrd, name, prec, jv):
+    h, z = CASES[name]()
+    nmg = 3 if h.n0[0] >= 16 else 2
+    mode = nrd.JV_FD if jv == "fd" else nrd.JV_ANALYTIC
+    ctx, o = make(nrd, h, z, pc_precision=prec, nmg=nmg, jv_mode=mode, rtol=1e-10, restart=30)
+    o.set_solver(nmg=nmg, jv_mode=O_FD if jv == "fd" else O_AN, rtol=1e-10)
+    u0 = W.initial_state(h)
+    # a warmed-up state: the Marshak front has entered
+    u0 = W.front_state(h, seed=9, noise=0.0, front=0.1, width=0.05)
+    un = dev(u0)
+    u = un.clone()
+    st = ctx.step(u, un, None, 1e-3)
+    uo, sto = o.newton(u0.copy(), u0.copy(), 1.0, 1e-3)
+    assert st["status"] == 0 and sto["status"] == 0
+    ug = u.cpu().numpy()
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    rel = np.abs(ug - uo)[leaf].max() / np.abs(uo[leaf]).max()
+    assert rel <= 1e-8, (rel, st, sto)
+
+
+def test_bdf2_step_matches_oracle(nrd):
+    h, z = CASES["tiny2"]()
+    ctx, o = make(nrd, h, z, pc_precision=0, nmg=2, jv_mode=nrd.JV_ANALYTIC, rtol=1e-10)
+    o.set_solver(nmg=2, jv_mode=O_AN, rtol=1e-10)
+    u1 = W.front_state(h, seed=1, noise=0.0, front=0.1)
+    u0 = W.front_state(h, seed=1, noise=0.0, front=0.08)
+    dt, dtp = 1e-3, 5e-4
+    al = dt / dtp
+    a0 = (1 + 2 * al) / (1 + al)
+    b = (1 + al) * u1 - al * al / (1 + al) * u0
+    u = dev(u1)
+    st = ctx.step(u, dev(u1), dev(u0), dt, dtp)
+    uo, sto = o.newton(u1.copy(), b, a0, dt)
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    rel = np.abs(u.cpu().numpy() - uo)[leaf].max() / np.abs(uo[leaf]).max()
+    assert st["status"] == 0 and rel <= 1e-8
+
+
+def test_full_size_residual_and_jv(nrd):
+    """The benchmark workload (64^3 base + a fine Marshak band, about 377k leaf
+    cells) in the benchmark's launch configuration: every cell checked."""
+    h, z = W.config_amr2(64, seed=0)
+    ctx, o = make(nrd, h, z)
+    u = W.front_state(h, seed=3, noise=0.05)
+    v = W.random_direction(h, 4)
+    a0, dt = 1.0, 5e-4
+    F = ctx.residual(dev(u), dev(u), a0, dt).cpu().numpy()
+    Fo = o.residual(u, u.copy(), a0, dt)
+    S = o.residual_scale(u, u.copy(), a0, dt)
+    assert np.all(np.abs(F - Fo) <= 1e-12 * S + 1e-300)
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_ANALYTIC).cpu().numpy()
+    Jo = o.jv_analytic(u, v, a0, dt)
+    Sj = o.jv_scale(u, v, a0, dt)
+    assert np.all(np.abs(J - Jo) <= 1e-12 * Sj + 1e-300)
+
+
+def test_errors_are_reported(nrd):
+    ctx = nrd.Context()
+    with pytest.raises(nrd.NrdError) as e:
+        ctx.residual(dev(np.ones(2)), dev(np.ones(2)), 1.0, 1.0)
+    assert e.value.code == nrd.ESTATE
+    # misaligned fine box
+    with pytest.raises(nrd.NrdError) as e:
+        ctx.set_hierarchy([1, 1], [0, 0, 0, 7, 7, 7, 1, 2, 2, 4, 5, 5], [1, 0, 0, 0, 0, 0],
+                          [1.0, 0, 0, 0, 0, 0])
+    assert e.value.code == nrd.EINVAL
+    # improperly nested third level
+    h = W.tiny_amr(8)
+    boxes = h.boxes_flat() + [0, 0, 0, 3, 3, 3]
+    with pytest.raises(nrd.NrdError) as e:
+        ctx.set_hierarchy(h.nboxes + [1], boxes, h.bc_type, h.bc_R)
+    assert e.value.code == nrd.EINVAL
