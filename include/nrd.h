@@ -81,7 +81,11 @@ enum {
 
 enum { NRD_BC_NEUMANN = 0, NRD_BC_ROBIN = 1 };
 enum { NRD_LIM_WILSON = 0, NRD_LIM_PAPER_LITERAL = 1 };
-enum { NRD_JV_FD = 0, NRD_JV_ANALYTIC = 1 };
+/* Jv forms: NRD_JV_FD finite difference of Sec. 4.1 (the plain form);
+ * NRD_JV_ANALYTIC exact tangent.  Inside nrd_newton / nrd_step the analytic
+ * form evaluates the tangent's face coefficients once per Newton iterate
+ * (nrd_linearise) and applies them per Krylov iteration (NRD_JV_FROZEN). */
+enum { NRD_JV_FD = 0, NRD_JV_ANALYTIC = 1, NRD_JV_FROZEN = 2 };
 enum { NRD_PC_F64 = 0, NRD_PC_F32 = 1 };
 
 /* Solver and model parameters.  nrd_params_default() fills the values used
@@ -178,10 +182,21 @@ int nrd_residual(nrd_ctx* ctx, const double* u, const double* b, double a0, doub
  *                         may be NULL);
  *   mode NRD_JV_FD:       (F(u + eps v) - F0)/eps of Sec. 4.1 Eq. Jac-free
  *                         with the two-branch eps of Sec. 4.1 (b required;
- *                         F0 = F(u) required).
+ *                         F0 = F(u) required);
+ *   mode NRD_JV_FROZEN:   the exact tangent at the state of the last
+ *                         nrd_linearise (u, b, F0 unused and may be NULL;
+ *                         NRD_ESTATE if there was none).
  * Jv: 2*ncells doubles, 0 on covered cells. */
 int nrd_jv(nrd_ctx* ctx, const double* u, const double* v, const double* b, const double* F0,
            double a0, double dt, int mode, double* Jv, cudaStream_t stream);
+
+/* Residual plus linearisation at u: writes F (as nrd_residual) and freezes
+ * (a) the partial derivatives of every face flux and of the coupling term at
+ * u (the exact Jacobian of Sec. 4.1, applied later by nrd_jv with
+ * NRD_JV_FROZEN), and (b) the preconditioner of Sec. 4.2 at u (as
+ * nrd_precond_setup).  u, b, F: 2*ncells doubles. */
+int nrd_linearise(nrd_ctx* ctx, const double* u, const double* b, double a0, double dt, double* F,
+                  cudaStream_t stream);
 
 /* The differencing parameter eps(u, v) of Sec. 4.1 (synchronises; result in
  * *eps_host). */

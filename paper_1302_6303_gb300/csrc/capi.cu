@@ -56,9 +56,10 @@ void set_model(nrd_ctx* c) {
 
 void free_fields(nrd_ctx* c) {
   auto F = [](void* p) { if (p) cudaFree(p); };
-  F(c->d_z); F(c->d_gz); F(c->d_gu); F(c->d_gv); F(c->d_cf); F(c->d_tmp);
+  F(c->d_z); F(c->d_gz); F(c->d_gu); F(c->d_gv); F(c->d_cf); F(c->d_tmp); F(c->d_jc); F(c->d_cc);
   c->d_z = nullptr; c->d_gz = nullptr; c->d_gu = nullptr; c->d_gv = nullptr; c->d_cf = nullptr;
-  c->d_tmp = nullptr;
+  c->d_tmp = nullptr; c->d_jc = nullptr; c->d_cc = nullptr;
+  c->lin_ready = false;
   reducer_free(c->R);
   if (c->pc) pc_free(c->pc);
   c->pc = nullptr;
@@ -87,9 +88,54 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
   return check_launch(c);
 }
 
+int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
+                  cudaStream_t s) {
+  Hier& H = c->H;
+  launch_ghost_fill(H, c->mp, c->d_z, u, c->d_gu, 1, s);
+  StencilIO io{};
+  io.u = u;
+  io.gu = c->d_gu;
+  io.b = b;
+  io.a0 = a0;
+  io.dt = dt;
+  io.out = F;
+  io.cfflux = c->d_cf;
+  io.jc = c->d_jc;
+  io.craw = pc_craw(c->pc);
+  io.cc = c->d_cc;
+  c->timer.begin(NRD_TK_RESIDUAL, s);
+  launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s);
+  c->timer.end(NRD_TK_RESIDUAL, s);
+  launch_reflux(H, io, ST_RESIDUAL, s);
+  c->timer.begin(NRD_TK_PC_SETUP, s);
+  int rc = pc_finish(c->pc, H, u, c->d_z, a0, dt, s);
+  c->timer.end(NRD_TK_PC_SETUP, s);
+  if (rc != NRD_OK) return fail(c, rc, "preconditioner set-up failed");
+  c->lin_ready = true;
+  c->pc_ready = true;
+  return check_launch(c);
+}
+
 int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const double* F0,
            double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s) {
   Hier& H = c->H;
+  if (mode == NRD_JV_FROZEN) {
+    c->timer.begin(NRD_TK_GHOST, s);
+    launch_ghost_fill(H, c->mp, c->d_z, v, c->d_gv, 0, s);
+    c->timer.end(NRD_TK_GHOST, s);
+    StencilIO io{};
+    io.v = v;
+    io.gv = c->d_gv;
+    io.a0 = a0;
+    io.dt = dt;
+    io.out = Jv;
+    io.cfflux = c->d_cf;
+    c->timer.begin(NRD_TK_JV, s);
+    launch_jv_frozen(H, c->mp, c->d_jc, c->d_cc, io, s);
+    c->timer.end(NRD_TK_JV, s);
+    launch_reflux(H, io, ST_JV, s);
+    return check_launch(c);
+  }
   if (fill_u_ghosts) launch_ghost_fill(H, c->mp, c->d_z, u, c->d_gu, 1, s);
   c->timer.begin(NRD_TK_GHOST, s);
   launch_ghost_fill(H, c->mp, c->d_z, v, c->d_gv, 0, s);
@@ -220,6 +266,8 @@ int nrd_set_hierarchy(nrd_ctx* c, int nlevels, const int* nboxes, const int* box
             cudaMalloc(&c->d_gv, 2 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_cf, 2 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_tmp, 2 * N * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_jc, 5 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_cc, 2 * N * sizeof(double)) == cudaSuccess &&
             reducer_init(c->R, (int)N) == NRD_OK;
   if (!ok) {
     free_fields(c);
@@ -262,6 +310,7 @@ int nrd_set_material(nrd_ctx* c, const float* z, cudaStream_t s) {
   launch_ghost_z(c->H, c->d_z, c->d_gz, s);
   c->have_mat = true;
   c->pc_ready = false;
+  c->lin_ready = false;
   return check_launch(c);
 }
 
@@ -296,9 +345,22 @@ int nrd_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const 
   int rc = need_ready(c);
   if (rc) return rc;
   if (!u || !v || !Jv) return fail(c, NRD_EINVAL, "null argument");
-  if (mode != NRD_JV_FD && mode != NRD_JV_ANALYTIC) return fail(c, NRD_EINVAL, "bad mode");
+  if (mode != NRD_JV_FD && mode != NRD_JV_ANALYTIC && mode != NRD_JV_FROZEN)
+    return fail(c, NRD_EINVAL, "bad mode");
   if (mode == NRD_JV_FD && (!b || !F0)) return fail(c, NRD_EINVAL, "FD mode needs b and F0");
+  if (mode == NRD_JV_FROZEN && !c->lin_ready)
+    return fail(c, NRD_ESTATE, "NRD_JV_FROZEN needs nrd_linearise first");
   return ctx_jv(c, u, v, b, F0, a0, dt, mode, Jv, true, s);
+}
+
+int nrd_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
+                  cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!u || !b || !F) return fail(c, NRD_EINVAL, "null argument");
+  if (!(a0 > 0.0) || !(dt > 0.0)) return fail(c, NRD_EINVAL, "a0 and dt must be positive");
+  return ctx_linearise(c, u, b, a0, dt, F, s);
 }
 
 int nrd_fd_eps(nrd_ctx* c, const double* u, const double* v, double* eps_host, cudaStream_t s) {
@@ -398,7 +460,7 @@ int nrd_tag(nrd_ctx* c, const double* u, double thr_c, double thr_g, double thr_
   size_t N = H.N;
   // composite values: covered cells := mean of their children
   cudaMemcpyAsync(c->d_tmp, u, 2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  launch_average_down(H, c->d_tmp, 1, (int)N, s);
+  launch_average_down(H, c->d_tmp, 2, (int)N, s);
   launch_ghost_fill(H, c->mp, c->d_z, c->d_tmp, c->d_gu, 1, s);
   launch_emax(H, c->R, u, 2, s);
   launch_tag(H, c->d_tmp, c->d_gu, thr_c, thr_g, thr_r, c->R.d_res + 2, tags, s);

@@ -968,10 +968,10 @@ void pc_free(PcState* ps) {
   delete ps;
 }
 
-int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u, const double* gu,
-             const float* z, const float* gz, double a0, double dt, cudaStream_t s) {
-  ps->beta = dt / a0;
-  ps->z = z;
+double* pc_craw(PcState* ps) { return ps->Craw; }
+
+static SetupArgs setup_args(PcState* ps, const Hier& H, const ModelParams* mp, const double* u,
+                            const double* gu, const float* z, const float* gz) {
   SetupArgs a;
   a.tiles = H.d_tiles;
   a.patches = H.d_patches;
@@ -989,15 +989,21 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
   a.ntiles = (int)H.tiles.size();
   a.ty = H.tile_y;
   a.tz = H.tile_z;
-  a.k = mp.k;
-  a.cL = (mp.limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
+  a.k = mp ? mp->k : 0.0;
+  a.cL = (mp && mp->limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
   a.beta = ps->beta;
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
     for (int d = 0; d < 3; d++) a.lh.h[l][d] = (l < H.L) ? H.lev[l].h[d] : 1.0;
   a.Craw = ps->Craw;
+  return a;
+}
+
+int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
+              cudaStream_t s) {
+  ps->beta = dt / a0;
+  ps->z = z;
+  SetupArgs a = setup_args(ps, H, nullptr, u, nullptr, z, nullptr);
   cudaMemcpyAsync(ps->Tk, u + H.N, (size_t)H.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  int nt = (int)H.tiles.size();
-  k_coef<<<std::min(nt, 152 * 8), BS, 0, s>>>(a);
   for (int l = H.L - 2; l >= 0; l--) {
     if (!H.ncz[l]) continue;
     dim3 g(g1(H.ncz[l]), 2);
@@ -1020,6 +1026,15 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
     scale_boxes<double>(ps, s);
   }
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
+}
+
+int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u, const double* gu,
+             const float* z, const float* gz, double a0, double dt, cudaStream_t s) {
+  ps->beta = dt / a0;
+  SetupArgs a = setup_args(ps, H, &mp, u, gu, z, gz);
+  int nt = (int)H.tiles.size();
+  k_coef<<<std::min(nt, 152 * 8), BS, 0, s>>>(a);
+  return pc_finish(ps, H, u, z, a0, dt, s);
 }
 
 int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {

@@ -16,6 +16,9 @@ namespace {
 
 struct LevelH {
   double h[NRD_MAX_LEVELS][3];
+  double rh[NRD_MAX_LEVELS][3];   // 1/h
+  double h3[NRD_MAX_LEVELS][3];   // 3h
+  double kh[NRD_MAX_LEVELS][3];   // k/h
 };
 
 struct GhostArgs {
@@ -101,7 +104,7 @@ struct StArgs {
 //           Zs = z_a^3 + z_b^3, dE = E_b - E_a, Tf = (T_a + T_b)/2
 //   Phi_T = k Tf^(5/2) (T_b - T_a)/h.
 __device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double Tb, double za,
-                                         double zb, double h, double kh, double cL, double& PE,
+                                         double zb, double h3, double kh, double cL, double& PE,
                                          double& PT) {
   double Tf = 0.5 * (Ta + Tb);
   double Tf2 = Tf * Tf;
@@ -110,14 +113,53 @@ __device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double
   double S = Ea + Eb;
   double Zs = za + zb;
   double num = 2.0 * Tf3 * dE * S;
-  double den = 3.0 * h * Zs * S + cL * Tf3 * fabs(dE);
+  double den = h3 * Zs * S + cL * Tf3 * fabs(dE);
   PE = num / den;
   PT = kh * Tf2 * sqrt(Tf) * (Tb - Ta);
 }
 
+// Linearisation of one face at the iterate: the fluxes, the frozen
+// coefficients D_E = 2 Tf^3 S h / den and D_T = k Tf^(5/2) of Sec. 4.2, and
+// the partial derivatives of Phi_E w.r.t. E_a, E_b and T_a (= w.r.t. T_b) and
+// of Phi_T w.r.t. T_a, T_b (sign(0) = 0).
+struct FaceLin {
+  double PE, PT, CE, CT, aEa, aEb, aT, bTa, bTb;
+};
+__device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, double Tb, double za,
+                                            double zb, double h, double h3, double kh, double k,
+                                            double cL) {
+  FaceLin r;
+  double Tf = 0.5 * (Ta + Tb);
+  double Tf2 = Tf * Tf;
+  double Tf3 = Tf2 * Tf;
+  double dE = Eb - Ea;
+  double S = Ea + Eb;
+  double Zs = za + zb;
+  double adE = fabs(dE);
+  double sg = (dE > 0.0) ? 1.0 : ((dE < 0.0) ? -1.0 : 0.0);
+  double hz = h3 * Zs;
+  double lt = cL * Tf3;
+  double rden = 1.0 / (hz * S + lt * adE);
+  double t2 = 2.0 * Tf3;
+  r.PE = t2 * S * dE * rden;
+  r.CE = t2 * S * h * rden;
+  r.aEa = (-2.0 * t2 * Ea - r.PE * (hz - lt * sg)) * rden;
+  r.aEb = (2.0 * t2 * Eb - r.PE * (hz + lt * sg)) * rden;
+  r.aT = (3.0 * Tf2 * S * dE - r.PE * 1.5 * cL * Tf2 * adE) * rden;
+  double sq = sqrt(Tf);
+  double T25 = Tf2 * sq, T15 = Tf * sq;
+  double dT = Tb - Ta;
+  r.CT = k * T25;
+  r.PT = kh * T25 * dT;
+  double q = 1.25 * T15 * dT;
+  r.bTa = kh * (q - T25);
+  r.bTb = kh * (q + T25);
+  return r;
+}
+
 // Tangent of flux_val in the direction (dEa, dEb, dTa, dTb); sign(0) = 0.
 __device__ __forceinline__ void flux_tan(double Ea, double Eb, double Ta, double Tb, double za,
-                                         double zb, double h, double kh, double cL, double vEa,
+                                         double zb, double h3, double kh, double cL, double vEa,
                                          double vEb, double vTa, double vTb, double& dPE,
                                          double& dPT) {
   double Tf = 0.5 * (Ta + Tb);
@@ -131,8 +173,8 @@ __device__ __forceinline__ void flux_tan(double Ea, double Eb, double Ta, double
   double sg = (dE > 0.0) ? 1.0 : ((dE < 0.0) ? -1.0 : 0.0);
   double num = 2.0 * Tf3 * dE * S;
   double dnum = 2.0 * (dTf3 * dE * S + Tf3 * (ddE * S + dE * dS));
-  double den = 3.0 * h * Zs * S + cL * Tf3 * fabs(dE);
-  double dden = 3.0 * h * Zs * dS + cL * (dTf3 * fabs(dE) + Tf3 * sg * ddE);
+  double den = h3 * Zs * S + cL * Tf3 * fabs(dE);
+  double dden = h3 * Zs * dS + cL * (dTf3 * fabs(dE) + Tf3 * sg * ddE);
   double rden = 1.0 / den;
   double PE = num * rden;
   dPE = (dnum - PE * dden) * rden;
@@ -166,6 +208,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
   constexpr int NC = TX * TY * TZ;
   constexpr bool TAN = (MODE == ST_JV);
+  constexpr bool LIN = (MODE == ST_LIN);
   extern __shared__ double smem[];
   double* sE = smem;
   double* sT = sE + NH;
@@ -180,15 +223,19 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   double* sZ = fzT + NFZ;                     // z^3 of the halo cells
 
   const int N = A.N, G = A.G;
+  const long NS = 3L * N + G;                  // face slots per coefficient array
   const StencilIO& io = A.io;
-  double eps = 0.0;
-  if (MODE == ST_FD) eps = *io.eps;
+  double eps = 0.0, reps = 0.0;
+  if (MODE == ST_FD) {
+    eps = *io.eps;
+    reps = 1.0 / eps;
+  }
 
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
     const TileDev tile = A.tiles[t];
     const PatchDev P = A.patches[tile.patch];
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const double hx = A.lh.h[P.level][0], hy = A.lh.h[P.level][1], hz = A.lh.h[P.level][2];
+    const int lvl = P.level;
     if (tile.flags & 1) {
       // every cell covered: not unknowns
       for (int c = threadIdx.x; c < NC; c += blockDim.x) {
@@ -217,7 +264,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         e = io.u[idx];
         tt = io.u[N + idx];
         z = (double)A.z[idx];
-        if (MODE != ST_RESIDUAL) {
+        if (MODE == ST_JV || MODE == ST_FD) {
           ve = io.v[idx];
           vt = io.v[N + idx];
         }
@@ -232,7 +279,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         e = io.gu[gi];
         tt = io.gu[G + gi];
         z = (double)A.gz[gi];
-        if (MODE != ST_RESIDUAL) {
+        if (MODE == ST_JV || MODE == ST_FD) {
           ve = io.gv[gi];
           vt = io.gv[G + gi];
         }
@@ -251,49 +298,100 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     }
     __syncthreads();
     // ---- face fluxes, each computed once
-    auto face = [&](int dir, int fi, int fj, int fk, double* outE, double* outT, int slot) {
+    for (int f = threadIdx.x; f < NFX + NFY + NFZ; f += blockDim.x) {
+      int dir, fi, fj, fk, slot;
+      double* outE;
+      double* outT;
+      if (f < NFX) {
+        dir = 0; slot = f;
+        fi = f % (TX + 1); fj = (f / (TX + 1)) % TY; fk = f / ((TX + 1) * TY);
+        outE = fxE; outT = fxT;
+      } else if (f < NFX + NFY) {
+        dir = 1; slot = f - NFX;
+        fi = slot % TX; fj = (slot / TX) % (TY + 1); fk = slot / (TX * (TY + 1));
+        outE = fyE; outT = fyT;
+      } else {
+        dir = 2; slot = f - NFX - NFY;
+        fi = slot % TX; fj = (slot / TX) % TY; fk = slot / (TX * TY);
+        outE = fzE; outT = fzT;
+      }
       // face on the low side of tile cell (fi, fj, fk) along dir
       int i = tile.i0 + fi, j = tile.j0 + fj, k = tile.k0 + fk;
+      if (i > nx || j > ny || k > nz) continue;
+      if ((dir != 0 && i >= nx) || (dir != 1 && j >= ny) || (dir != 2 && k >= nz)) continue;
       int pos = (dir == 0) ? i : ((dir == 1) ? j : k);
       int nd = P.n[dir];
-      if (i > nx || j > ny || k > nz) return;
-      if ((dir != 0 && i >= nx) || (dir != 1 && j >= ny) || (dir != 2 && k >= nz)) return;
       int hb = (fi + 1) + HX * ((fj + 1) + HY * (fk + 1));   // high-side cell
       int st = (dir == 0) ? 1 : ((dir == 1) ? HX : HX * HY);
       int ha = hb - st;                                      // low-side cell
-      double h = (dir == 0) ? hx : ((dir == 1) ? hy : hz);
-      double kh = A.k / h;
+      const double h = A.lh.h[lvl][dir], h3 = A.lh.h3[lvl][dir], kh = A.lh.kh[lvl][dir];
       double PE = 0.0, PT = 0.0;
       uint8_t gt = GT_SIBLING;
       int gi = -1;
+      long fslot;                                            // coefficient slot
       if (pos == 0 || pos == nd) {
-        int f = 2 * dir + (pos == nd ? 1 : 0);
+        int ff = 2 * dir + (pos == nd ? 1 : 0);
         int a, b;
         if (dir == 0) { a = j; b = k; }
         else if (dir == 1) { a = k; b = i; }
         else { a = i; b = j; }
-        gi = P.goff + P.fo[f] + a + P.n[(dir + 1) % 3] * b;
+        gi = P.goff + P.fo[ff] + a + P.n[(dir + 1) % 3] * b;
         gt = A.gtype[gi];
+        fslot = 3L * N + gi;
+      } else {
+        fslot = (long)dir * N + P.off + i + (long)nx * (j + (long)ny * k);
       }
       if (gt == GT_NEUMANN) {
         PE = 0.0;
         PT = 0.0;
+        if (LIN) {
+          for (int q = 0; q < 5; q++) io.jc[q * NS + fslot] = 0.0;
+          io.craw[fslot] = 0.0;
+          io.craw[NS + fslot] = 0.0;
+        }
       } else if (gt == GT_ROBIN) {
         int s = (pos == 0) ? -1 : 1;
         int hc = (pos == 0) ? hb : ha;      // the interior cell
-        int f = 2 * dir + (pos == nd ? 1 : 0);
-        if (TAN)
-          PE = robin_tan(sE[hc], sT[hc], sZ[hc], h, A.R[f], s, svE[hc], svT[hc]);
-        else
-          PE = robin_flux(sE[hc], sT[hc], sZ[hc], h, A.R[f], s);
+        int ff = 2 * dir + (pos == nd ? 1 : 0);
+        if (TAN) {
+          PE = robin_tan(sE[hc], sT[hc], sZ[hc], h, A.R[ff], s, svE[hc], svT[hc]);
+        } else {
+          PE = robin_flux(sE[hc], sT[hc], sZ[hc], h, A.R[ff], s);
+        }
+        if (LIN) {
+          // dPhi/dE_c and dPhi/dT_c in slots 0 and 1; raw P1 slot holds D_b
+          double Ec = sE[hc], Tc = sT[hc], zc = sZ[hc];
+          double Db = Tc * Tc * Tc / (3.0 * zc);
+          double qd = 4.0 * Db + h;
+          double rq = 1.0 / qd;
+          double m = 2.0 * Ec - 8.0 * A.R[ff];
+          io.jc[fslot] = -(double)s * 2.0 * Db * rq;
+          io.jc[NS + fslot] = -(double)s * (Tc * Tc / zc) * m * h * rq * rq;
+          io.jc[2 * NS + fslot] = 0.0;
+          io.jc[3 * NS + fslot] = 0.0;
+          io.jc[4 * NS + fslot] = 0.0;
+          io.craw[fslot] = Db;
+          io.craw[NS + fslot] = 0.0;
+        }
         PT = 0.0;
       } else {
-        if (TAN)
-          flux_tan(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, kh, A.cL,
-                   svE[ha], svE[hb], svT[ha], svT[hb], PE, PT);
-        else
-          flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, kh, A.cL,
-                   PE, PT);
+        if (TAN) {
+          flux_tan(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, svE[ha], svE[hb],
+                   svT[ha], svT[hb], PE, PT);
+        } else if (LIN) {
+          FaceLin L = flux_lin(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, h3, kh, A.k, A.cL);
+          PE = L.PE;
+          PT = L.PT;
+          io.jc[fslot] = L.aEa;
+          io.jc[NS + fslot] = L.aEb;
+          io.jc[2 * NS + fslot] = L.aT;
+          io.jc[3 * NS + fslot] = L.bTa;
+          io.jc[4 * NS + fslot] = L.bTb;
+          io.craw[fslot] = L.CE;
+          io.craw[NS + fslot] = L.CT;
+        } else {
+          flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, PE, PT);
+        }
         if (gt == GT_CF) {
           io.cfflux[gi] = PE;
           io.cfflux[G + gi] = PT;
@@ -301,23 +399,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
       outE[slot] = PE;
       outT[slot] = PT;
-    };
-    for (int f = threadIdx.x; f < NFX + NFY + NFZ; f += blockDim.x) {
-      if (f < NFX) {
-        int fi = f % (TX + 1), fj = (f / (TX + 1)) % TY, fk = f / ((TX + 1) * TY);
-        face(0, fi, fj, fk, fxE, fxT, f);
-      } else if (f < NFX + NFY) {
-        int g = f - NFX;
-        int fi = g % TX, fj = (g / TX) % (TY + 1), fk = g / (TX * (TY + 1));
-        face(1, fi, fj, fk, fyE, fyT, g);
-      } else {
-        int g = f - NFX - NFY;
-        int fi = g % TX, fj = (g / TX) % TY, fk = g / (TX * TY);
-        face(2, fi, fj, fk, fzE, fzT, g);
-      }
     }
     __syncthreads();
     // ---- cell balance
+    const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
     for (int c = threadIdx.x; c < NC; c += blockDim.x) {
       int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
       int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
@@ -327,22 +412,23 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       if (m & MASK_COVERED) {
         io.out[idx] = 0.0;
         io.out[N + idx] = 0.0;
+        if (LIN) {
+          io.cc[idx] = 0.0;
+          io.cc[N + idx] = 0.0;
+        }
         continue;
       }
       int xl = ci + (TX + 1) * (cj + TY * ck);
       int yl = ci + TX * (cj + (TY + 1) * ck);
       int zl = ci + TX * (cj + TY * ck);
       // coarse-side coarse-fine faces take their flux from flux matching
-      double xlo = (m & 2) ? 0.0 : 1.0, xhi = (m & 4) ? 0.0 : 1.0;
-      double ylo = (m & 8) ? 0.0 : 1.0, yhi = (m & 16) ? 0.0 : 1.0;
-      double zlo = (m & 32) ? 0.0 : 1.0, zhi = (m & 64) ? 0.0 : 1.0;
-      auto pick = [](double keep, double v) { return keep != 0.0 ? v : 0.0; };
-      double divE = (pick(xhi, fxE[xl + 1]) - pick(xlo, fxE[xl])) / hx +
-                    (pick(yhi, fyE[yl + TX]) - pick(ylo, fyE[yl])) / hy +
-                    (pick(zhi, fzE[zl + TX * TY]) - pick(zlo, fzE[zl])) / hz;
-      double divT = (pick(xhi, fxT[xl + 1]) - pick(xlo, fxT[xl])) / hx +
-                    (pick(yhi, fyT[yl + TX]) - pick(ylo, fyT[yl])) / hy +
-                    (pick(zhi, fzT[zl + TX * TY]) - pick(zlo, fzT[zl])) / hz;
+      auto pick = [](bool skip, double v) { return skip ? 0.0 : v; };
+      double divE = (pick(m & 4, fxE[xl + 1]) - pick(m & 2, fxE[xl])) * rhx +
+                    (pick(m & 16, fyE[yl + TX]) - pick(m & 8, fyE[yl])) * rhy +
+                    (pick(m & 64, fzE[zl + TX * TY]) - pick(m & 32, fzE[zl])) * rhz;
+      double divT = (pick(m & 4, fxT[xl + 1]) - pick(m & 2, fxT[xl])) * rhx +
+                    (pick(m & 16, fyT[yl + TX]) - pick(m & 8, fyT[yl])) * rhy +
+                    (pick(m & 64, fzT[zl + TX * TY]) - pick(m & 32, fzT[zl])) * rhz;
       int hc = (ci + 1) + HX * ((cj + 1) + HY * (ck + 1));
       double E = sE[hc], T = sT[hc], z = sZ[hc];
       double T2 = T * T, T3 = T2 * T;
@@ -353,20 +439,125 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         double dc = sig * ((T3 + 3.0 * E * rT) * vT - vE);
         io.out[idx] = io.a0 * vE - io.dt * (divE + dc);
         io.out[N + idx] = io.a0 * vT - io.dt * (divT - dc);
+      } else if (MODE == ST_LIN) {
+        double rT = 1.0 / T;
+        double sig = z * rT * rT * rT;
+        double cp = sig * (T2 * T2 - E);
+        io.out[idx] = io.a0 * E - io.b[idx] - io.dt * (divE + cp);
+        io.out[N + idx] = io.a0 * T - io.b[N + idx] - io.dt * (divT - cp);
+        // coupling tangent dc = cE vE + cT vT
+        io.cc[idx] = -sig;
+        io.cc[N + idx] = sig * (T3 + 3.0 * E * rT);
       } else {
         double sig = z / T3;
         double cp = sig * (T2 * T2 - E);
         double FE = io.a0 * E - io.b[idx] - io.dt * (divE + cp);
         double FT = io.a0 * T - io.b[N + idx] - io.dt * (divT - cp);
         if (MODE == ST_FD) {
-          FE = (FE - io.F0[idx]) / eps;
-          FT = (FT - io.F0[N + idx]) / eps;
+          FE = (FE - io.F0[idx]) * reps;
+          FT = (FT - io.F0[N + idx]) * reps;
         }
         io.out[idx] = FE;
         io.out[N + idx] = FT;
       }
     }
     __syncthreads();
+  }
+}
+
+// Jv with the Jacobian frozen at the last linearisation (ST_LIN): each face
+// tangent flux is a linear combination of the tangent values on its two
+// sides with the stored partial derivatives, so one Jv is a memory-bound
+// stencil application.  Same face classification as k_stencil.
+struct JfArgs {
+  const TileDev* tiles;
+  const PatchDev* patches;
+  const uint8_t* mask;
+  const uint8_t* gtype;
+  int ntiles, N, G, ty, tz;
+  LevelH lh;
+  const double* jc;   // [5][3N+G]
+  const double* cc;   // [2][N]
+  const double* v;    // [2][N]
+  const double* gv;   // [2][G] ghosts of v
+  double a0, dt;
+  double* out;
+  double* cfflux;
+};
+
+__global__ void __launch_bounds__(256) k_jv_frozen(JfArgs a) {
+  const int N = a.N, G = a.G;
+  const long NS = 3L * N + G;
+  const int nc = NRD_TX * a.ty * a.tz;
+  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const TileDev tile = a.tiles[t];
+    const PatchDev P = a.patches[tile.patch];
+    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
+    const int lvl = P.level;
+    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % a.ty;
+      int k = tile.k0 + c / (NRD_TX * a.ty);
+      if (i >= nx || j >= ny || k >= nz) continue;
+      const int idx = P.off + i + nx * (j + ny * k);
+      const uint8_t m = a.mask[idx];
+      if (m & MASK_COVERED) {
+        a.out[idx] = 0.0;
+        a.out[N + idx] = 0.0;
+        continue;
+      }
+      const double vEc = a.v[idx], vTc = a.v[N + idx];
+      const int loc[3] = {i, j, k};
+      const int st[3] = {1, nx, nx * ny};
+      double divE = 0.0, divT = 0.0;
+      for (int d = 0; d < 3; d++) {
+        double PEs[2], PTs[2];
+        for (int sd = 0; sd < 2; sd++) {
+          const int f = 2 * d + sd;
+          PEs[sd] = 0.0;
+          PTs[sd] = 0.0;
+          if (m & (2 << f)) continue;                      // coarse side: flux matching
+          const bool bnd = sd ? (loc[d] == P.n[d] - 1) : (loc[d] == 0);
+          long slot;
+          double vEa, vEb, vTa, vTb;
+          int gi = -1;
+          uint8_t gt = GT_SIBLING;
+          if (!bnd) {
+            const int nb = sd ? idx + st[d] : idx - st[d];
+            slot = (long)d * N + (sd ? nb : idx);
+            if (sd) { vEa = vEc; vTa = vTc; vEb = a.v[nb]; vTb = a.v[N + nb]; }
+            else { vEa = a.v[nb]; vTa = a.v[N + nb]; vEb = vEc; vTb = vTc; }
+          } else {
+            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+            gi = P.goff + P.fo[f] + loc[t1] + P.n[t1] * loc[t2];
+            gt = a.gtype[gi];
+            slot = 3L * N + gi;
+            const double gE = a.gv[gi], gT = a.gv[G + gi];
+            if (sd) { vEa = vEc; vTa = vTc; vEb = gE; vTb = gT; }
+            else { vEa = gE; vTa = gT; vEb = vEc; vTb = vTc; }
+          }
+          if (gt == GT_NEUMANN) continue;
+          if (gt == GT_ROBIN) {
+            PEs[sd] = a.jc[slot] * vEc + a.jc[NS + slot] * vTc;
+            continue;
+          }
+          const double pe = a.jc[slot] * vEa + a.jc[NS + slot] * vEb +
+                            a.jc[2 * NS + slot] * (vTa + vTb);
+          const double pt = a.jc[3 * NS + slot] * vTa + a.jc[4 * NS + slot] * vTb;
+          PEs[sd] = pe;
+          PTs[sd] = pt;
+          if (gt == GT_CF) {
+            a.cfflux[gi] = pe;
+            a.cfflux[G + gi] = pt;
+          }
+        }
+        const double rh = a.lh.rh[lvl][d];
+        divE += (PEs[1] - PEs[0]) * rh;
+        divT += (PTs[1] - PTs[0]) * rh;
+      }
+      const double dc = a.cc[idx] * vEc + a.cc[N + idx] * vTc;
+      a.out[idx] = a.a0 * vEc - a.dt * (divE + dc);
+      a.out[N + idx] = a.a0 * vTc - a.dt * (divT - dc);
+    }
   }
 }
 
@@ -477,10 +668,16 @@ int blocks_for(long n, int bs) {
   return (int)b;
 }
 
-LevelH level_h(const Hier& H) {
+LevelH level_h(const Hier& H, double k = 0.01) {
   LevelH lh;
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
-    for (int d = 0; d < 3; d++) lh.h[l][d] = (l < H.L) ? H.lev[l].h[d] : 1.0;
+    for (int d = 0; d < 3; d++) {
+      double h = (l < H.L) ? H.lev[l].h[d] : 1.0;
+      lh.h[l][d] = h;
+      lh.rh[l][d] = 1.0 / h;
+      lh.h3[l][d] = 3.0 * h;
+      lh.kh[l][d] = k / h;
+    }
   return lh;
 }
 
@@ -559,10 +756,11 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   a.k = mp.k;
   a.cL = (mp.limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
   for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
-  a.lh = level_h(H);
+  a.lh = level_h(H, mp.k);
   a.io = io;
   if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_y, H.tile_z, s);
+  else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_y, H.tile_z, s);
   else dispatch_tile<ST_FD>(a, H.tile_y, H.tile_z, s);
 }
 
@@ -580,6 +778,30 @@ void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s)
   a.lh = level_h(H);
   k_reflux<<<blocks_for(H.nrf, 128), 128, 0, s>>>(a, H.d_rf_level, io.cfflux, io.out, io.dt,
                                                    io.eps, mode);
+}
+
+void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, const double* cc,
+                      const StencilIO& io, cudaStream_t s) {
+  JfArgs a;
+  a.tiles = H.d_tiles;
+  a.patches = H.d_patches;
+  a.mask = H.d_mask;
+  a.gtype = H.d_gtype;
+  a.ntiles = (int)H.tiles.size();
+  a.N = H.N;
+  a.G = H.G;
+  a.ty = H.tile_y;
+  a.tz = H.tile_z;
+  a.lh = level_h(H, mp.k);
+  a.jc = jc;
+  a.cc = cc;
+  a.v = io.v;
+  a.gv = io.gv;
+  a.a0 = io.a0;
+  a.dt = io.dt;
+  a.out = io.out;
+  a.cfflux = io.cfflux;
+  k_jv_frozen<<<std::min(a.ntiles, 152 * 8), 256, 0, s>>>(a);
 }
 
 void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, double thr_g,

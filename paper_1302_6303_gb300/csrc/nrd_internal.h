@@ -110,7 +110,7 @@ int hier_upload(Hier& H, std::string& err);
 void hier_free(Hier& H);
 
 // Kernel launchers (k_stencil.cu)
-enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2 };
+enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2, ST_LIN = 3 };
 struct StencilIO {
   const double* u;      // state (E then T)
   const double* v;      // direction (JV, FD)
@@ -122,6 +122,10 @@ struct StencilIO {
   double a0, dt;
   double* out;          // F or Jv
   double* cfflux;       // [2][G] fine-side coarse-fine fluxes
+  // ST_LIN outputs (face slots: [3N low faces | G boundary faces])
+  double* jc;           // [5][3N+G] flux partial derivatives
+  double* craw;         // [2][3N+G] frozen D_E, D_T (Robin slots: D_b)
+  double* cc;           // [2][N] coupling tangent coefficients
 };
 void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
                        double* g, int nonlinear, cudaStream_t s);
@@ -129,6 +133,8 @@ void launch_ghost_z(const Hier& H, const float* z, float* gz, cudaStream_t s);
 void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const float* gz,
                     int mode, const StencilIO& io, cudaStream_t s);
 void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s);
+void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, const double* cc,
+                      const StencilIO& io, cudaStream_t s);
 void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, double thr_g,
                 double thr_r, const double* emax, uint8_t* tags, cudaStream_t s);
 void launch_average_down(const Hier& H, double* x, int nfield, int fstride, cudaStream_t s);
@@ -171,6 +177,11 @@ void pc_free(PcState* ps);
 int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u, const double* gu,
              const float* z, const float* gz, double a0, double dt, cudaStream_t s);
 int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s);
+// raw coefficient array [2][3N+G] the linearisation writes into
+double* pc_craw(PcState* ps);
+// coarsen + scale after the raw coefficients were written at u
+int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
+              cudaStream_t s);
 
 #define CUDA_TRY(x)                                         \
   do {                                                      \
@@ -227,6 +238,9 @@ struct nrd_ctx {
   double* d_gv = nullptr;      // 2G: ghosts of a direction
   double* d_cf = nullptr;      // 2G: fine-side coarse-fine fluxes
   double* d_tmp = nullptr;     // 2N scratch
+  double* d_jc = nullptr;      // [5][3N+G] frozen flux partial derivatives
+  double* d_cc = nullptr;      // [2][N] frozen coupling tangent coefficients
+  bool lin_ready = false;
   Reducer R;
   PcState* pc = nullptr;
   bool pc_ready = false;
@@ -253,3 +267,5 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
                  bool fill_ghosts, cudaStream_t s);
 int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const double* F0,
            double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s);
+int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
+                  cudaStream_t s);

@@ -144,7 +144,7 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
   const long stride = n2;
   const int m = c->kry_m;
   Small S = small_of(c);
-  const int mode = c->p.jv_mode;
+  const int mode = (c->p.jv_mode == NRD_JV_ANALYTIC) ? NRD_JV_FROZEN : NRD_JV_FD;
   cudaMemsetAsync(c->d_dx, 0, n2 * sizeof(double), s);
   // r0 = -F
   double rn2 = fn * fn;
@@ -223,7 +223,14 @@ int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, 
   const int n2 = 2 * H.N;
   nrd_stats loc{};
   loc.min_lambda = 1.0;
-  rc = ctx_residual(c, u, b, a0, dt, c->d_F, true, s);
+  // analytic form: residual, exact-Jacobian face coefficients and the
+  // preconditioner are produced together at every iterate
+  const bool lin = (c->p.jv_mode == NRD_JV_ANALYTIC);
+  auto evaluate = [&](void) -> int {
+    if (lin) return ctx_linearise(c, u, b, a0, dt, c->d_F, s);
+    return ctx_residual(c, u, b, a0, dt, c->d_F, true, s);
+  };
+  rc = evaluate();
   if (rc != NRD_OK) return rc;
   launch_wdot(H, c->R, c->d_F, c->d_F, SL_F, s);
   double fn = std::sqrt(read_slot(c, SL_F, s));
@@ -236,11 +243,13 @@ int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, 
   double eta = c->p.eta_max;
   int it = 0;
   while (fn > stop && it < c->p.max_newton) {
-    c->timer.begin(NRD_TK_PC_SETUP, s);
-    rc = pc_setup(c->pc, H, c->mp, u, c->d_gu, c->d_z, c->d_gz, a0, dt, s);
-    c->timer.end(NRD_TK_PC_SETUP, s);
-    if (rc != NRD_OK) { c->err = "preconditioner set-up failed"; return rc; }
-    c->pc_ready = true;
+    if (!lin) {
+      c->timer.begin(NRD_TK_PC_SETUP, s);
+      rc = pc_setup(c->pc, H, c->mp, u, c->d_gu, c->d_z, c->d_gz, a0, dt, s);
+      c->timer.end(NRD_TK_PC_SETUP, s);
+      if (rc != NRD_OK) { c->err = "preconditioner set-up failed"; return rc; }
+      c->pc_ready = true;
+    }
     loc.pc_setups++;
     int its = 0;
     rc = gmres(c, u, b, a0, dt, fn, eta * fn, &its, s);
@@ -256,7 +265,7 @@ int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, 
     }
     loc.min_lambda = std::min(loc.min_lambda, lam);
     launch_axpy(n2, lam, c->d_dx, u, s);
-    rc = ctx_residual(c, u, b, a0, dt, c->d_F, true, s);
+    rc = evaluate();
     if (rc != NRD_OK) return rc;
     launch_wdot(H, c->R, c->d_F, c->d_F, SL_F, s);
     double fold = fn;

@@ -18,13 +18,13 @@ _LIBPATH = os.path.join(_HERE, "libnrd.so")
 OK, EINVAL, ENOMEM, ENONCONV, ENEG, ENAN, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 BC_NEUMANN, BC_ROBIN = 0, 1
 LIM_WILSON, LIM_PAPER_LITERAL = 0, 1
-JV_FD, JV_ANALYTIC = 0, 1
+JV_FD, JV_ANALYTIC, JV_FROZEN = 0, 1, 2
 PC_F64, PC_F32 = 0, 1
 
 EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
-    "nrd_jv", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
+    "nrd_jv", "nrd_linearise", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
     "nrd_step", "nrd_tag", "nrd_timing_enable", "nrd_timing_read",
 ]
 TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST = range(7)
@@ -85,6 +85,7 @@ def load(path: str = _LIBPATH):
         "nrd_ghost_fill": (c_int, [vp, dp, dp, dp, fp, vp]),
         "nrd_residual": (c_int, [vp, dp, dp, c_dbl, c_dbl, dp, vp]),
         "nrd_jv": (c_int, [vp, dp, dp, dp, dp, c_dbl, c_dbl, c_int, dp, vp]),
+        "nrd_linearise": (c_int, [vp, dp, dp, c_dbl, c_dbl, dp, vp]),
         "nrd_fd_eps": (c_int, [vp, dp, dp, P(c_dbl), vp]),
         "nrd_dot": (c_int, [vp, dp, dp, P(c_dbl), vp]),
         "nrd_precond_setup": (c_int, [vp, dp, c_dbl, c_dbl, vp]),
@@ -197,6 +198,12 @@ class Context:
         self._check(self.lib.nrd_jv(self._h, _ptr(u, torch.float64), _ptr(v, torch.float64),
                                     _ptr(b, torch.float64), _ptr(F0, torch.float64), a0, dt, mode,
                                     _ptr(out, torch.float64), _stream()))
+        return out
+
+    def linearise(self, u, b, a0, dt, out=None):
+        out = torch.empty_like(u) if out is None else out
+        self._check(self.lib.nrd_linearise(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
+                                           a0, dt, _ptr(out, torch.float64), _stream()))
         return out
 
     def fd_eps(self, u, v):

@@ -253,3 +253,51 @@ def test_errors_are_reported(nrd):
     with pytest.raises(nrd.NrdError) as e:
         ctx.set_hierarchy(h.nboxes + [1], boxes, h.bc_type, h.bc_R)
     assert e.value.code == nrd.EINVAL
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_linearise_and_frozen_jv(nrd, name):
+    """nrd_linearise returns the residual and freezes the exact Jacobian: the
+    frozen Jv equals the oracle's tangent (dual numbers) within 1e-12 S."""
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z, pc_precision=0)
+    u = _state(h)
+    v = W.random_direction(h, 11)
+    b = u * 0.97
+    a0, dt = 1.3, 2e-3
+    F = ctx.linearise(dev(u), dev(b), a0, dt).cpu().numpy()
+    Fo = o.residual(u, b, a0, dt)
+    S = o.residual_scale(u, b, a0, dt)
+    assert np.all(np.abs(F - Fo) <= 1e-12 * S + 1e-300)
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_FROZEN).cpu().numpy()
+    Jo = o.jv_analytic(u, v, a0, dt)
+    Sj = o.jv_scale(u, v, a0, dt)
+    err = np.abs(J - Jo)
+    assert np.all(err <= 1e-12 * Sj + 1e-300), (err / np.maximum(Sj, 1e-300)).max()
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    assert np.all(J[~leaf] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["single32", "tiny3", "boundary", "amr2_16"])
+def test_linearise_sets_up_preconditioner(nrd, name):
+    h, z = CASES[name]()
+    nmg = auto_nmg(h, 3)
+    ctx, o = make(nrd, h, z, pc_precision=0, nmg=nmg)
+    o.set_solver(nmg=nmg, nu1=2, nu2=2, coarse_sweeps=4)
+    u = _state(h)
+    a0, dt = 1.2, 5e-3
+    ctx.linearise(dev(u), dev(u), a0, dt)
+    o.pc_setup(u, a0, dt)
+    w = W.random_direction(h, 6)
+    y = ctx.precond_apply(dev(w)).cpu().numpy()
+    yo = o.pc_apply(w)
+    assert np.abs(y - yo).max() <= 1e-11 * np.abs(yo).max()
+
+
+def test_frozen_jv_requires_linearise(nrd):
+    h, z = CASES["single32"]()
+    ctx, _ = make(nrd, h, z)
+    u = dev(_state(h))
+    with pytest.raises(nrd.NrdError) as e:
+        ctx.jv(u, u, 1.0, 1e-3, mode=nrd.JV_FROZEN)
+    assert e.value.code == nrd.ESTATE
