@@ -106,7 +106,9 @@ typedef struct {
   int max_newton;      /* Newton iteration cap */
   double eta_max;      /* Eisenstat-Walker forcing cap (and eta_0) */
   double ew_gamma;     /* Eisenstat-Walker gamma */
-  int tile_y, tile_z;  /* stencil tile shape 32 x tile_y x tile_z (0: auto) */
+  int tile_x, tile_y, tile_z;  /* stencil tile shape (0,0,0: 32 x 4 x 4); one of
+                                  32x4x4, 32x8x4, 32x4x8, 32x2x4, 16x8x4, 16x4x8,
+                                  16x8x8, 16x4x4, 8x8x8 */
 } nrd_params;
 
 /* Statistics of one Newton solve (nrd_newton / nrd_step). */
@@ -240,6 +242,14 @@ int nrd_step(nrd_ctx* ctx, double* u, const double* u_n, const double* u_nm1, do
  * (gradient), bit 2: h |grad E| / E > thr_r.  tags: ncells bytes. */
 int nrd_tag(nrd_ctx* ctx, const double* u, double thr_c, double thr_g, double thr_r,
             uint8_t* tags, cudaStream_t stream);
+
+/* Tile-shape autotuner: times the linearisation stencil, one frozen-Jacobian
+ * Jv and one preconditioner application at the state u for every supported
+ * tile shape (3 repetitions each, CUDA events, after one warm-up) and keeps
+ * the fastest for this context.  Synchronises.  tile_out_host[3] receives the
+ * chosen shape and ms_out_host the best time (either may be NULL). */
+int nrd_autotune(nrd_ctx* ctx, const double* u, const double* b, double a0, double dt,
+                 int* tile_out_host, double* ms_out_host, cudaStream_t stream);
 
 /* ------------------------------------------------------- kernel timing
  * Optional CUDA-event timing of the library's kernel groups, recorded on the

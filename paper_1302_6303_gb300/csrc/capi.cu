@@ -10,6 +10,11 @@ namespace {
 
 const char* kNullCtx = "null context";
 
+// tile shapes with compiled stencil instances
+const int kShapes[][3] = {{32, 4, 4}, {32, 8, 4}, {32, 4, 8}, {32, 2, 4}, {16, 8, 4},
+                          {16, 4, 8}, {16, 8, 8}, {16, 4, 4}, {8, 8, 8}};
+const int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
 int fail(nrd_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -38,10 +43,10 @@ int check_params(const nrd_params* p, std::string& err) {
   if (p->nmg < 1 || p->nmg > NRD_MAX_MG) { err = "nmg must be in [1, 12]"; return NRD_EINVAL; }
   if (!(p->rtol >= 0.0) || !(p->atol >= 0.0)) { err = "tolerances must be >= 0"; return NRD_EINVAL; }
   if (p->max_newton < 1) { err = "max_newton must be >= 1"; return NRD_EINVAL; }
-  int ty = p->tile_y, tz = p->tile_z;
-  bool ok = (ty == 0 && tz == 0) || (ty == 4 && tz == 4) || (ty == 8 && tz == 4) ||
-            (ty == 4 && tz == 8) || (ty == 2 && tz == 4) || (ty == 4 && tz == 2);
-  if (!ok) { err = "tile shape must be 32x{4x4,8x4,4x8,2x4,4x2}"; return NRD_EINVAL; }
+  bool ok = (p->tile_x == 0 && p->tile_y == 0 && p->tile_z == 0);
+  for (int t = 0; t < kNumShapes && !ok; t++)
+    ok = (p->tile_x == kShapes[t][0] && p->tile_y == kShapes[t][1] && p->tile_z == kShapes[t][2]);
+  if (!ok) { err = "unsupported tile shape"; return NRD_EINVAL; }
   return NRD_OK;
 }
 
@@ -188,6 +193,7 @@ int nrd_params_default(nrd_params* p) {
   p->max_newton = 20;
   p->eta_max = 0.9;
   p->ew_gamma = 0.9;
+  p->tile_x = 0;
   p->tile_y = 0;
   p->tile_z = 0;
   return NRD_OK;
@@ -226,15 +232,25 @@ int nrd_set_params(nrd_ctx* c, const nrd_params* p) {
   if (!c || !p) return NRD_EINVAL;
   std::string err;
   if (check_params(p, err) != NRD_OK) return fail(c, NRD_EINVAL, err);
-  bool retile = (p->tile_y != c->p.tile_y || p->tile_z != c->p.tile_z);
+  bool retile = (p->tile_x != c->p.tile_x || p->tile_y != c->p.tile_y ||
+                 p->tile_z != c->p.tile_z);
   bool repc = (p->nmg != c->p.nmg || p->pc_precision != c->p.pc_precision ||
                p->restart != c->p.restart);
   c->p = *p;
   set_model(c);
-  if (c->have_hier && (retile || repc)) {
-    // rebuild work-lists with the new tile shape / preconditioner levels
-    return fail(c, NRD_ESTATE, "tile shape, nmg, precision or restart changed: call "
-                               "nrd_set_hierarchy again");
+  if (c->pc) pc_set_sweeps(c->pc, p->nu1, p->nu2, p->coarse_sweeps);
+  if (c->have_hier && retile) {
+    c->H.tile_x = p->tile_x ? p->tile_x : 32;
+    c->H.tile_y = p->tile_y ? p->tile_y : 4;
+    c->H.tile_z = p->tile_z ? p->tile_z : 4;
+    std::string err;
+    int rc = hier_tiles(c->H, err);
+    if (rc != NRD_OK) return fail(c, rc, err);
+    if (c->pc) pc_drop_graphs(c->pc);
+  }
+  if (c->have_hier && repc) {
+    return fail(c, NRD_ESTATE, "nmg, precision or restart changed: call nrd_set_hierarchy "
+                               "again");
   }
   return NRD_OK;
 }
@@ -248,6 +264,7 @@ int nrd_set_hierarchy(nrd_ctx* c, int nlevels, const int* nboxes, const int* box
   c->have_hier = false;
   c->have_mat = false;
   c->H = Hier();
+  c->H.tile_x = c->p.tile_x ? c->p.tile_x : 32;
   c->H.tile_y = c->p.tile_y ? c->p.tile_y : 4;
   c->H.tile_z = c->p.tile_z ? c->p.tile_z : 4;
   std::string err;
@@ -464,6 +481,71 @@ int nrd_tag(nrd_ctx* c, const double* u, double thr_c, double thr_g, double thr_
   launch_ghost_fill(H, c->mp, c->d_z, c->d_tmp, c->d_gu, 1, s);
   launch_emax(H, c->R, u, 2, s);
   launch_tag(H, c->d_tmp, c->d_gu, thr_c, thr_g, thr_r, c->R.d_res + 2, tags, s);
+  return check_launch(c);
+}
+
+int nrd_autotune(nrd_ctx* c, const double* u, const double* b, double a0, double dt,
+                 int* tile_out, double* ms_out, cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!u || !b) return fail(c, NRD_EINVAL, "null argument");
+  if (!(a0 > 0.0) || !(dt > 0.0)) return fail(c, NRD_EINVAL, "a0 and dt must be positive");
+  rc = solver_alloc(c);
+  if (rc != NRD_OK) return rc;
+  Hier& H = c->H;
+  const size_t n2 = 2 * (size_t)H.N;
+  bool timer_on = c->timer.on;
+  c->timer.on = false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = -1;
+  float best_ms = 1e30f;
+  std::string err;
+  for (int t = 0; t < kNumShapes; t++) {
+    H.tile_x = kShapes[t][0];
+    H.tile_y = kShapes[t][1];
+    H.tile_z = kShapes[t][2];
+    if (hier_tiles(H, err) != NRD_OK) continue;
+    pc_drop_graphs(c->pc);
+    float ms = 0.0f;
+    for (int rep = 0; rep < 4; rep++) {
+      cudaEventRecord(e0, s);
+      ctx_linearise(c, u, b, a0, dt, c->d_F, s);
+      pc_apply(c->pc, H, c->d_F, c->d_w, s);
+      ctx_jv(c, u, c->d_w, nullptr, nullptr, a0, dt, NRD_JV_FROZEN, c->d_r, false, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        c->timer.on = timer_on;
+        return fail(c, NRD_ECUDA, "autotune synchronisation failed");
+      }
+      float m = 0.0f;
+      cudaEventElapsedTime(&m, e0, e1);
+      if (rep > 0) ms += m;
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timer.on = timer_on;
+  if (best < 0) return fail(c, NRD_ECUDA, "no tile shape could be timed");
+  H.tile_x = c->p.tile_x = kShapes[best][0];
+  H.tile_y = c->p.tile_y = kShapes[best][1];
+  H.tile_z = c->p.tile_z = kShapes[best][2];
+  if (hier_tiles(H, err) != NRD_OK) return fail(c, NRD_ECUDA, err);
+  pc_drop_graphs(c->pc);
+  c->lin_ready = false;
+  (void)n2;
+  if (tile_out) {
+    tile_out[0] = H.tile_x;
+    tile_out[1] = H.tile_y;
+    tile_out[2] = H.tile_z;
+  }
+  if (ms_out) *ms_out = best_ms / 3.0;
   return check_launch(c);
 }
 

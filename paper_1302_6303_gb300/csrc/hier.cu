@@ -421,31 +421,9 @@ int hier_upload(Hier& H, std::string& err) {
     const PatchDev& Q = H.patches[H.cell_patch[iq]];
     cov[l].push_back(make_int4(idx, iq, Q.n[0], Q.n[0] * Q.n[1]));
   }
-  // tiles
-  H.tiles.clear();
-  for (int l = 0; l < L; l++) {
-    LevelInfo& Lv = H.lev[l];
-    Lv.t0 = (int)H.tiles.size();
-    for (int p = Lv.p0; p < Lv.p0 + Lv.np; p++) {
-      const PatchDev& P = H.patches[p];
-      for (int k0 = 0; k0 < P.n[2]; k0 += H.tile_z)
-        for (int j0 = 0; j0 < P.n[1]; j0 += H.tile_y)
-          for (int i0 = 0; i0 < P.n[0]; i0 += NRD_TX) {
-            TileDev t{p, i0, j0, k0, 0};
-            bool all = true;
-            for (int k = k0; k < std::min(k0 + H.tile_z, P.n[2]) && all; k++)
-              for (int j = j0; j < std::min(j0 + H.tile_y, P.n[1]) && all; j++)
-                for (int i = i0; i < std::min(i0 + NRD_TX, P.n[0]) && all; i++)
-                  if (!(mask[P.off + i + P.n[0] * (j + P.n[1] * k)] & MASK_COVERED)) all = false;
-            t.flags = all ? 1 : 0;
-            H.tiles.push_back(t);
-          }
-    }
-    Lv.nt = (int)H.tiles.size() - Lv.t0;
-  }
+  H.hmask = mask;
   // upload
   UP(H.d_patches, H.patches);
-  UP(H.d_tiles, H.tiles);
   UP(H.d_mask, mask);
   UP(H.d_wvol, wvol);
   UP(H.d_gtype, gtype);
@@ -460,6 +438,10 @@ int hier_upload(Hier& H, std::string& err) {
   UP(H.d_rf_face, rf_face);
   UP(H.d_rf_g, rf_g);
   UP(H.d_rf_level, rf_level);
+  {
+    int rc = hier_tiles(H, err);
+    if (rc != NRD_OK) return rc;
+  }
   for (int l = 0; l < L; l++) {
     H.ncz[l] = (int)cz_tgt[l].size();
     UP(H.d_cz_tgt[l], cz_tgt[l]);
@@ -468,6 +450,36 @@ int hier_upload(Hier& H, std::string& err) {
     UP(H.d_cov[l], cov[l]);
     if (l + 1 < L) UP(H.d_lmap[l], H.lmap[l]);
   }
+  return NRD_OK;
+}
+
+int hier_tiles(Hier& H, std::string& err) {
+  const int L = H.L;
+  H.tiles.clear();
+  const int TX = H.tile_x, TY = H.tile_y, TZ = H.tile_z;
+  for (int l = 0; l < L; l++) {
+    LevelInfo& Lv = H.lev[l];
+    Lv.t0 = (int)H.tiles.size();
+    for (int p = Lv.p0; p < Lv.p0 + Lv.np; p++) {
+      const PatchDev& P = H.patches[p];
+      for (int k0 = 0; k0 < P.n[2]; k0 += TZ)
+        for (int j0 = 0; j0 < P.n[1]; j0 += TY)
+          for (int i0 = 0; i0 < P.n[0]; i0 += TX) {
+            TileDev t{p, i0, j0, k0, 0};
+            bool all = true;
+            for (int k = k0; k < std::min(k0 + TZ, P.n[2]) && all; k++)
+              for (int j = j0; j < std::min(j0 + TY, P.n[1]) && all; j++)
+                for (int i = i0; i < std::min(i0 + TX, P.n[0]) && all; i++)
+                  if (!(H.hmask[P.off + i + P.n[0] * (j + P.n[1] * k)] & MASK_COVERED)) all = false;
+            t.flags = all ? 1 : 0;
+            H.tiles.push_back(t);
+          }
+    }
+    Lv.nt = (int)H.tiles.size() - Lv.t0;
+  }
+  if (H.d_tiles) cudaFree(H.d_tiles);
+  H.d_tiles = nullptr;
+  UP(H.d_tiles, H.tiles);
   return NRD_OK;
 }
 

@@ -6,6 +6,7 @@
 // deterministic run to run.
 #include <algorithm>
 #include <cfloat>
+#include <utility>
 
 #include "nrd_internal.h"
 
@@ -140,27 +141,42 @@ __global__ void k_emax(const uint8_t* __restrict__ mask, const double* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
-// res[i] = <w, V_i>, i < nv: w read once, each V_i once.
+// res[i] = <w, V_i>, i < NV: w read once, each V_i once; NV is a template
+// parameter so the accumulators stay in registers.
+template <int NV>
 __global__ void k_mdot(const float* __restrict__ wv, const double* __restrict__ w,
-                       const double* __restrict__ V, long stride, int nv, int N, double* part) {
+                       const double* __restrict__ V, long stride, int N, double* part) {
   __shared__ double sh[32];
-  double acc[NVMAX];
+  double acc[NV];
 #pragma unroll
-  for (int q = 0; q < NVMAX; q++) acc[q] = 0.0;
+  for (int q = 0; q < NV; q++) acc[q] = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     double vol = (double)wv[i];
     double wE = vol * w[i], wT = vol * w[N + i];
 #pragma unroll
-    for (int q = 0; q < NVMAX; q++)
-      if (q < nv) acc[q] += wE * V[q * stride + i] + wT * V[q * stride + N + i];
+    for (int q = 0; q < NV; q++) acc[q] += wE * V[q * stride + i] + wT * V[q * stride + N + i];
   }
 #pragma unroll
-  for (int q = 0; q < NVMAX; q++) {
-    if (q < nv) {
-      double r = block_red<0>(acc[q], sh);
-      if (threadIdx.x == 0) part[(long)blockIdx.x * nv + q] = r;
-    }
+  for (int q = 0; q < NV; q++) {
+    double r = block_red<0>(acc[q], sh);
+    if (threadIdx.x == 0) part[(long)blockIdx.x * NV + q] = r;
   }
+}
+
+template <int NV>
+void mdot_launch(int nblk, cudaStream_t s, const float* wv, const double* w, const double* V,
+                 long stride, int N, double* part) {
+  k_mdot<NV><<<nblk, RB, 0, s>>>(wv, w, V, stride, N, part);
+}
+
+template <int... I>
+void mdot_dispatch(std::integer_sequence<int, I...>, int nv, int nblk, cudaStream_t s,
+                   const float* wv, const double* w, const double* V, long stride, int N,
+                   double* part) {
+  using Fn = void (*)(int, cudaStream_t, const float*, const double*, const double*, long, int,
+                      double*);
+  static const Fn table[] = {&mdot_launch<I + 1>...};
+  table[nv - 1](nblk, s, wv, w, V, stride, N, part);
 }
 
 __global__ void k_mupdate(int n2, double* __restrict__ w, const double* __restrict__ V, long stride,
@@ -268,7 +284,8 @@ void launch_emax(const Hier& H, Reducer& R, const double* E, int slot, cudaStrea
 
 void launch_mdot(const Hier& H, Reducer& R, const double* w, const double* V, long stride, int nv,
                  int slot, cudaStream_t s) {
-  k_mdot<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, nv, H.N, R.d_part);
+  mdot_dispatch(std::make_integer_sequence<int, NVMAX>{}, nv, R.nblk, s, H.d_wvol, w, V, stride,
+                H.N, R.d_part);
   k_finish<0><<<1, 1024, 0, s>>>(R.d_part, R.nblk, nv, R.d_res, slot);
 }
 

@@ -232,18 +232,18 @@ __device__ __forceinline__ void lev_row(const HierV<P>& V, const PatchDev& Pt, i
 }
 
 template <class P>
-__global__ void k_lev_rbgs(HierV<P> V, int t0, int nt, int ty, int tz, P* e, const P* f,
+__global__ void k_lev_rbgs(HierV<P> V, int t0, int nt, int tx, int ty, int tz, P* e, const P* f,
                            const P* gh, int colour) {
   const int fld = blockIdx.y;
   P* ef = e + (long)fld * V.N;
   const P* ff = f + (long)fld * V.N;
   const P* gf = gh + (long)fld * V.G;
-  const int nc = NRD_TX * ty * tz;
+  const int nc = tx * ty * tz;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     const TileDev tile = V.tiles[t0 + t];
     const PatchDev Pt = V.patches[tile.patch];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % ty, k = tile.k0 + c / (NRD_TX * ty);
+      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
       if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) continue;
       if (((Pt.lo[0] + i + Pt.lo[1] + j + Pt.lo[2] + k) & 1) != colour) continue;
       long idx = Pt.off + i + (long)Pt.n[0] * (j + (long)Pt.n[1] * k);
@@ -284,7 +284,7 @@ __global__ void k_lin_ghost(const uint8_t* gtype, const int* gt0, const int* gid
 // r = f - L^c u on leaf cells (composite operator with coarse-fine
 // interpolation); fine-side coarse-fine fluxes a (u_g - u_c) go to cf.
 template <class P>
-__global__ void k_comp_resid(HierV<P> V, int ntiles, int ty, int tz, const P* u, const P* f,
+__global__ void k_comp_resid(HierV<P> V, int ntiles, int tx, int ty, int tz, const P* u, const P* f,
                              const P* gh, P* r, P* cf) {
   const int fld = blockIdx.y;
   const long N = V.N;
@@ -294,13 +294,13 @@ __global__ void k_comp_resid(HierV<P> V, int ntiles, int ty, int tz, const P* u,
   const P* gf = gh + (long)fld * V.G;
   P* rf = r + fld * N;
   P* cff = cf + (long)fld * V.G;
-  const int nc = NRD_TX * ty * tz;
+  const int nc = tx * ty * tz;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const TileDev tile = V.tiles[t];
     const PatchDev Pt = V.patches[tile.patch];
     const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % ty, k = tile.k0 + c / (NRD_TX * ty);
+      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
       if (i >= nx || j >= ny || k >= nz) continue;
       long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
       uint8_t m = V.mask[idx];
@@ -376,18 +376,18 @@ __global__ void k_add_leaf(const uint8_t* mask, int c0, int n, int N, const P* e
 // pv(level m) = trilinear interpolation of src(level m-1) via the dense map;
 // u += pv on uncovered level-m cells
 template <class P>
-__global__ void k_prolong_level(const TileDev* tiles, const PatchDev* patches, int t0, int nt, int ty,
-                                int tz, const uint8_t* mask, const int* cmap, int cn0, int cn1,
+__global__ void k_prolong_level(const TileDev* tiles, const PatchDev* patches, int t0, int nt, int tx,
+                                int ty, int tz, const uint8_t* mask, const int* cmap, int cn0, int cn1,
                                 int cn2, int N, const P* src, P* pv, P* u) {
   const int fld = blockIdx.y;
   const int cn[3] = {cn0, cn1, cn2};
   const P* s = src + (long)fld * N;
-  const int nc = NRD_TX * ty * tz;
+  const int nc = tx * ty * tz;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     const TileDev tile = tiles[t0 + t];
     const PatchDev Pt = patches[tile.patch];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % ty, k = tile.k0 + c / (NRD_TX * ty);
+      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
       if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) continue;
       long idx = Pt.off + i + (long)Pt.n[0] * (j + (long)Pt.n[1] * k);
       int q[3] = {Pt.lo[0] + i, Pt.lo[1] + j, Pt.lo[2] + k};
@@ -400,11 +400,12 @@ __global__ void k_prolong_level(const TileDev* tiles, const PatchDev* patches, i
 
 // y = P2^{-1} z per leaf cell, P2 = [[1 + s b, -s b T^3], [-s b, 1 + s b T^3]],
 // s = z^3/T^3 at the frozen iterate (Sec. 4.2)
-template <class P>
-__global__ void k_p2(const uint8_t* mask, int N, const P* zin, const double* Tk, const float* zm,
-                     double beta, double* y) {
+// P2 data frozen at the iterate: p[c] = sigma beta, p[N+c] = sigma beta T^3,
+// p[2N+c] = 1/det with P2 = [[1 + p0, -p1], [-p0, 1 + p1]].
+__global__ void k_p2_setup(const uint8_t* mask, int N, const double* Tk, const float* zm,
+                           const double* beta_p, double* p) {
+  const double beta = *beta_p;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    if (mask[c] & MASK_COVERED) { y[c] = 0.0; y[N + c] = 0.0; continue; }
     double T = Tk[c];
     double T3 = T * T * T;
     double z = (double)zm[c];
@@ -412,9 +413,21 @@ __global__ void k_p2(const uint8_t* mask, int N, const P* zin, const double* Tk,
     double a = 1.0 + sig * beta, b = -sig * beta * T3;
     double cc = -sig * beta, d = 1.0 + sig * beta * T3;
     double det = a * d - b * cc;
+    bool cov = mask[c] & MASK_COVERED;
+    p[c] = cov ? 0.0 : sig * beta;
+    p[N + c] = cov ? 0.0 : sig * beta * T3;
+    p[2L * N + c] = cov ? 0.0 : 1.0 / det;
+  }
+}
+
+// y = P2^{-1} z per leaf cell (Sec. 4.2); covered cells get 0
+template <class P>
+__global__ void k_p2(int N, const P* zin, const double* p, double* y) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    double sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
     double zE = (double)zin[c], zT = (double)zin[N + c];
-    y[c] = (d * zE - b * zT) / det;
-    y[N + c] = (a * zT - cc * zE) / det;
+    y[c] = ((1.0 + sbt) * zE + sbt * zT) * rd;
+    y[N + c] = ((1.0 + sb) * zT + sb * zE) * rd;
   }
 }
 
@@ -426,6 +439,7 @@ __global__ void k_cast(int n, const double* w, P* out) {
 
 // ----------------------------------------------------------- set-up kernels
 struct SetupArgs {
+  double bh2[NRD_MAX_LEVELS][3];   // beta / h^2
   const TileDev* tiles;
   const PatchDev* patches;
   const uint8_t* mask;
@@ -437,7 +451,7 @@ struct SetupArgs {
   const double* gu;    // its ghosts
   const float* z;
   const float* gz;
-  int N, G, ntiles, ty, tz;
+  int N, G, ntiles, tx, ty, tz;
   double k, cL, beta;
   LevelHP lh;
   double* Craw;        // [2][3N+G]
@@ -462,14 +476,14 @@ __device__ __forceinline__ void coef_pair(double Ea, double Eb, double Ta, doubl
 __global__ void k_coef(SetupArgs a) {
   const int N = a.N, G = a.G;
   const long AF = 3L * N + G;
-  const int nc = NRD_TX * a.ty * a.tz;
+  const int nc = a.tx * a.ty * a.tz;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const TileDev tile = a.tiles[t];
     const PatchDev Pt = a.patches[tile.patch];
     const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
     const double* hh = a.lh.h[Pt.level];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % a.ty, k = tile.k0 + c / (NRD_TX * a.ty);
+      int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty, k = tile.k0 + c / (a.tx * a.ty);
       if (i >= nx || j >= ny || k >= nz) continue;
       long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
       bool cov = a.mask[idx] & MASK_COVERED;
@@ -530,7 +544,7 @@ template <class P>
 __global__ void k_scale_hier(SetupArgs a, const int* cell_level_unused, P* A) {
   const int N = a.N, G = a.G;
   const long AF = 3L * N + G;
-  const int nc = NRD_TX * a.ty * a.tz;
+  const int nc = a.tx * a.ty * a.tz;
   const int fld = blockIdx.y;
   const double* C = a.Craw + fld * AF;
   P* Af = A + fld * AF;
@@ -540,13 +554,14 @@ __global__ void k_scale_hier(SetupArgs a, const int* cell_level_unused, P* A) {
     const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
     const double* hh = a.lh.h[Pt.level];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % a.ty, k = tile.k0 + c / (NRD_TX * a.ty);
+      int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty, k = tile.k0 + c / (a.tx * a.ty);
       if (i >= nx || j >= ny || k >= nz) continue;
       long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
       int loc[3] = {i, j, k};
+      const double* bh2 = a.bh2[Pt.level];
       for (int d = 0; d < 3; d++) {
         double h = hh[d];
-        if (loc[d] > 0) Af[d * (long)N + idx] = (P)(a.beta * C[d * (long)N + idx] / (h * h));
+        if (loc[d] > 0) Af[d * (long)N + idx] = (P)(C[d * (long)N + idx] * bh2[d]);
         for (int s = 0; s < 2; s++) {
           bool at = s ? (loc[d] == Pt.n[d] - 1) : (loc[d] == 0);
           if (!at) continue;
@@ -560,7 +575,7 @@ __global__ void k_scale_hier(SetupArgs a, const int* cell_level_unused, P* A) {
             double Db = C[3L * N + g];
             v = (fld == 0) ? a.beta * 2.0 * Db / (h * (4.0 * Db + h)) : 0.0;
           } else {
-            v = a.beta * C[3L * N + g] / (h * h);
+            v = C[3L * N + g] * bh2[d];
           }
           Af[3L * N + g] = (P)v;
         }
@@ -628,6 +643,7 @@ __global__ void k_box_scale(BoxRaw B, const double* Craw, const int* gtype_box, 
   P* Af = A + fld * B.AF;
   const long nc = (long)B.n[0] * B.n[1] * B.n[2];
   const double hh[3] = {hx, hy, hz};
+  const double bh2[3] = {beta / (hx * hx), beta / (hy * hy), beta / (hz * hz)};
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < nc;
        c += (long)gridDim.x * blockDim.x) {
     int q[3];
@@ -638,7 +654,7 @@ __global__ void k_box_scale(BoxRaw B, const double* Craw, const int* gtype_box, 
     for (int d = 0; d < 3; d++) {
       double h = hh[d];
       int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-      if (q[d] > 0) Af[d * B.NA + c] = (P)(beta * C[d * B.NA + c] / (h * h));
+      if (q[d] > 0) Af[d * B.NA + c] = (P)(C[d * B.NA + c] * bh2[d]);
       for (int sd = 0; sd < 2; sd++) {
         bool at = sd ? (q[d] == B.n[d] - 1) : (q[d] == 0);
         if (!at) continue;
@@ -683,6 +699,17 @@ struct PcState {
   void* be[NRD_MAX_MG] = {nullptr};
   void* bf[NRD_MAX_MG] = {nullptr};
   int* bgt = nullptr;    // [6] boundary type per box face (1 = Robin)
+  double* d_beta = nullptr;
+  double* p2 = nullptr;  // [3][N] frozen P2 data
+  // CUDA graphs of one apply, per (w, y) pair, captured on a private stream
+  struct Graph {
+    const double* w;
+    double* y;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;
+  bool use_graph = true;
 };
 
 namespace {
@@ -777,7 +804,7 @@ void composite_residual(PcState* ps, const Hier& H, cudaStream_t s) {
   HierV<P> V = hview<P>(ps, H);
   int nt = (int)H.tiles.size();
   dim3 gt(std::min(nt, 152 * 8), 2);
-  k_comp_resid<P><<<gt, BS, 0, s>>>(V, nt, H.tile_y, H.tile_z, (const P*)ps->fu,
+  k_comp_resid<P><<<gt, BS, 0, s>>>(V, nt, H.tile_x, H.tile_y, H.tile_z, (const P*)ps->fu,
                                     (const P*)ps->ff, (const P*)ps->gh, (P*)ps->fr, (P*)ps->cf);
   if (H.nrf) {
     dim3 gr(g1(H.nrf), 2);
@@ -803,7 +830,7 @@ void correct(PcState* ps, const Hier& H, int l, cudaStream_t s) {
     const LevelInfo& Lm = H.lev[m];
     const LevelInfo& Lc = H.lev[m - 1];
     dim3 gt(std::max(1, std::min(Lm.nt, 152 * 8)), 2);
-    k_prolong_level<P><<<gt, BS, 0, s>>>(H.d_tiles, H.d_patches, Lm.t0, Lm.nt, H.tile_y, H.tile_z,
+    k_prolong_level<P><<<gt, BS, 0, s>>>(H.d_tiles, H.d_patches, Lm.t0, Lm.nt, H.tile_x, H.tile_y, H.tile_z,
                                          H.d_mask, H.d_lmap[m - 1], Lc.n[0], Lc.n[1], Lc.n[2], H.N,
                                          (const P*)src, (P*)ps->fp, (P*)ps->fu);
     src = ps->fp;
@@ -822,7 +849,7 @@ void level_smooth(PcState* ps, const Hier& H, int l, int sweeps, bool red_first,
       if (Lv.ng)
         k_sib_ghost<P><<<gg, BS, 0, s>>>(H.d_gtype, H.d_gt0, H.d_gidx, Lv.g0, Lv.ng, H.N, H.G,
                                          (const P*)ps->fe, (P*)ps->gh);
-      k_lev_rbgs<P><<<gt, BS, 0, s>>>(V, Lv.t0, Lv.nt, H.tile_y, H.tile_z, (P*)ps->fe,
+      k_lev_rbgs<P><<<gt, BS, 0, s>>>(V, Lv.t0, Lv.nt, H.tile_x, H.tile_y, H.tile_z, (P*)ps->fe,
                                       (const P*)ps->fr, (const P*)ps->gh, colour);
     }
 }
@@ -862,7 +889,7 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t
     level_smooth<P>(ps, H, l, ps->nu2, false, s);
     correct<P>(ps, H, l, s);
   }
-  k_p2<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, ps->Tk, ps->z, ps->beta, y);
+  k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, ps->p2, y);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }
 
@@ -915,7 +942,10 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
             cudaMalloc(&ps->gh, 2 * std::max(G, 1L) * e) == cudaSuccess &&
             cudaMalloc(&ps->cf, 2 * std::max(G, 1L) * e) == cudaSuccess &&
             cudaMalloc(&ps->Tk, N * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&ps->bgt, 6 * sizeof(int)) == cudaSuccess;
+            cudaMalloc(&ps->bgt, 6 * sizeof(int)) == cudaSuccess &&
+            cudaMalloc(&ps->d_beta, sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ps->p2, 3 * N * sizeof(double)) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&ps->cap, cudaStreamNonBlocking) == cudaSuccess;
   if (ok) {
     cudaMemset(ps->Craw, 0, 2 * ps->AF * sizeof(double));
     cudaMemset(ps->A, 0, 2 * ps->AF * e);
@@ -959,11 +989,15 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
   return NRD_OK;
 }
 
+void pc_drop_graphs(PcState* ps);
+
 void pc_free(PcState* ps) {
   if (!ps) return;
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(ps->Craw); F(ps->A); F(ps->fu); F(ps->fr); F(ps->fe); F(ps->fp); F(ps->ff); F(ps->gh);
-  F(ps->cf); F(ps->Tk); F(ps->bgt);
+  F(ps->cf); F(ps->Tk); F(ps->bgt); F(ps->d_beta); F(ps->p2);
+  pc_drop_graphs(ps);
+  if (ps->cap) cudaStreamDestroy(ps->cap);
   for (int m = 0; m < NRD_MAX_MG; m++) { F(ps->bCraw[m]); F(ps->bA[m]); F(ps->be[m]); F(ps->bf[m]); }
   delete ps;
 }
@@ -987,13 +1021,17 @@ static SetupArgs setup_args(PcState* ps, const Hier& H, const ModelParams* mp, c
   a.N = H.N;
   a.G = H.G;
   a.ntiles = (int)H.tiles.size();
+  a.tx = H.tile_x;
   a.ty = H.tile_y;
   a.tz = H.tile_z;
   a.k = mp ? mp->k : 0.0;
   a.cL = (mp && mp->limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
   a.beta = ps->beta;
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
-    for (int d = 0; d < 3; d++) a.lh.h[l][d] = (l < H.L) ? H.lev[l].h[d] : 1.0;
+    for (int d = 0; d < 3; d++) {
+      a.lh.h[l][d] = (l < H.L) ? H.lev[l].h[d] : 1.0;
+      a.bh2[l][d] = a.beta / (a.lh.h[l][d] * a.lh.h[l][d]);
+    }
   a.Craw = ps->Craw;
   return a;
 }
@@ -1001,9 +1039,12 @@ static SetupArgs setup_args(PcState* ps, const Hier& H, const ModelParams* mp, c
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
               cudaStream_t s) {
   ps->beta = dt / a0;
+  if (ps->z != z) pc_drop_graphs(ps);
   ps->z = z;
+  cudaMemcpyAsync(ps->d_beta, &ps->beta, sizeof(double), cudaMemcpyHostToDevice, s);
   SetupArgs a = setup_args(ps, H, nullptr, u, nullptr, z, nullptr);
   cudaMemcpyAsync(ps->Tk, u + H.N, (size_t)H.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  k_p2_setup<<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, ps->Tk, z, ps->d_beta, ps->p2);
   for (int l = H.L - 2; l >= 0; l--) {
     if (!H.ncz[l]) continue;
     dim3 g(g1(H.ncz[l]), 2);
@@ -1037,7 +1078,43 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
   return pc_finish(ps, H, u, z, a0, dt, s);
 }
 
-int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {
+static int apply_any(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {
   if (ps->prec == NRD_PC_F32) return apply_t<float>(ps, H, w, y, s);
   return apply_t<double>(ps, H, w, y, s);
+}
+
+void pc_drop_graphs(PcState* ps) {
+  for (auto& g : ps->graphs) cudaGraphExecDestroy(g.exec);
+  ps->graphs.clear();
+}
+
+void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw) {
+  if (ps->nu1 != nu1 || ps->nu2 != nu2 || ps->csw != csw) pc_drop_graphs(ps);
+  ps->nu1 = nu1;
+  ps->nu2 = nu2;
+  ps->csw = csw;
+}
+
+// One apply is a fixed sequence of about a hundred small launches; it is
+// captured once per (w, y) pair into a CUDA graph and replayed.  Everything
+// the launches read besides w is at fixed addresses (beta in device memory).
+int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {
+  if (!ps->use_graph) return apply_any(ps, H, w, y, s);
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : ps->graphs)
+    if (g.w == w && g.y == y) { exec = g.exec; break; }
+  if (!exec) {
+    if (ps->graphs.size() >= 64) pc_drop_graphs(ps);
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(ps->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return NRD_ECUDA;
+    int rc = apply_any(ps, H, w, y, ps->cap);
+    cudaError_t e = cudaStreamEndCapture(ps->cap, &graph);
+    if (rc != NRD_OK || e != cudaSuccess) return NRD_ECUDA;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return NRD_ECUDA;
+    ps->graphs.push_back({w, y, exec});
+  }
+  return cudaGraphLaunch(exec, s) == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }

@@ -200,9 +200,8 @@ __device__ __forceinline__ double robin_tan(double E, double T, double z, double
   return -(double)s * (dDb * m * h + Db * dm * q) / (q * q);
 }
 
-template <int MODE, int TY, int TZ>
+template <int MODE, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
-  constexpr int TX = NRD_TX;
   constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
   constexpr int NH = HX * HY * HZ;
   constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
@@ -474,7 +473,7 @@ struct JfArgs {
   const PatchDev* patches;
   const uint8_t* mask;
   const uint8_t* gtype;
-  int ntiles, N, G, ty, tz;
+  int ntiles, N, G, tx, ty, tz;
   LevelH lh;
   const double* jc;   // [5][3N+G]
   const double* cc;   // [2][N]
@@ -488,15 +487,15 @@ struct JfArgs {
 __global__ void __launch_bounds__(256) k_jv_frozen(JfArgs a) {
   const int N = a.N, G = a.G;
   const long NS = 3L * N + G;
-  const int nc = NRD_TX * a.ty * a.tz;
+  const int nc = a.tx * a.ty * a.tz;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const TileDev tile = a.tiles[t];
     const PatchDev P = a.patches[tile.patch];
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     const int lvl = P.level;
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % a.ty;
-      int k = tile.k0 + c / (NRD_TX * a.ty);
+      int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty;
+      int k = tile.k0 + c / (a.tx * a.ty);
       if (i >= nx || j >= ny || k >= nz) continue;
       const int idx = P.off + i + nx * (j + ny * k);
       const uint8_t m = a.mask[idx];
@@ -600,17 +599,17 @@ __global__ void k_reflux(RfArgs a, const int* __restrict__ rf_level, const doubl
 
 // Sec. 5 indicators on every cell.  E holds composite values (covered cells
 // already averaged from their children); gE its ghosts.
-__global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles, int ty, int tz,
+__global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles, int tx, int ty, int tz,
                       const double* E, const double* gE, double thr_c, double thr_g,
                       double thr_r, const double* emax_p, uint8_t* tags) {
   const double emax = *emax_p;
-  const int nc = NRD_TX * ty * tz;
+  const int nc = tx * ty * tz;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const TileDev tile = tiles[t];
     const PatchDev P = patches[tile.patch];
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % NRD_TX, j = tile.j0 + (c / NRD_TX) % ty, k = tile.k0 + c / (NRD_TX * ty);
+      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
       if (i >= nx || j >= ny || k >= nz) continue;
       int idx = P.off + i + nx * (j + ny * k);
       double Ec = E[idx];
@@ -681,21 +680,20 @@ LevelH level_h(const Hier& H, double k = 0.01) {
   return lh;
 }
 
-template <int MODE, int TY, int TZ>
+template <int MODE, int TX, int TY, int TZ>
 size_t stencil_smem() {
-  constexpr int TX = NRD_TX;
   constexpr int NH = (TX + 2) * (TY + 2) * (TZ + 2);
   constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
   size_t d = (size_t)NH * (MODE == ST_JV ? 5 : 3) + 2 * (size_t)NF;
   return d * sizeof(double);
 }
 
-template <int MODE, int TY, int TZ>
+template <int MODE, int TX, int TY, int TZ>
 void run_stencil(const StArgs& a, cudaStream_t s) {
-  size_t sm = stencil_smem<MODE, TY, TZ>();
+  size_t sm = stencil_smem<MODE, TX, TY, TZ>();
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_stencil<MODE, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_stencil<MODE, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sm);
     init = true;
   }
@@ -704,16 +702,20 @@ void run_stencil(const StArgs& a, cudaStream_t s) {
   if (per_sm > 4) per_sm = 4;
   int grid = std::min(a.ntiles, 152 * per_sm);
   if (grid < 1) return;
-  k_stencil<MODE, TY, TZ><<<grid, 256, sm, s>>>(a);
+  k_stencil<MODE, TX, TY, TZ><<<grid, 256, sm, s>>>(a);
 }
 
 template <int MODE>
-void dispatch_tile(const StArgs& a, int ty, int tz, cudaStream_t s) {
-  if (ty == 8 && tz == 4) run_stencil<MODE, 8, 4>(a, s);
-  else if (ty == 4 && tz == 8) run_stencil<MODE, 4, 8>(a, s);
-  else if (ty == 2 && tz == 4) run_stencil<MODE, 2, 4>(a, s);
-  else if (ty == 4 && tz == 2) run_stencil<MODE, 4, 2>(a, s);
-  else run_stencil<MODE, 4, 4>(a, s);
+void dispatch_tile(const StArgs& a, int tx, int ty, int tz, cudaStream_t s) {
+  if (tx == 32 && ty == 8 && tz == 4) run_stencil<MODE, 32, 8, 4>(a, s);
+  else if (tx == 32 && ty == 4 && tz == 8) run_stencil<MODE, 32, 4, 8>(a, s);
+  else if (tx == 32 && ty == 2 && tz == 4) run_stencil<MODE, 32, 2, 4>(a, s);
+  else if (tx == 16 && ty == 8 && tz == 4) run_stencil<MODE, 16, 8, 4>(a, s);
+  else if (tx == 16 && ty == 4 && tz == 8) run_stencil<MODE, 16, 4, 8>(a, s);
+  else if (tx == 16 && ty == 8 && tz == 8) run_stencil<MODE, 16, 8, 8>(a, s);
+  else if (tx == 16 && ty == 4 && tz == 4) run_stencil<MODE, 16, 4, 4>(a, s);
+  else if (tx == 8 && ty == 8 && tz == 8) run_stencil<MODE, 8, 8, 8>(a, s);
+  else run_stencil<MODE, 32, 4, 4>(a, s);
 }
 
 }  // namespace
@@ -758,10 +760,10 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
   a.lh = level_h(H, mp.k);
   a.io = io;
-  if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_y, H.tile_z, s);
-  else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_y, H.tile_z, s);
-  else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_y, H.tile_z, s);
-  else dispatch_tile<ST_FD>(a, H.tile_y, H.tile_z, s);
+  if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else dispatch_tile<ST_FD>(a, H.tile_x, H.tile_y, H.tile_z, s);
 }
 
 void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s) {
@@ -790,6 +792,7 @@ void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, co
   a.ntiles = (int)H.tiles.size();
   a.N = H.N;
   a.G = H.G;
+  a.tx = H.tile_x;
   a.ty = H.tile_y;
   a.tz = H.tile_z;
   a.lh = level_h(H, mp.k);
@@ -808,7 +811,7 @@ void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, 
                 double thr_r, const double* emax, uint8_t* tags, cudaStream_t s) {
   // tag tiles: reuse the stencil tile list (tiles are at most 32 x 8 x 8)
   k_tag<<<std::min((int)H.tiles.size(), 152 * 8), 256, 0, s>>>(
-      H.d_tiles, H.d_patches, (int)H.tiles.size(), H.tile_y, H.tile_z, E, gE, thr_c, thr_g, thr_r,
+      H.d_tiles, H.d_patches, (int)H.tiles.size(), H.tile_x, H.tile_y, H.tile_z, E, gE, thr_c, thr_g, thr_r,
       emax, tags);
 }
 

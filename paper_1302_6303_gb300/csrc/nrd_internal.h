@@ -11,7 +11,6 @@
 
 #define NRD_MAX_LEVELS 8
 #define NRD_MAX_MG 12
-#define NRD_TX 32
 
 // Ghost cell kinds (one per face cell of every patch).
 enum : uint8_t { GT_NEUMANN = 0, GT_ROBIN = 1, GT_SIBLING = 2, GT_CF = 3 };
@@ -52,7 +51,8 @@ struct Hier {
   int N = 0, G = 0, nleaf = 0;
   int bc_type[6];
   double bc_R[6];
-  int tile_y = 4, tile_z = 4;
+  int tile_x = 32, tile_y = 4, tile_z = 4;
+  std::vector<uint8_t> hmask;             // host copy of the cell masks
 
   // host copies
   std::vector<PatchDev> patches;
@@ -107,6 +107,8 @@ struct nrd_ctx_s;
 int hier_build(Hier& H, int nlevels, const int* nboxes, const int* boxes, const int* bc_type,
                const double* bc_R, std::string& err);
 int hier_upload(Hier& H, std::string& err);
+// (re)build and upload the stencil tile list for shape tile_x x tile_y x tile_z
+int hier_tiles(Hier& H, std::string& err);
 void hier_free(Hier& H);
 
 // Kernel launchers (k_stencil.cu)
@@ -179,6 +181,8 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
 int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s);
 // raw coefficient array [2][3N+G] the linearisation writes into
 double* pc_craw(PcState* ps);
+void pc_drop_graphs(PcState* ps);
+void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw);
 // coarsen + scale after the raw coefficients were written at u
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
               cudaStream_t s);

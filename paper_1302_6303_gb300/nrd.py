@@ -25,7 +25,7 @@ EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
-    "nrd_step", "nrd_tag", "nrd_timing_enable", "nrd_timing_read",
+    "nrd_step", "nrd_tag", "nrd_autotune", "nrd_timing_enable", "nrd_timing_read",
 ]
 TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST = range(7)
 TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost"]
@@ -38,7 +38,8 @@ class Params(ctypes.Structure):
         ("pc_precision", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
         ("nmg", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("rtol", ctypes.c_double),
         ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("eta_max", ctypes.c_double),
-        ("ew_gamma", ctypes.c_double), ("tile_y", ctypes.c_int), ("tile_z", ctypes.c_int),
+        ("ew_gamma", ctypes.c_double), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+        ("tile_z", ctypes.c_int),
     ]
 
 
@@ -93,6 +94,7 @@ def load(path: str = _LIBPATH):
         "nrd_newton": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
+        "nrd_autotune": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
         "nrd_timing_read": (c_int, [vp, c_int, P(c_dbl), P(ctypes.c_int64)]),
     }
@@ -242,6 +244,14 @@ class Context:
         if check and rc != OK:
             self._check(rc)
         return st.as_dict()
+
+    def autotune(self, u, b, a0, dt):
+        """Pick the fastest stencil tile shape for this hierarchy at state u."""
+        t = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        self._check(self.lib.nrd_autotune(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
+                                          a0, dt, t, ctypes.byref(ms), _stream()))
+        return (t[0], t[1], t[2]), ms.value
 
     def timing_enable(self, on=True):
         self._check(self.lib.nrd_timing_enable(self._h, 1 if on else 0))

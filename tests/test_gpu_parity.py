@@ -301,3 +301,41 @@ def test_frozen_jv_requires_linearise(nrd):
     with pytest.raises(nrd.NrdError) as e:
         ctx.jv(u, u, 1.0, 1e-3, mode=nrd.JV_FROZEN)
     assert e.value.code == nrd.ESTATE
+
+
+SHAPES = [(32, 4, 4), (32, 8, 4), (32, 4, 8), (32, 2, 4), (16, 8, 4), (16, 4, 8), (16, 8, 8),
+          (16, 4, 4), (8, 8, 8)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_every_tile_shape(nrd, shape):
+    """Residual, frozen Jv and one FP64 V-cycle agree with the oracle for every
+    compiled tile shape (ragged tiles on 16-wide fine patches included)."""
+    h, z = CASES["amr2_16"]()
+    tx, ty, tz = shape
+    ctx, o = make(nrd, h, z, pc_precision=0, nmg=3, tile_x=tx, tile_y=ty, tile_z=tz)
+    o.set_solver(nmg=3)
+    u = _state(h)
+    a0, dt = 1.0, 2e-3
+    F = ctx.linearise(dev(u), dev(u), a0, dt).cpu().numpy()
+    S = o.residual_scale(u, u.copy(), a0, dt)
+    assert np.all(np.abs(F - o.residual(u, u.copy(), a0, dt)) <= 1e-12 * S + 1e-300)
+    v = W.random_direction(h, 3)
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_FROZEN).cpu().numpy()
+    Sj = o.jv_scale(u, v, a0, dt)
+    assert np.all(np.abs(J - o.jv_analytic(u, v, a0, dt)) <= 1e-12 * Sj + 1e-300)
+    o.pc_setup(u, a0, dt)
+    y = ctx.precond_apply(dev(v)).cpu().numpy()
+    yo = o.pc_apply(v)
+    assert np.abs(y - yo).max() <= 1e-11 * np.abs(yo).max()
+
+
+def test_autotune_keeps_parity(nrd):
+    h, z = CASES["amr2_16"]()
+    ctx, o = make(nrd, h, z, pc_precision=0, nmg=3)
+    u = _state(h)
+    shape, ms = ctx.autotune(dev(u), dev(u), 1.0, 2e-3)
+    assert tuple(shape) in SHAPES and ms > 0
+    F = ctx.residual(dev(u), dev(u), 1.0, 2e-3).cpu().numpy()
+    S = o.residual_scale(u, u.copy(), 1.0, 2e-3)
+    assert np.all(np.abs(F - o.residual(u, u.copy(), 1.0, 2e-3)) <= 1e-12 * S + 1e-300)
