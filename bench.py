@@ -47,7 +47,24 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile", action="store_true",
+                    help="short run for profilers: 1 warm-up + 2 production steps, fixed "
+                         "8x8x8 tiles, no plain/CPU/e2e legs")
     return ap.parse_args()
+
+
+def profile_run():
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd
+    h, z, u0 = workload()
+    ctx = make_ctx(nrd, h, z, torch, production=True)
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=8)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    r = run_steps(ctx, torch, u0, 2, 1, flush, timing=False)
+    print(json.dumps({"profile_run": True, "ms": r["ms"], "krylov": r["krylov"]}))
+    return 0
 
 
 def workload():
@@ -272,6 +289,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile:
+        return profile_run()
     import torch
     import __graft_entry__ as g
     g.build()
