@@ -25,7 +25,8 @@ EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
-    "nrd_step", "nrd_tag", "nrd_autotune", "nrd_timing_enable", "nrd_timing_read",
+    "nrd_step", "nrd_tag", "nrd_autotune", "nrd_wdot_noalloc", "nrd_timing_enable",
+    "nrd_timing_read",
 ]
 TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST = range(7)
 TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost"]
@@ -95,6 +96,7 @@ def load(path: str = _LIBPATH):
         "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
         "nrd_autotune": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
+        "nrd_wdot_noalloc": (c_int, [dp, dp, fp, ctypes.c_int64, dp, vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
         "nrd_timing_read": (c_int, [vp, c_int, P(c_dbl), P(ctypes.c_int64)]),
     }
@@ -127,6 +129,20 @@ def _ptr(t, dtype):
 
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def wdot_noalloc(x, y, w, out=None):
+    """Allocation-free weighted dot (nrd_wdot_noalloc): out[0] =
+    sum_i w_i (x_i y_i + x_{n+i} y_{n+i}); returns the 1-element device tensor."""
+    lib = load()
+    n = w.numel()
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=x.device)
+    rc = lib.nrd_wdot_noalloc(_ptr(x, torch.float64), _ptr(y, torch.float64), _ptr(w, torch.float32),
+                              n, _ptr(out, torch.float64), _stream())
+    if rc != OK:
+        raise NrdError(rc, "nrd_wdot_noalloc failed")
+    return out
 
 
 class Context:
