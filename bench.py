@@ -37,6 +37,17 @@ FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
 FP64_PEAK_TFLOPS = 1.20
 DT = 5e-4
 WORKLOAD = "amr2_base64_marshak_band"
+# Algorithmic work per leaf cell (derivation in the design notes): the
+# linearisation stencil does 3 face linearisations (86.8 FP64 flop-equivalents
+# each, counting an FMA as 2 flops and a reciprocal / square root at their
+# measured FMA-equivalent cost) plus 48.4 per cell.
+LIN_FLOPS_PER_CELL = 3 * 86.8 + 48.4
+# DRAM bytes per launch of that kernel from the committed ncu capture of the
+# same kernel version, or None when the kernel changed since.
+LIN_TRAFFIC_BYTES = None
+# frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
+# 16 B + Jv 16 B + mask 1 B
+JV_BYTES_PER_CELL = 169.0
 
 
 def parse():
@@ -333,28 +344,28 @@ def main():
         tot_ms = float(t.item())
     value = world * leaf * r["krylov"] / (tot_ms * 1e-3) / 1e6
 
-    # dominant kernel group and its roofline
+    # roofline of the dominant single kernel: the FP64 linearisation stencil
+    # (residual + Jacobian partials + frozen P1/P2 data), measured live with
+    # CUDA events around each of its launches in the timed region
     kt = r["kernel"]
     hbm_peak, peak_src = peaks()
+    lin_ms, lin_n = kt["residual"]
     jv_ms, jv_n = kt["jv"]
-    pc_ms, pc_n = kt["pc_apply"]
-    dom = max(kt.items(), key=lambda kv: kv[1][0])[0]
-    roof = None
-    if dom == "jv" and jv_n:
-        # FP64 work of the analytic-tangent stencil per leaf cell, in
-        # FMA-equivalent flops (derivation in the design notes)
-        flops_cell = 2.0 * 228.0
-        ach = flops_cell * leaf / (jv_ms / jv_n * 1e-3) / 1e12
-        roof = {"kernel": "k_stencil<JV> (analytic tangent)", "bound": "alu", "achieved": ach,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": None, "peak_source": "measured FP64 FMA microbenchmark"}
-    else:
-        # one FP32 V-cycle application, algorithmic bytes per leaf cell
-        bytes_cell = 400.0
-        ach = bytes_cell * leaf / (pc_ms / max(pc_n, 1) * 1e-3) / 1e9
-        roof = {"kernel": "P^-1 apply (FAC/GMG V-cycle, FP32)", "bound": "hbm", "achieved": ach,
-                "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak, "traffic": None,
-                "peak_source": peak_src}
+    t_lin = lin_ms / max(lin_n, 1) * 1e-3
+    ach = LIN_FLOPS_PER_CELL * leaf / t_lin / 1e12
+    roof = {"kernel": "k_stencil<ST_LIN> (residual + linearisation, FP64)", "bound": "alu",
+            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": LIN_TRAFFIC_BYTES,
+            "per_launch_us": t_lin * 1e6, "launches": lin_n,
+            "peak_source": "measured FP64 FMA microbenchmark on this GB300 (no FP64 figure in "
+                           "MEASURED_PEAKS.json)",
+            "algorithmic": "%.1f FP64 flop-equivalents per leaf cell x %d leaf cells"
+                           % (LIN_FLOPS_PER_CELL, leaf)}
+    t_jv = jv_ms / max(jv_n, 1) * 1e-3
+    ach_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
+    roof_jv = {"kernel": "k_jv_frozen (frozen-Jacobian Jv)", "bound": "hbm", "achieved": ach_jv,
+               "peak": hbm_peak, "unit": "GB/s", "frac": ach_jv / hbm_peak,
+               "per_launch_us": t_jv * 1e6, "peak_source": peak_src}
 
     # plain form beside it
     plain = None
@@ -392,6 +403,7 @@ def main():
                    "l2": "256 MB buffer written between timed steps",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
+        "roofline_jv": roof_jv,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "plain": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / (tot_ms / args.steps)) if plain else None,

@@ -108,12 +108,14 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.jc = c->d_jc;
   io.craw = pc_craw(c->pc);
   io.cc = c->d_cc;
+  io.beta = dt / a0;
+  pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2);
   c->timer.begin(NRD_TK_RESIDUAL, s);
   launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s);
   c->timer.end(NRD_TK_RESIDUAL, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
   c->timer.begin(NRD_TK_PC_SETUP, s);
-  int rc = pc_finish(c->pc, H, u, c->d_z, a0, dt, s);
+  int rc = pc_finish(c->pc, H, u, c->d_z, a0, dt, true, s);
   c->timer.end(NRD_TK_PC_SETUP, s);
   if (rc != NRD_OK) return fail(c, rc, "preconditioner set-up failed");
   c->lin_ready = true;

@@ -197,6 +197,8 @@ struct HierV {
   const PatchDev* patches;
   const uint8_t* mask;
   const uint8_t* gtype;
+  const int* gt0;      // sibling ghost -> its source cell is gidx[gt0[g]]
+  const int* gidx;
   const P* A;        // field f at A + f * Afs; slots [3N | G]
   long Afs;
   int N, G;
@@ -215,7 +217,8 @@ __device__ __forceinline__ void lev_row(const HierV<P>& V, const PatchDev& Pt, i
     int g = Pt.goff + Pt.fo[f] + a + Pt.n[((f >> 1) + 1) % 3] * b;
     uint8_t t = V.gtype[g];
     P av = A[3 * N + g];
-    if (t == GT_SIBLING) { d += av; o += av * gh[g]; }
+    // a sibling cell has the other colour: read it directly
+    if (t == GT_SIBLING) { d += av; o += av * e[V.gidx[V.gt0[g]]]; }
     else if (t == GT_CF) d += P(2.0 / 3.0) * av;
     else d += av;   // Robin diagonal term, or 0 for Neumann
   };
@@ -528,13 +531,34 @@ __global__ void k_coef(SetupArgs a) {
   }
 }
 
-// covered faces of level l: mean of the 4 coincident faces on level l+1
-__global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, double* Craw) {
+// covered faces of level l: mean of the 4 coincident faces on level l+1;
+// with A non-null also the scaled coefficient of the target (level l)
+template <class P>
+__global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, int N,
+                               const uint8_t* gtype, const uint8_t* gface, double beta,
+                               LevelHP lh, int lvl, double* Craw, P* A) {
   const int fld = blockIdx.y;
   double* C = Craw + fld * AF;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     int4 s = src[q];
-    C[tgt[q]] = 0.25 * (C[s.x] + C[s.y] + C[s.z] + C[s.w]);
+    int t = tgt[q];
+    double c = 0.25 * (C[s.x] + C[s.y] + C[s.z] + C[s.w]);
+    C[t] = c;
+    if (!A) continue;
+    double v;
+    if (t < 3L * N) {
+      double h = lh.h[lvl][t / N];
+      v = c * beta / (h * h);
+    } else {
+      int g = t - 3 * N;
+      int d = (gface[g] & 7) / 2;
+      double h = lh.h[lvl][d];
+      uint8_t ty = gtype[g];
+      if (ty == GT_NEUMANN) v = 0.0;
+      else if (ty == GT_ROBIN) v = (fld == 0) ? beta * 2.0 * c / (h * (4.0 * c + h)) : 0.0;
+      else v = c * beta / (h * h);
+    }
+    A[fld * AF + t] = (P)v;
   }
 }
 
@@ -788,6 +812,8 @@ HierV<P> hview(PcState* ps, const Hier& H) {
   V.patches = H.d_patches;
   V.mask = H.d_mask;
   V.gtype = H.d_gtype;
+  V.gt0 = H.d_gt0;
+  V.gidx = H.d_gidx;
   V.A = (const P*)ps->A;
   V.Afs = ps->AF;
   V.N = H.N;
@@ -842,13 +868,9 @@ void level_smooth(PcState* ps, const Hier& H, int l, int sweeps, bool red_first,
   const LevelInfo& Lv = H.lev[l];
   HierV<P> V = hview<P>(ps, H);
   dim3 gt(std::max(1, std::min(Lv.nt, 152 * 8)), 2);
-  dim3 gg(g1(std::max(Lv.ng, 1)), 2);
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
       int colour = red_first ? pass : 1 - pass;
-      if (Lv.ng)
-        k_sib_ghost<P><<<gg, BS, 0, s>>>(H.d_gtype, H.d_gt0, H.d_gidx, Lv.g0, Lv.ng, H.N, H.G,
-                                         (const P*)ps->fe, (P*)ps->gh);
       k_lev_rbgs<P><<<gt, BS, 0, s>>>(V, Lv.t0, Lv.nt, H.tile_x, H.tile_y, H.tile_z, (P*)ps->fe,
                                       (const P*)ps->fr, (const P*)ps->gh, colour);
     }
@@ -1036,19 +1058,38 @@ static SetupArgs setup_args(PcState* ps, const Hier& H, const ModelParams* mp, c
   return a;
 }
 
+void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2) {
+  *a32 = (ps->prec == NRD_PC_F32) ? (float*)ps->A : nullptr;
+  *a64 = (ps->prec == NRD_PC_F32) ? nullptr : (double*)ps->A;
+  *p2 = ps->p2;
+}
+
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
-              cudaStream_t s) {
+              bool from_lin, cudaStream_t s) {
   ps->beta = dt / a0;
   if (ps->z != z) pc_drop_graphs(ps);
   ps->z = z;
   cudaMemcpyAsync(ps->d_beta, &ps->beta, sizeof(double), cudaMemcpyHostToDevice, s);
   SetupArgs a = setup_args(ps, H, nullptr, u, nullptr, z, nullptr);
-  cudaMemcpyAsync(ps->Tk, u + H.N, (size_t)H.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-  k_p2_setup<<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, ps->Tk, z, ps->d_beta, ps->p2);
+  if (!from_lin) {
+    cudaMemcpyAsync(ps->Tk, u + H.N, (size_t)H.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    k_p2_setup<<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, ps->Tk, z, ps->d_beta, ps->p2);
+  }
   for (int l = H.L - 2; l >= 0; l--) {
     if (!H.ncz[l]) continue;
     dim3 g(g1(H.ncz[l]), 2);
-    k_coef_coarsen<<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, ps->Craw);
+    if (from_lin && ps->prec == NRD_PC_F32)
+      k_coef_coarsen<float><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
+                                             H.d_gtype, H.d_gface, ps->beta, a.lh, l, ps->Craw,
+                                             (float*)ps->A);
+    else if (from_lin)
+      k_coef_coarsen<double><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
+                                              H.d_gtype, H.d_gface, ps->beta, a.lh, l, ps->Craw,
+                                              (double*)ps->A);
+    else
+      k_coef_coarsen<float><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
+                                             H.d_gtype, H.d_gface, ps->beta, a.lh, l, ps->Craw,
+                                             (float*)nullptr);
   }
   // GMG levels
   for (int m = 1; m < ps->nmg; m++) {
@@ -1060,10 +1101,10 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
     k_box_coarsen<<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m]);
   }
   if (ps->prec == NRD_PC_F32) {
-    scale_all<float>(ps, H, a, s);
+    if (!from_lin) scale_all<float>(ps, H, a, s);
     scale_boxes<float>(ps, s);
   } else {
-    scale_all<double>(ps, H, a, s);
+    if (!from_lin) scale_all<double>(ps, H, a, s);
     scale_boxes<double>(ps, s);
   }
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
@@ -1075,7 +1116,7 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
   SetupArgs a = setup_args(ps, H, &mp, u, gu, z, gz);
   int nt = (int)H.tiles.size();
   k_coef<<<std::min(nt, 152 * 8), BS, 0, s>>>(a);
-  return pc_finish(ps, H, u, z, a0, dt, s);
+  return pc_finish(ps, H, u, z, a0, dt, false, s);
 }
 
 static int apply_any(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {

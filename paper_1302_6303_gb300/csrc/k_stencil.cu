@@ -19,6 +19,7 @@ struct LevelH {
   double rh[NRD_MAX_LEVELS][3];   // 1/h
   double h3[NRD_MAX_LEVELS][3];   // 3h
   double kh[NRD_MAX_LEVELS][3];   // k/h
+  double bh2[NRD_MAX_LEVELS][3];  // beta/h^2 (linearisation only)
 };
 
 struct GhostArgs {
@@ -200,6 +201,19 @@ __device__ __forceinline__ double robin_tan(double E, double T, double z, double
   return -(double)s * (dDb * m * h + Db * dm * q) / (q * q);
 }
 
+// scaled P1 coefficient a = beta C / h^2 (or the Robin diagonal term) in the
+// V-cycle precision
+__device__ __forceinline__ void put_scaled(const StencilIO& io, long NS, long slot, double aE,
+                                           double aT) {
+  if (io.a32) {
+    io.a32[slot] = (float)aE;
+    io.a32[NS + slot] = (float)aT;
+  } else {
+    io.a64[slot] = aE;
+    io.a64[NS + slot] = aT;
+  }
+}
+
 template <int MODE, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
@@ -347,6 +361,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           for (int q = 0; q < 5; q++) io.jc[q * NS + fslot] = 0.0;
           io.craw[fslot] = 0.0;
           io.craw[NS + fslot] = 0.0;
+          put_scaled(io, NS, fslot, 0.0, 0.0);
         }
       } else if (gt == GT_ROBIN) {
         int s = (pos == 0) ? -1 : 1;
@@ -371,6 +386,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[4 * NS + fslot] = 0.0;
           io.craw[fslot] = Db;
           io.craw[NS + fslot] = 0.0;
+          put_scaled(io, NS, fslot, io.beta * 2.0 * Db * rq / h, 0.0);
         }
         PT = 0.0;
       } else {
@@ -388,6 +404,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[4 * NS + fslot] = L.bTb;
           io.craw[fslot] = L.CE;
           io.craw[NS + fslot] = L.CT;
+          const double b2 = A.lh.bh2[lvl][dir];
+          put_scaled(io, NS, fslot, L.CE * b2, L.CT * b2);
         } else {
           flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, PE, PT);
         }
@@ -414,6 +432,9 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         if (LIN) {
           io.cc[idx] = 0.0;
           io.cc[N + idx] = 0.0;
+          io.p2[idx] = 0.0;
+          io.p2[N + idx] = 0.0;
+          io.p2[2L * N + idx] = 0.0;
         }
         continue;
       }
@@ -447,6 +468,11 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         // coupling tangent dc = cE vE + cT vT
         io.cc[idx] = -sig;
         io.cc[N + idx] = sig * (T3 + 3.0 * E * rT);
+        // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
+        double sb = sig * io.beta, sbt = sb * T3;
+        io.p2[idx] = sb;
+        io.p2[N + idx] = sbt;
+        io.p2[2L * N + idx] = 1.0 / ((1.0 + sb) * (1.0 + sbt) - sbt * sb);
       } else {
         double sig = z / T3;
         double cp = sig * (T2 * T2 - E);
@@ -667,7 +693,7 @@ int blocks_for(long n, int bs) {
   return (int)b;
 }
 
-LevelH level_h(const Hier& H, double k = 0.01) {
+LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
   LevelH lh;
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
     for (int d = 0; d < 3; d++) {
@@ -676,6 +702,7 @@ LevelH level_h(const Hier& H, double k = 0.01) {
       lh.rh[l][d] = 1.0 / h;
       lh.h3[l][d] = 3.0 * h;
       lh.kh[l][d] = k / h;
+      lh.bh2[l][d] = beta / (h * h);
     }
   return lh;
 }
@@ -697,10 +724,8 @@ void run_stencil(const StArgs& a, cudaStream_t s) {
                          (int)sm);
     init = true;
   }
-  int per_sm = (int)(200 * 1024 / sm);
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 4) per_sm = 4;
-  int grid = std::min(a.ntiles, 152 * per_sm);
+  // one tile per CTA: the block scheduler balances tiles of uneven cost
+  int grid = a.ntiles;
   if (grid < 1) return;
   k_stencil<MODE, TX, TY, TZ><<<grid, 256, sm, s>>>(a);
 }
@@ -758,7 +783,7 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   a.k = mp.k;
   a.cL = (mp.limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
   for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
-  a.lh = level_h(H, mp.k);
+  a.lh = level_h(H, mp.k, io.beta);
   a.io = io;
   if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);

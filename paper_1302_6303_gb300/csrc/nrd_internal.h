@@ -128,6 +128,10 @@ struct StencilIO {
   double* jc;           // [5][3N+G] flux partial derivatives
   double* craw;         // [2][3N+G] frozen D_E, D_T (Robin slots: D_b)
   double* cc;           // [2][N] coupling tangent coefficients
+  double beta;          // dt / a0
+  float* a32;           // [2][3N+G] scaled P1 coefficients (FP32 V-cycle), or
+  double* a64;          //   the FP64 array when a32 is null
+  double* p2;           // [3][N] P2 data
 };
 void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
                        double* g, int nonlinear, cudaStream_t s);
@@ -183,9 +187,12 @@ int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_
 double* pc_craw(PcState* ps);
 void pc_drop_graphs(PcState* ps);
 void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw);
-// coarsen + scale after the raw coefficients were written at u
+// coarsen (and, unless the linearisation already did, scale) after the raw
+// coefficients were written at u
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
-              cudaStream_t s);
+              bool from_lin, cudaStream_t s);
+// where the linearisation writes scaled coefficients and P2 data
+void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2);
 
 #define CUDA_TRY(x)                                         \
   do {                                                      \
