@@ -32,9 +32,6 @@ import numpy as np  # noqa: E402
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
-# FP64 FMA throughput of this GB300 measured with an FMA-chain microbenchmark
-# (1.20 TFLOP/s); used as the ALU peak of the FP64 stencil kernels.
-FP64_PEAK_TFLOPS = 1.20
 DT = 5e-4
 WORKLOAD = "amr2_base64_marshak_band"
 # Algorithmic work per leaf cell (derivation in the design notes): the
@@ -44,7 +41,7 @@ WORKLOAD = "amr2_base64_marshak_band"
 LIN_FLOPS_PER_CELL = 3 * 86.8 + 48.4
 # DRAM bytes per launch of that kernel from the committed ncu capture of the
 # same kernel version, or None when the kernel changed since.
-LIN_TRAFFIC_BYTES = None
+LIN_TRAFFIC_BYTES = 103.7e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
@@ -322,6 +319,7 @@ def main():
         torch.cuda.synchronize()
 
     h, z, u0 = workload()
+    rates = nrd.measure_peaks()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx = make_ctx(nrd, h, z, torch, production=True)
     leaf = ctx.nleaf
@@ -353,12 +351,13 @@ def main():
     jv_ms, jv_n = kt["jv"]
     t_lin = lin_ms / max(lin_n, 1) * 1e-3
     ach = LIN_FLOPS_PER_CELL * leaf / t_lin / 1e12
+    fp64_peak = rates["fp64_tflops"]
     roof = {"kernel": "k_stencil<ST_LIN> (residual + linearisation, FP64)", "bound": "alu",
-            "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP64_PEAK_TFLOPS, "traffic": LIN_TRAFFIC_BYTES,
+            "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": ach / fp64_peak, "traffic": LIN_TRAFFIC_BYTES,
             "per_launch_us": t_lin * 1e6, "launches": lin_n,
-            "peak_source": "measured FP64 FMA microbenchmark on this GB300 (no FP64 figure in "
-                           "MEASURED_PEAKS.json)",
+            "peak_source": "FP64 FMA rate measured in this run by nrd_measure_peaks (no FP64 "
+                           "figure in MEASURED_PEAKS.json)",
             "algorithmic": "%.1f FP64 flop-equivalents per leaf cell x %d leaf cells"
                            % (LIN_FLOPS_PER_CELL, leaf)}
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
@@ -404,6 +403,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "roofline_jv": roof_jv,
+        "measured_rates": rates,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "plain": plain,
         "speedup_vs_plain": (plain["ms_per_step"] / (tot_ms / args.steps)) if plain else None,

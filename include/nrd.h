@@ -273,6 +273,14 @@ int nrd_autotune(nrd_ctx* ctx, const double* u, const double* b, double a0, doub
 int nrd_wdot_noalloc(const double* x, const double* y, const float* w, int64_t n, double* out,
                      cudaStream_t stream);
 
+/* Machine rates used as roofline denominators, measured on the current
+ * device: FP64 and FP32 FMA throughput in TFLOP/s (an FMA counts 2 flops;
+ * independent FMA chains on every SM) and device-to-device copy bandwidth in
+ * GB/s (read + write bytes of a 1 GiB copy), each the best of 3 runs timed with
+ * CUDA events.  Allocates and frees 2 GiB of scratch.  Synchronises. */
+int nrd_measure_peaks(double* fp64_tflops_host, double* fp32_tflops_host, double* copy_gbs_host,
+                      cudaStream_t stream);
+
 /* ------------------------------------------------------- kernel timing
  * Optional CUDA-event timing of the library's kernel groups, recorded on the
  * stream each group is launched on (a start/stop event pair around every

@@ -25,7 +25,8 @@ EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
-    "nrd_step", "nrd_tag", "nrd_autotune", "nrd_wdot_noalloc", "nrd_timing_enable",
+    "nrd_step", "nrd_tag", "nrd_autotune", "nrd_wdot_noalloc", "nrd_measure_peaks",
+    "nrd_timing_enable",
     "nrd_timing_read",
 ]
 TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST = range(7)
@@ -97,6 +98,7 @@ def load(path: str = _LIBPATH):
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
         "nrd_autotune": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
         "nrd_wdot_noalloc": (c_int, [dp, dp, fp, ctypes.c_int64, dp, vp]),
+        "nrd_measure_peaks": (c_int, [P(c_dbl), P(c_dbl), P(c_dbl), vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
         "nrd_timing_read": (c_int, [vp, c_int, P(c_dbl), P(ctypes.c_int64)]),
     }
@@ -129,6 +131,16 @@ def _ptr(t, dtype):
 
 def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def measure_peaks():
+    """FP64 / FP32 FMA TFLOP/s and copy GB/s of the current device."""
+    lib = load()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    rc = lib.nrd_measure_peaks(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), _stream())
+    if rc != OK:
+        raise NrdError(rc, "nrd_measure_peaks failed")
+    return {"fp64_tflops": a.value, "fp32_tflops": b.value, "copy_gbs": c.value}
 
 
 def wdot_noalloc(x, y, w, out=None):

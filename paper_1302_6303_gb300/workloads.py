@@ -274,3 +274,67 @@ def boundary_amr(n0=8):
     sibling pair sharing a face."""
     lv1 = [((0, 0, 0), (5, 7, 7)), ((6, 0, 0), (9, 7, 7)), ((0, 8, 0), (3, 11, 5))]
     return Hierarchy((n0, n0, n0), [[((0, 0, 0), (n0 - 1,) * 3)], lv1])
+
+
+def random_nested_level(rng, parent_boxes, n_fine, count, side_lo, side_hi, tries=200000,
+                        margin=1):
+    """Seeded rejection sampling of `count` non-overlapping fine boxes (sides
+    U{side_lo..side_hi}, even, aligned to ratio 2) properly nested in the
+    parent level (its boxes in parent index space): every fine box coarsened
+    and grown by `margin` coarse cells must lie inside one parent box."""
+    occ = np.zeros(n_fine, dtype=bool)
+    boxes = []
+    pb = [(np.array(lo), np.array(hi)) for lo, hi in parent_boxes]
+    t = 0
+    while len(boxes) < count and t < tries:
+        t += 1
+        p = pb[int(rng.integers(0, len(pb)))]
+        side = [2 * int(rng.integers((side_lo + 1) // 2, side_hi // 2 + 1)) for _ in range(3)]
+        # coarse extent of the fine box must fit inside the parent box with margin
+        clo = p[0] + margin
+        chi = p[1] - margin
+        span = [int(chi[d] - clo[d] + 1) for d in range(3)]
+        csd = [s // 2 for s in side]
+        if any(csd[d] > span[d] for d in range(3)):
+            continue
+        c0 = [int(clo[d] + rng.integers(0, span[d] - csd[d] + 1)) for d in range(3)]
+        lo = tuple(2 * c0[d] for d in range(3))
+        hi = tuple(lo[d] + side[d] - 1 for d in range(3))
+        sl = tuple(slice(lo[d], hi[d] + 1) for d in range(3))
+        if occ[sl].any():
+            continue
+        occ[sl] = True
+        boxes.append((lo, hi))
+    return boxes
+
+
+def config_batching(n0=128, seed=0, n1=500, n2=1500, side_lo=8, side_hi=48):
+    """Three levels, base n0^3, ratio 2: about n1 patches on level 1 and n2 on
+    level 2 with sides U{8..48} per axis, non-overlapping per level and
+    properly nested; z = 10 in 64 seeded cubes on z = 1."""
+    rng = np.random.default_rng(seed)
+    base = [((0, 0, 0), (n0 - 1,) * 3)]
+    l1 = random_nested_level(rng, base, (2 * n0,) * 3, n1, side_lo, side_hi)
+    # level-2 boxes nest inside single level-1 boxes (in level-1 index space)
+    l2 = random_nested_level(rng, l1, (4 * n0,) * 3, n2, side_lo, side_hi)
+    h = Hierarchy((n0, n0, n0), [base, l1, l2])
+    s_lo, s_hi = max(1, 4 * n0 // 64), max(1, 12 * n0 // 64)
+    cubes = random_cubes(rng, h.n0, 64, s_lo, s_hi)
+    return h, material_from_cubes(h, cubes)
+
+
+def config_adjoint(n0=96, seed=0, nbox=8):
+    """Two levels, base n0^3: `nbox` fine boxes of 16^3-32^3 fine cells near
+    x = 0 (seeded), z = 10 in 20 seeded cubes; the functional box is an
+    interior 16^3 (base-cell) box."""
+    rng = np.random.default_rng(seed)
+    base = [((0, 0, 0), (n0 - 1,) * 3)]
+    region = [((0, 0, 0), (max(3, n0 // 6), n0 - 1, n0 - 1))]
+    s_lo, s_hi = (16, 32) if n0 >= 64 else (4, 8)
+    l1 = random_nested_level(rng, region, (2 * n0,) * 3, nbox, s_lo, s_hi, margin=0)
+    h = Hierarchy((n0, n0, n0), [base, l1])
+    s_lo, s_hi = max(1, 4 * n0 // 64), max(1, 12 * n0 // 64)
+    cubes = random_cubes(rng, h.n0, 20, s_lo, s_hi)
+    c = n0 // 2 - n0 // 12
+    fbox = ((c,) * 3, (c + max(1, n0 // 6) - 1,) * 3)
+    return h, material_from_cubes(h, cubes), fbox
