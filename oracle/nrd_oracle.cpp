@@ -186,6 +186,7 @@ struct Hier {
 }
 
 inline double cube(double a) { return a * a * a; }
+inline Dual cube(Dual a) { return a * a * a; }
 
 // Composite value of a field at an existing level-l cell: its own value when
 // it is a leaf, the mean of its 8 children when covered by level l+1.
@@ -233,13 +234,17 @@ S cf_ghost(const Hier& H, const S* x, int l, const int c[3], int d, int s) {
   return (x[ic] + 2.0 * iv) / 3.0;
 }
 
-double cf_ghost_z(const Hier& H, int l, const int c[3], int d, int s) {
+template <class Z>
+Z cf_ghost_z(const Hier& H, const Z* z, int l, const int c[3], int d, int s) {
   int g[3] = {c[0], c[1], c[2]};
   g[d] += s;
   int P[3] = {g[0] / 2, g[1] / 2, g[2] / 2};
   long ip = H.cell(l - 1, P);
   if (ip < 0) fatal("cf_ghost_z: parent missing");
-  return H.z[ip];  // R15
+  return z[ip];  // R15
+}
+double cf_ghost_z(const Hier& H, int l, const int c[3], int d, int s) {
+  return cf_ghost_z<double>(H, H.z.data(), l, c, d, s);
 }
 
 // Face fluxes D (b - a)/h between cell a (low side) and b (high side).
@@ -249,7 +254,7 @@ template <class S>
 struct FluxPair { S E, T; };
 
 template <class S>
-FluxPair<S> pair_flux(const Hier& H, S Ea, S Eb, S Ta, S Tb, double za, double zb, double h) {
+FluxPair<S> pair_flux(const Hier& H, S Ea, S Eb, S Ta, S Tb, S za, S zb, double h) {
   S Tf = 0.5 * (Ta + Tb);
   S Dr = Tf * Tf * Tf / (3.0 * (cube(za) + cube(zb)));
   S g = fabs(Eb - Ea) / (0.5 * h * (Ea + Eb));
@@ -269,8 +274,8 @@ FluxPair<S> pair_flux(const Hier& H, S Ea, S Eb, S Ta, S Tb, double za, double z
 
 // Robin ghost of Sec. 3.1 Eq. robinbc discretised at the face (R4):
 // (1/2) D_b (E_g - E_0)/h + (E_g + E_0)/8 = R.
-template <class S>
-S robin_ghost(S E0, S T0, double z0, double h, double R) {
+template <class S, class Z>
+S robin_ghost(S E0, S T0, Z z0, double h, double R) {
   S Db = T0 * T0 * T0 / (3.0 * cube(z0));
   S a = Db / (2.0 * h);
   return (R + E0 * (a - 0.125)) / (a + 0.125);
@@ -279,7 +284,8 @@ S robin_ghost(S E0, S T0, double z0, double h, double R) {
 // Flux (in the +e_d direction) through face (c, d, s) of the leaf cell c at
 // level l, for the nonlinear residual.
 template <class S>
-FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, int l, const int c[3], int d, int s) {
+FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, const S* z, int l, const int c[3], int d,
+                      int s) {
   const Level& Lv = H.lev[l];
   double h = Lv.h[d];
   long ic = H.cell(l, c);
@@ -290,8 +296,8 @@ FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, int l, const int c[
     int face = 2 * d + (s > 0 ? 1 : 0);
     f.T = S(0.0);
     if (H.bc_type[face] == BC_ROBIN) {
-      S Eg = robin_ghost(E[ic], T[ic], H.z[ic], h, H.bc_R[face]);
-      S Db = T[ic] * T[ic] * T[ic] / (3.0 * cube(H.z[ic]));
+      S Eg = robin_ghost(E[ic], T[ic], z[ic], h, H.bc_R[face]);
+      S Db = T[ic] * T[ic] * T[ic] / (3.0 * cube(z[ic]));
       f.E = (s > 0) ? Db * (Eg - E[ic]) / h : Db * (E[ic] - Eg) / h;
     } else {
       f.E = S(0.0);
@@ -299,8 +305,7 @@ FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, int l, const int c[
     return f;
   }
   long ig = H.cell(l, g);
-  S Eg, Tg;
-  double zg;
+  S Eg, Tg, zg;
   if (ig >= 0) {
     if (H.covered(l, g)) {
       // Flux matching (Sec. 3.2.1, Fig. flux): the coarse face flux is the
@@ -315,7 +320,7 @@ FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, int l, const int c[
           q[d] = (s > 0) ? 2 * g[d] : 2 * g[d] + 1;
           q[t1] = 2 * c[t1] + a;
           q[t2] = 2 * c[t2] + b;
-          FluxPair<S> ff = face_flux(H, E, T, l + 1, q, d, -s);
+          FluxPair<S> ff = face_flux(H, E, T, z, l + 1, q, d, -s);
           sum.E += ff.E;
           sum.T += ff.T;
         }
@@ -325,14 +330,14 @@ FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, int l, const int c[
     }
     Eg = E[ig];
     Tg = T[ig];
-    zg = H.z[ig];
+    zg = z[ig];
   } else {
     Eg = cf_ghost(H, E, l, c, d, s);
     Tg = cf_ghost(H, T, l, c, d, s);
-    zg = cf_ghost_z(H, l, c, d, s);
+    zg = cf_ghost_z<S>(H, z, l, c, d, s);
   }
-  if (s > 0) return pair_flux(H, E[ic], Eg, T[ic], Tg, H.z[ic], zg, h);
-  return pair_flux(H, Eg, E[ic], Tg, T[ic], zg, H.z[ic], h);
+  if (s > 0) return pair_flux(H, E[ic], Eg, T[ic], Tg, z[ic], zg, h);
+  return pair_flux(H, Eg, E[ic], Tg, T[ic], zg, z[ic], h);
 }
 
 // F(u) = a0 u - b - dt f(u)  (Eq. nonlinearsystem per unit volume, R5), with
@@ -341,7 +346,8 @@ FluxPair<S> face_flux(const Hier& H, const S* E, const S* T, int l, const int c[
 // mag != nullptr receives, per cell and field, the sum of absolute values of
 // the terms (a scale for rounding-level comparisons).
 template <class S>
-void residual_t(const Hier& H, const S* u, const double* b, double a0, double dt, S* F, S* mag) {
+void residual_t(const Hier& H, const S* u, const S* z, const double* b, double a0, double dt, S* F,
+                S* mag) {
   const long N = H.N;
   const S* E = u;
   const S* T = u + N;
@@ -359,13 +365,13 @@ void residual_t(const Hier& H, const S* u, const double* b, double a0, double dt
     for (int d = 0; d < 3; d++) {
       double h = H.lev[l].h[d];
       for (int s = -1; s <= 1; s += 2) {
-        FluxPair<S> f = face_flux(H, E, T, l, c, d, s);
+        FluxPair<S> f = face_flux(H, E, T, z, l, c, d, s);
         divE += double(s) * f.E / h;
         divT += double(s) * f.T / h;
         if (mag) { absE += fabs(f.E) / h; absT += fabs(f.T) / h; }
       }
     }
-    double zc = cube(H.z[idx]);
+    S zc = cube(z[idx]);
     S Tc = T[idx];
     S sigma = zc / (Tc * Tc * Tc);
     S T4 = Tc * Tc * Tc * Tc;
@@ -429,7 +435,13 @@ double fd_eps(const Hier& H, const double* u, const double* v) {
 }
 
 void residual(const Hier& H, const double* u, const double* b, double a0, double dt, double* F) {
-  residual_t<double>(H, u, b, a0, dt, F, nullptr);
+  residual_t<double>(H, u, H.z.data(), b, a0, dt, F, nullptr);
+}
+
+std::vector<Dual> zconst(const Hier& H) {
+  std::vector<Dual> z(H.N);
+  for (long i = 0; i < H.N; i++) z[i] = Dual(H.z[i], 0.0);
+  return z;
 }
 
 void jv_analytic(const Hier& H, const double* u, const double* v, double a0, double dt, double* Jv) {
@@ -437,8 +449,42 @@ void jv_analytic(const Hier& H, const double* u, const double* v, double a0, dou
   std::vector<Dual> ud(n2), Fd(n2);
   std::vector<double> b0(n2, 0.0);
   for (long i = 0; i < n2; i++) ud[i] = Dual(u[i], v[i]);
-  residual_t<Dual>(H, ud.data(), b0.data(), a0, dt, Fd.data(), nullptr);
+  std::vector<Dual> zd = zconst(H);
+  residual_t<Dual>(H, ud.data(), zd.data(), b0.data(), a0, dt, Fd.data(), nullptr);
   for (long i = 0; i < n2; i++) Jv[i] = Fd[i].d;
+}
+
+// (dF/du)^T w and (dF/dz)^T w by their definition: one Jacobian column per
+// unknown (forward-mode tangent along a unit vector), each dotted with w.
+// O(N^2): for small hierarchies only.
+void vjp_bruteforce(const Hier& H, const double* u, const double* w, double a0, double dt,
+                    double* JTw, double* dz, double* JTw_abs) {
+  const long N = H.N, n2 = 2 * N;
+  std::vector<Dual> ud(n2), Fd(n2);
+  std::vector<double> b0(n2, 0.0);
+  std::vector<Dual> zd = zconst(H);
+  for (long i = 0; i < n2; i++) ud[i] = Dual(u[i], 0.0);
+  for (long j = 0; j < n2; j++) {
+    ud[j].d = 1.0;
+    residual_t<Dual>(H, ud.data(), zd.data(), b0.data(), a0, dt, Fd.data(), nullptr);
+    ud[j].d = 0.0;
+    double s = 0.0, sa = 0.0;
+    for (long i = 0; i < n2; i++) {
+      s += w[i] * Fd[i].d;
+      sa += std::fabs(w[i] * Fd[i].d);
+    }
+    JTw[j] = s;
+    if (JTw_abs) JTw_abs[j] = sa;
+  }
+  if (!dz) return;
+  for (long k = 0; k < N; k++) {
+    zd[k].d = 1.0;
+    residual_t<Dual>(H, ud.data(), zd.data(), b0.data(), a0, dt, Fd.data(), nullptr);
+    zd[k].d = 0.0;
+    double s = 0.0;
+    for (long i = 0; i < n2; i++) s += w[i] * Fd[i].d;
+    dz[k] = s;
+  }
 }
 
 void jv_fd(const Hier& H, const double* u, const double* v, const double* b, double a0, double dt,
@@ -1234,7 +1280,7 @@ void orc_residual_scale(orc_hier* h, const double* u, const double* b, double a0
                         double* S) {
   Hier* H = reinterpret_cast<Hier*>(h);
   std::vector<double> F(2 * H->N);
-  residual_t<double>(*H, u, b, a0, dt, F.data(), S);
+  residual_t<double>(*H, u, H->z.data(), b, a0, dt, F.data(), S);
 }
 
 void orc_jv_analytic(orc_hier* h, const double* u, const double* v, double a0, double dt,
@@ -1249,6 +1295,7 @@ void orc_jv_scale(orc_hier* h, const double* u, const double* v, double a0, doub
   const long N = H->N, n2 = 2 * N;
   std::vector<Dual> ud(n2);
   for (long i = 0; i < n2; i++) ud[i] = Dual(u[i], v[i]);
+  std::vector<Dual> zd = zconst(*H);
   const Dual* E = ud.data();
   const Dual* T = ud.data() + N;
   for (long idx = 0; idx < N; idx++) {
@@ -1258,7 +1305,7 @@ void orc_jv_scale(orc_hier* h, const double* u, const double* v, double a0, doub
     double aE = 0.0, aT = 0.0;
     for (int d = 0; d < 3; d++)
       for (int s = -1; s <= 1; s += 2) {
-        FluxPair<Dual> f = face_flux(*H, E, T, l, c, d, s);
+        FluxPair<Dual> f = face_flux(*H, E, T, zd.data(), l, c, d, s);
         aE += std::fabs(f.E.d) / H->lev[l].h[d];
         aT += std::fabs(f.T.d) / H->lev[l].h[d];
       }
@@ -1271,6 +1318,17 @@ void orc_jv_scale(orc_hier* h, const double* u, const double* v, double a0, doub
     S[idx] = a0 * std::fabs(v[idx]) + dt * (aE + cpl);
     S[N + idx] = a0 * std::fabs(v[N + idx]) + dt * (aT + cpl);
   }
+}
+
+void orc_vjp(orc_hier* h, const double* u, const double* w, double a0, double dt, double* JTw,
+             double* dz, double* JTw_abs) {
+  vjp_bruteforce(*reinterpret_cast<Hier*>(h), u, w, a0, dt, JTw, dz, JTw_abs);
+}
+
+// material in double precision (for finite-difference pins in z)
+void orc_set_material_f64(orc_hier* h, const double* z) {
+  Hier* H = reinterpret_cast<Hier*>(h);
+  for (long i = 0; i < H->N; i++) H->z[i] = z[i];
 }
 
 double orc_fd_eps(orc_hier* h, const double* u, const double* v) {

@@ -61,6 +61,8 @@ def _load():
         "orc_jv_analytic": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
         "orc_jv_scale": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
         "orc_fd_eps": (ctypes.c_double, [vp, _dp, _dp]),
+        "orc_vjp": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
+        "orc_set_material_f64": (None, [vp, _dp]),
         "orc_jv_fd": (ctypes.c_double, [vp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                         _dp, _dp]),
         "orc_dot": (ctypes.c_double, [vp, _dp, _dp]),
@@ -151,6 +153,18 @@ class Oracle:
         S = np.empty(2 * self.N)
         _lib.orc_jv_scale(self._h, _d(u), _d(v), a0, dt, _d(S))
         return S
+
+    def set_material_f64(self, z):
+        z = np.ascontiguousarray(z, dtype=np.float64)
+        _lib.orc_set_material_f64(self._h, _d(z))
+
+    def vjp(self, u, w, a0, dt, with_dz=True):
+        """(dF/du)^T w, (dF/dz)^T w and sum_i |w_i J_ij| (brute force, small N)."""
+        JTw = np.empty(2 * self.N)
+        Jab = np.empty(2 * self.N)
+        dz = np.empty(self.N) if with_dz else None
+        _lib.orc_vjp(self._h, _d(u), _d(np.ascontiguousarray(w)), a0, dt, _d(JTw), _d(dz), _d(Jab))
+        return JTw, dz, Jab
 
     def fd_eps(self, u, v):
         return _lib.orc_fd_eps(self._h, _d(u), _d(v))

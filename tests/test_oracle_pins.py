@@ -576,3 +576,49 @@ def test_tag_linear_field():
     assert np.all(t[inner] & 4)
     tr = o.tag(u, thr_r=float(rel[inner].max()) * (1 + 1e-9))
     assert np.all((tr[inner] & 4) == 0)
+
+
+# ------------------------------------------------------------------ adjoint
+def _tiny2():
+    h = W.Hierarchy((4, 4, 4), [[((0, 0, 0), (3, 3, 3))], [((2, 2, 2), (5, 5, 5))]])
+    return h
+
+
+@pytest.mark.parametrize("name", ["single", "tiny2"])
+def test_vjp_matches_central_differences(name):
+    """(dF/du)^T w and (dF/dz)^T w equal central differences of the scalar
+    phi = <w, F(u; z)> (plain sum) in every u_j and z_k."""
+    h = W.uniform((3, 3, 2)) if name == "single" else _tiny2()
+    z = W.material_from_cubes(h, [((1, 1, 0), 2, 10.0)]).astype(np.float64)
+    o = Oracle(h)
+    o.set_material_f64(z)
+    N = h.ncells
+    u = W.front_state(h, seed=3, noise=0.2)
+    b = u * 0.9
+    a0, dt = 1.1, 0.02
+    w = np.random.default_rng(1).standard_normal(2 * N)
+    JTw, dz, _ = o.vjp(u, w, a0, dt)
+    phi = lambda uu: float(np.dot(w, o.residual(uu, b, a0, dt)))
+    fd = np.empty(2 * N)
+    for j in range(2 * N):
+        hj = 1e-6 * abs(u[j])
+        up, um = u.copy(), u.copy()
+        up[j] += hj
+        um[j] -= hj
+        fd[j] = (phi(up) - phi(um)) / (2 * hj)
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    np.testing.assert_allclose(JTw[leaf], fd[leaf], rtol=0, atol=1e-6 * np.abs(fd).max())
+    assert np.all(JTw[~leaf] == 0.0)
+    fz = np.empty(N)
+    for k in range(N):
+        hk = 1e-6 * z[k]
+        zp, zm = z.copy(), z.copy()
+        zp[k] += hk
+        zm[k] -= hk
+        o.set_material_f64(zp)
+        fp = phi(u)
+        o.set_material_f64(zm)
+        fm = phi(u)
+        fz[k] = (fp - fm) / (2 * hk)
+    o.set_material_f64(z)
+    np.testing.assert_allclose(dz, fz, rtol=0, atol=1e-6 * np.abs(fz).max())
