@@ -200,6 +200,24 @@ int nrd_jv(nrd_ctx* ctx, const double* u, const double* v, const double* b, cons
 int nrd_linearise(nrd_ctx* ctx, const double* u, const double* b, double a0, double dt, double* F,
                   cudaStream_t stream);
 
+/* Adjoint of the residual at the state of the last nrd_linearise (the
+ * transpose of the exact Jacobian of Sec. 4.1; not in the paper, used to
+ * differentiate through implicit steps):
+ *   JTw = (dF/du)^T w   (2*ncells doubles; 0 on covered cells)
+ *   dz  = (dF/dz)^T w   (ncells doubles, may be NULL): sensitivity to the
+ *                       material z of each cell (0 on covered cells).
+ * Gather form (no atomics), deterministic.  a0, dt as in the linearisation. */
+int nrd_vjp(nrd_ctx* ctx, const double* w, double a0, double dt, double* JTw, double* dz,
+            cudaStream_t stream);
+
+/* Adjoint solve at the last nrd_linearise: J^T lam = g to
+ * ||g - J^T lam|| <= rtol ||g|| (volume-weighted norms), by restarted GMRES
+ * with the preconditioner of nrd_precond_apply on the right.  g, lam:
+ * 2*ncells doubles.  Returns NRD_ENONCONV if the tolerance is not reached
+ * within max_krylov iterations (lam holds the last iterate). */
+int nrd_adjoint_solve(nrd_ctx* ctx, const double* g, double a0, double dt, double rtol,
+                      double* lam, nrd_stats* stats, cudaStream_t stream);
+
 /* The differencing parameter eps(u, v) of Sec. 4.1 (synchronises; result in
  * *eps_host). */
 int nrd_fd_eps(nrd_ctx* ctx, const double* u, const double* v, double* eps_host,

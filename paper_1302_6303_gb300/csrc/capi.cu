@@ -62,8 +62,9 @@ void set_model(nrd_ctx* c) {
 void free_fields(nrd_ctx* c) {
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(c->d_z); F(c->d_gz); F(c->d_gu); F(c->d_gv); F(c->d_cf); F(c->d_tmp); F(c->d_jc); F(c->d_cc);
+  F(c->d_lam); F(c->d_gam);
   c->d_z = nullptr; c->d_gz = nullptr; c->d_gu = nullptr; c->d_gv = nullptr; c->d_cf = nullptr;
-  c->d_tmp = nullptr; c->d_jc = nullptr; c->d_cc = nullptr;
+  c->d_tmp = nullptr; c->d_jc = nullptr; c->d_cc = nullptr; c->d_lam = nullptr; c->d_gam = nullptr;
   c->lin_ready = false;
   reducer_free(c->R);
   if (c->pc) pc_free(c->pc);
@@ -285,8 +286,10 @@ int nrd_set_hierarchy(nrd_ctx* c, int nlevels, const int* nboxes, const int* box
             cudaMalloc(&c->d_gv, 2 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_cf, 2 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_tmp, 2 * N * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_jc, 5 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&c->d_cc, 2 * N * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_jc, 6 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_cc, 3 * N * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_lam, 2 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_gam, 3 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
             reducer_init(c->R, (int)N) == NRD_OK;
   if (!ok) {
     free_fields(c);
@@ -380,6 +383,28 @@ int nrd_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   if (!u || !b || !F) return fail(c, NRD_EINVAL, "null argument");
   if (!(a0 > 0.0) || !(dt > 0.0)) return fail(c, NRD_EINVAL, "a0 and dt must be positive");
   return ctx_linearise(c, u, b, a0, dt, F, s);
+}
+
+int nrd_vjp(nrd_ctx* c, const double* w, double a0, double dt, double* JTw, double* dz,
+            cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!w || !JTw) return fail(c, NRD_EINVAL, "null argument");
+  if (!c->lin_ready) return fail(c, NRD_ESTATE, "nrd_vjp needs nrd_linearise first");
+  launch_vjp(c->H, c->d_jc, c->d_cc, c->d_z, w, c->d_lam, c->d_gam, a0, dt, JTw, dz, s);
+  return check_launch(c);
+}
+
+int nrd_adjoint_solve(nrd_ctx* c, const double* g, double a0, double dt, double rtol,
+                      double* lam, nrd_stats* st, cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!g || !lam) return fail(c, NRD_EINVAL, "null argument");
+  if (!c->lin_ready) return fail(c, NRD_ESTATE, "nrd_adjoint_solve needs nrd_linearise first");
+  if (!(rtol > 0.0)) return fail(c, NRD_EINVAL, "rtol must be positive");
+  return solver_adjoint(c, g, a0, dt, rtol, lam, st, s);
 }
 
 int nrd_fd_eps(nrd_ctx* c, const double* u, const double* v, double* eps_host, cudaStream_t s) {

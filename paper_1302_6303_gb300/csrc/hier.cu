@@ -324,6 +324,35 @@ int hier_upload(Hier& H, std::string& err) {
   }
   gt0[G] = (int)gidx.size();
   H.nterm = (int)gidx.size();
+  // transposed ghost stencils for the adjoint
+  std::vector<int> ts_off(N + 1, 0), ts_g, tz_off(N + 1, 0), tz_g;
+  std::vector<double> ts_w;
+  {
+    std::vector<int> cnt(N, 0), zc(N, 0);
+    for (int g = 0; g < G; g++) {
+      if (gtype[g] != GT_SIBLING && gtype[g] != GT_CF) continue;
+      for (int q = gt0[g]; q < gt0[g + 1]; q++) cnt[gidx[q]]++;
+      zc[gzsrc[g]]++;
+    }
+    for (int c = 0; c < N; c++) {
+      ts_off[c + 1] = ts_off[c] + cnt[c];
+      tz_off[c + 1] = tz_off[c] + zc[c];
+    }
+    ts_g.assign(ts_off[N], 0);
+    ts_w.assign(ts_off[N], 0.0);
+    tz_g.assign(tz_off[N], 0);
+    std::vector<int> p1(ts_off.begin(), ts_off.end() - 1), p2(tz_off.begin(), tz_off.end() - 1);
+    for (int g = 0; g < G; g++) {
+      if (gtype[g] != GT_SIBLING && gtype[g] != GT_CF) continue;
+      for (int q = gt0[g]; q < gt0[g + 1]; q++) {
+        int c = gidx[q];
+        ts_g[p1[c]] = g;
+        ts_w[p1[c]] = gw[q];
+        p1[c]++;
+      }
+      tz_g[p2[gzsrc[g]]++] = g;
+    }
+  }
   // flux matching lists
   std::vector<int> rf_cell, rf_off, rf_face, rf_level;
   std::vector<int4> rf_g;
@@ -438,6 +467,11 @@ int hier_upload(Hier& H, std::string& err) {
   UP(H.d_rf_face, rf_face);
   UP(H.d_rf_g, rf_g);
   UP(H.d_rf_level, rf_level);
+  UP(H.d_ts_off, ts_off);
+  UP(H.d_ts_g, ts_g);
+  UP(H.d_ts_w, ts_w);
+  UP(H.d_tz_off, tz_off);
+  UP(H.d_tz_g, tz_g);
   {
     int rc = hier_tiles(H, err);
     if (rc != NRD_OK) return rc;
@@ -490,6 +524,9 @@ void hier_free(Hier& H) {
   F(H.d_patches); F(H.d_tiles); F(H.d_mask); F(H.d_wvol); F(H.d_gtype); F(H.d_gface);
   F(H.d_gcell); F(H.d_gzsrc); F(H.d_gt0); F(H.d_gidx); F(H.d_gw); F(H.d_rf_cell);
   F(H.d_rf_off); F(H.d_rf_face); F(H.d_rf_g); F(H.d_rf_level);
+  F(H.d_ts_off); F(H.d_ts_g); F(H.d_ts_w); F(H.d_tz_off); F(H.d_tz_g);
+  H.d_ts_off = nullptr; H.d_ts_g = nullptr; H.d_ts_w = nullptr; H.d_tz_off = nullptr;
+  H.d_tz_g = nullptr;
   for (int l = 0; l < NRD_MAX_LEVELS; l++) {
     F(H.d_cz_tgt[l]); F(H.d_cz_src[l]); F(H.d_cov[l]); F(H.d_lmap[l]);
     H.d_cz_tgt[l] = nullptr; H.d_cz_src[l] = nullptr; H.d_cov[l] = nullptr; H.d_lmap[l] = nullptr;

@@ -124,7 +124,7 @@ __device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double
 // the partial derivatives of Phi_E w.r.t. E_a, E_b and T_a (= w.r.t. T_b) and
 // of Phi_T w.r.t. T_a, T_b (sign(0) = 0).
 struct FaceLin {
-  double PE, PT, CE, CT, aEa, aEb, aT, bTa, bTb;
+  double PE, PT, CE, CT, aEa, aEb, aT, bTa, bTb, aZ;
 };
 __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, double Tb, double za,
                                             double zb, double h, double h3, double kh, double k,
@@ -147,6 +147,7 @@ __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, dou
   r.aEa = (-2.0 * t2 * Ea - r.PE * (hz - lt * sg)) * rden;
   r.aEb = (2.0 * t2 * Eb - r.PE * (hz + lt * sg)) * rden;
   r.aT = (3.0 * Tf2 * S * dE - r.PE * 1.5 * cL * Tf2 * adE) * rden;
+  r.aZ = -r.PE * h3 * S * rden;   // d Phi_E / d (z_a^3 + z_b^3)
   double sq = sqrt(Tf);
   double T25 = Tf2 * sq, T15 = Tf * sq;
   double dT = Tb - Ta;
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         PE = 0.0;
         PT = 0.0;
         if (LIN) {
-          for (int q = 0; q < 5; q++) io.jc[q * NS + fslot] = 0.0;
+          for (int q = 0; q < 6; q++) io.jc[q * NS + fslot] = 0.0;
           io.craw[fslot] = 0.0;
           io.craw[NS + fslot] = 0.0;
           put_scaled(io, NS, fslot, 0.0, 0.0);
@@ -384,6 +385,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[2 * NS + fslot] = 0.0;
           io.jc[3 * NS + fslot] = 0.0;
           io.jc[4 * NS + fslot] = 0.0;
+          io.jc[5 * NS + fslot] = (double)s * m * h * rq * rq * Db / zc;  // d Phi / d z_c^3
           io.craw[fslot] = Db;
           io.craw[NS + fslot] = 0.0;
           put_scaled(io, NS, fslot, io.beta * 2.0 * Db * rq / h, 0.0);
@@ -402,6 +404,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[2 * NS + fslot] = L.aT;
           io.jc[3 * NS + fslot] = L.bTa;
           io.jc[4 * NS + fslot] = L.bTb;
+          io.jc[5 * NS + fslot] = L.aZ;
           io.craw[fslot] = L.CE;
           io.craw[NS + fslot] = L.CT;
           const double b2 = A.lh.bh2[lvl][dir];
@@ -432,6 +435,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         if (LIN) {
           io.cc[idx] = 0.0;
           io.cc[N + idx] = 0.0;
+          io.cc[2L * N + idx] = 0.0;
           io.p2[idx] = 0.0;
           io.p2[N + idx] = 0.0;
           io.p2[2L * N + idx] = 0.0;
@@ -468,6 +472,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         // coupling tangent dc = cE vE + cT vT
         io.cc[idx] = -sig;
         io.cc[N + idx] = sig * (T3 + 3.0 * E * rT);
+        io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
         // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
         double sb = sig * io.beta, sbt = sb * T3;
         io.p2[idx] = sb;

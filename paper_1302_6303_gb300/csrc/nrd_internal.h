@@ -81,6 +81,13 @@ struct Hier {
   int* d_rf_face = nullptr;               // entries: face 0..5 of the coarse cell
   int4* d_rf_g = nullptr;                 // entries: ghost slots of the 4 fine fluxes
   int* d_rf_level = nullptr;              // nrf: level of the coarse cell
+  // transposed ghost stencils (adjoint): cell -> (ghost, weight), and the
+  // sibling / coarse-fine ghosts that take their z from a cell
+  int* d_ts_off = nullptr;
+  int* d_ts_g = nullptr;
+  double* d_ts_w = nullptr;
+  int* d_tz_off = nullptr;
+  int* d_tz_g = nullptr;
   // coefficient coarsening (per level l < L-1; sources on level l+1)
   int ncz[NRD_MAX_LEVELS] = {0};
   int* d_cz_tgt[NRD_MAX_LEVELS] = {nullptr};
@@ -125,9 +132,9 @@ struct StencilIO {
   double* out;          // F or Jv
   double* cfflux;       // [2][G] fine-side coarse-fine fluxes
   // ST_LIN outputs (face slots: [3N low faces | G boundary faces])
-  double* jc;           // [5][3N+G] flux partial derivatives
+  double* jc;           // [6][3N+G] flux partial derivatives (5: d Phi_E / d z^3)
   double* craw;         // [2][3N+G] frozen D_E, D_T (Robin slots: D_b)
-  double* cc;           // [2][N] coupling tangent coefficients
+  double* cc;           // [3][N] coupling partials (E, T, z^3)
   double beta;          // dt / a0
   float* a32;           // [2][3N+G] scaled P1 coefficients (FP32 V-cycle), or
   double* a64;          //   the FP64 array when a32 is null
@@ -141,6 +148,10 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
 void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s);
 void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, const double* cc,
                       const StencilIO& io, cudaStream_t s);
+// k_vjp.cu: JTw = (dF/du)^T w, dz = (dF/dz)^T w (dz may be null)
+void launch_vjp(const Hier& H, const double* jc, const double* cc, const float* z, const double* w,
+                double* lam, double* gam, double a0, double dt, double* out, double* dz,
+                cudaStream_t s);
 void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, double thr_g,
                 double thr_r, const double* emax, uint8_t* tags, cudaStream_t s);
 void launch_average_down(const Hier& H, double* x, int nfield, int fstride, cudaStream_t s);
@@ -249,8 +260,10 @@ struct nrd_ctx {
   double* d_gv = nullptr;      // 2G: ghosts of a direction
   double* d_cf = nullptr;      // 2G: fine-side coarse-fine fluxes
   double* d_tmp = nullptr;     // 2N scratch
-  double* d_jc = nullptr;      // [5][3N+G] frozen flux partial derivatives
-  double* d_cc = nullptr;      // [2][N] frozen coupling tangent coefficients
+  double* d_jc = nullptr;      // [6][3N+G] frozen flux partial derivatives
+  double* d_cc = nullptr;      // [3][N] frozen coupling partials
+  double* d_lam = nullptr;     // [2][3N+G] adjoint face scratch
+  double* d_gam = nullptr;     // [3][G] adjoint ghost scratch
   bool lin_ready = false;
   Reducer R;
   PcState* pc = nullptr;
@@ -272,6 +285,8 @@ struct nrd_ctx {
 int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
                   cudaStream_t s);
 int solver_alloc(nrd_ctx* c);
+int solver_adjoint(nrd_ctx* c, const double* g, double a0, double dt, double rtol, double* lam,
+                   nrd_stats* st, cudaStream_t s);
 void solver_free(nrd_ctx* c);
 // capi.cu helpers used by the solver
 int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,

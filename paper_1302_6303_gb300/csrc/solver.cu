@@ -88,10 +88,10 @@ __global__ void k_normalize(int n, const double* r, double* v, const double* nrm
     v[i] = sc * r[i];
 }
 
-// r = rhs_sign * F - Jx   (rhs = -F)
-__global__ void k_resid(int n, const double* F, const double* Jx, double* r) {
+// r = sign * rhs - Ax
+__global__ void k_resid(int n, const double* rhs, double sign, const double* Ax, double* r) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    r[i] = -F[i] - Jx[i];
+    r[i] = sign * rhs[i] - Ax[i];
 }
 
 int grid1(long n) {
@@ -136,20 +136,29 @@ void solver_free(nrd_ctx* c) {
   c->kry_m = 0;
 }
 
-// GMRES for J dx = -F to ||-F - J dx|| <= tol.  Returns iterations in *its.
-static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double fn,
-                 double tol, int* its, cudaStream_t s) {
+// GMRES for A x = sign * rhs to ||sign rhs - A x|| <= tol, with A = J (the
+// configured Jv form) or, when transposed, A = J^T at the last linearisation.
+// x: c->d_dx.  Returns iterations in *its.
+static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double dt,
+                 const double* rhs, double rhs_sign, double fn, double tol, bool transposed,
+                 int* its, cudaStream_t s) {
   Hier& H = c->H;
   const int n2 = 2 * H.N;
   const long stride = n2;
   const int m = c->kry_m;
   Small S = small_of(c);
   const int mode = (c->p.jv_mode == NRD_JV_ANALYTIC) ? NRD_JV_FROZEN : NRD_JV_FD;
+  auto apply = [&](const double* v, double* out) -> int {
+    if (transposed) {
+      launch_vjp(H, c->d_jc, c->d_cc, c->d_z, v, c->d_lam, c->d_gam, a0, dt, out, nullptr, s);
+      return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
+    }
+    return ctx_jv(c, u, v, b, c->d_F, a0, dt, mode, out, false, s);
+  };
   cudaMemsetAsync(c->d_dx, 0, n2 * sizeof(double), s);
-  // r0 = -F
   double rn2 = fn * fn;
-  const double* r0 = c->d_F;
-  double sign = -1.0;
+  const double* r0 = rhs;
+  double sign = rhs_sign;
   int total = 0;
   *its = 0;
   if (fn <= tol) return NRD_OK;
@@ -168,7 +177,7 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
       int rc = pc_apply(c->pc, H, Vj, Zj, s);
       c->timer.end(NRD_TK_PC_APPLY, s);
       if (rc != NRD_OK) return rc;
-      rc = ctx_jv(c, u, Zj, b, c->d_F, a0, dt, mode, c->d_w, false, s);
+      rc = apply(Zj, c->d_w);
       if (rc != NRD_OK) return rc;
       total++;
       // CGS2
@@ -199,10 +208,10 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
     launch_lincomb_dev(n2, c->d_dx, c->d_Z, stride, j, S.y, s);
     if (conv) break;
     if (total >= c->p.max_krylov) break;
-    // restart from the true residual r = -F - J dx
-    int rc = ctx_jv(c, u, c->d_dx, b, c->d_F, a0, dt, mode, c->d_w, false, s);
+    // restart from the true residual r = sign * rhs - A dx
+    int rc = apply(c->d_dx, c->d_w);
     if (rc != NRD_OK) return rc;
-    k_resid<<<grid1(n2), 256, 0, s>>>(n2, c->d_F, c->d_w, c->d_r);
+    k_resid<<<grid1(n2), 256, 0, s>>>(n2, rhs, rhs_sign, c->d_w, c->d_r);
     launch_wdot(H, c->R, c->d_r, c->d_r, SL_R, s);
     rn2 = read_slot(c, SL_R, s);
     r0 = c->d_r;
@@ -252,7 +261,7 @@ int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, 
     }
     loc.pc_setups++;
     int its = 0;
-    rc = gmres(c, u, b, a0, dt, fn, eta * fn, &its, s);
+    rc = gmres(c, u, b, a0, dt, c->d_F, -1.0, fn, eta * fn, false, &its, s);
     if (rc != NRD_OK) return rc;
     loc.krylov_its += its;
     // positivity-constrained update (Sec. 4.1 remark, reading R7)
@@ -294,5 +303,34 @@ int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, 
   loc.status = (fn > stop) ? NRD_ENONCONV : NRD_OK;
   if (st) *st = loc;
   if (loc.status != NRD_OK) c->err = "Newton did not converge within max_newton";
+  return loc.status;
+}
+
+// Solve J^T lam = g at the last linearisation (adjoint of one implicit step)
+// by GMRES with the forward preconditioner on the right.
+int solver_adjoint(nrd_ctx* c, const double* g, double a0, double dt, double rtol, double* lam,
+                   nrd_stats* st, cudaStream_t s) {
+  int rc = solver_alloc(c);
+  if (rc != NRD_OK) return rc;
+  Hier& H = c->H;
+  const int n2 = 2 * H.N;
+  launch_wdot(H, c->R, g, g, SL_F, s);
+  double gn = std::sqrt(read_slot(c, SL_F, s));
+  nrd_stats loc{};
+  loc.fnorm0 = gn;
+  int its = 0;
+  rc = gmres(c, nullptr, nullptr, a0, dt, g, 1.0, gn, rtol * gn, true, &its, s);
+  if (rc != NRD_OK) return rc;
+  cudaMemcpyAsync(lam, c->d_dx, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  // final residual of the adjoint system
+  launch_vjp(H, c->d_jc, c->d_cc, c->d_z, lam, c->d_lam, c->d_gam, a0, dt, c->d_w, nullptr, s);
+  k_resid<<<grid1(n2), 256, 0, s>>>(n2, g, 1.0, c->d_w, c->d_r);
+  launch_wdot(H, c->R, c->d_r, c->d_r, SL_R, s);
+  double rn = std::sqrt(read_slot(c, SL_R, s));
+  loc.krylov_its = its;
+  loc.fnorm = rn;
+  loc.status = (rn <= 10.0 * rtol * gn || gn == 0.0) ? NRD_OK : NRD_ENONCONV;
+  if (st) *st = loc;
+  if (loc.status != NRD_OK) c->err = "adjoint GMRES did not reach the tolerance";
   return loc.status;
 }

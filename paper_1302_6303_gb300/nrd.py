@@ -24,7 +24,7 @@ PC_F64, PC_F32 = 0, 1
 EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
-    "nrd_jv", "nrd_linearise", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
+    "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
     "nrd_step", "nrd_tag", "nrd_autotune", "nrd_wdot_noalloc", "nrd_measure_peaks",
     "nrd_timing_enable",
     "nrd_timing_read",
@@ -89,6 +89,8 @@ def load(path: str = _LIBPATH):
         "nrd_residual": (c_int, [vp, dp, dp, c_dbl, c_dbl, dp, vp]),
         "nrd_jv": (c_int, [vp, dp, dp, dp, dp, c_dbl, c_dbl, c_int, dp, vp]),
         "nrd_linearise": (c_int, [vp, dp, dp, c_dbl, c_dbl, dp, vp]),
+        "nrd_vjp": (c_int, [vp, dp, c_dbl, c_dbl, dp, dp, vp]),
+        "nrd_adjoint_solve": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, dp, P(Stats), vp]),
         "nrd_fd_eps": (c_int, [vp, dp, dp, P(c_dbl), vp]),
         "nrd_dot": (c_int, [vp, dp, dp, P(c_dbl), vp]),
         "nrd_precond_setup": (c_int, [vp, dp, c_dbl, c_dbl, vp]),
@@ -235,6 +237,25 @@ class Context:
         self._check(self.lib.nrd_linearise(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
                                            a0, dt, _ptr(out, torch.float64), _stream()))
         return out
+
+    def vjp(self, w, a0, dt, out=None, dz=None, want_dz=True):
+        """(dF/du)^T w and (dF/dz)^T w at the last linearisation."""
+        out = torch.empty_like(w) if out is None else out
+        if want_dz and dz is None:
+            dz = torch.empty(self.N, dtype=torch.float64, device=w.device)
+        self._check(self.lib.nrd_vjp(self._h, _ptr(w, torch.float64), a0, dt,
+                                     _ptr(out, torch.float64), _ptr(dz, torch.float64), _stream()))
+        return out, dz
+
+    def adjoint_solve(self, g, a0, dt, rtol=1e-10, out=None, check=True):
+        """Solve J^T lam = g at the last linearisation."""
+        out = torch.empty_like(g) if out is None else out
+        st = Stats()
+        rc = self.lib.nrd_adjoint_solve(self._h, _ptr(g, torch.float64), a0, dt, rtol,
+                                        _ptr(out, torch.float64), ctypes.byref(st), _stream())
+        if check and rc != OK:
+            self._check(rc)
+        return out, st.as_dict()
 
     def fd_eps(self, u, v):
         e = ctypes.c_double()

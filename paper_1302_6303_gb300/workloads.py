@@ -90,6 +90,18 @@ class Hierarchy:
             out.append((idx + 0.5) / n)
         return L, out[0], out[1], out[2]
 
+    def covered_mask(self):
+        """True for cells covered by the next finer level (layout only)."""
+        L, I, J, K = self.cell_ijk()
+        cov = np.zeros(I.size, dtype=bool)
+        for l in range(self.nlevels - 1):
+            fine = np.zeros(self.level_n(l + 1), dtype=bool)
+            for lo, hi in self.levels[l + 1]:
+                fine[lo[0]:hi[0] + 1, lo[1]:hi[1] + 1, lo[2]:hi[2] + 1] = True
+            sel = L == l
+            cov[sel] = fine[2 * I[sel], 2 * J[sel], 2 * K[sel]]
+        return cov
+
     def ghost_count_per_patch(self):
         out = []
         for lev in self.levels:
