@@ -299,6 +299,35 @@ int nrd_wdot_noalloc(const double* x, const double* y, const float* w, int64_t n
 int nrd_measure_peaks(double* fp64_tflops_host, double* fp32_tflops_host, double* copy_gbs_host,
                       cudaStream_t stream);
 
+/* ---------------------------------------------- time-step control (Sec. 3.4-3.5) */
+enum { NRD_DT_EPS = 0, NRD_DT_PC47 = 1 };
+
+/* Time derivative at t_{n+1} from the left-hand side of Eq. bdf2 (Remark 2 of
+ * Sec. 3.5): udot = (a0 u_{n+1} - (1+al) u_n + al^2/(1+al) u_{n-1}) / dt with
+ * al = dt/dt_prev; backward Euler (u_nm1 NULL): (u_{n+1} - u_n)/dt.
+ * All vectors 2*ncells doubles. */
+int nrd_time_derivative(nrd_ctx* ctx, const double* u_np1, const double* u_n,
+                        const double* u_nm1, double dt, double dt_prev, double* udot,
+                        cudaStream_t stream);
+
+/* Generalised leapfrog predictor (Eq. leapfrog), initial guess and error
+ * reference: u_p = u_n + (1+al) dt udot_n - al^2 (u_n - u_{n-1}), al = dt/dt_prev. */
+int nrd_predict(nrd_ctx* ctx, const double* u_n, const double* u_nm1, const double* udot_n,
+                double dt, double dt_prev, double* u_p, cudaStream_t stream);
+
+/* Local error estimate (Eq. bdf2le) e = (al+1)/(3 al+2) (u_{n+1} - u_p) in the
+ * scaled max norm of Sec. 3.5: max over leaf cells of |e_E/(E+eta_E)| and
+ * |e_T/(T+eta_T)|, with E, T from u_{n+1} (synchronises; *err_host). */
+int nrd_lte(nrd_ctx* ctx, const double* u_np1, const double* u_p, double alpha, double eta_E,
+            double eta_T, double* err_host, cudaStream_t stream);
+
+/* Step-size controllers (host arithmetic, no context): NRD_DT_EPS, Eq. odets,
+ * dt_{n+1} = (eps_t/err_n)^(1/3) dt_n; NRD_DT_PC47, Eq. pc47 with k kI = 0.4,
+ * k kP = 0.7, k = 3: alpha_{n+1} = (eps_t/err_n)^kI (err_{n-1}/err_n)^kP alpha_n,
+ * alpha_n = dt_n/dt_{n-1}, dt_{n+1} = alpha_{n+1} dt_n. */
+int nrd_dt_control(int kind, double eps_t, double err_n, double err_nm1, double dt_n,
+                   double dt_nm1, double* dt_next_host);
+
 /* ------------------------------------------------------- kernel timing
  * Optional CUDA-event timing of the library's kernel groups, recorded on the
  * stream each group is launched on (a start/stop event pair around every

@@ -1331,6 +1331,48 @@ void orc_set_material_f64(orc_hier* h, const double* z) {
   for (long i = 0; i < H->N; i++) H->z[i] = z[i];
 }
 
+// Sec. 3.5 Remark 2: time derivative at t_{n+1} from the left-hand side of
+// Eq. bdf2 (backward Euler when u_nm1 is null).
+void orc_time_derivative(orc_hier* h, const double* u_np1, const double* u_n,
+                         const double* u_nm1, double dt, double dt_prev, double* udot) {
+  Hier* H = reinterpret_cast<Hier*>(h);
+  for (long i = 0; i < 2 * H->N; i++) {
+    if (u_nm1) {
+      double al = dt / dt_prev;
+      double lhs = (1.0 + 2.0 * al) / (1.0 + al) * u_np1[i] - (1.0 + al) * u_n[i] +
+                   al * al / (1.0 + al) * u_nm1[i];
+      udot[i] = lhs / dt;
+    } else {
+      udot[i] = (u_np1[i] - u_n[i]) / dt;
+    }
+  }
+}
+
+// Eq. leapfrog: generalised leapfrog predictor.
+void orc_predict(orc_hier* h, const double* u_n, const double* u_nm1, const double* udot_n,
+                 double dt, double dt_prev, double* u_p) {
+  Hier* H = reinterpret_cast<Hier*>(h);
+  double al = dt / dt_prev;
+  for (long i = 0; i < 2 * H->N; i++)
+    u_p[i] = u_n[i] + (1.0 + al) * dt * udot_n[i] - al * al * (u_n[i] - u_nm1[i]);
+}
+
+// Eq. bdf2le with the scaled max norm of Sec. 3.5 over leaf cells.
+double orc_lte(orc_hier* h, const double* u_np1, const double* u_p, double alpha, double eta_E,
+               double eta_T) {
+  Hier* H = reinterpret_cast<Hier*>(h);
+  const long N = H->N;
+  double m = 0.0;
+  for (long i = 0; i < N; i++) {
+    if (H->covered_idx(i)) continue;
+    double eE = (alpha + 1.0) / (3.0 * alpha + 2.0) * (u_np1[i] - u_p[i]);
+    double eT = (alpha + 1.0) / (3.0 * alpha + 2.0) * (u_np1[N + i] - u_p[N + i]);
+    m = std::max(m, std::fabs(eE / (u_np1[i] + eta_E)));
+    m = std::max(m, std::fabs(eT / (u_np1[N + i] + eta_T)));
+  }
+  return m;
+}
+
 double orc_fd_eps(orc_hier* h, const double* u, const double* v) {
   return fd_eps(*reinterpret_cast<Hier*>(h), u, v);
 }

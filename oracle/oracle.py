@@ -63,6 +63,10 @@ def _load():
         "orc_fd_eps": (ctypes.c_double, [vp, _dp, _dp]),
         "orc_vjp": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp, _dp]),
         "orc_set_material_f64": (None, [vp, _dp]),
+        "orc_time_derivative": (None, [vp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
+        "orc_predict": (None, [vp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
+        "orc_lte": (ctypes.c_double, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double]),
         "orc_jv_fd": (ctypes.c_double, [vp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                         _dp, _dp]),
         "orc_dot": (ctypes.c_double, [vp, _dp, _dp]),
@@ -165,6 +169,19 @@ class Oracle:
         dz = np.empty(self.N) if with_dz else None
         _lib.orc_vjp(self._h, _d(u), _d(np.ascontiguousarray(w)), a0, dt, _d(JTw), _d(dz), _d(Jab))
         return JTw, dz, Jab
+
+    def time_derivative(self, u_np1, u_n, u_nm1, dt, dt_prev=0.0):
+        out = np.empty(2 * self.N)
+        _lib.orc_time_derivative(self._h, _d(u_np1), _d(u_n), _d(u_nm1), dt, dt_prev, _d(out))
+        return out
+
+    def predict(self, u_n, u_nm1, udot_n, dt, dt_prev):
+        out = np.empty(2 * self.N)
+        _lib.orc_predict(self._h, _d(u_n), _d(u_nm1), _d(udot_n), dt, dt_prev, _d(out))
+        return out
+
+    def lte(self, u_np1, u_p, alpha, eta_E=1e-5, eta_T=1e-3):
+        return _lib.orc_lte(self._h, _d(u_np1), _d(u_p), alpha, eta_E, eta_T)
 
     def fd_eps(self, u, v):
         return _lib.orc_fd_eps(self._h, _d(u), _d(v))

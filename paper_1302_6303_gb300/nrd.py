@@ -20,12 +20,14 @@ BC_NEUMANN, BC_ROBIN = 0, 1
 LIM_WILSON, LIM_PAPER_LITERAL = 0, 1
 JV_FD, JV_ANALYTIC, JV_FROZEN = 0, 1, 2
 PC_F64, PC_F32 = 0, 1
+DT_EPS, DT_PC47 = 0, 1
 
 EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
-    "nrd_step", "nrd_tag", "nrd_autotune", "nrd_wdot_noalloc", "nrd_measure_peaks",
+    "nrd_step", "nrd_tag", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
+    "nrd_autotune", "nrd_wdot_noalloc", "nrd_measure_peaks",
     "nrd_timing_enable",
     "nrd_timing_read",
 ]
@@ -99,6 +101,10 @@ def load(path: str = _LIBPATH):
         "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
         "nrd_autotune": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
+        "nrd_time_derivative": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, dp, vp]),
+        "nrd_predict": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, dp, vp]),
+        "nrd_lte": (c_int, [vp, dp, dp, c_dbl, c_dbl, c_dbl, P(c_dbl), vp]),
+        "nrd_dt_control": (c_int, [c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, P(c_dbl)]),
         "nrd_wdot_noalloc": (c_int, [dp, dp, fp, ctypes.c_int64, dp, vp]),
         "nrd_measure_peaks": (c_int, [P(c_dbl), P(c_dbl), P(c_dbl), vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
@@ -143,6 +149,15 @@ def measure_peaks():
     if rc != OK:
         raise NrdError(rc, "nrd_measure_peaks failed")
     return {"fp64_tflops": a.value, "fp32_tflops": b.value, "copy_gbs": c.value}
+
+
+def dt_control(kind, eps_t, err_n, err_nm1, dt_n, dt_nm1):
+    """EPS (Eq. odets) or PC.4.7 (Eq. pc47) step-size controller."""
+    out = ctypes.c_double()
+    rc = load().nrd_dt_control(kind, eps_t, err_n, err_nm1, dt_n, dt_nm1, ctypes.byref(out))
+    if rc != OK:
+        raise NrdError(rc, "nrd_dt_control: bad arguments")
+    return out.value
 
 
 def wdot_noalloc(x, y, w, out=None):
@@ -301,6 +316,27 @@ class Context:
         self._check(self.lib.nrd_autotune(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
                                           a0, dt, t, ctypes.byref(ms), _stream()))
         return (t[0], t[1], t[2]), ms.value
+
+    def time_derivative(self, u_np1, u_n, u_nm1, dt, dt_prev=0.0, out=None):
+        out = torch.empty_like(u_n) if out is None else out
+        self._check(self.lib.nrd_time_derivative(self._h, _ptr(u_np1, torch.float64),
+                                                 _ptr(u_n, torch.float64),
+                                                 _ptr(u_nm1, torch.float64), dt, dt_prev,
+                                                 _ptr(out, torch.float64), _stream()))
+        return out
+
+    def predict(self, u_n, u_nm1, udot_n, dt, dt_prev, out=None):
+        out = torch.empty_like(u_n) if out is None else out
+        self._check(self.lib.nrd_predict(self._h, _ptr(u_n, torch.float64),
+                                         _ptr(u_nm1, torch.float64), _ptr(udot_n, torch.float64),
+                                         dt, dt_prev, _ptr(out, torch.float64), _stream()))
+        return out
+
+    def lte(self, u_np1, u_p, alpha, eta_E=1e-5, eta_T=1e-3):
+        e = ctypes.c_double()
+        self._check(self.lib.nrd_lte(self._h, _ptr(u_np1, torch.float64), _ptr(u_p, torch.float64),
+                                     alpha, eta_E, eta_T, ctypes.byref(e), _stream()))
+        return e.value
 
     def timing_enable(self, on=True):
         self._check(self.lib.nrd_timing_enable(self._h, 1 if on else 0))

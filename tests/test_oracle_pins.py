@@ -622,3 +622,60 @@ def test_vjp_matches_central_differences(name):
         fz[k] = (fp - fm) / (2 * hk)
     o.set_material_f64(z)
     np.testing.assert_allclose(dz, fz, rtol=0, atol=1e-6 * np.abs(fz).max())
+
+
+# ---------------------------------------------------------- step control
+def _tfield(h, f):
+    """a field whose every component is f(t) times a positive spatial shape"""
+    L, x, y, zc = h.cell_centres()
+    shape = np.concatenate([1.0 + x + 0.5 * y, 2.0 + zc])
+    return lambda t: shape * f(t)
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 2.0])
+def test_leapfrog_predictor_error_closed_form(alpha):
+    """Eq. leapfrog with the exact derivative: exact for quadratics in time;
+    for u = t^3 its error is -(1 + dt_{n-1}/dt_n) dt_n^3/6 u''' (Sec. 3.5)."""
+    h = W.uniform(3)
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    tau = 0.01
+    dt = alpha * tau
+    for f, df, err in [(lambda t: 1 + 2 * t + 3 * t * t, lambda t: 2 + 6 * t, lambda: 0.0),
+                       (lambda t: t ** 3, lambda t: 3 * t * t,
+                        lambda: -(1 + tau / dt) * dt ** 3 / 6 * 6)]:
+        u = _tfield(h, f)
+        ud = _tfield(h, df)
+        up = o.predict(u(0.0), u(-tau), ud(0.0), dt, tau)
+        shape = _tfield(h, lambda t: 1.0)(0.0)
+        np.testing.assert_allclose(up - u(dt), err() * shape, rtol=0, atol=1e-14 * np.abs(u(dt)).max())
+
+
+@pytest.mark.parametrize("alpha", [1.0, 0.5, 2.0])
+def test_bdf2_error_estimate_exact_for_cubics(alpha):
+    """For u' = 3 t^2 (solution t^3) the BDF2 step from exact history, the
+    derivative from the left-hand side of Eq. bdf2 and the estimate of Eq.
+    bdf2le recover the true local error."""
+    h = W.uniform(2)
+    o = Oracle(h, np.ones(h.ncells, np.float32))
+    tau = 0.02
+    dt = alpha * tau
+    u = _tfield(h, lambda t: t ** 3)
+    un, unm1 = u(0.0), u(-tau)
+    # the BDF2 step: time derivative at t_{n+1} equals f = 3 t_{n+1}^2 (the
+    # derivative is affine in u_{n+1}: solve it from two evaluations)
+    shape = _tfield(h, lambda t: 1.0)(0.0)
+    target = 3 * dt * dt * shape
+    d0 = o.time_derivative(np.zeros_like(un), un, unm1, dt, tau)
+    d1 = o.time_derivative(np.ones_like(un), un, unm1, dt, tau)
+    u1 = (target - d0) / (d1 - d0)
+    true_err = u1 - u(dt)
+    # predictor with the derivative at t_n from the previous BDF2 step's LHS is
+    # not exact; use the exact derivative, as in the derivation of Eq. bdf2le
+    up = o.predict(un, unm1, _tfield(h, lambda t: 3 * t * t)(0.0), dt, tau)
+    est = (alpha + 1) / (3 * alpha + 2) * (u1 - up)
+    np.testing.assert_allclose(est, true_err, rtol=1e-10, atol=1e-18)
+    # and the scaled max norm
+    m = o.lte(u1, up, alpha, eta_E=0.5, eta_T=0.25)
+    N = h.ncells
+    ref = max(np.max(np.abs(est[:N] / (u1[:N] + 0.5))), np.max(np.abs(est[N:] / (u1[N:] + 0.25))))
+    assert abs(m - ref) <= 1e-15 * ref
