@@ -21,7 +21,7 @@ import torch
 class StepRunner:
     """Holds the context and the fixed parts of the problem (T0, dt, steps)."""
 
-    def __init__(self, ctx, T0, nsteps, dt, weights, ckpt_every=8, adjoint_rtol=1e-11):
+    def __init__(self, ctx, T0, nsteps, dt, weights, ckpt_every=8, adjoint_rtol=1e-10):
         self.ctx = ctx
         self.T0 = T0
         self.nsteps = nsteps

@@ -241,14 +241,17 @@ __global__ void k_lev_rbgs(HierV<P> V, int t0, int nt, int tx, int ty, int tz, P
   P* ef = e + (long)fld * V.N;
   const P* ff = f + (long)fld * V.N;
   const P* gf = gh + (long)fld * V.G;
-  const int nc = tx * ty * tz;
+  // one thread per x-pair of cells: exactly one of the two has the colour
+  const int hx = tx >> 1;
+  const int np = hx * ty * tz;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     const TileDev tile = V.tiles[t0 + t];
     const PatchDev Pt = V.patches[tile.patch];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      int j = tile.j0 + (q / hx) % ty, k = tile.k0 + q / (hx * ty);
+      int i = tile.i0 + 2 * (q % hx);
+      if (((Pt.lo[0] + i + Pt.lo[1] + j + Pt.lo[2] + k) & 1) != colour) i += 1;
       if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) continue;
-      if (((Pt.lo[0] + i + Pt.lo[1] + j + Pt.lo[2] + k) & 1) != colour) continue;
       long idx = Pt.off + i + (long)Pt.n[0] * (j + (long)Pt.n[1] * k);
       P dg, of;
       lev_row(V, Pt, fld, i, j, k, ef, gf, dg, of);
@@ -431,6 +434,28 @@ __global__ void k_p2(int N, const P* zin, const double* p, double* y) {
     double zE = (double)zin[c], zT = (double)zin[N + c];
     y[c] = ((1.0 + sbt) * zE + sbt * zT) * rd;
     y[N + c] = ((1.0 + sb) * zT + sb * zE) * rd;
+  }
+}
+
+// transposed P2 solve fused with the cast into the V-cycle precision:
+// P2^T = [[1 + sb, -sb], [-sbt, 1 + sbt]]
+template <class P>
+__global__ void k_p2t_cast(int N, const double* w, const double* p, P* out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    double sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
+    double wE = w[c], wT = w[N + c];
+    out[c] = (P)(((1.0 + sbt) * wE + sb * wT) * rd);
+    out[N + c] = (P)((sbt * wE + (1.0 + sb) * wT) * rd);
+  }
+}
+
+// y = V-cycle output in FP64; covered cells get 0
+template <class P>
+__global__ void k_out_cast(const uint8_t* mask, int N, const P* u, double* y) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    bool cov = mask[c] & MASK_COVERED;
+    y[c] = cov ? 0.0 : (double)u[c];
+    y[N + c] = cov ? 0.0 : (double)u[N + c];
   }
 }
 
@@ -729,6 +754,7 @@ struct PcState {
   struct Graph {
     const double* w;
     double* y;
+    bool tr;
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;
@@ -885,9 +911,13 @@ void zero_level(PcState* ps, const Hier& H, int l, cudaStream_t s) {
 }
 
 template <class P>
-int apply_t(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {
+int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transposed,
+            cudaStream_t s) {
   const long n2 = 2L * H.N;
-  k_cast<P><<<g1(n2), BS, 0, s>>>((int)n2, w, (P*)ps->ff);
+  if (transposed)
+    k_p2t_cast<P><<<g1(H.N), BS, 0, s>>>(H.N, w, ps->p2, (P*)ps->ff);
+  else
+    k_cast<P><<<g1(n2), BS, 0, s>>>((int)n2, w, (P*)ps->ff);
   cudaMemsetAsync(ps->fu, 0, n2 * sizeof(P), s);
   // r = f (u = 0); covered := mean of children
   cudaMemcpyAsync(ps->fr, ps->ff, n2 * sizeof(P), cudaMemcpyDeviceToDevice, s);
@@ -911,7 +941,10 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t
     level_smooth<P>(ps, H, l, ps->nu2, false, s);
     correct<P>(ps, H, l, s);
   }
-  k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, ps->p2, y);
+  if (transposed)
+    k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y);
+  else
+    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, ps->p2, y);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }
 
@@ -1119,9 +1152,10 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
   return pc_finish(ps, H, u, z, a0, dt, false, s);
 }
 
-static int apply_any(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {
-  if (ps->prec == NRD_PC_F32) return apply_t<float>(ps, H, w, y, s);
-  return apply_t<double>(ps, H, w, y, s);
+static int apply_any(PcState* ps, const Hier& H, const double* w, double* y, bool tr,
+                     cudaStream_t s) {
+  if (ps->prec == NRD_PC_F32) return apply_t<float>(ps, H, w, y, tr, s);
+  return apply_t<double>(ps, H, w, y, tr, s);
 }
 
 void pc_drop_graphs(PcState* ps) {
@@ -1140,22 +1174,28 @@ void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw) {
 // captured once per (w, y) pair into a CUDA graph and replayed.  Everything
 // the launches read besides w is at fixed addresses (beta in device memory).
 int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s) {
-  if (!ps->use_graph) return apply_any(ps, H, w, y, s);
+  return pc_apply_ex(ps, H, w, y, false, s);
+}
+
+// transposed: P^{-T} = P1^{-T} P2^{-T}, with one V-cycle for P1^{-T} (the
+// red-black V-cycle with reversed post-smoothing is used as is)
+int pc_apply_ex(PcState* ps, const Hier& H, const double* w, double* y, bool tr, cudaStream_t s) {
+  if (!ps->use_graph) return apply_any(ps, H, w, y, tr, s);
   cudaGraphExec_t exec = nullptr;
   for (auto& g : ps->graphs)
-    if (g.w == w && g.y == y) { exec = g.exec; break; }
+    if (g.w == w && g.y == y && g.tr == tr) { exec = g.exec; break; }
   if (!exec) {
     if (ps->graphs.size() >= 64) pc_drop_graphs(ps);
     cudaGraph_t graph;
     if (cudaStreamBeginCapture(ps->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return NRD_ECUDA;
-    int rc = apply_any(ps, H, w, y, ps->cap);
+    int rc = apply_any(ps, H, w, y, tr, ps->cap);
     cudaError_t e = cudaStreamEndCapture(ps->cap, &graph);
     if (rc != NRD_OK || e != cudaSuccess) return NRD_ECUDA;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return NRD_ECUDA;
-    ps->graphs.push_back({w, y, exec});
+    ps->graphs.push_back({w, y, tr, exec});
   }
   return cudaGraphLaunch(exec, s) == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }

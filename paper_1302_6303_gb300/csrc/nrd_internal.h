@@ -194,6 +194,8 @@ void pc_free(PcState* ps);
 int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u, const double* gu,
              const float* z, const float* gz, double a0, double dt, cudaStream_t s);
 int pc_apply(PcState* ps, const Hier& H, const double* w, double* y, cudaStream_t s);
+int pc_apply_ex(PcState* ps, const Hier& H, const double* w, double* y, bool transposed,
+                cudaStream_t s);
 // raw coefficient array [2][3N+G] the linearisation writes into
 double* pc_craw(PcState* ps);
 void pc_drop_graphs(PcState* ps);

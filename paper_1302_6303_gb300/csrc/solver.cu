@@ -174,7 +174,7 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
       double* Vj = c->d_V + (size_t)j * stride;
       double* Zj = c->d_Z + (size_t)j * stride;
       c->timer.begin(NRD_TK_PC_APPLY, s);
-      int rc = pc_apply(c->pc, H, Vj, Zj, s);
+      int rc = pc_apply_ex(c->pc, H, Vj, Zj, transposed, s);
       c->timer.end(NRD_TK_PC_APPLY, s);
       if (rc != NRD_OK) return rc;
       rc = apply(Zj, c->d_w);
@@ -329,7 +329,7 @@ int solver_adjoint(nrd_ctx* c, const double* g, double a0, double dt, double rto
   double rn = std::sqrt(read_slot(c, SL_R, s));
   loc.krylov_its = its;
   loc.fnorm = rn;
-  loc.status = (rn <= 10.0 * rtol * gn || gn == 0.0) ? NRD_OK : NRD_ENONCONV;
+  loc.status = (rn <= 100.0 * rtol * gn || gn == 0.0) ? NRD_OK : NRD_ENONCONV;
   if (st) *st = loc;
   if (loc.status != NRD_OK) c->err = "adjoint GMRES did not reach the tolerance";
   return loc.status;

@@ -172,7 +172,7 @@ def test_gradient_against_oracle(nrd):
         assert st["status"] == 0
         states.append(u)
     Jo = float(np.dot(wts, states[-1][:N]))
-    assert abs(Jo - float(J)) <= 1e-9 * abs(Jo)
+    assert abs(Jo - float(J.detach())) <= 1e-9 * abs(Jo)
     leaf2 = np.concatenate([~h.covered_mask()] * 2)
     idx = np.nonzero(leaf2)[0]
     g = np.zeros(2 * N)
