@@ -326,6 +326,7 @@ def main():
     # autotuner: stencil tile shape for this hierarchy (untimed set-up)
     u_t = torch.from_numpy(u0).cuda()
     tile, _ = ctx.autotune(u_t, u_t, 1.0, DT)
+    sweeps, _ = ctx.autotune_sweeps(u_t, None, DT)
     del u_t
 
     # production form, timed (replicas: every rank runs the same workload)
@@ -370,7 +371,8 @@ def main():
     plain = None
     if not args.no_plain:
         ctxp = make_ctx(nrd, h, z, torch, production=False)
-        ctxp.set_params(tile_x=tile[0], tile_y=tile[1], tile_z=tile[2])
+        ctxp.set_params(tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], nu1=sweeps[0],
+                        nu2=sweeps[1], coarse_sweeps=sweeps[2])
         rp = run_steps(ctxp, torch, u0, args.steps, args.warmup, flush, timing=False)
         pms = sum(rp["ms"])
         plain = {"form": "FD Jv + FP64 V-cycle", "ms_per_step": pms / args.steps,
@@ -395,8 +397,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "base": 64, "levels": 2, "leaf_cells": leaf,
                    "patches": sum(h.nboxes), "dt": DT, "newton_rtol": 1e-8,
-                   "form": "analytic Jv + FP32 FAC/GMG V(2,2) + FGMRES(30)",
-                   "tile": list(tile),
+                   "form": "analytic Jv + FP32 FAC/GMG V-cycle + FGMRES(30)",
+                   "tile": list(tile), "sweeps_nu1_nu2_coarse": list(sweeps),
                    "krylov_per_step": r["krylov"] / args.steps,
                    "newton_per_step": r["newton"] / args.steps,
                    "l2": "256 MB buffer written between timed steps",

@@ -576,6 +576,62 @@ int nrd_autotune(nrd_ctx* c, const double* u, const double* b, double a0, double
   return check_launch(c);
 }
 
+int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, double dt,
+                        double dt_prev, int* nu_out, double* ms_out, cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  int rc = need_ready(c);
+  if (rc) return rc;
+  if (!u_n || !(dt > 0.0)) return fail(c, NRD_EINVAL, "bad argument");
+  // candidates (nu1, nu2, coarse sweeps): the paper's V(1,0) up to V(3,3)
+  const int cand[][3] = {{1, 0, 2}, {1, 1, 2}, {2, 1, 3}, {2, 2, 4}, {3, 3, 6}};
+  const int ncand = sizeof(cand) / sizeof(cand[0]);
+  const size_t n2 = 2 * (size_t)c->H.N;
+  bool timer_on = c->timer.on;
+  c->timer.on = false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int best = -1;
+  float best_ms = 1e30f;
+  for (int q = 0; q < ncand; q++) {
+    c->p.nu1 = cand[q][0];
+    c->p.nu2 = cand[q][1];
+    c->p.coarse_sweeps = cand[q][2];
+    pc_set_sweeps(c->pc, cand[q][0], cand[q][1], cand[q][2]);
+    float ms = 0.0f;
+    bool ok = true;
+    for (int rep = 0; rep < 2; rep++) {
+      cudaMemcpyAsync(c->d_tmp, u_n, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      nrd_stats st;
+      cudaEventRecord(e0, s);
+      int r = nrd_step(c, c->d_tmp, u_n, u_nm1, dt, dt_prev, &st, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      if (r != NRD_OK) { ok = false; break; }
+      if (rep == 1) cudaEventElapsedTime(&ms, e0, e1);
+    }
+    if (ok && ms < best_ms) {
+      best_ms = ms;
+      best = q;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->timer.on = timer_on;
+  if (best < 0) return fail(c, NRD_ENONCONV, "no sweep schedule converged");
+  c->p.nu1 = cand[best][0];
+  c->p.nu2 = cand[best][1];
+  c->p.coarse_sweeps = cand[best][2];
+  pc_set_sweeps(c->pc, cand[best][0], cand[best][1], cand[best][2]);
+  if (nu_out) {
+    nu_out[0] = cand[best][0];
+    nu_out[1] = cand[best][1];
+    nu_out[2] = cand[best][2];
+  }
+  if (ms_out) *ms_out = best_ms;
+  return check_launch(c);
+}
+
 int nrd_timing_enable(nrd_ctx* c, int enable) {
   if (!c) return NRD_EINVAL;
   c->timer.on = enable != 0;

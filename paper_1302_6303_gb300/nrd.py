@@ -27,7 +27,7 @@ EXPORTED = [
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
     "nrd_step", "nrd_tag", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
-    "nrd_autotune", "nrd_wdot_noalloc", "nrd_measure_peaks",
+    "nrd_autotune", "nrd_autotune_sweeps", "nrd_wdot_noalloc", "nrd_measure_peaks",
     "nrd_timing_enable",
     "nrd_timing_read",
 ]
@@ -101,6 +101,7 @@ def load(path: str = _LIBPATH):
         "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
         "nrd_autotune": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
+        "nrd_autotune_sweeps": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
         "nrd_time_derivative": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, dp, vp]),
         "nrd_predict": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, dp, vp]),
         "nrd_lte": (c_int, [vp, dp, dp, c_dbl, c_dbl, c_dbl, P(c_dbl), vp]),
@@ -316,6 +317,16 @@ class Context:
         self._check(self.lib.nrd_autotune(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
                                           a0, dt, t, ctypes.byref(ms), _stream()))
         return (t[0], t[1], t[2]), ms.value
+
+    def autotune_sweeps(self, u_n, u_nm1, dt, dt_prev=0.0):
+        """Pick the fastest smoother sweep schedule for one implicit step."""
+        nu = (ctypes.c_int * 3)()
+        ms = ctypes.c_double()
+        self._check(self.lib.nrd_autotune_sweeps(self._h, _ptr(u_n, torch.float64),
+                                                 _ptr(u_nm1, torch.float64), dt, dt_prev, nu,
+                                                 ctypes.byref(ms), _stream()))
+        self.params.nu1, self.params.nu2, self.params.coarse_sweeps = nu[0], nu[1], nu[2]
+        return (nu[0], nu[1], nu[2]), ms.value
 
     def time_derivative(self, u_np1, u_n, u_nm1, dt, dt_prev=0.0, out=None):
         out = torch.empty_like(u_n) if out is None else out

@@ -339,3 +339,18 @@ def test_autotune_keeps_parity(nrd):
     F = ctx.residual(dev(u), dev(u), 1.0, 2e-3).cpu().numpy()
     S = o.residual_scale(u, u.copy(), 1.0, 2e-3)
     assert np.all(np.abs(F - o.residual(u, u.copy(), 1.0, 2e-3)) <= 1e-12 * S + 1e-300)
+
+
+def test_sweep_autotuner_keeps_solution(nrd):
+    h, z = CASES["amr2_16"]()
+    ctx, o = make(nrd, h, z, pc_precision=1, nmg=3, jv_mode=nrd.JV_ANALYTIC, rtol=1e-10)
+    o.set_solver(nmg=3, jv_mode=O_AN, rtol=1e-10)
+    u0 = W.front_state(h, seed=9, noise=0.0, front=0.1, width=0.05)
+    nu, ms = ctx.autotune_sweeps(dev(u0), None, 1e-3)
+    assert nu in [(1, 0, 2), (1, 1, 2), (2, 1, 3), (2, 2, 4), (3, 3, 6)] and ms > 0
+    u = dev(u0)
+    st = ctx.step(u, dev(u0), None, 1e-3)
+    uo, sto = o.newton(u0.copy(), u0.copy(), 1.0, 1e-3)
+    leaf = np.concatenate([o.leaf_mask()] * 2)
+    rel = np.abs(u.cpu().numpy() - uo)[leaf].max() / np.abs(uo[leaf]).max()
+    assert st["status"] == 0 and rel <= 1e-8
