@@ -41,7 +41,7 @@ WORKLOAD = "amr2_base64_marshak_band"
 LIN_FLOPS_PER_CELL = 3 * 86.8 + 48.4
 # DRAM bytes per launch of that kernel from the committed ncu capture of the
 # same kernel version, or None when the kernel changed since.
-LIN_TRAFFIC_BYTES = 103.7e6
+LIN_TRAFFIC_BYTES = None
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-regrid", action="store_true", help="skip the regrid/transfer leg")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profilers: 1 warm-up + 2 production steps, fixed "
                          "8x8x8 tiles, no plain/CPU/e2e legs")
@@ -187,7 +188,7 @@ def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
     kt = ctx.timing_read() if timing else None
     if timing:
         ctx.timing_enable(False)
-    return dict(ms=times, krylov=kry, newton=newt, kernel=kt, u=un, tags=tags)
+    return dict(ms=times, krylov=kry, newton=newt, kernel=kt, u=un, u_prev=unm1, tags=tags)
 
 
 def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
@@ -228,6 +229,56 @@ def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
         hnm1 = hn.clone()
         hn = hout.clone()
     return total, kry, h2d, d2h
+
+
+def regrid_leg(nrd, ctx, torch, h, z, r):
+    """One regrid of the benchmark state (Sec. 5), outside the timed steps:
+    device tags, host Berger-Rigoutsos clustering, conservative transfer of
+    u_n and u_{n-1} to the new hierarchy, and the warm-restart re-solve."""
+    from paper_1302_6303_gb300 import workloads as W
+    u = r["u"]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    tags = ctx.tag(u, thr_r=0.1)
+    e1.record()
+    torch.cuda.synchronize()
+    tag_ms = e0.elapsed_time(e1)
+    t0 = time.perf_counter()
+    levels = ctx.regrid_boxes(tags, tag_bits=4, buffer=1, efficiency=0.7, min_side=16,
+                              max_side=32, max_levels=2)
+    cluster_ms = (time.perf_counter() - t0) * 1e3
+    nh = W.Hierarchy(n0=h.n0, levels=levels, bc_type=h.bc_type, bc_R=h.bc_R)
+    _, cubes = W.config_amr2_cubes(h.n0[0], seed=0)
+    cn = make_ctx(nrd, nh, W.material_from_cubes(nh, cubes), torch, production=True)
+    cn.set_params(tile_x=ctx.params.tile_x, tile_y=ctx.params.tile_y, tile_z=ctx.params.tile_z,
+                  nu1=ctx.params.nu1, nu2=ctx.params.nu2, coarse_sweeps=ctx.params.coarse_sweeps)
+    hist = torch.stack([u, r["u_prev"]])
+    cn.timing_enable(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    moved = ctx.transfer_to(cn, hist)
+    transfer_ms = (time.perf_counter() - t0) * 1e3
+    k_ms, _ = cn.timing_read()["transfer"]
+    cn.timing_enable(False)
+    No, Nn, nvec = ctx.N, cn.N, 2
+    alg = 2 * 16 * nvec * No + 40 * Nn + 2 * 16 * nvec * Nn
+    # warm restart: the last step solved again (backward-Euler form from the
+    # transferred u_{n-1}) from the transferred u_n
+    un = moved[0].contiguous()
+    e0.record()
+    st = cn.step(un, moved[1].contiguous(), None, DT)
+    e1.record()
+    torch.cuda.synchronize()
+    return {"tag_ms": tag_ms, "cluster_ms_host": cluster_ms, "boxes": [len(l) for l in levels],
+            "leaf_cells_new": cn.nleaf, "transfer_ms_total": transfer_ms,
+            "transfer_kernel_ms": k_ms, "transfer_vectors": nvec,
+            "transfer_gbs": alg / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None,
+            "transfer_bytes": "copy of the old vectors (read+write) + 40 B descriptor + one "
+                              "read and one write per new value",
+            "resolve_ms": e0.elapsed_time(e1), "resolve_newton": st["newton_its"],
+            "resolve_krylov": st["krylov_its"], "fnorm_after_transfer": st["fnorm0"],
+            "fnorm_resolved": st["fnorm"]}
 
 
 def cpu_baseline(h, z, u0, leaf):
@@ -385,6 +436,10 @@ def main():
     e2e = {"value": world * leaf * e_kry / (e_ms * 1e-3) / 1e6, "unit": "Mcell/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    regrid = None
+    if not args.no_regrid:
+        regrid = regrid_leg(nrd, ctx, torch, h, z, r)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(h, z, u0, leaf)
@@ -411,6 +466,7 @@ def main():
         "speedup_vs_plain": (plain["ms_per_step"] / (tot_ms / args.steps)) if plain else None,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "regrid": regrid,
         "clocks": clocks,
         "gpu_launches": launches,
         "gpu_launches_note": "instrumented launch groups in the timed region",

@@ -12,8 +12,12 @@
  *   - the physics-based preconditioner P = P1 P2 of Sec. 4.2 with FAC
  *     V-cycles (Sec. 4.3, Algorithm 1) on the diffusion blocks;
  *   - right-preconditioned GMRES inside an inexact Newton solve (Sec. 4.1);
- *   - a BE / BDF2 implicit time step (Sec. 3.3);
- *   - the refinement indicators of Sec. 5.
+ *   - a BE / BDF2 implicit time step (Sec. 3.3) and the pieces of adaptive
+ *     step control (Sec. 3.4-3.5: predictor, local error, controllers);
+ *   - the refinement indicators, Berger-Rigoutsos clustering and the
+ *     conservative linear transfer between hierarchies of Sec. 5;
+ *   - the transposed Jacobian and adjoint solve of one implicit step
+ *     (gradients through time steps).
  *
  * Conventions
  *   - Every call returns an int status: NRD_OK (0) or a negative NRD_E* code;
@@ -261,6 +265,51 @@ int nrd_step(nrd_ctx* ctx, double* u, const double* u_n, const double* u_nm1, do
 int nrd_tag(nrd_ctx* ctx, const double* u, double thr_c, double thr_g, double thr_r,
             uint8_t* tags, cudaStream_t stream);
 
+/* ------------------------------------------------------- regridding (Sec. 5)
+ * Berger-Rigoutsos clustering of tagged cells into the boxes of a new
+ * hierarchy on the same base grid (host C++; the paper names the algorithm
+ * but gives no parameters).  Level by level from the coarsest, cells of the
+ * new level l whose tag byte has a bit of tag_bits (cells absent from the
+ * current level l inherit the tag of the finest current cell holding them)
+ * are dilated by `buffer` cells, kept where the finer level is properly
+ * nested (the cell's 26 neighbours inside the domain lie in the new level l),
+ * and clustered: a box is shrunk to its tags and accepted when
+ * tags/volume >= efficiency, it is properly nested and no side exceeds
+ * max_side/2; otherwise it is cut at a zero of a tag signature (nearest the
+ * middle, longest axis first), else at the strongest inflection of the
+ * signatures, else in the middle of its longest side, each part keeping at
+ * least min_side/2 planes unless proper nesting forces a narrower cut.  The
+ * accepted boxes refined by 2 form level l+1.
+ *   tags: device, ncells bytes (nrd_tag's output);  min_side, max_side: even,
+ *   2 <= min_side <= max_side, in cells of the new level;  max_levels: 1 ..
+ *   NRD_MAX_LEVELS, levels of the new hierarchy at most;  out (host):
+ *   *nlevels_out levels, nboxes_out[max_levels] boxes per level (0 past the
+ *   last), boxes_out[6*max_boxes] inclusive lo/hi per box in layout order
+ *   (level 0 is the base box), *total_out the total box count (also set when
+ *   it exceeds max_boxes, which returns NRD_EINVAL).  Synchronises. */
+int nrd_regrid_boxes(nrd_ctx* ctx, const uint8_t* tags, int tag_bits, int buffer,
+                     double efficiency, int min_side, int max_side, int max_levels,
+                     int max_boxes, int* nlevels_out, int* nboxes_out, int* boxes_out,
+                     int* total_out);
+
+/* Conservative linear refinement of Sec. 5: moves nvec state vectors from the
+ * hierarchy of ctx_src to that of ctx_dst (same base grid).  The old vectors
+ * are made composite first (covered cells := mean of their 8 children, on a
+ * private copy: u_src is not modified).  A new cell that exists on the same
+ * old level copies it; any other new cell takes, at its centre, the
+ * minmod-limited linear reconstruction of the finest old cell holding it
+ * (slope 0 along an axis where an old neighbour on that level is missing), so
+ * leaf sums of V u are conserved and no value leaves the range of the old
+ * neighbours (E, T stay positive).
+ *   u_src: device, nvec x 2*ncells(src) doubles;  u_dst: device,
+ *   nvec x 2*ncells(dst) doubles (every cell written).  Allocates and frees a
+ *   descriptor of 40 bytes per new cell and a copy of u_src.  Synchronises.
+ * Errors: NRD_ESTATE (a context without hierarchy), NRD_EINVAL (different
+ * base grids, null pointers, nvec < 1), NRD_ENOMEM, NRD_ECUDA; the message is
+ * stored in ctx_dst. */
+int nrd_transfer(nrd_ctx* ctx_src, nrd_ctx* ctx_dst, const double* u_src, double* u_dst,
+                 int nvec, cudaStream_t stream);
+
 /* Tile-shape autotuner: times the linearisation stencil, one frozen-Jacobian
  * Jv and one preconditioner application at the state u for every supported
  * tile shape (3 repetitions each, CUDA events, after one warm-up) and keeps
@@ -351,7 +400,8 @@ enum {
   NRD_TK_PC_SETUP = 4,   /* coefficient freeze and coarsening */
   NRD_TK_ORTHO = 5,      /* CGS2 orthogonalisation of one Krylov vector */
   NRD_TK_GHOST = 6,      /* ghost fill of a direction vector */
-  NRD_TK_COUNT = 7
+  NRD_TK_TRANSFER = 7,   /* regrid transfer: composite copy + gather (ctx_dst) */
+  NRD_TK_COUNT = 8
 };
 int nrd_timing_enable(nrd_ctx* ctx, int enable);
 int nrd_timing_read(nrd_ctx* ctx, int group, double* ms_host, int64_t* launches_host);

@@ -26,13 +26,13 @@ EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
-    "nrd_step", "nrd_tag", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
+    "nrd_step", "nrd_tag", "nrd_regrid_boxes", "nrd_transfer", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
     "nrd_autotune", "nrd_autotune_sweeps", "nrd_wdot_noalloc", "nrd_measure_peaks",
     "nrd_timing_enable",
     "nrd_timing_read",
 ]
-TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST = range(7)
-TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost"]
+TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST, TK_TRANSFER = range(8)
+TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost", "transfer"]
 
 
 class Params(ctypes.Structure):
@@ -100,6 +100,9 @@ def load(path: str = _LIBPATH):
         "nrd_newton": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
+        "nrd_regrid_boxes": (c_int, [vp, vp, c_int, c_int, c_dbl, c_int, c_int, c_int, c_int,
+                                     P(c_int), P(c_int), P(c_int), P(c_int)]),
+        "nrd_transfer": (c_int, [vp, vp, dp, dp, c_int, vp]),
         "nrd_autotune": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
         "nrd_autotune_sweeps": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(c_int), P(c_dbl), vp]),
         "nrd_time_derivative": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, dp, vp]),
@@ -186,7 +189,7 @@ class Context:
         if rc != OK:
             raise NrdError(rc, "nrd_create failed (bad parameters?)")
         self._h = h
-        self.N = self.G = self.nleaf = 0
+        self.N = self.G = self.nleaf = self.nlevels = 0
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -219,6 +222,7 @@ class Context:
         n, g, lf = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._check(self.lib.nrd_layout(self._h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(lf)))
         self.N, self.G, self.nleaf = n.value, g.value, lf.value
+        self.nlevels = len(nboxes)
 
     def set_hierarchy_from(self, hier):
         self.set_hierarchy(hier.nboxes, hier.boxes_flat(), hier.bc_type, hier.bc_R)
@@ -316,6 +320,7 @@ class Context:
         ms = ctypes.c_double()
         self._check(self.lib.nrd_autotune(self._h, _ptr(u, torch.float64), _ptr(b, torch.float64),
                                           a0, dt, t, ctypes.byref(ms), _stream()))
+        self.params.tile_x, self.params.tile_y, self.params.tile_z = t[0], t[1], t[2]
         return (t[0], t[1], t[2]), ms.value
 
     def autotune_sweeps(self, u_n, u_nm1, dt, dt_prev=0.0):
@@ -365,3 +370,37 @@ class Context:
         self._check(self.lib.nrd_tag(self._h, _ptr(u, torch.float64), thr_c, thr_g, thr_r,
                                      _ptr(t, torch.uint8), _stream()))
         return t
+
+    def regrid_boxes(self, tags, tag_bits=1, buffer=1, efficiency=0.7, min_side=4, max_side=32,
+                     max_levels=None, max_boxes=4096):
+        """Berger-Rigoutsos boxes of a new hierarchy from device tags
+        (nrd_regrid_boxes); returns levels[l] = [(lo, hi), ...]."""
+        if max_levels is None:
+            max_levels = self.nlevels
+        nl, tot = ctypes.c_int(), ctypes.c_int()
+        nb = (ctypes.c_int * max_levels)()
+        bx = (ctypes.c_int * (6 * max_boxes))()
+        self._check(self.lib.nrd_regrid_boxes(self._h, _ptr(tags, torch.uint8), tag_bits, buffer,
+                                              efficiency, min_side, max_side, max_levels,
+                                              max_boxes, ctypes.byref(nl), nb, bx,
+                                              ctypes.byref(tot)))
+        out, q = [], 0
+        for l in range(nl.value):
+            lev = []
+            for _ in range(nb[l]):
+                lev.append((tuple(bx[6 * q:6 * q + 3]), tuple(bx[6 * q + 3:6 * q + 6])))
+                q += 1
+            out.append(lev)
+        return out
+
+    def transfer_to(self, dst: "Context", u):
+        """Conservative limited-linear transfer (nrd_transfer) of one state
+        vector or a stack of them (shape (nvec, 2N)) to dst's hierarchy."""
+        stacked = u.dim() == 2
+        uu = u.contiguous() if stacked else u.reshape(1, -1).contiguous()
+        nvec = uu.shape[0]
+        out = torch.empty(nvec, 2 * dst.N, dtype=torch.float64, device=u.device)
+        rc = self.lib.nrd_transfer(self._h, dst._h, _ptr(uu, torch.float64),
+                                   _ptr(out, torch.float64), nvec, _stream())
+        dst._check(rc)
+        return out if stacked else out[0]

@@ -254,10 +254,9 @@ def config_256(n=256, seed=0):
     return h, material_from_cubes(h, cubes)
 
 
-def config_amr2(n0=64, seed=0, band=8, ncubes=20):
-    """Two levels, base n0^3, ratio 2: the fine level tiles the Marshak band
-    x in [0, band) base cells with patches of 16^3-32^3 fine cells; z = 10 in
-    `ncubes` seeded cubes of side 4-12 base cells on z = 1."""
+def config_amr2_cubes(n0=64, seed=0, band=8, ncubes=20):
+    """Hierarchy and material cubes of `config_amr2` (the cubes re-evaluate
+    the same material on any other hierarchy of the same base grid)."""
     rng = np.random.default_rng(seed)
     fine_lo = (0, 0, 0)
     fine_hi = (2 * band - 1, 2 * n0 - 1, 2 * n0 - 1)
@@ -266,6 +265,14 @@ def config_amr2(n0=64, seed=0, band=8, ncubes=20):
     h = Hierarchy((n0, n0, n0), [[((0, 0, 0), (n0 - 1,) * 3)], boxes])
     s_lo, s_hi = max(1, 4 * n0 // 64), max(1, 12 * n0 // 64)
     cubes = random_cubes(rng, h.n0, ncubes, s_lo, s_hi)
+    return h, cubes
+
+
+def config_amr2(n0=64, seed=0, band=8, ncubes=20):
+    """Two levels, base n0^3, ratio 2: the fine level tiles the Marshak band
+    x in [0, band) base cells with patches of 16^3-32^3 fine cells; z = 10 in
+    `ncubes` seeded cubes of side 4-12 base cells on z = 1."""
+    h, cubes = config_amr2_cubes(n0, seed, band, ncubes)
     return h, material_from_cubes(h, cubes)
 
 
