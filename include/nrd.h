@@ -113,6 +113,13 @@ typedef struct {
   int tile_x, tile_y, tile_z;  /* stencil tile shape (0,0,0: 32 x 4 x 4); one of
                                   32x4x4, 32x8x4, 32x4x8, 32x2x4, 16x8x4, 16x4x8,
                                   16x8x8, 16x4x4, 8x8x8 */
+  int graph;           /* 1 (default): with NRD_JV_ANALYTIC, nrd_newton / nrd_step run
+                          the whole Newton solve as one CUDA graph whose Newton,
+                          GMRES-cycle and Arnoldi loops are conditional graph nodes
+                          driven by device-side tests (one read-back per solve);
+                          0: host-driven loop, one read-back per Krylov iteration.
+                          The host-driven loop is also used while kernel timing is
+                          on.  Both give the same iterates up to rounding. */
 } nrd_params;
 
 /* Statistics of one Newton solve (nrd_newton / nrd_step). */
@@ -124,6 +131,9 @@ typedef struct {
   double fnorm0;       /* ||F(u0)|| (volume-weighted 2-norm over leaf cells) */
   double fnorm;        /* final ||F|| */
   double min_lambda;   /* smallest positivity damping factor used (Sec. 4.1) */
+  int64_t kernels;     /* graph form: kernel launches the solve executed (kernel nodes
+                          of each loop body times the iterations of that loop);
+                          host-driven form: 0 (not counted) */
 } nrd_stats;
 
 typedef struct nrd_ctx nrd_ctx;

@@ -15,7 +15,8 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libnrd.so")
 BUILD = os.path.join(HERE, "_build")
 UNITS = ["hier.cu", "k_stencil.cu", "k_blas.cu", "k_pc.cu", "solver.cu", "capi.cu",
-         "noalloc.cu", "peaks.cu", "k_vjp.cu", "k_time.cu", "regrid.cu"]
+         "noalloc.cu", "peaks.cu", "k_vjp.cu", "k_time.cu", "regrid.cu",
+         "nk_graph.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

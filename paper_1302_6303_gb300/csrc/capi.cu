@@ -43,6 +43,7 @@ int check_params(const nrd_params* p, std::string& err) {
   if (p->nmg < 1 || p->nmg > NRD_MAX_MG) { err = "nmg must be in [1, 12]"; return NRD_EINVAL; }
   if (!(p->rtol >= 0.0) || !(p->atol >= 0.0)) { err = "tolerances must be >= 0"; return NRD_EINVAL; }
   if (p->max_newton < 1) { err = "max_newton must be >= 1"; return NRD_EINVAL; }
+  if (p->graph != 0 && p->graph != 1) { err = "graph must be 0 or 1"; return NRD_EINVAL; }
   bool ok = (p->tile_x == 0 && p->tile_y == 0 && p->tile_z == 0);
   for (int t = 0; t < kNumShapes && !ok; t++)
     ok = (p->tile_x == kShapes[t][0] && p->tile_y == kShapes[t][1] && p->tile_z == kShapes[t][2]);
@@ -95,7 +96,7 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
 }
 
 int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
-                  cudaStream_t s) {
+                  cudaStream_t s, const double* par) {
   Hier& H = c->H;
   launch_ghost_fill(H, c->mp, c->d_z, u, c->d_gu, 1, s);
   StencilIO io{};
@@ -110,13 +111,14 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.craw = pc_craw(c->pc);
   io.cc = c->d_cc;
   io.beta = dt / a0;
+  io.par = par;
   pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2);
   c->timer.begin(NRD_TK_RESIDUAL, s);
   launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s);
   c->timer.end(NRD_TK_RESIDUAL, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
   c->timer.begin(NRD_TK_PC_SETUP, s);
-  int rc = pc_finish(c->pc, H, u, c->d_z, a0, dt, true, s);
+  int rc = pc_finish(c->pc, H, u, c->d_z, a0, dt, true, s, par != nullptr);
   c->timer.end(NRD_TK_PC_SETUP, s);
   if (rc != NRD_OK) return fail(c, rc, "preconditioner set-up failed");
   c->lin_ready = true;
@@ -125,7 +127,8 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
 }
 
 int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const double* F0,
-           double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s) {
+           double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s,
+           const double* par) {
   Hier& H = c->H;
   if (mode == NRD_JV_FROZEN) {
     c->timer.begin(NRD_TK_GHOST, s);
@@ -136,6 +139,7 @@ int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const 
     io.gv = c->d_gv;
     io.a0 = a0;
     io.dt = dt;
+    io.par = par;
     io.out = Jv;
     io.cfflux = c->d_cf;
     c->timer.begin(NRD_TK_JV, s);
@@ -199,6 +203,7 @@ int nrd_params_default(nrd_params* p) {
   p->tile_x = 0;
   p->tile_y = 0;
   p->tile_z = 0;
+  p->graph = 1;
   return NRD_OK;
 }
 
@@ -240,6 +245,7 @@ int nrd_set_params(nrd_ctx* c, const nrd_params* p) {
   bool repc = (p->nmg != c->p.nmg || p->pc_precision != c->p.pc_precision ||
                p->restart != c->p.restart);
   c->p = *p;
+  c->gen++;
   set_model(c);
   if (c->pc) pc_set_sweeps(c->pc, p->nu1, p->nu2, p->coarse_sweeps);
   if (c->have_hier && retile) {
@@ -534,6 +540,7 @@ int nrd_autotune(nrd_ctx* c, const double* u, const double* b, double a0, double
     H.tile_x = kShapes[t][0];
     H.tile_y = kShapes[t][1];
     H.tile_z = kShapes[t][2];
+    c->gen++;
     if (hier_tiles(H, err) != NRD_OK) continue;
     pc_drop_graphs(c->pc);
     float ms = 0.0f;
@@ -563,6 +570,7 @@ int nrd_autotune(nrd_ctx* c, const double* u, const double* b, double a0, double
   H.tile_x = c->p.tile_x = kShapes[best][0];
   H.tile_y = c->p.tile_y = kShapes[best][1];
   H.tile_z = c->p.tile_z = kShapes[best][2];
+  c->gen++;
   if (hier_tiles(H, err) != NRD_OK) return fail(c, NRD_ECUDA, err);
   pc_drop_graphs(c->pc);
   c->lin_ready = false;
@@ -598,6 +606,7 @@ int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, doub
     c->p.nu2 = cand[q][1];
     c->p.coarse_sweeps = cand[q][2];
     pc_set_sweeps(c->pc, cand[q][0], cand[q][1], cand[q][2]);
+    c->gen++;
     float ms = 0.0f;
     bool ok = true;
     for (int rep = 0; rep < 2; rep++) {
@@ -623,6 +632,7 @@ int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, doub
   c->p.nu2 = cand[best][1];
   c->p.coarse_sweeps = cand[best][2];
   pc_set_sweeps(c->pc, cand[best][0], cand[best][1], cand[best][2]);
+  c->gen++;
   if (nu_out) {
     nu_out[0] = cand[best][0];
     nu_out[1] = cand[best][1];

@@ -242,6 +242,80 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
+// ---- variants whose vector count is a device value (graph-captured solves)
+
+// res[q] = <w, V_q>, q < *jd + add, in groups of 4 vectors (w re-read per
+// group); the per-thread and block summation orders are those of k_mdot.
+__global__ void k_mdot_dyn(const float* __restrict__ wv, const double* __restrict__ w,
+                           const double* __restrict__ V, long stride, int N, const int* jd,
+                           int add, double* part) {
+  __shared__ double sh[32];
+  const int nv = min(*jd + add, NVMAX);
+  for (int q0 = 0; q0 < nv; q0 += 4) {
+    const int nq = min(4, nv - q0);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const double* Vq = V + (long)q0 * stride;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+      double vol = (double)wv[i];
+      double wE = vol * w[i], wT = vol * w[N + i];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (q < nq) acc[q] += wE * Vq[q * stride + i] + wT * Vq[q * stride + N + i];
+    }
+    for (int q = 0; q < nq; q++) {
+      double r = block_red<0>(acc[q], sh);
+      if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + q0 + q] = r;
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void k_finish_dyn(const double* part, int nblk, const int* jd, int add, double* res,
+                             int slot) {
+  __shared__ double sh[32];
+  const int nq = min(*jd + add, NVMAX);
+  for (int q = 0; q < nq; q++) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[(long)b * NVMAX + q];
+    double r = block_red<0>(acc, sh);
+    if (threadIdx.x == 0) res[slot + q] = r;
+    __syncthreads();
+  }
+}
+
+__global__ void k_mupdate_dyn(int n2, double* __restrict__ w, const double* __restrict__ V,
+                              long stride, const int* jd, int add, const double* __restrict__ h) {
+  __shared__ double hs[NVMAX];
+  const int nv = min(*jd + add, NVMAX);
+  if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
+    double s = w[i];
+    for (int q = 0; q < nv; q++) s -= hs[q] * V[q * stride + i];
+    w[i] = s;
+  }
+}
+
+__global__ void k_lincomb_dyn(int n, double* __restrict__ x, const double* __restrict__ Z,
+                              long stride, const int* jd, const double* __restrict__ y) {
+  __shared__ double ys[NVMAX];
+  const int nv = min(*jd, NVMAX);
+  if (threadIdx.x < nv) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double s = x[i];
+    for (int q = 0; q < nv; q++) s += ys[q] * Z[q * stride + i];
+    x[i] = s;
+  }
+}
+
+__global__ void k_axpy_dev(int n, const double* __restrict__ a, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  const double av = *a;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    y[i] += av * x[i];
+}
+
 int grid_for(long n) {
   long b = (n + RB - 1) / RB;
   return (int)std::max(1L, std::min(b, (long)152 * 8));
@@ -315,4 +389,24 @@ void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v,
                     cudaStream_t s) {
   k_poscap<<<R.nblk, RB, 0, s>>>(H.d_mask, u, v, H.N, R.d_part);
   k_finish<1><<<1, 1024, 0, s>>>(R.d_part, R.nblk, 1, R.d_res, slot);
+}
+
+void launch_mdot_dyn(const Hier& H, Reducer& R, const double* w, const double* V, long stride,
+                     const int* jd, int add, int slot, cudaStream_t s) {
+  k_mdot_dyn<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, H.N, jd, add, R.d_part);
+  k_finish_dyn<<<1, 1024, 0, s>>>(R.d_part, R.nblk, jd, add, R.d_res, slot);
+}
+
+void launch_mupdate_dyn(int n2, double* w, const double* V, long stride, const int* jd, int add,
+                        const double* h, cudaStream_t s) {
+  k_mupdate_dyn<<<grid_for(n2), RB, 0, s>>>(n2, w, V, stride, jd, add, h);
+}
+
+void launch_lincomb_dyn(int n, double* x, const double* Z, long stride, const int* jd,
+                        const double* y, cudaStream_t s) {
+  k_lincomb_dyn<<<grid_for(n), RB, 0, s>>>(n, x, Z, stride, jd, y);
+}
+
+void launch_axpy_dev(int n, const double* a, const double* x, double* y, cudaStream_t s) {
+  k_axpy_dev<<<grid_for(n), RB, 0, s>>>(n, a, x, y);
 }

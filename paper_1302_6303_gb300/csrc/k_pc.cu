@@ -428,12 +428,20 @@ __global__ void k_p2_setup(const uint8_t* mask, int N, const double* Tk, const f
 
 // y = P2^{-1} z per leaf cell (Sec. 4.2); covered cells get 0
 template <class P>
-__global__ void k_p2(int N, const P* zin, const double* p, double* y) {
+__global__ void k_p2(int N, const P* zin, const double* p, double* y, const int* jd, long jstride,
+                     double* y2) {
+  if (jd) y += (long)(*jd) * jstride;   // y = column *jd of a basis (device index)
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
     double sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
     double zE = (double)zin[c], zT = (double)zin[N + c];
-    y[c] = ((1.0 + sbt) * zE + sbt * zT) * rd;
-    y[N + c] = ((1.0 + sb) * zT + sb * zE) * rd;
+    double yE = ((1.0 + sbt) * zE + sbt * zT) * rd;
+    double yT = ((1.0 + sb) * zT + sb * zE) * rd;
+    y[c] = yE;
+    y[N + c] = yT;
+    if (y2) {
+      y2[c] = yE;
+      y2[N + c] = yT;
+    }
   }
 }
 
@@ -460,7 +468,8 @@ __global__ void k_out_cast(const uint8_t* mask, int N, const P* u, double* y) {
 }
 
 template <class P>
-__global__ void k_cast(int n, const double* w, P* out) {
+__global__ void k_cast(int n, const double* w, P* out, const int* jd, long jstride) {
+  if (jd) w += (long)(*jd) * jstride;   // w = column *jd of a basis (device index)
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     out[i] = (P)w[i];
 }
@@ -560,8 +569,9 @@ __global__ void k_coef(SetupArgs a) {
 // with A non-null also the scaled coefficient of the target (level l)
 template <class P>
 __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, int N,
-                               const uint8_t* gtype, const uint8_t* gface, double beta,
-                               LevelHP lh, int lvl, double* Craw, P* A) {
+                               const uint8_t* gtype, const uint8_t* gface,
+                               const double* dbeta, LevelHP lh, int lvl, double* Craw, P* A) {
+  const double beta = *dbeta;
   const int fld = blockIdx.y;
   double* C = Craw + fld * AF;
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -685,8 +695,9 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
 }
 
 template <class P>
-__global__ void k_box_scale(BoxRaw B, const double* Craw, const int* gtype_box, double beta,
-                            double hx, double hy, double hz, P* A) {
+__global__ void k_box_scale(BoxRaw B, const double* Craw, const int* gtype_box,
+                            const double* dbeta, double hx, double hy, double hz, P* A) {
+  const double beta = *dbeta;
   const int fld = blockIdx.y;
   const double* C = Craw + fld * B.AF;
   P* Af = A + fld * B.AF;
@@ -910,14 +921,17 @@ void zero_level(PcState* ps, const Hier& H, int l, cudaStream_t s) {
                     (size_t)Lv.ncell * sizeof(P), s);
 }
 
+// y = P^{-1} w.  With jd non-null (forward only) w and y are bases of
+// columns jstride apart and the column *jd (a device index) is used; y2, if
+// non-null, receives a second copy of the result.
 template <class P>
 int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transposed,
-            cudaStream_t s) {
+            cudaStream_t s, const int* jd = nullptr, long jstride = 0, double* y2 = nullptr) {
   const long n2 = 2L * H.N;
   if (transposed)
     k_p2t_cast<P><<<g1(H.N), BS, 0, s>>>(H.N, w, ps->p2, (P*)ps->ff);
   else
-    k_cast<P><<<g1(n2), BS, 0, s>>>((int)n2, w, (P*)ps->ff);
+    k_cast<P><<<g1(n2), BS, 0, s>>>((int)n2, w, (P*)ps->ff, jd, jstride);
   cudaMemsetAsync(ps->fu, 0, n2 * sizeof(P), s);
   // r = f (u = 0); covered := mean of children
   cudaMemcpyAsync(ps->fr, ps->ff, n2 * sizeof(P), cudaMemcpyDeviceToDevice, s);
@@ -944,7 +958,7 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
   if (transposed)
     k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y);
   else
-    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, ps->p2, y);
+    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, ps->p2, y, jd, jstride, y2);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }
 
@@ -961,7 +975,7 @@ void scale_boxes(PcState* ps, cudaStream_t s) {
     const BoxRaw& B = ps->box[m];
     long nc = (long)B.n[0] * B.n[1] * B.n[2];
     dim3 g(g1(nc), 2);
-    k_box_scale<P><<<g, BS, 0, s>>>(B, ps->bCraw[m], ps->bgt, ps->beta, ps->bh[m][0],
+    k_box_scale<P><<<g, BS, 0, s>>>(B, ps->bCraw[m], ps->bgt, ps->d_beta, ps->bh[m][0],
                                     ps->bh[m][1], ps->bh[m][2], (P*)ps->bA[m]);
   }
 }
@@ -1098,11 +1112,14 @@ void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2) {
 }
 
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
-              bool from_lin, cudaStream_t s) {
+              bool from_lin, cudaStream_t s, bool beta_on_device) {
   ps->beta = dt / a0;
   if (ps->z != z) pc_drop_graphs(ps);
   ps->z = z;
-  cudaMemcpyAsync(ps->d_beta, &ps->beta, sizeof(double), cudaMemcpyHostToDevice, s);
+  // beta = dt / a0 for the set-up kernels; a graph-captured solve writes it
+  // to the device itself before the launch
+  if (!beta_on_device)
+    cudaMemcpyAsync(ps->d_beta, &ps->beta, sizeof(double), cudaMemcpyHostToDevice, s);
   SetupArgs a = setup_args(ps, H, nullptr, u, nullptr, z, nullptr);
   if (!from_lin) {
     cudaMemcpyAsync(ps->Tk, u + H.N, (size_t)H.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
@@ -1113,15 +1130,15 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
     dim3 g(g1(H.ncz[l]), 2);
     if (from_lin && ps->prec == NRD_PC_F32)
       k_coef_coarsen<float><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
-                                             H.d_gtype, H.d_gface, ps->beta, a.lh, l, ps->Craw,
+                                             H.d_gtype, H.d_gface, ps->d_beta, a.lh, l, ps->Craw,
                                              (float*)ps->A);
     else if (from_lin)
       k_coef_coarsen<double><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
-                                              H.d_gtype, H.d_gface, ps->beta, a.lh, l, ps->Craw,
+                                              H.d_gtype, H.d_gface, ps->d_beta, a.lh, l, ps->Craw,
                                               (double*)ps->A);
     else
       k_coef_coarsen<float><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
-                                             H.d_gtype, H.d_gface, ps->beta, a.lh, l, ps->Craw,
+                                             H.d_gtype, H.d_gface, ps->d_beta, a.lh, l, ps->Craw,
                                              (float*)nullptr);
   }
   // GMG levels
@@ -1151,6 +1168,15 @@ int pc_setup(PcState* ps, const Hier& H, const ModelParams& mp, const double* u,
   k_coef<<<std::min(nt, 152 * 8), BS, 0, s>>>(a);
   return pc_finish(ps, H, u, z, a0, dt, false, s);
 }
+
+int pc_apply_indexed(PcState* ps, const Hier& H, const double* V, double* Z, const int* jd,
+                     long jstride, double* zcopy, cudaStream_t s) {
+  if (ps->prec == NRD_PC_F32)
+    return apply_t<float>(ps, H, V, Z, false, s, jd, jstride, zcopy);
+  return apply_t<double>(ps, H, V, Z, false, s, jd, jstride, zcopy);
+}
+
+double* pc_beta_device(PcState* ps) { return ps->d_beta; }
 
 static int apply_any(PcState* ps, const Hier& H, const double* w, double* y, bool tr,
                      cudaStream_t s) {

@@ -239,6 +239,13 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   const int N = A.N, G = A.G;
   const long NS = 3L * N + G;                  // face slots per coefficient array
   const StencilIO& io = A.io;
+  // a0, dt, beta: kernel arguments, or device values (graph-captured solves)
+  double a0v = io.a0, dtv = io.dt, betav = io.beta;
+  if (io.par) {
+    a0v = io.par[0];
+    dtv = io.par[1];
+    betav = io.par[2];
+  }
   double eps = 0.0, reps = 0.0;
   if (MODE == ST_FD) {
     eps = *io.eps;
@@ -388,7 +395,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[5 * NS + fslot] = (double)s * m * h * rq * rq * Db / zc;  // d Phi / d z_c^3
           io.craw[fslot] = Db;
           io.craw[NS + fslot] = 0.0;
-          put_scaled(io, NS, fslot, io.beta * 2.0 * Db * rq / h, 0.0);
+          put_scaled(io, NS, fslot, betav * 2.0 * Db * rq / h, 0.0);
         }
         PT = 0.0;
       } else {
@@ -407,7 +414,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[5 * NS + fslot] = L.aZ;
           io.craw[fslot] = L.CE;
           io.craw[NS + fslot] = L.CT;
-          const double b2 = A.lh.bh2[lvl][dir];
+          const double rhd = A.lh.rh[lvl][dir];
+          const double b2 = io.par ? betav * rhd * rhd : A.lh.bh2[lvl][dir];
           put_scaled(io, NS, fslot, L.CE * b2, L.CT * b2);
         } else {
           flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, PE, PT);
@@ -461,28 +469,28 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         double sig = z * rT * rT * rT;
         double vE = svE[hc], vT = svT[hc];
         double dc = sig * ((T3 + 3.0 * E * rT) * vT - vE);
-        io.out[idx] = io.a0 * vE - io.dt * (divE + dc);
-        io.out[N + idx] = io.a0 * vT - io.dt * (divT - dc);
+        io.out[idx] = a0v * vE - dtv * (divE + dc);
+        io.out[N + idx] = a0v * vT - dtv * (divT - dc);
       } else if (MODE == ST_LIN) {
         double rT = 1.0 / T;
         double sig = z * rT * rT * rT;
         double cp = sig * (T2 * T2 - E);
-        io.out[idx] = io.a0 * E - io.b[idx] - io.dt * (divE + cp);
-        io.out[N + idx] = io.a0 * T - io.b[N + idx] - io.dt * (divT - cp);
+        io.out[idx] = a0v * E - io.b[idx] - dtv * (divE + cp);
+        io.out[N + idx] = a0v * T - io.b[N + idx] - dtv * (divT - cp);
         // coupling tangent dc = cE vE + cT vT
         io.cc[idx] = -sig;
         io.cc[N + idx] = sig * (T3 + 3.0 * E * rT);
         io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
         // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
-        double sb = sig * io.beta, sbt = sb * T3;
+        double sb = sig * betav, sbt = sb * T3;
         io.p2[idx] = sb;
         io.p2[N + idx] = sbt;
         io.p2[2L * N + idx] = 1.0 / ((1.0 + sb) * (1.0 + sbt) - sbt * sb);
       } else {
         double sig = z / T3;
         double cp = sig * (T2 * T2 - E);
-        double FE = io.a0 * E - io.b[idx] - io.dt * (divE + cp);
-        double FT = io.a0 * T - io.b[N + idx] - io.dt * (divT - cp);
+        double FE = a0v * E - io.b[idx] - dtv * (divE + cp);
+        double FT = a0v * T - io.b[N + idx] - dtv * (divT - cp);
         if (MODE == ST_FD) {
           FE = (FE - io.F0[idx]) * reps;
           FT = (FT - io.F0[N + idx]) * reps;
@@ -511,6 +519,7 @@ struct JfArgs {
   const double* v;    // [2][N]
   const double* gv;   // [2][G] ghosts of v
   double a0, dt;
+  const double* par;  // device a0, dt (or null: the values above)
   double* out;
   double* cfflux;
 };
@@ -518,6 +527,7 @@ struct JfArgs {
 __global__ void __launch_bounds__(256) k_jv_frozen(JfArgs a) {
   const int N = a.N, G = a.G;
   const long NS = 3L * N + G;
+  const double a0v = a.par ? a.par[0] : a.a0, dtv = a.par ? a.par[1] : a.dt;
   const int nc = a.tx * a.ty * a.tz;
   for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const TileDev tile = a.tiles[t];
@@ -585,8 +595,8 @@ __global__ void __launch_bounds__(256) k_jv_frozen(JfArgs a) {
         divT += (PTs[1] - PTs[0]) * rh;
       }
       const double dc = a.cc[idx] * vEc + a.cc[N + idx] * vTc;
-      a.out[idx] = a.a0 * vEc - a.dt * (divE + dc);
-      a.out[N + idx] = a.a0 * vTc - a.dt * (divT - dc);
+      a.out[idx] = a0v * vEc - dtv * (divE + dc);
+      a.out[N + idx] = a0v * vTc - dtv * (divT - dc);
     }
   }
 }
@@ -605,7 +615,9 @@ struct RfArgs {
 // fine fluxes stored by the fine-side stencil; scale = -dt (RESIDUAL, JV) or
 // -dt/eps (FD).
 __global__ void k_reflux(RfArgs a, const int* __restrict__ rf_level, const double* cf,
-                         double* out, double dt, const double* eps, int mode) {
+                         double* out, double dt, const double* par, const double* eps,
+                         int mode) {
+  if (par) dt = par[1];
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < a.nrf; r += gridDim.x * blockDim.x) {
     int c = a.cell[r];
     int lvl = rf_level[r];
@@ -809,7 +821,7 @@ void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s)
   a.G = H.G;
   a.lh = level_h(H);
   k_reflux<<<blocks_for(H.nrf, 128), 128, 0, s>>>(a, H.d_rf_level, io.cfflux, io.out, io.dt,
-                                                   io.eps, mode);
+                                                   io.par, io.eps, mode);
 }
 
 void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, const double* cc,
@@ -832,6 +844,7 @@ void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, co
   a.gv = io.gv;
   a.a0 = io.a0;
   a.dt = io.dt;
+  a.par = io.par;
   a.out = io.out;
   a.cfflux = io.cfflux;
   k_jv_frozen<<<std::min(a.ntiles, 152 * 8), 256, 0, s>>>(a);

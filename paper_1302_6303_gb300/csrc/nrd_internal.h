@@ -139,6 +139,7 @@ struct StencilIO {
   float* a32;           // [2][3N+G] scaled P1 coefficients (FP32 V-cycle), or
   double* a64;          //   the FP64 array when a32 is null
   double* p2;           // [3][N] P2 data
+  const double* par;    // device [a0, dt, beta] overriding a0, dt, beta (or null)
 };
 void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
                        double* g, int nonlinear, cudaStream_t s);
@@ -186,6 +187,14 @@ void launch_lincomb_dev(int n, double* x, const double* Z, long stride, int nv, 
 void launch_zero_covered(const Hier& H, double* x, cudaStream_t s);
 void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v, int slot,
                     cudaStream_t s);
+// vector counts *jd + add (device values) for graph-captured solves
+void launch_mdot_dyn(const Hier& H, Reducer& R, const double* w, const double* V, long stride,
+                     const int* jd, int add, int slot, cudaStream_t s);
+void launch_mupdate_dyn(int n2, double* w, const double* V, long stride, const int* jd, int add,
+                        const double* h, cudaStream_t s);
+void launch_lincomb_dyn(int n, double* x, const double* Z, long stride, const int* jd,
+                        const double* y, cudaStream_t s);
+void launch_axpy_dev(int n, const double* a, const double* x, double* y, cudaStream_t s);
 
 // Preconditioner (k_pc.cu)
 struct PcState;
@@ -203,7 +212,13 @@ void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw);
 // coarsen (and, unless the linearisation already did, scale) after the raw
 // coefficients were written at u
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
-              bool from_lin, cudaStream_t s);
+              bool from_lin, cudaStream_t s, bool beta_on_device = false);
+// P^{-1} applied to column *jd of the basis V (columns jstride apart) into
+// column *jd of Z, and into zcopy; jd is a device index (graph capture).
+int pc_apply_indexed(PcState* ps, const Hier& H, const double* V, double* Z, const int* jd,
+                     long jstride, double* zcopy, cudaStream_t s);
+// device copy of beta = dt / a0 read by the set-up kernels
+double* pc_beta_device(PcState* ps);
 // where the linearisation writes scaled coefficients and P2 data
 void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2);
 
@@ -280,6 +295,9 @@ struct nrd_ctx {
   double* d_r = nullptr;       // 2N
   double* d_b = nullptr;       // 2N
   double* d_small = nullptr;   // Hessenberg, rotations, g, y
+  // Newton solve captured as one CUDA graph (nk_graph.cu)
+  struct NkGraph* nk = nullptr;
+  unsigned gen = 0;            // bumped whenever captured state may change
   std::string err;
 };
 
@@ -290,10 +308,18 @@ int solver_alloc(nrd_ctx* c);
 int solver_adjoint(nrd_ctx* c, const double* g, double a0, double dt, double rtol, double* lam,
                    nrd_stats* st, cudaStream_t s);
 void solver_free(nrd_ctx* c);
+// nk_graph.cu: the whole Newton solve as one graph with device-side loops
+// (analytic Jv form, timing off).  Same contract as solver_newton.
+int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
+                   cudaStream_t s);
+void nk_graph_free(nrd_ctx* c);
 // capi.cu helpers used by the solver
 int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
                  bool fill_ghosts, cudaStream_t s);
+// par: optional device [a0, dt, beta] read by the kernels instead of a0, dt
+// (graph-captured solves; the frozen Jv and the linearisation only)
 int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const double* F0,
-           double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s);
+           double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s,
+           const double* par = nullptr);
 int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
-                  cudaStream_t s);
+                  cudaStream_t s, const double* par = nullptr);

@@ -129,7 +129,25 @@ int solver_alloc(nrd_ctx* c) {
   return NRD_OK;
 }
 
+static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0, double dt,
+                              nrd_stats* st, cudaStream_t s);
+
+int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
+                  cudaStream_t s) {
+  if (c->p.graph && c->p.jv_mode == NRD_JV_ANALYTIC && !c->timer.on && c->p.restart < 32) {
+    int rc = solver_alloc(c);
+    if (rc != NRD_OK) return rc;
+    // the graph reads the history from the context's own buffer
+    if (b != c->d_b)
+      cudaMemcpyAsync(c->d_b, b, 2 * (size_t)c->H.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                      s);
+    return nk_graph_solve(c, u, c->d_b, a0, dt, st, s);
+  }
+  return solver_newton_host(c, u, b, a0, dt, st, s);
+}
+
 void solver_free(nrd_ctx* c) {
+  nk_graph_free(c);
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(c->d_V); F(c->d_Z); F(c->d_F); F(c->d_dx); F(c->d_w); F(c->d_r); F(c->d_b); F(c->d_small);
   c->d_V = c->d_Z = c->d_F = c->d_dx = c->d_w = c->d_r = c->d_b = c->d_small = nullptr;
@@ -224,8 +242,11 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
   return (cudaGetLastError() == cudaSuccess) ? NRD_OK : NRD_ECUDA;
 }
 
-int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
-                  cudaStream_t s) {
+// Host-driven form: one read-back per Krylov iteration.  Used when the
+// graph form is off, for the finite-difference Jv, and while kernel timing
+// is recorded (event records cannot sit inside the graph's loops).
+static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0, double dt,
+                              nrd_stats* st, cudaStream_t s) {
   int rc = solver_alloc(c);
   if (rc != NRD_OK) return rc;
   Hier& H = c->H;

@@ -43,7 +43,7 @@ class Params(ctypes.Structure):
         ("nmg", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("rtol", ctypes.c_double),
         ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("eta_max", ctypes.c_double),
         ("ew_gamma", ctypes.c_double), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-        ("tile_z", ctypes.c_int),
+        ("tile_z", ctypes.c_int), ("graph", ctypes.c_int),
     ]
 
 
@@ -51,7 +51,7 @@ class Stats(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("newton_its", ctypes.c_int), ("krylov_its", ctypes.c_int),
         ("pc_setups", ctypes.c_int), ("fnorm0", ctypes.c_double), ("fnorm", ctypes.c_double),
-        ("min_lambda", ctypes.c_double),
+        ("min_lambda", ctypes.c_double), ("kernels", ctypes.c_int64),
     ]
 
     def as_dict(self):

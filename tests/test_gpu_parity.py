@@ -354,3 +354,68 @@ def test_sweep_autotuner_keeps_solution(nrd):
     leaf = np.concatenate([o.leaf_mask()] * 2)
     rel = np.abs(u.cpu().numpy() - uo)[leaf].max() / np.abs(uo[leaf]).max()
     assert st["status"] == 0 and rel <= 1e-8
+
+
+# ------------------------------------------------- graph-captured Newton solve
+def _graph_pair(nrd, h, z, **kw):
+    kw.setdefault("nmg", auto_nmg(h))
+    out = []
+    for g in (1, 0):
+        ctx = nrd.Context(graph=g, **kw)
+        ctx.set_hierarchy_from(h)
+        ctx.set_material(dev(z.astype(np.float32)))
+        out.append(ctx)
+    return out
+
+
+@pytest.mark.parametrize("name", ["tiny2", "tiny3", "amr2_16", "ragged"])
+def test_graph_newton_matches_host_loop(nrd, name):
+    """The whole Newton solve as one CUDA graph (device-side loops) gives the
+    host-driven loop's iterates: the same Newton / Krylov counts and the same
+    converged state (BE step, then a BDF2 step with another dt on the same
+    instantiated graph)."""
+    h, z = CASES[name]()
+    cg, ch = _graph_pair(nrd, h, z, rtol=1e-10, jv_mode=nrd.JV_ANALYTIC)
+    u0 = W.front_state(h, seed=9, noise=0.0, front=0.1, width=0.05)
+    leaf = np.concatenate([~h.covered_mask()] * 2)
+    res = []
+    for ctx in (cg, ch):
+        un = dev(u0)
+        u1 = un.clone()
+        s1 = ctx.step(u1, un, None, 1e-3)
+        u2 = u1.clone()
+        s2 = ctx.step(u2, u1, un, 7e-4, 1e-3)
+        res.append((u1.cpu().numpy(), u2.cpu().numpy(), s1, s2))
+    (g1, g2, gs1, gs2), (h1, h2, hs1, hs2) = res
+    for a, b in ((g1, h1), (g2, h2)):
+        rel = np.abs(a - b)[leaf].max() / np.abs(b[leaf]).max()
+        assert rel <= 1e-8, rel
+    for sg, sh in ((gs1, hs1), (gs2, hs2)):
+        assert sg["status"] == 0 and sh["status"] == 0
+        assert abs(sg["newton_its"] - sh["newton_its"]) <= 1
+        assert abs(sg["krylov_its"] - sh["krylov_its"]) <= 2
+        assert abs(sg["fnorm0"] - sh["fnorm0"]) <= 1e-12 * sh["fnorm0"]
+
+
+def test_graph_newton_restarts_and_caps(nrd):
+    """GMRES restarts (restart length 2) and the Newton cap inside the graph:
+    the restarted solve converges to the host loop's state, and a capped solve
+    reports NRD_ENONCONV in both forms."""
+    h, z = CASES["amr2_16"]()
+    cg, ch = _graph_pair(nrd, h, z, rtol=1e-10, restart=2, pc_precision=nrd.PC_F32)
+    u0 = W.front_state(h, seed=2, noise=0.02, front=0.2, width=0.05)
+    outs = []
+    for ctx in (cg, ch):
+        u = dev(u0)
+        st = ctx.step(u, dev(u0), None, 2e-3)
+        outs.append((u.cpu().numpy(), st))
+    (ug, sg), (uh, sh) = outs
+    assert sg["status"] == 0 and sh["status"] == 0
+    assert sg["krylov_its"] > 2 * sg["newton_its"] - 1 or sh["krylov_its"] > 2 * sh["newton_its"] - 1
+    leaf = np.concatenate([~h.covered_mask()] * 2)
+    assert np.abs(ug - uh)[leaf].max() <= 1e-8 * np.abs(uh[leaf]).max()
+    for ctx in (cg, ch):
+        ctx.set_params(max_newton=1, rtol=1e-14)
+        u = dev(u0)
+        st = ctx.step(u, dev(u0), None, 2e-3, check=False)
+        assert st["status"] == nrd.ENONCONV and st["newton_its"] == 1
