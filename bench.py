@@ -34,14 +34,18 @@ MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
 DT = 5e-4
 WORKLOAD = "amr2_base64_marshak_band"
-# Algorithmic work per leaf cell (derivation in the design notes): the
-# linearisation stencil does 3 face linearisations (86.8 FP64 flop-equivalents
-# each, counting an FMA as 2 flops and a reciprocal / square root at their
-# measured FMA-equivalent cost) plus 48.4 per cell.
-LIN_FLOPS_PER_CELL = 3 * 86.8 + 48.4
+# Algorithmic work per leaf cell of the linearisation stencil, in FP64-pipe
+# instructions (the unit that bounds it on GB300, which issues 2 FP64
+# instructions per clock per SM): 3 faces x 60 (face flux, its 5 partials,
+# raw and scaled P1 coefficients, incl. the conversions of the refined
+# reciprocal and reciprocal square root) + 46 per cell (balance, coupling and
+# its partials, P2 data).  Derivation in the design notes.
+LIN_INST_PER_CELL = 3 * 60 + 46
 # DRAM bytes per launch of that kernel from the committed ncu capture of the
-# same kernel version, or None when the kernel changed since.
-LIN_TRAFFIC_BYTES = None
+# same kernel version (profiles/k_stencil_lin_amr2_base64.md), or None when
+# the kernel changed since.
+LIN_TRAFFIC_BYTES = 24.72e6 + 90.69e6
+JV_TRAFFIC_BYTES = 83.10e6 + 9.47e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
@@ -58,18 +62,22 @@ def parse():
     ap.add_argument("--no-regrid", action="store_true", help="skip the regrid/transfer leg")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profilers: 1 warm-up + 2 production steps, fixed "
-                         "8x8x8 tiles, no plain/CPU/e2e legs")
+                         "8x8x8 tiles and V(1,1)/2 sweeps, no plain/CPU/e2e legs; the "
+                         "Newton loop runs host-driven so that a profiler sees every kernel "
+                         "as its own launch (--profile-graph keeps the graph form)")
+    ap.add_argument("--profile-graph", action="store_true")
     return ap.parse_args()
 
 
-def profile_run():
+def profile_run(args):
     import torch
     import __graft_entry__ as g
     g.build()
     from paper_1302_6303_gb300 import nrd
     h, z, u0 = workload()
     ctx = make_ctx(nrd, h, z, torch, production=True)
-    ctx.set_params(tile_x=8, tile_y=8, tile_z=8)
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=8, nu1=1, nu2=1, coarse_sweeps=2,
+                   graph=1 if args.profile_graph else 0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     r = run_steps(ctx, torch, u0, 2, 1, flush, timing=False)
     print(json.dumps({"profile_run": True, "ms": r["ms"], "krylov": r["krylov"]}))
@@ -351,7 +359,7 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile:
-        return profile_run()
+        return profile_run(args)
     import torch
     import __graft_entry__ as g
     g.build()
@@ -409,22 +417,26 @@ def main():
     lin_ms, lin_n = kt["residual"]
     jv_ms, jv_n = kt["jv"]
     t_lin = lin_ms / max(lin_n, 1) * 1e-3
-    ach = LIN_FLOPS_PER_CELL * leaf / t_lin / 1e12
-    fp64_peak = rates["fp64_tflops"]
+    ach = LIN_INST_PER_CELL * leaf / t_lin / 1e9
+    # FP64 pipe issue rate: the measured FP64 FMA rate in instructions
+    # (one FMA = one instruction = 2 flops)
+    fp64_peak = rates["fp64_tflops"] * 1e3 / 2.0
     roof = {"kernel": "k_stencil<ST_LIN> (residual + linearisation, FP64)", "bound": "alu",
-            "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+            "achieved": ach, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
             "frac": ach / fp64_peak, "traffic": LIN_TRAFFIC_BYTES,
             "per_launch_us": t_lin * 1e6, "launches": lin_n,
             "timing": "CUDA events around each launch in an instrumented repeat of the timed "
                       "steps",
-            "peak_source": "FP64 FMA rate measured in this run by nrd_measure_peaks (no FP64 "
-                           "figure in MEASURED_PEAKS.json)",
-            "algorithmic": "%.1f FP64 flop-equivalents per leaf cell x %d leaf cells"
-                           % (LIN_FLOPS_PER_CELL, leaf)}
+            "peak_source": "FP64 FMA rate measured in this run by nrd_measure_peaks, in "
+                           "instructions (2 per clock per SM x 152 SMs x clock; no FP64 figure "
+                           "in MEASURED_PEAKS.json)",
+            "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
+                           % (LIN_INST_PER_CELL, leaf)}
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
     ach_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
-    roof_jv = {"kernel": "k_jv_frozen (frozen-Jacobian Jv)", "bound": "hbm", "achieved": ach_jv,
+    roof_jv = {"kernel": "k_stencil<ST_JVF> (frozen-Jacobian Jv)", "bound": "hbm", "achieved": ach_jv,
                "peak": hbm_peak, "unit": "GB/s", "frac": ach_jv / hbm_peak,
+               "traffic": JV_TRAFFIC_BYTES,
                "per_launch_us": t_jv * 1e6, "peak_source": peak_src}
 
     # plain form beside it

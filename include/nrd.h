@@ -350,6 +350,16 @@ int nrd_autotune(nrd_ctx* ctx, const double* u, const double* b, double a0, doub
 int nrd_wdot_noalloc(const double* x, const double* y, const float* w, int64_t n, double* out,
                      cudaStream_t stream);
 
+/* Check of the arithmetic the linearisation stencil uses instead of FP64
+ * division and square root (no counterpart in the paper): for n doubles x
+ * (device), out (device, 4n doubles) receives rcp(x), 1.0/x, rsqrt(x) and
+ * 1.0/sqrt(x), where rcp and rsqrt are the FP32 reciprocal (square root)
+ * refined by one Newton-Raphson step in FP64 and the others CUDA's correctly
+ * rounded operations.  Relative error bound of the refinements for x in the
+ * FP32 normal range: 1e-13 (outside it they return the rounded values).
+ * Asynchronous.  Errors: NRD_EINVAL, NRD_ECUDA. */
+int nrd_check_fastmath(const double* x, int64_t n, double* out, cudaStream_t stream);
+
 /* Machine rates used as roofline denominators, measured on the current
  * device: FP64 and FP32 FMA throughput in TFLOP/s (an FMA counts 2 flops;
  * independent FMA chains on every SM) and device-to-device copy bandwidth in

@@ -112,7 +112,7 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.cc = c->d_cc;
   io.beta = dt / a0;
   io.par = par;
-  pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2);
+  pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2, &io.p2f);
   c->timer.begin(NRD_TK_RESIDUAL, s);
   launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s);
   c->timer.end(NRD_TK_RESIDUAL, s);

@@ -198,9 +198,14 @@ __global__ void k_axpy(int n, double a, const double* __restrict__ x, double* __
 
 // x = num * x / sqrt(den_sq)   (num may be null -> 1)
 __global__ void k_scale_dev(int n, const double* num, const double* den_sq, double* x) {
-  double nn = num ? *num : 1.0;
-  double d = sqrt(*den_sq);
-  double s = (d > 0.0) ? nn / d : 0.0;
+  __shared__ double s_s;
+  if (threadIdx.x == 0) {
+    const double nn = num ? *num : 1.0;
+    const double d = sqrt(*den_sq);
+    s_s = (d > 0.0) ? nn / d : 0.0;
+  }
+  __syncthreads();
+  const double s = s_s;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     x[i] *= s;
 }
@@ -234,8 +239,13 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     if (mask[i] & MASK_COVERED) continue;
     for (int f = 0; f < 2; f++) {
-      double vv = v[f * N + i];
-      if (vv < 0.0) m = fmin(m, u[f * N + i] / (-vv));
+      // divide only when the ratio beats the running minimum
+      // (u/(-v) < m  <=>  u < m (-v) for v < 0), so the result is the same
+      const double vv = v[f * N + i];
+      if (vv < 0.0) {
+        const double uu = u[f * N + i];
+        if (uu < m * (-vv)) m = fmin(m, uu / (-vv));
+      }
     }
   }
   double r = block_red<1>(m, sh);

@@ -408,34 +408,35 @@ __global__ void k_prolong_level(const TileDev* tiles, const PatchDev* patches, i
 // s = z^3/T^3 at the frozen iterate (Sec. 4.2)
 // P2 data frozen at the iterate: p[c] = sigma beta, p[N+c] = sigma beta T^3,
 // p[2N+c] = 1/det with P2 = [[1 + p0, -p1], [-p0, 1 + p1]].
+// det P2 = (1 + p0)(1 + p1) - p0 p1 = 1 + p0 + p1 (formed without the
+// cancellation).  Stored in the V-cycle precision P.
+template <class P>
 __global__ void k_p2_setup(const uint8_t* mask, int N, const double* Tk, const float* zm,
-                           const double* beta_p, double* p) {
+                           const double* beta_p, P* p) {
   const double beta = *beta_p;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
     double T = Tk[c];
     double T3 = T * T * T;
     double z = (double)zm[c];
     double sig = z * z * z / T3;
-    double a = 1.0 + sig * beta, b = -sig * beta * T3;
-    double cc = -sig * beta, d = 1.0 + sig * beta * T3;
-    double det = a * d - b * cc;
+    double sb = sig * beta, sbt = sb * T3;
     bool cov = mask[c] & MASK_COVERED;
-    p[c] = cov ? 0.0 : sig * beta;
-    p[N + c] = cov ? 0.0 : sig * beta * T3;
-    p[2L * N + c] = cov ? 0.0 : 1.0 / det;
+    p[c] = cov ? P(0) : (P)sb;
+    p[N + c] = cov ? P(0) : (P)sbt;
+    p[2L * N + c] = cov ? P(0) : (P)(1.0 / (1.0 + sb + sbt));
   }
 }
 
 // y = P2^{-1} z per leaf cell (Sec. 4.2); covered cells get 0
 template <class P>
-__global__ void k_p2(int N, const P* zin, const double* p, double* y, const int* jd, long jstride,
+__global__ void k_p2(int N, const P* zin, const P* p, double* y, const int* jd, long jstride,
                      double* y2) {
   if (jd) y += (long)(*jd) * jstride;   // y = column *jd of a basis (device index)
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    double sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
-    double zE = (double)zin[c], zT = (double)zin[N + c];
-    double yE = ((1.0 + sbt) * zE + sbt * zT) * rd;
-    double yT = ((1.0 + sb) * zT + sb * zE) * rd;
+    const P sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
+    const P zE = zin[c], zT = zin[N + c];
+    const double yE = (double)(((P(1) + sbt) * zE + sbt * zT) * rd);
+    const double yT = (double)(((P(1) + sb) * zT + sb * zE) * rd);
     y[c] = yE;
     y[N + c] = yT;
     if (y2) {
@@ -448,12 +449,12 @@ __global__ void k_p2(int N, const P* zin, const double* p, double* y, const int*
 // transposed P2 solve fused with the cast into the V-cycle precision:
 // P2^T = [[1 + sb, -sb], [-sbt, 1 + sbt]]
 template <class P>
-__global__ void k_p2t_cast(int N, const double* w, const double* p, P* out) {
+__global__ void k_p2t_cast(int N, const double* w, const P* p, P* out) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    double sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
-    double wE = w[c], wT = w[N + c];
-    out[c] = (P)(((1.0 + sbt) * wE + sb * wT) * rd);
-    out[N + c] = (P)((sbt * wE + (1.0 + sb) * wT) * rd);
+    const P sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
+    const P wE = (P)w[c], wT = (P)w[N + c];
+    out[c] = ((P(1) + sbt) * wE + sb * wT) * rd;
+    out[N + c] = (sbt * wE + (P(1) + sb) * wT) * rd;
   }
 }
 
@@ -760,7 +761,7 @@ struct PcState {
   void* bf[NRD_MAX_MG] = {nullptr};
   int* bgt = nullptr;    // [6] boundary type per box face (1 = Robin)
   double* d_beta = nullptr;
-  double* p2 = nullptr;  // [3][N] frozen P2 data
+  void* p2 = nullptr;    // [3][N] frozen P2 data, V-cycle precision
   // CUDA graphs of one apply, per (w, y) pair, captured on a private stream
   struct Graph {
     const double* w;
@@ -771,6 +772,9 @@ struct PcState {
   std::vector<Graph> graphs;
   cudaStream_t cap = nullptr;
   bool use_graph = true;
+  // GMG levels tail_m.. run as one shared-memory kernel (0: off)
+  int tail_m = 0;
+  size_t tail_smem = 0;
 };
 
 namespace {
@@ -816,9 +820,163 @@ void box_smooth(const BoxV<P>& V, int sweeps, bool red_first, cudaStream_t s) {
     }
 }
 
+// ---- the coarse end of the GMG V-cycle in one kernel
+// Levels tail_m .. nmg-1 are small (at most 8,192 cells per field): one CTA
+// per field copies their coefficients and the rhs of level tail_m into
+// shared memory and runs the rest of the V-cycle there (the same smoothing,
+// restriction and prolongation arithmetic as the per-level kernels above),
+// with block barriers where the per-level form has kernel boundaries.
+constexpr int kTailThreads = 1024;
+constexpr size_t kTailSmemMax = 200 * 1024;
+
+template <class P>
+struct TailArgs {
+  int nlev;                       // levels tail_m .. nmg-1
+  BoxRaw B[NRD_MAX_MG];
+  const P* A[NRD_MAX_MG];         // coefficients (field f at + f * B.AF)
+  long offA[NRD_MAX_MG], offE[NRD_MAX_MG], offF[NRD_MAX_MG];   // in elements
+  const P* f0;                    // rhs of the first tail level (field stride vfs0)
+  P* e0;                          // its correction (output)
+  long vfs0;
+  int nu1, nu2, csw;
+};
+
+template <class P>
+__device__ BoxV<P> tail_view(const TailArgs<P>& a, P* sm, int l) {
+  BoxV<P> V;
+  const BoxRaw& B = a.B[l];
+  for (int d = 0; d < 3; d++) V.n[d] = B.n[d];
+  for (int q = 0; q < 6; q++) V.fo[q] = B.fo[q];
+  V.A = sm + a.offA[l];
+  V.Afs = 0;
+  V.NA = B.NA;
+  V.gbase = B.gbase;
+  V.cell0 = 0;
+  V.e = sm + a.offE[l];
+  V.f = sm + a.offF[l];
+  V.vfs = 0;
+  return V;
+}
+
+template <class P>
+__device__ void tail_smooth(const BoxV<P>& V, int sweeps, bool red_first) {
+  const long nc = (long)V.n[0] * V.n[1] * V.n[2];
+  for (int sw = 0; sw < sweeps; sw++)
+    for (int pass = 0; pass < 2; pass++) {
+      const int colour = red_first ? pass : 1 - pass;
+      for (long c = threadIdx.x; c < nc; c += blockDim.x) {
+        int i = (int)(c % V.n[0]);
+        long r = c / V.n[0];
+        int j = (int)(r % V.n[1]);
+        int k = (int)(r / V.n[1]);
+        if (((i + j + k) & 1) != colour) continue;
+        P dg, of;
+        box_row(V, 0, i, j, k, V.e, dg, of);
+        V.e[c] = (V.f[c] + of) / dg;
+      }
+      __syncthreads();
+    }
+}
+
+template <class P>
+__global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
+  extern __shared__ __align__(16) unsigned char tail_raw[];
+  P* sm = reinterpret_cast<P*>(tail_raw);
+  const int fld = blockIdx.x;
+  for (int l = 0; l < a.nlev; l++) {
+    const BoxRaw& B = a.B[l];
+    const P* A = a.A[l] + fld * B.AF;
+    for (long q = threadIdx.x; q < B.AF; q += blockDim.x) sm[a.offA[l] + q] = A[q];
+    const long nc = (long)B.n[0] * B.n[1] * B.n[2];
+    for (long q = threadIdx.x; q < nc; q += blockDim.x) sm[a.offE[l] + q] = P(0);
+  }
+  {
+    const long nc = (long)a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
+    for (long q = threadIdx.x; q < nc; q += blockDim.x)
+      sm[a.offF[0] + q] = a.f0[fld * a.vfs0 + q];
+  }
+  __syncthreads();
+  // down: smooth, restrict (8-cell average of f - L e)
+  for (int l = 0; l + 1 < a.nlev; l++) {
+    BoxV<P> V = tail_view(a, sm, l);
+    tail_smooth(V, a.nu1, true);
+    BoxV<P> C = tail_view(a, sm, l + 1);
+    const long ncc = (long)C.n[0] * C.n[1] * C.n[2];
+    for (long c = threadIdx.x; c < ncc; c += blockDim.x) {
+      int ci = (int)(c % C.n[0]);
+      long r = c / C.n[0];
+      int cj = (int)(r % C.n[1]), ck = (int)(r / C.n[1]);
+      P s = P(0);
+      for (int x = 0; x < 2; x++)
+        for (int y = 0; y < 2; y++)
+          for (int z = 0; z < 2; z++) {
+            int i = 2 * ci + x, j = 2 * cj + y, k = 2 * ck + z;
+            long q = i + (long)V.n[0] * (j + (long)V.n[1] * k);
+            P dg, of;
+            box_row(V, 0, i, j, k, V.e, dg, of);
+            s += V.f[q] - (dg * V.e[q] - of);
+          }
+      sm[a.offF[l + 1] + c] = s / P(8);
+    }
+    __syncthreads();
+  }
+  tail_smooth(tail_view(a, sm, a.nlev - 1), a.csw, true);
+  // up: trilinear prolongation of the coarse correction, smooth
+  for (int l = a.nlev - 2; l >= 0; l--) {
+    BoxV<P> V = tail_view(a, sm, l);
+    const BoxRaw& C = a.B[l + 1];
+    const int cn[3] = {C.n[0], C.n[1], C.n[2]};
+    const P* src = sm + a.offE[l + 1];
+    const long nf = (long)V.n[0] * V.n[1] * V.n[2];
+    for (long c = threadIdx.x; c < nf; c += blockDim.x) {
+      int q[3];
+      q[0] = (int)(c % V.n[0]);
+      long r = c / V.n[0];
+      q[1] = (int)(r % V.n[1]);
+      q[2] = (int)(r / V.n[1]);
+      V.e[c] += tri_interp(src, cn, q, (const int*)nullptr, 0);
+    }
+    __syncthreads();
+    tail_smooth(V, a.nu2, false);
+  }
+  const long nc0 = (long)a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
+  for (long q = threadIdx.x; q < nc0; q += blockDim.x) a.e0[fld * a.vfs0 + q] = sm[a.offE[0] + q];
+}
+
+template <class P>
+void run_tail(PcState* ps, cudaStream_t s) {
+  TailArgs<P> a;
+  const int m0 = ps->tail_m;
+  a.nlev = ps->nmg - m0;
+  long off = 0;
+  for (int l = 0; l < a.nlev; l++) {
+    const BoxRaw& B = ps->box[m0 + l];
+    const long nc = (long)B.n[0] * B.n[1] * B.n[2];
+    a.B[l] = B;
+    a.A[l] = (const P*)ps->bA[m0 + l];
+    a.offA[l] = off;
+    off += B.AF;
+    a.offE[l] = off;
+    off += nc;
+    a.offF[l] = off;
+    off += nc;
+  }
+  a.f0 = (const P*)ps->bf[m0];
+  a.e0 = (P*)ps->be[m0];
+  a.vfs0 = (long)ps->box[m0].n[0] * ps->box[m0].n[1] * ps->box[m0].n[2];
+  a.nu1 = ps->nu1;
+  a.nu2 = ps->nu2;
+  a.csw = ps->csw;
+  k_box_tail<P><<<2, kTailThreads, ps->tail_smem, s>>>(a);
+}
+
 // GMG V-cycle on box level m (m = 0: AMR level 0 inside the hierarchy vectors)
 template <class P>
 void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
+  if (m > 0 && m == ps->tail_m) {
+    run_tail<P>(ps, s);
+    return;
+  }
   BoxRaw B = (m == 0) ? level0_box(H) : ps->box[m];
   const void* A = (m == 0) ? ps->A : ps->bA[m];
   void* e = (m == 0) ? ps->fe : ps->be[m];
@@ -834,7 +992,7 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   long cn = (long)C.n[0] * C.n[1] * C.n[2];
   dim3 gc(g1(cn), 2);
   k_box_restrict<P><<<gc, BS, 0, s>>>(V, (P*)ps->bf[m + 1], cn);
-  cudaMemsetAsync(ps->be[m + 1], 0, 2 * cn * ps->esz, s);
+  if (m + 1 != ps->tail_m) cudaMemsetAsync(ps->be[m + 1], 0, 2 * cn * ps->esz, s);
   gmg_vcycle<P>(ps, H, m + 1, s);
   long nf = (long)B.n[0] * B.n[1] * B.n[2];
   dim3 gf(g1(nf), 2);
@@ -929,7 +1087,7 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
             cudaStream_t s, const int* jd = nullptr, long jstride = 0, double* y2 = nullptr) {
   const long n2 = 2L * H.N;
   if (transposed)
-    k_p2t_cast<P><<<g1(H.N), BS, 0, s>>>(H.N, w, ps->p2, (P*)ps->ff);
+    k_p2t_cast<P><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff);
   else
     k_cast<P><<<g1(n2), BS, 0, s>>>((int)n2, w, (P*)ps->ff, jd, jstride);
   cudaMemsetAsync(ps->fu, 0, n2 * sizeof(P), s);
@@ -958,7 +1116,7 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
   if (transposed)
     k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y);
   else
-    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, ps->p2, y, jd, jstride, y2);
+    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, (const P*)ps->p2, y, jd, jstride, y2);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }
 
@@ -1013,7 +1171,7 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
             cudaMalloc(&ps->Tk, N * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ps->bgt, 6 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ps->d_beta, sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&ps->p2, 3 * N * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&ps->p2, 3 * N * e) == cudaSuccess &&
             cudaStreamCreateWithFlags(&ps->cap, cudaStreamNonBlocking) == cudaSuccess;
   if (ok) {
     cudaMemset(ps->Craw, 0, 2 * ps->AF * sizeof(double));
@@ -1053,6 +1211,30 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
     pc_free(ps);
     err = "preconditioner allocation failed";
     return NRD_ENOMEM;
+  }
+  // the coarsest box levels whose data fit one CTA's shared memory run as
+  // one kernel (the first such level with at most 8,192 cells per field);
+  // FP32 V-cycles only: one SM's FP64 rate is too low for it
+  ps->tail_m = 0;
+  for (int m = 1; m < ps->nmg && !ps->tail_m && ps->prec == NRD_PC_F32; m++) {
+    const long nc = (long)ps->box[m].n[0] * ps->box[m].n[1] * ps->box[m].n[2];
+    if (nc > 8192) continue;
+    size_t need = 0;
+    for (int l = m; l < ps->nmg; l++) {
+      const BoxRaw& B = ps->box[l];
+      need += (size_t)(B.AF + 2L * B.n[0] * B.n[1] * B.n[2]) * e;
+    }
+    if (need <= kTailSmemMax) {
+      ps->tail_m = m;
+      ps->tail_smem = need;
+    }
+  }
+  // (set here, outside any stream capture)
+  if (ps->tail_m) {
+    cudaFuncSetAttribute(k_box_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTailSmemMax);
+    cudaFuncSetAttribute(k_box_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)kTailSmemMax);
   }
   *out = ps;
   return NRD_OK;
@@ -1105,10 +1287,11 @@ static SetupArgs setup_args(PcState* ps, const Hier& H, const ModelParams* mp, c
   return a;
 }
 
-void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2) {
+void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2, float** p2f) {
   *a32 = (ps->prec == NRD_PC_F32) ? (float*)ps->A : nullptr;
   *a64 = (ps->prec == NRD_PC_F32) ? nullptr : (double*)ps->A;
-  *p2 = ps->p2;
+  *p2 = (ps->prec == NRD_PC_F32) ? nullptr : (double*)ps->p2;
+  *p2f = (ps->prec == NRD_PC_F32) ? (float*)ps->p2 : nullptr;
 }
 
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
@@ -1123,7 +1306,12 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
   SetupArgs a = setup_args(ps, H, nullptr, u, nullptr, z, nullptr);
   if (!from_lin) {
     cudaMemcpyAsync(ps->Tk, u + H.N, (size_t)H.N * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    k_p2_setup<<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, ps->Tk, z, ps->d_beta, ps->p2);
+    if (ps->prec == NRD_PC_F32)
+      k_p2_setup<float><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, ps->Tk, z, ps->d_beta,
+                                               (float*)ps->p2);
+    else
+      k_p2_setup<double><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, ps->Tk, z, ps->d_beta,
+                                                (double*)ps->p2);
   }
   for (int l = H.L - 2; l >= 0; l--) {
     if (!H.ncz[l]) continue;

@@ -19,6 +19,7 @@ struct LevelH {
   double rh[NRD_MAX_LEVELS][3];   // 1/h
   double h3[NRD_MAX_LEVELS][3];   // 3h
   double kh[NRD_MAX_LEVELS][3];   // k/h
+  double kh5[NRD_MAX_LEVELS][3];  // 1.25 k/h
   double bh2[NRD_MAX_LEVELS][3];  // beta/h^2 (linearisation only)
 };
 
@@ -126,36 +127,76 @@ __device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double
 struct FaceLin {
   double PE, PT, CE, CT, aEa, aEb, aT, bTa, bTb, aZ;
 };
+
+// 1/x from the FP32 reciprocal refined by one Newton-Raphson step
+// (r1 = r0 + r0 (1 - x r0); relative error ~ the square of the seed's,
+// about 2^-46; see e.g. Muller et al., Handbook of Floating-Point
+// Arithmetic).  Outside the FP32 normal range the correctly rounded 1/x.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const float xf = (float)x;
+  const float ax = fabsf(xf);
+  if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
+  const double r = (double)__frcp_rn(xf);
+  return fma(r, fma(-x, r, 1.0), r);
+}
+
+// 1/sqrt(x) from the FP32 reciprocal square root refined by one
+// Newton-Raphson step (y1 = y0 + y0 (1 - x y0^2) / 2; relative error about
+// 1.5 times the square of the seed's, below 1e-13).  x > 0; outside the
+// FP32 normal range the correctly rounded 1/sqrt(x).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
+  const double y = (double)rsqrtf(xf);
+  return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+}
+
+// Face flux of flux_val and its partial derivatives at one iterate (the
+// frozen Jacobian), the raw P1 coefficients CE = D_E h and CT = D_T:
+//   PE = X dE, CE = X h with X = 2 Tf^3 S / den, den = 3h Zs S + cL Tf^3 |dE|
+//   d PE / d E_a = (-4 Tf^3 E_a - PE (3h Zs - cL Tf^3 sg)) / den
+//   d PE / d E_b = ( 4 Tf^3 E_b - PE (3h Zs + cL Tf^3 sg)) / den
+//   d PE / d T_a = d PE / d T_b = Tf^2 (3 S dE - 1.5 cL |dE| PE) / den
+//   d PE / d Zs  = -PE 3h S / den
+//   PT = (k/h) Tf^(5/2) dT, d PT / d T_{a,b} = (k/h)(1.25 Tf^(3/2) dT -/+ Tf^(5/2))
+// (sg = sign(dE), sign(0) = 0).  The reciprocal and Tf^(-1/2) come from
+// rcp_nr / rsqrt_nr, so the result differs from flux_val's correctly
+// rounded arithmetic by ~1e-13 relative.
 __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, double Tb, double za,
-                                            double zb, double h, double h3, double kh, double k,
-                                            double cL) {
+                                            double zb, double h, double h3, double kh,
+                                            double kh5, double k, double cL) {
   FaceLin r;
-  double Tf = 0.5 * (Ta + Tb);
-  double Tf2 = Tf * Tf;
-  double Tf3 = Tf2 * Tf;
-  double dE = Eb - Ea;
-  double S = Ea + Eb;
-  double Zs = za + zb;
-  double adE = fabs(dE);
-  double sg = (dE > 0.0) ? 1.0 : ((dE < 0.0) ? -1.0 : 0.0);
-  double hz = h3 * Zs;
-  double lt = cL * Tf3;
-  double rden = 1.0 / (hz * S + lt * adE);
-  double t2 = 2.0 * Tf3;
-  r.PE = t2 * S * dE * rden;
-  r.CE = t2 * S * h * rden;
-  r.aEa = (-2.0 * t2 * Ea - r.PE * (hz - lt * sg)) * rden;
-  r.aEb = (2.0 * t2 * Eb - r.PE * (hz + lt * sg)) * rden;
-  r.aT = (3.0 * Tf2 * S * dE - r.PE * 1.5 * cL * Tf2 * adE) * rden;
-  r.aZ = -r.PE * h3 * S * rden;   // d Phi_E / d (z_a^3 + z_b^3)
-  double sq = sqrt(Tf);
-  double T25 = Tf2 * sq, T15 = Tf * sq;
-  double dT = Tb - Ta;
+  const double Tf = 0.5 * (Ta + Tb);
+  const double Tf2 = Tf * Tf;
+  const double Tf3 = Tf2 * Tf;
+  const double dE = Eb - Ea;
+  const double S = Ea + Eb;
+  const double hz = h3 * (za + zb);
+  const double lt = cL * Tf3;
+  const double adE = fabs(dE);
+  const double rden = rcp_nr(fma(hz, S, lt * adE));
+  const double X = 2.0 * Tf3 * S * rden;
+  const double PE = X * dE;
+  r.PE = PE;
+  r.CE = X * h;
+  const double A = PE * hz;
+  const double B = PE * lt;
+  const double Bs = (dE > 0.0) ? B : ((dE < 0.0) ? -B : 0.0);
+  const double t4 = 4.0 * Tf3;
+  r.aEa = (fma(-t4, Ea, Bs) - A) * rden;
+  r.aEb = (fma(t4, Eb, -Bs) - A) * rden;
+  r.aT = (Tf2 * rden) * fma(-1.5 * cL, adE * PE, 3.0 * (S * dE));
+  r.aZ = -(PE * rden) * (h3 * S);
+  const double y = rsqrt_nr(Tf);
+  const double T15 = Tf2 * y;     // Tf^(3/2)
+  const double T25 = Tf * T15;    // Tf^(5/2)
+  const double dT = Tb - Ta;
   r.CT = k * T25;
-  r.PT = kh * T25 * dT;
-  double q = 1.25 * T15 * dT;
-  r.bTa = kh * (q - T25);
-  r.bTb = kh * (q + T25);
+  const double khT25 = kh * T25;
+  r.PT = khT25 * dT;
+  const double khq = kh5 * T15 * dT;
+  r.bTa = khq - khT25;
+  r.bTb = khq + khT25;
   return r;
 }
 
@@ -223,6 +264,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int NC = TX * TY * TZ;
   constexpr bool TAN = (MODE == ST_JV);
   constexpr bool LIN = (MODE == ST_LIN);
+  constexpr bool JVF = (MODE == ST_JVF);       // frozen-Jacobian Jv: sE, sT hold v
   extern __shared__ double smem[];
   double* sE = smem;
   double* sT = sE + NH;
@@ -279,7 +321,23 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       if ((ox != 0) + (oy != 0) + (oz != 0) > 1) continue;
       if (i > nx || j > ny || k > nz) continue;
       double e, tt, ve = 0.0, vt = 0.0;
-      double z;
+      double z = 0.0;
+      if (JVF) {
+        if (!ox && !oy && !oz) {
+          int idx = P.off + i + nx * (j + ny * k);
+          e = io.v[idx];
+          tt = io.v[N + idx];
+        } else {
+          int f = ox ? (ox < 0 ? 0 : 1) : (oy ? (oy < 0 ? 2 : 3) : (oz < 0 ? 4 : 5));
+          int a = ox ? j : (oy ? k : i), b = ox ? k : (oy ? i : j);
+          int gi = P.goff + P.fo[f] + a + P.n[(f / 2 + 1) % 3] * b;
+          e = io.gv[gi];
+          tt = io.gv[G + gi];
+        }
+        sE[hh] = e;
+        sT[hh] = tt;
+        continue;
+      }
       if (!ox && !oy && !oz) {
         int idx = P.off + i + nx * (j + ny * k);
         e = io.u[idx];
@@ -362,7 +420,21 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       } else {
         fslot = (long)dir * N + P.off + i + (long)nx * (j + (long)ny * k);
       }
-      if (gt == GT_NEUMANN) {
+      if (JVF) {
+        // tangent flux = stored partials times the direction (sE, sT hold v)
+        if (gt == GT_ROBIN) {
+          const int hc = (pos == 0) ? hb : ha;
+          PE = io.jc[fslot] * sE[hc] + io.jc[NS + fslot] * sT[hc];
+        } else if (gt != GT_NEUMANN) {
+          PE = io.jc[fslot] * sE[ha] + io.jc[NS + fslot] * sE[hb] +
+               io.jc[2 * NS + fslot] * (sT[ha] + sT[hb]);
+          PT = io.jc[3 * NS + fslot] * sT[ha] + io.jc[4 * NS + fslot] * sT[hb];
+          if (gt == GT_CF) {
+            io.cfflux[gi] = PE;
+            io.cfflux[G + gi] = PT;
+          }
+        }
+      } else if (gt == GT_NEUMANN) {
         PE = 0.0;
         PT = 0.0;
         if (LIN) {
@@ -403,7 +475,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           flux_tan(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, svE[ha], svE[hb],
                    svT[ha], svT[hb], PE, PT);
         } else if (LIN) {
-          FaceLin L = flux_lin(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, h3, kh, A.k, A.cL);
+          FaceLin L = flux_lin(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, h3, kh,
+                               A.lh.kh5[lvl][dir], A.k, A.cL);
           PE = L.PE;
           PT = L.PT;
           io.jc[fslot] = L.aEa;
@@ -444,9 +517,15 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.cc[idx] = 0.0;
           io.cc[N + idx] = 0.0;
           io.cc[2L * N + idx] = 0.0;
-          io.p2[idx] = 0.0;
-          io.p2[N + idx] = 0.0;
-          io.p2[2L * N + idx] = 0.0;
+          if (io.p2f) {
+            io.p2f[idx] = 0.0f;
+            io.p2f[N + idx] = 0.0f;
+            io.p2f[2L * N + idx] = 0.0f;
+          } else {
+            io.p2[idx] = 0.0;
+            io.p2[N + idx] = 0.0;
+            io.p2[2L * N + idx] = 0.0;
+          }
         }
         continue;
       }
@@ -464,7 +543,11 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       int hc = (ci + 1) + HX * ((cj + 1) + HY * (ck + 1));
       double E = sE[hc], T = sT[hc], z = sZ[hc];
       double T2 = T * T, T3 = T2 * T;
-      if (MODE == ST_JV) {
+      if (JVF) {
+        const double dc = io.cc[idx] * E + io.cc[N + idx] * T;
+        io.out[idx] = a0v * E - dtv * (divE + dc);
+        io.out[N + idx] = a0v * T - dtv * (divT - dc);
+      } else if (MODE == ST_JV) {
         double rT = 1.0 / T;
         double sig = z * rT * rT * rT;
         double vE = svE[hc], vT = svT[hc];
@@ -472,7 +555,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         io.out[idx] = a0v * vE - dtv * (divE + dc);
         io.out[N + idx] = a0v * vT - dtv * (divT - dc);
       } else if (MODE == ST_LIN) {
-        double rT = 1.0 / T;
+        double rT = rcp_nr(T);
         double sig = z * rT * rT * rT;
         double cp = sig * (T2 * T2 - E);
         io.out[idx] = a0v * E - io.b[idx] - dtv * (divE + cp);
@@ -482,10 +565,19 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         io.cc[N + idx] = sig * (T3 + 3.0 * E * rT);
         io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
         // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
-        double sb = sig * betav, sbt = sb * T3;
-        io.p2[idx] = sb;
-        io.p2[N + idx] = sbt;
-        io.p2[2L * N + idx] = 1.0 / ((1.0 + sb) * (1.0 + sbt) - sbt * sb);
+        // (det = (1 + sb)(1 + sbt) - sbt sb = 1 + sb + sbt), in the
+        // preconditioner's precision
+        if (io.p2f) {
+          const float sb = (float)sig * (float)betav, sbt = sb * (float)T3;
+          io.p2f[idx] = sb;
+          io.p2f[N + idx] = sbt;
+          io.p2f[2L * N + idx] = 1.0f / (1.0f + sb + sbt);
+        } else {
+          const double sb = sig * betav, sbt = sb * T3;
+          io.p2[idx] = sb;
+          io.p2[N + idx] = sbt;
+          io.p2[2L * N + idx] = rcp_nr(1.0 + sb + sbt);
+        }
       } else {
         double sig = z / T3;
         double cp = sig * (T2 * T2 - E);
@@ -500,104 +592,6 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
     }
     __syncthreads();
-  }
-}
-
-// Jv with the Jacobian frozen at the last linearisation (ST_LIN): each face
-// tangent flux is a linear combination of the tangent values on its two
-// sides with the stored partial derivatives, so one Jv is a memory-bound
-// stencil application.  Same face classification as k_stencil.
-struct JfArgs {
-  const TileDev* tiles;
-  const PatchDev* patches;
-  const uint8_t* mask;
-  const uint8_t* gtype;
-  int ntiles, N, G, tx, ty, tz;
-  LevelH lh;
-  const double* jc;   // [5][3N+G]
-  const double* cc;   // [2][N]
-  const double* v;    // [2][N]
-  const double* gv;   // [2][G] ghosts of v
-  double a0, dt;
-  const double* par;  // device a0, dt (or null: the values above)
-  double* out;
-  double* cfflux;
-};
-
-__global__ void __launch_bounds__(256) k_jv_frozen(JfArgs a) {
-  const int N = a.N, G = a.G;
-  const long NS = 3L * N + G;
-  const double a0v = a.par ? a.par[0] : a.a0, dtv = a.par ? a.par[1] : a.dt;
-  const int nc = a.tx * a.ty * a.tz;
-  for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const TileDev tile = a.tiles[t];
-    const PatchDev P = a.patches[tile.patch];
-    const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
-    const int lvl = P.level;
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty;
-      int k = tile.k0 + c / (a.tx * a.ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
-      const int idx = P.off + i + nx * (j + ny * k);
-      const uint8_t m = a.mask[idx];
-      if (m & MASK_COVERED) {
-        a.out[idx] = 0.0;
-        a.out[N + idx] = 0.0;
-        continue;
-      }
-      const double vEc = a.v[idx], vTc = a.v[N + idx];
-      const int loc[3] = {i, j, k};
-      const int st[3] = {1, nx, nx * ny};
-      double divE = 0.0, divT = 0.0;
-      for (int d = 0; d < 3; d++) {
-        double PEs[2], PTs[2];
-        for (int sd = 0; sd < 2; sd++) {
-          const int f = 2 * d + sd;
-          PEs[sd] = 0.0;
-          PTs[sd] = 0.0;
-          if (m & (2 << f)) continue;                      // coarse side: flux matching
-          const bool bnd = sd ? (loc[d] == P.n[d] - 1) : (loc[d] == 0);
-          long slot;
-          double vEa, vEb, vTa, vTb;
-          int gi = -1;
-          uint8_t gt = GT_SIBLING;
-          if (!bnd) {
-            const int nb = sd ? idx + st[d] : idx - st[d];
-            slot = (long)d * N + (sd ? nb : idx);
-            if (sd) { vEa = vEc; vTa = vTc; vEb = a.v[nb]; vTb = a.v[N + nb]; }
-            else { vEa = a.v[nb]; vTa = a.v[N + nb]; vEb = vEc; vTb = vTc; }
-          } else {
-            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-            gi = P.goff + P.fo[f] + loc[t1] + P.n[t1] * loc[t2];
-            gt = a.gtype[gi];
-            slot = 3L * N + gi;
-            const double gE = a.gv[gi], gT = a.gv[G + gi];
-            if (sd) { vEa = vEc; vTa = vTc; vEb = gE; vTb = gT; }
-            else { vEa = gE; vTa = gT; vEb = vEc; vTb = vTc; }
-          }
-          if (gt == GT_NEUMANN) continue;
-          if (gt == GT_ROBIN) {
-            PEs[sd] = a.jc[slot] * vEc + a.jc[NS + slot] * vTc;
-            continue;
-          }
-          const double pe = a.jc[slot] * vEa + a.jc[NS + slot] * vEb +
-                            a.jc[2 * NS + slot] * (vTa + vTb);
-          const double pt = a.jc[3 * NS + slot] * vTa + a.jc[4 * NS + slot] * vTb;
-          PEs[sd] = pe;
-          PTs[sd] = pt;
-          if (gt == GT_CF) {
-            a.cfflux[gi] = pe;
-            a.cfflux[G + gi] = pt;
-          }
-        }
-        const double rh = a.lh.rh[lvl][d];
-        divE += (PEs[1] - PEs[0]) * rh;
-        divT += (PTs[1] - PTs[0]) * rh;
-      }
-      const double dc = a.cc[idx] * vEc + a.cc[N + idx] * vTc;
-      a.out[idx] = a0v * vEc - dtv * (divE + dc);
-      a.out[N + idx] = a0v * vTc - dtv * (divT - dc);
-    }
   }
 }
 
@@ -710,6 +704,17 @@ int blocks_for(long n, int bs) {
   return (int)b;
 }
 
+__global__ void k_check_fastmath(const double* x, long n, double* out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    out[i] = rcp_nr(v);
+    out[n + i] = 1.0 / v;
+    out[2 * n + i] = rsqrt_nr(v);
+    out[3 * n + i] = 1.0 / sqrt(v);
+  }
+}
+
 LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
   LevelH lh;
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
@@ -719,6 +724,7 @@ LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
       lh.rh[l][d] = 1.0 / h;
       lh.h3[l][d] = 3.0 * h;
       lh.kh[l][d] = k / h;
+      lh.kh5[l][d] = 1.25 * k / h;
       lh.bh2[l][d] = beta / (h * h);
     }
   return lh;
@@ -728,7 +734,7 @@ template <int MODE, int TX, int TY, int TZ>
 size_t stencil_smem() {
   constexpr int NH = (TX + 2) * (TY + 2) * (TZ + 2);
   constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
-  size_t d = (size_t)NH * (MODE == ST_JV ? 5 : 3) + 2 * (size_t)NF;
+  size_t d = (size_t)NH * (MODE == ST_JV ? 5 : (MODE == ST_JVF ? 2 : 3)) + 2 * (size_t)NF;
   return d * sizeof(double);
 }
 
@@ -805,6 +811,7 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else if (mode == ST_JVF) dispatch_tile<ST_JVF>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else dispatch_tile<ST_FD>(a, H.tile_x, H.tile_y, H.tile_z, s);
 }
 
@@ -826,28 +833,12 @@ void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s)
 
 void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, const double* cc,
                       const StencilIO& io, cudaStream_t s) {
-  JfArgs a;
-  a.tiles = H.d_tiles;
-  a.patches = H.d_patches;
-  a.mask = H.d_mask;
-  a.gtype = H.d_gtype;
-  a.ntiles = (int)H.tiles.size();
-  a.N = H.N;
-  a.G = H.G;
-  a.tx = H.tile_x;
-  a.ty = H.tile_y;
-  a.tz = H.tile_z;
-  a.lh = level_h(H, mp.k);
-  a.jc = jc;
-  a.cc = cc;
-  a.v = io.v;
-  a.gv = io.gv;
-  a.a0 = io.a0;
-  a.dt = io.dt;
-  a.par = io.par;
-  a.out = io.out;
-  a.cfflux = io.cfflux;
-  k_jv_frozen<<<std::min(a.ntiles, 152 * 8), 256, 0, s>>>(a);
+  // the tiled stencil in ST_JVF mode: v staged in shared memory, each face's
+  // tangent flux formed once from the stored partials
+  StencilIO q = io;
+  q.jc = const_cast<double*>(jc);
+  q.cc = const_cast<double*>(cc);
+  launch_stencil(H, mp, nullptr, nullptr, ST_JVF, q, s);
 }
 
 void launch_tag(const Hier& H, const double* E, const double* gE, double thr_c, double thr_g,
@@ -864,4 +855,12 @@ void launch_average_down(const Hier& H, double* x, int nfield, int fstride, cuda
     k_avgdown<<<blocks_for(H.ncov[l], 256), 256, 0, s>>>(H.d_cov[l], H.ncov[l], x, nfield,
                                                           fstride);
   }
+}
+
+extern "C" int nrd_check_fastmath(const double* x, int64_t n, double* out, cudaStream_t s) {
+  if (!x || !out || n < 0) return NRD_EINVAL;
+  if (n == 0) return NRD_OK;
+  const int grid = (int)std::min<long>(152L * 8, (n + 255) / 256);
+  k_check_fastmath<<<grid, 256, 0, s>>>(x, n, out);
+  return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }

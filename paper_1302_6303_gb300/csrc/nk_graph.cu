@@ -124,8 +124,13 @@ __global__ void k_arn_start(NkCtl* c, int m, cudaGraphConditionalHandle hA) {
 __global__ void k_normalize_g(int n, const double* r, double* V, long stride, const int* jd,
                               int add, const double* nrm2, double sign) {
   double* v = V + (long)((jd ? *jd : 0) + add) * stride;
-  const double d = sqrt(*nrm2);
-  const double sc = (d > 0.0) ? sign / d : 0.0;
+  __shared__ double sc_s;
+  if (threadIdx.x == 0) {
+    const double d = sqrt(*nrm2);
+    sc_s = (d > 0.0) ? sign / d : 0.0;
+  }
+  __syncthreads();
+  const double sc = sc_s;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     v[i] = sc * r[i];
 }
@@ -473,6 +478,10 @@ int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt,
     // and leaves valid preconditioner data behind
     cudaMemcpyAsync(G->uw, u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
     rc = ctx_linearise(c, G->uw, b, a0, dt, c->d_F, s);
+    // and one frozen Jv: first launches set kernel attributes, which must
+    // not happen inside the capture
+    if (rc == NRD_OK)
+      rc = ctx_jv(c, G->uw, c->d_F, b, c->d_F, a0, dt, NRD_JV_FROZEN, c->d_w, false, s);
     if (rc == NRD_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = NRD_ECUDA;
     if (rc == NRD_OK) {
       Builder B{c, G, b};

@@ -119,7 +119,8 @@ int hier_tiles(Hier& H, std::string& err);
 void hier_free(Hier& H);
 
 // Kernel launchers (k_stencil.cu)
-enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2, ST_LIN = 3 };
+// stencil modes; ST_JVF applies the Jacobian frozen by ST_LIN (jc, cc) to v
+enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2, ST_LIN = 3, ST_JVF = 4 };
 struct StencilIO {
   const double* u;      // state (E then T)
   const double* v;      // direction (JV, FD)
@@ -138,7 +139,8 @@ struct StencilIO {
   double beta;          // dt / a0
   float* a32;           // [2][3N+G] scaled P1 coefficients (FP32 V-cycle), or
   double* a64;          //   the FP64 array when a32 is null
-  double* p2;           // [3][N] P2 data
+  double* p2;           // [3][N] P2 data (FP64 V-cycle), or
+  float* p2f;           //   FP32 (FP32 V-cycle)
   const double* par;    // device [a0, dt, beta] overriding a0, dt, beta (or null)
 };
 void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
@@ -220,7 +222,7 @@ int pc_apply_indexed(PcState* ps, const Hier& H, const double* V, double* Z, con
 // device copy of beta = dt / a0 read by the set-up kernels
 double* pc_beta_device(PcState* ps);
 // where the linearisation writes scaled coefficients and P2 data
-void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2);
+void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2, float** p2f);
 
 #define CUDA_TRY(x)                                         \
   do {                                                      \

@@ -82,8 +82,14 @@ __global__ void k_backsub(Small S, int m, int k) {
 
 // v0 = sign * r / sqrt(nrm2)
 __global__ void k_normalize(int n, const double* r, double* v, const double* nrm2, double sign) {
-  double d = sqrt(*nrm2);
-  double sc = (d > 0.0) ? sign / d : 0.0;
+  // the scale once per block (FP64 square root and division are slow)
+  __shared__ double sc_s;
+  if (threadIdx.x == 0) {
+    const double d = sqrt(*nrm2);
+    sc_s = (d > 0.0) ? sign / d : 0.0;
+  }
+  __syncthreads();
+  const double sc = sc_s;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     v[i] = sc * r[i];
 }

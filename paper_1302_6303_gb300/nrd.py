@@ -28,6 +28,7 @@ EXPORTED = [
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
     "nrd_step", "nrd_tag", "nrd_regrid_boxes", "nrd_transfer", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
     "nrd_autotune", "nrd_autotune_sweeps", "nrd_wdot_noalloc", "nrd_measure_peaks",
+    "nrd_check_fastmath",
     "nrd_timing_enable",
     "nrd_timing_read",
 ]
@@ -111,6 +112,7 @@ def load(path: str = _LIBPATH):
         "nrd_dt_control": (c_int, [c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, P(c_dbl)]),
         "nrd_wdot_noalloc": (c_int, [dp, dp, fp, ctypes.c_int64, dp, vp]),
         "nrd_measure_peaks": (c_int, [P(c_dbl), P(c_dbl), P(c_dbl), vp]),
+        "nrd_check_fastmath": (c_int, [dp, ctypes.c_int64, dp, vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
         "nrd_timing_read": (c_int, [vp, c_int, P(c_dbl), P(ctypes.c_int64)]),
     }
@@ -153,6 +155,17 @@ def measure_peaks():
     if rc != OK:
         raise NrdError(rc, "nrd_measure_peaks failed")
     return {"fp64_tflops": a.value, "fp32_tflops": b.value, "copy_gbs": c.value}
+
+
+def check_fastmath(x):
+    """[rcp(x), 1/x, rsqrt(x), 1/sqrt(x)] as evaluated by the stencil's
+    refined reciprocals and by CUDA's rounded operations (nrd_check_fastmath)."""
+    out = torch.empty(4, x.numel(), dtype=torch.float64, device=x.device)
+    rc = load().nrd_check_fastmath(_ptr(x, torch.float64), x.numel(), _ptr(out, torch.float64),
+                                   _stream())
+    if rc != OK:
+        raise NrdError(rc, "nrd_check_fastmath failed")
+    return out
 
 
 def dt_control(kind, eps_t, err_n, err_nm1, dt_n, dt_nm1):

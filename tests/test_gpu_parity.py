@@ -419,3 +419,18 @@ def test_graph_newton_restarts_and_caps(nrd):
         u = dev(u0)
         st = ctx.step(u, dev(u0), None, 2e-3, check=False)
         assert st["status"] == nrd.ENONCONV and st["newton_its"] == 1
+
+
+def test_refined_reciprocals_error_bound(nrd):
+    """The linearisation's FP32-seeded, Newton-Raphson-refined reciprocal and
+    reciprocal square root against CUDA's correctly rounded 1/x, 1/sqrt(x):
+    relative error below 1e-13 over 13 decades and at the FP32 range edges
+    (where the rounded operations are used)."""
+    rng = np.random.default_rng(0)
+    x = np.concatenate([10.0 ** rng.uniform(-6, 7, 200000), [1e-40, 1e-36, 1e36, 1e40, 1.0]])
+    out = nrd.check_fastmath(dev(x)).cpu().numpy()
+    r_err = np.abs(out[0] - out[1]) / out[1]
+    s_err = np.abs(out[2] - out[3]) / out[3]
+    assert r_err.max() <= 1e-13 and s_err.max() <= 1e-13, (r_err.max(), s_err.max())
+    # and they are accurate refinements, not the FP32 seeds
+    assert np.median(r_err) < 1e-14 and np.median(s_err) < 1e-14
