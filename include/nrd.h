@@ -112,7 +112,7 @@ typedef struct {
   double ew_gamma;     /* Eisenstat-Walker gamma */
   int tile_x, tile_y, tile_z;  /* stencil tile shape (0,0,0: 32 x 4 x 4); one of
                                   32x4x4, 32x8x4, 32x4x8, 32x2x4, 16x8x4, 16x4x8,
-                                  16x8x8, 16x4x4, 8x8x8 */
+                                  16x8x8, 16x4x4, 8x8x8, 8x8x4 */
   int graph;           /* 1 (default): with NRD_JV_ANALYTIC, nrd_newton / nrd_step run
                           the whole Newton solve as one CUDA graph whose Newton,
                           GMRES-cycle and Arnoldi loops are conditional graph nodes
@@ -353,10 +353,11 @@ int nrd_wdot_noalloc(const double* x, const double* y, const float* w, int64_t n
 /* Check of the arithmetic the linearisation stencil uses instead of FP64
  * division and square root (no counterpart in the paper): for n doubles x
  * (device), out (device, 4n doubles) receives rcp(x), 1.0/x, rsqrt(x) and
- * 1.0/sqrt(x), where rcp and rsqrt are the FP32 reciprocal (square root)
- * refined by one Newton-Raphson step in FP64 and the others CUDA's correctly
- * rounded operations.  Relative error bound of the refinements for x in the
- * FP32 normal range: 1e-13 (outside it they return the rounded values).
+ * 1.0/sqrt(x), where rcp and rsqrt are the PTX approximate FP64 reciprocal
+ * (square root) refined with the second-order series of the correction and
+ * the others CUDA's correctly rounded operations.  Relative error bound of
+ * the refinements for 1e-300 < x < 1e300: 1e-15 (outside, the rounded
+ * values).
  * Asynchronous.  Errors: NRD_EINVAL, NRD_ECUDA. */
 int nrd_check_fastmath(const double* x, int64_t n, double* out, cudaStream_t stream);
 

@@ -10,9 +10,11 @@ namespace {
 
 const char* kNullCtx = "null context";
 
-// tile shapes with compiled stencil instances
+// tile shapes with compiled stencil instances (32x8x8 is not one: the
+// tangent stencil's five halo fields and face fluxes would need 243 KB of
+// shared memory per CTA)
 const int kShapes[][3] = {{32, 4, 4}, {32, 8, 4}, {32, 4, 8}, {32, 2, 4}, {16, 8, 4},
-                          {16, 4, 8}, {16, 8, 8}, {16, 4, 4}, {8, 8, 8}};
+                          {16, 4, 8}, {16, 8, 8}, {16, 4, 4}, {8, 8, 8}, {8, 8, 4}};
 const int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 int fail(nrd_ctx* c, int code, const std::string& msg) {
@@ -63,7 +65,8 @@ void set_model(nrd_ctx* c) {
 void free_fields(nrd_ctx* c) {
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(c->d_z); F(c->d_gz); F(c->d_gu); F(c->d_gv); F(c->d_cf); F(c->d_tmp); F(c->d_jc); F(c->d_cc);
-  F(c->d_lam); F(c->d_gam);
+  F(c->d_lam); F(c->d_gam); F(c->d_z3);
+  c->d_z3 = nullptr;
   c->d_z = nullptr; c->d_gz = nullptr; c->d_gu = nullptr; c->d_gv = nullptr; c->d_cf = nullptr;
   c->d_tmp = nullptr; c->d_jc = nullptr; c->d_cc = nullptr; c->d_lam = nullptr; c->d_gam = nullptr;
   c->lin_ready = false;
@@ -89,7 +92,7 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
   io.out = F;
   io.cfflux = c->d_cf;
   c->timer.begin(NRD_TK_RESIDUAL, s);
-  launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_RESIDUAL, io, s);
+  launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_RESIDUAL, io, s, c->d_z3);
   c->timer.end(NRD_TK_RESIDUAL, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
   return check_launch(c);
@@ -114,7 +117,7 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.par = par;
   pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2, &io.p2f);
   c->timer.begin(NRD_TK_RESIDUAL, s);
-  launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s);
+  launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s, c->d_z3);
   c->timer.end(NRD_TK_RESIDUAL, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
   c->timer.begin(NRD_TK_PC_SETUP, s);
@@ -167,12 +170,12 @@ int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const 
     io.b = b;
     io.F0 = F0;
     io.eps = c->R.d_res + 0;
-    launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_FD, io, s);
+    launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_FD, io, s, c->d_z3);
     c->timer.end(NRD_TK_JV_FD, s);
     launch_reflux(H, io, ST_FD, s);
   } else {
     c->timer.begin(NRD_TK_JV, s);
-    launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_JV, io, s);
+    launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_JV, io, s, c->d_z3);
     c->timer.end(NRD_TK_JV, s);
     launch_reflux(H, io, ST_JV, s);
   }
@@ -296,6 +299,7 @@ int nrd_set_hierarchy(nrd_ctx* c, int nlevels, const int* nboxes, const int* box
             cudaMalloc(&c->d_cc, 3 * N * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_lam, 2 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_gam, 3 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_z3, (N + G) * sizeof(double)) == cudaSuccess &&
             reducer_init(c->R, (int)N) == NRD_OK;
   if (!ok) {
     free_fields(c);
@@ -336,6 +340,7 @@ int nrd_set_material(nrd_ctx* c, const float* z, cudaStream_t s) {
       cudaSuccess)
     return fail(c, NRD_ECUDA, "copy of z failed");
   launch_ghost_z(c->H, c->d_z, c->d_gz, s);
+  launch_cube(c->H, c->d_z, c->d_gz, c->d_z3, s);
   c->have_mat = true;
   c->pc_ready = false;
   c->lin_ready = false;

@@ -27,25 +27,67 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
   return v;
 }
-// block reduction; result valid in thread 0.  op: 0 sum, 1 min, 2 max
+// block reduction; result valid in thread 0.  op: 0 sum, 1 min, 2 max.
+// A shared-memory tree whose active warps halve (then one warp of shuffles):
+// GB300 issues an FP64 instruction at the same cost however many lanes are
+// active, so this needs 12 FP64 warp instructions for 256 threads where a
+// shuffle tree in every warp needs 45.  sh: at least blockDim.x doubles;
+// blockDim.x a power of two >= 32.
 template <int OP>
 __device__ double block_red(double v, double* sh) {
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  v = (OP == 0) ? warp_sum(v) : (OP == 1 ? warp_min(v) : warp_max(v));
+  const int t = threadIdx.x;
+  __syncthreads();   // sh may still be read by a previous call
+  sh[t] = v;
   __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
+  for (int s = blockDim.x >> 1; s >= 32; s >>= 1) {
+    if (t < s) {
+      const double a = sh[t], b = sh[t + s];
+      sh[t] = (OP == 0) ? a + b : (OP == 1 ? fmin(a, b) : fmax(a, b));
+    }
+    __syncthreads();
+  }
   double r = (OP == 0) ? 0.0 : (OP == 1 ? DBL_MAX : -DBL_MAX);
-  if (w == 0) {
-    r = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : r;
+  if (t < 32) {
+    r = sh[t];
     r = (OP == 0) ? warp_sum(r) : (OP == 1 ? warp_min(r) : warp_max(r));
   }
   return r;
 }
 
+// ---- last-block finishing: every block writes its partials, takes a ticket;
+// the block holding the last ticket sums the partials in block order (a fixed
+// order, so the result does not depend on which block finished last) and
+// resets the ticket counter for the next launch.
+__device__ bool lb_arrive(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  return last;
+}
+
+template <int OP>
+__device__ void lb_finish(const double* part, int nq, int pstride, double* res, int slot,
+                          unsigned* counter) {
+  __shared__ double sh[1024];
+  for (int q = 0; q < nq; q++) {
+    double acc = (OP == 0) ? 0.0 : (OP == 1 ? DBL_MAX : -DBL_MAX);
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+      const double v = __ldcg(&part[(long)b * pstride + q]);
+      acc = (OP == 0) ? acc + v : (OP == 1 ? fmin(acc, v) : fmax(acc, v));
+    }
+    const double r = block_red<OP>(acc, sh);
+    if (threadIdx.x == 0) res[slot + q] = r;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 __global__ void k_wdot(const float* __restrict__ wv, const double* __restrict__ x,
-                       const double* __restrict__ y, int N, double* part) {
-  __shared__ double sh[32];
+                       const double* __restrict__ y, int N, double* part, unsigned* counter,
+                       double* res, int slot) {
+  __shared__ double sh[1024];
   double acc = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     double w = (double)wv[i];
@@ -53,12 +95,13 @@ __global__ void k_wdot(const float* __restrict__ wv, const double* __restrict__ 
   }
   double r = block_red<0>(acc, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
+  if (lb_arrive(counter)) lb_finish<0>(part, 1, 1, res, slot, counter);
 }
 
 // sum (or min/max) of nblk partials per quantity -> res[slot + q]
 template <int OP>
 __global__ void k_finish(const double* part, int nblk, int nq, double* res, int slot) {
-  __shared__ double sh[32];
+  __shared__ double sh[1024];
   for (int q = 0; q < nq; q++) {
     double acc = (OP == 0) ? 0.0 : (OP == 1 ? DBL_MAX : -DBL_MAX);
     for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
@@ -77,7 +120,7 @@ __global__ void k_finish(const double* part, int nblk, int nq, double* res, int 
 __global__ void k_eps_part(const float* __restrict__ wv, const uint8_t* __restrict__ mask,
                            const double* __restrict__ u, const double* __restrict__ v, int N,
                            double* part) {
-  __shared__ double sh[32];
+  __shared__ double sh[1024];
   double suv = 0.0, sv1 = 0.0, svv = 0.0, mneg = DBL_MAX, mpos = DBL_MAX, mu = DBL_MAX;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     if (mask[i] & MASK_COVERED) continue;
@@ -102,7 +145,7 @@ __global__ void k_eps_part(const float* __restrict__ wv, const uint8_t* __restri
 }
 
 __global__ void k_eps_finish(const double* part, int nblk, double u_min, double* res, int slot) {
-  __shared__ double sh[32];
+  __shared__ double sh[1024];
   double q[6];
   for (int k = 0; k < 6; k++) {
     double acc = (k < 3) ? 0.0 : DBL_MAX;
@@ -133,62 +176,12 @@ __global__ void k_eps_finish(const double* part, int nblk, double u_min, double*
 
 __global__ void k_emax(const uint8_t* __restrict__ mask, const double* __restrict__ E, int N,
                        double* part) {
-  __shared__ double sh[32];
+  __shared__ double sh[1024];
   double m = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x)
     if (!(mask[i] & MASK_COVERED)) m = fmax(m, fabs(E[i]));
   double r = block_red<2>(m, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
-}
-
-// res[i] = <w, V_i>, i < NV: w read once, each V_i once; NV is a template
-// parameter so the accumulators stay in registers.
-template <int NV>
-__global__ void k_mdot(const float* __restrict__ wv, const double* __restrict__ w,
-                       const double* __restrict__ V, long stride, int N, double* part) {
-  __shared__ double sh[32];
-  double acc[NV];
-#pragma unroll
-  for (int q = 0; q < NV; q++) acc[q] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    double vol = (double)wv[i];
-    double wE = vol * w[i], wT = vol * w[N + i];
-#pragma unroll
-    for (int q = 0; q < NV; q++) acc[q] += wE * V[q * stride + i] + wT * V[q * stride + N + i];
-  }
-#pragma unroll
-  for (int q = 0; q < NV; q++) {
-    double r = block_red<0>(acc[q], sh);
-    if (threadIdx.x == 0) part[(long)blockIdx.x * NV + q] = r;
-  }
-}
-
-template <int NV>
-void mdot_launch(int nblk, cudaStream_t s, const float* wv, const double* w, const double* V,
-                 long stride, int N, double* part) {
-  k_mdot<NV><<<nblk, RB, 0, s>>>(wv, w, V, stride, N, part);
-}
-
-template <int... I>
-void mdot_dispatch(std::integer_sequence<int, I...>, int nv, int nblk, cudaStream_t s,
-                   const float* wv, const double* w, const double* V, long stride, int N,
-                   double* part) {
-  using Fn = void (*)(int, cudaStream_t, const float*, const double*, const double*, long, int,
-                      double*);
-  static const Fn table[] = {&mdot_launch<I + 1>...};
-  table[nv - 1](nblk, s, wv, w, V, stride, N, part);
-}
-
-__global__ void k_mupdate(int n2, double* __restrict__ w, const double* __restrict__ V, long stride,
-                          int nv, const double* __restrict__ h) {
-  __shared__ double hs[NVMAX];
-  if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
-  __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
-    double s = w[i];
-    for (int q = 0; q < nv; q++) s -= hs[q] * V[q * stride + i];
-    w[i] = s;
-  }
 }
 
 __global__ void k_axpy(int n, double a, const double* __restrict__ x, double* __restrict__ y) {
@@ -233,8 +226,9 @@ __global__ void k_zero_cov(const uint8_t* __restrict__ mask, int N, double* x) {
 // positivity cap of the Newton update (Sec. 4.1 remark): min over leaf
 // components with v < 0 of u/(-v)
 __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restrict__ u,
-                         const double* __restrict__ v, int N, double* part) {
-  __shared__ double sh[32];
+                         const double* __restrict__ v, int N, double* part, unsigned* counter,
+                         double* res, int slot) {
+  __shared__ double sh[1024];
   double m = DBL_MAX;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     if (mask[i] & MASK_COVERED) continue;
@@ -250,17 +244,19 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
   }
   double r = block_red<1>(m, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
+  if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);
 }
 
 // ---- variants whose vector count is a device value (graph-captured solves)
 
 // res[q] = <w, V_q>, q < *jd + add, in groups of 4 vectors (w re-read per
-// group); the per-thread and block summation orders are those of k_mdot.
+// group), a thread-strided sum per block, a block tree, then the last block
+// sums the block partials in block order.
 __global__ void k_mdot_dyn(const float* __restrict__ wv, const double* __restrict__ w,
                            const double* __restrict__ V, long stride, int N, const int* jd,
-                           int add, double* part) {
-  __shared__ double sh[32];
-  const int nv = min(*jd + add, NVMAX);
+                           int add, double* part, unsigned* counter, double* res, int slot) {
+  __shared__ double sh[1024];
+  const int nv = min((jd ? *jd : 0) + add, NVMAX);
   for (int q0 = 0; q0 < nv; q0 += 4) {
     const int nq = min(4, nv - q0);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -278,32 +274,89 @@ __global__ void k_mdot_dyn(const float* __restrict__ wv, const double* __restric
       __syncthreads();
     }
   }
+  if (lb_arrive(counter)) lb_finish<0>(part, nv, NVMAX, res, slot, counter);
 }
 
-__global__ void k_finish_dyn(const double* part, int nblk, const int* jd, int add, double* res,
-                             int slot) {
-  __shared__ double sh[32];
-  const int nq = min(*jd + add, NVMAX);
-  for (int q = 0; q < nq; q++) {
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) acc += part[(long)b * NVMAX + q];
-    double r = block_red<0>(acc, sh);
-    if (threadIdx.x == 0) res[slot + q] = r;
-    __syncthreads();
-  }
-}
-
-__global__ void k_mupdate_dyn(int n2, double* __restrict__ w, const double* __restrict__ V,
-                              long stride, const int* jd, int add, const double* __restrict__ h) {
+// CGS pass 2 fused with pass 1's update: w <- w - sum_q h_q V_q, then the
+// partial dots <w, V_q> (volume weighted) of the updated w; q < *jd + add.
+// The first 8 dots ride on the update; more are formed from the stored w.
+__global__ void k_cgs_upd_dots(const float* __restrict__ wv, double* __restrict__ w,
+                               const double* __restrict__ V, long stride, int N, const int* jd,
+                               int add, const double* __restrict__ h, double* part,
+                               unsigned* counter, double* res, int slot) {
+  __shared__ double sh[1024];
   __shared__ double hs[NVMAX];
-  const int nv = min(*jd + add, NVMAX);
+  const int nv = min((jd ? *jd : 0) + add, NVMAX);
   if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += gridDim.x * blockDim.x) {
-    double s = w[i];
-    for (int q = 0; q < nv; q++) s -= hs[q] * V[q * stride + i];
-    w[i] = s;
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; q++) acc[q] = 0.0;
+  const int n8 = min(nv, 8);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double sE = w[i], sT = w[N + i];
+    for (int q = 0; q < nv; q++) {
+      sE -= hs[q] * V[q * stride + i];
+      sT -= hs[q] * V[q * stride + N + i];
+    }
+    w[i] = sE;
+    w[N + i] = sT;
+    const double vol = (double)wv[i];
+    const double wE = vol * sE, wT = vol * sT;
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+      if (q < n8) acc[q] += wE * V[q * stride + i] + wT * V[q * stride + N + i];
   }
+  for (int q = 0; q < n8; q++) {
+    const double r = block_red<0>(acc[q], sh);
+    if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + q] = r;
+    __syncthreads();
+  }
+  for (int q0 = 8; q0 < nv; q0 += 8) {
+    const int nq = min(8, nv - q0);
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc[q] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+      const double vol = (double)wv[i];
+      const double wE = vol * w[i], wT = vol * w[N + i];
+#pragma unroll
+      for (int q = 0; q < 8; q++)
+        if (q < nq)
+          acc[q] += wE * V[(q0 + q) * stride + i] + wT * V[(q0 + q) * stride + N + i];
+    }
+    for (int q = 0; q < nq; q++) {
+      const double r = block_red<0>(acc[q], sh);
+      if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + q0 + q] = r;
+      __syncthreads();
+    }
+  }
+  if (lb_arrive(counter)) lb_finish<0>(part, nv, NVMAX, res, slot, counter);
+}
+
+// CGS pass 2's update fused with the squared norm of the result
+__global__ void k_cgs_upd_norm(const float* __restrict__ wv, double* __restrict__ w,
+                               const double* __restrict__ V, long stride, int N, const int* jd,
+                               int add, const double* __restrict__ h, double* part,
+                               unsigned* counter, double* res, int slot) {
+  __shared__ double sh[1024];
+  __shared__ double hs[NVMAX];
+  const int nv = min((jd ? *jd : 0) + add, NVMAX);
+  if (threadIdx.x < nv) hs[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double sE = w[i], sT = w[N + i];
+    for (int q = 0; q < nv; q++) {
+      sE -= hs[q] * V[q * stride + i];
+      sT -= hs[q] * V[q * stride + N + i];
+    }
+    w[i] = sE;
+    w[N + i] = sT;
+    acc += (double)wv[i] * (sE * sE + sT * sT);
+  }
+  const double r = block_red<0>(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+  if (lb_arrive(counter)) lb_finish<0>(part, 1, 1, res, slot, counter);
 }
 
 __global__ void k_lincomb_dyn(int n, double* __restrict__ x, const double* __restrict__ Z,
@@ -326,6 +379,243 @@ __global__ void k_axpy_dev(int n, const double* __restrict__ a, const double* __
     y[i] += av * x[i];
 }
 
+// ---- CGS2 of one Arnoldi step as one cooperative kernel
+// Grid-wide barrier for a cooperative launch (all blocks resident).  The
+// wait is bounded: after kSpinLimit polls the block records an error in
+// err[0] and carries on, so a launch that is not co-resident cannot hang.
+constexpr long kSpinLimit = 1L << 24;
+
+__device__ void grid_barrier(unsigned* bar, int* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long it = 0;
+      while (*gen == g) {
+        if (++it > kSpinLimit) {
+          atomicOr(err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// every block sums the nq block partials (stride NVMAX) in block order into
+// out[0..nq) (shared); the same order in every block, so all agree
+__device__ void coop_reduce(const double* part, int nq, double* out, double* sh) {
+  for (int q = 0; q < nq; q++) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      acc += __ldcg(&part[(long)b * NVMAX + q]);
+    const double r = block_red<0>(acc, sh);
+    if (threadIdx.x == 0) out[q] = r;
+    __syncthreads();
+  }
+}
+
+// Volume weights of a level-major vector whose covered cells are zero (every
+// Krylov vector, F and the Newton directions): the leaf-cell volume is
+// constant on a level, so a weighted dot is, per level, an FMA chain over
+// the level's cells times the level volume.  A thread's cells increase, so
+// it meets the level boundaries in order.
+struct LevW {
+  int L;
+  int end[NRD_MAX_LEVELS];     // one past the last cell of level l
+  double w[NRD_MAX_LEVELS];    // cell volume of level l
+};
+
+// Orthogonalisation of w against the nv = (jd ? *jd : 0) + add columns of V
+// (classical Gram-Schmidt with selective reorthogonalisation, the criterion
+// of Daniel, Gragg, Kaufman and Stewart): h1 = V^T W w and s0 = w^T W w in
+// one pass; w -= V h1 and s1 = w^T W w in the next; only when s1 < s0 / 2
+// (the norm fell below 1/sqrt(2) of its value) a second pass
+// h2 = V^T W w, w -= V h2, s2 = w^T W w.  Then V[nv] = w / sqrt(s).
+// res[slot_h1 + q] = h1_q, res[slot_h2 + q] = h2_q (0 without the second
+// pass), res[slot_nrm] = s.  Block partials ping-pong between pa and pb
+// (stride NVMAX) so each reduction needs one grid barrier.
+__global__ void __launch_bounds__(256) k_orth_coop(LevW lw, double* __restrict__ w,
+                                                   double* __restrict__ V, long stride, int N,
+                                                   const int* jd, int add, double* pa, double* pb,
+                                                   unsigned* bar, int* err, double* res,
+                                                   int slot_h1, int slot_h2, int slot_nrm) {
+  __shared__ double sh[1024];
+  __shared__ double h[NVMAX];
+  __shared__ double sred[NVMAX];
+  const int nv = min((jd ? *jd : 0) + add, NVMAX - 1);
+  const int T = gridDim.x * blockDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int l0 = 0;
+  while (l0 < lw.L - 1 && i0 >= lw.end[l0]) l0++;
+
+  // dots of w with V_q0 .. V_q0+nq-1 (nq <= 4) and, if withn, with itself;
+  // partials to part[blockIdx.x * NVMAX + col0 + q]
+  auto dots = [&](int q0, int nq, bool withn, double* part, int col0) {
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int l = l0, lend = lw.end[l0];
+    double lwt = lw.w[l0];
+    for (int i = i0; i < N; i += T) {
+      while (i >= lend) {
+#pragma unroll
+        for (int q = 0; q < 5; q++) {
+          tot[q] = fma(lwt, acc[q], tot[q]);
+          acc[q] = 0.0;
+        }
+        l++;
+        lend = lw.end[l];
+        lwt = lw.w[l];
+      }
+      const double wE = w[i], wT = w[N + i];
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (q < nq)
+          acc[q] = fma(wE, V[(q0 + q) * stride + i], fma(wT, V[(q0 + q) * stride + N + i], acc[q]));
+      if (withn) acc[4] = fma(wE, wE, fma(wT, wT, acc[4]));
+    }
+#pragma unroll
+    for (int q = 0; q < 5; q++) tot[q] = fma(lwt, acc[q], tot[q]);
+    for (int q = 0; q < nq; q++) {
+      const double r = block_red<0>(tot[q], sh);
+      if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + col0 + q] = r;
+    }
+    if (withn) {
+      const double r = block_red<0>(tot[4], sh);
+      if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + col0 + nq] = r;
+    }
+  };
+  // w -= V hq; returns this thread's share of w^T W w (level-weighted)
+  auto update_norm = [&](const double* hq) -> double {
+    double acc = 0.0, tot = 0.0;
+    int l = l0, lend = lw.end[l0];
+    double lwt = lw.w[l0];
+    for (int i = i0; i < N; i += T) {
+      while (i >= lend) {
+        tot = fma(lwt, acc, tot);
+        acc = 0.0;
+        l++;
+        lend = lw.end[l];
+        lwt = lw.w[l];
+      }
+      double sE = w[i], sT = w[N + i];
+      for (int q = 0; q < nv; q++) {
+        sE = fma(-hq[q], V[q * stride + i], sE);
+        sT = fma(-hq[q], V[q * stride + N + i], sT);
+      }
+      w[i] = sE;
+      w[N + i] = sT;
+      acc = fma(sE, sE, fma(sT, sT, acc));
+    }
+    return fma(lwt, acc, tot);
+  };
+  // sums of the block partials in block order (the same in every block)
+  auto reduce = [&](const double* part, int nq, double* out) {
+    for (int q = 0; q < nq; q++) {
+      double acc = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        acc += __ldcg(&part[(long)b * NVMAX + q]);
+      const double r = block_red<0>(acc, sh);
+      if (threadIdx.x == 0) out[q] = r;
+    }
+    __syncthreads();
+  };
+
+  // pass 1: h1 and s0 (partials in pa: columns 0..nv-1, nv)
+  for (int q0 = 0; q0 < nv; q0 += 4) dots(q0, min(4, nv - q0), q0 + 4 >= nv, pa, q0);
+  if (nv == 0) dots(0, 0, true, pa, 0);
+  grid_barrier(bar, err);
+  reduce(pa, nv + 1, sred);            // sred[0..nv-1] = h1, sred[nv] = s0
+  if (threadIdx.x < nv) h[threadIdx.x] = sred[threadIdx.x];
+  const double s0 = sred[nv];
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < nv) {
+    res[slot_h1 + threadIdx.x] = h[threadIdx.x];
+    res[slot_h2 + threadIdx.x] = 0.0;
+  }
+  // w -= V h1, s1 (partials in pb)
+  {
+    const double r = block_red<0>(update_norm(h), sh);
+    if (threadIdx.x == 0) pb[(long)blockIdx.x * NVMAX] = r;
+  }
+  grid_barrier(bar, err);
+  reduce(pb, 1, sred);
+  double s = sred[0];
+  if (s < 0.5 * s0) {
+    // second pass: h2 (partials in pa; every block read pa before the
+    // barrier above), w -= V h2, s2 (partials in pb, read before the next)
+    for (int q0 = 0; q0 < nv; q0 += 4) dots(q0, min(4, nv - q0), false, pa, q0);
+    grid_barrier(bar, err);
+    reduce(pa, nv, sred);
+    if (threadIdx.x < nv) h[threadIdx.x] = sred[threadIdx.x];
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x < nv) res[slot_h2 + threadIdx.x] = h[threadIdx.x];
+    const double r = block_red<0>(update_norm(h), sh);
+    if (threadIdx.x == 0) pa[(long)blockIdx.x * NVMAX + NVMAX - 1] = r;
+    grid_barrier(bar, err);
+    double t2 = 0.0;
+    {
+      double acc = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+        acc += __ldcg(&pa[(long)b * NVMAX + NVMAX - 1]);
+      t2 = block_red<0>(acc, sh);
+      if (threadIdx.x == 0) sred[0] = t2;
+      __syncthreads();
+    }
+    s = sred[0];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) res[slot_nrm] = s;
+  // V[nv] = w / sqrt(s) (the scale once per block: FP64 sqrt and division
+  // cost many FP64 issue slots)
+  __shared__ double s_sc;
+  if (threadIdx.x == 0) {
+    const double d = sqrt(s);
+    s_sc = (d > 0.0) ? 1.0 / d : 0.0;
+  }
+  __syncthreads();
+  const double sc = s_sc;
+  double* vn = V + (long)nv * stride;
+  for (int i = i0; i < N; i += T) {
+    vn[i] = sc * w[i];
+    vn[N + i] = sc * w[N + i];
+  }
+}
+
+// level-weighted <x, y> over both fields for vectors that vanish on covered
+// cells; last-block finish into res[slot]
+__global__ void k_wdot_lv(LevW lw, const double* __restrict__ x, const double* __restrict__ y,
+                          int N, double* part, unsigned* counter, double* res, int slot) {
+  __shared__ double sh[1024];
+  const int T = gridDim.x * blockDim.x;
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = 0;
+  while (l < lw.L - 1 && i0 >= lw.end[l]) l++;
+  int lend = lw.end[l];
+  double lwt = lw.w[l];
+  double acc = 0.0, tot = 0.0;
+  for (int i = i0; i < N; i += T) {
+    while (i >= lend) {
+      tot = fma(lwt, acc, tot);
+      acc = 0.0;
+      l++;
+      lend = lw.end[l];
+      lwt = lw.w[l];
+    }
+    acc = fma(x[i], y[i], fma(x[N + i], y[N + i], acc));
+  }
+  tot = fma(lwt, acc, tot);
+  const double r = block_red<0>(tot, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+  if (lb_arrive(counter)) lb_finish<0>(part, 1, 1, res, slot, counter);
+}
+
 int grid_for(long n) {
   long b = (n + RB - 1) / RB;
   return (int)std::max(1L, std::min(b, (long)152 * 8));
@@ -338,7 +628,25 @@ int reducer_init(Reducer& R, int N) {
   if (cudaMalloc(&R.d_part, sizeof(double) * (size_t)R.nblk * NVMAX) != cudaSuccess) return NRD_ENOMEM;
   if (cudaMalloc(&R.d_res, sizeof(double) * 256) != cudaSuccess) return NRD_ENOMEM;
   if (cudaMallocHost(&R.h_res, sizeof(double) * 256) != cudaSuccess) return NRD_ENOMEM;
+  if (cudaMalloc(&R.d_count, sizeof(unsigned)) != cudaSuccess) return NRD_ENOMEM;
+  if (cudaMalloc(&R.d_bar, 2 * sizeof(unsigned)) != cudaSuccess) return NRD_ENOMEM;
+  if (cudaMalloc(&R.d_part2, sizeof(double) * (size_t)R.nblk * NVMAX) != cudaSuccess)
+    return NRD_ENOMEM;
+  if (cudaMalloc(&R.d_err, sizeof(int)) != cudaSuccess) return NRD_ENOMEM;
   cudaMemset(R.d_res, 0, sizeof(double) * 256);
+  cudaMemset(R.d_count, 0, sizeof(unsigned));
+  cudaMemset(R.d_bar, 0, 2 * sizeof(unsigned));
+  cudaMemset(R.d_err, 0, sizeof(int));
+  // cooperative CGS2: every block resident, at most the partial buffer's rows
+  {
+    int dev = 0, nsm = 0, per = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_orth_coop, RB, 0);
+    int want = std::max(1, (N + RB - 1) / RB);
+    R.coop_blocks = coop ? std::min(std::min(nsm * std::min(per, 4), want), R.nblk) : 0;
+  }
   return NRD_OK;
 }
 
@@ -346,13 +654,20 @@ void reducer_free(Reducer& R) {
   if (R.d_part) cudaFree(R.d_part);
   if (R.d_res) cudaFree(R.d_res);
   if (R.h_res) cudaFreeHost(R.h_res);
+  if (R.d_count) cudaFree(R.d_count);
+  if (R.d_bar) cudaFree(R.d_bar);
+  if (R.d_part2) cudaFree(R.d_part2);
+  R.d_part2 = nullptr;
+  if (R.d_err) cudaFree(R.d_err);
   R.d_part = R.d_res = R.h_res = nullptr;
+  R.d_count = nullptr;
+  R.d_bar = nullptr;
+  R.d_err = nullptr;
 }
 
 void launch_wdot(const Hier& H, Reducer& R, const double* x, const double* y, int slot,
                  cudaStream_t s) {
-  k_wdot<<<R.nblk, RB, 0, s>>>(H.d_wvol, x, y, H.N, R.d_part);
-  k_finish<0><<<1, 1024, 0, s>>>(R.d_part, R.nblk, 1, R.d_res, slot);
+  k_wdot<<<R.nblk, RB, 0, s>>>(H.d_wvol, x, y, H.N, R.d_part, R.d_count, R.d_res, slot);
 }
 
 void launch_fd_eps(const Hier& H, Reducer& R, const double* u, const double* v, double u_min,
@@ -364,18 +679,6 @@ void launch_fd_eps(const Hier& H, Reducer& R, const double* u, const double* v, 
 void launch_emax(const Hier& H, Reducer& R, const double* E, int slot, cudaStream_t s) {
   k_emax<<<R.nblk, RB, 0, s>>>(H.d_mask, E, H.N, R.d_part);
   k_finish<2><<<1, 1024, 0, s>>>(R.d_part, R.nblk, 1, R.d_res, slot);
-}
-
-void launch_mdot(const Hier& H, Reducer& R, const double* w, const double* V, long stride, int nv,
-                 int slot, cudaStream_t s) {
-  mdot_dispatch(std::make_integer_sequence<int, NVMAX>{}, nv, R.nblk, s, H.d_wvol, w, V, stride,
-                H.N, R.d_part);
-  k_finish<0><<<1, 1024, 0, s>>>(R.d_part, R.nblk, nv, R.d_res, slot);
-}
-
-void launch_mupdate(int n2, double* w, const double* V, long stride, int nv, const double* h,
-                    cudaStream_t s) {
-  k_mupdate<<<grid_for(n2), RB, 0, s>>>(n2, w, V, stride, nv, h);
 }
 
 void launch_axpy(int n, double a, const double* x, double* y, cudaStream_t s) {
@@ -397,19 +700,56 @@ void launch_zero_covered(const Hier& H, double* x, cudaStream_t s) {
 
 void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v, int slot,
                     cudaStream_t s) {
-  k_poscap<<<R.nblk, RB, 0, s>>>(H.d_mask, u, v, H.N, R.d_part);
-  k_finish<1><<<1, 1024, 0, s>>>(R.d_part, R.nblk, 1, R.d_res, slot);
+  k_poscap<<<R.nblk, RB, 0, s>>>(H.d_mask, u, v, H.N, R.d_part, R.d_count, R.d_res, slot);
 }
 
 void launch_mdot_dyn(const Hier& H, Reducer& R, const double* w, const double* V, long stride,
                      const int* jd, int add, int slot, cudaStream_t s) {
-  k_mdot_dyn<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, H.N, jd, add, R.d_part);
-  k_finish_dyn<<<1, 1024, 0, s>>>(R.d_part, R.nblk, jd, add, R.d_res, slot);
+  k_mdot_dyn<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, H.N, jd, add, R.d_part, R.d_count,
+                                   R.d_res, slot);
 }
 
-void launch_mupdate_dyn(int n2, double* w, const double* V, long stride, const int* jd, int add,
-                        const double* h, cudaStream_t s) {
-  k_mupdate_dyn<<<grid_for(n2), RB, 0, s>>>(n2, w, V, stride, jd, add, h);
+LevW levw_of(const Hier& H) {
+  LevW lw;
+  lw.L = H.L;
+  for (int l = 0; l < NRD_MAX_LEVELS; l++) {
+    lw.end[l] = (l < H.L) ? H.lev[l].off + H.lev[l].ncell : H.N;
+    lw.w[l] = (l < H.L) ? H.lev[l].h[0] * H.lev[l].h[1] * H.lev[l].h[2] : 0.0;
+  }
+  return lw;
+}
+
+int launch_cgs2_coop(const Hier& H, Reducer& R, double* w, double* V, long stride, const int* jd,
+                     int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s) {
+  if (R.coop_blocks <= 0) return NRD_ECUDA;
+  LevW lw = levw_of(H);
+  int N = H.N;
+  double* pa = R.d_part;
+  double* pb = R.d_part2;
+  unsigned* bar = R.d_bar;
+  int* err = R.d_err;
+  double* res = R.d_res;
+  void* args[] = {(void*)&lw, (void*)&w, (void*)&V, (void*)&stride, (void*)&N, (void*)&jd,
+                  (void*)&add, (void*)&pa, (void*)&pb, (void*)&bar, (void*)&err, (void*)&res,
+                  (void*)&slot_h1, (void*)&slot_h2, (void*)&slot_nrm};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_orth_coop, dim3(R.coop_blocks),
+                                              dim3(RB), args, 0, s);
+  return e == cudaSuccess ? NRD_OK : NRD_ECUDA;
+}
+
+void launch_wdot_lv(const Hier& H, Reducer& R, const double* x, const double* y, int slot,
+                    cudaStream_t s) {
+  k_wdot_lv<<<R.nblk, RB, 0, s>>>(levw_of(H), x, y, H.N, R.d_part, R.d_count, R.d_res, slot);
+}
+
+void launch_cgs2(const Hier& H, Reducer& R, double* w, const double* V, long stride,
+                 const int* jd, int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s) {
+  k_mdot_dyn<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, H.N, jd, add, R.d_part, R.d_count,
+                                   R.d_res, slot_h1);
+  k_cgs_upd_dots<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, H.N, jd, add, R.d_res + slot_h1,
+                                       R.d_part, R.d_count, R.d_res, slot_h2);
+  k_cgs_upd_norm<<<R.nblk, RB, 0, s>>>(H.d_wvol, w, V, stride, H.N, jd, add, R.d_res + slot_h2,
+                                       R.d_part, R.d_count, R.d_res, slot_nrm);
 }
 
 void launch_lincomb_dyn(int n, double* x, const double* Z, long stride, const int* jd,

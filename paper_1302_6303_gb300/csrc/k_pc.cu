@@ -652,10 +652,20 @@ struct BoxRaw {
   long NA, gbase, cell0, AF;
 };
 
-__global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_raw) {
+// fused with the scaling of the coarse level:
+// A = beta C / h^2 on interior faces, beta 2 D_b / (h (4 D_b + h)) on Robin
+// faces of E, 0 elsewhere; rh2 = 1/h^2 per axis of the coarse level.
+template <class P>
+__global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_raw,
+                              const int* gtype_box, const double* dbeta, double hx, double hy,
+                              double hz, double rh2x, double rh2y, double rh2z, P* A) {
   const int fld = blockIdx.y;
   const double* cf = Cf + fld * F.AF;
   double* cc = Cc_raw + fld * Cc.AF;
+  P* Af = A + fld * Cc.AF;
+  const double beta = *dbeta;
+  const double hh[3] = {hx, hy, hz};
+  const double bh2[3] = {beta * rh2x, beta * rh2y, beta * rh2z};
   const long ncc = (long)Cc.n[0] * Cc.n[1] * Cc.n[2];
   for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncc;
        c += (long)gridDim.x * blockDim.x) {
@@ -678,6 +688,7 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
             s += cf[d * F.NA + fi];
           }
         cc[d * Cc.NA + c] = 0.25 * s;
+        Af[d * Cc.NA + c] = (P)(0.25 * s * bh2[d]);
       }
       for (int sd = 0; sd < 2; sd++) {
         bool at = sd ? (q[d] == Cc.n[d] - 1) : (q[d] == 0);
@@ -689,41 +700,11 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
             int p1 = 2 * q[t1] + a, p2 = 2 * q[t2] + b;
             s += cf[F.gbase + F.fo[f] + p1 + F.n[t1] * p2];
           }
-        cc[Cc.gbase + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2]] = 0.25 * s;
-      }
-    }
-  }
-}
-
-template <class P>
-__global__ void k_box_scale(BoxRaw B, const double* Craw, const int* gtype_box,
-                            const double* dbeta, double hx, double hy, double hz, P* A) {
-  const double beta = *dbeta;
-  const int fld = blockIdx.y;
-  const double* C = Craw + fld * B.AF;
-  P* Af = A + fld * B.AF;
-  const long nc = (long)B.n[0] * B.n[1] * B.n[2];
-  const double hh[3] = {hx, hy, hz};
-  const double bh2[3] = {beta / (hx * hx), beta / (hy * hy), beta / (hz * hz)};
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < nc;
-       c += (long)gridDim.x * blockDim.x) {
-    int q[3];
-    q[0] = (int)(c % B.n[0]);
-    long r = c / B.n[0];
-    q[1] = (int)(r % B.n[1]);
-    q[2] = (int)(r / B.n[1]);
-    for (int d = 0; d < 3; d++) {
-      double h = hh[d];
-      int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-      if (q[d] > 0) Af[d * B.NA + c] = (P)(C[d * B.NA + c] * bh2[d]);
-      for (int sd = 0; sd < 2; sd++) {
-        bool at = sd ? (q[d] == B.n[d] - 1) : (q[d] == 0);
-        if (!at) continue;
-        int f = 2 * d + sd;
-        long g = B.gbase + B.fo[f] + q[t1] + B.n[t1] * q[t2];
+        const long g = Cc.gbase + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2];
+        cc[g] = 0.25 * s;
         double v = 0.0;
         if (gtype_box[f] == 1 && fld == 0) {
-          double Db = C[g];
+          const double Db = 0.25 * s, h = hh[d];
           v = beta * 2.0 * Db / (h * (4.0 * Db + h));
         }
         Af[g] = (P)v;
@@ -1127,17 +1108,6 @@ void scale_all(PcState* ps, const Hier& H, SetupArgs& a, cudaStream_t s) {
   k_scale_hier<P><<<gt, BS, 0, s>>>(a, nullptr, (P*)ps->A);
 }
 
-template <class P>
-void scale_boxes(PcState* ps, cudaStream_t s) {
-  for (int m = 1; m < ps->nmg; m++) {
-    const BoxRaw& B = ps->box[m];
-    long nc = (long)B.n[0] * B.n[1] * B.n[2];
-    dim3 g(g1(nc), 2);
-    k_box_scale<P><<<g, BS, 0, s>>>(B, ps->bCraw[m], ps->bgt, ps->d_beta, ps->bh[m][0],
-                                    ps->bh[m][1], ps->bh[m][2], (P*)ps->bA[m]);
-  }
-}
-
 }  // namespace
 
 int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err) {
@@ -1336,14 +1306,20 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
     const BoxRaw& C = ps->box[m];
     long nc = (long)C.n[0] * C.n[1] * C.n[2];
     dim3 g(g1(nc), 2);
-    k_box_coarsen<<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m]);
+    const double* hb = ps->bh[m];
+    const double r2[3] = {1.0 / (hb[0] * hb[0]), 1.0 / (hb[1] * hb[1]), 1.0 / (hb[2] * hb[2])};
+    if (ps->prec == NRD_PC_F32)
+      k_box_coarsen<float><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta, hb[0],
+                                            hb[1], hb[2], r2[0], r2[1], r2[2],
+                                            (float*)ps->bA[m]);
+    else
+      k_box_coarsen<double><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta, hb[0],
+                                             hb[1], hb[2], r2[0], r2[1], r2[2],
+                                             (double*)ps->bA[m]);
   }
-  if (ps->prec == NRD_PC_F32) {
-    if (!from_lin) scale_all<float>(ps, H, a, s);
-    scale_boxes<float>(ps, s);
-  } else {
-    if (!from_lin) scale_all<double>(ps, H, a, s);
-    scale_boxes<double>(ps, s);
+  if (!from_lin) {
+    if (ps->prec == NRD_PC_F32) scale_all<float>(ps, H, a, s);
+    else scale_all<double>(ps, H, a, s);
   }
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }

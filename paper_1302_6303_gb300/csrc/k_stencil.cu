@@ -92,6 +92,7 @@ struct StArgs {
   const uint8_t* gtype;
   const float* z;     // material z per cell
   const float* gz;    // z of every ghost cell
+  const double* z3;   // z^3 of cells then ghosts (FP64), or null
   int ntiles, N, G;
   double k;       // D_T = k T^(5/2)
   double cL;      // limiter constant: 4 (Wilson form) or 2 (printed form)
@@ -126,29 +127,43 @@ __device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double
 // of Phi_T w.r.t. T_a, T_b (sign(0) = 0).
 struct FaceLin {
   double PE, PT, CE, CT, aEa, aEb, aT, bTa, bTb, aZ;
+  double X, T25;   // CE = X h, CT = k T25
 };
 
-// 1/x from the FP32 reciprocal refined by one Newton-Raphson step
-// (r1 = r0 + r0 (1 - x r0); relative error ~ the square of the seed's,
-// about 2^-46; see e.g. Muller et al., Handbook of Floating-Point
-// Arithmetic).  Outside the FP32 normal range the correctly rounded 1/x.
+// 1/x from the PTX approximate FP64 reciprocal (rcp.approx.ftz.f64, a
+// seed of about 20 good bits) refined with the second-order series of the
+// correction: with e = 1 - x r0, 1/x = r0 / (1 - e) = r0 (1 + e + e^2 + ...),
+// so r1 = r0 + r0 (e + e^2) leaves a relative error of e^3 (iterative
+// refinement of reciprocals, see e.g. Muller et al., Handbook of
+// Floating-Point Arithmetic): about 1e-18 before rounding.  For normal
+// x > 0 below 1e300; elsewhere the correctly rounded 1/x.
+__device__ __forceinline__ double rcp_approx(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
+__device__ __forceinline__ double rsqrt_approx(double x) {
+  double r;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  return r;
+}
 __device__ __forceinline__ double rcp_nr(double x) {
-  const float xf = (float)x;
-  const float ax = fabsf(xf);
-  if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
-  const double r = (double)__frcp_rn(xf);
-  return fma(r, fma(-x, r, 1.0), r);
+  if (!(x > 1e-300 && x < 1e300)) return 1.0 / x;
+  const double r = rcp_approx(x);
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
-// 1/sqrt(x) from the FP32 reciprocal square root refined by one
-// Newton-Raphson step (y1 = y0 + y0 (1 - x y0^2) / 2; relative error about
-// 1.5 times the square of the seed's, below 1e-13).  x > 0; outside the
-// FP32 normal range the correctly rounded 1/sqrt(x).
+// 1/sqrt(x) from the PTX approximate FP64 reciprocal square root
+// (rsqrt.approx.ftz.f64) refined with the second-order series: with
+// e = 1 - x y0^2, 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3 e^2/8 + ...),
+// a relative error of about (5/16) e^3 before rounding.  For normal x > 0
+// below 1e300; elsewhere the correctly rounded 1/sqrt(x).
 __device__ __forceinline__ double rsqrt_nr(double x) {
-  const float xf = (float)x;
-  if (!(xf > 1e-36f && xf < 1e36f)) return 1.0 / sqrt(x);
-  const double y = (double)rsqrtf(xf);
-  return fma(0.5 * y, fma(-x * y, y, 1.0), y);
+  if (!(x > 1e-300 && x < 1e300)) return 1.0 / sqrt(x);
+  const double y = rsqrt_approx(x);
+  const double e = fma(-x * y, y, 1.0);
+  return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
 // Face flux of flux_val and its partial derivatives at one iterate (the
@@ -178,6 +193,7 @@ __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, dou
   const double X = 2.0 * Tf3 * S * rden;
   const double PE = X * dE;
   r.PE = PE;
+  r.X = X;
   r.CE = X * h;
   const double A = PE * hz;
   const double B = PE * lt;
@@ -190,6 +206,7 @@ __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, dou
   const double y = rsqrt_nr(Tf);
   const double T15 = Tf2 * y;     // Tf^(3/2)
   const double T25 = Tf * T15;    // Tf^(5/2)
+  r.T25 = T25;
   const double dT = Tb - Ta;
   r.CT = k * T25;
   const double khT25 = kh * T25;
@@ -293,6 +310,14 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     eps = *io.eps;
     reps = 1.0 / eps;
   }
+  // FP32 scale factors of the V-cycle coefficients per level and axis:
+  // beta C_E / h^2 = X (beta / h), beta C_T / h^2 = T^(5/2) (beta k / h^2)
+  __shared__ float s_bh[LIN ? NRD_MAX_LEVELS * 3 : 1], s_bk[LIN ? NRD_MAX_LEVELS * 3 : 1];
+  if (LIN && threadIdx.x < NRD_MAX_LEVELS * 3) {
+    const double rh = A.lh.rh[threadIdx.x / 3][threadIdx.x % 3];
+    s_bh[threadIdx.x] = (float)(betav * rh);
+    s_bk[threadIdx.x] = (float)(betav * A.k * rh * rh);
+  }
 
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
     const TileDev tile = A.tiles[t];
@@ -342,7 +367,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         int idx = P.off + i + nx * (j + ny * k);
         e = io.u[idx];
         tt = io.u[N + idx];
-        z = (double)A.z[idx];
+        z = A.z3 ? A.z3[idx] : (double)A.z[idx];
         if (MODE == ST_JV || MODE == ST_FD) {
           ve = io.v[idx];
           vt = io.v[N + idx];
@@ -357,7 +382,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         int gi = P.goff + P.fo[f] + a + nt1 * b;
         e = io.gu[gi];
         tt = io.gu[G + gi];
-        z = (double)A.gz[gi];
+        z = A.z3 ? A.z3[(long)N + gi] : (double)A.gz[gi];
         if (MODE == ST_JV || MODE == ST_FD) {
           ve = io.gv[gi];
           vt = io.gv[G + gi];
@@ -369,7 +394,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
       sE[hh] = e;
       sT[hh] = tt;
-      sZ[hh] = z * z * z;
+      sZ[hh] = A.z3 ? z : z * z * z;
       if (TAN) {
         svE[hh] = ve;
         svT[hh] = vt;
@@ -487,9 +512,15 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[5 * NS + fslot] = L.aZ;
           io.craw[fslot] = L.CE;
           io.craw[NS + fslot] = L.CT;
-          const double rhd = A.lh.rh[lvl][dir];
-          const double b2 = io.par ? betav * rhd * rhd : A.lh.bh2[lvl][dir];
-          put_scaled(io, NS, fslot, L.CE * b2, L.CT * b2);
+          if (io.a32) {
+            io.a32[fslot] = (float)L.X * s_bh[3 * lvl + dir];
+            io.a32[NS + fslot] = (float)L.T25 * s_bk[3 * lvl + dir];
+          } else {
+            const double rhd = A.lh.rh[lvl][dir];
+            const double b2 = io.par ? betav * rhd * rhd : A.lh.bh2[lvl][dir];
+            io.a64[fslot] = L.CE * b2;
+            io.a64[NS + fslot] = L.CT * b2;
+          }
         } else {
           flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, PE, PT);
         }
@@ -763,6 +794,7 @@ void dispatch_tile(const StArgs& a, int tx, int ty, int tz, cudaStream_t s) {
   else if (tx == 16 && ty == 8 && tz == 8) run_stencil<MODE, 16, 8, 8>(a, s);
   else if (tx == 16 && ty == 4 && tz == 4) run_stencil<MODE, 16, 4, 4>(a, s);
   else if (tx == 8 && ty == 8 && tz == 8) run_stencil<MODE, 8, 8, 8>(a, s);
+  else if (tx == 8 && ty == 8 && tz == 4) run_stencil<MODE, 8, 8, 4>(a, s);
   else run_stencil<MODE, 32, 4, 4>(a, s);
 }
 
@@ -786,14 +818,28 @@ void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, con
   k_ghost_fill<<<blocks_for(H.G, 256), 256, 0, s>>>(a, u, g, nonlinear);
 }
 
+__global__ void k_cube(const float* z, long n, double* z3) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const double v = (double)z[i];
+    z3[i] = v * v * v;
+  }
+}
+
+void launch_cube(const Hier& H, const float* z, const float* gz, double* z3, cudaStream_t s) {
+  k_cube<<<blocks_for(H.N, 256), 256, 0, s>>>(z, H.N, z3);
+  if (H.G) k_cube<<<blocks_for(H.G, 256), 256, 0, s>>>(gz, H.G, z3 + H.N);
+}
+
 void launch_ghost_z(const Hier& H, const float* z, float* gz, cudaStream_t s) {
   if (H.G == 0) return;
   k_ghost_z<<<blocks_for(H.G, 256), 256, 0, s>>>(H.d_gzsrc, z, gz, H.G);
 }
 
 void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const float* gz,
-                    int mode, const StencilIO& io, cudaStream_t s) {
+                    int mode, const StencilIO& io, cudaStream_t s, const double* z3) {
   StArgs a;
+  a.z3 = z3;
   a.tiles = H.d_tiles;
   a.patches = H.d_patches;
   a.mask = H.d_mask;

@@ -143,7 +143,7 @@ __global__ void k_resid_g(int n, const double* F, const double* Ax, double* r) {
 
 // Hessenberg column j from the two CGS passes, Givens update, residual
 // estimate |g_{j+1}|; j and the iteration count advance.
-__global__ void k_arnoldi_g(NkCtl* c, SmallG S, int m, const double* res,
+__global__ void k_arnoldi_g(NkCtl* c, SmallG S, int m, const double* res, const int* err,
                             cudaGraphConditionalHandle hA) {
   const int j = c->j;
   double* col = S.Hm + (size_t)(m + 1) * j;
@@ -168,7 +168,7 @@ __global__ void k_arnoldi_g(NkCtl* c, SmallG S, int m, const double* res,
   c->gres = fabs(S.g[j + 1]);
   c->j = j + 1;
   c->total += 1;
-  if (!isfinite(c->gres)) c->flags |= NK_NAN;
+  if (!isfinite(c->gres) || *err) c->flags |= NK_NAN;
   const bool go = tick(c) && !c->flags && c->gres > c->tol && c->j < m &&
                   c->total < c->max_krylov;
   cudaGraphSetConditional(hA, go ? 1u : 0u);
@@ -297,7 +297,7 @@ struct Builder {
   void evaluate(cudaStream_t s) {
     int r = ctx_linearise(c, G->uw, b, 1.0, 1.0, c->d_F, s, par());
     if (r != NRD_OK) rc = r;
-    launch_wdot(c->H, c->R, c->d_F, c->d_F, G_F, s);
+    launch_wdot_lv(c->H, c->R, c->d_F, c->d_F, G_F, s);
   }
 
   void jv(const double* v, double* out, cudaStream_t s) {
@@ -315,13 +315,14 @@ struct Builder {
     if (r != NRD_OK) rc = r;
     jv(G->zf, c->d_w, s);
     const int* jd = &G->ctl->j;
-    launch_mdot_dyn(H, c->R, c->d_w, c->d_V, stride, jd, 1, G_H1, s);
-    launch_mupdate_dyn(n2, c->d_w, c->d_V, stride, jd, 1, res() + G_H1, s);
-    launch_mdot_dyn(H, c->R, c->d_w, c->d_V, stride, jd, 1, G_H2, s);
-    launch_mupdate_dyn(n2, c->d_w, c->d_V, stride, jd, 1, res() + G_H2, s);
-    launch_wdot(H, c->R, c->d_w, c->d_w, G_NRM, s);
-    k_normalize_g<<<grid1(n2), 256, 0, s>>>(n2, c->d_w, c->d_V, stride, jd, 1, res() + G_NRM, 1.0);
-    k_arnoldi_g<<<1, 1, 0, s>>>(G->ctl, small(), m, res(), hA);
+    if (launch_cgs2_coop(H, c->R, c->d_w, c->d_V, stride, jd, 1, G_H1, G_H2, G_NRM, s) !=
+        NRD_OK) {
+      cudaGetLastError();
+      launch_cgs2(H, c->R, c->d_w, c->d_V, stride, jd, 1, G_H1, G_H2, G_NRM, s);
+      k_normalize_g<<<grid1(n2), 256, 0, s>>>(n2, c->d_w, c->d_V, stride, jd, 1, res() + G_NRM,
+                                              1.0);
+    }
+    k_arnoldi_g<<<1, 1, 0, s>>>(G->ctl, small(), m, res(), c->R.d_err, hA);
   }
 
   // restart from the true residual (body of the IF node)
@@ -330,7 +331,7 @@ struct Builder {
     const int n2 = 2 * H.N;
     jv(c->d_dx, c->d_w, s);
     k_resid_g<<<grid1(n2), 256, 0, s>>>(n2, c->d_F, c->d_w, c->d_r);
-    launch_wdot(H, c->R, c->d_r, c->d_r, G_R, s);
+    launch_wdot_lv(H, c->R, c->d_r, c->d_r, G_R, s);
     k_gm_restart<<<1, 1, 0, s>>>(G->ctl, small(), c->kry_m, res());
     k_normalize_g<<<grid1(n2), 256, 0, s>>>(n2, c->d_r, c->d_V, n2, nullptr, 0, &G->ctl->rn2, 1.0);
   }

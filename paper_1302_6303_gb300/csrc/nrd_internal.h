@@ -146,8 +146,11 @@ struct StencilIO {
 void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
                        double* g, int nonlinear, cudaStream_t s);
 void launch_ghost_z(const Hier& H, const float* z, float* gz, cudaStream_t s);
+// z3 (optional): z^3 in FP64 for the cells followed by the ghosts (N + G)
 void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const float* gz,
-                    int mode, const StencilIO& io, cudaStream_t s);
+                    int mode, const StencilIO& io, cudaStream_t s, const double* z3 = nullptr);
+// z3[c] = z[c]^3 (cells), z3[N + g] = gz[g]^3 (ghosts), in FP64
+void launch_cube(const Hier& H, const float* z, const float* gz, double* z3, cudaStream_t s);
 void launch_reflux(const Hier& H, const StencilIO& io, int mode, cudaStream_t s);
 void launch_jv_frozen(const Hier& H, const ModelParams& mp, const double* jc, const double* cc,
                       const StencilIO& io, cudaStream_t s);
@@ -165,6 +168,11 @@ struct Reducer {
   double* d_part = nullptr;   // partials [nblk * 8]
   double* d_res = nullptr;    // results [64]
   double* h_res = nullptr;    // pinned host mirror [64]
+  unsigned* d_count = nullptr;  // last-block ticket counter (0 between launches)
+  unsigned* d_bar = nullptr;    // grid barrier: arrival count, generation
+  double* d_part2 = nullptr;    // second partial buffer (cooperative reductions)
+  int* d_err = nullptr;         // set when a grid barrier wait gave up
+  int coop_blocks = 0;          // grid of the cooperative CGS2 (0: unavailable)
 };
 int reducer_init(Reducer& R, int N);
 void reducer_free(Reducer& R);
@@ -177,11 +185,7 @@ void launch_fd_eps(const Hier& H, Reducer& R, const double* u, const double* v, 
 // max |E| over leaf cells into R.d_res[slot]
 void launch_emax(const Hier& H, Reducer& R, const double* E, int slot, cudaStream_t s);
 // multi-dot: res[slot + i] = <w, V_i> for i < nv (V given as base + i*stride)
-void launch_mdot(const Hier& H, Reducer& R, const double* w, const double* V, long stride, int nv,
-                 int slot, cudaStream_t s);
 // w -= sum_i h[i] V_i  (h device)
-void launch_mupdate(int n2, double* w, const double* V, long stride, int nv, const double* h,
-                    cudaStream_t s);
 void launch_axpy(int n, double a, const double* x, double* y, cudaStream_t s);
 void launch_scale_dev(int n, const double* num, const double* den_sq, double* x, cudaStream_t s);
 void launch_lincomb_dev(int n, double* x, const double* Z, long stride, int nv, const double* y,
@@ -192,11 +196,25 @@ void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v,
 // vector counts *jd + add (device values) for graph-captured solves
 void launch_mdot_dyn(const Hier& H, Reducer& R, const double* w, const double* V, long stride,
                      const int* jd, int add, int slot, cudaStream_t s);
-void launch_mupdate_dyn(int n2, double* w, const double* V, long stride, const int* jd, int add,
-                        const double* h, cudaStream_t s);
 void launch_lincomb_dyn(int n, double* x, const double* Z, long stride, const int* jd,
                         const double* y, cudaStream_t s);
 void launch_axpy_dev(int n, const double* a, const double* x, double* y, cudaStream_t s);
+// res[slot] = volume-weighted <x, y> for vectors that vanish on covered cells
+// (level volumes times FMA chains; one launch)
+void launch_wdot_lv(const Hier& H, Reducer& R, const double* x, const double* y, int slot,
+                    cudaStream_t s);
+// CGS2 against the nv = (jd ? *jd : 0) + add columns of V: res[slot_h1..] and
+// res[slot_h2..] receive the two passes' coefficients, res[slot_nrm] the
+// squared norm of the orthogonalised w (three launches)
+void launch_cgs2(const Hier& H, Reducer& R, double* w, const double* V, long stride,
+                 const int* jd, int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s);
+// one cooperative kernel: classical Gram-Schmidt with selective
+// reorthogonalisation (second pass only when the norm fell below 1/sqrt(2)
+// of its value; res[slot_h2..] = 0 otherwise), then V[nv] = w / sqrt(nrm).
+// For vectors that vanish on covered cells.  Returns NRD_ECUDA if a
+// cooperative launch is not possible.
+int launch_cgs2_coop(const Hier& H, Reducer& R, double* w, double* V, long stride, const int* jd,
+                     int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s);
 
 // Preconditioner (k_pc.cu)
 struct PcState;
@@ -283,6 +301,7 @@ struct nrd_ctx {
   double* d_cc = nullptr;      // [3][N] frozen coupling partials
   double* d_lam = nullptr;     // [2][3N+G] adjoint face scratch
   double* d_gam = nullptr;     // [3][G] adjoint ghost scratch
+  double* d_z3 = nullptr;      // [N + G] z^3 of cells and ghost cells (FP64)
   bool lin_ready = false;
   Reducer R;
   PcState* pc = nullptr;

@@ -40,7 +40,8 @@ Small small_of(nrd_ctx* c) {
 
 // Column j of the Hessenberg matrix from the two CGS passes, then the Givens
 // update of the least-squares problem; res[SL_G] = |g_{j+1}|.
-__global__ void k_arnoldi(Small S, int m, int j, double* res) {
+// (err: set by a grid barrier that gave up; the estimate then reads NaN)
+__global__ void k_arnoldi(Small S, int m, int j, double* res, const int* err) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double* col = S.Hm + (size_t)(m + 1) * j;
   for (int i = 0; i <= j; i++) col[i] = res[SL_H1 + i] + res[SL_H2 + i];
@@ -62,7 +63,7 @@ __global__ void k_arnoldi(Small S, int m, int j, double* res) {
   double gj = S.g[j];
   S.g[j + 1] = -sn * gj;
   S.g[j] = cs * gj;
-  res[SL_G] = fabs(S.g[j + 1]);
+  res[SL_G] = (*err) ? nan("") : fabs(S.g[j + 1]);
 }
 
 __global__ void k_ginit(Small S, int m, const double* nrm2, double* res) {
@@ -206,15 +207,15 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
       total++;
       // CGS2
       c->timer.begin(NRD_TK_ORTHO, s);
-      launch_mdot(H, c->R, c->d_w, c->d_V, stride, j + 1, SL_H1, s);
-      launch_mupdate(n2, c->d_w, c->d_V, stride, j + 1, c->R.d_res + SL_H1, s);
-      launch_mdot(H, c->R, c->d_w, c->d_V, stride, j + 1, SL_H2, s);
-      launch_mupdate(n2, c->d_w, c->d_V, stride, j + 1, c->R.d_res + SL_H2, s);
-      launch_wdot(H, c->R, c->d_w, c->d_w, SL_NRM, s);
-      k_normalize<<<grid1(n2), 256, 0, s>>>(n2, c->d_w, c->d_V + (size_t)(j + 1) * stride,
-                                             c->R.d_res + SL_NRM, 1.0);
+      if (launch_cgs2_coop(H, c->R, c->d_w, c->d_V, stride, nullptr, j + 1, SL_H1, SL_H2,
+                           SL_NRM, s) != NRD_OK) {
+        cudaGetLastError();
+        launch_cgs2(H, c->R, c->d_w, c->d_V, stride, nullptr, j + 1, SL_H1, SL_H2, SL_NRM, s);
+        k_normalize<<<grid1(n2), 256, 0, s>>>(n2, c->d_w, c->d_V + (size_t)(j + 1) * stride,
+                                               c->R.d_res + SL_NRM, 1.0);
+      }
       c->timer.end(NRD_TK_ORTHO, s);
-      k_arnoldi<<<1, 1, 0, s>>>(S, m, j, c->R.d_res);
+      k_arnoldi<<<1, 1, 0, s>>>(S, m, j, c->R.d_res, c->R.d_err);
       double gres = read_slot(c, SL_G, s);
       double hn2 = c->R.h_res[SL_NRM];
       (void)hn2;
@@ -236,7 +237,7 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
     int rc = apply(c->d_dx, c->d_w);
     if (rc != NRD_OK) return rc;
     k_resid<<<grid1(n2), 256, 0, s>>>(n2, rhs, rhs_sign, c->d_w, c->d_r);
-    launch_wdot(H, c->R, c->d_r, c->d_r, SL_R, s);
+    launch_wdot_lv(H, c->R, c->d_r, c->d_r, SL_R, s);
     rn2 = read_slot(c, SL_R, s);
     r0 = c->d_r;
     sign = 1.0;
@@ -268,7 +269,7 @@ static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0,
   };
   rc = evaluate();
   if (rc != NRD_OK) return rc;
-  launch_wdot(H, c->R, c->d_F, c->d_F, SL_F, s);
+  launch_wdot_lv(H, c->R, c->d_F, c->d_F, SL_F, s);
   double fn = std::sqrt(read_slot(c, SL_F, s));
   if (!std::isfinite(fn)) {
     c->err = "non-finite initial residual";
@@ -303,7 +304,7 @@ static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0,
     launch_axpy(n2, lam, c->d_dx, u, s);
     rc = evaluate();
     if (rc != NRD_OK) return rc;
-    launch_wdot(H, c->R, c->d_F, c->d_F, SL_F, s);
+    launch_wdot_lv(H, c->R, c->d_F, c->d_F, SL_F, s);
     double fold = fn;
     fn = std::sqrt(read_slot(c, SL_F, s));
     if (!std::isfinite(fn)) {
@@ -341,7 +342,12 @@ int solver_adjoint(nrd_ctx* c, const double* g, double a0, double dt, double rto
   if (rc != NRD_OK) return rc;
   Hier& H = c->H;
   const int n2 = 2 * H.N;
-  launch_wdot(H, c->R, g, g, SL_F, s);
+  // covered entries of g are not unknowns: a copy with them zeroed keeps
+  // every Krylov vector zero there (the level-weighted dots rely on it)
+  cudaMemcpyAsync(c->d_tmp, g, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  launch_zero_covered(H, c->d_tmp, s);
+  g = c->d_tmp;
+  launch_wdot_lv(H, c->R, g, g, SL_F, s);
   double gn = std::sqrt(read_slot(c, SL_F, s));
   nrd_stats loc{};
   loc.fnorm0 = gn;
@@ -352,7 +358,7 @@ int solver_adjoint(nrd_ctx* c, const double* g, double a0, double dt, double rto
   // final residual of the adjoint system
   launch_vjp(H, c->d_jc, c->d_cc, c->d_z, lam, c->d_lam, c->d_gam, a0, dt, c->d_w, nullptr, s);
   k_resid<<<grid1(n2), 256, 0, s>>>(n2, g, 1.0, c->d_w, c->d_r);
-  launch_wdot(H, c->R, c->d_r, c->d_r, SL_R, s);
+  launch_wdot_lv(H, c->R, c->d_r, c->d_r, SL_R, s);
   double rn = std::sqrt(read_slot(c, SL_R, s));
   loc.krylov_its = its;
   loc.fnorm = rn;

@@ -304,7 +304,7 @@ def test_frozen_jv_requires_linearise(nrd):
 
 
 SHAPES = [(32, 4, 4), (32, 8, 4), (32, 4, 8), (32, 2, 4), (16, 8, 4), (16, 4, 8), (16, 8, 8),
-          (16, 4, 4), (8, 8, 8)]
+          (16, 4, 4), (8, 8, 8), (8, 8, 4)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -422,15 +422,16 @@ def test_graph_newton_restarts_and_caps(nrd):
 
 
 def test_refined_reciprocals_error_bound(nrd):
-    """The linearisation's FP32-seeded, Newton-Raphson-refined reciprocal and
-    reciprocal square root against CUDA's correctly rounded 1/x, 1/sqrt(x):
-    relative error below 1e-13 over 13 decades and at the FP32 range edges
-    (where the rounded operations are used)."""
+    """The linearisation's refined reciprocal and reciprocal square root
+    (PTX approximate seeds, second-order series correction) against CUDA's
+    correctly rounded 1/x, 1/sqrt(x): relative error within a few units in
+    the last place over 26 decades, and the rounded operations at the range
+    edges."""
     rng = np.random.default_rng(0)
-    x = np.concatenate([10.0 ** rng.uniform(-6, 7, 200000), [1e-40, 1e-36, 1e36, 1e40, 1.0]])
+    x = np.concatenate([10.0 ** rng.uniform(-13, 13, 200000),
+                        [1e-305, 1e-300, 1e300, 1e305, 1.0, 0.5, 2.0]])
     out = nrd.check_fastmath(dev(x)).cpu().numpy()
     r_err = np.abs(out[0] - out[1]) / out[1]
     s_err = np.abs(out[2] - out[3]) / out[3]
-    assert r_err.max() <= 1e-13 and s_err.max() <= 1e-13, (r_err.max(), s_err.max())
-    # and they are accurate refinements, not the FP32 seeds
-    assert np.median(r_err) < 1e-14 and np.median(s_err) < 1e-14
+    assert r_err.max() <= 1e-15 and s_err.max() <= 1e-15, (r_err.max(), s_err.max())
+    assert out[0][-4] == out[1][-4] and out[2][-4] == out[3][-4]   # 1e305: rounded path
