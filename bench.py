@@ -36,15 +36,15 @@ DT = 5e-4
 WORKLOAD = "amr2_base64_marshak_band"
 # Algorithmic work per leaf cell of the linearisation stencil, in FP64-pipe
 # instructions (the unit that bounds it on GB300, which issues 2 FP64
-# instructions per clock per SM): 3 faces x 60 (face flux, its 5 partials,
-# raw and scaled P1 coefficients, incl. the conversions of the refined
-# reciprocal and reciprocal square root) + 46 per cell (balance, coupling and
-# its partials, P2 data).  Derivation in the design notes.
-LIN_INST_PER_CELL = 3 * 60 + 46
+# instructions per clock per SM): 3 faces x 51 (face flux, its 5 partials,
+# raw and scaled P1 coefficients incl. the refined reciprocal and reciprocal
+# square root and two conversions) + 36 per cell (balance, coupling and its
+# partials, P2 data).  Derivation in the design notes.
+LIN_INST_PER_CELL = 3 * 51 + 36
 # DRAM bytes per launch of that kernel from the committed ncu capture of the
 # same kernel version (profiles/k_stencil_lin_amr2_base64.md), or None when
 # the kernel changed since.
-LIN_TRAFFIC_BYTES = 24.72e6 + 90.69e6
+LIN_TRAFFIC_BYTES = 25.92e6 + 71.25e6
 JV_TRAFFIC_BYTES = 83.10e6 + 9.47e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B

@@ -219,7 +219,10 @@ int nrd_linearise(nrd_ctx* ctx, const double* u, const double* b, double a0, dou
  * differentiate through implicit steps):
  *   JTw = (dF/du)^T w   (2*ncells doubles; 0 on covered cells)
  *   dz  = (dF/dz)^T w   (ncells doubles, may be NULL): sensitivity to the
- *                       material z of each cell (0 on covered cells).
+ *                       material z of each cell (0 on covered cells).  Needs
+ *                       the material partials, which nrd_linearise forms and
+ *                       the Newton solves of nrd_newton / nrd_step do not
+ *                       (NRD_ESTATE after those).
  * Gather form (no atomics), deterministic.  a0, dt as in the linearisation. */
 int nrd_vjp(nrd_ctx* ctx, const double* w, double a0, double dt, double* JTw, double* dz,
             cudaStream_t stream);

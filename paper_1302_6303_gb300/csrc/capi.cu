@@ -99,7 +99,7 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
 }
 
 int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
-                  cudaStream_t s, const double* par) {
+                  cudaStream_t s, const double* par, bool with_dz) {
   Hier& H = c->H;
   launch_ghost_fill(H, c->mp, c->d_z, u, c->d_gu, 1, s);
   StencilIO io{};
@@ -117,7 +117,7 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.par = par;
   pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2, &io.p2f);
   c->timer.begin(NRD_TK_RESIDUAL, s);
-  launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_LIN, io, s, c->d_z3);
+  launch_stencil(H, c->mp, c->d_z, c->d_gz, with_dz ? ST_LINZ : ST_LIN, io, s, c->d_z3);
   c->timer.end(NRD_TK_RESIDUAL, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
   c->timer.begin(NRD_TK_PC_SETUP, s);
@@ -125,6 +125,7 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   c->timer.end(NRD_TK_PC_SETUP, s);
   if (rc != NRD_OK) return fail(c, rc, "preconditioner set-up failed");
   c->lin_ready = true;
+  c->lin_dz = with_dz;
   c->pc_ready = true;
   return check_launch(c);
 }
@@ -393,7 +394,7 @@ int nrd_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   if (rc) return rc;
   if (!u || !b || !F) return fail(c, NRD_EINVAL, "null argument");
   if (!(a0 > 0.0) || !(dt > 0.0)) return fail(c, NRD_EINVAL, "a0 and dt must be positive");
-  return ctx_linearise(c, u, b, a0, dt, F, s);
+  return ctx_linearise(c, u, b, a0, dt, F, s, nullptr, true);
 }
 
 int nrd_vjp(nrd_ctx* c, const double* w, double a0, double dt, double* JTw, double* dz,
@@ -403,6 +404,8 @@ int nrd_vjp(nrd_ctx* c, const double* w, double a0, double dt, double* JTw, doub
   if (rc) return rc;
   if (!w || !JTw) return fail(c, NRD_EINVAL, "null argument");
   if (!c->lin_ready) return fail(c, NRD_ESTATE, "nrd_vjp needs nrd_linearise first");
+  if (dz && !c->lin_dz)
+    return fail(c, NRD_ESTATE, "dz needs the material partials: call nrd_linearise first");
   launch_vjp(c->H, c->d_jc, c->d_cc, c->d_z, w, c->d_lam, c->d_gam, a0, dt, JTw, dz, s);
   return check_launch(c);
 }

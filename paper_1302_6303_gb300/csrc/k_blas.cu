@@ -434,157 +434,156 @@ struct LevW {
   double w[NRD_MAX_LEVELS];    // cell volume of level l
 };
 
+// One sweep over a thread's cells (level-weighted, see LevW): with UPD first
+// w -= sum_{q<nv} hu_q V_q (stored back), then the NQ dots
+// <w, V_{q0+q}> and, with NORM, <w, w>.  NQ, UPD and NORM are compile-time,
+// so no FP64 instruction is issued for an unused accumulator.  Block
+// partials to part[blockIdx.x * NVMAX + col0 + q] (the norm after the dots).
+template <int NQ, bool UPD, bool NORM>
+__device__ void orth_sweep(const LevW& lw, int l0, double* __restrict__ w,
+                           const double* __restrict__ V, long stride, int N, int nv,
+                           const double* hu, int q0, double* part, int col0, double* sh) {
+  constexpr int NA = NQ + (NORM ? 1 : 0);
+  double acc[NA > 0 ? NA : 1], tot[NA > 0 ? NA : 1];
+#pragma unroll
+  for (int q = 0; q < NA; q++) acc[q] = tot[q] = 0.0;
+  const int T = gridDim.x * blockDim.x;
+  int l = l0, lend = lw.end[l0];
+  double lwt = lw.w[l0];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
+    while (i >= lend) {
+#pragma unroll
+      for (int q = 0; q < NA; q++) {
+        tot[q] = fma(lwt, acc[q], tot[q]);
+        acc[q] = 0.0;
+      }
+      l++;
+      lend = lw.end[l];
+      lwt = lw.w[l];
+    }
+    double wE = w[i], wT = w[N + i];
+    if (UPD) {
+      for (int q = 0; q < nv; q++) {
+        wE = fma(-hu[q], V[q * stride + i], wE);
+        wT = fma(-hu[q], V[q * stride + N + i], wT);
+      }
+      w[i] = wE;
+      w[N + i] = wT;
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; q++)
+      acc[q] = fma(wE, V[(q0 + q) * stride + i], fma(wT, V[(q0 + q) * stride + N + i], acc[q]));
+    if (NORM) acc[NA - 1] = fma(wE, wE, fma(wT, wT, acc[NA - 1]));
+  }
+#pragma unroll
+  for (int q = 0; q < NA; q++) {
+    tot[q] = fma(lwt, acc[q], tot[q]);
+    const double r = block_red<0>(tot[q], sh);
+    if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + col0 + q] = r;
+  }
+}
+
+// the dots <w, V_q>, q < nv, in chunks of 4 (UPD and NORM on the first chunk)
+template <bool UPD, bool NORM>
+__device__ void orth_dots(const LevW& lw, int l0, double* w, const double* V, long stride, int N,
+                          int nv, const double* hu, double* part, double* sh) {
+  for (int q0 = 0; q0 < nv; q0 += 4) {
+    const int nq = min(4, nv - q0);
+    const bool first = (q0 == 0);
+    // norm column: right after the last dot (col nv)
+    if (first) {
+      switch (nq) {
+        case 1: orth_sweep<1, UPD, NORM>(lw, l0, w, V, stride, N, nv, hu, 0, part, 0, sh); break;
+        case 2: orth_sweep<2, UPD, NORM>(lw, l0, w, V, stride, N, nv, hu, 0, part, 0, sh); break;
+        case 3: orth_sweep<3, UPD, NORM>(lw, l0, w, V, stride, N, nv, hu, 0, part, 0, sh); break;
+        default: orth_sweep<4, UPD, NORM>(lw, l0, w, V, stride, N, nv, hu, 0, part, 0, sh);
+      }
+      if (NORM && nq < nv && threadIdx.x == 0) {
+        // move the norm partial from column nq to column nv
+        part[(long)blockIdx.x * NVMAX + nv] = part[(long)blockIdx.x * NVMAX + nq];
+      }
+    } else {
+      switch (nq) {
+        case 1: orth_sweep<1, false, false>(lw, l0, w, V, stride, N, nv, hu, q0, part, q0, sh); break;
+        case 2: orth_sweep<2, false, false>(lw, l0, w, V, stride, N, nv, hu, q0, part, q0, sh); break;
+        case 3: orth_sweep<3, false, false>(lw, l0, w, V, stride, N, nv, hu, q0, part, q0, sh); break;
+        default: orth_sweep<4, false, false>(lw, l0, w, V, stride, N, nv, hu, q0, part, q0, sh);
+      }
+    }
+  }
+}
+
+// sums of block partials in block order (the same in every block) -> out
+__device__ void coop_sum(const double* part, int nq, double* out, double* sh) {
+  for (int q = 0; q < nq; q++) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      acc += __ldcg(&part[(long)b * NVMAX + q]);
+    const double r = block_red<0>(acc, sh);
+    if (threadIdx.x == 0) out[q] = r;
+  }
+  __syncthreads();
+}
+
 // Orthogonalisation of w against the nv = (jd ? *jd : 0) + add columns of V
-// (classical Gram-Schmidt with selective reorthogonalisation, the criterion
-// of Daniel, Gragg, Kaufman and Stewart): h1 = V^T W w and s0 = w^T W w in
-// one pass; w -= V h1 and s1 = w^T W w in the next; only when s1 < s0 / 2
-// (the norm fell below 1/sqrt(2) of its value) a second pass
-// h2 = V^T W w, w -= V h2, s2 = w^T W w.  Then V[nv] = w / sqrt(s).
-// res[slot_h1 + q] = h1_q, res[slot_h2 + q] = h2_q (0 without the second
-// pass), res[slot_nrm] = s.  Block partials ping-pong between pa and pb
-// (stride NVMAX) so each reduction needs one grid barrier.
+// by classical Gram-Schmidt applied twice, with two grid-wide reductions:
+//   pass 1: h1 = V^T W w                                    (barrier)
+//   pass 2: w <- w - V h1; h2 = V^T W w and s = w^T W w     (barrier)
+//   then   V[nv] = (w - V h2) / sqrt(s - |h2|^2)
+// The last norm uses the Pythagorean identity |w - V h2|^2 = |w|^2 - |h2|^2
+// (V orthonormal, h2 = V^T W w), which is well conditioned in the second
+// pass where |h2| << |w| (low-synchronisation Gram-Schmidt, Swirydowicz et
+// al., Numer. Linear Algebra Appl. 2021).  W: leaf volumes (level-weighted
+// dots; w and V vanish on covered cells).  res[slot_h1 + q] = h1,
+// res[slot_h2 + q] = h2, res[slot_nrm] = s - |h2|^2.  Partials ping-pong
+// between pa and pb so that each reduction needs one barrier.
 __global__ void __launch_bounds__(256) k_orth_coop(LevW lw, double* __restrict__ w,
                                                    double* __restrict__ V, long stride, int N,
                                                    const int* jd, int add, double* pa, double* pb,
                                                    unsigned* bar, int* err, double* res,
                                                    int slot_h1, int slot_h2, int slot_nrm) {
   __shared__ double sh[1024];
-  __shared__ double h[NVMAX];
-  __shared__ double sred[NVMAX];
+  __shared__ double h[NVMAX + 1];
   const int nv = min((jd ? *jd : 0) + add, NVMAX - 1);
-  const int T = gridDim.x * blockDim.x;
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   int l0 = 0;
   while (l0 < lw.L - 1 && i0 >= lw.end[l0]) l0++;
 
-  // dots of w with V_q0 .. V_q0+nq-1 (nq <= 4) and, if withn, with itself;
-  // partials to part[blockIdx.x * NVMAX + col0 + q]
-  auto dots = [&](int q0, int nq, bool withn, double* part, int col0) {
-    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0}, tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    int l = l0, lend = lw.end[l0];
-    double lwt = lw.w[l0];
-    for (int i = i0; i < N; i += T) {
-      while (i >= lend) {
-#pragma unroll
-        for (int q = 0; q < 5; q++) {
-          tot[q] = fma(lwt, acc[q], tot[q]);
-          acc[q] = 0.0;
-        }
-        l++;
-        lend = lw.end[l];
-        lwt = lw.w[l];
-      }
-      const double wE = w[i], wT = w[N + i];
-#pragma unroll
-      for (int q = 0; q < 4; q++)
-        if (q < nq)
-          acc[q] = fma(wE, V[(q0 + q) * stride + i], fma(wT, V[(q0 + q) * stride + N + i], acc[q]));
-      if (withn) acc[4] = fma(wE, wE, fma(wT, wT, acc[4]));
-    }
-#pragma unroll
-    for (int q = 0; q < 5; q++) tot[q] = fma(lwt, acc[q], tot[q]);
-    for (int q = 0; q < nq; q++) {
-      const double r = block_red<0>(tot[q], sh);
-      if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + col0 + q] = r;
-    }
-    if (withn) {
-      const double r = block_red<0>(tot[4], sh);
-      if (threadIdx.x == 0) part[(long)blockIdx.x * NVMAX + col0 + nq] = r;
-    }
-  };
-  // w -= V hq; returns this thread's share of w^T W w (level-weighted)
-  auto update_norm = [&](const double* hq) -> double {
-    double acc = 0.0, tot = 0.0;
-    int l = l0, lend = lw.end[l0];
-    double lwt = lw.w[l0];
-    for (int i = i0; i < N; i += T) {
-      while (i >= lend) {
-        tot = fma(lwt, acc, tot);
-        acc = 0.0;
-        l++;
-        lend = lw.end[l];
-        lwt = lw.w[l];
-      }
-      double sE = w[i], sT = w[N + i];
-      for (int q = 0; q < nv; q++) {
-        sE = fma(-hq[q], V[q * stride + i], sE);
-        sT = fma(-hq[q], V[q * stride + N + i], sT);
-      }
-      w[i] = sE;
-      w[N + i] = sT;
-      acc = fma(sE, sE, fma(sT, sT, acc));
-    }
-    return fma(lwt, acc, tot);
-  };
-  // sums of the block partials in block order (the same in every block)
-  auto reduce = [&](const double* part, int nq, double* out) {
-    for (int q = 0; q < nq; q++) {
-      double acc = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        acc += __ldcg(&part[(long)b * NVMAX + q]);
-      const double r = block_red<0>(acc, sh);
-      if (threadIdx.x == 0) out[q] = r;
-    }
-    __syncthreads();
-  };
-
-  // pass 1: h1 and s0 (partials in pa: columns 0..nv-1, nv)
-  for (int q0 = 0; q0 < nv; q0 += 4) dots(q0, min(4, nv - q0), q0 + 4 >= nv, pa, q0);
-  if (nv == 0) dots(0, 0, true, pa, 0);
+  orth_dots<false, false>(lw, l0, w, V, stride, N, nv, nullptr, pa, sh);
   grid_barrier(bar, err);
-  reduce(pa, nv + 1, sred);            // sred[0..nv-1] = h1, sred[nv] = s0
-  if (threadIdx.x < nv) h[threadIdx.x] = sred[threadIdx.x];
-  const double s0 = sred[nv];
+  coop_sum(pa, nv, h, sh);                       // h = h1
+  if (blockIdx.x == 0 && threadIdx.x < nv) res[slot_h1 + threadIdx.x] = h[threadIdx.x];
+  __shared__ double hu[NVMAX];
+  if (threadIdx.x < nv) hu[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
-  if (blockIdx.x == 0 && threadIdx.x < nv) {
-    res[slot_h1 + threadIdx.x] = h[threadIdx.x];
-    res[slot_h2 + threadIdx.x] = 0.0;
-  }
-  // w -= V h1, s1 (partials in pb)
-  {
-    const double r = block_red<0>(update_norm(h), sh);
-    if (threadIdx.x == 0) pb[(long)blockIdx.x * NVMAX] = r;
-  }
+  orth_dots<true, true>(lw, l0, w, V, stride, N, nv, hu, pb, sh);
   grid_barrier(bar, err);
-  reduce(pb, 1, sred);
-  double s = sred[0];
-  if (s < 0.5 * s0) {
-    // second pass: h2 (partials in pa; every block read pa before the
-    // barrier above), w -= V h2, s2 (partials in pb, read before the next)
-    for (int q0 = 0; q0 < nv; q0 += 4) dots(q0, min(4, nv - q0), false, pa, q0);
-    grid_barrier(bar, err);
-    reduce(pa, nv, sred);
-    if (threadIdx.x < nv) h[threadIdx.x] = sred[threadIdx.x];
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x < nv) res[slot_h2 + threadIdx.x] = h[threadIdx.x];
-    const double r = block_red<0>(update_norm(h), sh);
-    if (threadIdx.x == 0) pa[(long)blockIdx.x * NVMAX + NVMAX - 1] = r;
-    grid_barrier(bar, err);
-    double t2 = 0.0;
-    {
-      double acc = 0.0;
-      for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-        acc += __ldcg(&pa[(long)b * NVMAX + NVMAX - 1]);
-      t2 = block_red<0>(acc, sh);
-      if (threadIdx.x == 0) sred[0] = t2;
-      __syncthreads();
-    }
-    s = sred[0];
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) res[slot_nrm] = s;
-  // V[nv] = w / sqrt(s) (the scale once per block: FP64 sqrt and division
-  // cost many FP64 issue slots)
-  __shared__ double s_sc;
+  coop_sum(pb, nv + 1, h, sh);                   // h = h2, h[nv] = |w|^2
+  __shared__ double s_sc, s_nrm;
   if (threadIdx.x == 0) {
-    const double d = sqrt(s);
-    s_sc = (d > 0.0) ? 1.0 / d : 0.0;
+    double q2 = 0.0;
+    for (int q = 0; q < nv; q++) q2 = fma(h[q], h[q], q2);
+    const double nrm = fmax(h[nv] - q2, 0.0);   // (a breakdown rounds to 0, not below)
+    s_nrm = nrm;
+    s_sc = (nrm > 0.0) ? 1.0 / sqrt(nrm) : 0.0;
   }
   __syncthreads();
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < nv) res[slot_h2 + threadIdx.x] = h[threadIdx.x];
+    if (threadIdx.x == 0) res[slot_nrm] = s_nrm;
+  }
+  // V[nv] = (w - V h2) * sc
   const double sc = s_sc;
+  const int T = gridDim.x * blockDim.x;
   double* vn = V + (long)nv * stride;
   for (int i = i0; i < N; i += T) {
-    vn[i] = sc * w[i];
-    vn[N + i] = sc * w[N + i];
+    double wE = w[i], wT = w[N + i];
+    for (int q = 0; q < nv; q++) {
+      wE = fma(-h[q], V[q * stride + i], wE);
+      wT = fma(-h[q], V[q * stride + N + i], wT);
+    }
+    vn[i] = sc * wE;
+    vn[N + i] = sc * wT;
   }
 }
 

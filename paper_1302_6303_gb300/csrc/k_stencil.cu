@@ -179,7 +179,7 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 // rounded arithmetic by ~1e-13 relative.
 __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, double Tb, double za,
                                             double zb, double h, double h3, double kh,
-                                            double kh5, double k, double cL) {
+                                            double kh5, double k, double cL, bool with_dz) {
   FaceLin r;
   const double Tf = 0.5 * (Ta + Tb);
   const double Tf2 = Tf * Tf;
@@ -189,20 +189,20 @@ __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, dou
   const double hz = h3 * (za + zb);
   const double lt = cL * Tf3;
   const double adE = fabs(dE);
-  const double rden = rcp_nr(fma(hz, S, lt * adE));
+  const double ltadE = lt * adE;
+  const double rden = rcp_nr(fma(hz, S, ltadE));
   const double X = 2.0 * Tf3 * S * rden;
   const double PE = X * dE;
   r.PE = PE;
   r.X = X;
   r.CE = X * h;
   const double A = PE * hz;
-  const double B = PE * lt;
-  const double Bs = (dE > 0.0) ? B : ((dE < 0.0) ? -B : 0.0);
+  const double Bs = X * ltadE;      // = PE cL Tf^3 sign(dE)
   const double t4 = 4.0 * Tf3;
   r.aEa = (fma(-t4, Ea, Bs) - A) * rden;
   r.aEb = (fma(t4, Eb, -Bs) - A) * rden;
   r.aT = (Tf2 * rden) * fma(-1.5 * cL, adE * PE, 3.0 * (S * dE));
-  r.aZ = -(PE * rden) * (h3 * S);
+  r.aZ = with_dz ? -(PE * rden) * (h3 * S) : 0.0;
   const double y = rsqrt_nr(Tf);
   const double T15 = Tf2 * y;     // Tf^(3/2)
   const double T25 = Tf * T15;    // Tf^(5/2)
@@ -280,7 +280,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
   constexpr int NC = TX * TY * TZ;
   constexpr bool TAN = (MODE == ST_JV);
-  constexpr bool LIN = (MODE == ST_LIN);
+  constexpr bool LIN = (MODE == ST_LIN || MODE == ST_LINZ);
+  constexpr bool DZ = (MODE == ST_LINZ);       // also the d/dz^3 partials
   constexpr bool JVF = (MODE == ST_JVF);       // frozen-Jacobian Jv: sE, sT hold v
   extern __shared__ double smem[];
   double* sE = smem;
@@ -489,7 +490,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[2 * NS + fslot] = 0.0;
           io.jc[3 * NS + fslot] = 0.0;
           io.jc[4 * NS + fslot] = 0.0;
-          io.jc[5 * NS + fslot] = (double)s * m * h * rq * rq * Db / zc;  // d Phi / d z_c^3
+          if (DZ) io.jc[5 * NS + fslot] = (double)s * m * h * rq * rq * Db / zc;  // d Phi / d z_c^3
           io.craw[fslot] = Db;
           io.craw[NS + fslot] = 0.0;
           put_scaled(io, NS, fslot, betav * 2.0 * Db * rq / h, 0.0);
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
                    svT[ha], svT[hb], PE, PT);
         } else if (LIN) {
           FaceLin L = flux_lin(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, h3, kh,
-                               A.lh.kh5[lvl][dir], A.k, A.cL);
+                               A.lh.kh5[lvl][dir], A.k, A.cL, DZ);
           PE = L.PE;
           PT = L.PT;
           io.jc[fslot] = L.aEa;
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[2 * NS + fslot] = L.aT;
           io.jc[3 * NS + fslot] = L.bTa;
           io.jc[4 * NS + fslot] = L.bTb;
-          io.jc[5 * NS + fslot] = L.aZ;
+          if (DZ) io.jc[5 * NS + fslot] = L.aZ;
           io.craw[fslot] = L.CE;
           io.craw[NS + fslot] = L.CT;
           if (io.a32) {
@@ -547,7 +548,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         if (LIN) {
           io.cc[idx] = 0.0;
           io.cc[N + idx] = 0.0;
-          io.cc[2L * N + idx] = 0.0;
+          if (DZ) io.cc[2L * N + idx] = 0.0;
           if (io.p2f) {
             io.p2f[idx] = 0.0f;
             io.p2f[N + idx] = 0.0f;
@@ -585,7 +586,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         double dc = sig * ((T3 + 3.0 * E * rT) * vT - vE);
         io.out[idx] = a0v * vE - dtv * (divE + dc);
         io.out[N + idx] = a0v * vT - dtv * (divT - dc);
-      } else if (MODE == ST_LIN) {
+      } else if (LIN) {
         double rT = rcp_nr(T);
         double sig = z * rT * rT * rT;
         double cp = sig * (T2 * T2 - E);
@@ -593,8 +594,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         io.out[N + idx] = a0v * T - io.b[N + idx] - dtv * (divT - cp);
         // coupling tangent dc = cE vE + cT vT
         io.cc[idx] = -sig;
-        io.cc[N + idx] = sig * (T3 + 3.0 * E * rT);
-        io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
+        io.cc[N + idx] = sig * fma(3.0 * E, rT, T3);
+        if (DZ) io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
         // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
         // (det = (1 + sb)(1 + sbt) - sbt sb = 1 + sb + sbt), in the
         // preconditioner's precision
@@ -671,6 +672,10 @@ __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles,
                       const double* E, const double* gE, double thr_c, double thr_g,
                       double thr_r, const double* emax_p, uint8_t* tags) {
   const double emax = *emax_p;
+  const double sc = 0.1 * emax;
+  // an infinite threshold never tags: skip that indicator (uniform branch;
+  // the enabled ones keep the plain formulas, so decisions are unchanged)
+  const bool want_c = thr_c < INFINITY, want_g = thr_g < INFINITY, want_r = thr_r < INFINITY;
   const int nc = tx * ty * tz;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const TileDev tile = tiles[t];
@@ -697,15 +702,15 @@ __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles,
           }
         }
         // no contraction: the same roundings as a plain evaluation
-        tc += fabs(__dadd_rn(__dsub_rn(Ev[1], __dmul_rn(2.0, Ec)), Ev[0]));
-        tg += __dmul_rn(0.5, fabs(__dsub_rn(Ev[1], Ev[0])));
-        double df = __dsub_rn(Ev[1], Ev[0]);
-        gr2 = __dadd_rn(gr2, __dmul_rn(__dmul_rn(0.25, df), df));
+        if (want_c) tc += fabs(__dadd_rn(__dsub_rn(Ev[1], __dmul_rn(2.0, Ec)), Ev[0]));
+        const double df = __dsub_rn(Ev[1], Ev[0]);
+        if (want_g) tg += __dmul_rn(0.5, fabs(df));
+        if (want_r) gr2 = __dadd_rn(gr2, __dmul_rn(__dmul_rn(0.25, df), df));
       }
       uint8_t tag = 0;
-      if (tc / (0.1 * emax) > thr_c) tag |= 1;
-      if (tg / (0.1 * emax) > thr_g) tag |= 2;
-      if (sqrt(gr2) / Ec > thr_r) tag |= 4;
+      if (want_c && tc / sc > thr_c) tag |= 1;
+      if (want_g && tg / sc > thr_g) tag |= 2;
+      if (want_r && sqrt(gr2) / Ec > thr_r) tag |= 4;
       tags[idx] = tag;
     }
   }
@@ -857,6 +862,7 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else if (mode == ST_LINZ) dispatch_tile<ST_LINZ>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JVF) dispatch_tile<ST_JVF>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else dispatch_tile<ST_FD>(a, H.tile_x, H.tile_y, H.tile_z, s);
 }

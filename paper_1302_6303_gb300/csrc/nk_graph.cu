@@ -513,6 +513,7 @@ int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt,
     return NRD_ECUDA;
   }
   c->lin_ready = true;
+  c->lin_dz = false;
   c->pc_ready = true;
   const NkCtl& h = *G->h_ctl;
   nrd_stats loc{};

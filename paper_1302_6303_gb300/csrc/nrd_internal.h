@@ -119,8 +119,9 @@ int hier_tiles(Hier& H, std::string& err);
 void hier_free(Hier& H);
 
 // Kernel launchers (k_stencil.cu)
-// stencil modes; ST_JVF applies the Jacobian frozen by ST_LIN (jc, cc) to v
-enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2, ST_LIN = 3, ST_JVF = 4 };
+// stencil modes; ST_JVF applies the Jacobian frozen by ST_LIN (jc, cc) to v;
+// ST_LINZ is ST_LIN that also forms the partials with respect to z^3
+enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2, ST_LIN = 3, ST_JVF = 4, ST_LINZ = 5 };
 struct StencilIO {
   const double* u;      // state (E then T)
   const double* v;      // direction (JV, FD)
@@ -208,11 +209,10 @@ void launch_wdot_lv(const Hier& H, Reducer& R, const double* x, const double* y,
 // squared norm of the orthogonalised w (three launches)
 void launch_cgs2(const Hier& H, Reducer& R, double* w, const double* V, long stride,
                  const int* jd, int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s);
-// one cooperative kernel: classical Gram-Schmidt with selective
-// reorthogonalisation (second pass only when the norm fell below 1/sqrt(2)
-// of its value; res[slot_h2..] = 0 otherwise), then V[nv] = w / sqrt(nrm).
-// For vectors that vanish on covered cells.  Returns NRD_ECUDA if a
-// cooperative launch is not possible.
+// one cooperative kernel: classical Gram-Schmidt applied twice with two
+// grid-wide reductions (the second pass's norm by the Pythagorean identity),
+// writing V[nv] = w'' / |w''|.  For vectors that vanish on covered cells.
+// Returns NRD_ECUDA if a cooperative launch is not possible.
 int launch_cgs2_coop(const Hier& H, Reducer& R, double* w, double* V, long stride, const int* jd,
                      int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s);
 
@@ -303,6 +303,7 @@ struct nrd_ctx {
   double* d_gam = nullptr;     // [3][G] adjoint ghost scratch
   double* d_z3 = nullptr;      // [N + G] z^3 of cells and ghost cells (FP64)
   bool lin_ready = false;
+  bool lin_dz = false;         // the last linearisation holds the d/dz^3 partials
   Reducer R;
   PcState* pc = nullptr;
   bool pc_ready = false;
@@ -343,4 +344,4 @@ int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const 
            double a0, double dt, int mode, double* Jv, bool fill_u_ghosts, cudaStream_t s,
            const double* par = nullptr);
 int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
-                  cudaStream_t s, const double* par = nullptr);
+                  cudaStream_t s, const double* par = nullptr, bool with_dz = false);
