@@ -224,24 +224,29 @@ __global__ void k_zero_cov(const uint8_t* __restrict__ mask, int N, double* x) {
 }
 
 // positivity cap of the Newton update (Sec. 4.1 remark): min over leaf
-// components with v < 0 of u/(-v)
+// components with v < 0 of u/(-v).  Each thread keeps its best ratio as a
+// pair (a, b) = (u, -v), compared by cross-multiplication (both b > 0), and
+// divides once at the end: FP64 division is a long instruction sequence on
+// GB300.  (a/b < c/d <=> a d < c b; a near-tie may pick the other element,
+// whose quotient then differs in the last bit at most.)
 __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restrict__ u,
                          const double* __restrict__ v, int N, double* part, unsigned* counter,
                          double* res, int slot) {
   __shared__ double sh[1024];
-  double m = DBL_MAX;
+  double ba = 1.0, bb = 0.0;   // no candidate yet: b = 0
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-    if (mask[i] & MASK_COVERED) continue;
-    for (int f = 0; f < 2; f++) {
-      // divide only when the ratio beats the running minimum
-      // (u/(-v) < m  <=>  u < m (-v) for v < 0), so the result is the same
-      const double vv = v[f * N + i];
-      if (vv < 0.0) {
-        const double uu = u[f * N + i];
-        if (uu < m * (-vv)) m = fmin(m, uu / (-vv));
-      }
+    const bool leaf = !(mask[i] & MASK_COVERED);
+    const double v0 = v[i], v1 = v[N + i];
+    if (leaf && v0 < 0.0) {
+      const double a = u[i], b = -v0;
+      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+    }
+    if (leaf && v1 < 0.0) {
+      const double a = u[N + i], b = -v1;
+      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
     }
   }
+  const double m = (bb > 0.0) ? ba / bb : DBL_MAX;
   double r = block_red<1>(m, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);

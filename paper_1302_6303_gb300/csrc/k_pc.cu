@@ -32,326 +32,338 @@ struct LevelHP {
   double h[NRD_MAX_LEVELS][3];
 };
 
-// ------------------------------------------------------------- box levels
+// ---------------------------------------------------------------- V-cycle
+// All apply kernels work on 8x8x8 tiles (ragged at patch and box edges):
+// one tile per block of 256 threads, so every in-tile coordinate is a shift
+// or a mask and every index is 32-bit (pc_alloc rejects hierarchies whose
+// coefficient slots exceed 2^31).  Red-black passes give each thread one
+// x-pair of cells, exactly one of which has the pass colour.
+constexpr int VT = 8;
+constexpr int VTHREADS = 256;
+constexpr int kTilePatch = 0x3fffffff;
+constexpr int kTileCovered = 1 << 30;
+
+// thread -> x-pair of a red-black pass: pair (t & 3), row (t >> 2) & 7,
+// plane t >> 5
+__device__ __forceinline__ int rb_px(int t) { return 2 * (t & 3); }
+__device__ __forceinline__ int rb_j(int t) { return (t >> 2) & 7; }
+__device__ __forceinline__ int rb_k(int t) { return t >> 5; }
+// thread -> cell of a full-tile sweep (512 threads): x (t & 7), row
+// (t >> 3) & 7, plane t >> 6
+constexpr int FTHREADS = 512;
+__device__ __forceinline__ int ft_i(int t) { return t & 7; }
+__device__ __forceinline__ int ft_j(int t) { return (t >> 3) & 7; }
+__device__ __forceinline__ int ft_k(int t) { return t >> 6; }
+
+// ---- box levels (level 0 inside the hierarchy vectors, and the GMG boxes)
 template <class P>
-struct BoxV {
-  int n[3];
-  int fo[6];
+struct BoxK {
+  int n0, n1, n2;
+  int fo[6];      // boundary slot offset of each face, relative to gbase
   const P* A;     // coefficients of field 0; field f at A + f * Afs
   long Afs;
-  long NA;        // stride of the low-face blocks
-  long gbase;     // index of the first boundary slot
-  long cell0;     // first cell of the box in the vectors
+  int NA;         // stride of the low-face blocks
+  int gbase;      // index of the first boundary slot
   P* e;           // correction, field f at e + f * vfs
   const P* f;     // right-hand side
   long vfs;
 };
 
-template <class P>
-__device__ __forceinline__ void box_row(const BoxV<P>& V, int fld, int i, int j, int k, const P* e,
-                                        P& dg, P& of) {
-  const P* A = V.A + fld * V.Afs;
-  const int n0 = V.n[0], n1 = V.n[1], n2 = V.n[2];
-  long idx = i + (long)n0 * (j + (long)n1 * k);
-  long ci = V.cell0 + idx;
+// diagonal and off-diagonal sum of row (i, j, k) of I - beta div D grad on a
+// box (all box faces physical); ZERO: the neighbours are 0
+template <class P, bool ZERO>
+__device__ __forceinline__ void box_row(const BoxK<P>& B, const P* A, const P* e, int i, int j,
+                                        int k, P& dg, P& of) {
+  const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
+  const int idx = i + n0 * (j + n1 * k);
+  const int s2 = n0 * n1;
   P d = P(1), o = P(0), a;
-  if (i > 0) { a = A[ci]; d += a; o += a * e[idx - 1]; }
-  else d += A[V.gbase + V.fo[0] + j + n1 * k];
-  if (i < n0 - 1) { a = A[ci + 1]; d += a; o += a * e[idx + 1]; }
-  else d += A[V.gbase + V.fo[1] + j + n1 * k];
-  if (j > 0) { a = A[V.NA + ci]; d += a; o += a * e[idx - n0]; }
-  else d += A[V.gbase + V.fo[2] + k + n2 * i];
-  if (j < n1 - 1) { a = A[V.NA + ci + n0]; d += a; o += a * e[idx + n0]; }
-  else d += A[V.gbase + V.fo[3] + k + n2 * i];
-  long s2 = (long)n0 * n1;
-  if (k > 0) { a = A[2 * V.NA + ci]; d += a; o += a * e[idx - s2]; }
-  else d += A[V.gbase + V.fo[4] + i + n0 * j];
-  if (k < n2 - 1) { a = A[2 * V.NA + ci + s2]; d += a; o += a * e[idx + s2]; }
-  else d += A[V.gbase + V.fo[5] + i + n0 * j];
+  if (i > 0) { a = A[idx]; d += a; if (!ZERO) o += a * e[idx - 1]; }
+  else d += A[B.gbase + B.fo[0] + j + n1 * k];
+  if (i < n0 - 1) { a = A[idx + 1]; d += a; if (!ZERO) o += a * e[idx + 1]; }
+  else d += A[B.gbase + B.fo[1] + j + n1 * k];
+  if (j > 0) { a = A[B.NA + idx]; d += a; if (!ZERO) o += a * e[idx - n0]; }
+  else d += A[B.gbase + B.fo[2] + k + n2 * i];
+  if (j < n1 - 1) { a = A[B.NA + idx + n0]; d += a; if (!ZERO) o += a * e[idx + n0]; }
+  else d += A[B.gbase + B.fo[3] + k + n2 * i];
+  if (k > 0) { a = A[2 * B.NA + idx]; d += a; if (!ZERO) o += a * e[idx - s2]; }
+  else d += A[B.gbase + B.fo[4] + i + n0 * j];
+  if (k < n2 - 1) { a = A[2 * B.NA + idx + s2]; d += a; if (!ZERO) o += a * e[idx + s2]; }
+  else d += A[B.gbase + B.fo[5] + i + n0 * j];
   dg = d;
   of = o;
 }
 
-// one colour of a red-black Gauss-Seidel sweep on a box level
-template <class P>
-__global__ void k_box_rbgs(BoxV<P> V, int colour) {
-  const int fld = blockIdx.y;
-  P* e = V.e + fld * V.vfs;
-  const P* f = V.f + fld * V.vfs;
-  const long nc = (long)V.n[0] * V.n[1] * V.n[2];
-  // thread t handles the t-th cell of the requested colour
-  const long nhalf = (nc + 1) / 2;
-  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < nhalf;
-       t += (long)gridDim.x * blockDim.x) {
-    long idx = 2 * t;
-    int i = (int)(idx % V.n[0]);
-    long r = idx / V.n[0];
-    int j = (int)(r % V.n[1]);
-    int k = (int)(r / V.n[1]);
-    if (((i + j + k) & 1) != colour) {
-      i += 1;
-      if (i >= V.n[0]) continue;  // only when n0 is odd; the cell is picked up elsewhere
+// one colour of a red-black Gauss-Seidel pass on a box; grid (tiles x,
+// tiles y, 2 x tiles z), the upper half of z for field 1.
+// ZERO: the correction starts from 0 (the pass writes 0 to the other colour);
+// ADD:  last pass of the level: u += e on both cells of the pair where the
+//       cell is not covered (level 0 inside the hierarchy vectors)
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, const uint8_t* mask,
+                                                       P* u) {
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int t = threadIdx.x;
+  const int j = blockIdx.y * VT + rb_j(t), k = (blockIdx.z - fld * ntz) * VT + rb_k(t);
+  if (j >= B.n1 || k >= B.n2) return;
+  const int ib = blockIdx.x * VT + rb_px(t);
+  const int par = (j + k + colour) & 1;          // box cells: colour = parity of i + j + k
+  const int i = ib + par, ip = ib + 1 - par;     // this colour, the other one
+  P* e = B.e + fld * B.vfs;
+  const P* A = B.A + fld * B.Afs;
+  const int row = B.n0 * (j + B.n1 * k);
+  P ev = P(0);
+  if (i < B.n0) {
+    P dg, of;
+    box_row<P, ZERO>(B, A, e, i, j, k, dg, of);
+    ev = (B.f[fld * B.vfs + row + i] + of) / dg;
+    e[row + i] = ev;
+    if (ADD && !(mask[row + i] & MASK_COVERED)) u[fld * B.vfs + row + i] += ev;
+  }
+  if (ip < B.n0) {
+    if (ZERO) e[row + ip] = P(0);
+    if (ADD && !(mask[row + ip] & MASK_COVERED)) u[fld * B.vfs + row + ip] += e[row + ip];
+  }
+}
+
+// coarse rhs = 8-cell average of the fine residual f - L e (Sec. 4.3: simple
+// averaging restriction).  BLACK0: the last pass on the fine box was black,
+// so the residual of the black children is zero (up to rounding) and only
+// the 4 red children are summed.  Four consecutive threads share a coarse
+// cell, one red child (and one black child unless BLACK0) each, and sum by
+// shuffles; a block covers 8 x 4 x 2 coarse cells.
+constexpr int RX = 8, RY = 4, RZ = 2;
+dim3 restrict_grid(int cn0, int cn1, int cn2) {
+  return dim3((cn0 + RX - 1) / RX, (cn1 + RY - 1) / RY, 2 * ((cn2 + RZ - 1) / RZ));
+}
+
+template <class P, bool BLACK0>
+__global__ void __launch_bounds__(VTHREADS) k_brestrict(BoxK<P> F, P* fc, int cn0, int cn1,
+                                                         int cn2) {
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int t = threadIdx.x;
+  const int q = t & 3;
+  const int ci = blockIdx.x * RX + ((t >> 2) & 7), cj = blockIdx.y * RY + ((t >> 5) & 3);
+  const int ck = (blockIdx.z - fld * ntz) * RZ + (t >> 7);
+  const bool in = ci < cn0 && cj < cn1 && ck < cn2;
+  P s = P(0);
+  if (in) {
+    const P* e = F.e + fld * F.vfs;
+    const P* f = F.f + fld * F.vfs;
+    const P* A = F.A + fld * F.Afs;
+    // red children (0,0,0) (1,1,0) (1,0,1) (0,1,1); black (1,0,0) (0,1,0) (0,0,1) (1,1,1)
+    const int rx = (q == 1 || q == 2), ry = (q == 1 || q == 3), rz = (q >= 2);
+    const int bx = (q == 0 || q == 3), by = (q == 1 || q == 3), bz = (q == 2 || q == 3);
+#pragma unroll
+    for (int c = 0; c < (BLACK0 ? 1 : 2); c++) {
+      const int i = 2 * ci + (c ? bx : rx), j = 2 * cj + (c ? by : ry), k = 2 * ck + (c ? bz : rz);
+      P dg, of;
+      box_row<P, false>(F, A, e, i, j, k, dg, of);
+      const int idx = i + F.n0 * (j + F.n1 * k);
+      s += f[idx] - (dg * e[idx] - of);
     }
-    long c = i + (long)V.n[0] * (j + (long)V.n[1] * k);
-    P dg, of;
-    box_row(V, fld, i, j, k, e, dg, of);
-    e[c] = (f[c] + of) / dg;
   }
-}
-
-// same, for boxes with odd n0: one thread per cell
-template <class P>
-__global__ void k_box_rbgs_odd(BoxV<P> V, int colour) {
-  const int fld = blockIdx.y;
-  P* e = V.e + fld * V.vfs;
-  const P* f = V.f + fld * V.vfs;
-  const long nc = (long)V.n[0] * V.n[1] * V.n[2];
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < nc;
-       c += (long)gridDim.x * blockDim.x) {
-    int i = (int)(c % V.n[0]);
-    long r = c / V.n[0];
-    int j = (int)(r % V.n[1]);
-    int k = (int)(r / V.n[1]);
-    if (((i + j + k) & 1) != colour) continue;
-    P dg, of;
-    box_row(V, fld, i, j, k, e, dg, of);
-    e[c] = (f[c] + of) / dg;
-  }
-}
-
-// coarse f = 8-cell average of the fine residual f - L e (Sec. 4.3: simple
-// averaging restriction)
-template <class P>
-__global__ void k_box_restrict(BoxV<P> F, P* fc, long cfs) {
-  const int fld = blockIdx.y;
-  const P* e = F.e + fld * F.vfs;
-  const P* f = F.f + fld * F.vfs;
-  const int cn0 = F.n[0] / 2, cn1 = F.n[1] / 2, cn2 = F.n[2] / 2;
-  const long ncc = (long)cn0 * cn1 * cn2;
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncc;
-       c += (long)gridDim.x * blockDim.x) {
-    int ci = (int)(c % cn0);
-    long r = c / cn0;
-    int cj = (int)(r % cn1), ck = (int)(r / cn1);
-    P s = P(0);
-    for (int a = 0; a < 2; a++)
-      for (int b = 0; b < 2; b++)
-        for (int d = 0; d < 2; d++) {
-          int i = 2 * ci + a, j = 2 * cj + b, k = 2 * ck + d;
-          long q = i + (long)F.n[0] * (j + (long)F.n[1] * k);
-          P dg, of;
-          box_row(F, fld, i, j, k, e, dg, of);
-          s += f[q] - (dg * e[q] - of);
-        }
-    fc[fld * cfs + c] = s / P(8);
-  }
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  if (in && q == 0) fc[fld * ((long)cn0 * cn1 * cn2) + ci + cn0 * (cj + cn1 * ck)] = s / P(8);
 }
 
 // trilinear interpolation weight along one axis: (3/4 parent, 1/4 neighbour);
-// neighbours outside the domain fall back to the parent
+// neighbours outside the domain fall back to the parent.  map: dense level
+// map of the coarse level (cell or -1), else src is the coarse box itself.
 template <class P>
-__device__ __forceinline__ P tri_interp(const P* src, const int cn[3], const int q[3],
-                                        const int* map, long moff) {
-  int p[3], o[3];
-  for (int d = 0; d < 3; d++) {
-    p[d] = q[d] >> 1;
-    o[d] = (q[d] & 1) ? 1 : -1;
-    if (p[d] + o[d] < 0 || p[d] + o[d] >= cn[d]) o[d] = 0;
-  }
+__device__ __forceinline__ P tri_interp(const P* src, int cn0, int cn1, int cn2, int q0, int q1,
+                                        int q2, const int* map) {
+  const int p0 = q0 >> 1, p1 = q1 >> 1, p2 = q2 >> 1;
+  int o0 = (q0 & 1) ? 1 : -1, o1 = (q1 & 1) ? 1 : -1, o2 = (q2 & 1) ? 1 : -1;
+  if (p0 + o0 < 0 || p0 + o0 >= cn0) o0 = 0;
+  if (p1 + o1 < 0 || p1 + o1 >= cn1) o1 = 0;
+  if (p2 + o2 < 0 || p2 + o2 >= cn2) o2 = 0;
+  int parent = -1;
   P s = P(0);
-  for (int a = 0; a < 2; a++)
-    for (int b = 0; b < 2; b++)
-      for (int d = 0; d < 2; d++) {
-        P w = (a ? P(0.25) : P(0.75)) * (b ? P(0.25) : P(0.75)) * (d ? P(0.25) : P(0.75));
-        int i = p[0] + (a ? o[0] : 0), j = p[1] + (b ? o[1] : 0), k = p[2] + (d ? o[2] : 0);
-        long li = i + (long)cn[0] * (j + (long)cn[1] * k);
-        long si = map ? (long)map[li] : li + moff;
-        if (si < 0) si = map[p[0] + (long)cn[0] * (p[1] + (long)cn[1] * p[2])];  // nesting guard
-        s += w * src[si];
-      }
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int a = q & 1, b = (q >> 1) & 1, d = q >> 2;
+    const P w = (a ? P(0.25) : P(0.75)) * (b ? P(0.25) : P(0.75)) * (d ? P(0.25) : P(0.75));
+    const int li = (p0 + a * o0) + cn0 * ((p1 + b * o1) + cn1 * (p2 + d * o2));
+    int si = map ? map[li] : li;
+    if (si < 0) {   // nesting guard: a missing neighbour takes the parent
+      if (parent < 0) parent = map[p0 + cn0 * (p1 + cn1 * p2)];
+      si = parent;
+    }
+    s += w * src[si];
+  }
   return s;
 }
 
+// e(fine box) += trilinear interpolation of the coarse correction
 template <class P>
-__global__ void k_box_prolong_add(const P* ec, long cfs, int cn0, int cn1, int cn2, BoxV<P> F) {
-  const int fld = blockIdx.y;
+__global__ void __launch_bounds__(FTHREADS) k_bprolong(const P* ec, int cn0, int cn1, int cn2,
+                                                        BoxK<P> F) {
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * VT + ft_i(t), j = blockIdx.y * VT + ft_j(t);
+  const int k = (blockIdx.z - fld * ntz) * VT + ft_k(t);
+  if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
   P* e = F.e + fld * F.vfs;
-  const P* src = ec + fld * cfs;
-  const int cn[3] = {cn0, cn1, cn2};
-  const long nc = (long)F.n[0] * F.n[1] * F.n[2];
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < nc;
-       c += (long)gridDim.x * blockDim.x) {
-    int q[3];
-    q[0] = (int)(c % F.n[0]);
-    long r = c / F.n[0];
-    q[1] = (int)(r % F.n[1]);
-    q[2] = (int)(r / F.n[1]);
-    e[c] += tri_interp(src, cn, q, (const int*)nullptr, 0);
-  }
+  const P* src = ec + fld * ((long)cn0 * cn1 * cn2);
+  e[i + F.n0 * (j + F.n1 * k)] += tri_interp(src, cn0, cn1, cn2, i, j, k, (const int*)nullptr);
 }
 
 // ------------------------------------------------- AMR (multi-patch) levels
 template <class P>
-struct HierV {
-  const TileDev* tiles;
+struct VLev {
+  const int4* vt;          // tiles: x patch | kTileCovered, y i0, z j0, w k0
   const PatchDev* patches;
   const uint8_t* mask;
-  const uint8_t* gtype;
-  const int* gt0;      // sibling ghost -> its source cell is gidx[gt0[g]]
-  const int* gidx;
-  const P* A;        // field f at A + f * Afs; slots [3N | G]
+  const int2* gsrc;        // per ghost: (sibling source cell, 0), (-1, 0) physical,
+                           // (-2 - first term, end of terms) coarse-fine
+  const int* gidx;         // coarse-fine ghost terms: source cells and weights
+  const P* gw;
+  const P* A;              // field f at A + f * Afs; slots [3N | G]
   long Afs;
   int N, G;
 };
 
-// level-l row of I - beta div D grad (homogeneous coarse-fine ghosts)
-template <class P>
-__device__ __forceinline__ void lev_row(const HierV<P>& V, const PatchDev& Pt, int fld, int i,
-                                        int j, int k, const P* e, const P* gh, P& dg, P& of) {
-  const P* A = V.A + fld * V.Afs;
+// ghost slot of face fc of cell (a, b) in the face's (t1, t2) coordinates
+__device__ __forceinline__ int ghost_slot(const PatchDev& Pt, int fc, int a, int b) {
+  return Pt.goff + Pt.fo[fc] + a + Pt.n[((fc >> 1) + 1) % 3] * b;
+}
+
+// one colour of a red-black pass of the level-l error equation (homogeneous
+// coarse-fine ghosts e_g = e_c/3; sibling cells have the other colour and
+// are read directly); grid (level tiles, 2).  ZERO / ADD as for k_bsmooth.
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int colour, P* e,
+                                                       const P* f, P* u) {
+  const int fld = blockIdx.y;
+  const int4 tl = V.vt[t0 + blockIdx.x];
+  const PatchDev& Pt = V.patches[tl.x & kTilePatch];
   const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
-  const long N = V.N;
-  long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
-  P d = P(1), o = P(0);
-  auto bnd = [&](int f, int a, int b) {
-    int g = Pt.goff + Pt.fo[f] + a + Pt.n[((f >> 1) + 1) % 3] * b;
-    uint8_t t = V.gtype[g];
-    P av = A[3 * N + g];
-    // a sibling cell has the other colour: read it directly
-    if (t == GT_SIBLING) { d += av; o += av * e[V.gidx[V.gt0[g]]]; }
-    else if (t == GT_CF) d += P(2.0 / 3.0) * av;
-    else d += av;   // Robin diagonal term, or 0 for Neumann
-  };
-  P a;
-  if (i > 0) { a = A[idx]; d += a; o += a * e[idx - 1]; } else bnd(0, j, k);
-  if (i < nx - 1) { a = A[idx + 1]; d += a; o += a * e[idx + 1]; } else bnd(1, j, k);
-  if (j > 0) { a = A[N + idx]; d += a; o += a * e[idx - nx]; } else bnd(2, k, i);
-  if (j < ny - 1) { a = A[N + idx + nx]; d += a; o += a * e[idx + nx]; } else bnd(3, k, i);
-  long s2 = (long)nx * ny;
-  if (k > 0) { a = A[2 * N + idx]; d += a; o += a * e[idx - s2]; } else bnd(4, i, j);
-  if (k < nz - 1) { a = A[2 * N + idx + s2]; d += a; o += a * e[idx + s2]; } else bnd(5, i, j);
-  dg = d;
-  of = o;
-}
-
-template <class P>
-__global__ void k_lev_rbgs(HierV<P> V, int t0, int nt, int tx, int ty, int tz, P* e, const P* f,
-                           const P* gh, int colour) {
-  const int fld = blockIdx.y;
-  P* ef = e + (long)fld * V.N;
-  const P* ff = f + (long)fld * V.N;
-  const P* gf = gh + (long)fld * V.G;
-  // one thread per x-pair of cells: exactly one of the two has the colour
-  const int hx = tx >> 1;
-  const int np = hx * ty * tz;
-  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    const TileDev tile = V.tiles[t0 + t];
-    const PatchDev Pt = V.patches[tile.patch];
-    for (int q = threadIdx.x; q < np; q += blockDim.x) {
-      int j = tile.j0 + (q / hx) % ty, k = tile.k0 + q / (hx * ty);
-      int i = tile.i0 + 2 * (q % hx);
-      if (((Pt.lo[0] + i + Pt.lo[1] + j + Pt.lo[2] + k) & 1) != colour) i += 1;
-      if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) continue;
-      long idx = Pt.off + i + (long)Pt.n[0] * (j + (long)Pt.n[1] * k);
-      P dg, of;
-      lev_row(V, Pt, fld, i, j, k, ef, gf, dg, of);
-      ef[idx] = (ff[idx] + of) / dg;
-    }
-  }
-}
-
-// sibling ghosts of a level vector (raw copies)
-template <class P>
-__global__ void k_sib_ghost(const uint8_t* gtype, const int* gt0, const int* gidx, int g0, int ng,
-                            int N, int G, const P* e, P* gh) {
-  const int fld = blockIdx.y;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < ng; q += gridDim.x * blockDim.x) {
-    int g = g0 + q;
-    if (gtype[g] != GT_SIBLING) continue;
-    gh[(long)fld * G + g] = e[(long)fld * N + gidx[gt0[g]]];
-  }
-}
-
-// sibling and coarse-fine ghosts of a composite vector
-template <class P>
-__global__ void k_lin_ghost(const uint8_t* gtype, const int* gt0, const int* gidx, const double* gw,
-                            int N, int G, const P* u, P* gh) {
-  const int fld = blockIdx.y;
-  const P* uf = u + (long)fld * N;
-  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
-    uint8_t t = gtype[g];
-    if (t != GT_SIBLING && t != GT_CF) continue;
-    double s = 0.0;
-    for (int q = gt0[g]; q < gt0[g + 1]; q++) s += gw[q] * (double)uf[gidx[q]];
-    gh[(long)fld * G + g] = (P)s;
-  }
-}
-
-// r = f - L^c u on leaf cells (composite operator with coarse-fine
-// interpolation); fine-side coarse-fine fluxes a (u_g - u_c) go to cf.
-template <class P>
-__global__ void k_comp_resid(HierV<P> V, int ntiles, int tx, int ty, int tz, const P* u, const P* f,
-                             const P* gh, P* r, P* cf) {
-  const int fld = blockIdx.y;
-  const long N = V.N;
+  const int t = threadIdx.x;
+  const int j = tl.z + rb_j(t), k = tl.w + rb_k(t);
+  if (j >= ny || k >= nz) return;
+  const int ib = tl.y + rb_px(t);
+  const int par = (Pt.lo[0] + Pt.lo[1] + Pt.lo[2] + j + k + colour) & 1;
+  const int i = ib + par, ip = ib + 1 - par;
+  const int N = V.N;
+  const long fo = (long)fld * N;
+  P* ef = e + fo;
   const P* A = V.A + fld * V.Afs;
-  const P* uf = u + fld * N;
-  const P* ff = f + fld * N;
-  const P* gf = gh + (long)fld * V.G;
-  P* rf = r + fld * N;
-  P* cff = cf + (long)fld * V.G;
-  const int nc = tx * ty * tz;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const TileDev tile = V.tiles[t];
-    const PatchDev Pt = V.patches[tile.patch];
-    const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
-      long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
-      uint8_t m = V.mask[idx];
-      if (m & MASK_COVERED) { rf[idx] = P(0); continue; }
-      P uc = uf[idx];
-      P Lu = uc;
-      auto bnd = [&](int f, int a, int b) {
-        int g = Pt.goff + Pt.fo[f] + a + Pt.n[((f >> 1) + 1) % 3] * b;
-        uint8_t t = V.gtype[g];
-        P av = A[3 * N + g];
-        if (t == GT_SIBLING || t == GT_CF) {
-          P ug = gf[g];
-          Lu += av * (uc - ug);
-          if (t == GT_CF) cff[g] = av * (ug - uc);
-        } else {
-          Lu += av * uc;   // Robin term (0 for Neumann)
-        }
-      };
-      P a;
-      if (!(m & 2)) { if (i > 0) { a = A[idx]; Lu += a * (uc - uf[idx - 1]); } else bnd(0, j, k); }
-      if (!(m & 4)) { if (i < nx - 1) { a = A[idx + 1]; Lu += a * (uc - uf[idx + 1]); } else bnd(1, j, k); }
-      if (!(m & 8)) { if (j > 0) { a = A[N + idx]; Lu += a * (uc - uf[idx - nx]); } else bnd(2, k, i); }
-      if (!(m & 16)) { if (j < ny - 1) { a = A[N + idx + nx]; Lu += a * (uc - uf[idx + nx]); } else bnd(3, k, i); }
-      long s2 = (long)nx * ny;
-      if (!(m & 32)) { if (k > 0) { a = A[2 * N + idx]; Lu += a * (uc - uf[idx - s2]); } else bnd(4, i, j); }
-      if (!(m & 64)) { if (k < nz - 1) { a = A[2 * N + idx + s2]; Lu += a * (uc - uf[idx + s2]); } else bnd(5, i, j); }
-      rf[idx] = ff[idx] - Lu;
-    }
+  const int row = Pt.off + nx * (j + ny * k);
+  if (i < nx) {
+    const int idx = row + i;
+    P d = P(1), o = P(0), a;
+    auto bnd = [&](int fc, int a1, int b1) {
+      const int g = ghost_slot(Pt, fc, a1, b1);
+      const P av = A[3 * N + g];
+      const int src = V.gsrc[g].x;
+      if (src >= 0) { d += av; if (!ZERO) o += av * ef[src]; }
+      else if (src < -1) d += P(2.0 / 3.0) * av;
+      else d += av;   // Robin diagonal term, or 0 for Neumann
+    };
+    if (i > 0) { a = A[idx]; d += a; if (!ZERO) o += a * ef[idx - 1]; } else bnd(0, j, k);
+    if (i < nx - 1) { a = A[idx + 1]; d += a; if (!ZERO) o += a * ef[idx + 1]; } else bnd(1, j, k);
+    if (j > 0) { a = A[N + idx]; d += a; if (!ZERO) o += a * ef[idx - nx]; } else bnd(2, k, i);
+    if (j < ny - 1) { a = A[N + idx + nx]; d += a; if (!ZERO) o += a * ef[idx + nx]; } else bnd(3, k, i);
+    const int s2 = nx * ny;
+    if (k > 0) { a = A[2 * N + idx]; d += a; if (!ZERO) o += a * ef[idx - s2]; } else bnd(4, i, j);
+    if (k < nz - 1) { a = A[2 * N + idx + s2]; d += a; if (!ZERO) o += a * ef[idx + s2]; } else bnd(5, i, j);
+    const P ev = (f[fo + idx] + o) / d;
+    ef[idx] = ev;
+    if (ADD && !(V.mask[idx] & MASK_COVERED)) u[fo + idx] += ev;
+  }
+  if (ip < nx) {
+    const int idx = row + ip;
+    if (ZERO) ef[idx] = P(0);
+    if (ADD && !(V.mask[idx] & MASK_COVERED)) u[fo + idx] += ef[idx];
   }
 }
 
-// flux matching for the composite operator: coarse cell gets sum(phi)/8 per
-// coarse-fine face
+// r = f - L^c u on the leaf cells of every tile (composite operator): the
+// sibling and coarse-fine ghosts of u are formed here (the coarse-fine one
+// from its interpolation terms, Sec. 3.2.1); the fine-side coarse-fine
+// fluxes a (u_g - u_c) go to cf for flux matching.  Faces marked in the mask
+// as coarse sides of coarse-fine faces are left to flux matching; covered
+// cells are left to the average-down.  grid (all tiles, 2).
 template <class P>
-__global__ void k_comp_reflux(const int* cell, const int* off, const int4* gq, int nrf, int N,
-                              int G, const P* cf, P* r) {
+__global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* u, const P* f, P* r,
+                                                      P* cf) {
+  const int fld = blockIdx.y;
+  const int4 tl = V.vt[blockIdx.x];
+  if (tl.x & kTileCovered) return;
+  const PatchDev& Pt = V.patches[tl.x & kTilePatch];
+  const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
+  const int t = threadIdx.x;
+  const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int N = V.N;
+  const long fo = (long)fld * N;
+  const int idx = Pt.off + i + nx * (j + ny * k);
+  const uint8_t m = V.mask[idx];
+  if (m & MASK_COVERED) return;
+  const P* A = V.A + fld * V.Afs;
+  const P* uf = u + fo;
+  P* cff = cf + (long)fld * V.G;
+  const int s2 = nx * ny;
+  const P uc = uf[idx];
+  P Lu = uc, a;
+  auto bnd = [&](int fc, int a1, int b1) {
+    const int g = ghost_slot(Pt, fc, a1, b1);
+    const P av = A[3 * N + g];
+    const int2 src = V.gsrc[g];
+    if (src.x >= 0) {
+      Lu += av * (uc - uf[src.x]);
+    } else if (src.x < -1) {
+      P ug = P(0);
+      for (int q = -2 - src.x; q < src.y; q++) ug += V.gw[q] * uf[V.gidx[q]];
+      Lu += av * (uc - ug);
+      cff[g] = av * (ug - uc);
+    } else {
+      Lu += av * uc;   // Robin term (0 for Neumann)
+    }
+  };
+  if (!(m & 2)) { if (i > 0) { a = A[idx]; Lu += a * (uc - uf[idx - 1]); } else bnd(0, j, k); }
+  if (!(m & 4)) { if (i < nx - 1) { a = A[idx + 1]; Lu += a * (uc - uf[idx + 1]); } else bnd(1, j, k); }
+  if (!(m & 8)) { if (j > 0) { a = A[N + idx]; Lu += a * (uc - uf[idx - nx]); } else bnd(2, k, i); }
+  if (!(m & 16)) { if (j < ny - 1) { a = A[N + idx + nx]; Lu += a * (uc - uf[idx + nx]); } else bnd(3, k, i); }
+  if (!(m & 32)) { if (k > 0) { a = A[2 * N + idx]; Lu += a * (uc - uf[idx - s2]); } else bnd(4, i, j); }
+  if (!(m & 64)) { if (k < nz - 1) { a = A[2 * N + idx + s2]; Lu += a * (uc - uf[idx + s2]); } else bnd(5, i, j); }
+  r[fo + idx] = f[fo + idx] - Lu;
+}
+
+// flux matching of the composite operator (each coarse cell with coarse-fine
+// faces gets -sum(fine fluxes)/8 per face) fused with the average-down of the
+// finest covered level: the two write disjoint cells, and the covered cells
+// of the level below the finest read only finest-level cells, which flux
+// matching never writes.
+template <class P>
+__global__ void k_reflux_avg(const int* cell, const int* off, const int4* gq, int nrf,
+                             const int4* __restrict__ cov, int ncov, int N, int G, const P* cf,
+                             P* r) {
   const int fld = blockIdx.y;
   const P* c = cf + (long)fld * G;
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nrf; q += gridDim.x * blockDim.x) {
-    P s = P(0);
-    for (int e = off[q]; e < off[q + 1]; e++) {
-      int4 g = gq[e];
-      s += c[g.x] + c[g.y] + c[g.z] + c[g.w];
+  P* rf = r + (long)fld * N;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nrf + ncov;
+       q += gridDim.x * blockDim.x) {
+    if (q < nrf) {
+      P s = P(0);
+      for (int e = off[q]; e < off[q + 1]; e++) {
+        const int4 g = gq[e];
+        s += c[g.x] + c[g.y] + c[g.z] + c[g.w];
+      }
+      rf[cell[q]] -= s / P(8);
+    } else {
+      const int4 v = cov[q - nrf];
+      P s = P(0);
+      for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++)
+          for (int e = 0; e < 2; e++) s += rf[v.y + a + b * v.z + e * v.w];
+      rf[v.x] = s / P(8);
     }
-    r[(long)fld * N + cell[q]] -= s / P(8);
   }
 }
 
@@ -369,7 +381,8 @@ __global__ void k_avgdown_p(const int4* __restrict__ cov, int n, P* x, int N) {
   }
 }
 
-// u += e on the uncovered cells of [c0, c0 + n)
+// u += e on the uncovered cells of [c0, c0 + n) (a level whose last pass
+// could not do it: no smoothing sweeps)
 template <class P>
 __global__ void k_add_leaf(const uint8_t* mask, int c0, int n, int N, const P* e, P* u) {
   const int fld = blockIdx.y;
@@ -379,29 +392,65 @@ __global__ void k_add_leaf(const uint8_t* mask, int c0, int n, int N, const P* e
   }
 }
 
-// pv(level m) = trilinear interpolation of src(level m-1) via the dense map;
-// u += pv on uncovered level-m cells
-template <class P>
-__global__ void k_prolong_level(const TileDev* tiles, const PatchDev* patches, int t0, int nt, int tx,
-                                int ty, int tz, const uint8_t* mask, const int* cmap, int cn0, int cn1,
-                                int cn2, int N, const P* src, P* pv, P* u) {
+// v(level m) = trilinear interpolation of src(level m-1) via its dense map;
+// u += v on uncovered level-m cells; PV: also keep v for the next level
+template <class P, bool PV>
+__global__ void __launch_bounds__(FTHREADS) k_vprolong(VLev<P> V, int t0, const int* cmap,
+                                                        int cn0, int cn1, int cn2, const P* src,
+                                                        P* pv, P* u) {
   const int fld = blockIdx.y;
-  const int cn[3] = {cn0, cn1, cn2};
-  const P* s = src + (long)fld * N;
-  const int nc = tx * ty * tz;
-  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    const TileDev tile = tiles[t0 + t];
-    const PatchDev Pt = patches[tile.patch];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) {
-      int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
-      if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) continue;
-      long idx = Pt.off + i + (long)Pt.n[0] * (j + (long)Pt.n[1] * k);
-      int q[3] = {Pt.lo[0] + i, Pt.lo[1] + j, Pt.lo[2] + k};
-      P v = tri_interp(s, cn, q, cmap, 0);
-      pv[(long)fld * N + idx] = v;
-      if (!(mask[idx] & MASK_COVERED)) u[(long)fld * N + idx] += v;
+  const int4 tl = V.vt[t0 + blockIdx.x];
+  const PatchDev& Pt = V.patches[tl.x & kTilePatch];
+  const int t = threadIdx.x;
+  const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
+  if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) return;
+  const long fo = (long)fld * V.N;
+  const int idx = Pt.off + i + Pt.n[0] * (j + Pt.n[1] * k);
+  const P v = tri_interp(src + fo, cn0, cn1, cn2, Pt.lo[0] + i, Pt.lo[1] + j, Pt.lo[2] + k, cmap);
+  if (PV) pv[fo + idx] = v;
+  if (!(V.mask[idx] & MASK_COVERED)) u[fo + idx] += v;
+}
+
+// V-cycle input: ff = fr = w (the residual of u = 0), u = 0; TR: w goes
+// through the transposed P2 solve first, P2^T = [[1 + sb, -sb], [-sbt, 1 + sbt]]
+template <class P, bool TR>
+__global__ void k_vc_init(int N, const double* w, const P* p, P* ff, P* fr, P* fu, const int* jd,
+                          long jstride) {
+  if (jd) w += (long)(*jd) * jstride;   // w = column *jd of a basis (device index)
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    P xE, xT;
+    if (TR) {
+      const P sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
+      const P wE = (P)w[c], wT = (P)w[N + c];
+      xE = ((P(1) + sbt) * wE + sb * wT) * rd;
+      xT = (sbt * wE + (P(1) + sb) * wT) * rd;
+    } else {
+      xE = (P)w[c];
+      xT = (P)w[N + c];
     }
+    ff[c] = xE;
+    ff[N + c] = xT;
+    fr[c] = xE;
+    fr[N + c] = xT;
+    fu[c] = P(0);
+    fu[N + c] = P(0);
   }
+}
+
+// ghost descriptors for the V-cycle: sibling (source cell, 0), physical
+// (-1, 0), coarse-fine (-2 - first term, end of terms); the coarse-fine
+// weights in the V-cycle precision
+template <class P>
+__global__ void k_vc_ghosts(const uint8_t* gtype, const int* gt0, const int* gidx, int G,
+                            const double* gw, int nterm, int2* gsrc, P* gwp) {
+  for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < G; g += gridDim.x * blockDim.x) {
+    const uint8_t t = gtype[g];
+    gsrc[g] = (t == GT_SIBLING) ? make_int2(gidx[gt0[g]], 0)
+              : (t == GT_CF)    ? make_int2(-2 - gt0[g], gt0[g + 1])
+                                : make_int2(-1, 0);
+  }
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nterm; q += gridDim.x * blockDim.x)
+    gwp[q] = (P)gw[q];
 }
 
 // y = P2^{-1} z per leaf cell, P2 = [[1 + s b, -s b T^3], [-s b, 1 + s b T^3]],
@@ -446,18 +495,6 @@ __global__ void k_p2(int N, const P* zin, const P* p, double* y, const int* jd, 
   }
 }
 
-// transposed P2 solve fused with the cast into the V-cycle precision:
-// P2^T = [[1 + sb, -sb], [-sbt, 1 + sbt]]
-template <class P>
-__global__ void k_p2t_cast(int N, const double* w, const P* p, P* out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    const P sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
-    const P wE = (P)w[c], wT = (P)w[N + c];
-    out[c] = ((P(1) + sbt) * wE + sb * wT) * rd;
-    out[N + c] = (sbt * wE + (P(1) + sb) * wT) * rd;
-  }
-}
-
 // y = V-cycle output in FP64; covered cells get 0
 template <class P>
 __global__ void k_out_cast(const uint8_t* mask, int N, const P* u, double* y) {
@@ -466,13 +503,6 @@ __global__ void k_out_cast(const uint8_t* mask, int N, const P* u, double* y) {
     y[c] = cov ? 0.0 : (double)u[c];
     y[N + c] = cov ? 0.0 : (double)u[N + c];
   }
-}
-
-template <class P>
-__global__ void k_cast(int n, const double* w, P* out, const int* jd, long jstride) {
-  if (jd) w += (long)(*jd) * jstride;   // w = column *jd of a basis (device index)
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    out[i] = (P)w[i];
 }
 
 // ----------------------------------------------------------- set-up kernels
@@ -575,6 +605,8 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
   const double beta = *dbeta;
   const int fld = blockIdx.y;
   double* C = Craw + fld * AF;
+  const double* hl = lh.h[lvl];
+  const double bh2[3] = {beta / (hl[0] * hl[0]), beta / (hl[1] * hl[1]), beta / (hl[2] * hl[2])};
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     int4 s = src[q];
     int t = tgt[q];
@@ -582,9 +614,8 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
     C[t] = c;
     if (!A) continue;
     double v;
-    if (t < 3L * N) {
-      double h = lh.h[lvl][t / N];
-      v = c * beta / (h * h);
+    if (t < 3 * N) {   // low-face slot of axis t / N (3N + G < 2^31)
+      v = c * bh2[(t >= N) + (t >= 2 * N)];
     } else {
       int g = t - 3 * N;
       int d = (gface[g] & 7) / 2;
@@ -666,29 +697,34 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
   const double beta = *dbeta;
   const double hh[3] = {hx, hy, hz};
   const double bh2[3] = {beta * rh2x, beta * rh2y, beta * rh2z};
-  const long ncc = (long)Cc.n[0] * Cc.n[1] * Cc.n[2];
-  for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < ncc;
-       c += (long)gridDim.x * blockDim.x) {
+  // every box starts at cell 0 of its vectors; indices are 32-bit (3N + G
+  // < 2^31 for the hierarchy, which bounds every box)
+  const int ncc = Cc.n[0] * Cc.n[1] * Cc.n[2];
+  const int fNA = (int)F.NA, cNA = (int)Cc.NA, fgb = (int)F.gbase, cgb = (int)Cc.gbase;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncc; c += gridDim.x * blockDim.x) {
     int q[3];
-    q[0] = (int)(c % Cc.n[0]);
-    long r = c / Cc.n[0];
-    q[1] = (int)(r % Cc.n[1]);
-    q[2] = (int)(r / Cc.n[1]);
+    const int r = c / Cc.n[0];
+    q[0] = c - r * Cc.n[0];
+    q[2] = r / Cc.n[1];
+    q[1] = r - q[2] * Cc.n[1];
+#pragma unroll
     for (int d = 0; d < 3; d++) {
-      int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
       if (q[d] > 0) {
         double s = 0.0;
+#pragma unroll
         for (int a = 0; a < 2; a++)
+#pragma unroll
           for (int b = 0; b < 2; b++) {
             int p[3];
             p[d] = 2 * q[d];
             p[t1] = 2 * q[t1] + a;
             p[t2] = 2 * q[t2] + b;
-            long fi = F.cell0 + p[0] + (long)F.n[0] * (p[1] + (long)F.n[1] * p[2]);
-            s += cf[d * F.NA + fi];
+            const int fi = p[0] + F.n[0] * (p[1] + F.n[1] * p[2]);
+            s += cf[d * fNA + fi];
           }
-        cc[d * Cc.NA + c] = 0.25 * s;
-        Af[d * Cc.NA + c] = (P)(0.25 * s * bh2[d]);
+        cc[d * cNA + c] = 0.25 * s;
+        Af[d * cNA + c] = (P)(0.25 * s * bh2[d]);
       }
       for (int sd = 0; sd < 2; sd++) {
         bool at = sd ? (q[d] == Cc.n[d] - 1) : (q[d] == 0);
@@ -698,9 +734,9 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
         for (int a = 0; a < 2; a++)
           for (int b = 0; b < 2; b++) {
             int p1 = 2 * q[t1] + a, p2 = 2 * q[t2] + b;
-            s += cf[F.gbase + F.fo[f] + p1 + F.n[t1] * p2];
+            s += cf[fgb + F.fo[f] + p1 + F.n[t1] * p2];
           }
-        const long g = Cc.gbase + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2];
+        const int g = cgb + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2];
         cc[g] = 0.25 * s;
         double v = 0.0;
         if (gtype_box[f] == 1 && fld == 0) {
@@ -756,6 +792,12 @@ struct PcState {
   // GMG levels tail_m.. run as one shared-memory kernel (0: off)
   int tail_m = 0;
   size_t tail_smem = 0;
+  // 8^3 tiles of all patches for the V-cycle kernels, level by level
+  int4* vt = nullptr;
+  int vt0[NRD_MAX_LEVELS] = {0}, vnt[NRD_MAX_LEVELS] = {0};
+  int ntile = 0;
+  int2* gsrc = nullptr;  // [G] V-cycle ghost descriptors
+  void* gwp = nullptr;   // [nterm] coarse-fine weights in precision P
 };
 
 namespace {
@@ -773,31 +815,41 @@ BoxRaw level0_box(const Hier& H) {
 }
 
 template <class P>
-BoxV<P> view_of(const BoxRaw& B, const void* A, void* e, const void* f, long vfs) {
-  BoxV<P> V;
-  for (int d = 0; d < 3; d++) V.n[d] = B.n[d];
+BoxK<P> boxk(const BoxRaw& B, const void* A, void* e, const void* f, long vfs) {
+  BoxK<P> V;
+  V.n0 = B.n[0];
+  V.n1 = B.n[1];
+  V.n2 = B.n[2];
   for (int q = 0; q < 6; q++) V.fo[q] = B.fo[q];
   V.A = (const P*)A;
   V.Afs = B.AF;
-  V.NA = B.NA;
-  V.gbase = B.gbase;
-  V.cell0 = B.cell0;
+  V.NA = (int)B.NA;
+  V.gbase = (int)B.gbase;
   V.e = (P*)e;
   V.f = (const P*)f;
   V.vfs = vfs;
   return V;
 }
 
+// 8^3 tiles of an n0 x n1 x n2 box, both fields (field 1 in the upper half of z)
+dim3 tile_grid(int n0, int n1, int n2) {
+  return dim3((n0 + VT - 1) / VT, (n1 + VT - 1) / VT, 2 * ((n2 + VT - 1) / VT));
+}
+
+// red-black sweeps on a box; zero: the first pass starts from e = 0; addu:
+// the last pass adds e to u on uncovered cells (level 0)
 template <class P>
-void box_smooth(const BoxV<P>& V, int sweeps, bool red_first, cudaStream_t s) {
-  long nc = (long)V.n[0] * V.n[1] * V.n[2];
-  bool odd = (V.n[0] & 1);
-  dim3 grid(g1(odd ? nc : (nc + 1) / 2), 2);
+void box_smooth(const BoxK<P>& V, int sweeps, bool red_first, bool zero, const uint8_t* mask,
+                P* addu, cudaStream_t s) {
+  const dim3 g = tile_grid(V.n0, V.n1, V.n2);
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
-      int colour = red_first ? pass : 1 - pass;
-      if (odd) k_box_rbgs_odd<P><<<grid, BS, 0, s>>>(V, colour);
-      else k_box_rbgs<P><<<grid, BS, 0, s>>>(V, colour);
+      const int colour = red_first ? pass : 1 - pass;
+      const bool Z = zero && sw == 0 && pass == 0;
+      const bool D = addu && sw == sweeps - 1 && pass == 1;
+      if (Z) k_bsmooth<P, true, false><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
+      else if (D) k_bsmooth<P, false, true><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
+      else k_bsmooth<P, false, false><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
     }
 }
 
@@ -815,48 +867,66 @@ struct TailArgs {
   int nlev;                       // levels tail_m .. nmg-1
   BoxRaw B[NRD_MAX_MG];
   const P* A[NRD_MAX_MG];         // coefficients (field f at + f * B.AF)
-  long offA[NRD_MAX_MG], offE[NRD_MAX_MG], offF[NRD_MAX_MG];   // in elements
+  int offA[NRD_MAX_MG], offE[NRD_MAX_MG], offF[NRD_MAX_MG];   // in elements
   const P* f0;                    // rhs of the first tail level (field stride vfs0)
   P* e0;                          // its correction (output)
-  long vfs0;
+  int vfs0;
   int nu1, nu2, csw;
 };
 
 template <class P>
-__device__ BoxV<P> tail_view(const TailArgs<P>& a, P* sm, int l) {
-  BoxV<P> V;
+__device__ BoxK<P> tail_view(const TailArgs<P>& a, P* sm, int l) {
+  BoxK<P> V;
   const BoxRaw& B = a.B[l];
-  for (int d = 0; d < 3; d++) V.n[d] = B.n[d];
+  V.n0 = B.n[0];
+  V.n1 = B.n[1];
+  V.n2 = B.n[2];
   for (int q = 0; q < 6; q++) V.fo[q] = B.fo[q];
   V.A = sm + a.offA[l];
   V.Afs = 0;
-  V.NA = B.NA;
-  V.gbase = B.gbase;
-  V.cell0 = 0;
+  V.NA = (int)B.NA;
+  V.gbase = (int)B.gbase;
   V.e = sm + a.offE[l];
   V.f = sm + a.offF[l];
   V.vfs = 0;
   return V;
 }
 
+// red-black sweeps by one CTA, each thread over the x-pairs of the box
 template <class P>
-__device__ void tail_smooth(const BoxV<P>& V, int sweeps, bool red_first) {
-  const long nc = (long)V.n[0] * V.n[1] * V.n[2];
+__device__ void tail_smooth(const BoxK<P>& V, int sweeps, bool red_first) {
+  const int n0 = V.n0, n1 = V.n1;
+  const int hx = (n0 + 1) >> 1, np = hx * n1 * V.n2;
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
       const int colour = red_first ? pass : 1 - pass;
-      for (long c = threadIdx.x; c < nc; c += blockDim.x) {
-        int i = (int)(c % V.n[0]);
-        long r = c / V.n[0];
-        int j = (int)(r % V.n[1]);
-        int k = (int)(r / V.n[1]);
-        if (((i + j + k) & 1) != colour) continue;
+      for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        const int r = p / hx, px = p - r * hx;
+        const int k = r / n1, j = r - k * n1;
+        const int i = 2 * px + ((j + k + colour) & 1);
+        if (i >= n0) continue;
         P dg, of;
-        box_row(V, 0, i, j, k, V.e, dg, of);
-        V.e[c] = (V.f[c] + of) / dg;
+        box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
+        const int idx = i + n0 * (j + n1 * k);
+        V.e[idx] = (V.f[idx] + of) / dg;
       }
       __syncthreads();
     }
+}
+
+// dst[0, n) = src[0, n) by one CTA, 8 loads in flight per thread
+template <class P>
+__device__ void cta_copy(P* dst, const P* __restrict__ src, int n) {
+  const int bd = blockDim.x;
+  int q = threadIdx.x;
+  for (; q + 7 * bd < n; q += 8 * bd) {
+    P v[8];
+#pragma unroll
+    for (int u = 0; u < 8; u++) v[u] = src[q + u * bd];
+#pragma unroll
+    for (int u = 0; u < 8; u++) dst[q + u * bd] = v[u];
+  }
+  for (; q < n; q += bd) dst[q] = src[q];
 }
 
 template <class P>
@@ -866,37 +936,34 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
   const int fld = blockIdx.x;
   for (int l = 0; l < a.nlev; l++) {
     const BoxRaw& B = a.B[l];
-    const P* A = a.A[l] + fld * B.AF;
-    for (long q = threadIdx.x; q < B.AF; q += blockDim.x) sm[a.offA[l] + q] = A[q];
-    const long nc = (long)B.n[0] * B.n[1] * B.n[2];
-    for (long q = threadIdx.x; q < nc; q += blockDim.x) sm[a.offE[l] + q] = P(0);
+    cta_copy(sm + a.offA[l], a.A[l] + fld * B.AF, (int)B.AF);
+    const int nc = B.n[0] * B.n[1] * B.n[2];
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) sm[a.offE[l] + q] = P(0);
   }
-  {
-    const long nc = (long)a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
-    for (long q = threadIdx.x; q < nc; q += blockDim.x)
-      sm[a.offF[0] + q] = a.f0[fld * a.vfs0 + q];
-  }
+  cta_copy(sm + a.offF[0], a.f0 + fld * a.vfs0, a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2]);
   __syncthreads();
-  // down: smooth, restrict (8-cell average of f - L e)
+  // down: smooth, restrict (8-cell average of f - L e; after a red-first
+  // sweep the black children's residual is zero)
   for (int l = 0; l + 1 < a.nlev; l++) {
-    BoxV<P> V = tail_view(a, sm, l);
+    BoxK<P> V = tail_view(a, sm, l);
     tail_smooth(V, a.nu1, true);
-    BoxV<P> C = tail_view(a, sm, l + 1);
-    const long ncc = (long)C.n[0] * C.n[1] * C.n[2];
-    for (long c = threadIdx.x; c < ncc; c += blockDim.x) {
-      int ci = (int)(c % C.n[0]);
-      long r = c / C.n[0];
-      int cj = (int)(r % C.n[1]), ck = (int)(r / C.n[1]);
+    const BoxRaw& C = a.B[l + 1];
+    const int c0 = C.n[0], c1 = C.n[1];
+    const int ncc = c0 * c1 * C.n[2];
+    const bool black0 = a.nu1 > 0;
+    for (int c = threadIdx.x; c < ncc; c += blockDim.x) {
+      const int r = c / c0, ci = c - r * c0;
+      const int ck = r / c1, cj = r - ck * c1;
       P s = P(0);
-      for (int x = 0; x < 2; x++)
-        for (int y = 0; y < 2; y++)
-          for (int z = 0; z < 2; z++) {
-            int i = 2 * ci + x, j = 2 * cj + y, k = 2 * ck + z;
-            long q = i + (long)V.n[0] * (j + (long)V.n[1] * k);
-            P dg, of;
-            box_row(V, 0, i, j, k, V.e, dg, of);
-            s += V.f[q] - (dg * V.e[q] - of);
-          }
+      for (int q = 0; q < 8; q++) {
+        const int x = q & 1, y = (q >> 1) & 1, z = q >> 2;
+        if (black0 && ((x + y + z) & 1)) continue;
+        const int i = 2 * ci + x, j = 2 * cj + y, k = 2 * ck + z;
+        const int idx = i + V.n0 * (j + V.n1 * k);
+        P dg, of;
+        box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
+        s += V.f[idx] - (dg * V.e[idx] - of);
+      }
       sm[a.offF[l + 1] + c] = s / P(8);
     }
     __syncthreads();
@@ -904,24 +971,20 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
   tail_smooth(tail_view(a, sm, a.nlev - 1), a.csw, true);
   // up: trilinear prolongation of the coarse correction, smooth
   for (int l = a.nlev - 2; l >= 0; l--) {
-    BoxV<P> V = tail_view(a, sm, l);
+    BoxK<P> V = tail_view(a, sm, l);
     const BoxRaw& C = a.B[l + 1];
-    const int cn[3] = {C.n[0], C.n[1], C.n[2]};
     const P* src = sm + a.offE[l + 1];
-    const long nf = (long)V.n[0] * V.n[1] * V.n[2];
-    for (long c = threadIdx.x; c < nf; c += blockDim.x) {
-      int q[3];
-      q[0] = (int)(c % V.n[0]);
-      long r = c / V.n[0];
-      q[1] = (int)(r % V.n[1]);
-      q[2] = (int)(r / V.n[1]);
-      V.e[c] += tri_interp(src, cn, q, (const int*)nullptr, 0);
+    const int nf = V.n0 * V.n1 * V.n2;
+    for (int c = threadIdx.x; c < nf; c += blockDim.x) {
+      const int r = c / V.n0, i = c - r * V.n0;
+      const int k = r / V.n1, j = r - k * V.n1;
+      V.e[c] += tri_interp(src, C.n[0], C.n[1], C.n[2], i, j, k, (const int*)nullptr);
     }
     __syncthreads();
     tail_smooth(V, a.nu2, false);
   }
-  const long nc0 = (long)a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
-  for (long q = threadIdx.x; q < nc0; q += blockDim.x) a.e0[fld * a.vfs0 + q] = sm[a.offE[0] + q];
+  const int nc0 = a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
+  for (int q = threadIdx.x; q < nc0; q += blockDim.x) a.e0[fld * a.vfs0 + q] = sm[a.offE[0] + q];
 }
 
 template <class P>
@@ -929,14 +992,14 @@ void run_tail(PcState* ps, cudaStream_t s) {
   TailArgs<P> a;
   const int m0 = ps->tail_m;
   a.nlev = ps->nmg - m0;
-  long off = 0;
+  int off = 0;
   for (int l = 0; l < a.nlev; l++) {
     const BoxRaw& B = ps->box[m0 + l];
-    const long nc = (long)B.n[0] * B.n[1] * B.n[2];
+    const int nc = B.n[0] * B.n[1] * B.n[2];
     a.B[l] = B;
     a.A[l] = (const P*)ps->bA[m0 + l];
     a.offA[l] = off;
-    off += B.AF;
+    off += (int)B.AF;
     a.offE[l] = off;
     off += nc;
     a.offF[l] = off;
@@ -944,52 +1007,22 @@ void run_tail(PcState* ps, cudaStream_t s) {
   }
   a.f0 = (const P*)ps->bf[m0];
   a.e0 = (P*)ps->be[m0];
-  a.vfs0 = (long)ps->box[m0].n[0] * ps->box[m0].n[1] * ps->box[m0].n[2];
+  a.vfs0 = ps->box[m0].n[0] * ps->box[m0].n[1] * ps->box[m0].n[2];
   a.nu1 = ps->nu1;
   a.nu2 = ps->nu2;
   a.csw = ps->csw;
   k_box_tail<P><<<2, kTailThreads, ps->tail_smem, s>>>(a);
 }
 
-// GMG V-cycle on box level m (m = 0: AMR level 0 inside the hierarchy vectors)
 template <class P>
-void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
-  if (m > 0 && m == ps->tail_m) {
-    run_tail<P>(ps, s);
-    return;
-  }
-  BoxRaw B = (m == 0) ? level0_box(H) : ps->box[m];
-  const void* A = (m == 0) ? ps->A : ps->bA[m];
-  void* e = (m == 0) ? ps->fe : ps->be[m];
-  const void* f = (m == 0) ? ps->fr : ps->bf[m];
-  long vfs = (m == 0) ? H.N : (long)B.n[0] * B.n[1] * B.n[2];
-  BoxV<P> V = view_of<P>(B, A, e, f, vfs);
-  if (m == ps->nmg - 1) {
-    box_smooth(V, ps->csw, true, s);
-    return;
-  }
-  box_smooth(V, ps->nu1, true, s);
-  BoxRaw C = ps->box[m + 1];
-  long cn = (long)C.n[0] * C.n[1] * C.n[2];
-  dim3 gc(g1(cn), 2);
-  k_box_restrict<P><<<gc, BS, 0, s>>>(V, (P*)ps->bf[m + 1], cn);
-  if (m + 1 != ps->tail_m) cudaMemsetAsync(ps->be[m + 1], 0, 2 * cn * ps->esz, s);
-  gmg_vcycle<P>(ps, H, m + 1, s);
-  long nf = (long)B.n[0] * B.n[1] * B.n[2];
-  dim3 gf(g1(nf), 2);
-  k_box_prolong_add<P><<<gf, BS, 0, s>>>((const P*)ps->be[m + 1], cn, C.n[0], C.n[1], C.n[2], V);
-  box_smooth(V, ps->nu2, false, s);
-}
-
-template <class P>
-HierV<P> hview(PcState* ps, const Hier& H) {
-  HierV<P> V;
-  V.tiles = H.d_tiles;
+VLev<P> vlev(PcState* ps, const Hier& H) {
+  VLev<P> V;
+  V.vt = ps->vt;
   V.patches = H.d_patches;
   V.mask = H.d_mask;
-  V.gtype = H.d_gtype;
-  V.gt0 = H.d_gt0;
+  V.gsrc = ps->gsrc;
   V.gidx = H.d_gidx;
+  V.gw = (const P*)ps->gwp;
   V.A = (const P*)ps->A;
   V.Afs = ps->AF;
   V.N = H.N;
@@ -997,67 +1030,115 @@ HierV<P> hview(PcState* ps, const Hier& H) {
   return V;
 }
 
-// r = ff - L^c fu, then covered cells := mean of their children
+// u += e on the uncovered cells of level l (used when no pass of the level
+// could do it)
+template <class P>
+void add_level(PcState* ps, const Hier& H, int l, cudaStream_t s) {
+  const LevelInfo& Lv = H.lev[l];
+  dim3 g(g1(Lv.ncell), 2);
+  k_add_leaf<P><<<g, BS, 0, s>>>(H.d_mask, Lv.off, Lv.ncell, H.N, (const P*)ps->fe, (P*)ps->fu);
+}
+
+// GMG V-cycle on box level m (m = 0: AMR level 0 inside the hierarchy
+// vectors).  Every level's correction starts from zero; on level 0 the last
+// pass also adds the correction to the composite solution.
+template <class P>
+void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
+  if (m > 0 && m == ps->tail_m) {
+    run_tail<P>(ps, s);
+    return;
+  }
+  const BoxRaw B = (m == 0) ? level0_box(H) : ps->box[m];
+  const void* A = (m == 0) ? ps->A : ps->bA[m];
+  void* e = (m == 0) ? ps->fe : ps->be[m];
+  const void* f = (m == 0) ? ps->fr : ps->bf[m];
+  const long nc = (long)B.n[0] * B.n[1] * B.n[2];
+  const long vfs = (m == 0) ? H.N : nc;
+  const BoxK<P> V = boxk<P>(B, A, e, f, vfs);
+  const uint8_t* mask = (m == 0) ? H.d_mask : nullptr;
+  P* addu = (m == 0) ? (P*)ps->fu : nullptr;
+  auto zero_e = [&]() {
+    for (int fld = 0; fld < 2; fld++)
+      cudaMemsetAsync((char*)e + fld * vfs * (long)sizeof(P), 0, nc * sizeof(P), s);
+  };
+  if (m == ps->nmg - 1) {
+    if (ps->csw > 0) box_smooth(V, ps->csw, true, true, mask, addu, s);
+    else zero_e();   // no correction
+    return;
+  }
+  if (ps->nu1 > 0) box_smooth(V, ps->nu1, true, true, nullptr, (P*)nullptr, s);
+  else zero_e();
+  const BoxRaw& C = ps->box[m + 1];
+  const dim3 gc = restrict_grid(C.n[0], C.n[1], C.n[2]);
+  if (ps->nu1 > 0)
+    k_brestrict<P, true><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);
+  else
+    k_brestrict<P, false><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);
+  gmg_vcycle<P>(ps, H, m + 1, s);
+  k_bprolong<P><<<tile_grid(B.n[0], B.n[1], B.n[2]), FTHREADS, 0, s>>>(
+      (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V);
+  if (ps->nu2 > 0) box_smooth(V, ps->nu2, false, false, mask, addu, s);
+  else if (m == 0) add_level<P>(ps, H, 0, s);
+}
+
+// r = ff - L^c fu on leaf cells; flux matching; covered cells := mean of
+// their children
 template <class P>
 void composite_residual(PcState* ps, const Hier& H, cudaStream_t s) {
-  dim3 gg(g1(std::max(H.G, 1)), 2);
-  if (H.G) k_lin_ghost<P><<<gg, BS, 0, s>>>(H.d_gtype, H.d_gt0, H.d_gidx, H.d_gw, H.N, H.G,
-                                           (const P*)ps->fu, (P*)ps->gh);
-  HierV<P> V = hview<P>(ps, H);
-  int nt = (int)H.tiles.size();
-  dim3 gt(std::min(nt, 152 * 8), 2);
-  k_comp_resid<P><<<gt, BS, 0, s>>>(V, nt, H.tile_x, H.tile_y, H.tile_z, (const P*)ps->fu,
-                                    (const P*)ps->ff, (const P*)ps->gh, (P*)ps->fr, (P*)ps->cf);
-  if (H.nrf) {
-    dim3 gr(g1(H.nrf), 2);
-    k_comp_reflux<P><<<gr, BS, 0, s>>>(H.d_rf_cell, H.d_rf_off, H.d_rf_g, H.nrf, H.N, H.G,
-                                       (const P*)ps->cf, (P*)ps->fr);
-  }
-  for (int l = H.L - 2; l >= 0; l--) {
+  const VLev<P> V = vlev<P>(ps, H);
+  k_cresid<P><<<dim3(ps->ntile, 2), FTHREADS, 0, s>>>(V, (const P*)ps->fu, (const P*)ps->ff,
+                                                      (P*)ps->fr, (P*)ps->cf);
+  if (H.L < 2) return;
+  const int lc = H.L - 2;
+  const int n = H.nrf + H.ncov[lc];
+  if (n)
+    k_reflux_avg<P><<<dim3(g1(n), 2), BS, 0, s>>>(H.d_rf_cell, H.d_rf_off, H.d_rf_g, H.nrf,
+                                                  H.d_cov[lc], H.ncov[lc], H.N, H.G,
+                                                  (const P*)ps->cf, (P*)ps->fr);
+  for (int l = H.L - 3; l >= 0; l--) {
     if (!H.ncov[l]) continue;
     dim3 ga(g1(H.ncov[l]), 2);
     k_avgdown_p<P><<<ga, BS, 0, s>>>(H.d_cov[l], H.ncov[l], (P*)ps->fr, H.N);
   }
 }
 
-// u^c += P^c_l e^l: add on uncovered level-l cells, then interpolate to every
-// finer level
+// the level-l correction (already added on level l) interpolated to every
+// finer level and added on its uncovered cells
 template <class P>
-void correct(PcState* ps, const Hier& H, int l, cudaStream_t s) {
-  const LevelInfo& Lv = H.lev[l];
-  dim3 g(g1(Lv.ncell), 2);
-  k_add_leaf<P><<<g, BS, 0, s>>>(H.d_mask, Lv.off, Lv.ncell, H.N, (const P*)ps->fe, (P*)ps->fu);
+void prolong_finer(PcState* ps, const Hier& H, int l, cudaStream_t s) {
+  const VLev<P> V = vlev<P>(ps, H);
   const void* src = ps->fe;
   for (int m = l + 1; m < H.L; m++) {
-    const LevelInfo& Lm = H.lev[m];
     const LevelInfo& Lc = H.lev[m - 1];
-    dim3 gt(std::max(1, std::min(Lm.nt, 152 * 8)), 2);
-    k_prolong_level<P><<<gt, BS, 0, s>>>(H.d_tiles, H.d_patches, Lm.t0, Lm.nt, H.tile_x, H.tile_y, H.tile_z,
-                                         H.d_mask, H.d_lmap[m - 1], Lc.n[0], Lc.n[1], Lc.n[2], H.N,
-                                         (const P*)src, (P*)ps->fp, (P*)ps->fu);
+    const dim3 g(ps->vnt[m], 2);
+    if (m + 1 < H.L)
+      k_vprolong<P, true><<<g, FTHREADS, 0, s>>>(V, ps->vt0[m], H.d_lmap[m - 1], Lc.n[0], Lc.n[1],
+                                                 Lc.n[2], (const P*)src, (P*)ps->fp, (P*)ps->fu);
+    else
+      k_vprolong<P, false><<<g, FTHREADS, 0, s>>>(V, ps->vt0[m], H.d_lmap[m - 1], Lc.n[0], Lc.n[1],
+                                                  Lc.n[2], (const P*)src, (P*)ps->fp, (P*)ps->fu);
     src = ps->fp;
   }
 }
 
+// sweeps > 0 red-black sweeps of the level-l error equation from e = 0; the
+// last pass adds e to the composite solution
 template <class P>
 void level_smooth(PcState* ps, const Hier& H, int l, int sweeps, bool red_first, cudaStream_t s) {
-  const LevelInfo& Lv = H.lev[l];
-  HierV<P> V = hview<P>(ps, H);
-  dim3 gt(std::max(1, std::min(Lv.nt, 152 * 8)), 2);
+  const VLev<P> V = vlev<P>(ps, H);
+  const dim3 g(ps->vnt[l], 2);
+  P* e = (P*)ps->fe;
+  const P* f = (const P*)ps->fr;
+  P* u = (P*)ps->fu;
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
-      int colour = red_first ? pass : 1 - pass;
-      k_lev_rbgs<P><<<gt, BS, 0, s>>>(V, Lv.t0, Lv.nt, H.tile_x, H.tile_y, H.tile_z, (P*)ps->fe,
-                                      (const P*)ps->fr, (const P*)ps->gh, colour);
+      const int colour = red_first ? pass : 1 - pass;
+      const bool Z = sw == 0 && pass == 0;
+      const bool D = sw == sweeps - 1 && pass == 1;
+      if (Z) k_lsmooth<P, true, false><<<g, VTHREADS, 0, s>>>(V, ps->vt0[l], colour, e, f, u);
+      else if (D) k_lsmooth<P, false, true><<<g, VTHREADS, 0, s>>>(V, ps->vt0[l], colour, e, f, u);
+      else k_lsmooth<P, false, false><<<g, VTHREADS, 0, s>>>(V, ps->vt0[l], colour, e, f, u);
     }
-}
-
-template <class P>
-void zero_level(PcState* ps, const Hier& H, int l, cudaStream_t s) {
-  const LevelInfo& Lv = H.lev[l];
-  for (int f = 0; f < 2; f++)
-    cudaMemsetAsync((char*)ps->fe + ((long)f * H.N + Lv.off) * sizeof(P), 0,
-                    (size_t)Lv.ncell * sizeof(P), s);
 }
 
 // y = P^{-1} w.  With jd non-null (forward only) w and y are bases of
@@ -1066,33 +1147,35 @@ void zero_level(PcState* ps, const Hier& H, int l, cudaStream_t s) {
 template <class P>
 int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transposed,
             cudaStream_t s, const int* jd = nullptr, long jstride = 0, double* y2 = nullptr) {
-  const long n2 = 2L * H.N;
-  if (transposed)
-    k_p2t_cast<P><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff);
-  else
-    k_cast<P><<<g1(n2), BS, 0, s>>>((int)n2, w, (P*)ps->ff, jd, jstride);
-  cudaMemsetAsync(ps->fu, 0, n2 * sizeof(P), s);
   // r = f (u = 0); covered := mean of children
-  cudaMemcpyAsync(ps->fr, ps->ff, n2 * sizeof(P), cudaMemcpyDeviceToDevice, s);
+  if (transposed)
+    k_vc_init<P, true><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff, (P*)ps->fr,
+                                              (P*)ps->fu, nullptr, 0);
+  else
+    k_vc_init<P, false><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff, (P*)ps->fr,
+                                               (P*)ps->fu, jd, jstride);
   for (int l = H.L - 2; l >= 0; l--) {
     if (!H.ncov[l]) continue;
     dim3 ga(g1(H.ncov[l]), 2);
     k_avgdown_p<P><<<ga, BS, 0, s>>>(H.d_cov[l], H.ncov[l], (P*)ps->fr, H.N);
   }
+  // down: finest to level 1 (no sweeps: a zero correction)
   for (int l = H.L - 1; l >= 1; l--) {
-    zero_level<P>(ps, H, l, s);
-    level_smooth<P>(ps, H, l, ps->nu1, true, s);
-    correct<P>(ps, H, l, s);
+    if (ps->nu1 > 0) {
+      level_smooth<P>(ps, H, l, ps->nu1, true, s);
+      prolong_finer<P>(ps, H, l, s);
+    }
     composite_residual<P>(ps, H, s);
   }
-  zero_level<P>(ps, H, 0, s);
   gmg_vcycle<P>(ps, H, 0, s);
-  correct<P>(ps, H, 0, s);
+  prolong_finer<P>(ps, H, 0, s);
+  // up: level 1 to finest
   for (int l = 1; l < H.L; l++) {
     composite_residual<P>(ps, H, s);
-    zero_level<P>(ps, H, l, s);
-    level_smooth<P>(ps, H, l, ps->nu2, false, s);
-    correct<P>(ps, H, l, s);
+    if (ps->nu2 > 0) {
+      level_smooth<P>(ps, H, l, ps->nu2, false, s);
+      prolong_finer<P>(ps, H, l, s);
+    }
   }
   if (transposed)
     k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y);
@@ -1128,6 +1211,11 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
       }
   const long N = H.N, G = H.G;
   ps->AF = 3 * N + G;
+  if (ps->AF >= (1L << 31)) {
+    err = "hierarchy too large for the V-cycle's 32-bit indices (3N + G >= 2^31)";
+    delete ps;
+    return NRD_EINVAL;
+  }
   size_t e = ps->esz;
   bool ok = cudaMalloc(&ps->Craw, 2 * ps->AF * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ps->A, 2 * ps->AF * e) == cudaSuccess &&
@@ -1142,6 +1230,8 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
             cudaMalloc(&ps->bgt, 6 * sizeof(int)) == cudaSuccess &&
             cudaMalloc(&ps->d_beta, sizeof(double)) == cudaSuccess &&
             cudaMalloc(&ps->p2, 3 * N * e) == cudaSuccess &&
+            cudaMalloc(&ps->gsrc, std::max(G, 1L) * sizeof(int2)) == cudaSuccess &&
+            cudaMalloc(&ps->gwp, std::max(H.nterm, 1) * e) == cudaSuccess &&
             cudaStreamCreateWithFlags(&ps->cap, cudaStreamNonBlocking) == cudaSuccess;
   if (ok) {
     cudaMemset(ps->Craw, 0, 2 * ps->AF * sizeof(double));
@@ -1151,6 +1241,40 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
     int bt[6];
     for (int f = 0; f < 6; f++) bt[f] = (H.bc_type[f] == NRD_BC_ROBIN) ? 1 : 0;
     cudaMemcpy(ps->bgt, bt, sizeof bt, cudaMemcpyHostToDevice);
+    if (G) {
+      if (ps->prec == NRD_PC_F32)
+        k_vc_ghosts<float><<<g1(G), BS>>>(H.d_gtype, H.d_gt0, H.d_gidx, (int)G, H.d_gw, H.nterm,
+                                          ps->gsrc, (float*)ps->gwp);
+      else
+        k_vc_ghosts<double><<<g1(G), BS>>>(H.d_gtype, H.d_gt0, H.d_gidx, (int)G, H.d_gw, H.nterm,
+                                           ps->gsrc, (double*)ps->gwp);
+    }
+    // V-cycle tiles: 8^3 blocks of every patch, level by level; a tile all
+    // of whose cells are covered is flagged (no composite residual there)
+    std::vector<int4> vt;
+    for (int l = 0; l < H.L; l++) {
+      const LevelInfo& Lv = H.lev[l];
+      ps->vt0[l] = (int)vt.size();
+      for (int p = Lv.p0; p < Lv.p0 + Lv.np; p++) {
+        const PatchDev& Q = H.patches[p];
+        for (int k0 = 0; k0 < Q.n[2]; k0 += VT)
+          for (int j0 = 0; j0 < Q.n[1]; j0 += VT)
+            for (int i0 = 0; i0 < Q.n[0]; i0 += VT) {
+              bool all = true;
+              for (int k = k0; k < std::min(k0 + VT, Q.n[2]) && all; k++)
+                for (int j = j0; j < std::min(j0 + VT, Q.n[1]) && all; j++)
+                  for (int i = i0; i < std::min(i0 + VT, Q.n[0]) && all; i++)
+                    if (!(H.hmask[Q.off + i + Q.n[0] * (j + Q.n[1] * k)] & MASK_COVERED))
+                      all = false;
+              vt.push_back(make_int4(p | (all ? kTileCovered : 0), i0, j0, k0));
+            }
+      }
+      ps->vnt[l] = (int)vt.size() - ps->vt0[l];
+    }
+    ps->ntile = (int)vt.size();
+    ok = cudaMalloc(&ps->vt, vt.size() * sizeof(int4)) == cudaSuccess &&
+         cudaMemcpy(ps->vt, vt.data(), vt.size() * sizeof(int4), cudaMemcpyHostToDevice) ==
+             cudaSuccess;
   }
   ps->box[0] = level0_box(H);
   for (int m = 1; ok && m < ps->nmg; m++) {
@@ -1216,7 +1340,7 @@ void pc_free(PcState* ps) {
   if (!ps) return;
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(ps->Craw); F(ps->A); F(ps->fu); F(ps->fr); F(ps->fe); F(ps->fp); F(ps->ff); F(ps->gh);
-  F(ps->cf); F(ps->Tk); F(ps->bgt); F(ps->d_beta); F(ps->p2);
+  F(ps->cf); F(ps->Tk); F(ps->bgt); F(ps->d_beta); F(ps->p2); F(ps->vt); F(ps->gsrc); F(ps->gwp);
   pc_drop_graphs(ps);
   if (ps->cap) cudaStreamDestroy(ps->cap);
   for (int m = 0; m < NRD_MAX_MG; m++) { F(ps->bCraw[m]); F(ps->bA[m]); F(ps->be[m]); F(ps->bf[m]); }
