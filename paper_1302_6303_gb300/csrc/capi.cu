@@ -80,7 +80,7 @@ void free_fields(nrd_ctx* c) {
 }  // namespace
 
 int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
-                 bool fill_ghosts, cudaStream_t s) {
+                 bool fill_ghosts, cudaStream_t s, const double* par) {
   Hier& H = c->H;
   if (fill_ghosts) launch_ghost_fill(H, c->mp, c->d_z, u, c->d_gu, 1, s);
   StencilIO io{};
@@ -89,6 +89,7 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
   io.b = b;
   io.a0 = a0;
   io.dt = dt;
+  io.par = par;
   io.out = F;
   io.cfflux = c->d_cf;
   c->timer.begin(NRD_TK_RESIDUAL, s);

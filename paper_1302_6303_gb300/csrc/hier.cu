@@ -487,30 +487,60 @@ int hier_upload(Hier& H, std::string& err) {
   return NRD_OK;
 }
 
+// Stencil tiles of shape tile_x x tile_y x tile_z over every patch.  One
+// tile is one CTA, and the block scheduler starts CTAs in index order, so
+// the list runs from the most to the least expensive item: whole tiles,
+// then the last kSplit whole tiles cut into two halves along z (the last
+// wave then holds half tiles and ends sooner), then the tiles whose cells
+// are all covered (they only write zeros).  Per-level ranges are not kept:
+// every consumer of the list works on single tiles.
 int hier_tiles(Hier& H, std::string& err) {
-  const int L = H.L;
-  H.tiles.clear();
+  (void)err;
+  int dev = 0, nsm = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int kSplit = 3 * std::max(nsm, 1);   // about one wave of the linearisation stencil
   const int TX = H.tile_x, TY = H.tile_y, TZ = H.tile_z;
-  for (int l = 0; l < L; l++) {
+  std::vector<TileDev> full, covered;
+  for (int l = 0; l < H.L; l++) {
     LevelInfo& Lv = H.lev[l];
-    Lv.t0 = (int)H.tiles.size();
+    Lv.t0 = 0;
+    Lv.nt = 0;
     for (int p = Lv.p0; p < Lv.p0 + Lv.np; p++) {
       const PatchDev& P = H.patches[p];
       for (int k0 = 0; k0 < P.n[2]; k0 += TZ)
         for (int j0 = 0; j0 < P.n[1]; j0 += TY)
           for (int i0 = 0; i0 < P.n[0]; i0 += TX) {
-            TileDev t{p, i0, j0, k0, 0};
+            const int k1 = std::min(k0 + TZ, P.n[2]);
             bool all = true;
-            for (int k = k0; k < std::min(k0 + TZ, P.n[2]) && all; k++)
+            for (int k = k0; k < k1 && all; k++)
               for (int j = j0; j < std::min(j0 + TY, P.n[1]) && all; j++)
                 for (int i = i0; i < std::min(i0 + TX, P.n[0]) && all; i++)
                   if (!(H.hmask[P.off + i + P.n[0] * (j + P.n[1] * k)] & MASK_COVERED)) all = false;
-            t.flags = all ? 1 : 0;
-            H.tiles.push_back(t);
+            TileDev t{p, i0, j0, k0, k1, all ? 1 : 0};
+            (all ? covered : full).push_back(t);
           }
     }
-    Lv.nt = (int)H.tiles.size() - Lv.t0;
   }
+  H.tiles.clear();
+  const int nsplit = std::min((int)full.size(), kSplit);
+  const int nkeep = (int)full.size() - nsplit;
+  H.tiles.insert(H.tiles.end(), full.begin(), full.begin() + nkeep);
+  for (int q = nkeep; q < (int)full.size(); q++) {
+    TileDev t = full[q];
+    const int depth = t.k1 - t.k0;
+    if (depth < 2) {
+      H.tiles.push_back(t);
+      continue;
+    }
+    const int km = t.k0 + depth / 2;
+    TileDev lo = t, hi = t;
+    lo.k1 = km;
+    hi.k0 = km;
+    H.tiles.push_back(lo);
+    H.tiles.push_back(hi);
+  }
+  H.tiles.insert(H.tiles.end(), covered.begin(), covered.end());
   if (H.d_tiles) cudaFree(H.d_tiles);
   H.d_tiles = nullptr;
   UP(H.d_tiles, H.tiles);

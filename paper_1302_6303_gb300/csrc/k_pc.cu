@@ -30,6 +30,7 @@ int g1(long n) {
 
 struct LevelHP {
   double h[NRD_MAX_LEVELS][3];
+  double r2[NRD_MAX_LEVELS][3];   // 1 / h^2
 };
 
 // ---------------------------------------------------------------- V-cycle
@@ -552,7 +553,7 @@ __global__ void k_coef(SetupArgs a) {
     const double* hh = a.lh.h[Pt.level];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty, k = tile.k0 + c / (a.tx * a.ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
+      if (i >= nx || j >= ny || k >= tile.k1) continue;
       long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
       bool cov = a.mask[idx] & MASK_COVERED;
       double Ec = a.u[idx], Tc = a.u[N + idx], zc = (double)a.z[idx];
@@ -605,8 +606,7 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
   const double beta = *dbeta;
   const int fld = blockIdx.y;
   double* C = Craw + fld * AF;
-  const double* hl = lh.h[lvl];
-  const double bh2[3] = {beta / (hl[0] * hl[0]), beta / (hl[1] * hl[1]), beta / (hl[2] * hl[2])};
+  const double bx = beta * lh.r2[lvl][0], by = beta * lh.r2[lvl][1], bz = beta * lh.r2[lvl][2];
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     int4 s = src[q];
     int t = tgt[q];
@@ -615,7 +615,7 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
     if (!A) continue;
     double v;
     if (t < 3 * N) {   // low-face slot of axis t / N (3N + G < 2^31)
-      v = c * bh2[(t >= N) + (t >= 2 * N)];
+      v = c * ((t >= 2 * N) ? bz : (t >= N) ? by : bx);
     } else {
       int g = t - 3 * N;
       int d = (gface[g] & 7) / 2;
@@ -623,7 +623,7 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
       uint8_t ty = gtype[g];
       if (ty == GT_NEUMANN) v = 0.0;
       else if (ty == GT_ROBIN) v = (fld == 0) ? beta * 2.0 * c / (h * (4.0 * c + h)) : 0.0;
-      else v = c * beta / (h * h);
+      else v = c * beta * lh.r2[lvl][d];
     }
     A[fld * AF + t] = (P)v;
   }
@@ -646,7 +646,7 @@ __global__ void k_scale_hier(SetupArgs a, const int* cell_level_unused, P* A) {
     const double* hh = a.lh.h[Pt.level];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty, k = tile.k0 + c / (a.tx * a.ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
+      if (i >= nx || j >= ny || k >= tile.k1) continue;
       long idx = Pt.off + i + (long)nx * (j + (long)ny * k);
       int loc[3] = {i, j, k};
       const double* bh2 = a.bh2[Pt.level];
@@ -1375,6 +1375,7 @@ static SetupArgs setup_args(PcState* ps, const Hier& H, const ModelParams* mp, c
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
     for (int d = 0; d < 3; d++) {
       a.lh.h[l][d] = (l < H.L) ? H.lev[l].h[d] : 1.0;
+      a.lh.r2[l][d] = 1.0 / (a.lh.h[l][d] * a.lh.h[l][d]);
       a.bh2[l][d] = a.beta / (a.lh.h[l][d] * a.lh.h[l][d]);
     }
   a.Craw = ps->Craw;

@@ -101,26 +101,6 @@ struct StArgs {
   StencilIO io;
 };
 
-// Face flux in the +e_d direction between cells a (low) and b (high):
-//   Phi_E = D_E (E_b - E_a)/h with D_E = D_h/(1 + D_h g) (or the printed form)
-//         = 2 Tf^3 S dE / (3 h Zs S + cL Tf^3 |dE|),  S = E_a + E_b,
-//           Zs = z_a^3 + z_b^3, dE = E_b - E_a, Tf = (T_a + T_b)/2
-//   Phi_T = k Tf^(5/2) (T_b - T_a)/h.
-__device__ __forceinline__ void flux_val(double Ea, double Eb, double Ta, double Tb, double za,
-                                         double zb, double h3, double kh, double cL, double& PE,
-                                         double& PT) {
-  double Tf = 0.5 * (Ta + Tb);
-  double Tf2 = Tf * Tf;
-  double Tf3 = Tf2 * Tf;
-  double dE = Eb - Ea;
-  double S = Ea + Eb;
-  double Zs = za + zb;
-  double num = 2.0 * Tf3 * dE * S;
-  double den = h3 * Zs * S + cL * Tf3 * fabs(dE);
-  PE = num / den;
-  PT = kh * Tf2 * sqrt(Tf) * (Tb - Ta);
-}
-
 // Linearisation of one face at the iterate: the fluxes, the frozen
 // coefficients D_E = 2 Tf^3 S h / den and D_T = k Tf^(5/2) of Sec. 4.2, and
 // the partial derivatives of Phi_E w.r.t. E_a, E_b and T_a (= w.r.t. T_b) and
@@ -166,7 +146,42 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
-// Face flux of flux_val and its partial derivatives at one iterate (the
+// Face flux in the +e_d direction between cells a (low) and b (high):
+//   Phi_E = D_E (E_b - E_a)/h with D_E = D_h/(1 + D_h g) (or the printed form)
+//         = 2 Tf^3 S dE / (3 h Zs S + cL Tf^3 |dE|),  S = E_a + E_b,
+//           Zs = z_a^3 + z_b^3, dE = E_b - E_a, Tf = (T_a + T_b)/2
+//   Phi_T = k Tf^(5/2) (T_b - T_a)/h,
+// with the intermediate quantities the partial derivatives reuse.  The
+// residual and the linearisation both take their fluxes from here, so the
+// two produce bit-identical residuals.
+struct FaceCore {
+  double Tf, Tf2, Tf3, dE, adE, S, hz, ltadE, rden, X, PE, T15, T25, dT, khT25, PT;
+};
+__device__ __forceinline__ FaceCore face_core(double Ea, double Eb, double Ta, double Tb,
+                                              double za, double zb, double h3, double kh,
+                                              double cL) {
+  FaceCore q;
+  q.Tf = 0.5 * (Ta + Tb);
+  q.Tf2 = q.Tf * q.Tf;
+  q.Tf3 = q.Tf2 * q.Tf;
+  q.dE = Eb - Ea;
+  q.S = Ea + Eb;
+  q.hz = h3 * (za + zb);
+  q.adE = fabs(q.dE);
+  q.ltadE = (cL * q.Tf3) * q.adE;
+  q.rden = rcp_nr(fma(q.hz, q.S, q.ltadE));
+  q.X = 2.0 * q.Tf3 * q.S * q.rden;
+  q.PE = q.X * q.dE;
+  const double y = rsqrt_nr(q.Tf);
+  q.T15 = q.Tf2 * y;     // Tf^(3/2)
+  q.T25 = q.Tf * q.T15;  // Tf^(5/2)
+  q.dT = Tb - Ta;
+  q.khT25 = kh * q.T25;
+  q.PT = q.khT25 * q.dT;
+  return q;
+}
+
+// Face flux of face_core and its partial derivatives at one iterate (the
 // frozen Jacobian), the raw P1 coefficients CE = D_E h and CT = D_T:
 //   PE = X dE, CE = X h with X = 2 Tf^3 S / den, den = 3h Zs S + cL Tf^3 |dE|
 //   d PE / d E_a = (-4 Tf^3 E_a - PE (3h Zs - cL Tf^3 sg)) / den
@@ -175,49 +190,49 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 //   d PE / d Zs  = -PE 3h S / den
 //   PT = (k/h) Tf^(5/2) dT, d PT / d T_{a,b} = (k/h)(1.25 Tf^(3/2) dT -/+ Tf^(5/2))
 // (sg = sign(dE), sign(0) = 0).  The reciprocal and Tf^(-1/2) come from
-// rcp_nr / rsqrt_nr, so the result differs from flux_val's correctly
-// rounded arithmetic by ~1e-13 relative.
+// rcp_nr / rsqrt_nr (within ~1e-13 relative of correctly rounded
+// arithmetic).
 __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, double Tb, double za,
                                             double zb, double h, double h3, double kh,
                                             double kh5, double k, double cL, bool with_dz) {
+  const FaceCore q = face_core(Ea, Eb, Ta, Tb, za, zb, h3, kh, cL);
   FaceLin r;
-  const double Tf = 0.5 * (Ta + Tb);
-  const double Tf2 = Tf * Tf;
-  const double Tf3 = Tf2 * Tf;
-  const double dE = Eb - Ea;
-  const double S = Ea + Eb;
-  const double hz = h3 * (za + zb);
-  const double lt = cL * Tf3;
-  const double adE = fabs(dE);
-  const double ltadE = lt * adE;
-  const double rden = rcp_nr(fma(hz, S, ltadE));
-  const double X = 2.0 * Tf3 * S * rden;
-  const double PE = X * dE;
-  r.PE = PE;
-  r.X = X;
-  r.CE = X * h;
-  const double A = PE * hz;
-  const double Bs = X * ltadE;      // = PE cL Tf^3 sign(dE)
-  const double t4 = 4.0 * Tf3;
-  r.aEa = (fma(-t4, Ea, Bs) - A) * rden;
-  r.aEb = (fma(t4, Eb, -Bs) - A) * rden;
-  r.aT = (Tf2 * rden) * fma(-1.5 * cL, adE * PE, 3.0 * (S * dE));
-  r.aZ = with_dz ? -(PE * rden) * (h3 * S) : 0.0;
-  const double y = rsqrt_nr(Tf);
-  const double T15 = Tf2 * y;     // Tf^(3/2)
-  const double T25 = Tf * T15;    // Tf^(5/2)
-  r.T25 = T25;
-  const double dT = Tb - Ta;
-  r.CT = k * T25;
-  const double khT25 = kh * T25;
-  r.PT = khT25 * dT;
-  const double khq = kh5 * T15 * dT;
-  r.bTa = khq - khT25;
-  r.bTb = khq + khT25;
+  r.PE = q.PE;
+  r.X = q.X;
+  r.CE = q.X * h;
+  const double A = q.PE * q.hz;
+  const double Bs = q.X * q.ltadE;      // = PE cL Tf^3 sign(dE)
+  const double t4 = 4.0 * q.Tf3;
+  r.aEa = (fma(-t4, Ea, Bs) - A) * q.rden;
+  r.aEb = (fma(t4, Eb, -Bs) - A) * q.rden;
+  r.aT = (q.Tf2 * q.rden) * fma(-1.5 * cL, q.adE * q.PE, 3.0 * (q.S * q.dE));
+  r.aZ = with_dz ? -(q.PE * q.rden) * (h3 * q.S) : 0.0;
+  r.T25 = q.T25;
+  r.CT = k * q.T25;
+  r.PT = q.PT;
+  const double khq = kh5 * q.T15 * q.dT;
+  r.bTa = khq - q.khT25;
+  r.bTb = khq + q.khT25;
   return r;
 }
 
-// Tangent of flux_val in the direction (dEa, dEb, dTa, dTb); sign(0) = 0.
+// Balance of one cell (Eq. nonlinearsystem, per unit volume):
+//   F_E = a0 E - b_E - dt (div_E + c),  F_T = a0 T - b_T - dt (div_T - c),
+//   c = sigma (T^4 - E), sigma = z^3 / T^3,
+// shared by the residual and the linearisation (bit-identical F); returns
+// 1/T and sigma for the partial derivatives.
+__device__ __forceinline__ void cell_balance(double a0, double dt, double E, double T, double z3,
+                                             double bE, double bT, double divE, double divT,
+                                             double& FE, double& FT, double& rT, double& sig) {
+  rT = rcp_nr(T);
+  sig = z3 * rT * rT * rT;
+  const double T2 = T * T;
+  const double cp = sig * (T2 * T2 - E);
+  FE = a0 * E - bE - dt * (divE + cp);
+  FT = a0 * T - bT - dt * (divT - cp);
+}
+
+// Tangent of the face fluxes in the direction (dEa, dEb, dTa, dTb); sign(0) = 0.
 __device__ __forceinline__ void flux_tan(double Ea, double Eb, double Ta, double Tb, double za,
                                          double zb, double h3, double kh, double cL, double vEa,
                                          double vEb, double vTa, double vTb, double& dPE,
@@ -330,7 +345,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       for (int c = threadIdx.x; c < NC; c += blockDim.x) {
         int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
         int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
-        if (i >= nx || j >= ny || k >= nz) continue;
+        if (i >= nx || j >= ny || k >= tile.k1) continue;
         int idx = P.off + i + nx * (j + ny * k);
         io.out[idx] = 0.0;
         io.out[N + idx] = 0.0;
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       int oy = (j < 0) ? -1 : ((j >= ny) ? 1 : 0);
       int oz = (k < 0) ? -1 : ((k >= nz) ? 1 : 0);
       if ((ox != 0) + (oy != 0) + (oz != 0) > 1) continue;
-      if (i > nx || j > ny || k > nz) continue;
+      if (i > nx || j > ny || k > tile.k1) continue;
       double e, tt, ve = 0.0, vt = 0.0;
       double z = 0.0;
       if (JVF) {
@@ -422,8 +437,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
       // face on the low side of tile cell (fi, fj, fk) along dir
       int i = tile.i0 + fi, j = tile.j0 + fj, k = tile.k0 + fk;
-      if (i > nx || j > ny || k > nz) continue;
-      if ((dir != 0 && i >= nx) || (dir != 1 && j >= ny) || (dir != 2 && k >= nz)) continue;
+      if (i > nx || j > ny || k > tile.k1) continue;
+      if ((dir != 0 && i >= nx) || (dir != 1 && j >= ny) || (dir != 2 && k >= tile.k1)) continue;
       int pos = (dir == 0) ? i : ((dir == 1) ? j : k);
       int nd = P.n[dir];
       int hb = (fi + 1) + HX * ((fj + 1) + HY * (fk + 1));   // high-side cell
@@ -523,7 +538,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
             io.a64[NS + fslot] = L.CT * b2;
           }
         } else {
-          flux_val(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, PE, PT);
+          const FaceCore q = face_core(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh,
+                                       A.cL);
+          PE = q.PE;
+          PT = q.PT;
         }
         if (gt == GT_CF) {
           io.cfflux[gi] = PE;
@@ -539,7 +557,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     for (int c = threadIdx.x; c < NC; c += blockDim.x) {
       int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
       int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
-      if (i >= nx || j >= ny || k >= nz) continue;
+      if (i >= nx || j >= ny || k >= tile.k1) continue;
       int idx = P.off + i + nx * (j + ny * k);
       uint8_t m = A.mask[idx];
       if (m & MASK_COVERED) {
@@ -587,11 +605,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         io.out[idx] = a0v * vE - dtv * (divE + dc);
         io.out[N + idx] = a0v * vT - dtv * (divT - dc);
       } else if (LIN) {
-        double rT = rcp_nr(T);
-        double sig = z * rT * rT * rT;
-        double cp = sig * (T2 * T2 - E);
-        io.out[idx] = a0v * E - io.b[idx] - dtv * (divE + cp);
-        io.out[N + idx] = a0v * T - io.b[N + idx] - dtv * (divT - cp);
+        double FE, FT, rT, sig;
+        cell_balance(a0v, dtv, E, T, z, io.b[idx], io.b[N + idx], divE, divT, FE, FT, rT, sig);
+        io.out[idx] = FE;
+        io.out[N + idx] = FT;
         // coupling tangent dc = cE vE + cT vT
         io.cc[idx] = -sig;
         io.cc[N + idx] = sig * fma(3.0 * E, rT, T3);
@@ -611,10 +628,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.p2[2L * N + idx] = rcp_nr(1.0 + sb + sbt);
         }
       } else {
-        double sig = z / T3;
-        double cp = sig * (T2 * T2 - E);
-        double FE = a0v * E - io.b[idx] - dtv * (divE + cp);
-        double FT = a0v * T - io.b[N + idx] - dtv * (divT - cp);
+        double FE, FT, rT, sig;
+        cell_balance(a0v, dtv, E, T, z, io.b[idx], io.b[N + idx], divE, divT, FE, FT, rT, sig);
         if (MODE == ST_FD) {
           FE = (FE - io.F0[idx]) * reps;
           FT = (FT - io.F0[N + idx]) * reps;
@@ -683,7 +698,7 @@ __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles,
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       int i = tile.i0 + c % tx, j = tile.j0 + (c / tx) % ty, k = tile.k0 + c / (tx * ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
+      if (i >= nx || j >= ny || k >= tile.k1) continue;
       int idx = P.off + i + nx * (j + ny * k);
       double Ec = E[idx];
       double tc = 0.0, tg = 0.0, gr2 = 0.0;

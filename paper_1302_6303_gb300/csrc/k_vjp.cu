@@ -57,7 +57,7 @@ __global__ void k_vjp_faces(VjpArgs a) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty, k = tile.k0 + c / (a.tx * a.ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
+      if (i >= nx || j >= ny || k >= tile.k1) continue;
       const int idx = P.off + i + nx * (j + ny * k);
       const int loc[3] = {i, j, k};
       const int st[3] = {1, nx, nx * ny};
@@ -146,7 +146,7 @@ __global__ void k_vjp_cells(VjpArgs a) {
     const int nx = P.n[0], ny = P.n[1], nz = P.n[2];
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       int i = tile.i0 + c % a.tx, j = tile.j0 + (c / a.tx) % a.ty, k = tile.k0 + c / (a.tx * a.ty);
-      if (i >= nx || j >= ny || k >= nz) continue;
+      if (i >= nx || j >= ny || k >= tile.k1) continue;
       const int idx = P.off + i + nx * (j + ny * k);
       const uint8_t m = a.mask[idx];
       if (m & MASK_COVERED) {

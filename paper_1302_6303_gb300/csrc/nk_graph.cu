@@ -13,7 +13,10 @@
 //         v_{j+1} = w/||w||; Givens update of the least-squares problem
 //       dx += sum_i y_i z_i (back substitution on the device)
 //     lambda = min(1, 0.9 min u/(-dx)); u += lambda dx    (positivity cap)
-//     re-linearise at u; Eisenstat-Walker forcing eta_{k+1}
+//     if (lambda = 1 and the solve aimed at the forcing floor):
+//       F(u) alone; re-linearise only if ||F|| > stop
+//     else re-linearise at u
+//     Eisenstat-Walker forcing eta_{k+1}
 //   covered cells := mean of their children
 //
 // The loops are conditional WHILE / IF graph nodes whose conditions are set
@@ -44,6 +47,8 @@ struct NkCtl {
   int j, total, it, krylov, flags, ticks;
   int max_newton, max_krylov;
   int cycles, restarts;           // executions of the cycle and restart bodies
+  int nres, nlin;                 // residual-only and linearising evaluations in the loop
+  int lin_last;                   // the last evaluation linearised (frozen J at u)
 };
 
 struct SmallG {
@@ -84,6 +89,9 @@ __global__ void k_nk_init(NkCtl* c, const double* res, cudaGraphConditionalHandl
   c->restarts = 0;
   c->min_lambda = 1.0;
   c->lam = 1.0;
+  c->nres = 0;
+  c->nlin = 0;
+  c->lin_last = 1;
   c->flags = isfinite(fn) ? 0 : NK_NAN;
   const bool go = tick(c) && !c->flags && fn > c->stop && c->it < c->max_newton;
   cudaGraphSetConditional(hN, go ? 1u : 0u);
@@ -204,6 +212,35 @@ __global__ void k_nk_lambda(NkCtl* c, const double* res) {
   c->krylov += c->total;
 }
 
+// Predicted convergence: a full step (lambda = 1) whose linear solve was
+// asked to reach the forcing floor (tol = eta ||F|| = stop/2) leaves a new
+// residual of about stop/2 plus the nonlinear remainder, so the iterate is
+// probably the last one: evaluate F alone first and linearise only if
+// ||F|| > stop after all (the residual is bit-identical either way).
+__device__ __forceinline__ bool nk_predict(const NkCtl* c) {
+  return !c->flags && c->lam == 1.0 && c->tol <= 0.5 * c->stop * (1.0 + 1e-12);
+}
+
+__global__ void k_nk_predict(NkCtl* c, cudaGraphConditionalHandle hP,
+                             cudaGraphConditionalHandle hL) {
+  const bool pred = nk_predict(c);
+  c->lin_last = pred ? 0 : 1;
+  if (pred) c->nres += 1;
+  else c->nlin += 1;
+  cudaGraphSetConditional(hP, pred ? 1u : 0u);
+  cudaGraphSetConditional(hL, pred ? 0u : 1u);
+}
+
+// after the residual-only evaluation: linearise unless converged
+__global__ void k_nk_checkres(NkCtl* c, const double* res, cudaGraphConditionalHandle hL) {
+  const bool need = !(sqrt(res[G_F]) <= c->stop);
+  if (need) {
+    c->lin_last = 1;
+    c->nlin += 1;
+  }
+  cudaGraphSetConditional(hL, need ? 1u : 0u);
+}
+
 // new residual norm, Eisenstat-Walker forcing (Kelley's safeguarded choice)
 __global__ void k_nk_update(NkCtl* c, const double* res, cudaGraphConditionalHandle hN) {
   c->fold = c->fn;
@@ -242,8 +279,9 @@ struct NkGraph {
   double* zf = nullptr;      // the current preconditioned direction (2N)
   cudaStream_t cs[4] = {nullptr, nullptr, nullptr, nullptr};
   // kernel nodes per execution of: the top level, the Newton body, the cycle
-  // body, the restart body, the Arnoldi body
-  long kn[5] = {0, 0, 0, 0, 0};
+  // body, the restart body, the Arnoldi body, the residual-only evaluation,
+  // the linearising evaluation
+  long kn[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -276,7 +314,7 @@ struct Builder {
   nrd_ctx* c;
   NkGraph* G;
   const double* b;
-  cudaGraphConditionalHandle hN, hC, hR, hA;
+  cudaGraphConditionalHandle hN, hC, hR, hA, hP, hL;
   cudaError_t err = cudaSuccess;
   int rc = NRD_OK;
 
@@ -395,7 +433,17 @@ struct Builder {
     launch_pos_cap(H, c->R, G->uw, c->d_dx, G_CAP, s);
     k_nk_lambda<<<1, 1, 0, s>>>(G->ctl, res());
     launch_axpy_dev(n2, &G->ctl->lam, c->d_dx, G->uw, s);
-    evaluate(s);
+    k_nk_predict<<<1, 1, 0, s>>>(G->ctl, hP, hL);
+    cudaGraph_t bP, bL;
+    if (!ok(add_conditional(s, hP, cudaGraphCondTypeIf, &bP))) return;
+    capture_body(bP, 2, &G->kn[5], [&](cudaStream_t s2) {
+      int r = ctx_residual(c, G->uw, b, 1.0, 1.0, c->d_F, true, s2, par());
+      if (r != NRD_OK) rc = r;
+      launch_wdot_lv(c->H, c->R, c->d_F, c->d_F, G_F, s2);
+      k_nk_checkres<<<1, 1, 0, s2>>>(G->ctl, res(), hL);
+    });
+    if (!ok(add_conditional(s, hL, cudaGraphCondTypeIf, &bL))) return;
+    capture_body(bL, 2, &G->kn[6], [&](cudaStream_t s2) { evaluate(s2); });
     k_nk_update<<<1, 1, 0, s>>>(G->ctl, res(), hN);
   }
 
@@ -405,7 +453,9 @@ struct Builder {
     if (!ok(cudaGraphConditionalHandleCreate(&hN, G->graph, 0, dflt)) ||
         !ok(cudaGraphConditionalHandleCreate(&hC, G->graph, 0, dflt)) ||
         !ok(cudaGraphConditionalHandleCreate(&hR, G->graph, 0, dflt)) ||
-        !ok(cudaGraphConditionalHandleCreate(&hA, G->graph, 0, dflt)))
+        !ok(cudaGraphConditionalHandleCreate(&hA, G->graph, 0, dflt)) ||
+        !ok(cudaGraphConditionalHandleCreate(&hP, G->graph, 0, dflt)) ||
+        !ok(cudaGraphConditionalHandleCreate(&hL, G->graph, 0, dflt)))
       return NRD_ECUDA;
     cudaStream_t s = G->cs[0];
     if (!ok(cudaStreamBeginCaptureToGraph(s, G->graph, nullptr, nullptr, 0,
@@ -512,10 +562,11 @@ int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt,
     c->err = "Newton graph execution failed";
     return NRD_ECUDA;
   }
-  c->lin_ready = true;
+  const NkCtl& h = *G->h_ctl;
+  // the frozen Jacobian belongs to u unless the last evaluation was F alone
+  c->lin_ready = h.lin_last != 0;
   c->lin_dz = false;
   c->pc_ready = true;
-  const NkCtl& h = *G->h_ctl;
   nrd_stats loc{};
   loc.newton_its = h.it;
   loc.krylov_its = h.krylov;
@@ -524,7 +575,8 @@ int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt,
   loc.fnorm = h.fn;
   loc.min_lambda = h.min_lambda;
   loc.kernels = G->kn[0] + (long)h.it * G->kn[1] + (long)h.cycles * G->kn[2] +
-                (long)h.restarts * G->kn[3] + (long)h.krylov * G->kn[4];
+                (long)h.restarts * G->kn[3] + (long)h.krylov * G->kn[4] +
+                (long)h.nres * G->kn[5] + (long)h.nlin * G->kn[6];
   if (h.flags & NK_NEG) {
     loc.status = NRD_ENEG;
     c->err = "positivity cap vanished";

@@ -32,6 +32,8 @@ struct PatchDev {
 struct TileDev {
   int patch;
   int i0, j0, k0;
+  int k1;       // end plane (exclusive): k0 + tile_z, or less at the patch top
+                // and for tiles split in two along z
   int flags;    // bit 0: every cell of the tile is covered
 };
 
@@ -336,8 +338,10 @@ int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt,
                    cudaStream_t s);
 void nk_graph_free(nrd_ctx* c);
 // capi.cu helpers used by the solver
+// par: optional device [a0, dt, beta] read instead of a0, dt (graph-captured
+// solves).  The residual is bit-identical to the one ctx_linearise writes.
 int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
-                 bool fill_ghosts, cudaStream_t s);
+                 bool fill_ghosts, cudaStream_t s, const double* par = nullptr);
 // par: optional device [a0, dt, beta] read by the kernels instead of a0, dt
 // (graph-captured solves; the frozen Jv and the linearisation only)
 int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const double* F0,

@@ -278,6 +278,21 @@ def test_linearise_and_frozen_jv(nrd, name):
     assert np.all(J[~leaf] == 0.0)
 
 
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_bitwise_equals_linearise(nrd, name):
+    """The residual-only evaluation and the linearisation share their face
+    and cell arithmetic: the same F bit for bit (the Newton loop evaluates F
+    alone at a predicted last iterate and relies on this)."""
+    h, z = CASES[name]()
+    ctx, _ = make(nrd, h, z, pc_precision=0)
+    u = _state(h)
+    b = u * 0.97
+    a0, dt = 1.3, 2e-3
+    F1 = ctx.residual(dev(u), dev(b), a0, dt)
+    F2 = ctx.linearise(dev(u), dev(b), a0, dt)
+    assert torch.equal(F1, F2)
+
+
 @pytest.mark.parametrize("name", ["single32", "tiny3", "boundary", "amr2_16"])
 def test_linearise_sets_up_preconditioner(nrd, name):
     h, z = CASES[name]()
