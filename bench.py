@@ -473,6 +473,8 @@ def main():
     line = {
         "metric": "Mcell/s of Jv+V-cycle", "value": value, "unit": "Mcell/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+        "step_ms": {"min": min(r["ms"]), "median": float(np.median(r["ms"])),
+                    "max": max(r["ms"])},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "base": 64, "levels": 2, "leaf_cells": leaf,

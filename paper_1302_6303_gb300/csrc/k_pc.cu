@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int col
                                                        const P* f, P* u) {
   const int fld = blockIdx.y;
   const int4 tl = V.vt[t0 + blockIdx.x];
-  const PatchDev& Pt = V.patches[tl.x & kTilePatch];
+  const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
   const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
   const int t = threadIdx.x;
   const int j = tl.z + rb_j(t), k = tl.w + rb_k(t);
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* u, cons
   const int fld = blockIdx.y;
   const int4 tl = V.vt[blockIdx.x];
   if (tl.x & kTileCovered) return;
-  const PatchDev& Pt = V.patches[tl.x & kTilePatch];
+  const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
   const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
   const int t = threadIdx.x;
   const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(FTHREADS) k_vprolong(VLev<P> V, int t0, const 
                                                         P* pv, P* u) {
   const int fld = blockIdx.y;
   const int4 tl = V.vt[t0 + blockIdx.x];
-  const PatchDev& Pt = V.patches[tl.x & kTilePatch];
+  const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
   const int t = threadIdx.x;
   const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
   if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) return;
@@ -892,24 +892,40 @@ __device__ BoxK<P> tail_view(const TailArgs<P>& a, P* sm, int l) {
   return V;
 }
 
+// body(a, b, c) over an na x nb x nc grid by one CTA.  When a whole number of
+// (a, b) planes fits the block, each thread keeps its (a, b) and steps c (no
+// division in the loop); otherwise a flat index is split per item.
+template <class F>
+__device__ __forceinline__ void cta_for3(int na, int nb, int nc, F body) {
+  const int plane = na * nb, bd = blockDim.x, t = threadIdx.x;
+  if (plane <= bd && bd % plane == 0) {
+    const int a = t % na, b = (t / na) % nb;
+    for (int c = t / plane; c < nc; c += bd / plane) body(a, b, c);
+  } else {
+    for (int q = t; q < plane * nc; q += bd) {
+      const int r = q / na, a = q - r * na;
+      const int c = r / nb, b = r - c * nb;
+      body(a, b, c);
+    }
+  }
+}
+
 // red-black sweeps by one CTA, each thread over the x-pairs of the box
 template <class P>
 __device__ void tail_smooth(const BoxK<P>& V, int sweeps, bool red_first) {
   const int n0 = V.n0, n1 = V.n1;
-  const int hx = (n0 + 1) >> 1, np = hx * n1 * V.n2;
+  const int hx = (n0 + 1) >> 1;
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
       const int colour = red_first ? pass : 1 - pass;
-      for (int p = threadIdx.x; p < np; p += blockDim.x) {
-        const int r = p / hx, px = p - r * hx;
-        const int k = r / n1, j = r - k * n1;
+      cta_for3(hx, n1, V.n2, [&](int px, int j, int k) {
         const int i = 2 * px + ((j + k + colour) & 1);
-        if (i >= n0) continue;
+        if (i >= n0) return;
         P dg, of;
         box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
         const int idx = i + n0 * (j + n1 * k);
         V.e[idx] = (V.f[idx] + of) / dg;
-      }
+      });
       __syncthreads();
     }
 }
@@ -949,11 +965,9 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
     tail_smooth(V, a.nu1, true);
     const BoxRaw& C = a.B[l + 1];
     const int c0 = C.n[0], c1 = C.n[1];
-    const int ncc = c0 * c1 * C.n[2];
     const bool black0 = a.nu1 > 0;
-    for (int c = threadIdx.x; c < ncc; c += blockDim.x) {
-      const int r = c / c0, ci = c - r * c0;
-      const int ck = r / c1, cj = r - ck * c1;
+    P* fc = sm + a.offF[l + 1];
+    cta_for3(c0, c1, C.n[2], [&](int ci, int cj, int ck) {
       P s = P(0);
       for (int q = 0; q < 8; q++) {
         const int x = q & 1, y = (q >> 1) & 1, z = q >> 2;
@@ -964,8 +978,8 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
         box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
         s += V.f[idx] - (dg * V.e[idx] - of);
       }
-      sm[a.offF[l + 1] + c] = s / P(8);
-    }
+      fc[ci + c0 * (cj + c1 * ck)] = s / P(8);
+    });
     __syncthreads();
   }
   tail_smooth(tail_view(a, sm, a.nlev - 1), a.csw, true);
@@ -974,12 +988,10 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
     BoxK<P> V = tail_view(a, sm, l);
     const BoxRaw& C = a.B[l + 1];
     const P* src = sm + a.offE[l + 1];
-    const int nf = V.n0 * V.n1 * V.n2;
-    for (int c = threadIdx.x; c < nf; c += blockDim.x) {
-      const int r = c / V.n0, i = c - r * V.n0;
-      const int k = r / V.n1, j = r - k * V.n1;
-      V.e[c] += tri_interp(src, C.n[0], C.n[1], C.n[2], i, j, k, (const int*)nullptr);
-    }
+    cta_for3(V.n0, V.n1, V.n2, [&](int i, int j, int k) {
+      V.e[i + V.n0 * (j + V.n1 * k)] +=
+          tri_interp(src, C.n[0], C.n[1], C.n[2], i, j, k, (const int*)nullptr);
+    });
     __syncthreads();
     tail_smooth(V, a.nu2, false);
   }

@@ -115,8 +115,16 @@ struct FaceLin {
 // correction: with e = 1 - x r0, 1/x = r0 / (1 - e) = r0 (1 + e + e^2 + ...),
 // so r1 = r0 + r0 (e + e^2) leaves a relative error of e^3 (iterative
 // refinement of reciprocals, see e.g. Muller et al., Handbook of
-// Floating-Point Arithmetic): about 1e-18 before rounding.  For normal
-// x > 0 below 1e300; elsewhere the correctly rounded 1/x.
+// Floating-Point Arithmetic): about 1e-18 before rounding.  For positive
+// x in [2^-997, 2^997) (about 7.5e-301 to 1.3e300); elsewhere (zero,
+// subnormal, negative, huge, inf, NaN) the correctly rounded 1/x.  The range
+// test looks at the high word of x with integer instructions: FP64 compares
+// would take FP64-pipe issue slots, the scarce resource of these kernels.
+__device__ __forceinline__ bool in_refine_range(double x) {
+  // biased exponent in [26, 2020) and sign bit clear
+  const unsigned hi = (unsigned)__double2hiint(x);
+  return hi - (26u << 20) < ((2020u - 26u) << 20);
+}
 __device__ __forceinline__ double rcp_approx(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
@@ -128,7 +136,7 @@ __device__ __forceinline__ double rsqrt_approx(double x) {
   return r;
 }
 __device__ __forceinline__ double rcp_nr(double x) {
-  if (!(x > 1e-300 && x < 1e300)) return 1.0 / x;
+  if (!in_refine_range(x)) return 1.0 / x;
   const double r = rcp_approx(x);
   const double e = fma(-x, r, 1.0);
   return fma(r, fma(e, e, e), r);
@@ -137,10 +145,10 @@ __device__ __forceinline__ double rcp_nr(double x) {
 // 1/sqrt(x) from the PTX approximate FP64 reciprocal square root
 // (rsqrt.approx.ftz.f64) refined with the second-order series: with
 // e = 1 - x y0^2, 1/sqrt(x) = y0 (1 - e)^(-1/2) = y0 (1 + e/2 + 3 e^2/8 + ...),
-// a relative error of about (5/16) e^3 before rounding.  For normal x > 0
-// below 1e300; elsewhere the correctly rounded 1/sqrt(x).
+// a relative error of about (5/16) e^3 before rounding.  For x in the range
+// of rcp_nr; elsewhere the correctly rounded 1/sqrt(x).
 __device__ __forceinline__ double rsqrt_nr(double x) {
-  if (!(x > 1e-300 && x < 1e300)) return 1.0 / sqrt(x);
+  if (!in_refine_range(x)) return 1.0 / sqrt(x);
   const double y = rsqrt_approx(x);
   const double e = fma(-x * y, y, 1.0);
   return fma(y * e, fma(0.375, e, 0.5), y);
