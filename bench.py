@@ -44,8 +44,8 @@ LIN_INST_PER_CELL = 3 * 51 + 36
 # DRAM bytes per launch of that kernel from the committed ncu capture of the
 # same kernel version (profiles/k_stencil_lin_amr2_base64.md), or None when
 # the kernel changed since.
-LIN_TRAFFIC_BYTES = 25.92e6 + 71.25e6
-JV_TRAFFIC_BYTES = 83.10e6 + 9.47e6
+LIN_TRAFFIC_BYTES = 25.79e6 + 69.75e6
+JV_TRAFFIC_BYTES = 83.16e6 + 13.41e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-regrid", action="store_true", help="skip the regrid/transfer leg")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profilers: 1 warm-up + 2 production steps, fixed "
-                         "8x8x8 tiles and V(1,1)/2 sweeps, no plain/CPU/e2e legs; the "
+                         "8x8x4 tiles and V(1,1)/2 sweeps, no plain/CPU/e2e legs; the "
                          "Newton loop runs host-driven so that a profiler sees every kernel "
                          "as its own launch (--profile-graph keeps the graph form)")
     ap.add_argument("--profile-graph", action="store_true")
@@ -76,7 +76,7 @@ def profile_run(args):
     from paper_1302_6303_gb300 import nrd
     h, z, u0 = workload()
     ctx = make_ctx(nrd, h, z, torch, production=True)
-    ctx.set_params(tile_x=8, tile_y=8, tile_z=8, nu1=1, nu2=1, coarse_sweeps=2,
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=4, nu1=1, nu2=1, coarse_sweeps=2,
                    graph=1 if args.profile_graph else 0)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     r = run_steps(ctx, torch, u0, 2, 1, flush, timing=False)
@@ -414,7 +414,7 @@ def main():
     # CUDA events around each of its launches in the timed region
     kt = rk["kernel"]
     hbm_peak, peak_src = peaks()
-    lin_ms, lin_n = kt["residual"]
+    lin_ms, lin_n = kt["linearise"]
     jv_ms, jv_n = kt["jv"]
     t_lin = lin_ms / max(lin_n, 1) * 1e-3
     ach = LIN_INST_PER_CELL * leaf / t_lin / 1e9

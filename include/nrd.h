@@ -417,7 +417,7 @@ int nrd_autotune_sweeps(nrd_ctx* ctx, const double* u_n, const double* u_nm1, do
  * the counters.  nrd_timing_read synchronises on the recorded events and
  * returns the summed device time (ms) and the number of launches. */
 enum {
-  NRD_TK_RESIDUAL = 0,   /* residual stencil (all levels, one launch) */
+  NRD_TK_RESIDUAL = 0,   /* residual-only stencil (all levels, one launch) */
   NRD_TK_JV = 1,         /* analytic-tangent stencil */
   NRD_TK_JV_FD = 2,      /* finite-difference Jv stencil (incl. eps reduction) */
   NRD_TK_PC_APPLY = 3,   /* one P^{-1} application: FAC/GMG V-cycles + P2 */
@@ -425,7 +425,8 @@ enum {
   NRD_TK_ORTHO = 5,      /* CGS2 orthogonalisation of one Krylov vector */
   NRD_TK_GHOST = 6,      /* ghost fill of a direction vector */
   NRD_TK_TRANSFER = 7,   /* regrid transfer: composite copy + gather (ctx_dst) */
-  NRD_TK_COUNT = 8
+  NRD_TK_LINEARISE = 8,  /* residual + linearisation stencil (nrd_linearise, Newton) */
+  NRD_TK_COUNT = 9
 };
 int nrd_timing_enable(nrd_ctx* ctx, int enable);
 int nrd_timing_read(nrd_ctx* ctx, int group, double* ms_host, int64_t* launches_host);

@@ -117,9 +117,9 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.beta = dt / a0;
   io.par = par;
   pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2, &io.p2f);
-  c->timer.begin(NRD_TK_RESIDUAL, s);
+  c->timer.begin(NRD_TK_LINEARISE, s);
   launch_stencil(H, c->mp, c->d_z, c->d_gz, with_dz ? ST_LINZ : ST_LIN, io, s, c->d_z3);
-  c->timer.end(NRD_TK_RESIDUAL, s);
+  c->timer.end(NRD_TK_LINEARISE, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
   c->timer.begin(NRD_TK_PC_SETUP, s);
   int rc = pc_finish(c->pc, H, u, c->d_z, a0, dt, true, s, par != nullptr);

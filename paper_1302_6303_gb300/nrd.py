@@ -33,7 +33,8 @@ EXPORTED = [
     "nrd_timing_read",
 ]
 TK_RESIDUAL, TK_JV, TK_JV_FD, TK_PC_APPLY, TK_PC_SETUP, TK_ORTHO, TK_GHOST, TK_TRANSFER = range(8)
-TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost", "transfer"]
+TK_NAMES = ["residual", "jv", "jv_fd", "pc_apply", "pc_setup", "ortho", "ghost", "transfer",
+            "linearise"]
 
 
 class Params(ctypes.Structure):
