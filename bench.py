@@ -6,9 +6,12 @@ Workload: 2-level AMR, base 64^3, refinement ratio 2, fine patches of
 side 4-12 base cells on z = 1, E0 = 1e-5, T0 = E0^(1/4), Robin R = 1 at x = 0;
 BDF2 steps (first backward Euler) with dt = 5e-4, Newton rtol 1e-8.
 
-One benchmark step = one implicit time step through the public API (nrd_step:
-ghost fill, residual, Jv, GMRES, preconditioner set-up and V-cycles, P2,
-Newton updates) followed by the refinement indicators (nrd_tag).
+One benchmark step = one implicit time step through the public API: the
+generalised leapfrog predictor as the Newton initial guess (nrd_predict, Eq.
+leapfrog), the Newton solve (nrd_step: ghost fill, residual, Jv, GMRES,
+preconditioner set-up and V-cycles, P2, Newton updates), the time derivative
+at the new level for the next prediction (nrd_time_derivative), and the
+refinement indicators (nrd_tag).
 
 metric: Mcell/s of Jv + V-cycle = leaf cells x Krylov iterations (each one Jv
 plus one P^{-1} application) / total implicit-step time.  Reported for the
@@ -164,11 +167,17 @@ def make_ctx(nrd, h, z, torch, production):
 
 def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
     """Integrate warmup + nsteps BDF2 steps (first BE); time the last nsteps
-    with CUDA events per step (L2 flushed between steps, outside the events)."""
+    with CUDA events per step (L2 flushed between steps, outside the events).
+    A step is the paper's: the generalised leapfrog predictor (Eq. leapfrog,
+    with the time derivative from the left-hand side of the previous step)
+    gives the Newton initial guess, the Newton solve, the time derivative at
+    the new level, the refinement indicators."""
     dev = torch.device("cuda")
     un = torch.from_numpy(u0).to(dev)
     unm1 = None
+    udot = None
     u = un.clone()
+    ud_next = torch.empty_like(un)
     tags = None
     times, kry, newt, kern = [], 0, 0, 0
     for s in range(warmup + nsteps):
@@ -180,9 +189,13 @@ def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
         flush.zero_()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
-        u.copy_(un)
+        if udot is None:
+            u.copy_(un)
         ev0.record()
+        if udot is not None:
+            ctx.predict(un, unm1, udot, DT, DT, out=u)
         st = ctx.step(u, un, unm1, DT, DT if unm1 is not None else 0.0)
+        ctx.time_derivative(u, un, unm1, DT, DT if unm1 is not None else 0.0, out=ud_next)
         tags = ctx.tag(u, thr_r=0.1)
         ev1.record()
         torch.cuda.synchronize()
@@ -194,6 +207,7 @@ def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
         unm1 = un
         un = u
         u = torch.empty_like(un)
+        udot, ud_next = ud_next, (udot if udot is not None else torch.empty_like(un))
     kt = ctx.timing_read() if timing else None
     if timing:
         ctx.timing_enable(False)
@@ -203,15 +217,20 @@ def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
 
 def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
     """Same metric through the public API with host buffers: each step copies
-    u_n, u_{n-1} from pinned host memory, steps, tags, and reads u_{n+1} and
-    the tags back."""
+    u_n, u_{n-1} and the time derivative at t_n from pinned host memory,
+    predicts, steps, forms the new time derivative, tags, and reads u_{n+1},
+    its time derivative and the tags back."""
     N2 = u0.size
     hn = torch.from_numpy(u0.copy()).pin_memory()
     hnm1 = None
+    hdot = None
     hout = torch.empty(N2, dtype=torch.float64).pin_memory()
+    hdot_out = torch.empty(N2, dtype=torch.float64).pin_memory()
     htag = torch.empty(N2 // 2, dtype=torch.uint8).pin_memory()
     d_n = torch.empty(N2, dtype=torch.float64, device="cuda")
     d_nm1 = torch.empty_like(d_n)
+    d_dot = torch.empty_like(d_n)
+    d_dot_out = torch.empty_like(d_n)
     d_u = torch.empty_like(d_n)
     total, kry = 0.0, 0
     h2d = d2h = 0
@@ -224,20 +243,29 @@ def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
         if hnm1 is not None:
             d_nm1.copy_(hnm1, non_blocking=True)
             b_in += N2 * 8
-        d_u.copy_(d_n)
+        if hdot is not None:
+            d_dot.copy_(hdot, non_blocking=True)
+            b_in += N2 * 8
+            ctx.predict(d_n, d_nm1, d_dot, DT, DT, out=d_u)
+        else:
+            d_u.copy_(d_n)
         st = ctx.step(d_u, d_n, d_nm1 if hnm1 is not None else None, DT,
                       DT if hnm1 is not None else 0.0)
+        ctx.time_derivative(d_u, d_n, d_nm1 if hnm1 is not None else None, DT,
+                            DT if hnm1 is not None else 0.0, out=d_dot_out)
         t = ctx.tag(d_u, thr_r=0.1)
         hout.copy_(d_u, non_blocking=True)
+        hdot_out.copy_(d_dot_out, non_blocking=True)
         htag.copy_(t, non_blocking=True)
         ev1.record()
         torch.cuda.synchronize()
         if s >= warmup:
             total += ev0.elapsed_time(ev1)
             kry += st["krylov_its"]
-            h2d, d2h = b_in, N2 * 8 + N2 // 2
+            h2d, d2h = b_in, 2 * N2 * 8 + N2 // 2
         hnm1 = hn.clone()
         hn = hout.clone()
+        hdot = hdot_out.clone()
     return total, kry, h2d, d2h
 
 
@@ -468,8 +496,9 @@ def main():
     # kernels executed in the timed region: the Newton graph's kernel nodes
     # times the iterations of their loops (counted by the library), plus the
     # refinement indicators (average-down per covered level, ghost fill, two
-    # reduction kernels, the tag kernel) per step
-    launches = r["kernels"] + args.steps * ((h.nlevels - 1) + 4)
+    # reduction kernels, the tag kernel), the predictor and the time
+    # derivative (one kernel each) per step
+    launches = r["kernels"] + args.steps * ((h.nlevels - 1) + 4 + 2)
     line = {
         "metric": "Mcell/s of Jv+V-cycle", "value": value, "unit": "Mcell/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
@@ -496,8 +525,8 @@ def main():
         "regrid": regrid,
         "clocks": clocks,
         "gpu_launches": launches,
-        "gpu_launches_note": "kernel nodes executed by the Newton graphs plus the tagging "
-                             "kernels, timed steps only",
+        "gpu_launches_note": "kernel nodes executed by the Newton graphs plus the predictor, "
+                             "time-derivative and tagging kernels, timed steps only",
         "kernel_ms_note": "kernel_ms_per_step from the instrumented repeat (host-driven loop)",
         "instrumented_ms_per_step": sum(rk["ms"]) / args.steps,
     }
