@@ -530,41 +530,88 @@ __device__ void coop_sum(const double* part, int nq, double* out, double* sh) {
   __syncthreads();
 }
 
+// V[nv] = (w - V h) * sc, one sweep
+__device__ void orth_final(double* __restrict__ w, double* __restrict__ V, long stride, int N,
+                           int nv, const double* h, double sc) {
+  const int T = gridDim.x * blockDim.x;
+  double* vn = V + (long)nv * stride;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += T) {
+    double wE = w[i], wT = w[N + i];
+    for (int q = 0; q < nv; q++) {
+      wE = fma(-h[q], V[q * stride + i], wE);
+      wT = fma(-h[q], V[q * stride + N + i], wT);
+    }
+    vn[i] = sc * wE;
+    vn[N + i] = sc * wT;
+  }
+}
+
+// A second Gram-Schmidt pass runs when the first one removed more than this
+// fraction of |w|^2 (|w'| < |w| / 100): then one classical pass may have
+// lost orthogonality (its error grows like eps |w| / |w'|) and the
+// Pythagorean norm below would cancel.
+constexpr double kReorthFrac = 1e-4;
+
 // Orthogonalisation of w against the nv = (jd ? *jd : 0) + add columns of V
-// by classical Gram-Schmidt applied twice, with two grid-wide reductions:
-//   pass 1: h1 = V^T W w                                    (barrier)
-//   pass 2: w <- w - V h1; h2 = V^T W w and s = w^T W w     (barrier)
-//   then   V[nv] = (w - V h2) / sqrt(s - |h2|^2)
-// The last norm uses the Pythagorean identity |w - V h2|^2 = |w|^2 - |h2|^2
-// (V orthonormal, h2 = V^T W w), which is well conditioned in the second
-// pass where |h2| << |w| (low-synchronisation Gram-Schmidt, Swirydowicz et
-// al., Numer. Linear Algebra Appl. 2021).  W: leaf volumes (level-weighted
-// dots; w and V vanish on covered cells).  res[slot_h1 + q] = h1,
-// res[slot_h2 + q] = h2, res[slot_nrm] = s - |h2|^2.  Partials ping-pong
-// between pa and pb so that each reduction needs one barrier.
+// by classical Gram-Schmidt with a conditional second pass:
+//   pass 1: h1 = V^T W w and s0 = w^T W w                    (barrier)
+//   s1 = s0 - |h1|^2 = |w - V h1|^2 (Pythagoras, V orthonormal)
+//   if s1 > 1e-4 s0:  V[nv] = (w - V h1) / sqrt(s1)          (h2 = 0)
+//   else:  pass 2: w <- w - V h1; h2 = V^T W w and s = w^T W w  (barrier)
+//          V[nv] = (w - V h2) / sqrt(s - |h2|^2)
+// The first branch is the common one: one grid barrier and two sweeps over
+// V.  The Pythagorean norms are well conditioned where they are used (s1 >
+// 1e-4 s0; |h2| << |w| in the second pass: low-synchronisation
+// Gram-Schmidt, Swirydowicz et al., Numer. Linear Algebra Appl. 2021).  W:
+// leaf volumes (level-weighted dots; w and V vanish on covered cells).
+// res[slot_h1 + q] = h1, res[slot_h2 + q] = h2 (0 without a second pass),
+// res[slot_nrm] = the squared norm of the orthogonalised w.  Partials
+// ping-pong between pa and pb so that each reduction needs one barrier.
+// Every block sums the partials in the same order, so all take the same
+// branch.  always2: the second pass every time (CGS2; solves that need an
+// orthogonal basis to working precision, such as the adjoint's).
 __global__ void __launch_bounds__(256) k_orth_coop(LevW lw, double* __restrict__ w,
                                                    double* __restrict__ V, long stride, int N,
                                                    const int* jd, int add, double* pa, double* pb,
                                                    unsigned* bar, int* err, double* res,
-                                                   int slot_h1, int slot_h2, int slot_nrm) {
+                                                   int slot_h1, int slot_h2, int slot_nrm,
+                                                   int always2) {
   __shared__ double sh[1024];
   __shared__ double h[NVMAX + 1];
+  __shared__ double hu[NVMAX];
+  __shared__ double s_sc, s_nrm;
+  __shared__ int s_re;
   const int nv = min((jd ? *jd : 0) + add, NVMAX - 1);
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   int l0 = 0;
   while (l0 < lw.L - 1 && i0 >= lw.end[l0]) l0++;
 
-  orth_dots<false, false>(lw, l0, w, V, stride, N, nv, nullptr, pa, sh);
+  orth_dots<false, true>(lw, l0, w, V, stride, N, nv, nullptr, pa, sh);
   grid_barrier(bar, err);
-  coop_sum(pa, nv, h, sh);                       // h = h1
-  if (blockIdx.x == 0 && threadIdx.x < nv) res[slot_h1 + threadIdx.x] = h[threadIdx.x];
-  __shared__ double hu[NVMAX];
+  coop_sum(pa, nv + 1, h, sh);                   // h = h1, h[nv] = |w|^2
+  if (threadIdx.x == 0) {
+    double q2 = 0.0;
+    for (int q = 0; q < nv; q++) q2 = fma(h[q], h[q], q2);
+    const double s0 = h[nv], s1 = s0 - q2;
+    const bool re = always2 || !(s1 > kReorthFrac * s0);   // (NaN: the second pass reports it)
+    s_re = re ? 1 : 0;
+    s_nrm = re ? 0.0 : s1;
+    s_sc = re ? 0.0 : 1.0 / sqrt(s1);
+  }
   if (threadIdx.x < nv) hu[threadIdx.x] = h[threadIdx.x];
   __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x < nv) res[slot_h1 + threadIdx.x] = hu[threadIdx.x];
+  if (!s_re) {
+    if (blockIdx.x == 0) {
+      if (threadIdx.x < nv) res[slot_h2 + threadIdx.x] = 0.0;
+      if (threadIdx.x == 0) res[slot_nrm] = s_nrm;
+    }
+    orth_final(w, V, stride, N, nv, hu, s_sc);
+    return;
+  }
   orth_dots<true, true>(lw, l0, w, V, stride, N, nv, hu, pb, sh);
   grid_barrier(bar, err);
   coop_sum(pb, nv + 1, h, sh);                   // h = h2, h[nv] = |w|^2
-  __shared__ double s_sc, s_nrm;
   if (threadIdx.x == 0) {
     double q2 = 0.0;
     for (int q = 0; q < nv; q++) q2 = fma(h[q], h[q], q2);
@@ -577,19 +624,7 @@ __global__ void __launch_bounds__(256) k_orth_coop(LevW lw, double* __restrict__
     if (threadIdx.x < nv) res[slot_h2 + threadIdx.x] = h[threadIdx.x];
     if (threadIdx.x == 0) res[slot_nrm] = s_nrm;
   }
-  // V[nv] = (w - V h2) * sc
-  const double sc = s_sc;
-  const int T = gridDim.x * blockDim.x;
-  double* vn = V + (long)nv * stride;
-  for (int i = i0; i < N; i += T) {
-    double wE = w[i], wT = w[N + i];
-    for (int q = 0; q < nv; q++) {
-      wE = fma(-h[q], V[q * stride + i], wE);
-      wT = fma(-h[q], V[q * stride + N + i], wT);
-    }
-    vn[i] = sc * wE;
-    vn[N + i] = sc * wT;
-  }
+  orth_final(w, V, stride, N, nv, h, s_sc);
 }
 
 // level-weighted <x, y> over both fields for vectors that vanish on covered
@@ -724,7 +759,8 @@ LevW levw_of(const Hier& H) {
 }
 
 int launch_cgs2_coop(const Hier& H, Reducer& R, double* w, double* V, long stride, const int* jd,
-                     int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s) {
+                     int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s,
+                     bool always2) {
   if (R.coop_blocks <= 0) return NRD_ECUDA;
   LevW lw = levw_of(H);
   int N = H.N;
@@ -733,9 +769,10 @@ int launch_cgs2_coop(const Hier& H, Reducer& R, double* w, double* V, long strid
   unsigned* bar = R.d_bar;
   int* err = R.d_err;
   double* res = R.d_res;
+  int a2 = always2 ? 1 : 0;
   void* args[] = {(void*)&lw, (void*)&w, (void*)&V, (void*)&stride, (void*)&N, (void*)&jd,
                   (void*)&add, (void*)&pa, (void*)&pb, (void*)&bar, (void*)&err, (void*)&res,
-                  (void*)&slot_h1, (void*)&slot_h2, (void*)&slot_nrm};
+                  (void*)&slot_h1, (void*)&slot_h2, (void*)&slot_nrm, (void*)&a2};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_orth_coop, dim3(R.coop_blocks),
                                               dim3(RB), args, 0, s);
   return e == cudaSuccess ? NRD_OK : NRD_ECUDA;

@@ -211,12 +211,15 @@ void launch_wdot_lv(const Hier& H, Reducer& R, const double* x, const double* y,
 // squared norm of the orthogonalised w (three launches)
 void launch_cgs2(const Hier& H, Reducer& R, double* w, const double* V, long stride,
                  const int* jd, int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s);
-// one cooperative kernel: classical Gram-Schmidt applied twice with two
-// grid-wide reductions (the second pass's norm by the Pythagorean identity),
-// writing V[nv] = w'' / |w''|.  For vectors that vanish on covered cells.
+// one cooperative kernel: classical Gram-Schmidt with a second pass only
+// when the first removed more than 1 - 1e-4 of |w|^2 (one grid-wide
+// reduction in the common case, two otherwise; norms by the Pythagorean
+// identity), writing V[nv] = w' / |w'|.  For vectors that vanish on covered
+// cells.  always2: the second pass every time (CGS2).
 // Returns NRD_ECUDA if a cooperative launch is not possible.
 int launch_cgs2_coop(const Hier& H, Reducer& R, double* w, double* V, long stride, const int* jd,
-                     int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s);
+                     int add, int slot_h1, int slot_h2, int slot_nrm, cudaStream_t s,
+                     bool always2 = false);
 
 // Preconditioner (k_pc.cu)
 struct PcState;

@@ -207,8 +207,9 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
       total++;
       // CGS2
       c->timer.begin(NRD_TK_ORTHO, s);
+      // the adjoint solve runs to a tight tolerance: always two passes
       if (launch_cgs2_coop(H, c->R, c->d_w, c->d_V, stride, nullptr, j + 1, SL_H1, SL_H2,
-                           SL_NRM, s) != NRD_OK) {
+                           SL_NRM, s, transposed) != NRD_OK) {
         cudaGetLastError();
         launch_cgs2(H, c->R, c->d_w, c->d_V, stride, nullptr, j + 1, SL_H1, SL_H2, SL_NRM, s);
         k_normalize<<<grid1(n2), 256, 0, s>>>(n2, c->d_w, c->d_V + (size_t)(j + 1) * stride,
