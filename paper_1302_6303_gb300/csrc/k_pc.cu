@@ -1093,21 +1093,29 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   else if (m == 0) add_level<P>(ps, H, 0, s);
 }
 
-// r = ff - L^c fu on leaf cells; flux matching; covered cells := mean of
-// their children
+// r = ff - L^c fu on the leaf cells of levels lmin and finer; flux matching;
+// covered cells of those levels := mean of their children.  The caller
+// needs the residual on levels >= lmin only (a level's covered cells take
+// the means of the finer levels): lmin = l - 1 before smoothing level l - 1
+// on the down-leg, lmin = l before smoothing level l on the up-leg, which on
+// the finest level leaves one sweep over that level's tiles.
 template <class P>
-void composite_residual(PcState* ps, const Hier& H, cudaStream_t s) {
+void composite_residual(PcState* ps, const Hier& H, int lmin, cudaStream_t s) {
   const VLev<P> V = vlev<P>(ps, H);
-  k_cresid<P><<<dim3(ps->ntile, 2), FTHREADS, 0, s>>>(V, (const P*)ps->fu, (const P*)ps->ff,
-                                                      (P*)ps->fr, (P*)ps->cf);
-  if (H.L < 2) return;
+  const int t0 = ps->vt0[lmin];
+  VLev<P> Vs = V;
+  Vs.vt = V.vt + t0;
+  k_cresid<P><<<dim3(ps->ntile - t0, 2), FTHREADS, 0, s>>>(Vs, (const P*)ps->fu,
+                                                           (const P*)ps->ff, (P*)ps->fr,
+                                                           (P*)ps->cf);
+  if (H.L < 2 || lmin > H.L - 2) return;
   const int lc = H.L - 2;
   const int n = H.nrf + H.ncov[lc];
   if (n)
     k_reflux_avg<P><<<dim3(g1(n), 2), BS, 0, s>>>(H.d_rf_cell, H.d_rf_off, H.d_rf_g, H.nrf,
                                                   H.d_cov[lc], H.ncov[lc], H.N, H.G,
                                                   (const P*)ps->cf, (P*)ps->fr);
-  for (int l = H.L - 3; l >= 0; l--) {
+  for (int l = H.L - 3; l >= lmin; l--) {
     if (!H.ncov[l]) continue;
     dim3 ga(g1(H.ncov[l]), 2);
     k_avgdown_p<P><<<ga, BS, 0, s>>>(H.d_cov[l], H.ncov[l], (P*)ps->fr, H.N);
@@ -1177,13 +1185,13 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
       level_smooth<P>(ps, H, l, ps->nu1, true, s);
       prolong_finer<P>(ps, H, l, s);
     }
-    composite_residual<P>(ps, H, s);
+    composite_residual<P>(ps, H, l - 1, s);
   }
   gmg_vcycle<P>(ps, H, 0, s);
   prolong_finer<P>(ps, H, 0, s);
   // up: level 1 to finest
   for (int l = 1; l < H.L; l++) {
-    composite_residual<P>(ps, H, s);
+    composite_residual<P>(ps, H, l, s);
     if (ps->nu2 > 0) {
       level_smooth<P>(ps, H, l, ps->nu2, false, s);
       prolong_finer<P>(ps, H, l, s);

@@ -691,6 +691,31 @@ __global__ void k_reflux(RfArgs a, const int* __restrict__ rf_level, const doubl
 
 // Sec. 5 indicators on every cell.  E holds composite values (covered cells
 // already averaged from their children); gE its ghosts.
+// The indicator decisions sqrt(s) / b > t (and a / b > t) exactly as the
+// correctly rounded formula takes them, with the rounded square root and
+// division evaluated only near the threshold: the rounded quotient is within
+// 3e-16 relative of the exact one, and t b, (t b)^2 within 7e-16, so away
+// from a band of 1e-12 around the threshold the squared comparison decides
+// the same.  FP64 square roots and divisions are long instruction sequences
+// on GB300's FP64 pipe.
+__device__ __forceinline__ bool fast_range(double x) { return x > 1e-290 && x < 1e290; }
+__device__ __forceinline__ bool sqrt_ratio_gt(double s, double b, double t) {
+  const double tb = t * b, tb2 = tb * tb;
+  if (b > 0.0 && t >= 0.0 && s >= 0.0 && fast_range(tb2) && s < 1e300) {
+    if (s > tb2 * (1.0 + 1e-12)) return true;
+    if (s < tb2 * (1.0 - 1e-12)) return false;
+  }
+  return sqrt(s) / b > t;
+}
+__device__ __forceinline__ bool ratio_gt(double a, double b, double t) {
+  const double tb = t * b;
+  if (b > 0.0 && t >= 0.0 && a >= 0.0 && fast_range(tb) && a < 1e300) {
+    if (a > tb * (1.0 + 1e-12)) return true;
+    if (a < tb * (1.0 - 1e-12)) return false;
+  }
+  return a / b > t;
+}
+
 __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles, int tx, int ty, int tz,
                       const double* E, const double* gE, double thr_c, double thr_g,
                       double thr_r, const double* emax_p, uint8_t* tags) {
@@ -731,9 +756,9 @@ __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles,
         if (want_r) gr2 = __dadd_rn(gr2, __dmul_rn(__dmul_rn(0.25, df), df));
       }
       uint8_t tag = 0;
-      if (want_c && tc / sc > thr_c) tag |= 1;
-      if (want_g && tg / sc > thr_g) tag |= 2;
-      if (want_r && sqrt(gr2) / Ec > thr_r) tag |= 4;
+      if (want_c && ratio_gt(tc, sc, thr_c)) tag |= 1;
+      if (want_g && ratio_gt(tg, sc, thr_g)) tag |= 2;
+      if (want_r && sqrt_ratio_gt(gr2, Ec, thr_r)) tag |= 4;
       tags[idx] = tag;
     }
   }
