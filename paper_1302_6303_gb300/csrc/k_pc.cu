@@ -236,11 +236,13 @@ __device__ __forceinline__ int ghost_slot(const PatchDev& Pt, int fc, int a, int
 
 // one colour of a red-black pass of the level-l error equation (homogeneous
 // coarse-fine ghosts e_g = e_c/3; sibling cells have the other colour and
-// are read directly); grid (level tiles, 2).  ZERO / ADD as for k_bsmooth.
+// are read directly); grid (level tiles), both fields per thread.  ZERO /
+// ADD as for k_bsmooth.
 template <class P, bool ZERO, bool ADD>
-__global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int colour, P* e,
-                                                       const P* f, P* u) {
-  const int fld = blockIdx.y;
+__global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int colour,
+                                                       P* __restrict__ e,
+                                                       const P* __restrict__ f,
+                                                       P* __restrict__ u) {
   const int4 tl = V.vt[t0 + blockIdx.x];
   const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
   const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
@@ -251,36 +253,67 @@ __global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int col
   const int par = (Pt.lo[0] + Pt.lo[1] + Pt.lo[2] + j + k + colour) & 1;
   const int i = ib + par, ip = ib + 1 - par;
   const int N = V.N;
-  const long fo = (long)fld * N;
-  P* ef = e + fo;
-  const P* A = V.A + fld * V.Afs;
+  P* e0 = e;
+  P* e1 = e + N;
+  const P* A0 = V.A;
+  const P* A1 = V.A + V.Afs;
   const int row = Pt.off + nx * (j + ny * k);
   if (i < nx) {
     const int idx = row + i;
-    P d = P(1), o = P(0), a;
+    P d0 = P(1), o0 = P(0), d1 = P(1), o1 = P(0);
+    auto face = [&](int off, int nb) {
+      const P a0 = A0[off], a1 = A1[off];
+      d0 += a0;
+      d1 += a1;
+      if (!ZERO) {
+        o0 += a0 * e0[nb];
+        o1 += a1 * e1[nb];
+      }
+    };
     auto bnd = [&](int fc, int a1, int b1) {
       const int g = ghost_slot(Pt, fc, a1, b1);
-      const P av = A[3 * N + g];
+      const P av0 = A0[3 * N + g], av1 = A1[3 * N + g];
       const int src = V.gsrc[g].x;
-      if (src >= 0) { d += av; if (!ZERO) o += av * ef[src]; }
-      else if (src < -1) d += P(2.0 / 3.0) * av;
-      else d += av;   // Robin diagonal term, or 0 for Neumann
+      if (src >= 0) {
+        d0 += av0;
+        d1 += av1;
+        if (!ZERO) {
+          o0 += av0 * e0[src];
+          o1 += av1 * e1[src];
+        }
+      } else if (src < -1) {
+        d0 += P(2.0 / 3.0) * av0;
+        d1 += P(2.0 / 3.0) * av1;
+      } else {   // Robin diagonal term, or 0 for Neumann
+        d0 += av0;
+        d1 += av1;
+      }
     };
-    if (i > 0) { a = A[idx]; d += a; if (!ZERO) o += a * ef[idx - 1]; } else bnd(0, j, k);
-    if (i < nx - 1) { a = A[idx + 1]; d += a; if (!ZERO) o += a * ef[idx + 1]; } else bnd(1, j, k);
-    if (j > 0) { a = A[N + idx]; d += a; if (!ZERO) o += a * ef[idx - nx]; } else bnd(2, k, i);
-    if (j < ny - 1) { a = A[N + idx + nx]; d += a; if (!ZERO) o += a * ef[idx + nx]; } else bnd(3, k, i);
     const int s2 = nx * ny;
-    if (k > 0) { a = A[2 * N + idx]; d += a; if (!ZERO) o += a * ef[idx - s2]; } else bnd(4, i, j);
-    if (k < nz - 1) { a = A[2 * N + idx + s2]; d += a; if (!ZERO) o += a * ef[idx + s2]; } else bnd(5, i, j);
-    const P ev = (f[fo + idx] + o) / d;
-    ef[idx] = ev;
-    if (ADD && !(V.mask[idx] & MASK_COVERED)) u[fo + idx] += ev;
+    if (i > 0) face(idx, idx - 1); else bnd(0, j, k);
+    if (i < nx - 1) face(idx + 1, idx + 1); else bnd(1, j, k);
+    if (j > 0) face(N + idx, idx - nx); else bnd(2, k, i);
+    if (j < ny - 1) face(N + idx + nx, idx + nx); else bnd(3, k, i);
+    if (k > 0) face(2 * N + idx, idx - s2); else bnd(4, i, j);
+    if (k < nz - 1) face(2 * N + idx + s2, idx + s2); else bnd(5, i, j);
+    const P ev0 = (f[idx] + o0) / d0, ev1 = (f[N + idx] + o1) / d1;
+    e0[idx] = ev0;
+    e1[idx] = ev1;
+    if (ADD && !(V.mask[idx] & MASK_COVERED)) {
+      u[idx] += ev0;
+      u[N + idx] += ev1;
+    }
   }
   if (ip < nx) {
     const int idx = row + ip;
-    if (ZERO) ef[idx] = P(0);
-    if (ADD && !(V.mask[idx] & MASK_COVERED)) u[fo + idx] += ef[idx];
+    if (ZERO) {
+      e0[idx] = P(0);
+      e1[idx] = P(0);
+    }
+    if (ADD && !(V.mask[idx] & MASK_COVERED)) {
+      u[idx] += e0[idx];
+      u[N + idx] += e1[idx];
+    }
   }
 }
 
@@ -289,11 +322,11 @@ __global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int col
 // from its interpolation terms, Sec. 3.2.1); the fine-side coarse-fine
 // fluxes a (u_g - u_c) go to cf for flux matching.  Faces marked in the mask
 // as coarse sides of coarse-fine faces are left to flux matching; covered
-// cells are left to the average-down.  grid (all tiles, 2).
+// cells are left to the average-down.  grid (tiles); both fields per thread.
 template <class P>
-__global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* u, const P* f, P* r,
-                                                      P* cf) {
-  const int fld = blockIdx.y;
+__global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* __restrict__ u,
+                                                      const P* __restrict__ f,
+                                                      P* __restrict__ r, P* __restrict__ cf) {
   const int4 tl = V.vt[blockIdx.x];
   if (tl.x & kTileCovered) return;
   const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
@@ -302,38 +335,54 @@ __global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* u, cons
   const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
   if (i >= nx || j >= ny || k >= nz) return;
   const int N = V.N;
-  const long fo = (long)fld * N;
   const int idx = Pt.off + i + nx * (j + ny * k);
   const uint8_t m = V.mask[idx];
   if (m & MASK_COVERED) return;
-  const P* A = V.A + fld * V.Afs;
-  const P* uf = u + fo;
-  P* cff = cf + (long)fld * V.G;
+  // both fields in one thread: independent loads, shared index work
+  const P* A0 = V.A;
+  const P* A1 = V.A + V.Afs;
+  const P* u0 = u;
+  const P* u1 = u + N;
   const int s2 = nx * ny;
-  const P uc = uf[idx];
-  P Lu = uc, a;
+  const P uc0 = u0[idx], uc1 = u1[idx];
+  P L0 = uc0, L1 = uc1;
+  auto face = [&](int off, int nb) {
+    const P a0 = A0[off], a1 = A1[off];
+    L0 += a0 * (uc0 - u0[nb]);
+    L1 += a1 * (uc1 - u1[nb]);
+  };
   auto bnd = [&](int fc, int a1, int b1) {
     const int g = ghost_slot(Pt, fc, a1, b1);
-    const P av = A[3 * N + g];
+    const P av0 = A0[3 * N + g], av1 = A1[3 * N + g];
     const int2 src = V.gsrc[g];
     if (src.x >= 0) {
-      Lu += av * (uc - uf[src.x]);
+      L0 += av0 * (uc0 - u0[src.x]);
+      L1 += av1 * (uc1 - u1[src.x]);
     } else if (src.x < -1) {
-      P ug = P(0);
-      for (int q = -2 - src.x; q < src.y; q++) ug += V.gw[q] * uf[V.gidx[q]];
-      Lu += av * (uc - ug);
-      cff[g] = av * (ug - uc);
+      P ug0 = P(0), ug1 = P(0);
+      for (int q = -2 - src.x; q < src.y; q++) {
+        const int c = V.gidx[q];
+        const P w = V.gw[q];
+        ug0 += w * u0[c];
+        ug1 += w * u1[c];
+      }
+      L0 += av0 * (uc0 - ug0);
+      L1 += av1 * (uc1 - ug1);
+      cf[g] = av0 * (ug0 - uc0);
+      cf[(long)V.G + g] = av1 * (ug1 - uc1);
     } else {
-      Lu += av * uc;   // Robin term (0 for Neumann)
+      L0 += av0 * uc0;   // Robin term (0 for Neumann)
+      L1 += av1 * uc1;
     }
   };
-  if (!(m & 2)) { if (i > 0) { a = A[idx]; Lu += a * (uc - uf[idx - 1]); } else bnd(0, j, k); }
-  if (!(m & 4)) { if (i < nx - 1) { a = A[idx + 1]; Lu += a * (uc - uf[idx + 1]); } else bnd(1, j, k); }
-  if (!(m & 8)) { if (j > 0) { a = A[N + idx]; Lu += a * (uc - uf[idx - nx]); } else bnd(2, k, i); }
-  if (!(m & 16)) { if (j < ny - 1) { a = A[N + idx + nx]; Lu += a * (uc - uf[idx + nx]); } else bnd(3, k, i); }
-  if (!(m & 32)) { if (k > 0) { a = A[2 * N + idx]; Lu += a * (uc - uf[idx - s2]); } else bnd(4, i, j); }
-  if (!(m & 64)) { if (k < nz - 1) { a = A[2 * N + idx + s2]; Lu += a * (uc - uf[idx + s2]); } else bnd(5, i, j); }
-  r[fo + idx] = f[fo + idx] - Lu;
+  if (!(m & 2)) { if (i > 0) face(idx, idx - 1); else bnd(0, j, k); }
+  if (!(m & 4)) { if (i < nx - 1) face(idx + 1, idx + 1); else bnd(1, j, k); }
+  if (!(m & 8)) { if (j > 0) face(N + idx, idx - nx); else bnd(2, k, i); }
+  if (!(m & 16)) { if (j < ny - 1) face(N + idx + nx, idx + nx); else bnd(3, k, i); }
+  if (!(m & 32)) { if (k > 0) face(2 * N + idx, idx - s2); else bnd(4, i, j); }
+  if (!(m & 64)) { if (k < nz - 1) face(2 * N + idx + s2, idx + s2); else bnd(5, i, j); }
+  r[idx] = f[idx] - L0;
+  r[N + idx] = f[N + idx] - L1;
 }
 
 // flux matching of the composite operator (each coarse cell with coarse-fine
@@ -394,22 +443,48 @@ __global__ void k_add_leaf(const uint8_t* mask, int c0, int n, int N, const P* e
 }
 
 // v(level m) = trilinear interpolation of src(level m-1) via its dense map;
-// u += v on uncovered level-m cells; PV: also keep v for the next level
+// u += v on uncovered level-m cells; PV: also keep v for the next level.
+// Both fields per thread (the map lookups are shared).
 template <class P, bool PV>
 __global__ void __launch_bounds__(FTHREADS) k_vprolong(VLev<P> V, int t0, const int* cmap,
-                                                        int cn0, int cn1, int cn2, const P* src,
-                                                        P* pv, P* u) {
-  const int fld = blockIdx.y;
+                                                        int cn0, int cn1, int cn2,
+                                                        const P* __restrict__ src,
+                                                        P* __restrict__ pv, P* __restrict__ u) {
   const int4 tl = V.vt[t0 + blockIdx.x];
   const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
   const int t = threadIdx.x;
   const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
   if (i >= Pt.n[0] || j >= Pt.n[1] || k >= Pt.n[2]) return;
-  const long fo = (long)fld * V.N;
+  const int N = V.N;
   const int idx = Pt.off + i + Pt.n[0] * (j + Pt.n[1] * k);
-  const P v = tri_interp(src + fo, cn0, cn1, cn2, Pt.lo[0] + i, Pt.lo[1] + j, Pt.lo[2] + k, cmap);
-  if (PV) pv[fo + idx] = v;
-  if (!(V.mask[idx] & MASK_COVERED)) u[fo + idx] += v;
+  const int q0 = Pt.lo[0] + i, q1 = Pt.lo[1] + j, q2 = Pt.lo[2] + k;
+  const int p0 = q0 >> 1, p1 = q1 >> 1, p2 = q2 >> 1;
+  int o0 = (q0 & 1) ? 1 : -1, o1 = (q1 & 1) ? 1 : -1, o2 = (q2 & 1) ? 1 : -1;
+  if (p0 + o0 < 0 || p0 + o0 >= cn0) o0 = 0;
+  if (p1 + o1 < 0 || p1 + o1 >= cn1) o1 = 0;
+  if (p2 + o2 < 0 || p2 + o2 >= cn2) o2 = 0;
+  int parent = -1;
+  P v0 = P(0), v1 = P(0);
+#pragma unroll
+  for (int q = 0; q < 8; q++) {
+    const int a = q & 1, b = (q >> 1) & 1, d = q >> 2;
+    const P w = (a ? P(0.25) : P(0.75)) * (b ? P(0.25) : P(0.75)) * (d ? P(0.25) : P(0.75));
+    int si = cmap[(p0 + a * o0) + cn0 * ((p1 + b * o1) + cn1 * (p2 + d * o2))];
+    if (si < 0) {   // nesting guard: a missing neighbour takes the parent
+      if (parent < 0) parent = cmap[p0 + cn0 * (p1 + cn1 * p2)];
+      si = parent;
+    }
+    v0 += w * src[si];
+    v1 += w * src[N + si];
+  }
+  if (PV) {
+    pv[idx] = v0;
+    pv[N + idx] = v1;
+  }
+  if (!(V.mask[idx] & MASK_COVERED)) {
+    u[idx] += v0;
+    u[N + idx] += v1;
+  }
 }
 
 // V-cycle input: ff = fr = w (the residual of u = 0), u = 0; TR: w goes
@@ -1105,9 +1180,8 @@ void composite_residual(PcState* ps, const Hier& H, int lmin, cudaStream_t s) {
   const int t0 = ps->vt0[lmin];
   VLev<P> Vs = V;
   Vs.vt = V.vt + t0;
-  k_cresid<P><<<dim3(ps->ntile - t0, 2), FTHREADS, 0, s>>>(Vs, (const P*)ps->fu,
-                                                           (const P*)ps->ff, (P*)ps->fr,
-                                                           (P*)ps->cf);
+  k_cresid<P><<<ps->ntile - t0, FTHREADS, 0, s>>>(Vs, (const P*)ps->fu, (const P*)ps->ff,
+                                                  (P*)ps->fr, (P*)ps->cf);
   if (H.L < 2 || lmin > H.L - 2) return;
   const int lc = H.L - 2;
   const int n = H.nrf + H.ncov[lc];
@@ -1130,7 +1204,7 @@ void prolong_finer(PcState* ps, const Hier& H, int l, cudaStream_t s) {
   const void* src = ps->fe;
   for (int m = l + 1; m < H.L; m++) {
     const LevelInfo& Lc = H.lev[m - 1];
-    const dim3 g(ps->vnt[m], 2);
+    const dim3 g(ps->vnt[m]);
     if (m + 1 < H.L)
       k_vprolong<P, true><<<g, FTHREADS, 0, s>>>(V, ps->vt0[m], H.d_lmap[m - 1], Lc.n[0], Lc.n[1],
                                                  Lc.n[2], (const P*)src, (P*)ps->fp, (P*)ps->fu);
@@ -1146,7 +1220,7 @@ void prolong_finer(PcState* ps, const Hier& H, int l, cudaStream_t s) {
 template <class P>
 void level_smooth(PcState* ps, const Hier& H, int l, int sweeps, bool red_first, cudaStream_t s) {
   const VLev<P> V = vlev<P>(ps, H);
-  const dim3 g(ps->vnt[l], 2);
+  const dim3 g(ps->vnt[l]);
   P* e = (P*)ps->fe;
   const P* f = (const P*)ps->fr;
   P* u = (P*)ps->fu;
