@@ -140,6 +140,8 @@ struct Hier {
   // solver settings
   int restart = 30, max_krylov = 300, jv_mode = JV_FD;
   int nu1 = 2, nu2 = 2, nmg = 4, coarse_sweeps = 4;
+  int smoother = 0;                 // 0 red-black Gauss-Seidel, 1 damped point Jacobi
+  double omega = 6.0 / 7.0;         // Jacobi damping
   double rtol = 1e-8, atol = 0.0;
   int max_newton = 20;
   double eta_max = 0.9, ew_gamma = 0.9, u_min = 1e-6;
@@ -778,6 +780,35 @@ void rbgs(const Grid& G, std::vector<double>& e, const std::vector<double>& f, i
     }
 }
 
+// Damped point Jacobi sweeps (Sec. 4.3 names damped point Jacobi as an
+// alternative smoother): every cell from the previous iterate,
+//   e <- e + omega ((f + off(e)) / diag - e).
+void jacobi(const Grid& G, std::vector<double>& e, const std::vector<double>& f, int sweeps,
+            double omega) {
+  std::vector<double> en;
+  for (int sw = 0; sw < sweeps; sw++) {
+    en = e;
+    for (int k = 0; k < G.O->n[2]; k++)
+      for (int j = 0; j < G.O->n[1]; j++)
+        for (int i = 0; i < G.O->n[0]; i++) {
+          int c[3] = {i, j, k};
+          if (!G.exists(c)) continue;
+          double dg, of;
+          level_row(G, e, c, &dg, &of);
+          const long q = G.di(c);
+          en[q] = e[q] + omega * ((f[q] + of) / dg - e[q]);
+        }
+    e.swap(en);
+  }
+}
+
+// the smoother selected for the V-cycle
+void smooth(const Grid& G, std::vector<double>& e, const std::vector<double>& f, int sweeps,
+            bool red_first) {
+  if (G.H->smoother == 1) jacobi(G, e, f, sweeps, G.H->omega);
+  else rbgs(G, e, f, sweeps, red_first);
+}
+
 // Trilinear prolongation of a coarse dense array to one fine cell q (R13).
 double prolong_at(const int cn[3], const std::vector<double>& ec, const int q[3]) {
   int p[3], o[3];
@@ -801,10 +832,10 @@ double prolong_at(const int cn[3], const std::vector<double>& ec, const int q[3]
 void gmg_vcycle(const Hier& H, int fld, int m, std::vector<double>& e, const std::vector<double>& f) {
   Grid G{&H, &H.mg[fld][m], fld};
   if (m == H.nmg - 1) {
-    rbgs(G, e, f, H.coarse_sweeps, true);
+    smooth(G, e, f, H.coarse_sweeps, true);
     return;
   }
-  rbgs(G, e, f, H.nu1, true);
+  smooth(G, e, f, H.nu1, true);
   std::vector<double> Le;
   level_apply(G, e, Le);
   const Hier::OpLevel& Oc = H.mg[fld][m + 1];
@@ -830,7 +861,7 @@ void gmg_vcycle(const Hier& H, int fld, int m, std::vector<double>& e, const std
         int q[3] = {i, j, k};
         e[G.di(q)] += prolong_at(Oc.n, ec, q);
       }
-  rbgs(G, e, f, H.nu2, false);
+  smooth(G, e, f, H.nu2, false);
 }
 
 // Composite operator L^c of one P1 block applied to a leaf vector x (Sec. 4.3):
@@ -960,7 +991,7 @@ void fac_vcycle(const Hier& H, int fld, const double* f, double* u) {
     gather_level(H, l, r.data(), fl);
     el.assign(fl.size(), 0.0);
     Grid G{&H, &H.opl[fld][l], fld};
-    rbgs(G, el, fl, H.nu1, true);
+    smooth(G, el, fl, H.nu1, true);
     correct_composite(H, l, el, u);
     update_residual();
   }
@@ -973,7 +1004,7 @@ void fac_vcycle(const Hier& H, int fld, const double* f, double* u) {
     gather_level(H, l, r.data(), fl);
     el.assign(fl.size(), 0.0);
     Grid G{&H, &H.opl[fld][l], fld};
-    rbgs(G, el, fl, H.nu2, false);
+    smooth(G, el, fl, H.nu2, false);
     correct_composite(H, l, el, u);
   }
   for (long i = 0; i < N; i++)
@@ -1265,6 +1296,13 @@ void orc_set_solver(orc_hier* h, int restart, int max_krylov, int jv_mode, int n
   H->rtol = rtol;
   H->atol = atol;
   H->max_newton = max_newton;
+}
+
+// smoother of the V-cycle: 0 red-black Gauss-Seidel, 1 damped point Jacobi
+void orc_set_smoother(orc_hier* h, int kind, double omega) {
+  Hier* H = reinterpret_cast<Hier*>(h);
+  H->smoother = kind;
+  H->omega = omega;
 }
 
 void orc_leaf_mask(orc_hier* h, unsigned char* leaf) {

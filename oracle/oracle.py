@@ -56,6 +56,7 @@ def _load():
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, ctypes.c_int]),
         "orc_leaf_mask": (None, [vp, _up]),
+        "orc_set_smoother": (None, [vp, ctypes.c_int, ctypes.c_double]),
         "orc_residual": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
         "orc_residual_scale": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
         "orc_jv_analytic": (None, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp]),
@@ -132,6 +133,10 @@ class Oracle:
             coarse_sweeps = nu1 + nu2
         _lib.orc_set_solver(self._h, restart, max_krylov, jv_mode, nu1, nu2, nmg, coarse_sweeps,
                             rtol, atol, max_newton)
+
+    def set_smoother(self, kind=0, omega=6.0 / 7.0):
+        """V-cycle smoother: 0 red-black Gauss-Seidel, 1 damped point Jacobi."""
+        _lib.orc_set_smoother(self._h, kind, omega)
 
     def leaf_mask(self):
         m = np.zeros(self.N, dtype=np.uint8)

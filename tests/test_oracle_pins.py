@@ -457,6 +457,65 @@ def test_fac_converges_to_direct_solve(three, fld):
     assert errs[3] / errs[2] < 0.5
 
 
+@pytest.mark.parametrize("fld", [0, 1])
+def test_jacobi_sweeps_match_dense_formula(fld):
+    """The damped point Jacobi smoother (Sec. 4.3 names it beside red-black
+    Gauss-Seidel) takes, from e = 0, e_1 = w D^-1 f and then
+    e_(k+1) = e_k + w D^-1 (f - A e_k), with A the dense single-level
+    operator (Robin and Neumann faces) and D its diagonal: the smoothing-only
+    coarsest level (one GMG level) with 1 and 3 sweeps."""
+    h = W.uniform(5)
+    N = h.ncells
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(N)
+    w = 0.7
+    for sweeps in (1, 3):
+        o, _ = _setup_pc(h, nmg=1, coarse_sweeps=sweeps)
+        o.set_smoother(1, w)
+        A = np.zeros((N, N))
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = 1.0
+            A[:, j] = o.comp_apply(fld, e)
+        D = np.diag(A)
+        x = w * f / D
+        for _ in range(sweeps - 1):
+            x = x + w * (f - A @ x) / D
+        y = o.gmg(fld, f)
+        assert np.abs(y - x).max() <= 1e-13 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("fld", [0, 1])
+def test_fac_with_jacobi_converges_to_direct_solve(fld):
+    """FAC (Algorithm 1) with the damped Jacobi smoother on every level and
+    the coarse GMG grids still converges to the dense direct solution of the
+    composite operator."""
+    h = W.tiny_amr(8)
+    o, _ = _setup_pc(h, nmg=3, dt=0.2)
+    o.set_smoother(1, 6.0 / 7.0)
+    leaf = o.leaf_mask()
+    idx = np.nonzero(leaf)[0]
+    N = h.ncells
+    A = np.zeros((idx.size, idx.size))
+    for jj, j in enumerate(idx):
+        e = np.zeros(N)
+        e[j] = 1.0
+        A[:, jj] = o.comp_apply(fld, e)[idx]
+    rng = np.random.default_rng(8)
+    f = np.zeros(N)
+    f[idx] = rng.standard_normal(idx.size)
+    xd = np.linalg.solve(A, f[idx])
+    x = np.zeros(N)
+    errs = []
+    for _ in range(40):
+        r = f - o.comp_apply(fld, x)
+        r[~leaf] = 0.0
+        x += o.fac(fld, r)
+        errs.append(np.abs(x[idx] - xd).max())
+    assert errs[-1] <= 1e-10 * np.abs(xd).max()
+    assert errs[5] / errs[4] < 0.8
+
+
 def test_p2_solve_matches_printed_matrix():
     """y = P^{-1} w = P2^{-1} P1^{-1} w with P2 as printed in Sec. 4.2."""
     h = W.uniform(4)
