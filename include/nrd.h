@@ -91,6 +91,9 @@ enum { NRD_LIM_WILSON = 0, NRD_LIM_PAPER_LITERAL = 1 };
  * (nrd_linearise) and applies them per Krylov iteration (NRD_JV_FROZEN). */
 enum { NRD_JV_FD = 0, NRD_JV_ANALYTIC = 1, NRD_JV_FROZEN = 2 };
 enum { NRD_PC_F64 = 0, NRD_PC_F32 = 1 };
+/* V-cycle smoothers (Sec. 4.3): red-black Gauss-Seidel (the paper's runs) or
+ * damped point Jacobi, e <- e + omega ((f + off(e)) / diag - e) */
+enum { NRD_SMOOTH_RBGS = 0, NRD_SMOOTH_JACOBI = 1 };
 
 /* Solver and model parameters.  nrd_params_default() fills the values used
  * by the paper (Sec. 3.1: k = 0.01; Sec. 4.1: u_min = 1e-6) and the
@@ -103,9 +106,9 @@ typedef struct {
   int max_krylov;      /* cap on Krylov iterations per Newton step */
   int jv_mode;         /* NRD_JV_FD (plain) or NRD_JV_ANALYTIC */
   int pc_precision;    /* NRD_PC_F64 or NRD_PC_F32 V-cycle arithmetic */
-  int nu1, nu2;        /* pre-/post-smoothing red-black GS sweeps */
+  int nu1, nu2;        /* pre-/post-smoothing sweeps */
   int nmg;             /* GMG levels on the base box, including the base */
-  int coarse_sweeps;   /* RB-GS sweeps on the coarsest GMG grid */
+  int coarse_sweeps;   /* smoothing sweeps on the coarsest GMG grid */
   double rtol, atol;   /* Newton stop: ||F|| <= rtol ||F(u0)|| + atol */
   int max_newton;      /* Newton iteration cap */
   double eta_max;      /* Eisenstat-Walker forcing cap (and eta_0) */
@@ -120,6 +123,9 @@ typedef struct {
                           0: host-driven loop, one read-back per Krylov iteration.
                           The host-driven loop is also used while kernel timing is
                           on.  Both give the same iterates up to rounding. */
+  int smoother;        /* NRD_SMOOTH_RBGS (default) or NRD_SMOOTH_JACOBI, on every AMR
+                          level and GMG grid */
+  double omega;        /* damping of NRD_SMOOTH_JACOBI, 0 < omega <= 1 (default 6/7) */
 } nrd_params;
 
 /* Statistics of one Newton solve (nrd_newton / nrd_step). */

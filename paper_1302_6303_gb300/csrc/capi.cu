@@ -46,6 +46,8 @@ int check_params(const nrd_params* p, std::string& err) {
   if (!(p->rtol >= 0.0) || !(p->atol >= 0.0)) { err = "tolerances must be >= 0"; return NRD_EINVAL; }
   if (p->max_newton < 1) { err = "max_newton must be >= 1"; return NRD_EINVAL; }
   if (p->graph != 0 && p->graph != 1) { err = "graph must be 0 or 1"; return NRD_EINVAL; }
+  if (p->smoother != NRD_SMOOTH_RBGS && p->smoother != NRD_SMOOTH_JACOBI) { err = "bad smoother"; return NRD_EINVAL; }
+  if (!(p->omega > 0.0 && p->omega <= 1.0)) { err = "omega must be in (0, 1]"; return NRD_EINVAL; }
   bool ok = (p->tile_x == 0 && p->tile_y == 0 && p->tile_z == 0);
   for (int t = 0; t < kNumShapes && !ok; t++)
     ok = (p->tile_x == kShapes[t][0] && p->tile_y == kShapes[t][1] && p->tile_z == kShapes[t][2]);
@@ -209,6 +211,8 @@ int nrd_params_default(nrd_params* p) {
   p->tile_y = 0;
   p->tile_z = 0;
   p->graph = 1;
+  p->smoother = NRD_SMOOTH_RBGS;
+  p->omega = 6.0 / 7.0;
   return NRD_OK;
 }
 
@@ -252,7 +256,10 @@ int nrd_set_params(nrd_ctx* c, const nrd_params* p) {
   c->p = *p;
   c->gen++;
   set_model(c);
-  if (c->pc) pc_set_sweeps(c->pc, p->nu1, p->nu2, p->coarse_sweeps);
+  if (c->pc) {
+    pc_set_sweeps(c->pc, p->nu1, p->nu2, p->coarse_sweeps);
+    pc_set_smoother(c->pc, p->smoother, p->omega);
+  }
   if (c->have_hier && retile) {
     c->H.tile_x = p->tile_x ? p->tile_x : 32;
     c->H.tile_y = p->tile_y ? p->tile_y : 4;

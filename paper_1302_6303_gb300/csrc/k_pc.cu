@@ -128,6 +128,32 @@ __global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, con
   }
 }
 
+// one damped point Jacobi sweep on a box (Sec. 4.3): ed = es + omega
+// ((f + off(es)) / diag - es); ZERO: es = 0; ADD: u += ed on uncovered cells
+// (level 0).  One cell per thread; grid (tiles x, tiles y, 2 x tiles z).
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(FTHREADS) k_bjacobi(BoxK<P> B, P omega,
+                                                       const P* __restrict__ es,
+                                                       P* __restrict__ ed,
+                                                       const uint8_t* __restrict__ mask,
+                                                       P* __restrict__ u) {
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * VT + ft_i(t), j = blockIdx.y * VT + ft_j(t);
+  const int k = (blockIdx.z - fld * ntz) * VT + ft_k(t);
+  if (i >= B.n0 || j >= B.n1 || k >= B.n2) return;
+  const long fo = fld * B.vfs;
+  const P* e = es + fo;
+  P dg, of;
+  box_row<P, ZERO>(B, B.A + fld * B.Afs, e, i, j, k, dg, of);
+  const int idx = i + B.n0 * (j + B.n1 * k);
+  const P fv = B.f[fo + idx];
+  const P ev = ZERO ? omega * (fv / dg) : e[idx] + omega * ((fv + of) / dg - e[idx]);
+  ed[fo + idx] = ev;
+  if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] += ev;
+}
+
 // coarse rhs = 8-cell average of the fine residual f - L e (Sec. 4.3: simple
 // averaging restriction).  BLACK0: the last pass on the fine box was black,
 // so the residual of the black children is zero (up to rounding) and only
@@ -200,18 +226,20 @@ __device__ __forceinline__ P tri_interp(const P* src, int cn0, int cn1, int cn2,
 }
 
 // e(fine box) += trilinear interpolation of the coarse correction
+// out = e + P ec (out may be e itself)
 template <class P>
 __global__ void __launch_bounds__(FTHREADS) k_bprolong(const P* ec, int cn0, int cn1, int cn2,
-                                                        BoxK<P> F) {
+                                                        BoxK<P> F, P* out) {
   const int ntz = gridDim.z >> 1;
   const int fld = blockIdx.z >= ntz;
   const int t = threadIdx.x;
   const int i = blockIdx.x * VT + ft_i(t), j = blockIdx.y * VT + ft_j(t);
   const int k = (blockIdx.z - fld * ntz) * VT + ft_k(t);
   if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
-  P* e = F.e + fld * F.vfs;
+  const long fo = fld * F.vfs;
   const P* src = ec + fld * ((long)cn0 * cn1 * cn2);
-  e[i + F.n0 * (j + F.n1 * k)] += tri_interp(src, cn0, cn1, cn2, i, j, k, (const int*)nullptr);
+  const int idx = i + F.n0 * (j + F.n1 * k);
+  out[fo + idx] = F.e[fo + idx] + tri_interp(src, cn0, cn1, cn2, i, j, k, (const int*)nullptr);
 }
 
 // ------------------------------------------------- AMR (multi-patch) levels
@@ -314,6 +342,80 @@ __global__ void __launch_bounds__(VTHREADS) k_lsmooth(VLev<P> V, int t0, int col
       u[idx] += e0[idx];
       u[N + idx] += e1[idx];
     }
+  }
+}
+
+// one damped point Jacobi sweep of the level-l error equation (Sec. 4.3):
+// ed = es + omega ((f + off(es)) / diag - es) with the level operator of
+// k_lsmooth; ZERO: es = 0, ed = omega (f / diag); ADD: u += ed on uncovered
+// cells.  One cell per thread, both fields; grid (level tiles).
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(FTHREADS) k_ljacobi(VLev<P> V, int t0, P omega,
+                                                       const P* __restrict__ es,
+                                                       P* __restrict__ ed,
+                                                       const P* __restrict__ f,
+                                                       P* __restrict__ u) {
+  const int4 tl = V.vt[t0 + blockIdx.x];
+  const PatchDev Pt = V.patches[tl.x & kTilePatch];   // a register copy: no reloads after stores
+  const int nx = Pt.n[0], ny = Pt.n[1], nz = Pt.n[2];
+  const int t = threadIdx.x;
+  const int i = tl.y + ft_i(t), j = tl.z + ft_j(t), k = tl.w + ft_k(t);
+  if (i >= nx || j >= ny || k >= nz) return;
+  const int N = V.N;
+  const int idx = Pt.off + i + nx * (j + ny * k);
+  const P* e0 = es;
+  const P* e1 = es + N;
+  const P* A0 = V.A;
+  const P* A1 = V.A + V.Afs;
+  P d0 = P(1), o0 = P(0), d1 = P(1), o1 = P(0);
+  auto face = [&](int off, int nb) {
+    const P a0 = A0[off], a1 = A1[off];
+    d0 += a0;
+    d1 += a1;
+    if (!ZERO) {
+      o0 += a0 * e0[nb];
+      o1 += a1 * e1[nb];
+    }
+  };
+  auto bnd = [&](int fc, int a1, int b1) {
+    const int g = ghost_slot(Pt, fc, a1, b1);
+    const P av0 = A0[3 * N + g], av1 = A1[3 * N + g];
+    const int src = V.gsrc[g].x;
+    if (src >= 0) {
+      d0 += av0;
+      d1 += av1;
+      if (!ZERO) {
+        o0 += av0 * e0[src];
+        o1 += av1 * e1[src];
+      }
+    } else if (src < -1) {
+      d0 += P(2.0 / 3.0) * av0;
+      d1 += P(2.0 / 3.0) * av1;
+    } else {   // Robin diagonal term, or 0 for Neumann
+      d0 += av0;
+      d1 += av1;
+    }
+  };
+  const int s2 = nx * ny;
+  if (i > 0) face(idx, idx - 1); else bnd(0, j, k);
+  if (i < nx - 1) face(idx + 1, idx + 1); else bnd(1, j, k);
+  if (j > 0) face(N + idx, idx - nx); else bnd(2, k, i);
+  if (j < ny - 1) face(N + idx + nx, idx + nx); else bnd(3, k, i);
+  if (k > 0) face(2 * N + idx, idx - s2); else bnd(4, i, j);
+  if (k < nz - 1) face(2 * N + idx + s2, idx + s2); else bnd(5, i, j);
+  P ev0, ev1;
+  if (ZERO) {
+    ev0 = omega * (f[idx] / d0);
+    ev1 = omega * (f[N + idx] / d1);
+  } else {
+    ev0 = e0[idx] + omega * ((f[idx] + o0) / d0 - e0[idx]);
+    ev1 = e1[idx] + omega * ((f[N + idx] + o1) / d1 - e1[idx]);
+  }
+  ed[idx] = ev0;
+  ed[N + idx] = ev1;
+  if (ADD && !(V.mask[idx] & MASK_COVERED)) {
+    u[idx] += ev0;
+    u[N + idx] += ev1;
   }
 }
 
@@ -872,6 +974,11 @@ struct PcState {
   int vt0[NRD_MAX_LEVELS] = {0}, vnt[NRD_MAX_LEVELS] = {0};
   int ntile = 0;
   int2* gsrc = nullptr;  // [G] V-cycle ghost descriptors
+  // smoother (NRD_SMOOTH_*) and the damped-Jacobi scratch vectors
+  int smoother = NRD_SMOOTH_RBGS;
+  double omega = 6.0 / 7.0;
+  void* fj = nullptr;    // [2][N]
+  void* bj[NRD_MAX_MG] = {nullptr};
   void* gwp = nullptr;   // [nterm] coarse-fine weights in precision P
 };
 
@@ -913,6 +1020,34 @@ dim3 tile_grid(int n0, int n1, int n2) {
 
 // red-black sweeps on a box; zero: the first pass starts from e = 0; addu:
 // the last pass adds e to u on uncovered cells (level 0)
+// damped Jacobi sweeps between e and a scratch vector of the same layout:
+// from zero, the first sweep writes whichever buffer makes the last land in
+// e; from the current e, the sweeps alternate starting e -> scratch, and the
+// caller arranges an even count or a start in the scratch (see
+// jacobi_start_in_scratch)
+template <class P>
+void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bool from_scratch,
+                const uint8_t* mask, P* addu, cudaStream_t s) {
+  const dim3 g = tile_grid(V.n0, V.n1, V.n2);
+  P* buf[2] = {V.e, scratch};
+  int cur = zero ? (((sweeps - 1) % 2 == 0) ? 0 : 1) : (from_scratch ? 1 : 0);
+  for (int sw = 0; sw < sweeps; sw++) {
+    const bool D = addu && sw == sweeps - 1;
+    if (zero && sw == 0) {
+      if (D) k_bjacobi<P, true, true><<<g, FTHREADS, 0, s>>>(V, omega, nullptr, buf[cur], mask, addu);
+      else k_bjacobi<P, true, false><<<g, FTHREADS, 0, s>>>(V, omega, nullptr, buf[cur], mask, addu);
+      continue;
+    }
+    if (D) k_bjacobi<P, false, true><<<g, FTHREADS, 0, s>>>(V, omega, buf[cur], buf[1 - cur], mask, addu);
+    else k_bjacobi<P, false, false><<<g, FTHREADS, 0, s>>>(V, omega, buf[cur], buf[1 - cur], mask, addu);
+    cur = 1 - cur;
+  }
+}
+
+// a nonzero start for `sweeps` Jacobi sweeps that must end in e: in the
+// scratch when the count is odd
+inline bool jacobi_start_in_scratch(int sweeps) { return (sweeps % 2) == 1; }
+
 template <class P>
 void box_smooth(const BoxK<P>& V, int sweeps, bool red_first, bool zero, const uint8_t* mask,
                 P* addu, cudaStream_t s) {
@@ -947,6 +1082,8 @@ struct TailArgs {
   P* e0;                          // its correction (output)
   int vfs0;
   int nu1, nu2, csw;
+  int jacobi;                     // smoother: 0 red-black Gauss-Seidel, 1 damped Jacobi
+  P omega;
 };
 
 template <class P>
@@ -985,9 +1122,41 @@ __device__ __forceinline__ void cta_for3(int na, int nb, int nc, F body) {
   }
 }
 
-// red-black sweeps by one CTA, each thread over the x-pairs of the box
+// damped Jacobi sweeps by one CTA: every thread forms the new values of its
+// cells (at most 8: tail levels hold at most 8,192 cells) from the old
+// iterate, then all write
 template <class P>
-__device__ void tail_smooth(const BoxK<P>& V, int sweeps, bool red_first) {
+__device__ void tail_jacobi(const BoxK<P>& V, int sweeps, P omega) {
+  const int n0 = V.n0, n1 = V.n1;
+  for (int sw = 0; sw < sweeps; sw++) {
+    P nv[8];
+    int cnt = 0;
+    cta_for3(n0, n1, V.n2, [&](int i, int j, int k) {
+      P dg, of;
+      box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
+      const int idx = i + n0 * (j + n1 * k);
+      if (cnt < 8) nv[cnt] = V.e[idx] + omega * ((V.f[idx] + of) / dg - V.e[idx]);
+      cnt++;
+    });
+    __syncthreads();
+    cnt = 0;
+    cta_for3(n0, n1, V.n2, [&](int i, int j, int k) {
+      if (cnt < 8) V.e[i + n0 * (j + n1 * k)] = nv[cnt];
+      cnt++;
+    });
+    __syncthreads();
+  }
+}
+
+// red-black sweeps by one CTA, each thread over the x-pairs of the box (or
+// damped Jacobi sweeps)
+template <class P>
+__device__ void tail_smooth(const TailArgs<P>& a, const BoxK<P>& V, int sweeps,
+                            bool red_first) {
+  if (a.jacobi) {
+    tail_jacobi(V, sweeps, a.omega);
+    return;
+  }
   const int n0 = V.n0, n1 = V.n1;
   const int hx = (n0 + 1) >> 1;
   for (int sw = 0; sw < sweeps; sw++)
@@ -1037,10 +1206,10 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
   // sweep the black children's residual is zero)
   for (int l = 0; l + 1 < a.nlev; l++) {
     BoxK<P> V = tail_view(a, sm, l);
-    tail_smooth(V, a.nu1, true);
+    tail_smooth(a, V, a.nu1, true);
     const BoxRaw& C = a.B[l + 1];
     const int c0 = C.n[0], c1 = C.n[1];
-    const bool black0 = a.nu1 > 0;
+    const bool black0 = a.nu1 > 0 && !a.jacobi;
     P* fc = sm + a.offF[l + 1];
     cta_for3(c0, c1, C.n[2], [&](int ci, int cj, int ck) {
       P s = P(0);
@@ -1057,7 +1226,7 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
     });
     __syncthreads();
   }
-  tail_smooth(tail_view(a, sm, a.nlev - 1), a.csw, true);
+  tail_smooth(a, tail_view(a, sm, a.nlev - 1), a.csw, true);
   // up: trilinear prolongation of the coarse correction, smooth
   for (int l = a.nlev - 2; l >= 0; l--) {
     BoxK<P> V = tail_view(a, sm, l);
@@ -1068,7 +1237,7 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
           tri_interp(src, C.n[0], C.n[1], C.n[2], i, j, k, (const int*)nullptr);
     });
     __syncthreads();
-    tail_smooth(V, a.nu2, false);
+    tail_smooth(a, V, a.nu2, false);
   }
   const int nc0 = a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
   for (int q = threadIdx.x; q < nc0; q += blockDim.x) a.e0[fld * a.vfs0 + q] = sm[a.offE[0] + q];
@@ -1098,6 +1267,8 @@ void run_tail(PcState* ps, cudaStream_t s) {
   a.nu1 = ps->nu1;
   a.nu2 = ps->nu2;
   a.csw = ps->csw;
+  a.jacobi = ps->smoother == NRD_SMOOTH_JACOBI;
+  a.omega = (P)ps->omega;
   k_box_tail<P><<<2, kTailThreads, ps->tail_smem, s>>>(a);
 }
 
@@ -1148,24 +1319,38 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
     for (int fld = 0; fld < 2; fld++)
       cudaMemsetAsync((char*)e + fld * vfs * (long)sizeof(P), 0, nc * sizeof(P), s);
   };
+  const bool jac = ps->smoother == NRD_SMOOTH_JACOBI;
+  const P omega = (P)ps->omega;
+  P* scratch = (P*)((m == 0) ? ps->fj : ps->bj[m]);
   if (m == ps->nmg - 1) {
-    if (ps->csw > 0) box_smooth(V, ps->csw, true, true, mask, addu, s);
-    else zero_e();   // no correction
+    if (ps->csw == 0) zero_e();   // no correction
+    else if (jac) box_jacobi(V, omega, scratch, ps->csw, true, false, mask, addu, s);
+    else box_smooth(V, ps->csw, true, true, mask, addu, s);
     return;
   }
-  if (ps->nu1 > 0) box_smooth(V, ps->nu1, true, true, nullptr, (P*)nullptr, s);
-  else zero_e();
+  if (ps->nu1 == 0) zero_e();
+  else if (jac) box_jacobi(V, omega, scratch, ps->nu1, true, false, nullptr, (P*)nullptr, s);
+  else box_smooth(V, ps->nu1, true, true, nullptr, (P*)nullptr, s);
   const BoxRaw& C = ps->box[m + 1];
   const dim3 gc = restrict_grid(C.n[0], C.n[1], C.n[2]);
-  if (ps->nu1 > 0)
+  // after a red-first Gauss-Seidel sweep the black residuals are zero
+  if (ps->nu1 > 0 && !jac)
     k_brestrict<P, true><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);
   else
     k_brestrict<P, false><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);
   gmg_vcycle<P>(ps, H, m + 1, s);
+  // e + P e_c: into the scratch when an odd number of Jacobi sweeps follows,
+  // so that the last one writes e
+  const bool to_scratch = jac && ps->nu2 > 0 && jacobi_start_in_scratch(ps->nu2);
   k_bprolong<P><<<tile_grid(B.n[0], B.n[1], B.n[2]), FTHREADS, 0, s>>>(
-      (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V);
-  if (ps->nu2 > 0) box_smooth(V, ps->nu2, false, false, mask, addu, s);
-  else if (m == 0) add_level<P>(ps, H, 0, s);
+      (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V, to_scratch ? scratch : V.e);
+  if (ps->nu2 == 0) {
+    if (m == 0) add_level<P>(ps, H, 0, s);
+  } else if (jac) {
+    box_jacobi(V, omega, scratch, ps->nu2, false, to_scratch, mask, addu, s);
+  } else {
+    box_smooth(V, ps->nu2, false, false, mask, addu, s);
+  }
 }
 
 // r = ff - L^c fu on the leaf cells of levels lmin and finer; flux matching;
@@ -1219,6 +1404,30 @@ void prolong_finer(PcState* ps, const Hier& H, int l, cudaStream_t s) {
 // last pass adds e to the composite solution
 template <class P>
 void level_smooth(PcState* ps, const Hier& H, int l, int sweeps, bool red_first, cudaStream_t s) {
+  if (ps->smoother == NRD_SMOOTH_JACOBI) {
+    // from zero; the first sweep writes whichever of fe / fj makes the last
+    // land in fe, which also adds the correction to the composite solution
+    const VLev<P> V = vlev<P>(ps, H);
+    const dim3 g(ps->vnt[l]);
+    const int t0 = ps->vt0[l];
+    const P omega = (P)ps->omega;
+    P* buf[2] = {(P*)ps->fe, (P*)ps->fj};
+    const P* f = (const P*)ps->fr;
+    P* u = (P*)ps->fu;
+    int cur = ((sweeps - 1) % 2 == 0) ? 0 : 1;
+    for (int sw = 0; sw < sweeps; sw++) {
+      const bool D = sw == sweeps - 1;
+      if (sw == 0) {
+        if (D) k_ljacobi<P, true, true><<<g, FTHREADS, 0, s>>>(V, t0, omega, nullptr, buf[cur], f, u);
+        else k_ljacobi<P, true, false><<<g, FTHREADS, 0, s>>>(V, t0, omega, nullptr, buf[cur], f, u);
+        continue;
+      }
+      if (D) k_ljacobi<P, false, true><<<g, FTHREADS, 0, s>>>(V, t0, omega, buf[cur], buf[1 - cur], f, u);
+      else k_ljacobi<P, false, false><<<g, FTHREADS, 0, s>>>(V, t0, omega, buf[cur], buf[1 - cur], f, u);
+      cur = 1 - cur;
+    }
+    return;
+  }
   const VLev<P> V = vlev<P>(ps, H);
   const dim3 g(ps->vnt[l]);
   P* e = (P*)ps->fe;
@@ -1295,6 +1504,8 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
   ps->nu1 = p.nu1;
   ps->nu2 = p.nu2;
   ps->csw = p.coarse_sweeps;
+  ps->smoother = p.smoother;
+  ps->omega = p.omega;
   const PatchDev& P0 = H.patches[0];
   for (int m = 1; m < ps->nmg; m++)
     for (int d = 0; d < 3; d++)
@@ -1317,6 +1528,7 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
             cudaMalloc(&ps->fr, 2 * N * e) == cudaSuccess &&
             cudaMalloc(&ps->fe, 2 * N * e) == cudaSuccess &&
             cudaMalloc(&ps->fp, 2 * N * e) == cudaSuccess &&
+            cudaMalloc(&ps->fj, 2 * N * e) == cudaSuccess &&
             cudaMalloc(&ps->ff, 2 * N * e) == cudaSuccess &&
             cudaMalloc(&ps->gh, 2 * std::max(G, 1L) * e) == cudaSuccess &&
             cudaMalloc(&ps->cf, 2 * std::max(G, 1L) * e) == cudaSuccess &&
@@ -1389,6 +1601,7 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
     ok = cudaMalloc(&ps->bCraw[m], 2 * B.AF * sizeof(double)) == cudaSuccess &&
          cudaMalloc(&ps->bA[m], 2 * B.AF * e) == cudaSuccess &&
          cudaMalloc(&ps->be[m], 2 * nc * e) == cudaSuccess &&
+         cudaMalloc(&ps->bj[m], 2 * nc * e) == cudaSuccess &&
          cudaMalloc(&ps->bf[m], 2 * nc * e) == cudaSuccess;
     if (ok) {
       cudaMemset(ps->bCraw[m], 0, 2 * B.AF * sizeof(double));
@@ -1433,11 +1646,13 @@ void pc_drop_graphs(PcState* ps);
 void pc_free(PcState* ps) {
   if (!ps) return;
   auto F = [](void* p) { if (p) cudaFree(p); };
-  F(ps->Craw); F(ps->A); F(ps->fu); F(ps->fr); F(ps->fe); F(ps->fp); F(ps->ff); F(ps->gh);
+  F(ps->Craw); F(ps->A); F(ps->fu); F(ps->fr); F(ps->fe); F(ps->fp); F(ps->fj); F(ps->ff); F(ps->gh);
   F(ps->cf); F(ps->Tk); F(ps->bgt); F(ps->d_beta); F(ps->p2); F(ps->vt); F(ps->gsrc); F(ps->gwp);
   pc_drop_graphs(ps);
   if (ps->cap) cudaStreamDestroy(ps->cap);
-  for (int m = 0; m < NRD_MAX_MG; m++) { F(ps->bCraw[m]); F(ps->bA[m]); F(ps->be[m]); F(ps->bf[m]); }
+  for (int m = 0; m < NRD_MAX_MG; m++) {
+    F(ps->bCraw[m]); F(ps->bA[m]); F(ps->be[m]); F(ps->bj[m]); F(ps->bf[m]);
+  }
   delete ps;
 }
 
@@ -1570,6 +1785,12 @@ static int apply_any(PcState* ps, const Hier& H, const double* w, double* y, boo
 void pc_drop_graphs(PcState* ps) {
   for (auto& g : ps->graphs) cudaGraphExecDestroy(g.exec);
   ps->graphs.clear();
+}
+
+void pc_set_smoother(PcState* ps, int kind, double omega) {
+  if (ps->smoother != kind || ps->omega != omega) pc_drop_graphs(ps);
+  ps->smoother = kind;
+  ps->omega = omega;
 }
 
 void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw) {

@@ -234,6 +234,7 @@ int pc_apply_ex(PcState* ps, const Hier& H, const double* w, double* y, bool tra
 double* pc_craw(PcState* ps);
 void pc_drop_graphs(PcState* ps);
 void pc_set_sweeps(PcState* ps, int nu1, int nu2, int csw);
+void pc_set_smoother(PcState* ps, int kind, double omega);
 // coarsen (and, unless the linearisation already did, scale) after the raw
 // coefficients were written at u
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,

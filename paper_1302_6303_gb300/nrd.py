@@ -20,6 +20,7 @@ BC_NEUMANN, BC_ROBIN = 0, 1
 LIM_WILSON, LIM_PAPER_LITERAL = 0, 1
 JV_FD, JV_ANALYTIC, JV_FROZEN = 0, 1, 2
 PC_F64, PC_F32 = 0, 1
+SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
 DT_EPS, DT_PC47 = 0, 1
 
 EXPORTED = [
@@ -45,7 +46,8 @@ class Params(ctypes.Structure):
         ("nmg", ctypes.c_int), ("coarse_sweeps", ctypes.c_int), ("rtol", ctypes.c_double),
         ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("eta_max", ctypes.c_double),
         ("ew_gamma", ctypes.c_double), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-        ("tile_z", ctypes.c_int), ("graph", ctypes.c_int),
+        ("tile_z", ctypes.c_int), ("graph", ctypes.c_int), ("smoother", ctypes.c_int),
+        ("omega", ctypes.c_double),
     ]
 
 
