@@ -290,7 +290,8 @@ def regrid_leg(nrd, ctx, torch, h, z, r):
     _, cubes = W.config_amr2_cubes(h.n0[0], seed=0)
     cn = make_ctx(nrd, nh, W.material_from_cubes(nh, cubes), torch, production=True)
     cn.set_params(tile_x=ctx.params.tile_x, tile_y=ctx.params.tile_y, tile_z=ctx.params.tile_z,
-                  nu1=ctx.params.nu1, nu2=ctx.params.nu2, coarse_sweeps=ctx.params.coarse_sweeps)
+                  nu1=ctx.params.nu1, nu2=ctx.params.nu2, coarse_sweeps=ctx.params.coarse_sweeps,
+                  smoother=ctx.params.smoother)
     hist = torch.stack([u, r["u_prev"]])
     cn.timing_enable(True)
     torch.cuda.synchronize()
@@ -472,7 +473,7 @@ def main():
     if not args.no_plain:
         ctxp = make_ctx(nrd, h, z, torch, production=False)
         ctxp.set_params(tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], nu1=sweeps[0],
-                        nu2=sweeps[1], coarse_sweeps=sweeps[2])
+                        nu2=sweeps[1], coarse_sweeps=sweeps[2], smoother=sweeps[3])
         rp = run_steps(ctxp, torch, u0, args.steps, args.warmup, flush, timing=False)
         pms = sum(rp["ms"])
         plain = {"form": "FD Jv + FP64 V-cycle", "ms_per_step": pms / args.steps,
@@ -509,7 +510,8 @@ def main():
         "config": {"workload": WORKLOAD, "base": 64, "levels": 2, "leaf_cells": leaf,
                    "patches": sum(h.nboxes), "dt": DT, "newton_rtol": 1e-8,
                    "form": "analytic Jv + FP32 FAC/GMG V-cycle + FGMRES(30)",
-                   "tile": list(tile), "sweeps_nu1_nu2_coarse": list(sweeps),
+                   "tile": list(tile), "sweeps_nu1_nu2_coarse": list(sweeps[:3]),
+                   "smoother": "jacobi" if sweeps[3] == nrd.SMOOTH_JACOBI else "rbgs",
                    "krylov_per_step": r["krylov"] / args.steps,
                    "newton_per_step": r["newton"] / args.steps,
                    "l2": "256 MB buffer written between timed steps",

@@ -407,11 +407,13 @@ int nrd_lte(nrd_ctx* ctx, const double* u_np1, const double* u_p, double alpha, 
 int nrd_dt_control(int kind, double eps_t, double err_n, double err_nm1, double dt_n,
                    double dt_nm1, double* dt_next_host);
 
-/* Sweep-schedule autotuner: for (nu1, nu2, coarse_sweeps) in {(1,0,2) (the
- * paper's V(1,0)), (1,1,2), (2,1,3), (2,2,4), (3,3,6)} times one implicit step
- * from u_n (BE when u_nm1 is NULL, else BDF2) with CUDA events (second of two
- * runs) and keeps the fastest schedule that converges.  Synchronises; uses the
- * context's scratch for the trial states.  nu_out_host[3] receives the choice. */
+/* Smoother autotuner: for (nu1, nu2, coarse_sweeps) in {(1,0,2) (the paper's
+ * V(1,0)), (1,1,2), (2,1,3), (2,2,4), (3,3,6)}, each with red-black
+ * Gauss-Seidel and with damped Jacobi (the context's omega), times one
+ * implicit step from u_n (BE when u_nm1 is NULL, else BDF2) with CUDA events
+ * (second of two runs) and keeps the fastest combination that converges.
+ * Synchronises; uses the context's scratch for the trial states.
+ * nu_out_host[4] receives the choice: nu1, nu2, coarse_sweeps, smoother. */
 int nrd_autotune_sweeps(nrd_ctx* ctx, const double* u_n, const double* u_nm1, double dt,
                         double dt_prev, int* nu_out_host, double* ms_out_host,
                         cudaStream_t stream);

@@ -606,9 +606,16 @@ int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, doub
   int rc = need_ready(c);
   if (rc) return rc;
   if (!u_n || !(dt > 0.0)) return fail(c, NRD_EINVAL, "bad argument");
-  // candidates (nu1, nu2, coarse sweeps): the paper's V(1,0) up to V(3,3)
-  const int cand[][3] = {{1, 0, 2}, {1, 1, 2}, {2, 1, 3}, {2, 2, 4}, {3, 3, 6}};
-  const int ncand = sizeof(cand) / sizeof(cand[0]);
+  // candidates (nu1, nu2, coarse sweeps, smoother): the paper's V(1,0) up to
+  // V(3,3), with red-black Gauss-Seidel and with damped Jacobi (Sec. 4.3)
+  const int sched[][3] = {{1, 0, 2}, {1, 1, 2}, {2, 1, 3}, {2, 2, 4}, {3, 3, 6}};
+  const int nsched = sizeof(sched) / sizeof(sched[0]);
+  int cand[2 * nsched][4];
+  for (int q = 0; q < 2 * nsched; q++) {
+    for (int t = 0; t < 3; t++) cand[q][t] = sched[q % nsched][t];
+    cand[q][3] = (q < nsched) ? NRD_SMOOTH_RBGS : NRD_SMOOTH_JACOBI;
+  }
+  const int ncand = 2 * nsched;
   const size_t n2 = 2 * (size_t)c->H.N;
   bool timer_on = c->timer.on;
   c->timer.on = false;
@@ -621,7 +628,9 @@ int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, doub
     c->p.nu1 = cand[q][0];
     c->p.nu2 = cand[q][1];
     c->p.coarse_sweeps = cand[q][2];
+    c->p.smoother = cand[q][3];
     pc_set_sweeps(c->pc, cand[q][0], cand[q][1], cand[q][2]);
+    pc_set_smoother(c->pc, cand[q][3], c->p.omega);
     c->gen++;
     float ms = 0.0f;
     bool ok = true;
@@ -647,12 +656,15 @@ int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, doub
   c->p.nu1 = cand[best][0];
   c->p.nu2 = cand[best][1];
   c->p.coarse_sweeps = cand[best][2];
+  c->p.smoother = cand[best][3];
   pc_set_sweeps(c->pc, cand[best][0], cand[best][1], cand[best][2]);
+  pc_set_smoother(c->pc, cand[best][3], c->p.omega);
   c->gen++;
   if (nu_out) {
     nu_out[0] = cand[best][0];
     nu_out[1] = cand[best][1];
     nu_out[2] = cand[best][2];
+    nu_out[3] = cand[best][3];
   }
   if (ms_out) *ms_out = best_ms;
   return check_launch(c);

@@ -340,14 +340,16 @@ class Context:
         return (t[0], t[1], t[2]), ms.value
 
     def autotune_sweeps(self, u_n, u_nm1, dt, dt_prev=0.0):
-        """Pick the fastest smoother sweep schedule for one implicit step."""
-        nu = (ctypes.c_int * 3)()
+        """Pick the fastest smoother and sweep schedule for one implicit step;
+        returns ((nu1, nu2, coarse_sweeps, smoother), ms)."""
+        nu = (ctypes.c_int * 4)()
         ms = ctypes.c_double()
         self._check(self.lib.nrd_autotune_sweeps(self._h, _ptr(u_n, torch.float64),
                                                  _ptr(u_nm1, torch.float64), dt, dt_prev, nu,
                                                  ctypes.byref(ms), _stream()))
         self.params.nu1, self.params.nu2, self.params.coarse_sweeps = nu[0], nu[1], nu[2]
-        return (nu[0], nu[1], nu[2]), ms.value
+        self.params.smoother = nu[3]
+        return (nu[0], nu[1], nu[2], nu[3]), ms.value
 
     def time_derivative(self, u_np1, u_n, u_nm1, dt, dt_prev=0.0, out=None):
         out = torch.empty_like(u_n) if out is None else out

@@ -362,7 +362,9 @@ def test_sweep_autotuner_keeps_solution(nrd):
     o.set_solver(nmg=3, jv_mode=O_AN, rtol=1e-10)
     u0 = W.front_state(h, seed=9, noise=0.0, front=0.1, width=0.05)
     nu, ms = ctx.autotune_sweeps(dev(u0), None, 1e-3)
-    assert nu in [(1, 0, 2), (1, 1, 2), (2, 1, 3), (2, 2, 4), (3, 3, 6)] and ms > 0
+    assert nu[:3] in [(1, 0, 2), (1, 1, 2), (2, 1, 3), (2, 2, 4), (3, 3, 6)] and ms > 0
+    assert nu[3] in (nrd.SMOOTH_RBGS, nrd.SMOOTH_JACOBI)
+    assert ctx.params.smoother == nu[3]
     u = dev(u0)
     st = ctx.step(u, dev(u0), None, 1e-3)
     uo, sto = o.newton(u0.copy(), u0.copy(), 1.0, 1e-3)
