@@ -69,6 +69,10 @@ def parse():
                          "Newton loop runs host-driven so that a profiler sees every kernel "
                          "as its own launch (--profile-graph keeps the graph form)")
     ap.add_argument("--profile-graph", action="store_true")
+    ap.add_argument("--profile-pc", type=int, default=0, metavar="N",
+                    help="short run for profilers: N preconditioner applies (cached graph) "
+                         "on the bench workload after one set-up, 8x8x4 tiles, V(1,1)/2 "
+                         "red-black sweeps; prints the mean time per apply")
     return ap.parse_args()
 
 
@@ -84,6 +88,32 @@ def profile_run(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     r = run_steps(ctx, torch, u0, 2, 1, flush, timing=False)
     print(json.dumps({"profile_run": True, "ms": r["ms"], "krylov": r["krylov"]}))
+    return 0
+
+
+def profile_pc_run(args):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd
+    h, z, u0 = workload()
+    ctx = make_ctx(nrd, h, z, torch, production=True)
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=4, nu1=1, nu2=1, coarse_sweeps=2)
+    u = torch.from_numpy(u0).cuda()
+    ctx.precond_setup(u, 1.0, DT)
+    w = torch.from_numpy(np.random.default_rng(5).standard_normal(u0.size)).cuda()
+    y = torch.empty_like(w)
+    ctx.precond_apply(w, out=y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.profile_pc):
+        ctx.precond_apply(w, out=y)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_pc": True, "applies": args.profile_pc,
+                      "us_per_apply": e0.elapsed_time(e1) * 1e3 / args.profile_pc}))
     return 0
 
 
@@ -389,6 +419,8 @@ def main():
         return reference_arm(args)
     if args.profile:
         return profile_run(args)
+    if args.profile_pc:
+        return profile_pc_run(args)
     import torch
     import __graft_entry__ as g
     g.build()
