@@ -252,6 +252,46 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
   if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);
 }
 
+// x += sum_q y_q Z_q (the Newton update from the Krylov basis, both fields of
+// a cell per thread, the same per-element sums as k_lincomb) fused with the
+// positivity cap of the result: min over leaf components with x < 0 of
+// u / (-x), pairs compared by cross-multiplication as in k_poscap, into
+// res[slot] by last-block finishing.  nv = *jd when jd is given (device
+// count), else nvh.
+__global__ void k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* __restrict__ x,
+                              const double* __restrict__ Z, long stride, const int* jd, int nvh,
+                              const double* __restrict__ y, const double* __restrict__ u,
+                              double* part, unsigned* counter, double* res, int slot) {
+  __shared__ double sh[1024];
+  __shared__ double ys[NVMAX];
+  const int nv = min(jd ? *jd : nvh, NVMAX);
+  if (threadIdx.x < nv) ys[threadIdx.x] = y[threadIdx.x];
+  __syncthreads();
+  double ba = 1.0, bb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double s0 = x[i], s1 = x[N + i];
+    for (int q = 0; q < nv; q++) {
+      s0 += ys[q] * Z[q * stride + i];
+      s1 += ys[q] * Z[q * stride + N + i];
+    }
+    x[i] = s0;
+    x[N + i] = s1;
+    const bool leaf = !(mask[i] & MASK_COVERED);
+    if (leaf && s0 < 0.0) {
+      const double a = u[i], b = -s0;
+      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+    }
+    if (leaf && s1 < 0.0) {
+      const double a = u[N + i], b = -s1;
+      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+    }
+  }
+  const double m = (bb > 0.0) ? ba / bb : DBL_MAX;
+  double r = block_red<1>(m, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+  if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);
+}
+
 // ---- variants whose vector count is a device value (graph-captured solves)
 
 // res[q] = <w, V_q>, q < *jd + add, in groups of 4 vectors (w re-read per
@@ -740,6 +780,13 @@ void launch_zero_covered(const Hier& H, double* x, cudaStream_t s) {
 void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v, int slot,
                     cudaStream_t s) {
   k_poscap<<<R.nblk, RB, 0, s>>>(H.d_mask, u, v, H.N, R.d_part, R.d_count, R.d_res, slot);
+}
+
+void launch_lincomb_cap(const Hier& H, Reducer& R, double* x, const double* Z, long stride,
+                        const int* jd, int nv, const double* y, const double* u, int slot,
+                        cudaStream_t s) {
+  k_lincomb_cap<<<R.nblk, RB, 0, s>>>(H.d_mask, H.N, x, Z, stride, jd, nv, y, u, R.d_part,
+                                      R.d_count, R.d_res, slot);
 }
 
 void launch_mdot_dyn(const Hier& H, Reducer& R, const double* w, const double* V, long stride,

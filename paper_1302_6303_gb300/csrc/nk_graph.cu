@@ -415,7 +415,9 @@ struct Builder {
     capture_body(bA, 3, &G->kn[4], [&](cudaStream_t s3) { arnoldi(s3); });
     k_backsub_g<<<1, 1, 0, s>>>(G->ctl, small(), c->kry_m);
     const int n2 = 2 * c->H.N;
-    launch_lincomb_dyn(n2, c->d_dx, c->d_Z, n2, &G->ctl->j, small().y, s);
+    // dx += Z y, with the positivity cap of dx at u (the last cycle's stands)
+    launch_lincomb_cap(c->H, c->R, c->d_dx, c->d_Z, n2, &G->ctl->j, 0, small().y, G->uw, G_CAP,
+                       s);
     k_cycle_end<<<1, 1, 0, s>>>(G->ctl, hC, hR);
   }
 
@@ -430,7 +432,6 @@ struct Builder {
     cudaGraph_t bC;
     if (!ok(add_conditional(s, hC, cudaGraphCondTypeWhile, &bC))) return;
     capture_body(bC, 2, &G->kn[2], [&](cudaStream_t s2) { cycle(s2); });
-    launch_pos_cap(H, c->R, G->uw, c->d_dx, G_CAP, s);
     k_nk_lambda<<<1, 1, 0, s>>>(G->ctl, res());
     launch_axpy_dev(n2, &G->ctl->lam, c->d_dx, G->uw, s);
     k_nk_predict<<<1, 1, 0, s>>>(G->ctl, hP, hL);

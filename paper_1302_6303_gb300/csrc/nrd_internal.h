@@ -196,6 +196,11 @@ void launch_lincomb_dev(int n, double* x, const double* Z, long stride, int nv, 
 void launch_zero_covered(const Hier& H, double* x, cudaStream_t s);
 void launch_pos_cap(const Hier& H, Reducer& R, const double* u, const double* v, int slot,
                     cudaStream_t s);
+// x += sum_q y_q Z_q over nv = (jd ? *jd : nv) columns, and the positivity cap
+// of x at u (as launch_pos_cap) into res[slot]; one launch
+void launch_lincomb_cap(const Hier& H, Reducer& R, double* x, const double* Z, long stride,
+                        const int* jd, int nv, const double* y, const double* u, int slot,
+                        cudaStream_t s);
 // vector counts *jd + add (device values) for graph-captured solves
 void launch_mdot_dyn(const Hier& H, Reducer& R, const double* w, const double* V, long stride,
                      const int* jd, int add, int slot, cudaStream_t s);

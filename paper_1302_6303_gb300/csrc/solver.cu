@@ -231,7 +231,9 @@ static int gmres(nrd_ctx* c, const double* u, const double* b, double a0, double
       }
     }
     k_backsub<<<1, 1, 0, s>>>(S, m, j);
-    launch_lincomb_dev(n2, c->d_dx, c->d_Z, stride, j, S.y, s);
+    // the forward solve's update comes with its positivity cap at u
+    if (transposed) launch_lincomb_dev(n2, c->d_dx, c->d_Z, stride, j, S.y, s);
+    else launch_lincomb_cap(H, c->R, c->d_dx, c->d_Z, stride, nullptr, j, S.y, u, SL_CAP, s);
     if (conv) break;
     if (total >= c->p.max_krylov) break;
     // restart from the true residual r = sign * rhs - A dx
@@ -293,8 +295,9 @@ static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0,
     rc = gmres(c, u, b, a0, dt, c->d_F, -1.0, fn, eta * fn, false, &its, s);
     if (rc != NRD_OK) return rc;
     loc.krylov_its += its;
-    // positivity-constrained update (Sec. 4.1 remark, reading R7)
-    launch_pos_cap(H, c->R, u, c->d_dx, SL_CAP, s);
+    // positivity-constrained update (Sec. 4.1 remark, reading R7): the cap
+    // came with the last update of dx (none without Krylov iterations)
+    if (its == 0) launch_pos_cap(H, c->R, u, c->d_dx, SL_CAP, s);
     double m = read_slot(c, SL_CAP, s);
     double lam = std::min(1.0, 0.9 * m);
     if (!(lam > 0.0)) {
