@@ -26,6 +26,7 @@
 // all loops when it is reached (a bound independent of the tolerances).
 // The arithmetic is that of the host-driven solver in solver.cu (same
 // kernels, same reduction orders, the same forcing and cap rules).
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -95,20 +96,6 @@ __global__ void k_nk_init(NkCtl* c, const double* res, cudaGraphConditionalHandl
   c->flags = isfinite(fn) ? 0 : NK_NAN;
   const bool go = tick(c) && !c->flags && fn > c->stop && c->it < c->max_newton;
   cudaGraphSetConditional(hN, go ? 1u : 0u);
-}
-
-// GMRES start: r_0 = -F (normalised by the next kernel), g = ||r_0|| e_0
-__global__ void k_gm_init(NkCtl* c, SmallG S, int m, cudaGraphConditionalHandle hC,
-                          cudaGraphConditionalHandle hR) {
-  c->rn2 = c->fn * c->fn;
-  c->tol = c->eta * c->fn;
-  c->j = 0;
-  c->total = 0;
-  for (int i = 0; i <= m; i++) S.g[i] = 0.0;
-  S.g[0] = sqrt(c->rn2);
-  c->gres = S.g[0];
-  cudaGraphSetConditional(hC, tick(c) ? 1u : 0u);
-  cudaGraphSetConditional(hR, 0u);
 }
 
 // restart from the true residual r = -F - J dx (its squared norm in res)
@@ -182,36 +169,6 @@ __global__ void k_arnoldi_g(NkCtl* c, SmallG S, int m, const double* res, const 
   cudaGraphSetConditional(hA, go ? 1u : 0u);
 }
 
-__global__ void k_backsub_g(const NkCtl* c, SmallG S, int m) {
-  const int k = c->j;
-  for (int i = k - 1; i >= 0; i--) {
-    double s = S.g[i];
-    for (int t = i + 1; t < k; t++) s -= S.Hm[i + (size_t)(m + 1) * t] * S.y[t];
-    S.y[i] = s / S.Hm[i + (size_t)(m + 1) * i];
-  }
-}
-
-__global__ void k_cycle_end(NkCtl* c, cudaGraphConditionalHandle hC,
-                            cudaGraphConditionalHandle hR) {
-  c->cycles += 1;
-  const bool conv = c->gres <= c->tol;
-  const bool go = tick(c) && !conv && !c->flags && c->total < c->max_krylov;
-  cudaGraphSetConditional(hC, go ? 1u : 0u);
-  cudaGraphSetConditional(hR, go ? 1u : 0u);
-}
-
-// positivity-constrained step length (Sec. 4.1 remark)
-__global__ void k_nk_lambda(NkCtl* c, const double* res) {
-  double lam = fmin(1.0, 0.9 * res[G_CAP]);
-  if (!(lam > 0.0)) {
-    c->flags |= NK_NEG;
-    lam = 0.0;
-  }
-  c->lam = lam;
-  c->min_lambda = fmin(c->min_lambda, lam);
-  c->krylov += c->total;
-}
-
 // Predicted convergence: a full step (lambda = 1) whose linear solve was
 // asked to reach the forcing floor (tol = eta ||F|| = stop/2) leaves a new
 // residual of about stop/2 plus the nonlinear remainder, so the iterate is
@@ -219,16 +176,6 @@ __global__ void k_nk_lambda(NkCtl* c, const double* res) {
 // ||F|| > stop after all (the residual is bit-identical either way).
 __device__ __forceinline__ bool nk_predict(const NkCtl* c) {
   return !c->flags && c->lam == 1.0 && c->tol <= 0.5 * c->stop * (1.0 + 1e-12);
-}
-
-__global__ void k_nk_predict(NkCtl* c, cudaGraphConditionalHandle hP,
-                             cudaGraphConditionalHandle hL) {
-  const bool pred = nk_predict(c);
-  c->lin_last = pred ? 0 : 1;
-  if (pred) c->nres += 1;
-  else c->nlin += 1;
-  cudaGraphSetConditional(hP, pred ? 1u : 0u);
-  cudaGraphSetConditional(hL, pred ? 0u : 1u);
 }
 
 // after the residual-only evaluation: linearise unless converged
@@ -264,6 +211,150 @@ __global__ void k_nk_update(NkCtl* c, const double* res, cudaGraphConditionalHan
 int grid1(long n) {
   long b = (n + 255) / 256;
   return (int)std::max(1L, std::min(b, 152L * 8));
+}
+
+// ---- vector kernels fused with the one-thread control steps around them
+// (the graph form; the host-driven loop in solver.cu does the same
+// arithmetic in separate kernels and on the host).
+
+// block minimum (tree), valid in every thread; blockDim.x a power of two
+__device__ double blk_min(double v, double* sh) {
+  const int t = threadIdx.x;
+  __syncthreads();
+  sh[t] = v;
+  __syncthreads();
+  for (int s = blockDim.x >> 1; s > 0; s >>= 1) {
+    if (t < s) sh[t] = fmin(sh[t], sh[t + s]);
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// true in the block that arrives last (ticket on a counter left at 0)
+__device__ bool last_block(unsigned* counter) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  return last;
+}
+
+// The start of a Newton iteration's GMRES: dx = 0, v_0 = -F / ||F|| and, in
+// block 0, the solve's set-up: tolerance eta ||F||, least-squares right-hand
+// side g = ||r_0|| e_0, the first cycle (no restart).
+__global__ void k_gm_start_g(NkCtl* c, SmallG S, int m, int n, const double* __restrict__ F,
+                             double* __restrict__ V, double* __restrict__ dx,
+                             cudaGraphConditionalHandle hC, cudaGraphConditionalHandle hR) {
+  const double fn = c->fn;
+  __shared__ double sc_s;
+  if (threadIdx.x == 0) {
+    const double d = sqrt(fn * fn);
+    sc_s = (d > 0.0) ? -1.0 / d : 0.0;
+  }
+  __syncthreads();
+  const double sc = sc_s;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    V[i] = sc * F[i];
+    dx[i] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    c->rn2 = fn * fn;
+    c->tol = c->eta * fn;
+    c->j = 0;
+    c->total = 0;
+    for (int i = 0; i <= m; i++) S.g[i] = 0.0;
+    S.g[0] = sqrt(c->rn2);
+    c->gres = S.g[0];
+    cudaGraphSetConditional(hC, tick(c) ? 1u : 0u);
+    cudaGraphSetConditional(hR, 0u);
+  }
+}
+
+// The end of a GMRES cycle: every block solves the k x k triangular system
+// R y = g (back substitution) into shared memory, dx += Z y with the
+// positivity cap of dx at u (as k_lincomb_cap), and the last block finishes
+// the cap's minimum into res[G_CAP] and decides whether another cycle
+// (restart) follows.  256 threads.
+__global__ void __launch_bounds__(256) k_cycle_update_g(
+    NkCtl* c, SmallG S, int m, const uint8_t* __restrict__ mask, int N,
+    double* __restrict__ dx, const double* __restrict__ Z, long stride,
+    const double* __restrict__ u, double* part, unsigned* counter, double* res,
+    cudaGraphConditionalHandle hC, cudaGraphConditionalHandle hR) {
+  __shared__ double ys[NVMAXG];
+  __shared__ double sh[256];
+  const int k = min(c->j, NVMAXG);
+  if (threadIdx.x == 0) {
+    for (int i = k - 1; i >= 0; i--) {
+      double s = S.g[i];
+      for (int t = i + 1; t < k; t++) s -= S.Hm[i + (size_t)(m + 1) * t] * ys[t];
+      ys[i] = s / S.Hm[i + (size_t)(m + 1) * i];
+    }
+    if (blockIdx.x == 0)
+      for (int i = 0; i < k; i++) S.y[i] = ys[i];
+  }
+  __syncthreads();
+  double ba = 1.0, bb = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    double s0 = dx[i], s1 = dx[N + i];
+    for (int q = 0; q < k; q++) {
+      s0 += ys[q] * Z[q * stride + i];
+      s1 += ys[q] * Z[q * stride + N + i];
+    }
+    dx[i] = s0;
+    dx[N + i] = s1;
+    const bool leaf = !(mask[i] & MASK_COVERED);
+    if (leaf && s0 < 0.0) {
+      const double a = u[i], b = -s0;
+      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+    }
+    if (leaf && s1 < 0.0) {
+      const double a = u[N + i], b = -s1;
+      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+    }
+  }
+  const double r = blk_min((bb > 0.0) ? ba / bb : DBL_MAX, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = r;
+  if (last_block(counter)) {
+    double acc = DBL_MAX;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc = fmin(acc, __ldcg(&part[b]));
+    const double mm = blk_min(acc, sh);
+    if (threadIdx.x == 0) {
+      res[G_CAP] = mm;
+      *counter = 0u;
+      c->cycles += 1;
+      const bool conv = c->gres <= c->tol;
+      const bool go = tick(c) && !conv && !c->flags && c->total < c->max_krylov;
+      cudaGraphSetConditional(hC, go ? 1u : 0u);
+      cudaGraphSetConditional(hR, go ? 1u : 0u);
+    }
+  }
+}
+
+// u += lambda dx with lambda = min(1, 0.9 cap) (the positivity-constrained
+// step, Sec. 4.1 remark) and, in block 0, the step's bookkeeping (lambda,
+// its minimum, a vanished cap, the Krylov count) and the last-iterate
+// prediction (nk_predict).
+__global__ void k_nk_step_g(NkCtl* c, const double* res, int n, const double* __restrict__ dx,
+                            double* __restrict__ u, cudaGraphConditionalHandle hP,
+                            cudaGraphConditionalHandle hL) {
+  double lam = fmin(1.0, 0.9 * res[G_CAP]);
+  const bool neg = !(lam > 0.0);
+  if (neg) lam = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    u[i] += lam * dx[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (neg) c->flags |= NK_NEG;
+    c->lam = lam;
+    c->min_lambda = fmin(c->min_lambda, lam);
+    c->krylov += c->total;
+    const bool pred = nk_predict(c);
+    c->lin_last = pred ? 0 : 1;
+    if (pred) c->nres += 1;
+    else c->nlin += 1;
+    cudaGraphSetConditional(hP, pred ? 1u : 0u);
+    cudaGraphSetConditional(hL, pred ? 0u : 1u);
+  }
 }
 
 }  // namespace
@@ -413,28 +504,24 @@ struct Builder {
     k_arn_start<<<1, 1, 0, s>>>(G->ctl, c->kry_m, hA);
     if (!ok(add_conditional(s, hA, cudaGraphCondTypeWhile, &bA))) return;
     capture_body(bA, 3, &G->kn[4], [&](cudaStream_t s3) { arnoldi(s3); });
-    k_backsub_g<<<1, 1, 0, s>>>(G->ctl, small(), c->kry_m);
     const int n2 = 2 * c->H.N;
-    // dx += Z y, with the positivity cap of dx at u (the last cycle's stands)
-    launch_lincomb_cap(c->H, c->R, c->d_dx, c->d_Z, n2, &G->ctl->j, 0, small().y, G->uw, G_CAP,
-                       s);
-    k_cycle_end<<<1, 1, 0, s>>>(G->ctl, hC, hR);
+    // back substitution, dx += Z y with the positivity cap of dx at u (the
+    // last cycle's stands), the cycle-end test
+    k_cycle_update_g<<<c->R.nblk, 256, 0, s>>>(G->ctl, small(), c->kry_m, c->H.d_mask, c->H.N,
+                                               c->d_dx, c->d_Z, n2, G->uw, c->R.d_part,
+                                               c->R.d_count, res(), hC, hR);
   }
 
   // the Newton loop body
   void newton(cudaStream_t s) {
     Hier& H = c->H;
     const int n2 = 2 * H.N;
-    cudaMemsetAsync(c->d_dx, 0, n2 * sizeof(double), s);
-    k_gm_init<<<1, 1, 0, s>>>(G->ctl, small(), c->kry_m, hC, hR);
-    k_normalize_g<<<grid1(n2), 256, 0, s>>>(n2, c->d_F, c->d_V, n2, nullptr, 0, &G->ctl->rn2,
-                                            -1.0);
+    k_gm_start_g<<<grid1(n2), 256, 0, s>>>(G->ctl, small(), c->kry_m, n2, c->d_F, c->d_V,
+                                           c->d_dx, hC, hR);
     cudaGraph_t bC;
     if (!ok(add_conditional(s, hC, cudaGraphCondTypeWhile, &bC))) return;
     capture_body(bC, 2, &G->kn[2], [&](cudaStream_t s2) { cycle(s2); });
-    k_nk_lambda<<<1, 1, 0, s>>>(G->ctl, res());
-    launch_axpy_dev(n2, &G->ctl->lam, c->d_dx, G->uw, s);
-    k_nk_predict<<<1, 1, 0, s>>>(G->ctl, hP, hL);
+    k_nk_step_g<<<grid1(n2), 256, 0, s>>>(G->ctl, res(), n2, c->d_dx, G->uw, hP, hL);
     cudaGraph_t bP, bL;
     if (!ok(add_conditional(s, hP, cudaGraphCondTypeIf, &bP))) return;
     capture_body(bP, 2, &G->kn[5], [&](cudaStream_t s2) {
