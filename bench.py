@@ -52,6 +52,10 @@ JV_TRAFFIC_BYTES = 83.16e6 + 13.41e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
+# and its FP64-pipe instructions per leaf cell, the bound that binds it on
+# GB300: 3 faces x 6 (the two tangent fluxes from the five partials) + 20 per
+# cell (two divergences, the coupling tangent, a0 v - dt (...) for both fields)
+JV_INST_PER_CELL = 3 * 6 + 20
 
 
 def parse():
@@ -501,11 +505,17 @@ def main():
             "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
                            % (LIN_INST_PER_CELL, leaf)}
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
-    ach_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
-    roof_jv = {"kernel": "k_stencil<ST_JVF> (frozen-Jacobian Jv)", "bound": "hbm", "achieved": ach_jv,
-               "peak": hbm_peak, "unit": "GB/s", "frac": ach_jv / hbm_peak,
-               "traffic": JV_TRAFFIC_BYTES,
-               "per_launch_us": t_jv * 1e6, "peak_source": peak_src}
+    ach_jv = JV_INST_PER_CELL * leaf / t_jv / 1e9
+    gbs_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
+    roof_jv = {"kernel": "k_stencil<ST_JVF> (frozen-Jacobian Jv)", "bound": "alu",
+               "achieved": ach_jv, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
+               "frac": ach_jv / fp64_peak, "traffic": JV_TRAFFIC_BYTES,
+               "per_launch_us": t_jv * 1e6,
+               "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
+                              % (JV_INST_PER_CELL, leaf),
+               "hbm": {"achieved": gbs_jv, "peak": hbm_peak, "unit": "GB/s",
+                       "frac": gbs_jv / hbm_peak, "peak_source": peak_src,
+                       "algorithmic": "%d B per leaf cell" % JV_BYTES_PER_CELL}}
 
     # plain form beside it
     plain = None
