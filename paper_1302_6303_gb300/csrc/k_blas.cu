@@ -237,13 +237,14 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const bool leaf = !(mask[i] & MASK_COVERED);
     const double v0 = v[i], v1 = v[N + i];
+    const double u0 = u[i], u1 = u[N + i];   // fetched with v, not after the sign test
     if (leaf && v0 < 0.0) {
-      const double a = u[i], b = -v0;
-      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+      const double b = -v0;
+      if (bb == 0.0 || u0 * bb < ba * b) { ba = u0; bb = b; }
     }
     if (leaf && v1 < 0.0) {
-      const double a = u[N + i], b = -v1;
-      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+      const double b = -v1;
+      if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
     }
   }
   const double m = (bb > 0.0) ? ba / bb : DBL_MAX;
@@ -269,6 +270,9 @@ __global__ void k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* _
   __syncthreads();
   double ba = 1.0, bb = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    // u and the mask are fetched with dx and Z, not after the sign test
+    const double u0 = u[i], u1 = u[N + i];
+    const bool leaf = !(mask[i] & MASK_COVERED);
     double s0 = x[i], s1 = x[N + i];
     for (int q = 0; q < nv; q++) {
       s0 += ys[q] * Z[q * stride + i];
@@ -276,14 +280,13 @@ __global__ void k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* _
     }
     x[i] = s0;
     x[N + i] = s1;
-    const bool leaf = !(mask[i] & MASK_COVERED);
     if (leaf && s0 < 0.0) {
-      const double a = u[i], b = -s0;
-      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+      const double b = -s0;
+      if (bb == 0.0 || u0 * bb < ba * b) { ba = u0; bb = b; }
     }
     if (leaf && s1 < 0.0) {
-      const double a = u[N + i], b = -s1;
-      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+      const double b = -s1;
+      if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
     }
   }
   const double m = (bb > 0.0) ? ba / bb : DBL_MAX;

@@ -775,8 +775,12 @@ __global__ void k_coef(SetupArgs a) {
 }
 
 // covered faces of level l: mean of the 4 coincident faces on level l+1;
-// with A non-null also the scaled coefficient of the target (level l)
-template <class P>
+// with A non-null also the scaled coefficient of the target (level l).
+// SCALED (after the linearisation, which writes scaled coefficients and raw
+// values on Robin faces only): the scaled coefficient of a non-Robin face is
+// the mean of the 4 fine scaled ones over 4 (beta C / h^2 with C the mean of
+// the fine C and h twice the fine h), the Robin faces average the raw D_b.
+template <class P, bool SCALED>
 __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, int N,
                                const uint8_t* gtype, const uint8_t* gface,
                                const double* dbeta, LevelHP lh, int lvl, double* Craw, P* A) {
@@ -787,6 +791,23 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
     int4 s = src[q];
     int t = tgt[q];
+    if (SCALED) {
+      const P* Af = A + fld * AF;
+      double v;
+      const uint8_t ty = (t < 3 * N) ? GT_SIBLING : gtype[t - 3 * N];
+      if (ty == GT_NEUMANN) {
+        v = 0.0;
+      } else if (ty == GT_ROBIN) {
+        const double c = 0.25 * (C[s.x] + C[s.y] + C[s.z] + C[s.w]);
+        C[t] = c;
+        const double h = lh.h[lvl][(gface[t - 3 * N] & 7) / 2];
+        v = (fld == 0) ? beta * 2.0 * c / (h * (4.0 * c + h)) : 0.0;
+      } else {
+        v = 0.0625 * ((double)Af[s.x] + (double)Af[s.y] + (double)Af[s.z] + (double)Af[s.w]);
+      }
+      A[fld * AF + t] = (P)v;
+      continue;
+    }
     double c = 0.25 * (C[s.x] + C[s.y] + C[s.z] + C[s.w]);
     C[t] = c;
     if (!A) continue;
@@ -863,12 +884,17 @@ struct BoxRaw {
 // fused with the scaling of the coarse level:
 // A = beta C / h^2 on interior faces, beta 2 D_b / (h (4 D_b + h)) on Robin
 // faces of E, 0 elsewhere; rh2 = 1/h^2 per axis of the coarse level.
-template <class P>
+// SCALED (after the linearisation): interior faces average the finer
+// level's scaled coefficients Ain (the mean over 4, as the raw C, then
+// 1/4 for the doubled h), box faces the raw Robin D_b.
+template <class P, bool SCALED>
 __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_raw,
                               const int* gtype_box, const double* dbeta, double hx, double hy,
-                              double hz, double rh2x, double rh2y, double rh2z, P* A) {
+                              double hz, double rh2x, double rh2y, double rh2z, P* A,
+                              const P* Ain) {
   const int fld = blockIdx.y;
   const double* cf = Cf + fld * F.AF;
+  const P* ain = SCALED ? Ain + fld * F.AF : nullptr;
   double* cc = Cc_raw + fld * Cc.AF;
   P* Af = A + fld * Cc.AF;
   const double beta = *dbeta;
@@ -898,10 +924,14 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
             p[t1] = 2 * q[t1] + a;
             p[t2] = 2 * q[t2] + b;
             const int fi = p[0] + F.n[0] * (p[1] + F.n[1] * p[2]);
-            s += cf[d * fNA + fi];
+            s += SCALED ? (double)ain[d * fNA + fi] : cf[d * fNA + fi];
           }
-        cc[d * cNA + c] = 0.25 * s;
-        Af[d * cNA + c] = (P)(0.25 * s * bh2[d]);
+        if (SCALED) {
+          Af[d * cNA + c] = (P)(0.0625 * s);
+        } else {
+          cc[d * cNA + c] = 0.25 * s;
+          Af[d * cNA + c] = (P)(0.25 * s * bh2[d]);
+        }
       }
       for (int sd = 0; sd < 2; sd++) {
         bool at = sd ? (q[d] == Cc.n[d] - 1) : (q[d] == 0);
@@ -1721,17 +1751,19 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
     if (!H.ncz[l]) continue;
     dim3 g(g1(H.ncz[l]), 2);
     if (from_lin && ps->prec == NRD_PC_F32)
-      k_coef_coarsen<float><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
-                                             H.d_gtype, H.d_gface, ps->d_beta, a.lh, l, ps->Craw,
-                                             (float*)ps->A);
+      k_coef_coarsen<float, true><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF,
+                                                   H.N, H.d_gtype, H.d_gface, ps->d_beta, a.lh,
+                                                   l, ps->Craw, (float*)ps->A);
     else if (from_lin)
-      k_coef_coarsen<double><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
-                                              H.d_gtype, H.d_gface, ps->d_beta, a.lh, l, ps->Craw,
-                                              (double*)ps->A);
+      k_coef_coarsen<double, true><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l],
+                                                    ps->AF, H.N, H.d_gtype, H.d_gface,
+                                                    ps->d_beta, a.lh, l, ps->Craw,
+                                                    (double*)ps->A);
     else
-      k_coef_coarsen<float><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l], ps->AF, H.N,
-                                             H.d_gtype, H.d_gface, ps->d_beta, a.lh, l, ps->Craw,
-                                             (float*)nullptr);
+      k_coef_coarsen<float, false><<<g, BS, 0, s>>>(H.d_cz_tgt[l], H.d_cz_src[l], H.ncz[l],
+                                                    ps->AF, H.N, H.d_gtype, H.d_gface,
+                                                    ps->d_beta, a.lh, l, ps->Craw,
+                                                    (float*)nullptr);
   }
   // GMG levels
   for (int m = 1; m < ps->nmg; m++) {
@@ -1742,14 +1774,25 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
     dim3 g(g1(nc), 2);
     const double* hb = ps->bh[m];
     const double r2[3] = {1.0 / (hb[0] * hb[0]), 1.0 / (hb[1] * hb[1]), 1.0 / (hb[2] * hb[2])};
-    if (ps->prec == NRD_PC_F32)
-      k_box_coarsen<float><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta, hb[0],
-                                            hb[1], hb[2], r2[0], r2[1], r2[2],
-                                            (float*)ps->bA[m]);
+    // after the linearisation the finer level's scaled coefficients are the
+    // source (raw values exist on Robin faces only)
+    const void* Ain = (m == 1) ? ps->A : ps->bA[m - 1];
+    if (ps->prec == NRD_PC_F32 && from_lin)
+      k_box_coarsen<float, true><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
+                                                  hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
+                                                  (float*)ps->bA[m], (const float*)Ain);
+    else if (ps->prec == NRD_PC_F32)
+      k_box_coarsen<float, false><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
+                                                   hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
+                                                   (float*)ps->bA[m], (const float*)nullptr);
+    else if (from_lin)
+      k_box_coarsen<double, true><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
+                                                   hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
+                                                   (double*)ps->bA[m], (const double*)Ain);
     else
-      k_box_coarsen<double><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta, hb[0],
-                                             hb[1], hb[2], r2[0], r2[1], r2[2],
-                                             (double*)ps->bA[m]);
+      k_box_coarsen<double, false><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
+                                                    hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
+                                                    (double*)ps->bA[m], (const double*)nullptr);
   }
   if (!from_lin) {
     if (ps->prec == NRD_PC_F32) scale_all<float>(ps, H, a, s);

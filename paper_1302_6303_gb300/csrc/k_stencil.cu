@@ -488,8 +488,6 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         PT = 0.0;
         if (LIN) {
           for (int q = 0; q < 6; q++) io.jc[q * NS + fslot] = 0.0;
-          io.craw[fslot] = 0.0;
-          io.craw[NS + fslot] = 0.0;
           put_scaled(io, NS, fslot, 0.0, 0.0);
         }
       } else if (gt == GT_ROBIN) {
@@ -534,16 +532,16 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.jc[3 * NS + fslot] = L.bTa;
           io.jc[4 * NS + fslot] = L.bTb;
           if (DZ) io.jc[5 * NS + fslot] = L.aZ;
-          io.craw[fslot] = L.CE;
-          io.craw[NS + fslot] = L.CT;
+          // only the scaled P1 coefficients: the coarsening averages them
+          // (raw values are kept for Robin faces alone)
           if (io.a32) {
             io.a32[fslot] = (float)L.X * s_bh[3 * lvl + dir];
             io.a32[NS + fslot] = (float)L.T25 * s_bk[3 * lvl + dir];
           } else {
-            const double rhd = A.lh.rh[lvl][dir];
-            const double b2 = io.par ? betav * rhd * rhd : A.lh.bh2[lvl][dir];
-            io.a64[fslot] = L.CE * b2;
-            io.a64[NS + fslot] = L.CT * b2;
+            // beta D_E / h^2 = X beta / h, beta D_T / h^2 = T^(5/2) beta k / h^2
+            const double bh = betav * A.lh.rh[lvl][dir];
+            io.a64[fslot] = L.X * bh;
+            io.a64[NS + fslot] = L.T25 * (bh * A.k * A.lh.rh[lvl][dir]);
           }
         } else {
           const FaceCore q = face_core(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh,

@@ -296,6 +296,9 @@ __global__ void __launch_bounds__(256) k_cycle_update_g(
   __syncthreads();
   double ba = 1.0, bb = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    // u and the mask are fetched with dx and Z, not after the sign test
+    const double u0 = u[i], u1 = u[N + i];
+    const bool leaf = !(mask[i] & MASK_COVERED);
     double s0 = dx[i], s1 = dx[N + i];
     for (int q = 0; q < k; q++) {
       s0 += ys[q] * Z[q * stride + i];
@@ -303,14 +306,13 @@ __global__ void __launch_bounds__(256) k_cycle_update_g(
     }
     dx[i] = s0;
     dx[N + i] = s1;
-    const bool leaf = !(mask[i] & MASK_COVERED);
     if (leaf && s0 < 0.0) {
-      const double a = u[i], b = -s0;
-      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+      const double b = -s0;
+      if (bb == 0.0 || u0 * bb < ba * b) { ba = u0; bb = b; }
     }
     if (leaf && s1 < 0.0) {
-      const double a = u[N + i], b = -s1;
-      if (bb == 0.0 || a * bb < ba * b) { ba = a; bb = b; }
+      const double b = -s1;
+      if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
     }
   }
   const double r = blk_min((bb > 0.0) ? ba / bb : DBL_MAX, sh);
