@@ -438,20 +438,32 @@ __global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* __restr
   if (i >= nx || j >= ny || k >= nz) return;
   const int N = V.N;
   const int idx = Pt.off + i + nx * (j + ny * k);
-  const uint8_t m = V.mask[idx];
-  if (m & MASK_COVERED) return;
   // both fields in one thread: independent loads, shared index work
   const P* A0 = V.A;
   const P* A1 = V.A + V.Afs;
   const P* u0 = u;
   const P* u1 = u + N;
   const int s2 = nx * ny;
+  // the in-patch faces' coefficients and neighbour values are fetched before
+  // the mask is known (it only selects which of them count)
+  const int off6[6] = {idx, idx + 1, N + idx, N + idx + nx, 2 * N + idx, 2 * N + idx + s2};
+  const int nb6[6] = {idx - 1, idx + 1, idx - nx, idx + nx, idx - s2, idx + s2};
+  const bool in6[6] = {i > 0, i < nx - 1, j > 0, j < ny - 1, k > 0, k < nz - 1};
+  P fa0[6], fa1[6], fv0[6], fv1[6];
+#pragma unroll
+  for (int q = 0; q < 6; q++) {
+    fa0[q] = in6[q] ? A0[off6[q]] : P(0);
+    fa1[q] = in6[q] ? A1[off6[q]] : P(0);
+    fv0[q] = in6[q] ? u0[nb6[q]] : P(0);
+    fv1[q] = in6[q] ? u1[nb6[q]] : P(0);
+  }
+  const uint8_t m = V.mask[idx];
   const P uc0 = u0[idx], uc1 = u1[idx];
+  if (m & MASK_COVERED) return;
   P L0 = uc0, L1 = uc1;
-  auto face = [&](int off, int nb) {
-    const P a0 = A0[off], a1 = A1[off];
-    L0 += a0 * (uc0 - u0[nb]);
-    L1 += a1 * (uc1 - u1[nb]);
+  auto face = [&](int q) {
+    L0 += fa0[q] * (uc0 - fv0[q]);
+    L1 += fa1[q] * (uc1 - fv1[q]);
   };
   auto bnd = [&](int fc, int a1, int b1) {
     const int g = ghost_slot(Pt, fc, a1, b1);
@@ -477,12 +489,12 @@ __global__ void __launch_bounds__(FTHREADS) k_cresid(VLev<P> V, const P* __restr
       L1 += av1 * uc1;
     }
   };
-  if (!(m & 2)) { if (i > 0) face(idx, idx - 1); else bnd(0, j, k); }
-  if (!(m & 4)) { if (i < nx - 1) face(idx + 1, idx + 1); else bnd(1, j, k); }
-  if (!(m & 8)) { if (j > 0) face(N + idx, idx - nx); else bnd(2, k, i); }
-  if (!(m & 16)) { if (j < ny - 1) face(N + idx + nx, idx + nx); else bnd(3, k, i); }
-  if (!(m & 32)) { if (k > 0) face(2 * N + idx, idx - s2); else bnd(4, i, j); }
-  if (!(m & 64)) { if (k < nz - 1) face(2 * N + idx + s2, idx + s2); else bnd(5, i, j); }
+  if (!(m & 2)) { if (in6[0]) face(0); else bnd(0, j, k); }
+  if (!(m & 4)) { if (in6[1]) face(1); else bnd(1, j, k); }
+  if (!(m & 8)) { if (in6[2]) face(2); else bnd(2, k, i); }
+  if (!(m & 16)) { if (in6[3]) face(3); else bnd(3, k, i); }
+  if (!(m & 32)) { if (in6[4]) face(4); else bnd(4, i, j); }
+  if (!(m & 64)) { if (in6[5]) face(5); else bnd(5, i, j); }
   r[idx] = f[idx] - L0;
   r[N + idx] = f[N + idx] - L1;
 }
