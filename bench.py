@@ -39,15 +39,16 @@ DT = 5e-4
 WORKLOAD = "amr2_base64_marshak_band"
 # Algorithmic work per leaf cell of the linearisation stencil, in FP64-pipe
 # instructions (the unit that bounds it on GB300, which issues 2 FP64
-# instructions per clock per SM): 3 faces x 49 (face flux, its 5 partials,
-# the two scaled P1 coefficients incl. the refined reciprocal and reciprocal
-# square root and two conversions) + 36 per cell (balance, coupling and its
-# partials, P2 data).  Derivation in the design notes.
-LIN_INST_PER_CELL = 3 * 49 + 36
+# instructions per clock per SM): 3 faces x 45 (face flux, its 5 partials and
+# the two P1 coefficients incl. the refined reciprocal and reciprocal square
+# root; the FP32 narrowing of the coefficients runs on the integer pipe) + 34
+# per cell (balance, coupling and its partials, P2 data).  Derivation in the
+# design notes.
+LIN_INST_PER_CELL = 3 * 45 + 34
 # DRAM bytes per launch of that kernel from the committed ncu capture of the
 # same kernel version (profiles/k_stencil_lin_amr2_base64.md), or None when
 # the kernel changed since.
-LIN_TRAFFIC_BYTES = 25.21e6 + 53.10e6
+LIN_TRAFFIC_BYTES = 25.11e6 + 45.89e6
 JV_TRAFFIC_BYTES = 83.16e6 + 13.41e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B

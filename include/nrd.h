@@ -370,6 +370,14 @@ int nrd_wdot_noalloc(const double* x, const double* y, const float* w, int64_t n
  * Asynchronous.  Errors: NRD_EINVAL, NRD_ECUDA. */
 int nrd_check_fastmath(const double* x, int64_t n, double* out, cudaStream_t stream);
 
+/* Check of the FP64 -> FP32 narrowing the linearisation stencil forms with
+ * integer instructions (no counterpart in the paper): for n doubles x
+ * (device), out (device, 2n floats) receives the integer-instruction
+ * round-to-nearest-even narrowing of each x and CUDA's __double2float_rn of
+ * it; the two are bit-identical for every input.
+ * Asynchronous.  Errors: NRD_EINVAL (null pointer, n < 0), NRD_ECUDA. */
+int nrd_check_narrow(const double* x, int64_t n, float* out, cudaStream_t stream);
+
 /* Machine rates used as roofline denominators, measured on the current
  * device: FP64 and FP32 FMA throughput in TFLOP/s (an FMA counts 2 flops;
  * independent FMA chains on every SM) and device-to-device copy bandwidth in

@@ -389,6 +389,11 @@ int hier_upload(Hier& H, std::string& err) {
     }
   }
   H.nrf = (int)rf_cell.size();
+  for (int l = 0; l <= NRD_MAX_LEVELS; l++) {
+    int q = 0;
+    while (q < H.nrf && rf_level[q] < l) q++;
+    H.rf_lstart[l] = q;
+  }
   rf_off.push_back((int)rf_face.size());
   // coefficient coarsening lists: faces of level l with a covered side
   std::vector<std::vector<int>> cz_tgt(L);

@@ -247,7 +247,8 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
       if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
     }
   }
-  const double m = (bb > 0.0) ? ba / bb : DBL_MAX;
+  double m = DBL_MAX;
+  if (bb > 0.0) m = ba / bb;
   double r = block_red<1>(m, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);
@@ -289,7 +290,8 @@ __global__ void k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* _
       if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
     }
   }
-  const double m = (bb > 0.0) ? ba / bb : DBL_MAX;
+  double m = DBL_MAX;
+  if (bb > 0.0) m = ba / bb;
   double r = block_red<1>(m, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);

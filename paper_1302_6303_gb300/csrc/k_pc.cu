@@ -1401,20 +1401,34 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
 // the means of the finer levels): lmin = l - 1 before smoothing level l - 1
 // on the down-leg, lmin = l before smoothing level l on the up-leg, which on
 // the finest level leaves one sweep over that level's tiles.
+// With zero_base (lmin = 0, on the down-leg) the correction is still zero on
+// the base level, which has no coarse-fine ghosts: there L u = 0, so the
+// residual of its uncovered cells is the rhs that fr already holds, and only
+// the flux matching (the fine fluxes at its coarse-fine faces) and the
+// covered means change it.  That needs fr = ff on the base level's uncovered
+// cells, which holds because flux matching only touches levels >= lmin.  (A
+// finer level has no such shortcut: its coarse-fine ghosts interpolate
+// composite values of covered coarse cells, i.e. means of finer values.)
 template <class P>
-void composite_residual(PcState* ps, const Hier& H, int lmin, cudaStream_t s) {
+void composite_residual(PcState* ps, const Hier& H, int lmin, cudaStream_t s,
+                        bool zero_base = false) {
   const VLev<P> V = vlev<P>(ps, H);
-  const int t0 = ps->vt0[lmin];
+  const int t0 = ps->vt0[(zero_base && lmin == 0) ? 1 : lmin];
   VLev<P> Vs = V;
   Vs.vt = V.vt + t0;
-  k_cresid<P><<<ps->ntile - t0, FTHREADS, 0, s>>>(Vs, (const P*)ps->fu, (const P*)ps->ff,
-                                                  (P*)ps->fr, (P*)ps->cf);
+  if (ps->ntile > t0)
+    k_cresid<P><<<ps->ntile - t0, FTHREADS, 0, s>>>(Vs, (const P*)ps->fu, (const P*)ps->ff,
+                                                    (P*)ps->fr, (P*)ps->cf);
   if (H.L < 2 || lmin > H.L - 2) return;
   const int lc = H.L - 2;
-  const int n = H.nrf + H.ncov[lc];
+  // flux matching of the coarse cells on levels >= lmin only (the levels
+  // below are not read before the next residual that covers them)
+  const int r0 = H.rf_lstart[lmin];
+  const int nrf = H.nrf - r0;
+  const int n = nrf + H.ncov[lc];
   if (n)
-    k_reflux_avg<P><<<dim3(g1(n), 2), BS, 0, s>>>(H.d_rf_cell, H.d_rf_off, H.d_rf_g, H.nrf,
-                                                  H.d_cov[lc], H.ncov[lc], H.N, H.G,
+    k_reflux_avg<P><<<dim3(g1(n), 2), BS, 0, s>>>(H.d_rf_cell + r0, H.d_rf_off + r0, H.d_rf_g,
+                                                  nrf, H.d_cov[lc], H.ncov[lc], H.N, H.G,
                                                   (const P*)ps->cf, (P*)ps->fr);
   for (int l = H.L - 3; l >= lmin; l--) {
     if (!H.ncov[l]) continue;
@@ -1510,7 +1524,7 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
       level_smooth<P>(ps, H, l, ps->nu1, true, s);
       prolong_finer<P>(ps, H, l, s);
     }
-    composite_residual<P>(ps, H, l - 1, s);
+    composite_residual<P>(ps, H, l - 1, s, l == 1);
   }
   gmg_vcycle<P>(ps, H, 0, s);
   prolong_finer<P>(ps, H, 0, s);

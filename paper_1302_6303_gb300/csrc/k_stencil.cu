@@ -21,7 +21,15 @@ struct LevelH {
   double kh[NRD_MAX_LEVELS][3];   // k/h
   double kh5[NRD_MAX_LEVELS][3];  // 1.25 k/h
   double bh2[NRD_MAX_LEVELS][3];  // beta/h^2 (linearisation only)
+  // the face fluxes' constants in terms of Ts = T_a + T_b (face_core)
+  double h12[NRD_MAX_LEVELS][3];  // 12h
+  double khs[NRD_MAX_LEVELS][3];  // 2^(-5/2) k/h
+  double kh5s[NRD_MAX_LEVELS][3]; // 2^(-3/2) 1.25 k/h
 };
+
+// 2^(-5/2) and 2^(-3/2): Tf^(5/2) = 2^(-5/2) Ts^(5/2), Tf^(3/2) = 2^(-3/2) Ts^(3/2)
+constexpr double kP52 = 0.17677669529663688;
+constexpr double kP32 = 0.35355339059327376;
 
 struct GhostArgs {
   const uint8_t* gtype;
@@ -96,6 +104,8 @@ struct StArgs {
   int ntiles, N, G;
   double k;       // D_T = k T^(5/2)
   double cL;      // limiter constant: 4 (Wilson form) or 2 (printed form)
+  double cL2;     // cL / 2 (face_core's Ts form)
+  double m15cL;   // -1.5 cL
   double R[6];
   LevelH lh;
   StencilIO io;
@@ -106,8 +116,8 @@ struct StArgs {
 // the partial derivatives of Phi_E w.r.t. E_a, E_b and T_a (= w.r.t. T_b) and
 // of Phi_T w.r.t. T_a, T_b (sign(0) = 0).
 struct FaceLin {
-  double PE, PT, CE, CT, aEa, aEb, aT, bTa, bTb, aZ;
-  double X, T25;   // CE = X h, CT = k T25
+  double PE, PT, aEa, aEb, aT, bTa, bTb, aZ;
+  double X, T25;   // C_E = X h, C_D = k 2^(-5/2) T25
 };
 
 // 1/x from the PTX approximate FP64 reciprocal (rcp.approx.ftz.f64, a
@@ -154,6 +164,29 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return fma(y * e, fma(0.375, e, 0.5), y);
 }
 
+// FP64 -> FP32 with round-to-nearest-even (the IEEE narrowing conversion,
+// bit-identical to the (float) cast) from integer instructions: on GB300 the
+// conversion instruction issues on the FP64 pipe, which bounds the
+// linearisation.  With the FP64 exponent field e in [897, 1150] the result is a
+// normal float: its exponent is e - 896 and its 23 mantissa bits are the top
+// 23 of the 52; the 29 dropped bits d round up when d > 2^28, or d = 2^28 and
+// the kept lsb is odd, i.e. exactly when d + (2^28 - 1) + lsb >= 2^29.  A
+// mantissa carry runs into the exponent (up to infinity when the rounded value
+// overflows, as IEEE narrowing gives).  Other exponents (zero, subnormal or
+// overflowing results, inf, NaN) take the conversion instruction, in a
+// function of its own: inlined, the compiler predicates the conversion instead
+// of branching around it, and a predicated-off instruction still takes its
+// FP64-pipe issue slot.
+__device__ __noinline__ float narrow_slow(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float narrow_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7ffu;
+  if (e - 897u > 253u) return narrow_slow(x);
+  const unsigned top = __funnelshift_l(lo, hi & 0x7fffffffu, 3);   // exponent+mantissa bits
+  const unsigned rnd = ((lo & 0x1fffffffu) + 0x0fffffffu + (top & 1u)) >> 29;
+  return __uint_as_float((hi & 0x80000000u) | (top - (896u << 23) + rnd));
+}
+
 // Face flux in the +e_d direction between cells a (low) and b (high):
 //   Phi_E = D_E (E_b - E_a)/h with D_E = D_h/(1 + D_h g) (or the printed form)
 //         = 2 Tf^3 S dE / (3 h Zs S + cL Tf^3 |dE|),  S = E_a + E_b,
@@ -162,63 +195,69 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
 // with the intermediate quantities the partial derivatives reuse.  The
 // residual and the linearisation both take their fluxes from here, so the
 // two produce bit-identical residuals.
+// Evaluated in Ts = T_a + T_b = 2 Tf with the powers of 2 folded into the
+// constants (two FP64 multiplies fewer per face): with
+//   den' = 4 den = 12h Zs S + (cL/2) Ts^3 |dE|,   X = 2 Tf^3 S / den = Ts^3 S / den',
+//   Tf^(5/2) = 2^(-5/2) Ts^(5/2)  (2^(-5/2) in khs = 2^(-5/2) k/h).
+// rden = 1/den', hz = 12h Zs, ltadE = (cL/2) Ts^3 |dE| (4 times the Tf-form
+// terms), T15 = Ts^(3/2), T25 = Ts^(5/2), khT25 = (k/h) Tf^(5/2).
 struct FaceCore {
-  double Tf, Tf2, Tf3, dE, adE, S, hz, ltadE, rden, X, PE, T15, T25, dT, khT25, PT;
+  double Ts, Ts2, Ts3, dE, adE, S, hz, ltadE, rden, X, PE, T15, T25, dT, khT25, PT;
 };
 __device__ __forceinline__ FaceCore face_core(double Ea, double Eb, double Ta, double Tb,
-                                              double za, double zb, double h3, double kh,
-                                              double cL) {
+                                              double za, double zb, double h12, double khs,
+                                              double cL2) {
   FaceCore q;
-  q.Tf = 0.5 * (Ta + Tb);
-  q.Tf2 = q.Tf * q.Tf;
-  q.Tf3 = q.Tf2 * q.Tf;
+  q.Ts = Ta + Tb;
+  q.Ts2 = q.Ts * q.Ts;
+  q.Ts3 = q.Ts2 * q.Ts;
   q.dE = Eb - Ea;
   q.S = Ea + Eb;
-  q.hz = h3 * (za + zb);
+  q.hz = h12 * (za + zb);
   q.adE = fabs(q.dE);
-  q.ltadE = (cL * q.Tf3) * q.adE;
+  q.ltadE = (cL2 * q.Ts3) * q.adE;
   q.rden = rcp_nr(fma(q.hz, q.S, q.ltadE));
-  q.X = 2.0 * q.Tf3 * q.S * q.rden;
+  q.X = (q.Ts3 * q.S) * q.rden;
   q.PE = q.X * q.dE;
-  const double y = rsqrt_nr(q.Tf);
-  q.T15 = q.Tf2 * y;     // Tf^(3/2)
-  q.T25 = q.Tf * q.T15;  // Tf^(5/2)
+  const double y = rsqrt_nr(q.Ts);
+  q.T15 = q.Ts2 * y;     // Ts^(3/2)
+  q.T25 = q.Ts * q.T15;  // Ts^(5/2)
   q.dT = Tb - Ta;
-  q.khT25 = kh * q.T25;
+  q.khT25 = khs * q.T25;
   q.PT = q.khT25 * q.dT;
   return q;
 }
 
 // Face flux of face_core and its partial derivatives at one iterate (the
-// frozen Jacobian), the raw P1 coefficients CE = D_E h and CT = D_T:
-//   PE = X dE, CE = X h with X = 2 Tf^3 S / den, den = 3h Zs S + cL Tf^3 |dE|
+// frozen Jacobian), with X = 2 Tf^3 S / den, den = 3h Zs S + cL Tf^3 |dE|:
+//   PE = X dE (the P1 coefficient C_E = D_E h is X h)
 //   d PE / d E_a = (-4 Tf^3 E_a - PE (3h Zs - cL Tf^3 sg)) / den
 //   d PE / d E_b = ( 4 Tf^3 E_b - PE (3h Zs + cL Tf^3 sg)) / den
 //   d PE / d T_a = d PE / d T_b = Tf^2 (3 S dE - 1.5 cL |dE| PE) / den
 //   d PE / d Zs  = -PE 3h S / den
 //   PT = (k/h) Tf^(5/2) dT, d PT / d T_{a,b} = (k/h)(1.25 Tf^(3/2) dT -/+ Tf^(5/2))
-// (sg = sign(dE), sign(0) = 0).  The reciprocal and Tf^(-1/2) come from
-// rcp_nr / rsqrt_nr (within ~1e-13 relative of correctly rounded
-// arithmetic).
+// (sg = sign(dE), sign(0) = 0), each evaluated in face_core's Ts form (the
+// factor 4 of den' cancels against the factor 4 of the Ts-form terms:
+// 4 Tf^3 = Ts^3 / 2, Tf^2 / den = Ts^2 / den').  The reciprocal and
+// Ts^(-1/2) come from rcp_nr / rsqrt_nr (within ~1e-13 relative of correctly
+// rounded arithmetic).  T25 is Ts^(5/2): C_D = k 2^(-5/2) T25.
 __device__ __forceinline__ FaceLin flux_lin(double Ea, double Eb, double Ta, double Tb, double za,
-                                            double zb, double h, double h3, double kh,
-                                            double kh5, double k, double cL, bool with_dz) {
-  const FaceCore q = face_core(Ea, Eb, Ta, Tb, za, zb, h3, kh, cL);
+                                            double zb, double h12, double khs, double kh5s,
+                                            double cL2, double m15cL, bool with_dz) {
+  const FaceCore q = face_core(Ea, Eb, Ta, Tb, za, zb, h12, khs, cL2);
   FaceLin r;
   r.PE = q.PE;
   r.X = q.X;
-  r.CE = q.X * h;
   const double A = q.PE * q.hz;
-  const double Bs = q.X * q.ltadE;      // = PE cL Tf^3 sign(dE)
-  const double t4 = 4.0 * q.Tf3;
-  r.aEa = (fma(-t4, Ea, Bs) - A) * q.rden;
-  r.aEb = (fma(t4, Eb, -Bs) - A) * q.rden;
-  r.aT = (q.Tf2 * q.rden) * fma(-1.5 * cL, q.adE * q.PE, 3.0 * (q.S * q.dE));
-  r.aZ = with_dz ? -(q.PE * q.rden) * (h3 * q.S) : 0.0;
+  const double Bs = q.X * q.ltadE;      // = 4 PE cL Tf^3 sign(dE)
+  const double t16 = q.Ts3 + q.Ts3;     // 16 Tf^3
+  r.aEa = (fma(-t16, Ea, Bs) - A) * q.rden;
+  r.aEb = (fma(t16, Eb, -Bs) - A) * q.rden;
+  r.aT = (q.Ts2 * q.rden) * fma(m15cL, q.adE * q.PE, 3.0 * (q.S * q.dE));
+  r.aZ = with_dz ? -(q.PE * q.rden) * (h12 * q.S) : 0.0;
   r.T25 = q.T25;
-  r.CT = k * q.T25;
   r.PT = q.PT;
-  const double khq = kh5 * q.T15 * q.dT;
+  const double khq = kh5s * q.T15 * q.dT;
   r.bTa = khq - q.khT25;
   r.bTb = khq + q.khT25;
   return r;
@@ -335,13 +374,14 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     reps = 1.0 / eps;
   }
   // FP32 scale factors of the V-cycle coefficients per level and axis:
-  // beta C_E / h^2 = X (beta / h), beta C_T / h^2 = T^(5/2) (beta k / h^2)
+  // beta C_E / h^2 = X (beta / h), beta C_T / h^2 = Ts^(5/2) (2^(-5/2) beta k / h^2)
   __shared__ float s_bh[LIN ? NRD_MAX_LEVELS * 3 : 1], s_bk[LIN ? NRD_MAX_LEVELS * 3 : 1];
   if (LIN && threadIdx.x < NRD_MAX_LEVELS * 3) {
     const double rh = A.lh.rh[threadIdx.x / 3][threadIdx.x % 3];
     s_bh[threadIdx.x] = (float)(betav * rh);
-    s_bk[threadIdx.x] = (float)(betav * A.k * rh * rh);
+    s_bk[threadIdx.x] = (float)(kP52 * (betav * A.k * rh * rh));
   }
+  const float betaf = (float)betav;
 
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
     const TileDev tile = A.tiles[t];
@@ -522,8 +562,9 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           flux_tan(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh, A.cL, svE[ha], svE[hb],
                    svT[ha], svT[hb], PE, PT);
         } else if (LIN) {
-          FaceLin L = flux_lin(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h, h3, kh,
-                               A.lh.kh5[lvl][dir], A.k, A.cL, DZ);
+          FaceLin L = flux_lin(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb],
+                               A.lh.h12[lvl][dir], A.lh.khs[lvl][dir], A.lh.kh5s[lvl][dir], A.cL2,
+                               A.m15cL, DZ);
           PE = L.PE;
           PT = L.PT;
           io.jc[fslot] = L.aEa;
@@ -535,17 +576,17 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           // only the scaled P1 coefficients: the coarsening averages them
           // (raw values are kept for Robin faces alone)
           if (io.a32) {
-            io.a32[fslot] = (float)L.X * s_bh[3 * lvl + dir];
-            io.a32[NS + fslot] = (float)L.T25 * s_bk[3 * lvl + dir];
+            io.a32[fslot] = narrow_rn(L.X) * s_bh[3 * lvl + dir];
+            io.a32[NS + fslot] = narrow_rn(L.T25) * s_bk[3 * lvl + dir];
           } else {
-            // beta D_E / h^2 = X beta / h, beta D_T / h^2 = T^(5/2) beta k / h^2
+            // beta D_E / h^2 = X beta / h, beta D_T / h^2 = Ts^(5/2) 2^(-5/2) beta k / h^2
             const double bh = betav * A.lh.rh[lvl][dir];
             io.a64[fslot] = L.X * bh;
-            io.a64[NS + fslot] = L.T25 * (bh * A.k * A.lh.rh[lvl][dir]);
+            io.a64[NS + fslot] = L.T25 * (kP52 * (bh * A.k * A.lh.rh[lvl][dir]));
           }
         } else {
-          const FaceCore q = face_core(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb], h3, kh,
-                                       A.cL);
+          const FaceCore q = face_core(sE[ha], sE[hb], sT[ha], sT[hb], sZ[ha], sZ[hb],
+                                       A.lh.h12[lvl][dir], A.lh.khs[lvl][dir], A.cL2);
           PE = q.PE;
           PT = q.PT;
         }
@@ -623,7 +664,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         // (det = (1 + sb)(1 + sbt) - sbt sb = 1 + sb + sbt), in the
         // preconditioner's precision
         if (io.p2f) {
-          const float sb = (float)sig * (float)betav, sbt = sb * (float)T3;
+          const float sb = narrow_rn(sig) * betaf, sbt = sb * narrow_rn(T3);
           io.p2f[idx] = sb;
           io.p2f[N + idx] = sbt;
           io.p2f[2L * N + idx] = 1.0f / (1.0f + sb + sbt);
@@ -797,6 +838,15 @@ __global__ void k_check_fastmath(const double* x, long n, double* out) {
   }
 }
 
+__global__ void k_check_narrow(const double* x, long n, float* out) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n;
+       i += (long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    out[i] = narrow_rn(v);
+    out[n + i] = __double2float_rn(v);
+  }
+}
+
 LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
   LevelH lh;
   for (int l = 0; l < NRD_MAX_LEVELS; l++)
@@ -808,6 +858,9 @@ LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
       lh.kh[l][d] = k / h;
       lh.kh5[l][d] = 1.25 * k / h;
       lh.bh2[l][d] = beta / (h * h);
+      lh.h12[l][d] = 12.0 * h;
+      lh.khs[l][d] = kP52 * (k / h);
+      lh.kh5s[l][d] = kP32 * (1.25 * k / h);
     }
   return lh;
 }
@@ -902,6 +955,8 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   a.G = H.G;
   a.k = mp.k;
   a.cL = (mp.limiter == NRD_LIM_PAPER_LITERAL) ? 2.0 : 4.0;
+  a.cL2 = 0.5 * a.cL;
+  a.m15cL = -1.5 * a.cL;
   for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
   a.lh = level_h(H, mp.k, io.beta);
   a.io = io;
@@ -960,5 +1015,13 @@ extern "C" int nrd_check_fastmath(const double* x, int64_t n, double* out, cudaS
   if (n == 0) return NRD_OK;
   const int grid = (int)std::min<long>(152L * 8, (n + 255) / 256);
   k_check_fastmath<<<grid, 256, 0, s>>>(x, n, out);
+  return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
+}
+
+extern "C" int nrd_check_narrow(const double* x, int64_t n, float* out, cudaStream_t s) {
+  if (!x || !out || n < 0) return NRD_EINVAL;
+  if (n == 0) return NRD_OK;
+  const int grid = (int)std::min<long>(152L * 8, (n + 255) / 256);
+  k_check_narrow<<<grid, 256, 0, s>>>(x, n, out);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }

@@ -315,7 +315,9 @@ __global__ void __launch_bounds__(256) k_cycle_update_g(
       if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
     }
   }
-  const double r = blk_min((bb > 0.0) ? ba / bb : DBL_MAX, sh);
+  double mq = DBL_MAX;
+  if (bb > 0.0) mq = ba / bb;
+  const double r = blk_min(mq, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (last_block(counter)) {
     double acc = DBL_MAX;

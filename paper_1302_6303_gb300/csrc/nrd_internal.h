@@ -83,6 +83,7 @@ struct Hier {
   int* d_rf_face = nullptr;               // entries: face 0..5 of the coarse cell
   int4* d_rf_g = nullptr;                 // entries: ghost slots of the 4 fine fluxes
   int* d_rf_level = nullptr;              // nrf: level of the coarse cell
+  int rf_lstart[NRD_MAX_LEVELS + 1] = {}; // first entry of each level (cells ascend by level)
   // transposed ghost stencils (adjoint): cell -> (ghost, weight), and the
   // sibling / coarse-fine ghosts that take their z from a cell
   int* d_ts_off = nullptr;
@@ -168,7 +169,7 @@ void launch_average_down(const Hier& H, double* x, int nfield, int fstride, cuda
 // BLAS / reductions (k_blas.cu)
 struct Reducer {
   int nblk = 0;
-  double* d_part = nullptr;   // partials [nblk * 8]
+  double* d_part = nullptr;   // partials [nblk * NVMAX]
   double* d_res = nullptr;    // results [64]
   double* h_res = nullptr;    // pinned host mirror [64]
   unsigned* d_count = nullptr;  // last-block ticket counter (0 between launches)

@@ -29,7 +29,7 @@ EXPORTED = [
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
     "nrd_step", "nrd_tag", "nrd_regrid_boxes", "nrd_transfer", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
     "nrd_autotune", "nrd_autotune_sweeps", "nrd_wdot_noalloc", "nrd_measure_peaks",
-    "nrd_check_fastmath",
+    "nrd_check_fastmath", "nrd_check_narrow",
     "nrd_timing_enable",
     "nrd_timing_read",
 ]
@@ -116,6 +116,7 @@ def load(path: str = _LIBPATH):
         "nrd_wdot_noalloc": (c_int, [dp, dp, fp, ctypes.c_int64, dp, vp]),
         "nrd_measure_peaks": (c_int, [P(c_dbl), P(c_dbl), P(c_dbl), vp]),
         "nrd_check_fastmath": (c_int, [dp, ctypes.c_int64, dp, vp]),
+        "nrd_check_narrow": (c_int, [dp, ctypes.c_int64, fp, vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
         "nrd_timing_read": (c_int, [vp, c_int, P(c_dbl), P(ctypes.c_int64)]),
     }
@@ -168,6 +169,17 @@ def check_fastmath(x):
                                    _stream())
     if rc != OK:
         raise NrdError(rc, "nrd_check_fastmath failed")
+    return out
+
+
+def check_narrow(x):
+    """[narrow(x), (float) x]: the stencil's integer-instruction FP64 -> FP32
+    round-to-nearest-even narrowing and CUDA's conversion (nrd_check_narrow)."""
+    out = torch.empty(2, x.numel(), dtype=torch.float32, device=x.device)
+    rc = load().nrd_check_narrow(_ptr(x, torch.float64), x.numel(), _ptr(out, torch.float32),
+                                 _stream())
+    if rc != OK:
+        raise NrdError(rc, "nrd_check_narrow failed")
     return out
 
 

@@ -452,3 +452,34 @@ def test_refined_reciprocals_error_bound(nrd):
     s_err = np.abs(out[2] - out[3]) / out[3]
     assert r_err.max() <= 1e-15 and s_err.max() <= 1e-15, (r_err.max(), s_err.max())
     assert out[0][-4] == out[1][-4] and out[2][-4] == out[3][-4]   # 1e305: rounded path
+
+
+def test_integer_narrowing_bit_identical(nrd):
+    """The stencil's FP64 -> FP32 narrowing from integer instructions against
+    CUDA's conversion, bit for bit: random values over the whole FP64 range,
+    random bit patterns (zero, subnormals, inf, NaN included), and doubles whose
+    29 dropped bits sit at and around the rounding tie with an even and an odd
+    kept lsb, at the float range edges and with a mantissa carry into the
+    exponent (up to overflow).  The normal-range results also equal numpy's
+    round-to-nearest-even cast."""
+    rng = np.random.default_rng(3)
+    xs = [rng.standard_normal(200000) * 10.0 ** rng.uniform(-50, 50, 200000)]
+    bits = rng.integers(0, 2 ** 63, 200000, dtype=np.uint64)
+    bits |= rng.integers(0, 2, 200000, dtype=np.uint64) << np.uint64(63)
+    xs.append(bits.view(np.float64))
+    tops = np.array([0x3F800000, 0x3F800001, 0x3FFFFFFF, 0x7F7FFFFF, 0x7F7FFFFE, 0x00800000,
+                     0x00800001, 0x007FFFFF, 0x00000001], dtype=np.uint32)
+    base = tops.view(np.float32).astype(np.float64).view(np.uint64)
+    low = np.array([0, 1, 0x0FFFFFFF, 0x10000000, 0x10000001, 0x1FFFFFFF], dtype=np.uint64)
+    edge = ((base[:, None] & ~np.uint64(0x1FFFFFFF)) | low[None, :]).ravel()
+    edge = np.concatenate([edge, edge | (np.uint64(1) << np.uint64(63))])
+    xs.append(edge.view(np.float64))
+    xs.append(np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 3.4028235677973366e38,
+                        3.4028235677973362e38, 1.1754942807573643e-38, 5e-324]))
+    x = np.concatenate(xs)
+    out = nrd.check_narrow(dev(x)).cpu().numpy()
+    assert np.array_equal(out[0].view(np.uint32), out[1].view(np.uint32))
+    with np.errstate(over="ignore", invalid="ignore"):
+        ref = x.astype(np.float32)
+    normal = np.isfinite(ref) & (np.abs(ref) >= np.finfo(np.float32).tiny)
+    assert np.array_equal(out[0][normal].view(np.uint32), ref[normal].view(np.uint32))
