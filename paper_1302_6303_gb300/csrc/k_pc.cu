@@ -17,7 +17,11 @@
 #include <algorithm>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "nrd_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -792,6 +796,12 @@ __global__ void k_coef(SetupArgs a) {
 // values on Robin faces only): the scaled coefficient of a non-Robin face is
 // the mean of the 4 fine scaled ones over 4 (beta C / h^2 with C the mean of
 // the fine C and h twice the fine h), the Robin faces average the raw D_b.
+// (a + b + c + d) / 16: the mean of four scaled P1 coefficients over 4
+template <class P>
+__device__ __forceinline__ P mean16(P a, P b, P c, P d) {
+  return P(0.0625) * ((a + b) + (c + d));
+}
+
 template <class P, bool SCALED>
 __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, int N,
                                const uint8_t* gtype, const uint8_t* gface,
@@ -815,7 +825,9 @@ __global__ void k_coef_coarsen(const int* tgt, const int4* src, int n, long AF, 
         const double h = lh.h[lvl][(gface[t - 3 * N] & 7) / 2];
         v = (fld == 0) ? beta * 2.0 * c / (h * (4.0 * c + h)) : 0.0;
       } else {
-        v = 0.0625 * ((double)Af[s.x] + (double)Af[s.y] + (double)Af[s.z] + (double)Af[s.w]);
+        // the mean of four scaled coefficients over 4, in their own precision
+        A[fld * AF + t] = mean16<P>(Af[s.x], Af[s.y], Af[s.z], Af[s.w]);
+        continue;
       }
       A[fld * AF + t] = (P)v;
       continue;
@@ -898,7 +910,11 @@ struct BoxRaw {
 // faces of E, 0 elsewhere; rh2 = 1/h^2 per axis of the coarse level.
 // SCALED (after the linearisation): interior faces average the finer
 // level's scaled coefficients Ain (the mean over 4, as the raw C, then
-// 1/4 for the doubled h), box faces the raw Robin D_b.
+// 1/4 for the doubled h), box faces the raw Robin D_b.  One thread per
+// (coarse cell, axis): the axis's low face and, on the box's faces, its
+// boundary faces (short dependency chains; these launches are small).  FP32
+// coefficients are averaged in FP32 (FP64 arithmetic and conversions issue
+// on GB300's narrow FP64 pipe).
 template <class P, bool SCALED>
 __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_raw,
                               const int* gtype_box, const double* dbeta, double hx, double hy,
@@ -909,61 +925,58 @@ __global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_
   const P* ain = SCALED ? Ain + fld * F.AF : nullptr;
   double* cc = Cc_raw + fld * Cc.AF;
   P* Af = A + fld * Cc.AF;
-  const double beta = *dbeta;
-  const double hh[3] = {hx, hy, hz};
-  const double bh2[3] = {beta * rh2x, beta * rh2y, beta * rh2z};
   // every box starts at cell 0 of its vectors; indices are 32-bit (3N + G
   // < 2^31 for the hierarchy, which bounds every box)
   const int ncc = Cc.n[0] * Cc.n[1] * Cc.n[2];
   const int fNA = (int)F.NA, cNA = (int)Cc.NA, fgb = (int)F.gbase, cgb = (int)Cc.gbase;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncc; c += gridDim.x * blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * ncc;
+       t += gridDim.x * blockDim.x) {
+    const int d = t / ncc, c = t - d * ncc;
     int q[3];
     const int r = c / Cc.n[0];
     q[0] = c - r * Cc.n[0];
     q[2] = r / Cc.n[1];
     q[1] = r - q[2] * Cc.n[1];
+    const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+    const double rh2 = (d == 0) ? rh2x : ((d == 1) ? rh2y : rh2z);
+    if (q[d] > 0) {
+      int fi[4];
 #pragma unroll
-    for (int d = 0; d < 3; d++) {
-      const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-      if (q[d] > 0) {
-        double s = 0.0;
+      for (int a = 0; a < 2; a++)
 #pragma unroll
-        for (int a = 0; a < 2; a++)
-#pragma unroll
-          for (int b = 0; b < 2; b++) {
-            int p[3];
-            p[d] = 2 * q[d];
-            p[t1] = 2 * q[t1] + a;
-            p[t2] = 2 * q[t2] + b;
-            const int fi = p[0] + F.n[0] * (p[1] + F.n[1] * p[2]);
-            s += SCALED ? (double)ain[d * fNA + fi] : cf[d * fNA + fi];
-          }
-        if (SCALED) {
-          Af[d * cNA + c] = (P)(0.0625 * s);
-        } else {
-          cc[d * cNA + c] = 0.25 * s;
-          Af[d * cNA + c] = (P)(0.25 * s * bh2[d]);
+        for (int b = 0; b < 2; b++) {
+          int p[3];
+          p[d] = 2 * q[d];
+          p[t1] = 2 * q[t1] + a;
+          p[t2] = 2 * q[t2] + b;
+          fi[2 * a + b] = d * fNA + p[0] + F.n[0] * (p[1] + F.n[1] * p[2]);
         }
+      if (SCALED) {
+        Af[d * cNA + c] = mean16<P>(ain[fi[0]], ain[fi[1]], ain[fi[2]], ain[fi[3]]);
+      } else {
+        const double sm = ((cf[fi[0]] + cf[fi[1]]) + cf[fi[2]]) + cf[fi[3]];
+        cc[d * cNA + c] = 0.25 * sm;
+        Af[d * cNA + c] = (P)(0.25 * sm * (*dbeta * rh2));
       }
-      for (int sd = 0; sd < 2; sd++) {
-        bool at = sd ? (q[d] == Cc.n[d] - 1) : (q[d] == 0);
-        if (!at) continue;
-        int f = 2 * d + sd;
-        double s = 0.0;
-        for (int a = 0; a < 2; a++)
-          for (int b = 0; b < 2; b++) {
-            int p1 = 2 * q[t1] + a, p2 = 2 * q[t2] + b;
-            s += cf[fgb + F.fo[f] + p1 + F.n[t1] * p2];
-          }
-        const int g = cgb + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2];
-        cc[g] = 0.25 * s;
-        double v = 0.0;
-        if (gtype_box[f] == 1 && fld == 0) {
-          const double Db = 0.25 * s, h = hh[d];
-          v = beta * 2.0 * Db / (h * (4.0 * Db + h));
+    }
+    for (int sd = 0; sd < 2; sd++) {
+      const bool at = sd ? (q[d] == Cc.n[d] - 1) : (q[d] == 0);
+      if (!at) continue;
+      const int f = 2 * d + sd;
+      double sm = 0.0;
+      for (int a = 0; a < 2; a++)
+        for (int b = 0; b < 2; b++) {
+          const int p1 = 2 * q[t1] + a, p2 = 2 * q[t2] + b;
+          sm += cf[fgb + F.fo[f] + p1 + F.n[t1] * p2];
         }
-        Af[g] = (P)v;
+      const int g = cgb + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2];
+      cc[g] = 0.25 * sm;
+      double v = 0.0;
+      if (gtype_box[f] == 1 && fld == 0) {
+        const double Db = 0.25 * sm, h = (d == 0) ? hx : ((d == 1) ? hy : hz);
+        v = *dbeta * 2.0 * Db / (h * (4.0 * Db + h));
       }
+      Af[g] = (P)v;
     }
   }
 }
@@ -1011,6 +1024,7 @@ struct PcState {
   // GMG levels tail_m.. run as one shared-memory kernel (0: off)
   int tail_m = 0;
   size_t tail_smem = 0;
+  int tail_cl = 1;   // CTAs per field of the tail's cluster
   // 8^3 tiles of all patches for the V-cycle kernels, level by level
   int4* vt = nullptr;
   int vt0[NRD_MAX_LEVELS] = {0}, vnt[NRD_MAX_LEVELS] = {0};
@@ -1113,6 +1127,7 @@ void box_smooth(const BoxK<P>& V, int sweeps, bool red_first, bool zero, const u
 // with block barriers where the per-level form has kernel boundaries.
 constexpr int kTailThreads = 1024;
 constexpr size_t kTailSmemMax = 200 * 1024;
+constexpr int kTailClusterMax = 4;   // CTAs per field (4 measured fastest; 8 is portable)
 
 template <class P>
 struct TailArgs {
@@ -1126,6 +1141,7 @@ struct TailArgs {
   int nu1, nu2, csw;
   int jacobi;                     // smoother: 0 red-black Gauss-Seidel, 1 damped Jacobi
   P omega;
+  int pb[NRD_MAX_MG + 1];         // first z-plane of each level in the plane lists
 };
 
 template <class P>
@@ -1148,11 +1164,19 @@ __device__ BoxK<P> tail_view(const TailArgs<P>& a, P* sm, int l) {
 
 // body(a, b, c) over an na x nb x nc grid by one CTA.  When a whole number of
 // (a, b) planes fits the block, each thread keeps its (a, b) and steps c (no
-// division in the loop); otherwise a flat index is split per item.
+// division in the loop); otherwise a flat index is split per item.  Plane
+// sides that are powers of 2 (the usual coarse boxes) take shifts and masks
+// instead of the integer divisions, which cost about 20 instructions each and
+// dominated the one-CTA levels.
+__device__ __forceinline__ bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
 template <class F>
 __device__ __forceinline__ void cta_for3(int na, int nb, int nc, F body) {
   const int plane = na * nb, bd = blockDim.x, t = threadIdx.x;
-  if (plane <= bd && bd % plane == 0) {
+  if (is_pow2(na) && is_pow2(nb) && plane <= bd && is_pow2(bd)) {
+    const int la = __ffs(na) - 1, lp = la + __ffs(nb) - 1;
+    const int a = t & (na - 1), b = (t >> la) & (nb - 1);
+    for (int c = t >> lp; c < nc; c += bd >> lp) body(a, b, c);
+  } else if (plane <= bd && bd % plane == 0) {
     const int a = t % na, b = (t / na) % nb;
     for (int c = t / plane; c < nc; c += bd / plane) body(a, b, c);
   } else {
@@ -1164,39 +1188,92 @@ __device__ __forceinline__ void cta_for3(int na, int nb, int nc, F body) {
   }
 }
 
-// damped Jacobi sweeps by one CTA: every thread forms the new values of its
-// cells (at most 8: tail levels hold at most 8,192 cells) from the old
-// iterate, then all write
+// The tail's cluster: every CTA holds a replica of all tail levels in its
+// shared memory and forms the values of its share of the z-planes of each
+// level; a value it writes goes into the replicas of the CTAs that read its
+// plane (distributed shared memory stores are slow: about 2 per clock per
+// SM), and a cluster barrier ends each phase.  Readers of a plane of level X:
+// for the correction e the CTAs owning a plane within 1 of it (smoothing),
+// restricting from it (the fine planes 2 c0 - 1 .. 2 c1 of their coarse planes
+// [c0, c1)) or prolonging from it (the coarse planes (f0 >> 1) - 1 ..
+// ((f1 - 1) >> 1) + 1 of their fine planes [f0, f1)); for the rhs f its owner
+// and the CTAs restricting from it (fine planes 2 c0 .. 2 c1 - 1).
+constexpr int kTailPlanes = 256;   // plane-reader masks kept for up to this many planes
+
 template <class P>
-__device__ void tail_jacobi(const BoxK<P>& V, int sweeps, P omega) {
+struct TailCl {
+  P* sm;          // this CTA's replica
+  P* const* rb;   // every CTA's replica, by rank (shared memory of this CTA)
+  const uint8_t* me;   // reader masks of the e planes (null: every CTA)
+  const uint8_t* mf;   // reader masks of the f planes
+  const int* pb;       // first plane of each level in the masks
+  int r, C, lgC;  // rank, cluster size (a power of 2), log2 of it
+  __device__ __forceinline__ void put(P* p, P v, unsigned mask) const {
+    const long o = p - sm;
+    for (int q = 0; q < C; q++) {
+      if (!((mask >> q) & 1u)) continue;
+      if (q == r) *p = v;
+      else rb[q][o] = v;
+    }
+  }
+  // write a value of plane k of level l to its readers
+  __device__ __forceinline__ void put_e(int l, int k, P* p, P v) const {
+    put(p, v, me ? me[pb[l] + k] : 0xffu);
+  }
+  __device__ __forceinline__ void put_f(int l, int k, P* p, P v) const {
+    put(p, v, mf ? mf[pb[l] + k] : 0xffu);
+  }
+  __device__ __forceinline__ void sync() const {
+    if (C > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  }
+  __device__ __forceinline__ void own(int nz, int rank, int& c0, int& c1) const {
+    c0 = (rank * nz) >> lgC;
+    c1 = ((rank + 1) * nz) >> lgC;
+  }
+};
+
+// cta_for3 over this CTA's planes [r nc / C, (r + 1) nc / C) of c
+template <class P, class F>
+__device__ __forceinline__ void cl_for3(const TailCl<P>& cl, int na, int nb, int nc, F body) {
+  const int c0 = (cl.r * nc) >> cl.lgC, c1 = ((cl.r + 1) * nc) >> cl.lgC;
+  cta_for3(na, nb, c1 - c0, [&](int a, int b, int c) { body(a, b, c0 + c); });
+}
+
+// damped Jacobi sweeps: every thread forms the new values of its cells (at
+// most 8: tail levels hold at most 8,192 cells) from the old iterate, then,
+// once every CTA has read the old iterate, all write
+template <class P>
+__device__ void tail_jacobi(const TailCl<P>& cl, int l, const BoxK<P>& V, int sweeps, P omega) {
   const int n0 = V.n0, n1 = V.n1;
   for (int sw = 0; sw < sweeps; sw++) {
     P nv[8];
     int cnt = 0;
-    cta_for3(n0, n1, V.n2, [&](int i, int j, int k) {
+    cl_for3(cl, n0, n1, V.n2, [&](int i, int j, int k) {
       P dg, of;
       box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
       const int idx = i + n0 * (j + n1 * k);
       if (cnt < 8) nv[cnt] = V.e[idx] + omega * ((V.f[idx] + of) / dg - V.e[idx]);
       cnt++;
     });
-    __syncthreads();
+    cl.sync();
     cnt = 0;
-    cta_for3(n0, n1, V.n2, [&](int i, int j, int k) {
-      if (cnt < 8) V.e[i + n0 * (j + n1 * k)] = nv[cnt];
+    cl_for3(cl, n0, n1, V.n2, [&](int i, int j, int k) {
+      if (cnt < 8) cl.put_e(l, k, V.e + i + n0 * (j + n1 * k), nv[cnt]);
       cnt++;
     });
-    __syncthreads();
+    cl.sync();
   }
 }
 
-// red-black sweeps by one CTA, each thread over the x-pairs of the box (or
-// damped Jacobi sweeps)
+// red-black sweeps, each thread over x-pairs of its CTA's planes (or damped
+// Jacobi sweeps); a pass reads only the other colour, so its writes can go
+// out while it runs
 template <class P>
-__device__ void tail_smooth(const TailArgs<P>& a, const BoxK<P>& V, int sweeps,
-                            bool red_first) {
+__device__ void tail_smooth(const TailCl<P>& cl, const TailArgs<P>& a, int l, const BoxK<P>& V,
+                            int sweeps, bool red_first) {
   if (a.jacobi) {
-    tail_jacobi(V, sweeps, a.omega);
+    tail_jacobi(cl, l, V, sweeps, a.omega);
     return;
   }
   const int n0 = V.n0, n1 = V.n1;
@@ -1204,15 +1281,15 @@ __device__ void tail_smooth(const TailArgs<P>& a, const BoxK<P>& V, int sweeps,
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
       const int colour = red_first ? pass : 1 - pass;
-      cta_for3(hx, n1, V.n2, [&](int px, int j, int k) {
+      cl_for3(cl, hx, n1, V.n2, [&](int px, int j, int k) {
         const int i = 2 * px + ((j + k + colour) & 1);
         if (i >= n0) return;
         P dg, of;
         box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
         const int idx = i + n0 * (j + n1 * k);
-        V.e[idx] = (V.f[idx] + of) / dg;
+        cl.put_e(l, k, V.e + idx, (V.f[idx] + of) / dg);
       });
-      __syncthreads();
+      cl.sync();
     }
 }
 
@@ -1231,11 +1308,54 @@ __device__ void cta_copy(P* dst, const P* __restrict__ src, int n) {
   for (; q < n; q += bd) dst[q] = src[q];
 }
 
+// grid: 2 clusters of C CTAs (field = cluster; C a power of 2), launched
+// with cluster dimension C (C = 1: one CTA per field)
 template <class P>
 __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
   extern __shared__ __align__(16) unsigned char tail_raw[];
+  __shared__ P* s_rb[kTailClusterMax];
   P* sm = reinterpret_cast<P*>(tail_raw);
-  const int fld = blockIdx.x;
+  cg::cluster_group cluster = cg::this_cluster();
+  TailCl<P> cl;
+  cl.sm = sm;
+  cl.rb = s_rb;
+  cl.C = (int)cluster.num_blocks();
+  cl.r = (int)cluster.block_rank();
+  cl.lgC = 31 - __clz(cl.C);
+  const int fld = blockIdx.x / cl.C;
+  if (threadIdx.x < cl.C) s_rb[threadIdx.x] = cluster.map_shared_rank(sm, (int)threadIdx.x);
+  __shared__ uint8_t s_me[kTailPlanes], s_mf[kTailPlanes];
+  const int npl = a.pb[a.nlev];
+  cl.pb = a.pb;
+  cl.me = (cl.C > 1 && npl <= kTailPlanes) ? s_me : nullptr;
+  cl.mf = cl.me ? s_mf : nullptr;
+  if (cl.me) {
+    for (int q = threadIdx.x; q < npl; q += blockDim.x) {
+      int X = 0;
+      while (q >= a.pb[X + 1]) X++;
+      const int p = q - a.pb[X];
+      unsigned me = 0u, mf = 0u;
+      for (int rr = 0; rr < cl.C; rr++) {
+        int o0, o1;
+        cl.own(a.B[X].n[2], rr, o0, o1);
+        if (o0 < o1 && p >= o0 - 1 && p <= o1) me |= 1u << rr;
+        if (p >= o0 && p < o1) mf |= 1u << rr;
+        if (X + 1 < a.nlev) {
+          int c0, c1;
+          cl.own(a.B[X + 1].n[2], rr, c0, c1);
+          if (c0 < c1 && p >= 2 * c0 - 1 && p <= 2 * c1) me |= 1u << rr;
+          if (c0 < c1 && p >= 2 * c0 && p < 2 * c1) mf |= 1u << rr;
+        }
+        if (X > 0) {
+          int f0, f1;
+          cl.own(a.B[X - 1].n[2], rr, f0, f1);
+          if (f0 < f1 && p >= (f0 >> 1) - 1 && p <= ((f1 - 1) >> 1) + 1) me |= 1u << rr;
+        }
+      }
+      s_me[q] = (uint8_t)me;
+      s_mf[q] = (uint8_t)mf;
+    }
+  }
   for (int l = 0; l < a.nlev; l++) {
     const BoxRaw& B = a.B[l];
     cta_copy(sm + a.offA[l], a.A[l] + fld * B.AF, (int)B.AF);
@@ -1243,17 +1363,19 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
     for (int q = threadIdx.x; q < nc; q += blockDim.x) sm[a.offE[l] + q] = P(0);
   }
   cta_copy(sm + a.offF[0], a.f0 + fld * a.vfs0, a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2]);
-  __syncthreads();
+  // every replica initialised (and every CTA of the cluster running) before
+  // the first remote write
+  cl.sync();
   // down: smooth, restrict (8-cell average of f - L e; after a red-first
   // sweep the black children's residual is zero)
   for (int l = 0; l + 1 < a.nlev; l++) {
     BoxK<P> V = tail_view(a, sm, l);
-    tail_smooth(a, V, a.nu1, true);
+    tail_smooth(cl, a, l, V, a.nu1, true);
     const BoxRaw& C = a.B[l + 1];
     const int c0 = C.n[0], c1 = C.n[1];
     const bool black0 = a.nu1 > 0 && !a.jacobi;
     P* fc = sm + a.offF[l + 1];
-    cta_for3(c0, c1, C.n[2], [&](int ci, int cj, int ck) {
+    cl_for3(cl, c0, c1, C.n[2], [&](int ci, int cj, int ck) {
       P s = P(0);
       for (int q = 0; q < 8; q++) {
         const int x = q & 1, y = (q >> 1) & 1, z = q >> 2;
@@ -1264,25 +1386,30 @@ __global__ void __launch_bounds__(kTailThreads) k_box_tail(TailArgs<P> a) {
         box_row<P, false>(V, V.A, V.e, i, j, k, dg, of);
         s += V.f[idx] - (dg * V.e[idx] - of);
       }
-      fc[ci + c0 * (cj + c1 * ck)] = s / P(8);
+      cl.put_f(l + 1, ck, fc + ci + c0 * (cj + c1 * ck), s / P(8));
     });
-    __syncthreads();
+    cl.sync();
   }
-  tail_smooth(a, tail_view(a, sm, a.nlev - 1), a.csw, true);
+  tail_smooth(cl, a, a.nlev - 1, tail_view(a, sm, a.nlev - 1), a.csw, true);
   // up: trilinear prolongation of the coarse correction, smooth
   for (int l = a.nlev - 2; l >= 0; l--) {
     BoxK<P> V = tail_view(a, sm, l);
     const BoxRaw& C = a.B[l + 1];
     const P* src = sm + a.offE[l + 1];
-    cta_for3(V.n0, V.n1, V.n2, [&](int i, int j, int k) {
-      V.e[i + V.n0 * (j + V.n1 * k)] +=
-          tri_interp(src, C.n[0], C.n[1], C.n[2], i, j, k, (const int*)nullptr);
+    cl_for3(cl, V.n0, V.n1, V.n2, [&](int i, int j, int k) {
+      P* pe = V.e + i + V.n0 * (j + V.n1 * k);
+      cl.put_e(l, k, pe,
+               *pe + tri_interp(src, C.n[0], C.n[1], C.n[2], i, j, k, (const int*)nullptr));
     });
-    __syncthreads();
-    tail_smooth(a, V, a.nu2, false);
+    cl.sync();
+    tail_smooth(cl, a, l, V, a.nu2, false);
   }
-  const int nc0 = a.B[0].n[0] * a.B[0].n[1] * a.B[0].n[2];
-  for (int q = threadIdx.x; q < nc0; q += blockDim.x) a.e0[fld * a.vfs0 + q] = sm[a.offE[0] + q];
+  // every replica is complete: each CTA stores its planes of level 0
+  const BoxRaw& B0 = a.B[0];
+  cl_for3(cl, B0.n[0], B0.n[1], B0.n[2], [&](int i, int j, int k) {
+    const int q = i + B0.n[0] * (j + B0.n[1] * k);
+    a.e0[fld * a.vfs0 + q] = sm[a.offE[0] + q];
+  });
 }
 
 template <class P>
@@ -1303,6 +1430,8 @@ void run_tail(PcState* ps, cudaStream_t s) {
     a.offF[l] = off;
     off += nc;
   }
+  a.pb[0] = 0;
+  for (int l = 0; l < a.nlev; l++) a.pb[l + 1] = a.pb[l] + ps->box[m0 + l].n[2];
   a.f0 = (const P*)ps->bf[m0];
   a.e0 = (P*)ps->be[m0];
   a.vfs0 = ps->box[m0].n[0] * ps->box[m0].n[1] * ps->box[m0].n[2];
@@ -1311,7 +1440,20 @@ void run_tail(PcState* ps, cudaStream_t s) {
   a.csw = ps->csw;
   a.jacobi = ps->smoother == NRD_SMOOTH_JACOBI;
   a.omega = (P)ps->omega;
-  k_box_tail<P><<<2, kTailThreads, ps->tail_smem, s>>>(a);
+  const int C = std::max(1, ps->tail_cl);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2 * C);
+  cfg.blockDim = dim3(kTailThreads);
+  cfg.dynamicSmemBytes = ps->tail_smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_box_tail<P>, a);
 }
 
 template <class P>
@@ -1670,8 +1812,9 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
     return NRD_ENOMEM;
   }
   // the coarsest box levels whose data fit one CTA's shared memory run as
-  // one kernel (the first such level with at most 8,192 cells per field);
-  // FP32 V-cycles only: one SM's FP64 rate is too low for it
+  // one kernel (the first such level with at most 8,192 cells per field),
+  // one thread-block cluster per field; FP32 V-cycles only: the few SMs'
+  // FP64 rate is too low for it
   ps->tail_m = 0;
   for (int m = 1; m < ps->nmg && !ps->tail_m && ps->prec == NRD_PC_F32; m++) {
     const long nc = (long)ps->box[m].n[0] * ps->box[m].n[1] * ps->box[m].n[2];
@@ -1692,6 +1835,28 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
                          (int)kTailSmemMax);
     cudaFuncSetAttribute(k_box_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)kTailSmemMax);
+    // the largest cluster (up to kTailClusterMax CTAs, one per SM) that can be resident
+    ps->tail_cl = 1;
+    for (int C = kTailClusterMax; C > 1; C /= 2) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2 * C);
+      cfg.blockDim = dim3(kTailThreads);
+      cfg.dynamicSmemBytes = ps->tail_smem;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = C;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_box_tail<float>, &cfg) == cudaSuccess &&
+          ncl >= 1) {
+        ps->tail_cl = C;
+        break;
+      }
+      cudaGetLastError();   // clear a refused query
+    }
   }
   *out = ps;
   return NRD_OK;
@@ -1797,7 +1962,7 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
     const double* Cf = (m == 1) ? ps->Craw : ps->bCraw[m - 1];
     const BoxRaw& C = ps->box[m];
     long nc = (long)C.n[0] * C.n[1] * C.n[2];
-    dim3 g(g1(nc), 2);
+    dim3 g(g1(3 * nc), 2);
     const double* hb = ps->bh[m];
     const double r2[3] = {1.0 / (hb[0] * hb[0]), 1.0 / (hb[1] * hb[1]), 1.0 / (hb[2] * hb[2])};
     // after the linearisation the finer level's scaled coefficients are the
