@@ -229,27 +229,28 @@ __global__ void k_zero_cov(const uint8_t* __restrict__ mask, int N, double* x) {
 // divides once at the end: FP64 division is a long instruction sequence on
 // GB300.  (a/b < c/d <=> a d < c b; a near-tie may pick the other element,
 // whose quotient then differs in the last bit at most.)
+// Entries are screened by cap_candidate (integer instructions); blocks with
+// no candidate skip the FP64 minimum tree.
+
 __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restrict__ u,
                          const double* __restrict__ v, int N, double* part, unsigned* counter,
                          double* res, int slot) {
   __shared__ double sh[1024];
-  double ba = 1.0, bb = 0.0;   // no candidate yet: b = 0
+  double ba = 1.0, bb = 0.0;
+  bool have = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     const bool leaf = !(mask[i] & MASK_COVERED);
     const double v0 = v[i], v1 = v[N + i];
     const double u0 = u[i], u1 = u[N + i];   // fetched with v, not after the sign test
-    if (leaf && v0 < 0.0) {
-      const double b = -v0;
-      if (bb == 0.0 || u0 * bb < ba * b) { ba = u0; bb = b; }
-    }
-    if (leaf && v1 < 0.0) {
-      const double b = -v1;
-      if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
-    }
+    if (leaf && cap_candidate(u0, v0)) cap_take(u0, v0, have, ba, bb);
+    if (leaf && cap_candidate(u1, v1)) cap_take(u1, v1, have, ba, bb);
   }
-  double m = DBL_MAX;
-  if (bb > 0.0) m = ba / bb;
-  double r = block_red<1>(m, sh);
+  double r = DBL_MAX;
+  if (__syncthreads_or(have)) {
+    double m = DBL_MAX;
+    if (have) m = ba / bb;
+    r = block_red<1>(m, sh);
+  }
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);
 }
@@ -260,7 +261,7 @@ __global__ void k_poscap(const uint8_t* __restrict__ mask, const double* __restr
 // u / (-x), pairs compared by cross-multiplication as in k_poscap, into
 // res[slot] by last-block finishing.  nv = *jd when jd is given (device
 // count), else nvh.
-__global__ void k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* __restrict__ x,
+__global__ void __launch_bounds__(256) k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* __restrict__ x,
                               const double* __restrict__ Z, long stride, const int* jd, int nvh,
                               const double* __restrict__ y, const double* __restrict__ u,
                               double* part, unsigned* counter, double* res, int slot) {
@@ -270,29 +271,30 @@ __global__ void k_lincomb_cap(const uint8_t* __restrict__ mask, int N, double* _
   if (threadIdx.x < nv) ys[threadIdx.x] = y[threadIdx.x];
   __syncthreads();
   double ba = 1.0, bb = 0.0;
+  bool have = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     // u and the mask are fetched with dx and Z, not after the sign test
     const double u0 = u[i], u1 = u[N + i];
     const bool leaf = !(mask[i] & MASK_COVERED);
     double s0 = x[i], s1 = x[N + i];
+    // 4 basis vectors in flight; fuller unrolling takes the registers of a
+    // fourth resident block (80 instead of 60), and the grid then runs in two waves
+#pragma unroll 4
     for (int q = 0; q < nv; q++) {
       s0 += ys[q] * Z[q * stride + i];
       s1 += ys[q] * Z[q * stride + N + i];
     }
     x[i] = s0;
     x[N + i] = s1;
-    if (leaf && s0 < 0.0) {
-      const double b = -s0;
-      if (bb == 0.0 || u0 * bb < ba * b) { ba = u0; bb = b; }
-    }
-    if (leaf && s1 < 0.0) {
-      const double b = -s1;
-      if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
-    }
+    if (leaf && cap_candidate(u0, s0)) cap_take(u0, s0, have, ba, bb);
+    if (leaf && cap_candidate(u1, s1)) cap_take(u1, s1, have, ba, bb);
   }
-  double m = DBL_MAX;
-  if (bb > 0.0) m = ba / bb;
-  double r = block_red<1>(m, sh);
+  double r = DBL_MAX;
+  if (__syncthreads_or(have)) {
+    double m = DBL_MAX;
+    if (have) m = ba / bb;
+    r = block_red<1>(m, sh);
+  }
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (lb_arrive(counter)) lb_finish<1>(part, 1, 1, res, slot, counter);
 }

@@ -719,9 +719,9 @@ __global__ void k_reflux(RfArgs a, const int* __restrict__ rf_level, const doubl
       int4 g = a.g[q];
       double PE = 0.25 * (cf[g.x] + cf[g.y] + cf[g.z] + cf[g.w]);
       double PT = 0.25 * (cf[a.G + g.x] + cf[a.G + g.y] + cf[a.G + g.z] + cf[a.G + g.w]);
-      double h = a.lh.h[lvl][d];
-      dE += s * PE / h;
-      dT += s * PT / h;
+      const double rh = a.lh.rh[lvl][d];   // 1/h: no FP64 division per face
+      dE += s * PE * rh;
+      dT += s * PT * rh;
     }
     out[c] += sc * dE;
     out[a.N + c] += sc * dT;

@@ -295,29 +295,31 @@ __global__ void __launch_bounds__(256) k_cycle_update_g(
   }
   __syncthreads();
   double ba = 1.0, bb = 0.0;
+  bool have = false;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
     // u and the mask are fetched with dx and Z, not after the sign test
     const double u0 = u[i], u1 = u[N + i];
     const bool leaf = !(mask[i] & MASK_COVERED);
     double s0 = dx[i], s1 = dx[N + i];
+    // 4 basis vectors in flight; fuller unrolling takes the registers of a
+    // fourth resident block (80 instead of 60), and the grid then runs in two waves
+#pragma unroll 4
     for (int q = 0; q < k; q++) {
       s0 += ys[q] * Z[q * stride + i];
       s1 += ys[q] * Z[q * stride + N + i];
     }
     dx[i] = s0;
     dx[N + i] = s1;
-    if (leaf && s0 < 0.0) {
-      const double b = -s0;
-      if (bb == 0.0 || u0 * bb < ba * b) { ba = u0; bb = b; }
-    }
-    if (leaf && s1 < 0.0) {
-      const double b = -s1;
-      if (bb == 0.0 || u1 * bb < ba * b) { ba = u1; bb = b; }
-    }
+    // candidates screened with integer instructions (cap_candidate)
+    if (leaf && cap_candidate(u0, s0)) cap_take(u0, s0, have, ba, bb);
+    if (leaf && cap_candidate(u1, s1)) cap_take(u1, s1, have, ba, bb);
   }
-  double mq = DBL_MAX;
-  if (bb > 0.0) mq = ba / bb;
-  const double r = blk_min(mq, sh);
+  double r = DBL_MAX;
+  if (__syncthreads_or(have)) {
+    double mq = DBL_MAX;
+    if (have) mq = ba / bb;
+    r = blk_min(mq, sh);
+  }
   if (threadIdx.x == 0) part[blockIdx.x] = r;
   if (last_block(counter)) {
     double acc = DBL_MAX;

@@ -359,3 +359,30 @@ int ctx_jv(nrd_ctx* c, const double* u, const double* v, const double* b, const 
            const double* par = nullptr);
 int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, double dt, double* F,
                   cudaStream_t s, const double* par = nullptr, bool with_dz = false);
+
+#ifdef __CUDACC__
+// Candidate test of the positivity cap (Sec. 4.1 remark: lambda =
+// min(1, 0.9 min over x_i < 0 of u_i / (-x_i))): true when x < 0 (not -0, not
+// NaN) and u / (-x) may be below 2, read from the exponent fields with integer
+// instructions.  An entry with u / (-x) > 2 cannot set lambda (0.9 x 2 > 1), so
+// leaving it out gives the same lambda as the full minimum, and most entries of
+// a Newton update are decided without FP64 instructions, which issue on
+// GB300's narrow FP64 pipe.  (With e_u >= e_x + 2, u >= 2^(e_u - 1023) and
+// -x < 2^(e_x - 1022), so u / (-x) > 2.)  A negative u always counts: it
+// makes lambda <= 0, the failure the callers report.
+__device__ __forceinline__ bool cap_candidate(double u, double x) {
+  const unsigned xh = (unsigned)__double2hiint(x), xl = (unsigned)__double2loint(x);
+  const unsigned ax = xh & 0x7fffffffu;
+  if (!(xh >> 31) || (ax | xl) == 0u) return false;                       // x >= 0 or -0
+  if (ax > 0x7ff00000u || (ax == 0x7ff00000u && xl != 0u)) return false;  // NaN
+  const unsigned uh = (unsigned)__double2hiint(u);
+  if (uh >> 31) return true;
+  return (uh >> 20) <= (ax >> 20) + 1u;
+}
+// a thread's best candidate so far as the pair (a, b) = (u, -x): a/b < c/d
+// compared as a d < c b (both b > 0), one division at the end
+__device__ __forceinline__ void cap_take(double u, double x, bool& have, double& ba, double& bb) {
+  const double b = -x;
+  if (!have || u * bb < ba * b) { ba = u; bb = b; have = true; }
+}
+#endif
