@@ -737,22 +737,52 @@ __global__ void k_reflux(RfArgs a, const int* __restrict__ rf_level, const doubl
 // from a band of 1e-12 around the threshold the squared comparison decides
 // the same.  FP64 square roots and divisions are long instruction sequences
 // on GB300's FP64 pipe.
-__device__ __forceinline__ bool fast_range(double x) { return x > 1e-290 && x < 1e290; }
+// For non-negative doubles (not NaN) the order of the values is the order of
+// their bit patterns as signed 64-bit integers, so the comparisons below take
+// integer instructions instead of FP64 compares (which issue on GB300's narrow
+// FP64 pipe).  A band of 2^14 units in the last place around the threshold is
+// at least 1.8e-12 relative (an ulp step is between 2^-53 and 2^-52
+// relative), wider than the 1e-12 the exact-decision argument needs.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+constexpr long long kBits1em290 = 0x03b8f2b061aea072LL;   // 1e-290
+constexpr long long kBits1e290 = 0x7c2485ce9e7a065fLL;    // 1e290
+constexpr long long kBits1e300 = 0x7e37e43c8800759cLL;    // 1e300
+constexpr long long kBand = 1LL << 14;
+__device__ __forceinline__ bool fast_range(double x) {
+  const long long xb = dbits(x);
+  return xb > kBits1em290 && xb < kBits1e290;
+}
 __device__ __forceinline__ bool sqrt_ratio_gt(double s, double b, double t) {
   const double tb = t * b, tb2 = tb * tb;
-  if (b > 0.0 && t >= 0.0 && s >= 0.0 && fast_range(tb2) && s < 1e300) {
-    if (s > tb2 * (1.0 + 1e-12)) return true;
-    if (s < tb2 * (1.0 - 1e-12)) return false;
+  const long long sb = dbits(s), t2b = dbits(tb2);
+  if (dbits(b) > 0 && t >= 0.0 && sb >= 0 && fast_range(tb2) && sb < kBits1e300) {
+    if (sb > t2b + kBand) return true;
+    if (sb < t2b - kBand) return false;
   }
   return sqrt(s) / b > t;
 }
 __device__ __forceinline__ bool ratio_gt(double a, double b, double t) {
   const double tb = t * b;
-  if (b > 0.0 && t >= 0.0 && a >= 0.0 && fast_range(tb) && a < 1e300) {
-    if (a > tb * (1.0 + 1e-12)) return true;
-    if (a < tb * (1.0 - 1e-12)) return false;
+  const long long ab = dbits(a), tbb = dbits(tb);
+  if (b > 0.0 && t >= 0.0 && ab >= 0 && fast_range(tb) && ab < kBits1e300) {
+    if (ab > tbb + kBand) return true;
+    if (ab < tbb - kBand) return false;
   }
   return a / b > t;
+}
+
+// x 2^k (k = 1, -1, -2) exactly, by adding k to the exponent field when x is
+// normal and stays normal (the product of a power of 2 is then exact, so the
+// result is bit-identical to the multiplication), x itself for +-0; other
+// values (subnormal, near overflow, inf, NaN) take the multiplication.
+__device__ __noinline__ double scale2_slow(double x, double f) { return __dmul_rn(f, x); }
+template <int K>
+__device__ __forceinline__ double scale2(double x) {
+  const long long xb = dbits(x);
+  const long long e = (xb >> 52) & 0x7ff;
+  if (e >= 3 && e <= 2044) return __longlong_as_double(xb + ((long long)K << 52));
+  if ((xb & 0x7fffffffffffffffLL) == 0) return x;
+  return scale2_slow(x, K == 1 ? 2.0 : (K == -1 ? 0.5 : 0.25));
 }
 
 __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles, int tx, int ty, int tz,
@@ -788,11 +818,12 @@ __global__ void k_tag(const TileDev* tiles, const PatchDev* patches, int ntiles,
             Ev[si] = gE[P.goff + P.fo[f] + a + P.n[(d + 1) % 3] * b];
           }
         }
-        // no contraction: the same roundings as a plain evaluation
-        if (want_c) tc += fabs(__dadd_rn(__dsub_rn(Ev[1], __dmul_rn(2.0, Ec)), Ev[0]));
+        // no contraction: the same roundings as a plain evaluation (the
+        // power-of-2 scalings are exact either way)
+        if (want_c) tc += fabs(__dadd_rn(__dsub_rn(Ev[1], scale2<1>(Ec)), Ev[0]));
         const double df = __dsub_rn(Ev[1], Ev[0]);
-        if (want_g) tg += __dmul_rn(0.5, fabs(df));
-        if (want_r) gr2 = __dadd_rn(gr2, __dmul_rn(__dmul_rn(0.25, df), df));
+        if (want_g) tg += scale2<-1>(fabs(df));
+        if (want_r) gr2 = __dadd_rn(gr2, __dmul_rn(scale2<-2>(df), df));
       }
       uint8_t tag = 0;
       if (want_c && ratio_gt(tc, sc, thr_c)) tag |= 1;
