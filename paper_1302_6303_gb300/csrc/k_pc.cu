@@ -905,78 +905,95 @@ struct BoxRaw {
   long NA, gbase, cell0, AF;
 };
 
-// fused with the scaling of the coarse level:
-// A = beta C / h^2 on interior faces, beta 2 D_b / (h (4 D_b + h)) on Robin
-// faces of E, 0 elsewhere; rh2 = 1/h^2 per axis of the coarse level.
-// SCALED (after the linearisation): interior faces average the finer
-// level's scaled coefficients Ain (the mean over 4, as the raw C, then
-// 1/4 for the doubled h), box faces the raw Robin D_b.  One thread per
-// (coarse cell, axis): the axis's low face and, on the box's faces, its
-// boundary faces (short dependency chains; these launches are small).  FP32
-// coefficients are averaged in FP32 (FP64 arithmetic and conversions issue
-// on GB300's narrow FP64 pipe).
+// Every GMG level m >= 1 of the base box in one launch, each straight from
+// the base level: a level-m face covers S^2 base faces (S = 2^m), and the
+// level-by-level rule (coarse C = mean of the 4 finer C; scaled
+// A = beta C / h^2 with h doubling per level) composes to
+//   C_m = mean of the S^2 base C,   A_m = (sum of the S^2 base A) / S^4,
+// so no level waits for the one above it.  Fused with the scaling: A = beta C
+// / h^2 on interior faces, beta 2 D_b / (h (4 D_b + h)) on Robin faces of E
+// (D_b the mean of the S^2 base D_b), 0 elsewhere.  SCALED (after the
+// linearisation): interior faces from the base level's scaled coefficients
+// Ain, box faces from the raw Robin D_b.  One thread per (level, coarse cell,
+// axis); FP32 coefficients are summed in FP32 (FP64 arithmetic and
+// conversions issue on GB300's narrow FP64 pipe).
+template <class P>
+struct CoarsenAll {
+  int nlev;                        // levels 1 .. nlev
+  BoxRaw F;                        // the base box (level 0 of the GMG hierarchy)
+  BoxRaw C[NRD_MAX_MG];            // level m at C[m]
+  P* A[NRD_MAX_MG];                // scaled coefficients of level m (field f at + f AF)
+  double h[NRD_MAX_MG][3];
+  int item0[NRD_MAX_MG + 1];       // first item of level m (3 per coarse cell); the
+                                   // coarsest level first (its items sum the most terms)
+};
+
 template <class P, bool SCALED>
-__global__ void k_box_coarsen(BoxRaw F, const double* Cf, BoxRaw Cc, double* Cc_raw,
-                              const int* gtype_box, const double* dbeta, double hx, double hy,
-                              double hz, double rh2x, double rh2y, double rh2z, P* A,
-                              const P* Ain) {
+__global__ void k_box_coarsen(CoarsenAll<P> a, const double* Cf, const P* Ain,
+                              const int* gtype_box, const double* dbeta) {
   const int fld = blockIdx.y;
+  const BoxRaw& F = a.F;
   const double* cf = Cf + fld * F.AF;
   const P* ain = SCALED ? Ain + fld * F.AF : nullptr;
-  double* cc = Cc_raw + fld * Cc.AF;
-  P* Af = A + fld * Cc.AF;
-  // every box starts at cell 0 of its vectors; indices are 32-bit (3N + G
-  // < 2^31 for the hierarchy, which bounds every box)
-  const int ncc = Cc.n[0] * Cc.n[1] * Cc.n[2];
-  const int fNA = (int)F.NA, cNA = (int)Cc.NA, fgb = (int)F.gbase, cgb = (int)Cc.gbase;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 3 * ncc;
+  // indices are 32-bit (3N + G < 2^31 for the hierarchy, which bounds every box)
+  const int fNA = (int)F.NA, fgb = (int)F.gbase;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < a.item0[0];
        t += gridDim.x * blockDim.x) {
-    const int d = t / ncc, c = t - d * ncc;
+    int m = a.nlev;
+    while (t >= a.item0[m - 1]) m--;
+    const BoxRaw& Cc = a.C[m];
+    const int ncc = Cc.n[0] * Cc.n[1] * Cc.n[2];
+    const int it = t - a.item0[m];
+    const int d = it / ncc, c = it - d * ncc;
     int q[3];
     const int r = c / Cc.n[0];
     q[0] = c - r * Cc.n[0];
     q[2] = r / Cc.n[1];
     q[1] = r - q[2] * Cc.n[1];
     const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-    const double rh2 = (d == 0) ? rh2x : ((d == 1) ? rh2y : rh2z);
+    const int S = 1 << m, S2 = S * S;
+    const int cNA = (int)Cc.NA, cgb = (int)Cc.gbase;
+    P* Af = a.A[m] + fld * Cc.AF;
+    const double beta = *dbeta;
+    const double hd = a.h[m][d];
     if (q[d] > 0) {
-      int fi[4];
-#pragma unroll
-      for (int a = 0; a < 2; a++)
-#pragma unroll
-        for (int b = 0; b < 2; b++) {
-          int p[3];
-          p[d] = 2 * q[d];
-          p[t1] = 2 * q[t1] + a;
-          p[t2] = 2 * q[t2] + b;
-          fi[2 * a + b] = d * fNA + p[0] + F.n[0] * (p[1] + F.n[1] * p[2]);
-        }
+      int p[3];
+      p[d] = S * q[d];
       if (SCALED) {
-        Af[d * cNA + c] = mean16<P>(ain[fi[0]], ain[fi[1]], ain[fi[2]], ain[fi[3]]);
+        P acc[4] = {P(0), P(0), P(0), P(0)};
+#pragma unroll 4
+        for (int u = 0; u < S2; u++) {
+          p[t1] = S * q[t1] + (u & (S - 1));
+          p[t2] = S * q[t2] + (u >> m);
+          acc[u & 3] += ain[d * fNA + p[0] + F.n[0] * (p[1] + F.n[1] * p[2])];
+        }
+        // 1 / S^4 is a power of 2: the scaling is exact
+        Af[d * cNA + c] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) * (P(1) / (P(S2) * P(S2)));
       } else {
-        const double sm = ((cf[fi[0]] + cf[fi[1]]) + cf[fi[2]]) + cf[fi[3]];
-        cc[d * cNA + c] = 0.25 * sm;
-        Af[d * cNA + c] = (P)(0.25 * sm * (*dbeta * rh2));
+        double acc = 0.0;
+        for (int u = 0; u < S2; u++) {
+          p[t1] = S * q[t1] + (u & (S - 1));
+          p[t2] = S * q[t2] + (u >> m);
+          acc += cf[d * fNA + p[0] + F.n[0] * (p[1] + F.n[1] * p[2])];
+        }
+        Af[d * cNA + c] = (P)((acc / S2) * (beta / (hd * hd)));
       }
     }
     for (int sd = 0; sd < 2; sd++) {
       const bool at = sd ? (q[d] == Cc.n[d] - 1) : (q[d] == 0);
       if (!at) continue;
       const int f = 2 * d + sd;
-      double sm = 0.0;
-      for (int a = 0; a < 2; a++)
-        for (int b = 0; b < 2; b++) {
-          const int p1 = 2 * q[t1] + a, p2 = 2 * q[t2] + b;
-          sm += cf[fgb + F.fo[f] + p1 + F.n[t1] * p2];
-        }
-      const int g = cgb + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2];
-      cc[g] = 0.25 * sm;
       double v = 0.0;
       if (gtype_box[f] == 1 && fld == 0) {
-        const double Db = 0.25 * sm, h = (d == 0) ? hx : ((d == 1) ? hy : hz);
-        v = *dbeta * 2.0 * Db / (h * (4.0 * Db + h));
+        double acc = 0.0;
+        for (int u = 0; u < S2; u++) {
+          const int p1 = S * q[t1] + (u & (S - 1)), p2 = S * q[t2] + (u >> m);
+          acc += cf[fgb + F.fo[f] + p1 + F.n[t1] * p2];
+        }
+        const double Db = acc / S2;
+        v = beta * 2.0 * Db / (hd * (4.0 * Db + hd));
       }
-      Af[g] = (P)v;
+      Af[cgb + Cc.fo[f] + q[t1] + Cc.n[t1] * q[t2]] = (P)v;
     }
   }
 }
@@ -1004,7 +1021,6 @@ struct PcState {
   // GMG levels m = 1..nmg-1
   BoxRaw box[NRD_MAX_MG];
   double bh[NRD_MAX_MG][3];
-  double* bCraw[NRD_MAX_MG] = {nullptr};
   void* bA[NRD_MAX_MG] = {nullptr};
   void* be[NRD_MAX_MG] = {nullptr};
   void* bf[NRD_MAX_MG] = {nullptr};
@@ -1796,13 +1812,11 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
     B.gbase = 3 * nc;
     B.AF = 3 * nc + fo;
     for (int d = 0; d < 3; d++) ps->bh[m][d] = H.lev[0].h[d] * (double)(1 << m);
-    ok = cudaMalloc(&ps->bCraw[m], 2 * B.AF * sizeof(double)) == cudaSuccess &&
-         cudaMalloc(&ps->bA[m], 2 * B.AF * e) == cudaSuccess &&
+    ok = cudaMalloc(&ps->bA[m], 2 * B.AF * e) == cudaSuccess &&
          cudaMalloc(&ps->be[m], 2 * nc * e) == cudaSuccess &&
          cudaMalloc(&ps->bj[m], 2 * nc * e) == cudaSuccess &&
          cudaMalloc(&ps->bf[m], 2 * nc * e) == cudaSuccess;
     if (ok) {
-      cudaMemset(ps->bCraw[m], 0, 2 * B.AF * sizeof(double));
       cudaMemset(ps->bA[m], 0, 2 * B.AF * e);
     }
   }
@@ -1872,7 +1886,7 @@ void pc_free(PcState* ps) {
   pc_drop_graphs(ps);
   if (ps->cap) cudaStreamDestroy(ps->cap);
   for (int m = 0; m < NRD_MAX_MG; m++) {
-    F(ps->bCraw[m]); F(ps->bA[m]); F(ps->be[m]); F(ps->bj[m]); F(ps->bf[m]);
+    F(ps->bA[m]); F(ps->be[m]); F(ps->bj[m]); F(ps->bf[m]);
   }
   delete ps;
 }
@@ -1919,6 +1933,27 @@ void pc_lin_targets(PcState* ps, float** a32, double** a64, double** p2, float**
   *p2f = (ps->prec == NRD_PC_F32) ? (float*)ps->p2 : nullptr;
 }
 
+template <class P>
+void coarsen_all(PcState* ps, bool scaled, cudaStream_t s) {
+  CoarsenAll<P> a;
+  a.nlev = ps->nmg - 1;
+  a.F = ps->box[0];
+  // items of level m: [item0[m], item0[m - 1]), item0[nlev] = 0, item0[0] = all
+  a.item0[ps->nmg - 1] = 0;
+  for (int m = ps->nmg - 1; m >= 1; m--) {
+    a.C[m] = ps->box[m];
+    a.A[m] = (P*)ps->bA[m];
+    for (int d = 0; d < 3; d++) a.h[m][d] = ps->bh[m][d];
+    a.item0[m - 1] = a.item0[m] + 3 * ps->box[m].n[0] * ps->box[m].n[1] * ps->box[m].n[2];
+  }
+  const dim3 g(g1(a.item0[0]), 2);
+  if (scaled)
+    k_box_coarsen<P, true><<<g, BS, 0, s>>>(a, ps->Craw, (const P*)ps->A, ps->bgt, ps->d_beta);
+  else
+    k_box_coarsen<P, false><<<g, BS, 0, s>>>(a, ps->Craw, (const P*)nullptr, ps->bgt,
+                                             ps->d_beta);
+}
+
 int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, double a0, double dt,
               bool from_lin, cudaStream_t s, bool beta_on_device) {
   ps->beta = dt / a0;
@@ -1956,34 +1991,10 @@ int pc_finish(PcState* ps, const Hier& H, const double* u, const float* z, doubl
                                                     ps->d_beta, a.lh, l, ps->Craw,
                                                     (float*)nullptr);
   }
-  // GMG levels
-  for (int m = 1; m < ps->nmg; m++) {
-    const BoxRaw& F = (m == 1) ? ps->box[0] : ps->box[m - 1];
-    const double* Cf = (m == 1) ? ps->Craw : ps->bCraw[m - 1];
-    const BoxRaw& C = ps->box[m];
-    long nc = (long)C.n[0] * C.n[1] * C.n[2];
-    dim3 g(g1(3 * nc), 2);
-    const double* hb = ps->bh[m];
-    const double r2[3] = {1.0 / (hb[0] * hb[0]), 1.0 / (hb[1] * hb[1]), 1.0 / (hb[2] * hb[2])};
-    // after the linearisation the finer level's scaled coefficients are the
-    // source (raw values exist on Robin faces only)
-    const void* Ain = (m == 1) ? ps->A : ps->bA[m - 1];
-    if (ps->prec == NRD_PC_F32 && from_lin)
-      k_box_coarsen<float, true><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
-                                                  hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
-                                                  (float*)ps->bA[m], (const float*)Ain);
-    else if (ps->prec == NRD_PC_F32)
-      k_box_coarsen<float, false><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
-                                                   hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
-                                                   (float*)ps->bA[m], (const float*)nullptr);
-    else if (from_lin)
-      k_box_coarsen<double, true><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
-                                                   hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
-                                                   (double*)ps->bA[m], (const double*)Ain);
-    else
-      k_box_coarsen<double, false><<<g, BS, 0, s>>>(F, Cf, C, ps->bCraw[m], ps->bgt, ps->d_beta,
-                                                    hb[0], hb[1], hb[2], r2[0], r2[1], r2[2],
-                                                    (double*)ps->bA[m], (const double*)nullptr);
+  // GMG levels, all from the base level in one launch
+  if (ps->nmg > 1) {
+    if (ps->prec == NRD_PC_F32) coarsen_all<float>(ps, from_lin, s);
+    else coarsen_all<double>(ps, from_lin, s);
   }
   if (!from_lin) {
     if (ps->prec == NRD_PC_F32) scale_all<float>(ps, H, a, s);
