@@ -1664,18 +1664,15 @@ void level_smooth(PcState* ps, const Hier& H, int l, int sweeps, bool red_first,
 template <class P>
 int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transposed,
             cudaStream_t s, const int* jd = nullptr, long jstride = 0, double* y2 = nullptr) {
-  // r = f (u = 0); covered := mean of children
+  // r = f (u = 0).  The covered cells' residual is not averaged down here:
+  // the finest level has none, and every coarser level's covered cells are
+  // re-averaged by the down-leg composite residual that precedes its smoothing
   if (transposed)
     k_vc_init<P, true><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff, (P*)ps->fr,
                                               (P*)ps->fu, nullptr, 0);
   else
     k_vc_init<P, false><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff, (P*)ps->fr,
                                                (P*)ps->fu, jd, jstride);
-  for (int l = H.L - 2; l >= 0; l--) {
-    if (!H.ncov[l]) continue;
-    dim3 ga(g1(H.ncov[l]), 2);
-    k_avgdown_p<P><<<ga, BS, 0, s>>>(H.d_cov[l], H.ncov[l], (P*)ps->fr, H.N);
-  }
   // down: finest to level 1 (no sweeps: a zero correction)
   for (int l = H.L - 1; l >= 1; l--) {
     if (ps->nu1 > 0) {
