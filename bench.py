@@ -49,7 +49,7 @@ LIN_INST_PER_CELL = 3 * 45 + 34
 # same kernel version (profiles/k_stencil_lin_amr2_base64.md), or None when
 # the kernel changed since.
 LIN_TRAFFIC_BYTES = 25.11e6 + 45.89e6
-JV_TRAFFIC_BYTES = 83.16e6 + 13.41e6
+JV_TRAFFIC_BYTES = 83.17e6 + 12.98e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
