@@ -278,6 +278,21 @@ int nrd_newton(nrd_ctx* ctx, double* u, const double* b, double a0, double dt, n
 int nrd_step(nrd_ctx* ctx, double* u, const double* u_n, const double* u_nm1, double dt,
              double dt_prev, nrd_stats* stats, cudaStream_t stream);
 
+/* nrd_step in two halves, so that work using the step's result can be
+ * enqueued before the host waits for it.  nrd_step_begin checks the
+ * arguments as nrd_step does and enqueues the whole step on `stream` (the
+ * device-loop form; the host-driven form runs to the end here and keeps its
+ * result).  Until nrd_step_end the step is pending: only nrd_time_derivative,
+ * nrd_predict, nrd_lte, nrd_tag and nrd_dot may be called on the context, on
+ * the same stream (they are ordered after the step); any other call returns
+ * NRD_ESTATE, as does a second nrd_step_begin.  nrd_step_end waits for the
+ * stream and returns what nrd_step would have (status and stats; stats may
+ * be NULL); NRD_ESTATE if no step is pending.  u is complete when
+ * nrd_step_end returns (stream-ordered uses may read it earlier). */
+int nrd_step_begin(nrd_ctx* ctx, double* u, const double* u_n, const double* u_nm1, double dt,
+                   double dt_prev, cudaStream_t stream);
+int nrd_step_end(nrd_ctx* ctx, nrd_stats* stats);
+
 /* Refinement indicators of Sec. 5 on every cell (covered cells use the mean
  * of their children): bit 0: tau^c > thr_c (curvature), bit 1: tau^g > thr_g
  * (gradient), bit 2: h |grad E| / E > thr_r.  tags: ncells bytes. */

@@ -6,6 +6,19 @@
 
 #include "nrd_internal.h"
 
+int step_pending_check(nrd_ctx* c, bool pending_ok, cudaStream_t s) {
+  if (!c->pend) return NRD_OK;
+  if (!pending_ok) {
+    c->err = "a step is pending: call nrd_step_end first";
+    return NRD_ESTATE;
+  }
+  if (s != c->pend_s) {
+    c->err = "a step is pending: use the stream of nrd_step_begin";
+    return NRD_ESTATE;
+  }
+  return NRD_OK;
+}
+
 namespace {
 
 const char* kNullCtx = "null context";
@@ -28,10 +41,13 @@ int check_launch(nrd_ctx* c) {
   return NRD_OK;
 }
 
-int need_ready(nrd_ctx* c) {
+// hierarchy and material present; with pending_ok, a step begun by
+// nrd_step_begin may be in flight (the call must then use its stream),
+// otherwise none may be
+int need_ready(nrd_ctx* c, bool pending_ok = false, cudaStream_t s = nullptr) {
   if (!c->have_hier) return fail(c, NRD_ESTATE, "no hierarchy: call nrd_set_hierarchy first");
   if (!c->have_mat) return fail(c, NRD_ESTATE, "no material: call nrd_set_material first");
-  return NRD_OK;
+  return step_pending_check(c, pending_ok, s);
 }
 
 int check_params(const nrd_params* p, std::string& err) {
@@ -233,6 +249,7 @@ int nrd_create(const nrd_params* p, nrd_ctx** out) {
 
 int nrd_destroy(nrd_ctx* c) {
   if (!c) return NRD_EINVAL;
+  if (c->pend) cudaStreamSynchronize(c->pend_s);   // nothing in flight may outlive the buffers
   c->timer.destroy();
   free_fields(c);
   if (c->have_hier) hier_free(c->H);
@@ -247,6 +264,7 @@ const char* nrd_last_error(const nrd_ctx* c) {
 
 int nrd_set_params(nrd_ctx* c, const nrd_params* p) {
   if (!c || !p) return NRD_EINVAL;
+  if (step_pending_check(c, false, nullptr)) return NRD_ESTATE;
   std::string err;
   if (check_params(p, err) != NRD_OK) return fail(c, NRD_EINVAL, err);
   bool retile = (p->tile_x != c->p.tile_x || p->tile_y != c->p.tile_y ||
@@ -279,6 +297,7 @@ int nrd_set_params(nrd_ctx* c, const nrd_params* p) {
 int nrd_set_hierarchy(nrd_ctx* c, int nlevels, const int* nboxes, const int* boxes,
                       const int* bc_type, const double* bc_R) {
   if (!c) return NRD_EINVAL;
+  if (step_pending_check(c, false, nullptr)) return NRD_ESTATE;
   if (!nboxes || !boxes || !bc_type || !bc_R) return fail(c, NRD_EINVAL, "null argument");
   free_fields(c);
   if (c->have_hier) hier_free(c->H);
@@ -343,6 +362,7 @@ int nrd_layout(const nrd_ctx* c, int64_t* ncells, int64_t* nghosts, int64_t* nle
 
 int nrd_set_material(nrd_ctx* c, const float* z, cudaStream_t s) {
   if (!c) return NRD_EINVAL;
+  if (step_pending_check(c, false, nullptr)) return NRD_ESTATE;
   if (!c->have_hier) return fail(c, NRD_ESTATE, "no hierarchy");
   if (!z) return fail(c, NRD_EINVAL, "null z");
   if (cudaMemcpyAsync(c->d_z, z, (size_t)c->H.N * sizeof(float), cudaMemcpyDeviceToDevice, s) !=
@@ -444,6 +464,7 @@ int nrd_fd_eps(nrd_ctx* c, const double* u, const double* v, double* eps_host, c
 int nrd_dot(nrd_ctx* c, const double* x, const double* y, double* out, cudaStream_t s) {
   if (!c) return NRD_EINVAL;
   if (!c->have_hier) return fail(c, NRD_ESTATE, "no hierarchy");
+  if (step_pending_check(c, true, s)) return NRD_ESTATE;
   if (!x || !y || !out) return fail(c, NRD_EINVAL, "null argument");
   launch_wdot(c->H, c->R, x, y, 1, s);
   cudaMemcpyAsync(c->R.h_res + 1, c->R.d_res + 1, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -490,36 +511,58 @@ int nrd_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd
   return solver_newton(c, u, b, a0, dt, st, s);
 }
 
-int nrd_step(nrd_ctx* c, double* u, const double* u_n, const double* u_nm1, double dt,
-             double dt_prev, nrd_stats* st, cudaStream_t s) {
-  if (!c) return NRD_EINVAL;
+// checks and the history combination of a step:
+// b = (1+alpha) u_n - alpha^2/(1+alpha) u_{n-1}, a0 = (1+2 alpha)/(1+alpha)
+// (Eq. bdf2); backward Euler (Eq. be): b = u_n, a0 = 1.
+static int step_prepare(nrd_ctx* c, double* u, const double* u_n, const double* u_nm1,
+                        double dt, double dt_prev, double* a0, cudaStream_t s) {
   int rc = need_ready(c);
   if (rc) return rc;
   if (!u || !u_n) return fail(c, NRD_EINVAL, "null argument");
   if (!(dt > 0.0)) return fail(c, NRD_EINVAL, "dt must be positive");
+  if (u_nm1 && !(dt_prev > 0.0)) return fail(c, NRD_EINVAL, "dt_prev must be positive for BDF2");
   rc = solver_alloc(c);
   if (rc != NRD_OK) return rc;
   const int n2 = 2 * c->H.N;
-  double a0;
-  // b = (1+alpha) u_n - alpha^2/(1+alpha) u_{n-1}, a0 = (1+2 alpha)/(1+alpha)
-  // (Eq. bdf2); backward Euler (Eq. be): b = u_n, a0 = 1.
   cudaMemcpyAsync(c->d_b, u_n, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
   if (u_nm1) {
-    if (!(dt_prev > 0.0)) return fail(c, NRD_EINVAL, "dt_prev must be positive for BDF2");
-    double al = dt / dt_prev;
-    a0 = (1.0 + 2.0 * al) / (1.0 + al);
+    const double al = dt / dt_prev;
+    *a0 = (1.0 + 2.0 * al) / (1.0 + al);
     launch_axpy(n2, al, u_n, c->d_b, s);                       // (1 + al) u_n
     launch_axpy(n2, -al * al / (1.0 + al), u_nm1, c->d_b, s);
   } else {
-    a0 = 1.0;
+    *a0 = 1.0;
   }
+  return NRD_OK;
+}
+
+int nrd_step(nrd_ctx* c, double* u, const double* u_n, const double* u_nm1, double dt,
+             double dt_prev, nrd_stats* st, cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  double a0 = 1.0;
+  const int rc = step_prepare(c, u, u_n, u_nm1, dt, dt_prev, &a0, s);
+  if (rc) return rc;
   return solver_newton(c, u, c->d_b, a0, dt, st, s);
+}
+
+int nrd_step_begin(nrd_ctx* c, double* u, const double* u_n, const double* u_nm1, double dt,
+                   double dt_prev, cudaStream_t s) {
+  if (!c) return NRD_EINVAL;
+  double a0 = 1.0;
+  const int rc = step_prepare(c, u, u_n, u_nm1, dt, dt_prev, &a0, s);
+  if (rc) return rc;
+  return solver_newton_begin(c, u, c->d_b, a0, dt, s);
+}
+
+int nrd_step_end(nrd_ctx* c, nrd_stats* st) {
+  if (!c) return NRD_EINVAL;
+  return solver_newton_end(c, st);
 }
 
 int nrd_tag(nrd_ctx* c, const double* u, double thr_c, double thr_g, double thr_r, uint8_t* tags,
             cudaStream_t s) {
   if (!c) return NRD_EINVAL;
-  int rc = need_ready(c);
+  int rc = need_ready(c, true, s);
   if (rc) return rc;
   if (!u || !tags) return fail(c, NRD_EINVAL, "null argument");
   Hier& H = c->H;
@@ -672,6 +715,7 @@ int nrd_autotune_sweeps(nrd_ctx* c, const double* u_n, const double* u_nm1, doub
 
 int nrd_timing_enable(nrd_ctx* c, int enable) {
   if (!c) return NRD_EINVAL;
+  if (step_pending_check(c, false, nullptr)) return NRD_ESTATE;
   c->timer.on = enable != 0;
   c->timer.reset();
   return NRD_OK;

@@ -73,6 +73,7 @@ int nrd_time_derivative(nrd_ctx* c, const double* u_np1, const double* u_n, cons
                         double dt, double dt_prev, double* udot, cudaStream_t s) {
   if (!c) return NRD_EINVAL;
   if (!c->have_hier) { c->err = "no hierarchy"; return NRD_ESTATE; }
+  if (step_pending_check(c, true, s)) return NRD_ESTATE;
   if (!u_np1 || !u_n || !udot || !(dt > 0.0)) { c->err = "bad argument"; return NRD_EINVAL; }
   double a0 = 1.0, c1 = 1.0, c2 = 0.0;
   if (u_nm1) {
@@ -91,6 +92,7 @@ int nrd_predict(nrd_ctx* c, const double* u_n, const double* u_nm1, const double
                 double dt, double dt_prev, double* u_p, cudaStream_t s) {
   if (!c) return NRD_EINVAL;
   if (!c->have_hier) { c->err = "no hierarchy"; return NRD_ESTATE; }
+  if (step_pending_check(c, true, s)) return NRD_ESTATE;
   if (!u_n || !u_nm1 || !udot_n || !u_p || !(dt > 0.0) || !(dt_prev > 0.0)) {
     c->err = "bad argument";
     return NRD_EINVAL;
@@ -104,6 +106,7 @@ int nrd_lte(nrd_ctx* c, const double* u_np1, const double* u_p, double alpha, do
             double eta_T, double* err_host, cudaStream_t s) {
   if (!c) return NRD_EINVAL;
   if (!c->have_hier) { c->err = "no hierarchy"; return NRD_ESTATE; }
+  if (step_pending_check(c, true, s)) return NRD_ESTATE;
   if (!u_np1 || !u_p || !err_host || !(alpha >= 0.0)) { c->err = "bad argument"; return NRD_EINVAL; }
   const double coef = (alpha + 1.0) / (3.0 * alpha + 2.0);
   const int nb = c->R.nblk;

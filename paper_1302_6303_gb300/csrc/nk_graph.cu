@@ -591,6 +591,15 @@ void nk_graph_free(nrd_ctx* c) {
 
 int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
                    cudaStream_t s) {
+  const int rc = nk_graph_launch(c, u, b, a0, dt, s);
+  if (rc != NRD_OK) return rc;
+  return nk_graph_collect(c, st, s);
+}
+
+// Enqueue the whole Newton solve (graph, result copy, control read-back) on
+// s without waiting for it.
+int nk_graph_launch(nrd_ctx* c, double* u, const double* b, double a0, double dt,
+                    cudaStream_t s) {
   int rc = solver_alloc(c);
   if (rc != NRD_OK) return rc;
   if (c->kry_m > NVMAXG - 1) {
@@ -652,6 +661,13 @@ int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt,
   }
   cudaMemcpyAsync(u, G->uw, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
   cudaMemcpyAsync(G->h_ctl, G->ctl, sizeof(NkCtl), cudaMemcpyDeviceToHost, s);
+  return NRD_OK;
+}
+
+// Wait for the solve nk_graph_launch enqueued on s and report it.
+int nk_graph_collect(nrd_ctx* c, nrd_stats* st, cudaStream_t s) {
+  NkGraph* G = c->nk;
+  if (!G) return NRD_ESTATE;
   if (cudaStreamSynchronize(s) != cudaSuccess) {
     c->err = "Newton graph execution failed";
     return NRD_ECUDA;

@@ -332,6 +332,12 @@ struct nrd_ctx {
   // Newton solve captured as one CUDA graph (nk_graph.cu)
   struct NkGraph* nk = nullptr;
   unsigned gen = 0;            // bumped whenever captured state may change
+  // a step begun by nrd_step_begin and not yet ended: 0 none, 1 the Newton
+  // graph in flight on pend_s, 2 finished by the host-driven loop
+  int pend = 0;
+  cudaStream_t pend_s = nullptr;
+  int pend_rc = 0;
+  nrd_stats pend_st{};
   std::string err;
 };
 
@@ -346,6 +352,19 @@ void solver_free(nrd_ctx* c);
 // (analytic Jv form, timing off).  Same contract as solver_newton.
 int nk_graph_solve(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
                    cudaStream_t s);
+// the same in two halves: enqueue without waiting, then wait and report
+int nk_graph_launch(nrd_ctx* c, double* u, const double* b, double a0, double dt,
+                    cudaStream_t s);
+int nk_graph_collect(nrd_ctx* c, nrd_stats* st, cudaStream_t s);
+// solver_newton in two halves (nrd_step_begin / nrd_step_end): the graph
+// form is enqueued and collected later; the host-driven loop runs to the end
+// in the first half and keeps its result for the second
+int solver_newton_begin(nrd_ctx* c, double* u, const double* b, double a0, double dt,
+                        cudaStream_t s);
+int solver_newton_end(nrd_ctx* c, nrd_stats* st);
+// capi.cu: NRD_OK when no step is pending, or when pending_ok and s is the
+// stream of the pending step; otherwise NRD_ESTATE with the context's error set
+int step_pending_check(nrd_ctx* c, bool pending_ok, cudaStream_t s);
 void nk_graph_free(nrd_ctx* c);
 // capi.cu helpers used by the solver
 // par: optional device [a0, dt, beta] read instead of a0, dt (graph-captured

@@ -222,6 +222,7 @@ int nrd_regrid_boxes(nrd_ctx* c, const uint8_t* tags, int tag_bits, int buffer,
     c->err = "no hierarchy";
     return NRD_ESTATE;
   }
+  if (step_pending_check(c, false, nullptr)) return NRD_ESTATE;
   if (!tags || !nlevels_out || !nboxes_out || !boxes_out || !total_out || buffer < 0 ||
       !(efficiency > 0.0 && efficiency <= 1.0) || min_side < 2 || max_side < min_side ||
       (min_side % 2) || (max_side % 2) || max_levels < 1 || max_levels > NRD_MAX_LEVELS ||
@@ -332,6 +333,8 @@ int nrd_transfer(nrd_ctx* src, nrd_ctx* dst, const double* u_src, double* u_dst,
     dst->err = "both contexts need a hierarchy";
     return NRD_ESTATE;
   }
+  if (step_pending_check(src, false, nullptr) || step_pending_check(dst, false, nullptr))
+    return NRD_ESTATE;
   if (!u_src || !u_dst || nvec < 1) {
     dst->err = "bad argument to nrd_transfer";
     return NRD_EINVAL;

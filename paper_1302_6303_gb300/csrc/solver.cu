@@ -139,18 +139,52 @@ int solver_alloc(nrd_ctx* c) {
 static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0, double dt,
                               nrd_stats* st, cudaStream_t s);
 
+static bool use_graph(const nrd_ctx* c) {
+  return c->p.graph && c->p.jv_mode == NRD_JV_ANALYTIC && !c->timer.on && c->p.restart < 32;
+}
+
 int solver_newton(nrd_ctx* c, double* u, const double* b, double a0, double dt, nrd_stats* st,
                   cudaStream_t s) {
-  if (c->p.graph && c->p.jv_mode == NRD_JV_ANALYTIC && !c->timer.on && c->p.restart < 32) {
+  const int rc = solver_newton_begin(c, u, b, a0, dt, s);
+  if (rc != NRD_OK) {
+    c->pend = 0;
+    return rc;
+  }
+  return solver_newton_end(c, st);
+}
+
+int solver_newton_begin(nrd_ctx* c, double* u, const double* b, double a0, double dt,
+                        cudaStream_t s) {
+  if (use_graph(c)) {
     int rc = solver_alloc(c);
     if (rc != NRD_OK) return rc;
     // the graph reads the history from the context's own buffer
     if (b != c->d_b)
       cudaMemcpyAsync(c->d_b, b, 2 * (size_t)c->H.N * sizeof(double), cudaMemcpyDeviceToDevice,
                       s);
-    return nk_graph_solve(c, u, c->d_b, a0, dt, st, s);
+    rc = nk_graph_launch(c, u, c->d_b, a0, dt, s);
+    if (rc != NRD_OK) return rc;
+    c->pend = 1;
+    c->pend_s = s;
+    return NRD_OK;
   }
-  return solver_newton_host(c, u, b, a0, dt, st, s);
+  c->pend_st = nrd_stats{};
+  c->pend_rc = solver_newton_host(c, u, b, a0, dt, &c->pend_st, s);
+  c->pend = 2;
+  c->pend_s = s;
+  return NRD_OK;
+}
+
+int solver_newton_end(nrd_ctx* c, nrd_stats* st) {
+  const int pend = c->pend;
+  c->pend = 0;
+  if (pend == 1) return nk_graph_collect(c, st, c->pend_s);
+  if (pend == 2) {
+    if (st) *st = c->pend_st;
+    return c->pend_rc;
+  }
+  c->err = "no step pending";
+  return NRD_ESTATE;
 }
 
 void solver_free(nrd_ctx* c) {

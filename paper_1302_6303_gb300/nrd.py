@@ -27,7 +27,7 @@ EXPORTED = [
     "nrd_params_default", "nrd_create", "nrd_destroy", "nrd_last_error", "nrd_set_params",
     "nrd_set_hierarchy", "nrd_layout", "nrd_set_material", "nrd_ghost_fill", "nrd_residual",
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
-    "nrd_step", "nrd_tag", "nrd_regrid_boxes", "nrd_transfer", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
+    "nrd_step", "nrd_step_begin", "nrd_step_end", "nrd_tag", "nrd_regrid_boxes", "nrd_transfer", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
     "nrd_autotune", "nrd_autotune_sweeps", "nrd_wdot_noalloc", "nrd_measure_peaks",
     "nrd_check_fastmath", "nrd_check_narrow",
     "nrd_timing_enable",
@@ -103,6 +103,8 @@ def load(path: str = _LIBPATH):
         "nrd_precond_apply": (c_int, [vp, dp, dp, vp]),
         "nrd_newton": (c_int, [vp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
         "nrd_step": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, P(Stats), vp]),
+        "nrd_step_begin": (c_int, [vp, dp, dp, dp, c_dbl, c_dbl, vp]),
+        "nrd_step_end": (c_int, [vp, P(Stats)]),
         "nrd_tag": (c_int, [vp, dp, c_dbl, c_dbl, c_dbl, vp, vp]),
         "nrd_regrid_boxes": (c_int, [vp, vp, c_int, c_int, c_dbl, c_int, c_int, c_int, c_int,
                                      P(c_int), P(c_int), P(c_int), P(c_int)]),
@@ -338,6 +340,21 @@ class Context:
         st = Stats()
         rc = self.lib.nrd_step(self._h, _ptr(u, torch.float64), _ptr(u_n, torch.float64),
                                _ptr(u_nm1, torch.float64), dt, dt_prev, ctypes.byref(st), _stream())
+        if check and rc != OK:
+            self._check(rc)
+        return st.as_dict()
+
+    def step_begin(self, u, u_n, u_nm1, dt, dt_prev=0.0):
+        """Enqueue one implicit step on the current stream without waiting
+        (nrd_step_begin); finish it with step_end()."""
+        self._check(self.lib.nrd_step_begin(self._h, _ptr(u, torch.float64),
+                                            _ptr(u_n, torch.float64), _ptr(u_nm1, torch.float64),
+                                            dt, dt_prev, _stream()))
+
+    def step_end(self, check=True):
+        """Wait for the step begun by step_begin(); its stats (nrd_step_end)."""
+        st = Stats()
+        rc = self.lib.nrd_step_end(self._h, ctypes.byref(st))
         if check and rc != OK:
             self._check(rc)
         return st.as_dict()
