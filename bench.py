@@ -290,7 +290,7 @@ def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
     total, kry = 0.0, 0
     h2d = d2h = 0
     side = torch.cuda.Stream()
-    stepped, copied = torch.cuda.Event(), torch.cuda.Event()
+    stepped, derived, copied = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
     for s in range(warmup + nsteps):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -314,11 +314,15 @@ def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
         with torch.cuda.stream(side):
             side.wait_event(stepped)
             hout.copy_(d_u, non_blocking=True)
-            copied.record()
         ctx.time_derivative(d_u, d_n, d_nm1 if hnm1 is not None else None, DT,
                             DT if hnm1 is not None else 0.0, out=d_dot_out)
+        # and so does the time derivative while the indicators run
+        derived.record()
+        with torch.cuda.stream(side):
+            side.wait_event(derived)
+            hdot_out.copy_(d_dot_out, non_blocking=True)
+            copied.record()
         t = ctx.tag(d_u, thr_r=0.1)
-        hdot_out.copy_(d_dot_out, non_blocking=True)
         htag.copy_(t, non_blocking=True)
         torch.cuda.current_stream().wait_event(copied)
         ev1.record()
