@@ -45,10 +45,10 @@ WORKLOAD = "amr2_base64_marshak_band"
 # per cell (balance, coupling and its partials, P2 data).  Derivation in the
 # design notes.
 LIN_INST_PER_CELL = 3 * 45 + 34
-# DRAM bytes per launch of that kernel from the committed ncu capture of the
-# same kernel version (profiles/k_stencil_lin_amr2_base64.md), or None when
-# the kernel changed since.
-LIN_TRAFFIC_BYTES = 25.11e6 + 45.89e6
+# DRAM bytes per linearisation (its face and cell launches) from the committed
+# ncu capture of the same kernel version (profiles/k_stencil_lin_amr2_base64.md),
+# or None when the kernels changed since.
+LIN_TRAFFIC_BYTES = (16.44e6 + 50.96e6) + (47.82e6 + 2.15e6)   # face launch + cell launch
 JV_TRAFFIC_BYTES = 83.17e6 + 12.98e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
@@ -522,12 +522,13 @@ def main():
     # FP64 pipe issue rate: the measured FP64 FMA rate in instructions
     # (one FMA = one instruction = 2 flops)
     fp64_peak = rates["fp64_tflops"] * 1e3 / 2.0
-    roof = {"kernel": "k_stencil<ST_LIN> (residual + linearisation, FP64)", "bound": "alu",
+    roof = {"kernel": "k_stencil<ST_LINF> + k_stencil<ST_LINC> (residual + linearisation, "
+                      "FP64: every face once, then the cells)", "bound": "alu",
             "achieved": ach, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
             "frac": ach / fp64_peak, "traffic": LIN_TRAFFIC_BYTES,
             "per_launch_us": t_lin * 1e6, "launches": lin_n,
-            "timing": "CUDA events around each launch in an instrumented repeat of the timed "
-                      "steps",
+            "timing": "CUDA events around each linearisation (its face and cell launches) in "
+                      "an instrumented repeat of the timed steps",
             "peak_source": "FP64 FMA rate measured in this run by nrd_measure_peaks, in "
                            "instructions (2 per clock per SM x 152 SMs x clock; no FP64 figure "
                            "in MEASURED_PEAKS.json)",

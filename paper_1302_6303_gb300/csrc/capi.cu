@@ -82,11 +82,11 @@ void set_model(nrd_ctx* c) {
 
 void free_fields(nrd_ctx* c) {
   auto F = [](void* p) { if (p) cudaFree(p); };
-  F(c->d_z); F(c->d_gz); F(c->d_gu); F(c->d_gv); F(c->d_cf); F(c->d_tmp); F(c->d_jc); F(c->d_cc);
+  F(c->d_z); F(c->d_gz); F(c->d_gu); F(c->d_gv); F(c->d_cf); F(c->d_tmp); F(c->d_jc); F(c->d_pef); F(c->d_cc);
   F(c->d_lam); F(c->d_gam); F(c->d_z3);
   c->d_z3 = nullptr;
   c->d_z = nullptr; c->d_gz = nullptr; c->d_gu = nullptr; c->d_gv = nullptr; c->d_cf = nullptr;
-  c->d_tmp = nullptr; c->d_jc = nullptr; c->d_cc = nullptr; c->d_lam = nullptr; c->d_gam = nullptr;
+  c->d_tmp = nullptr; c->d_jc = nullptr; c->d_pef = nullptr; c->d_cc = nullptr; c->d_lam = nullptr; c->d_gam = nullptr;
   c->lin_ready = false;
   reducer_free(c->R);
   if (c->pc) pc_free(c->pc);
@@ -136,6 +136,7 @@ int ctx_linearise(nrd_ctx* c, const double* u, const double* b, double a0, doubl
   io.par = par;
   pc_lin_targets(c->pc, &io.a32, &io.a64, &io.p2, &io.p2f);
   c->timer.begin(NRD_TK_LINEARISE, s);
+  io.pef = with_dz ? nullptr : c->d_pef;   // the split form (every face once)
   launch_stencil(H, c->mp, c->d_z, c->d_gz, with_dz ? ST_LINZ : ST_LIN, io, s, c->d_z3);
   c->timer.end(NRD_TK_LINEARISE, s);
   launch_reflux(H, io, ST_RESIDUAL, s);
@@ -324,6 +325,7 @@ int nrd_set_hierarchy(nrd_ctx* c, int nlevels, const int* nboxes, const int* box
             cudaMalloc(&c->d_cf, 2 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_tmp, 2 * N * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_jc, 6 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&c->d_pef, 2 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_cc, 3 * N * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_lam, 2 * (3 * N + G) * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&c->d_gam, 3 * (G ? G : 1) * sizeof(double)) == cudaSuccess &&

@@ -335,6 +335,56 @@ __device__ __forceinline__ void put_scaled(const StencilIO& io, long NS, long sl
   }
 }
 
+// The linearisation's cell outputs (shared by the fused and the split form):
+// F from cell_balance, the coupling partials and the P2 data.
+template <bool DZ>
+__device__ __forceinline__ void lin_cell(const StencilIO& io, int N, int idx, double a0v,
+                                         double dtv, double betav, float betaf, double E,
+                                         double T, double z, double divE, double divT) {
+  const double T2 = T * T, T3 = T2 * T;
+  double FE, FT, rT, sig;
+  cell_balance(a0v, dtv, E, T, z, io.b[idx], io.b[N + idx], divE, divT, FE, FT, rT, sig);
+  io.out[idx] = FE;
+  io.out[N + idx] = FT;
+  // coupling tangent dc = cE vE + cT vT
+  io.cc[idx] = -sig;
+  io.cc[N + idx] = sig * fma(3.0 * E, rT, T3);
+  if (DZ) io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
+  // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
+  // (det = (1 + sb)(1 + sbt) - sbt sb = 1 + sb + sbt), in the
+  // preconditioner's precision
+  if (io.p2f) {
+    const float sb = narrow_rn(sig) * betaf, sbt = sb * narrow_rn(T3);
+    io.p2f[idx] = sb;
+    io.p2f[N + idx] = sbt;
+    io.p2f[2L * N + idx] = 1.0f / (1.0f + sb + sbt);
+  } else {
+    const double sb = sig * betav, sbt = sb * T3;
+    io.p2[idx] = sb;
+    io.p2[N + idx] = sbt;
+    io.p2[2L * N + idx] = rcp_nr(1.0 + sb + sbt);
+  }
+}
+
+// covered cell: not an unknown
+template <bool DZ>
+__device__ __forceinline__ void lin_cell_covered(const StencilIO& io, int N, int idx) {
+  io.out[idx] = 0.0;
+  io.out[N + idx] = 0.0;
+  io.cc[idx] = 0.0;
+  io.cc[N + idx] = 0.0;
+  if (DZ) io.cc[2L * N + idx] = 0.0;
+  if (io.p2f) {
+    io.p2f[idx] = 0.0f;
+    io.p2f[N + idx] = 0.0f;
+    io.p2f[2L * N + idx] = 0.0f;
+  } else {
+    io.p2[idx] = 0.0;
+    io.p2[N + idx] = 0.0;
+    io.p2[2L * N + idx] = 0.0;
+  }
+}
+
 template <int MODE, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
@@ -342,7 +392,9 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int NFX = (TX + 1) * TY * TZ, NFY = TX * (TY + 1) * TZ, NFZ = TX * TY * (TZ + 1);
   constexpr int NC = TX * TY * TZ;
   constexpr bool TAN = (MODE == ST_JV);
-  constexpr bool LIN = (MODE == ST_LIN || MODE == ST_LINZ);
+  constexpr bool LINF = (MODE == ST_LINF);     // the split linearisation's face launch
+  constexpr bool LINC = (MODE == ST_LINC);     // and its cell launch
+  constexpr bool LIN = (MODE == ST_LIN || MODE == ST_LINZ || LINF);   // writes the face data
   constexpr bool DZ = (MODE == ST_LINZ);       // also the d/dz^3 partials
   constexpr bool JVF = (MODE == ST_JVF);       // frozen-Jacobian Jv: sE, sT hold v
   extern __shared__ double smem[];
@@ -397,6 +449,48 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         int idx = P.off + i + nx * (j + ny * k);
         io.out[idx] = 0.0;
         io.out[N + idx] = 0.0;
+      }
+      continue;
+    }
+    if (LINC) {
+      // the split linearisation's cell launch: the face fluxes come from pef
+      // (written by the face launch, each face once), the divergence is
+      // formed in the fused kernel's order, so F is bit-identical to it
+      const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
+      const double* pE = io.pef;
+      const double* pT = io.pef + NS;
+      for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+        const int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
+        const int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
+        if (i >= nx || j >= ny || k >= tile.k1) continue;
+        const int idx = P.off + i + nx * (j + ny * k);
+        const uint8_t m = A.mask[idx];
+        if (m & MASK_COVERED) {
+          lin_cell_covered<false>(io, N, idx);
+          continue;
+        }
+        // face slots: interior faces at dir N + (low-side cell), patch faces at
+        // 3N + their ghost index
+        auto gslot = [&](int ff, int a, int b) {
+          return 3L * N + P.goff + P.fo[ff] + a + P.n[((ff >> 1) + 1) % 3] * b;
+        };
+        const long xl = (i == 0) ? gslot(0, j, k) : (long)idx;
+        const long xh = (i == nx - 1) ? gslot(1, j, k) : (long)idx + 1;
+        const long yl = (j == 0) ? gslot(2, k, i) : (long)N + idx;
+        const long yh = (j == ny - 1) ? gslot(3, k, i) : (long)N + idx + nx;
+        const long zl = (k == 0) ? gslot(4, i, j) : 2L * N + idx;
+        const long zh = (k == nz - 1) ? gslot(5, i, j) : 2L * N + idx + (long)nx * ny;
+        auto pick = [](bool skip, double v) { return skip ? 0.0 : v; };
+        const double divE = (pick(m & 4, pE[xh]) - pick(m & 2, pE[xl])) * rhx +
+                            (pick(m & 16, pE[yh]) - pick(m & 8, pE[yl])) * rhy +
+                            (pick(m & 64, pE[zh]) - pick(m & 32, pE[zl])) * rhz;
+        const double divT = (pick(m & 4, pT[xh]) - pick(m & 2, pT[xl])) * rhx +
+                            (pick(m & 16, pT[yh]) - pick(m & 8, pT[yl])) * rhy +
+                            (pick(m & 64, pT[zh]) - pick(m & 32, pT[zl])) * rhz;
+        const double E = io.u[idx], T = io.u[N + idx];
+        const double z = A.z3 ? A.z3[idx] : (double)A.z[idx];
+        lin_cell<false>(io, N, idx, a0v, dtv, betav, betaf, E, T, A.z3 ? z : z * z * z, divE,
+                        divT);
       }
       continue;
     }
@@ -465,12 +559,35 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
     }
     __syncthreads();
-    // ---- face fluxes, each computed once
-    for (int f = threadIdx.x; f < NFX + NFY + NFZ; f += blockDim.x) {
-      int dir, fi, fj, fk, slot;
-      double* outE;
-      double* outT;
-      if (f < NFX) {
+    // ---- face fluxes, each computed once per tile (LINF: once in the launch:
+    // the low faces of the tile's cells, and the patch's high boundary faces
+    // where the tile ends the patch, enumerated without gaps so that whole
+    // warps skip what is not there)
+    const int tzl = tile.k1 - tile.k0;
+    const int nlow = LINF ? TX * TY * tzl : 0;
+    const int nbx = (LINF && tile.i0 + TX == nx) ? TY * tzl : 0;
+    const int nby = (LINF && tile.j0 + TY == ny) ? TX * tzl : 0;
+    const int nbz = (LINF && tile.k1 == nz) ? TX * TY : 0;
+    const int nfaces = LINF ? 3 * nlow + nbx + nby + nbz : NFX + NFY + NFZ;
+    for (int f = threadIdx.x; f < nfaces; f += blockDim.x) {
+      int dir, fi, fj, fk, slot = 0;
+      double* outE = nullptr;
+      double* outT = nullptr;
+      if (LINF) {
+        int q = f;
+        if (q < 3 * nlow) {
+          dir = q / nlow;
+          q -= dir * nlow;
+          fi = q % TX; fj = (q / TX) % TY; fk = q / (TX * TY);
+        } else if ((q -= 3 * nlow) < nbx) {
+          dir = 0; fi = TX; fj = q % TY; fk = q / TY;
+        } else if ((q -= nbx) < nby) {
+          dir = 1; fj = TY; fi = q % TX; fk = q / TX;
+        } else {
+          q -= nby;
+          dir = 2; fk = tzl; fi = q % TX; fj = q / TX;
+        }
+      } else if (f < NFX) {
         dir = 0; slot = f;
         fi = f % (TX + 1); fj = (f / (TX + 1)) % TY; fk = f / ((TX + 1) * TY);
         outE = fxE; outT = fxT;
@@ -595,10 +712,16 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.cfflux[G + gi] = PT;
         }
       }
-      outE[slot] = PE;
-      outT[slot] = PT;
+      if (LINF) {
+        io.pef[fslot] = PE;
+        io.pef[NS + fslot] = PT;
+      } else {
+        outE[slot] = PE;
+        outT[slot] = PT;
+      }
     }
     __syncthreads();
+    if (LINF) continue;   // the cell launch forms the balance
     // ---- cell balance
     const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
     for (int c = threadIdx.x; c < NC; c += blockDim.x) {
@@ -608,21 +731,11 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       int idx = P.off + i + nx * (j + ny * k);
       uint8_t m = A.mask[idx];
       if (m & MASK_COVERED) {
-        io.out[idx] = 0.0;
-        io.out[N + idx] = 0.0;
         if (LIN) {
-          io.cc[idx] = 0.0;
-          io.cc[N + idx] = 0.0;
-          if (DZ) io.cc[2L * N + idx] = 0.0;
-          if (io.p2f) {
-            io.p2f[idx] = 0.0f;
-            io.p2f[N + idx] = 0.0f;
-            io.p2f[2L * N + idx] = 0.0f;
-          } else {
-            io.p2[idx] = 0.0;
-            io.p2[N + idx] = 0.0;
-            io.p2[2L * N + idx] = 0.0;
-          }
+          lin_cell_covered<DZ>(io, N, idx);
+        } else {
+          io.out[idx] = 0.0;
+          io.out[N + idx] = 0.0;
         }
         continue;
       }
@@ -652,28 +765,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         io.out[idx] = a0v * vE - dtv * (divE + dc);
         io.out[N + idx] = a0v * vT - dtv * (divT - dc);
       } else if (LIN) {
-        double FE, FT, rT, sig;
-        cell_balance(a0v, dtv, E, T, z, io.b[idx], io.b[N + idx], divE, divT, FE, FT, rT, sig);
-        io.out[idx] = FE;
-        io.out[N + idx] = FT;
-        // coupling tangent dc = cE vE + cT vT
-        io.cc[idx] = -sig;
-        io.cc[N + idx] = sig * fma(3.0 * E, rT, T3);
-        if (DZ) io.cc[2L * N + idx] = (T2 * T2 - E) * rT * rT * rT;   // d coupling / d z^3
-        // P2 of Sec. 4.2 at this iterate: [[1 + sb, -sbt], [-sb, 1 + sbt]]
-        // (det = (1 + sb)(1 + sbt) - sbt sb = 1 + sb + sbt), in the
-        // preconditioner's precision
-        if (io.p2f) {
-          const float sb = narrow_rn(sig) * betaf, sbt = sb * narrow_rn(T3);
-          io.p2f[idx] = sb;
-          io.p2f[N + idx] = sbt;
-          io.p2f[2L * N + idx] = 1.0f / (1.0f + sb + sbt);
-        } else {
-          const double sb = sig * betav, sbt = sb * T3;
-          io.p2[idx] = sb;
-          io.p2[N + idx] = sbt;
-          io.p2[2L * N + idx] = rcp_nr(1.0 + sb + sbt);
-        }
+        lin_cell<DZ>(io, N, idx, a0v, dtv, betav, betaf, E, T, z, divE, divT);
       } else {
         double FE, FT, rT, sig;
         cell_balance(a0v, dtv, E, T, z, io.b[idx], io.b[N + idx], divE, divT, FE, FT, rT, sig);
@@ -898,6 +990,7 @@ LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
 
 template <int MODE, int TX, int TY, int TZ>
 size_t stencil_smem() {
+  if (MODE == ST_LINC) return 0;   // reads its cells and faces from global memory
   constexpr int NH = (TX + 2) * (TY + 2) * (TZ + 2);
   constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
   size_t d = (size_t)NH * (MODE == ST_JV ? 5 : (MODE == ST_JVF ? 2 : 3)) + 2 * (size_t)NF;
@@ -993,7 +1086,10 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   a.io = io;
   if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);
-  else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else if (mode == ST_LIN && io.pef) {
+    dispatch_tile<ST_LINF>(a, H.tile_x, H.tile_y, H.tile_z, s);
+    dispatch_tile<ST_LINC>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  } else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_LINZ) dispatch_tile<ST_LINZ>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JVF) dispatch_tile<ST_JVF>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else dispatch_tile<ST_FD>(a, H.tile_x, H.tile_y, H.tile_z, s);
