@@ -110,6 +110,7 @@ int ctx_residual(nrd_ctx* c, const double* u, const double* b, double a0, double
   io.par = par;
   io.out = F;
   io.cfflux = c->d_cf;
+  io.pef = c->d_pef;   // the split form (every face once)
   c->timer.begin(NRD_TK_RESIDUAL, s);
   launch_stencil(H, c->mp, c->d_z, c->d_gz, ST_RESIDUAL, io, s, c->d_z3);
   c->timer.end(NRD_TK_RESIDUAL, s);

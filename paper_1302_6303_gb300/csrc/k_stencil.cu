@@ -394,6 +394,8 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr bool TAN = (MODE == ST_JV);
   constexpr bool LINF = (MODE == ST_LINF);     // the split linearisation's face launch
   constexpr bool LINC = (MODE == ST_LINC);     // and its cell launch
+  constexpr bool FACES = LINF || MODE == ST_RESF;   // split forms: faces only
+  constexpr bool CELLS = LINC || MODE == ST_RESC;   // split forms: cells only
   constexpr bool LIN = (MODE == ST_LIN || MODE == ST_LINZ || LINF);   // writes the face data
   constexpr bool DZ = (MODE == ST_LINZ);       // also the d/dz^3 partials
   constexpr bool JVF = (MODE == ST_JVF);       // frozen-Jacobian Jv: sE, sT hold v
@@ -452,10 +454,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
       continue;
     }
-    if (LINC) {
-      // the split linearisation's cell launch: the face fluxes come from pef
-      // (written by the face launch, each face once), the divergence is
-      // formed in the fused kernel's order, so F is bit-identical to it
+    if (CELLS) {
+      // the split forms' cell launch: the face fluxes come from pef (written
+      // by the face launch, each face once), the divergence is formed in the
+      // fused kernel's order, so F is bit-identical to it
       const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
       const double* pE = io.pef;
       const double* pT = io.pef + NS;
@@ -466,7 +468,12 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         const int idx = P.off + i + nx * (j + ny * k);
         const uint8_t m = A.mask[idx];
         if (m & MASK_COVERED) {
-          lin_cell_covered<false>(io, N, idx);
+          if (LINC) {
+            lin_cell_covered<false>(io, N, idx);
+          } else {
+            io.out[idx] = 0.0;
+            io.out[N + idx] = 0.0;
+          }
           continue;
         }
         // face slots: interior faces at dir N + (low-side cell), patch faces at
@@ -489,8 +496,16 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
                             (pick(m & 64, pT[zh]) - pick(m & 32, pT[zl])) * rhz;
         const double E = io.u[idx], T = io.u[N + idx];
         const double z = A.z3 ? A.z3[idx] : (double)A.z[idx];
-        lin_cell<false>(io, N, idx, a0v, dtv, betav, betaf, E, T, A.z3 ? z : z * z * z, divE,
-                        divT);
+        const double z3c = A.z3 ? z : z * z * z;
+        if (LINC) {
+          lin_cell<false>(io, N, idx, a0v, dtv, betav, betaf, E, T, z3c, divE, divT);
+        } else {
+          double FE, FT, rT, sig;
+          cell_balance(a0v, dtv, E, T, z3c, io.b[idx], io.b[N + idx], divE, divT, FE, FT, rT,
+                       sig);
+          io.out[idx] = FE;
+          io.out[N + idx] = FT;
+        }
       }
       continue;
     }
@@ -559,21 +574,21 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
     }
     __syncthreads();
-    // ---- face fluxes, each computed once per tile (LINF: once in the launch:
+    // ---- face fluxes, each computed once per tile (split forms: once in the launch:
     // the low faces of the tile's cells, and the patch's high boundary faces
     // where the tile ends the patch, enumerated without gaps so that whole
     // warps skip what is not there)
     const int tzl = tile.k1 - tile.k0;
-    const int nlow = LINF ? TX * TY * tzl : 0;
-    const int nbx = (LINF && tile.i0 + TX == nx) ? TY * tzl : 0;
-    const int nby = (LINF && tile.j0 + TY == ny) ? TX * tzl : 0;
-    const int nbz = (LINF && tile.k1 == nz) ? TX * TY : 0;
-    const int nfaces = LINF ? 3 * nlow + nbx + nby + nbz : NFX + NFY + NFZ;
+    const int nlow = FACES ? TX * TY * tzl : 0;
+    const int nbx = (FACES && tile.i0 + TX == nx) ? TY * tzl : 0;
+    const int nby = (FACES && tile.j0 + TY == ny) ? TX * tzl : 0;
+    const int nbz = (FACES && tile.k1 == nz) ? TX * TY : 0;
+    const int nfaces = FACES ? 3 * nlow + nbx + nby + nbz : NFX + NFY + NFZ;
     for (int f = threadIdx.x; f < nfaces; f += blockDim.x) {
       int dir, fi, fj, fk, slot = 0;
       double* outE = nullptr;
       double* outT = nullptr;
-      if (LINF) {
+      if (FACES) {
         int q = f;
         if (q < 3 * nlow) {
           dir = q / nlow;
@@ -712,7 +727,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           io.cfflux[G + gi] = PT;
         }
       }
-      if (LINF) {
+      if (FACES) {
         io.pef[fslot] = PE;
         io.pef[NS + fslot] = PT;
       } else {
@@ -721,7 +736,7 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       }
     }
     __syncthreads();
-    if (LINF) continue;   // the cell launch forms the balance
+    if (FACES) continue;   // the cell launch forms the balance
     // ---- cell balance
     const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
     for (int c = threadIdx.x; c < NC; c += blockDim.x) {
@@ -990,7 +1005,7 @@ LevelH level_h(const Hier& H, double k = 0.01, double beta = 0.0) {
 
 template <int MODE, int TX, int TY, int TZ>
 size_t stencil_smem() {
-  if (MODE == ST_LINC) return 0;   // reads its cells and faces from global memory
+  if (MODE == ST_LINC || MODE == ST_RESC) return 0;   // cells and faces from global memory
   constexpr int NH = (TX + 2) * (TY + 2) * (TZ + 2);
   constexpr int NF = (TX + 1) * TY * TZ + TX * (TY + 1) * TZ + TX * TY * (TZ + 1);
   size_t d = (size_t)NH * (MODE == ST_JV ? 5 : (MODE == ST_JVF ? 2 : 3)) + 2 * (size_t)NF;
@@ -1084,7 +1099,10 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   for (int f = 0; f < 6; f++) a.R[f] = mp.bc_R[f];
   a.lh = level_h(H, mp.k, io.beta);
   a.io = io;
-  if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  if (mode == ST_RESIDUAL && io.pef) {
+    dispatch_tile<ST_RESF>(a, H.tile_x, H.tile_y, H.tile_z, s);
+    dispatch_tile<ST_RESC>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  } else if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_LIN && io.pef) {
     dispatch_tile<ST_LINF>(a, H.tile_x, H.tile_y, H.tile_z, s);

@@ -124,10 +124,10 @@ void hier_free(Hier& H);
 // Kernel launchers (k_stencil.cu)
 // stencil modes; ST_JVF applies the Jacobian frozen by ST_LIN (jc, cc) to v;
 // ST_LINZ is ST_LIN that also forms the partials with respect to z^3
-// ST_LINF / ST_LINC: ST_LIN in two launches, every face once (face fluxes to
-// StencilIO::pef), then the cell balance from them
+// ST_LINF / ST_LINC (ST_RESF / ST_RESC): ST_LIN (ST_RESIDUAL) in two launches,
+// every face once (face fluxes to StencilIO::pef), then the cell balance from them
 enum { ST_RESIDUAL = 0, ST_JV = 1, ST_FD = 2, ST_LIN = 3, ST_JVF = 4, ST_LINZ = 5, ST_LINF = 6,
-       ST_LINC = 7 };
+       ST_LINC = 7, ST_RESF = 8, ST_RESC = 9 };
 struct StencilIO {
   const double* u;      // state (E then T)
   const double* v;      // direction (JV, FD)
@@ -149,7 +149,7 @@ struct StencilIO {
   double* p2;           // [3][N] P2 data (FP64 V-cycle), or
   float* p2f;           //   FP32 (FP32 V-cycle)
   const double* par;    // device [a0, dt, beta] overriding a0, dt, beta (or null)
-  double* pef = nullptr;  // [2][3N+G] face fluxes: ST_LIN runs as ST_LINF + ST_LINC when set
+  double* pef = nullptr;  // [2][3N+G] face fluxes: ST_LIN / ST_RESIDUAL run split when set
 };
 void launch_ghost_fill(const Hier& H, const ModelParams& mp, const float* z, const double* u,
                        double* g, int nonlinear, cudaStream_t s);
