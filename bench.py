@@ -48,7 +48,7 @@ LIN_INST_PER_CELL = 3 * 45 + 34
 # DRAM bytes per linearisation (its face and cell launches) from the committed
 # ncu capture of the same kernel version (profiles/k_stencil_lin_amr2_base64.md),
 # or None when the kernels changed since.
-LIN_TRAFFIC_BYTES = (16.44e6 + 50.96e6) + (47.82e6 + 2.15e6)   # face launch + cell launch
+LIN_TRAFFIC_BYTES = (16.42e6 + 51.09e6) + (47.82e6 + 2.52e6)   # face launch + cell launch
 JV_TRAFFIC_BYTES = 83.17e6 + 12.98e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
