@@ -1,10 +1,19 @@
 #!/usr/bin/env python
 """Benchmark of the implicit radiation-diffusion hot path on one GB300.
 
-Workload: 2-level AMR, base 64^3, refinement ratio 2, fine patches of
-16^3-32^3 cells tiling the Marshak band x < 1/8, z = 10 in 20 seeded cubes of
-side 4-12 base cells on z = 1, E0 = 1e-5, T0 = E0^(1/4), Robin R = 1 at x = 0;
-BDF2 steps (first backward Euler) with dt = 5e-4, Newton rtol 1e-8.
+Workloads (``--workload``; the default is the largest single-GPU one):
+
+* ``single256`` (default): one level of 256^3 cells (16.8M) on the unit cube,
+  z in {1, 5, 10} in 64 seeded cubes of side 8-32 cells, E0 = 1e-5,
+  T0 = E0^(1/4), Robin R = 1 at x = 0, Neumann elsewhere.  FP64 Newton
+  residual, Jv and FGMRES(30) orthogonalisation; FP32 4-level V-cycle with
+  3 red-black Gauss-Seidel sweeps before and after; Newton rtol 1e-8.
+* ``amr2_base64``: 2-level AMR, base 64^3, refinement ratio 2, fine patches
+  of 16^3-32^3 cells tiling the Marshak band x < 1/8, z = 10 in 20 seeded
+  cubes of side 4-12 base cells on z = 1; sweep schedule from the autotuner.
+
+Both: BDF2 steps (the first one backward Euler) with dt = 5e-4 from the
+initial state (Sec. 3.1), Newton rtol 1e-8.
 
 One benchmark step = one implicit time step through the public API: the
 generalised leapfrog predictor as the Newton initial guess (nrd_predict, Eq.
@@ -36,20 +45,36 @@ import numpy as np  # noqa: E402
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
 DT = 5e-4
-WORKLOAD = "amr2_base64_marshak_band"
+
+# The workloads.  `solver` holds the V-cycle schedule where the workload
+# states one (config "3 red-black Gauss-Seidel sweeps": V(3,3) with 2 x 3
+# sweeps on the coarsest grid); None lets the sweep autotuner choose.
+# `cpu_n` is the grid of the bounded oracle sample timed on the host (the
+# same layout scaled), None for the full workload.
+WORKLOADS = {
+    "single256": {
+        "name": "single_level_256cubed_64cubes_z1_5_10",
+        "sizes": "256^3 cells, one level",
+        "solver": dict(nmg=4, nu1=3, nu2=3, coarse_sweeps=6),
+        "regrid": False,
+        "cpu_n": 128,
+    },
+    "amr2_base64": {
+        "name": "amr2_base64_marshak_band",
+        "sizes": "base 64^3 + 31 fine patches of 16^3-32^3 cells",
+        "solver": None,
+        "regrid": True,
+        "cpu_n": None,
+    },
+}
+
 # Algorithmic work per leaf cell of the linearisation stencil, in FP64-pipe
 # instructions (the unit that bounds it on GB300, which issues 2 FP64
 # instructions per clock per SM): 3 faces x 45 (face flux, its 5 partials and
 # the two P1 coefficients incl. the refined reciprocal and reciprocal square
 # root; the FP32 narrowing of the coefficients runs on the integer pipe) + 34
-# per cell (balance, coupling and its partials, P2 data).  Derivation in the
-# design notes.
+# per cell (balance, coupling and its partials, P2 data).
 LIN_INST_PER_CELL = 3 * 45 + 34
-# DRAM bytes per linearisation (its face and cell launches) from the committed
-# ncu capture of the same kernel version (profiles/k_stencil_lin_amr2_base64.md),
-# or None when the kernels changed since.
-LIN_TRAFFIC_BYTES = (16.42e6 + 51.09e6) + (47.82e6 + 2.52e6)   # face launch + cell launch
-JV_TRAFFIC_BYTES = 83.17e6 + 12.98e6
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
@@ -57,6 +82,12 @@ JV_BYTES_PER_CELL = 169.0
 # GB300: 3 faces x 6 (the two tangent fluxes from the five partials) + 20 per
 # cell (two divergences, the coupling tangent, a0 v - dt (...) for both fields)
 JV_INST_PER_CELL = 3 * 6 + 20
+# DRAM bytes per launch group from an ncu capture of the current kernels,
+# per workload (None: not captured for this kernel version and workload)
+TRAFFIC = {
+    "amr2_base64": {"linearise": None, "jv": None},
+    "single256": {"linearise": None, "jv": None},
+}
 
 
 def parse():
@@ -65,19 +96,21 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="single256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-regrid", action="store_true", help="skip the regrid/transfer leg")
     ap.add_argument("--profile", action="store_true",
                     help="short run for profilers: 1 warm-up + 2 production steps, fixed "
-                         "8x8x4 tiles and V(1,1)/2 sweeps, no plain/CPU/e2e legs; the "
+                         "8x8x4 tiles, the workload's sweep schedule (V(1,1)/2 where the "
+                         "autotuner would choose), no plain/CPU/e2e legs; the "
                          "Newton loop runs host-driven so that a profiler sees every kernel "
                          "as its own launch (--profile-graph keeps the graph form)")
     ap.add_argument("--profile-graph", action="store_true")
     ap.add_argument("--profile-pc", type=int, default=0, metavar="N",
                     help="short run for profilers: N preconditioner applies (cached graph) "
-                         "on the bench workload after one set-up, 8x8x4 tiles, V(1,1)/2 "
-                         "red-black sweeps; prints the mean time per apply")
+                         "on the workload after one set-up, 8x8x4 tiles, the workload's "
+                         "schedule (else V(1,1)/2); prints the mean time per apply")
     return ap.parse_args()
 
 
@@ -86,10 +119,11 @@ def profile_run(args):
     import __graft_entry__ as g
     g.build()
     from paper_1302_6303_gb300 import nrd
-    h, z, u0 = workload()
-    ctx = make_ctx(nrd, h, z, torch, production=True)
-    ctx.set_params(tile_x=8, tile_y=8, tile_z=4, nu1=1, nu2=1, coarse_sweeps=2,
-                   graph=1 if args.profile_graph else 0)
+    h, z, u0 = workload(args.workload)
+    ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=4, graph=1 if args.profile_graph else 0)
+    if WORKLOADS[args.workload]["solver"] is None:
+        ctx.set_params(nu1=1, nu2=1, coarse_sweeps=2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     r = run_steps(ctx, torch, u0, 2, 1, flush, timing=False)
     print(json.dumps({"profile_run": True, "ms": r["ms"], "krylov": r["krylov"]}))
@@ -101,9 +135,11 @@ def profile_pc_run(args):
     import __graft_entry__ as g
     g.build()
     from paper_1302_6303_gb300 import nrd
-    h, z, u0 = workload()
-    ctx = make_ctx(nrd, h, z, torch, production=True)
-    ctx.set_params(tile_x=8, tile_y=8, tile_z=4, nu1=1, nu2=1, coarse_sweeps=2)
+    h, z, u0 = workload(args.workload)
+    ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=4)
+    if WORKLOADS[args.workload]["solver"] is None:
+        ctx.set_params(nu1=1, nu2=1, coarse_sweeps=2)
     u = torch.from_numpy(u0).cuda()
     ctx.precond_setup(u, 1.0, DT)
     w = torch.from_numpy(np.random.default_rng(5).standard_normal(u0.size)).cuda()
@@ -134,9 +170,14 @@ def replicas_value(dist, world, units, ms, device):
     return world * units / (ms * 1e-3) / 1e6, ms
 
 
-def workload():
+def workload(key, n=None):
+    """Hierarchy, material and initial state of workload `key` (`n`: the
+    base grid of a scaled copy, for the host sample)."""
     from paper_1302_6303_gb300 import workloads as W
-    h, z = W.config_amr2(64, seed=0)
+    if key == "single256":
+        h, z = W.config_256(n or 256, seed=0)
+    else:
+        h, z = W.config_amr2(n or 64, seed=0)
     return h, z, W.initial_state(h)
 
 
@@ -201,12 +242,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def make_ctx(nrd, h, z, torch, production):
+def make_ctx(nrd, h, z, torch, production, wl=None):
     if production:
         p = dict(jv_mode=nrd.JV_ANALYTIC, pc_precision=nrd.PC_F32)
     else:
         p = dict(jv_mode=nrd.JV_FD, pc_precision=nrd.PC_F64)
-    ctx = nrd.Context(nu1=2, nu2=2, nmg=4, coarse_sweeps=4, restart=30, rtol=1e-8, **p)
+    sv = dict(nu1=2, nu2=2, nmg=4, coarse_sweeps=4)
+    if wl is not None and wl["solver"] is not None:
+        sv.update(wl["solver"])
+    ctx = nrd.Context(restart=30, rtol=1e-8, **sv, **p)
     ctx.set_hierarchy_from(h)
     ctx.set_material(torch.from_numpy(z).cuda())
     return ctx
@@ -358,7 +402,8 @@ def regrid_leg(nrd, ctx, torch, h, z, r):
     cluster_ms = (time.perf_counter() - t0) * 1e3
     nh = W.Hierarchy(n0=h.n0, levels=levels, bc_type=h.bc_type, bc_R=h.bc_R)
     _, cubes = W.config_amr2_cubes(h.n0[0], seed=0)
-    cn = make_ctx(nrd, nh, W.material_from_cubes(nh, cubes), torch, production=True)
+    cn = make_ctx(nrd, nh, W.material_from_cubes(nh, cubes), torch, production=True,
+                  wl=WORKLOADS["amr2_base64"])
     cn.set_params(tile_x=ctx.params.tile_x, tile_y=ctx.params.tile_y, tile_z=ctx.params.tile_z,
                   nu1=ctx.params.nu1, nu2=ctx.params.nu2, coarse_sweeps=ctx.params.coarse_sweeps,
                   smoother=ctx.params.smoother)
@@ -390,43 +435,111 @@ def regrid_leg(nrd, ctx, torch, h, z, r):
             "fnorm_resolved": st["fnorm"]}
 
 
-def cpu_baseline(h, z, u0, leaf, sweeps=(1, 1, 2, 0), its=18):
-    """The oracle as it stands, on the host: preconditioner set-up, then `its`
-    Krylov iterations' worth of P^{-1} and Jv on the full workload (about 10 s
-    of one host core), with the V-cycle schedule and smoother the GPU run
-    uses (sweeps = (nu1, nu2, coarse sweeps, smoother))."""
-    from oracle.oracle import Oracle, JV_ANALYTIC
+def host_cpu():
+    """Host core count and CPU model (nproc, lscpu)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_krylov_rate(h, z, u0, sweeps, threads, budget_s, min_its=2):
+    """The oracle as it stands, on `threads` host threads: preconditioner
+    set-up, then Krylov iterations' worth of P^{-1} (FAC/GMG) and analytic Jv
+    until `budget_s` seconds have passed (at least `min_its`), with the
+    V-cycle schedule and smoother the GPU run uses (sweeps = (nu1, nu2,
+    coarse sweeps, smoother)).  Returns (Mcell/s, iterations, seconds)."""
+    from oracle.oracle import Oracle, JV_ANALYTIC, set_threads
+    set_threads(threads)
     o = Oracle(h, z)
     o.set_solver(jv_mode=JV_ANALYTIC, nu1=int(sweeps[0]), nu2=int(sweeps[1]), nmg=4,
                  coarse_sweeps=int(sweeps[2]))
     if len(sweeps) > 3 and int(sweeps[3]) == 1:   # damped Jacobi
         o.set_smoother(1, 6.0 / 7.0)
+    leaf = int(o.leaf_mask().sum())
     rng = np.random.default_rng(0)
     w = rng.standard_normal(u0.size)
     o.pc_setup(u0, 1.0, DT)
+    its = 0
     t0 = time.perf_counter()
-    for _ in range(its):
+    while its < min_its or time.perf_counter() - t0 < budget_s:
         y = o.pc_apply(w)
         w = o.jv_analytic(u0, y, 1.0, DT)
         w /= np.sqrt(max(o.dot(w, w), 1e-300))
+        its += 1
     dt = time.perf_counter() - t0
-    return {"value": leaf * its / dt / 1e6, "unit": "Mcell/s", "cores": 1, "kind": "oracle",
-            "sample": "%d Krylov iterations (P^-1 FAC/GMG apply + analytic Jv) of the FP64 "
-                      "oracle on the full workload (%d leaf cells), single thread" % (its, leaf),
-            "seconds": dt}
+    return leaf * its / dt / 1e6, its, dt, leaf
+
+
+def oracle_step_seconds(h, z, u0, sweeps, threads):
+    """Seconds of one oracle implicit step (backward Euler from u0, the
+    GPU schedule, analytic Jv, rtol 1e-8) on `threads` host threads."""
+    from oracle.oracle import Oracle, JV_ANALYTIC, set_threads
+    set_threads(threads)
+    o = Oracle(h, z)
+    o.set_solver(jv_mode=JV_ANALYTIC, nu1=int(sweeps[0]), nu2=int(sweeps[1]), nmg=4,
+                 coarse_sweeps=int(sweeps[2]), rtol=1e-8)
+    if len(sweeps) > 3 and int(sweeps[3]) == 1:
+        o.set_smoother(1, 6.0 / 7.0)
+    t0 = time.perf_counter()
+    _, st = o.newton(u0.copy(), u0.copy(), 1.0, DT)
+    return time.perf_counter() - t0, st
+
+
+def cpu_baseline(key, sweeps):
+    """The oracle timed on the host cores, single thread and all cores: Jv +
+    V-cycle Mcell/s on a bounded sample of the workload (the full workload,
+    or the same layout at a smaller grid), and the seconds of one implicit
+    step on the 64^3 version of the layout."""
+    from paper_1302_6303_gb300 import workloads as W  # noqa: F401
+    wl = WORKLOADS[key]
+    h, z, u0 = workload(key, wl["cpu_n"])
+    cores, model = host_cpu()
+    v1, it1, s1, leaf = oracle_krylov_rate(h, z, u0, sweeps, 1, 8.0)
+    vn, itn, sn, _ = oracle_krylov_rate(h, z, u0, sweeps, cores, 8.0)
+    hs, zs, us = workload(key, 64 if key == "single256" else 16)
+    step_s, st = oracle_step_seconds(hs, zs, us, sweeps, cores)
+    where = ("the full workload" if wl["cpu_n"] is None
+             else "the %d^3 version of the layout" % wl["cpu_n"])
+    return {"value": vn, "unit": "Mcell/s", "cores": cores, "kind": "oracle",
+            "sample": "Krylov iterations (P^-1 FAC/GMG apply + analytic Jv) of the FP64 oracle "
+                      "on %s (%d leaf cells): %d iterations in %.1f s on %d threads; "
+                      "single thread %.3f Mcell/s (%d iterations in %.1f s)"
+                      % (where, leaf, itn, sn, cores, v1, it1, s1),
+            "single_thread": {"value": v1, "unit": "Mcell/s", "iterations": it1, "seconds": s1},
+            "cpu_model": model, "nproc": cores,
+            "step": {"seconds": step_s, "threads": cores,
+                     "workload": "one backward-Euler step of the same layout at base %d^3 "
+                                 "(%d cells) from the initial state"
+                                 % (hs.n0[0], hs.ncells),
+                     "newton_its": st["newton_its"], "krylov_its": st["krylov_its"]}}
 
 
 def reference_arm(args):
     """The oracle timed as the reference arm: each step = one Krylov iteration
-    (P^{-1} + Jv) of the oracle on the full workload, host cores."""
+    (P^{-1} + Jv) of the oracle on all host cores, on the workload, or for
+    the 256^3 workload on its 128^3 version (a bounded sample: the metric is
+    per cell)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    h, z, u0 = workload()
-    from oracle.oracle import Oracle, JV_ANALYTIC
+    key = args.workload
+    wl = WORKLOADS[key]
+    h, z, u0 = workload(key, wl["cpu_n"])
+    from oracle.oracle import Oracle, JV_ANALYTIC, set_threads
+    cores, model = host_cpu()
+    set_threads(cores)
     o = Oracle(h, z)
-    # the V-cycle schedule the GPU bench's autotuner picks on this workload
-    o.set_solver(jv_mode=JV_ANALYTIC, nu1=1, nu2=1, nmg=4, coarse_sweeps=2)
+    sv = wl["solver"] or dict(nu1=1, nu2=1, coarse_sweeps=2)
+    # the GPU run's V-cycle schedule (the autotuner's pick where it chooses)
+    o.set_solver(jv_mode=JV_ANALYTIC, nu1=sv["nu1"], nu2=sv["nu2"], nmg=4,
+                 coarse_sweeps=sv["coarse_sweeps"])
     leaf = int(o.leaf_mask().sum())
     o.pc_setup(u0, 1.0, DT)
     rng = np.random.default_rng(0)
@@ -442,20 +555,38 @@ def reference_arm(args):
             times.append(t1 - t0)
     tot = sum(times)
     val = leaf * args.steps / tot / 1e6
+    sample = ("one FP64 oracle Krylov iteration (FAC/GMG P^-1 + analytic Jv) per step on %s "
+              "(%d leaf cells), %d host threads"
+              % ("the full workload" if wl["cpu_n"] is None
+                 else "the %d^3 version of the layout" % wl["cpu_n"], leaf, cores))
     line = {
         "impl": "reference", "metric": "Mcell/s of Jv+V-cycle", "value": val, "unit": "Mcell/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "leaf_cells": leaf, "step": "one Krylov iteration"},
-        "cpu_baseline": {"value": val, "unit": "Mcell/s", "cores": 1, "kind": "oracle",
-                         "sample": "one FP64 oracle Krylov iteration (FAC/GMG P^-1 + analytic "
-                                   "Jv) per step on the full workload, single thread"},
+        "config": {"workload": wl["name"], "sample_leaf_cells": leaf,
+                   "step": "one Krylov iteration"},
+        "cpu_baseline": {"value": val, "unit": "Mcell/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu_model": model},
         "e2e": {"value": val, "unit": "Mcell/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
     return 0
+
+
+def vcycle_bytes_per_cell(h, sweeps):
+    """Algorithmic DRAM bytes of one FP32 V-cycle apply per leaf cell, both
+    fields: per red-black sweep of a level (the two colours fused, perfect
+    neighbour reuse) the 3 face-coefficient arrays, e read and written and
+    the rhs, 4 B each: 24 B per cell and field; per level visit the residual
+    (e, rhs, 3 coefficients, r written: 24 B), restriction (r read, coarse rhs
+    written: 4.5 B) and prolongation (coarse e, e read and written: 8.5 B);
+    the coarser levels add 1/8 each; the FP64 input (16 B), the P2 data
+    (12 B: three FP32 values) and the FP64 output (16 B) once."""
+    nu = int(sweeps[0]) + int(sweeps[1])
+    per_field = 24.0 * nu + 24.0 + 4.5 + 8.5
+    return 2 * per_field * 8.0 / 7.0 + 16 + 12 + 16
 
 
 def main():
@@ -485,15 +616,22 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    h, z, u0 = workload()
+    key = args.workload
+    wl = WORKLOADS[key]
+    h, z, u0 = workload(key)
     rates = nrd.measure_peaks()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    ctx = make_ctx(nrd, h, z, torch, production=True)
+    ctx = make_ctx(nrd, h, z, torch, production=True, wl=wl)
     leaf = ctx.nleaf
-    # autotuner: stencil tile shape for this hierarchy (untimed set-up)
+    # autotuners: stencil tile shape for this hierarchy, and the smoother
+    # schedule where the workload does not state one (untimed set-up)
     u_t = torch.from_numpy(u0).cuda()
     tile, _ = ctx.autotune(u_t, u_t, 1.0, DT)
-    sweeps, _ = ctx.autotune_sweeps(u_t, None, DT)
+    if wl["solver"] is None:
+        sweeps, _ = ctx.autotune_sweeps(u_t, None, DT)
+    else:
+        sv = wl["solver"]
+        sweeps = (sv["nu1"], sv["nu2"], sv["coarse_sweeps"], nrd.SMOOTH_RBGS)
     del u_t
 
     # production form, timed (replicas: every rank runs the same workload):
@@ -510,52 +648,65 @@ def main():
     rk = run_steps(ctx, torch, u0, args.steps, args.warmup, flush, timing=True)
     value, tot_ms = replicas_value(dist, world, leaf * r["krylov"], sum(r["ms"]), "cuda")
 
-    # roofline of the dominant single kernel: the FP64 linearisation stencil
-    # (residual + Jacobian partials + frozen P1/P2 data), measured live with
-    # CUDA events around each of its launches in the timed region
+    # rooflines, measured live with CUDA events around each launch group in
+    # the instrumented repeat of the timed steps
     kt = rk["kernel"]
     hbm_peak, peak_src = peaks()
-    lin_ms, lin_n = kt["linearise"]
-    jv_ms, jv_n = kt["jv"]
-    t_lin = lin_ms / max(lin_n, 1) * 1e-3
-    ach = LIN_INST_PER_CELL * leaf / t_lin / 1e9
     # FP64 pipe issue rate: the measured FP64 FMA rate in instructions
     # (one FMA = one instruction = 2 flops)
     fp64_peak = rates["fp64_tflops"] * 1e3 / 2.0
+    fp64_src = ("FP64 FMA rate measured in this run by nrd_measure_peaks, in instructions "
+                "(2 per clock per SM x 152 SMs x clock; MEASURED_PEAKS.json has no FP64 figure)")
+    traffic = TRAFFIC.get(key, {})
+    lin_ms, lin_n = kt["linearise"]
+    t_lin = lin_ms / max(lin_n, 1) * 1e-3
+    ach = LIN_INST_PER_CELL * leaf / t_lin / 1e9
     roof = {"kernel": "k_stencil<ST_LINF> + k_stencil<ST_LINC> (residual + linearisation, "
                       "FP64: every face once, then the cells)", "bound": "alu",
             "achieved": ach, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
-            "frac": ach / fp64_peak, "traffic": LIN_TRAFFIC_BYTES,
+            "frac": ach / fp64_peak, "traffic": traffic.get("linearise"),
             "per_launch_us": t_lin * 1e6, "launches": lin_n,
             "timing": "CUDA events around each linearisation (its face and cell launches) in "
                       "an instrumented repeat of the timed steps",
-            "peak_source": "FP64 FMA rate measured in this run by nrd_measure_peaks, in "
-                           "instructions (2 per clock per SM x 152 SMs x clock; no FP64 figure "
-                           "in MEASURED_PEAKS.json)",
+            "peak_source": fp64_src,
             "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
                            % (LIN_INST_PER_CELL, leaf)}
+    jv_ms, jv_n = kt["jv"]
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
     ach_jv = JV_INST_PER_CELL * leaf / t_jv / 1e9
     gbs_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
     roof_jv = {"kernel": "k_stencil<ST_JVF> (frozen-Jacobian Jv)", "bound": "alu",
                "achieved": ach_jv, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
-               "frac": ach_jv / fp64_peak, "traffic": JV_TRAFFIC_BYTES,
-               "per_launch_us": t_jv * 1e6,
+               "frac": ach_jv / fp64_peak, "traffic": traffic.get("jv"),
+               "per_launch_us": t_jv * 1e6, "launches": jv_n,
                "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
                               % (JV_INST_PER_CELL, leaf),
                "hbm": {"achieved": gbs_jv, "peak": hbm_peak, "unit": "GB/s",
                        "frac": gbs_jv / hbm_peak, "peak_source": peak_src,
                        "algorithmic": "%d B per leaf cell" % JV_BYTES_PER_CELL}}
+    pc_ms, pc_n = kt["pc_apply"]
+    t_pc = pc_ms / max(pc_n, 1) * 1e-3
+    vb = vcycle_bytes_per_cell(h, sweeps)
+    gbs_pc = vb * leaf / t_pc / 1e9
+    roof_pc = {"kernel": "V-cycle apply (FP32 FAC/GMG, every kernel of one P^-1 apply)",
+               "bound": "hbm", "achieved": gbs_pc, "peak": hbm_peak, "unit": "GB/s",
+               "frac": gbs_pc / hbm_peak, "per_launch_us": t_pc * 1e6, "launches": pc_n,
+               "peak_source": peak_src,
+               "algorithmic": "%.0f B per leaf cell (fused red-black sweeps, both fields, "
+                              "all levels) x %d leaf cells" % (vb, leaf)}
 
     # plain form beside it
     plain = None
     if not args.no_plain:
-        ctxp = make_ctx(nrd, h, z, torch, production=False)
+        ctxp = make_ctx(nrd, h, z, torch, production=False, wl=wl)
         ctxp.set_params(tile_x=tile[0], tile_y=tile[1], tile_z=tile[2], nu1=sweeps[0],
                         nu2=sweeps[1], coarse_sweeps=sweeps[2], smoother=sweeps[3])
         rp = run_steps(ctxp, torch, u0, args.steps, args.warmup, flush, timing=False)
         pms = sum(rp["ms"])
-        plain = {"form": "FD Jv + FP64 V-cycle", "ms_per_step": pms / args.steps,
+        plain = {"form": "FD Jv + FP64 V-cycle, Newton loop driven from the host (no "
+                         "graphs); the same batched tile kernels (one launch per sweep over "
+                         "all patches), not per-patch launches",
+                 "ms_per_step": pms / args.steps,
                  "value": leaf * rp["krylov"] / (pms * 1e-3) / 1e6,
                  "krylov_per_step": rp["krylov"] / args.steps,
                  "newton_per_step": rp["newton"] / args.steps}
@@ -568,12 +719,12 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     regrid = None
-    if not args.no_regrid:
+    if not args.no_regrid and wl["regrid"]:
         regrid = regrid_leg(nrd, ctx, torch, h, z, r)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(h, z, u0, leaf, sweeps)
+        cpu = cpu_baseline(key, sweeps)
 
     # kernels executed in the timed region: the Newton graph's kernel nodes
     # times the iterations of their loops (counted by the library), plus the
@@ -588,17 +739,23 @@ def main():
                     "max": max(r["ms"])},
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "base": 64, "levels": 2, "leaf_cells": leaf,
+        "config": {"workload": wl["name"], "sizes": wl["sizes"], "base": h.n0[0],
+                   "levels": h.nlevels, "leaf_cells": leaf,
                    "patches": sum(h.nboxes), "dt": DT, "newton_rtol": 1e-8,
                    "form": "analytic Jv + FP32 FAC/GMG V-cycle + FGMRES(30)",
                    "tile": list(tile), "sweeps_nu1_nu2_coarse": list(sweeps[:3]),
+                   "sweeps_from": "autotuner" if wl["solver"] is None else "workload",
+                   "gmg_levels": 4,
                    "smoother": "jacobi" if sweeps[3] == nrd.SMOOTH_JACOBI else "rbgs",
                    "krylov_per_step": r["krylov"] / args.steps,
                    "newton_per_step": r["newton"] / args.steps,
-                   "l2": "256 MB buffer written between timed steps",
+                   "l2": "256 MB buffer written between timed steps" + (
+                       "; every state vector (%d MB) is larger than L2" % (16 * ctx.N >> 20)
+                       if 16 * ctx.N > 129e6 else ""),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roof,
         "roofline_jv": roof_jv,
+        "roofline_vcycle": roof_pc,
         "measured_rates": rates,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
         "plain": plain,

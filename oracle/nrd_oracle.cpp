@@ -71,6 +71,21 @@
 #include <string>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+// Threads: built with OpenMP, the loops over cells whose iterations are
+// independent (every cell written by exactly one iteration, reading only
+// values no iteration of the same loop writes: the residual and its tangent
+// per cell, one colour of a red-black pass, a Jacobi sweep into a second
+// array, restriction, prolongation, averaging, the frozen-coefficient
+// set-up) run on several threads.  Each result is the same expression in
+// the same order as on one thread, so results are bit-identical for any
+// thread count.  Sums over cells (the inner products) stay serial, in cell
+// order.
+#define ORC_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+
 namespace {
 
 enum { BC_NEUMANN = 0, BC_ROBIN = 1 };
@@ -353,6 +368,7 @@ void residual_t(const Hier& H, const S* u, const S* z, const double* b, double a
   const long N = H.N;
   const S* E = u;
   const S* T = u + N;
+  ORC_PARALLEL_FOR
   for (long idx = 0; idx < N; idx++) {
     int l = H.cell_level[idx];
     const int* c = &H.cell_ijk[3 * idx];
@@ -555,6 +571,7 @@ void pc_setup(Hier& H, const double* u, double a0, double dt) {
         long nf = (long)fdim(O.n, d, 0) * fdim(O.n, d, 1) * fdim(O.n, d, 2);
         O.C[d].assign(nf, 0.0);
         int t1 = plane_t1(d), t2 = plane_t2(d);
+        ORC_PARALLEL_FOR
         for (int k = 0; k < fdim(O.n, d, 2); k++)
           for (int j = 0; j < fdim(O.n, d, 1); j++)
             for (int i = 0; i < fdim(O.n, d, 0); i++) {
@@ -647,6 +664,7 @@ void pc_setup(Hier& H, const double* u, double a0, double dt) {
         int t1 = plane_t1(d), t2 = plane_t2(d);
         long nf = (long)fdim(O.n, d, 0) * fdim(O.n, d, 1) * fdim(O.n, d, 2);
         O.C[d].assign(nf, 0.0);
+        ORC_PARALLEL_FOR
         for (int k = 0; k < fdim(O.n, d, 2); k++)
           for (int j = 0; j < fdim(O.n, d, 1); j++)
             for (int i = 0; i < fdim(O.n, d, 0); i++) {
@@ -750,6 +768,7 @@ void level_row(const Grid& G, const std::vector<double>& e, const int c[3], doub
 
 void level_apply(const Grid& G, const std::vector<double>& e, std::vector<double>& y) {
   y.assign(G.ncell(), 0.0);
+  ORC_PARALLEL_FOR
   for (int k = 0; k < G.O->n[2]; k++)
     for (int j = 0; j < G.O->n[1]; j++)
       for (int i = 0; i < G.O->n[0]; i++) {
@@ -767,6 +786,7 @@ void rbgs(const Grid& G, std::vector<double>& e, const std::vector<double>& f, i
   for (int sw = 0; sw < sweeps; sw++)
     for (int pass = 0; pass < 2; pass++) {
       int colour = red_first ? pass : 1 - pass;
+      ORC_PARALLEL_FOR
       for (int k = 0; k < G.O->n[2]; k++)
         for (int j = 0; j < G.O->n[1]; j++)
           for (int i = 0; i < G.O->n[0]; i++) {
@@ -788,6 +808,7 @@ void jacobi(const Grid& G, std::vector<double>& e, const std::vector<double>& f,
   std::vector<double> en;
   for (int sw = 0; sw < sweeps; sw++) {
     en = e;
+    ORC_PARALLEL_FOR
     for (int k = 0; k < G.O->n[2]; k++)
       for (int j = 0; j < G.O->n[1]; j++)
         for (int i = 0; i < G.O->n[0]; i++) {
@@ -841,6 +862,7 @@ void gmg_vcycle(const Hier& H, int fld, int m, std::vector<double>& e, const std
   const Hier::OpLevel& Oc = H.mg[fld][m + 1];
   Grid Gc{&H, &Oc, fld};
   std::vector<double> fc(Gc.ncell(), 0.0), ec(Gc.ncell(), 0.0);
+  ORC_PARALLEL_FOR
   for (int k = 0; k < Oc.n[2]; k++)
     for (int j = 0; j < Oc.n[1]; j++)
       for (int i = 0; i < Oc.n[0]; i++) {
@@ -855,6 +877,7 @@ void gmg_vcycle(const Hier& H, int fld, int m, std::vector<double>& e, const std
         fc[Gc.di(cc)] = s / 8.0;
       }
   gmg_vcycle(H, fld, m + 1, ec, fc);
+  ORC_PARALLEL_FOR
   for (int k = 0; k < G.O->n[2]; k++)
     for (int j = 0; j < G.O->n[1]; j++)
       for (int i = 0; i < G.O->n[0]; i++) {
@@ -910,6 +933,7 @@ double comp_flux(const Hier& H, int fld, const double* x, int l, const int c[3],
 
 // y = L^c x for one field (x, y of length N); covered cells get 0.
 void comp_apply(const Hier& H, int fld, const double* x, double* y) {
+  ORC_PARALLEL_FOR
   for (long idx = 0; idx < H.N; idx++) {
     int l = H.cell_level[idx];
     const int* c = &H.cell_ijk[3 * idx];
@@ -924,7 +948,8 @@ void comp_apply(const Hier& H, int fld, const double* x, double* y) {
 
 // Replace covered values by the mean of their children, finest first.
 void average_down(const Hier& H, double* x) {
-  for (int l = H.L - 2; l >= 0; l--)
+  for (int l = H.L - 2; l >= 0; l--) {
+    ORC_PARALLEL_FOR
     for (long idx = 0; idx < H.N; idx++) {
       if (H.cell_level[idx] != l) continue;
       const int* c = &H.cell_ijk[3 * idx];
@@ -936,12 +961,14 @@ void average_down(const Hier& H, double* x) {
             s += x[H.cell(l + 1, 2 * c[0] + a, 2 * c[1] + b, 2 * c[2] + e)];
       x[idx] = s / 8.0;
     }
+  }
 }
 
 // Dense level array <-> hierarchy vector helpers
 void gather_level(const Hier& H, int l, const double* x, std::vector<double>& out) {
   const Level& Lv = H.lev[l];
   out.assign((long)Lv.n[0] * Lv.n[1] * Lv.n[2], 0.0);
+  ORC_PARALLEL_FOR
   for (long idx = 0; idx < H.N; idx++) {
     if (H.cell_level[idx] != l) continue;
     const int* c = &H.cell_ijk[3 * idx];
@@ -958,6 +985,7 @@ void correct_composite(const Hier& H, int l, const std::vector<double>& e, doubl
     if (m > l) {
       const Level& Lc = H.lev[m - 1];
       next.assign((long)Lv.n[0] * Lv.n[1] * Lv.n[2], 0.0);
+      ORC_PARALLEL_FOR
       for (long idx = 0; idx < H.N; idx++) {
         if (H.cell_level[idx] != m) continue;
         const int* q = &H.cell_ijk[3 * idx];
@@ -966,6 +994,7 @@ void correct_composite(const Hier& H, int l, const std::vector<double>& e, doubl
       }
       cur.swap(next);
     }
+    ORC_PARALLEL_FOR
     for (long idx = 0; idx < H.N; idx++) {
       if (H.cell_level[idx] != m) continue;
       const int* c = &H.cell_ijk[3 * idx];
@@ -1018,6 +1047,7 @@ void pc_apply(const Hier& H, const double* w, double* y) {
   fac_vcycle(H, 0, w, zE.data());
   fac_vcycle(H, 1, w + N, zT.data());
   const double beta = H.beta;
+  ORC_PARALLEL_FOR
   for (long i = 0; i < N; i++) {
     if (H.covered_idx(i)) { y[i] = 0.0; y[N + i] = 0.0; continue; }
     double T = H.uk[N + i];
@@ -1275,6 +1305,17 @@ orc_hier* orc_create(int nlevels, const int* nboxes, const int* boxes, const int
 }
 
 void orc_destroy(orc_hier* h) { delete reinterpret_cast<Hier*>(h); }
+
+// Host threads for the cell loops (1 without OpenMP); returns the count used.
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 long orc_ncells(orc_hier* h) { return reinterpret_cast<Hier*>(h)->N; }
 
