@@ -1511,6 +1511,18 @@ void orc_comp_apply(orc_hier* h, int fld, const double* x, double* y) {
   comp_apply(*reinterpret_cast<Hier*>(h), fld, x, y);
 }
 
+// y = the level-l operator of the FAC V-cycle (R9: homogeneous coarse-fine
+// ghosts) applied to x; x and y dense over level l's index space, 0 where
+// the level has no cell.  Needs orc_pc_setup.
+void orc_level_apply(orc_hier* h, int fld, int l, const double* x, double* y) {
+  Hier& H = *reinterpret_cast<Hier*>(h);
+  if (!H.pc_ready || l < 0 || l >= H.L) fatal("orc_level_apply: no set-up or bad level");
+  Grid G{&H, &H.opl[fld][l], fld};
+  std::vector<double> e(x, x + G.ncell()), out;
+  level_apply(G, e, out);
+  std::copy(out.begin(), out.end(), y);
+}
+
 void orc_fac(orc_hier* h, int fld, const double* f, double* u) {
   fac_vcycle(*reinterpret_cast<Hier*>(h), fld, f, u);
 }

@@ -80,6 +80,7 @@ def _load():
         "orc_pc_setup": (None, [vp, _dp, ctypes.c_double, ctypes.c_double]),
         "orc_pc_apply": (None, [vp, _dp, _dp]),
         "orc_comp_apply": (None, [vp, ctypes.c_int, _dp, _dp]),
+        "orc_level_apply": (None, [vp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
         "orc_fac": (None, [vp, ctypes.c_int, _dp, _dp]),
         "orc_gmg": (None, [vp, ctypes.c_int, _dp, _dp]),
         "orc_average_down": (None, [vp, _dp]),
@@ -230,6 +231,15 @@ class Oracle:
     def comp_apply(self, fld, x):
         y = np.empty(self.N)
         _lib.orc_comp_apply(self._h, fld, _d(np.ascontiguousarray(x)), _d(y))
+        return y
+
+    def level_apply(self, fld, lev, x):
+        """The FAC level operator of level `lev` (homogeneous coarse-fine
+        ghosts) on a vector dense over that level's index space."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        assert x.size == int(np.prod(self.hier.level_n(lev)))
+        y = np.empty_like(x)
+        _lib.orc_level_apply(self._h, fld, lev, _d(x), _d(y))
         return y
 
     def fac(self, fld, f):

@@ -361,6 +361,41 @@ def test_linop_constant_on_amr(fld):
     assert np.abs(y[leaf] - 1.0).max() <= 1e-12
 
 
+@pytest.mark.parametrize("fld", [0, 1])
+@pytest.mark.parametrize("box", [((4, 4, 4), (11, 11, 7)), ((0, 4, 2), (7, 11, 9))],
+                         ids=["interior", "robin_face"])
+def test_level_operator_is_composite_with_zero_coarse_data(fld, box):
+    """Algorithm 1's level error equation (reading R9: homogeneous coarse-fine
+    ghosts) is the composite operator of Sec. 3.2.1 with the coarse data set
+    to zero.  With one fine box every coarse value that a coarse-fine ghost
+    interpolates is an uncovered coarse cell, so on every fine cell the level
+    operator applied to x must equal the composite operator applied to x
+    extended by zero on level 0: the ghost is then (1/3) x_f + (2/3) 0.  The
+    fine cells next to the coarse-fine interface pin the level operator's
+    coarse-fine row."""
+    h = W.Hierarchy((8, 8, 8), [[((0, 0, 0), (7, 7, 7))], [box]])
+    o, _ = _setup_pc(h, dt=0.02)
+    L, I, J, K = h.cell_ijk()
+    fine = L == 1
+    rng = np.random.default_rng(11)
+    x = np.zeros(h.ncells)
+    x[fine] = rng.uniform(0.5, 1.5, int(fine.sum()))
+    yc = o.comp_apply(fld, x)
+    n1 = h.level_n(1)
+    di = I[fine] + n1[0] * (J[fine] + n1[1] * K[fine])
+    xd = np.zeros(int(np.prod(n1)))
+    xd[di] = x[fine]
+    yl = o.level_apply(fld, 1, xd)[di]
+    assert np.abs(yl - yc[fine]).max() <= 1e-13 * np.abs(yc[fine]).max()
+    # the coarse-fine rows carry a term of the size being pinned
+    lo, hi = box
+    edge = np.zeros(int(fine.sum()), dtype=bool)
+    for d, idx in enumerate((I[fine], J[fine], K[fine])):
+        edge |= ((idx == lo[d]) & (lo[d] > 0)) | ((idx == hi[d]) & (hi[d] < n1[d] - 1))
+    assert edge.any()
+    assert np.abs(yl[edge] - x[fine][edge]).max() > 1e-3
+
+
 def test_cf_ghost_linear_exact():
     """Linear coarse-fine interpolation (Sec. 3.2.1) reproduces linear fields
     exactly at fine ghost centres; sibling ghosts are exact cell values."""
