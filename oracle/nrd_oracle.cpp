@@ -1554,10 +1554,11 @@ int orc_newton(orc_hier* h, double* u, const double* b, double a0, double dt, in
 }
 
 // Error indicators of Sec. 5 plus the relative gradient h |grad E| / E, on
-// every cell of every level (covered cells use composite values).  Bit 0:
-// tau^c > thr_c; bit 1: tau^g > thr_g; bit 2: h|grad E|/E > thr_r.
-void orc_tag(orc_hier* h, const double* u, double thr_c, double thr_g, double thr_r,
-             unsigned char* tags) {
+// every cell of every level (covered cells use composite values).
+// The three refinement indicators of every cell (Sec. 5; R16): ind[3 idx]
+// = tau^c / (0.1 max|E|), ind[3 idx + 1] = tau^g / (0.1 max|E|),
+// ind[3 idx + 2] = h|grad E| / E, on composite values.
+void orc_tag_values(orc_hier* h, const double* u, double* ind) {
   Hier* H = reinterpret_cast<Hier*>(h);
   const long N = H->N;
   double emax = 0.0;
@@ -1592,10 +1593,24 @@ void orc_tag(orc_hier* h, const double* u, double thr_c, double thr_g, double th
       tg += 0.5 * std::fabs(Ev[1] - Ev[0]);
       gr2 += 0.25 * (Ev[1] - Ev[0]) * (Ev[1] - Ev[0]);
     }
+    ind[3 * idx] = tc / (0.1 * emax);
+    ind[3 * idx + 1] = tg / (0.1 * emax);
+    ind[3 * idx + 2] = std::sqrt(gr2) / Ec;
+  }
+}
+
+// Refinement tags of Sec. 5 from the indicators above, thresholds strict:
+// bit 0 tau^c > thr_c; bit 1 tau^g > thr_g; bit 2 h|grad E|/E > thr_r.
+void orc_tag(orc_hier* h, const double* u, double thr_c, double thr_g, double thr_r,
+             unsigned char* tags) {
+  Hier* H = reinterpret_cast<Hier*>(h);
+  std::vector<double> ind(3 * H->N);
+  orc_tag_values(h, u, ind.data());
+  for (long idx = 0; idx < H->N; idx++) {
     unsigned char t = 0;
-    if (tc / (0.1 * emax) > thr_c) t |= 1;
-    if (tg / (0.1 * emax) > thr_g) t |= 2;
-    if (std::sqrt(gr2) / Ec > thr_r) t |= 4;
+    if (ind[3 * idx] > thr_c) t |= 1;
+    if (ind[3 * idx + 1] > thr_g) t |= 2;
+    if (ind[3 * idx + 2] > thr_r) t |= 4;
     tags[idx] = t;
   }
 }

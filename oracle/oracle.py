@@ -87,6 +87,7 @@ def _load():
         "orc_newton": (ctypes.c_int, [vp, _dp, _dp, ctypes.c_double, ctypes.c_double, _ip, _ip,
                                       _dp, _dp]),
         "orc_tag": (None, [vp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _up]),
+        "orc_tag_values": (None, [vp, _dp, _dp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -266,6 +267,13 @@ class Oracle:
                              ctypes.byref(f0), ctypes.byref(f1))
         return u, dict(status=rc, newton_its=ni.value, krylov_its=ki.value, fnorm0=f0.value,
                        fnorm=f1.value)
+
+    def tag_values(self, u):
+        """Per cell (rows) the indicators tau^c / (0.1 max|E|),
+        tau^g / (0.1 max|E|) and h|grad E|/E that the tags compare."""
+        ind = np.empty(3 * self.N)
+        _lib.orc_tag_values(self._h, _d(np.ascontiguousarray(u)), _d(ind))
+        return ind.reshape(self.N, 3)
 
     def tag(self, u, thr_c=np.inf, thr_g=np.inf, thr_r=np.inf):
         t = np.zeros(self.N, dtype=np.uint8)

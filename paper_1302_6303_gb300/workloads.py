@@ -127,6 +127,33 @@ def all_neumann(h: Hierarchy) -> Hierarchy:
 def material_from_cubes(hier: Hierarchy, cubes, background=1.0):
     """z per cell: the value of the last cube (in base-cell units, half-open
     [lo, lo+side)) containing the cell centre, else the background."""
+    integral = all(float(v).is_integer() for lo, side, _ in cubes
+                   for v in list(lo) + list(side if np.ndim(side) else (side,)))
+    if not integral:
+        return _material_from_centres(hier, cubes, background)
+    # integer cube corners: a level-l cell i (centre (i + 1/2) / 2^l base
+    # cells, never an integer) lies in [lo, lo + side) exactly when
+    # lo 2^l <= i <= (lo + side) 2^l - 1, so each cube is a slice of a patch
+    zval = np.full(hier.ncells, background, dtype=np.float32)
+    for l, lo, hi, off in hier.patches():
+        n = [hi[d] - lo[d] + 1 for d in range(3)]
+        zp = zval[off:off + n[0] * n[1] * n[2]].reshape(n[2], n[1], n[0])
+        r = 1 << l
+        for clo, side, val in cubes:
+            sd = side if np.ndim(side) else (side,) * 3
+            sl = []
+            for d in range(3):
+                a = max(int(clo[d]) * r, lo[d])
+                b = min((int(clo[d]) + int(sd[d])) * r - 1, hi[d])
+                if a > b:
+                    break
+                sl.append(slice(a - lo[d], b - lo[d] + 1))
+            else:
+                zp[sl[2], sl[1], sl[0]] = val
+    return zval
+
+
+def _material_from_centres(hier: Hierarchy, cubes, background=1.0):
     L, x, y, zc = hier.cell_centres()
     nb = np.array(hier.n0, dtype=np.float64)
     zval = np.full(x.size, background, dtype=np.float32)
@@ -327,15 +354,43 @@ def random_nested_level(rng, parent_boxes, n_fine, count, side_lo, side_hi, trie
     return boxes
 
 
-def config_batching(n0=128, seed=0, n1=500, n2=1500, side_lo=8, side_hi=48):
-    """Three levels, base n0^3, ratio 2: about n1 patches on level 1 and n2 on
-    level 2 with sides U{8..48} per axis, non-overlapping per level and
-    properly nested; z = 10 in 64 seeded cubes on z = 1."""
+def tile_region_guillotine(lo, hi, side_lo, side_hi, rng):
+    """Tile the box [lo, hi] (inclusive, even-aligned, even extents) with
+    boxes whose sides lie in [side_lo, side_hi]: seeded slabs along z, each
+    slab cut into seeded rows along y, each row into seeded lengths along x.
+    Each box draws its own x side and shares its y side with its row and its
+    z side with its slab; every side is even, so the boxes align to ratio 2."""
+    boxes = []
+    z0 = lo[2]
+    for sz in split_extent(hi[2] - lo[2] + 1, side_lo, side_hi, rng):
+        y0 = lo[1]
+        for sy in split_extent(hi[1] - lo[1] + 1, side_lo, side_hi, rng):
+            x0 = lo[0]
+            for sx in split_extent(hi[0] - lo[0] + 1, side_lo, side_hi, rng):
+                boxes.append(((x0, y0, z0), (x0 + sx - 1, y0 + sy - 1, z0 + sz - 1)))
+                x0 += sx
+            y0 += sy
+        z0 += sz
+    return boxes
+
+
+def config_batching(n0=128, seed=0, side_lo=8, side_hi=48):
+    """Three levels, base n0^3, ratio 2, patches with sides drawn uniformly
+    (even) from [side_lo, side_hi] per axis.  Level 1 tiles the slab
+    x < 168/256 of the domain (at n0 = 128: 256 x 256 x 168 level-1 cells,
+    about 500 patches); level 2 tiles x < 124/512 of the domain inside it
+    (124 x 512 x 512 level-2 cells, about 1,450 patches), which keeps one
+    level-1 cell between the level-2 region and the level-1 boundary inside
+    the domain (proper nesting).  About 2,000 patches and 44M fine cells at
+    n0 = 128.  z = 10 in 64 seeded cubes of side 4-12 (scaled) base cells on
+    z = 1."""
     rng = np.random.default_rng(seed)
     base = [((0, 0, 0), (n0 - 1,) * 3)]
-    l1 = random_nested_level(rng, base, (2 * n0,) * 3, n1, side_lo, side_hi)
-    # level-2 boxes nest inside single level-1 boxes (in level-1 index space)
-    l2 = random_nested_level(rng, l1, (4 * n0,) * 3, n2, side_lo, side_hi)
+    n1, n2 = 2 * n0, 4 * n0
+    x1 = max(2, 2 * int(round(168 * n1 / 256 / 2)))
+    x2 = max(2, min(2 * (x1 - 1), 2 * int(round(124 * n2 / 512 / 2))))
+    l1 = tile_region_guillotine((0, 0, 0), (x1 - 1, n1 - 1, n1 - 1), side_lo, side_hi, rng)
+    l2 = tile_region_guillotine((0, 0, 0), (x2 - 1, n2 - 1, n2 - 1), side_lo, side_hi, rng)
     h = Hierarchy((n0, n0, n0), [base, l1, l2])
     s_lo, s_hi = max(1, 4 * n0 // 64), max(1, 12 * n0 // 64)
     cubes = random_cubes(rng, h.n0, 64, s_lo, s_hi)
