@@ -111,7 +111,7 @@ typedef struct {
   int coarse_sweeps;   /* smoothing sweeps on the coarsest GMG grid */
   double rtol, atol;   /* Newton stop: ||F|| <= rtol ||F(u0)|| + atol */
   int max_newton;      /* Newton iteration cap */
-  double eta_max;      /* Eisenstat-Walker forcing cap (and eta_0) */
+  double eta_max;      /* Eisenstat-Walker forcing cap */
   double ew_gamma;     /* Eisenstat-Walker gamma */
   int tile_x, tile_y, tile_z;  /* stencil tile shape (0,0,0: 32 x 4 x 4); one of
                                   32x4x4, 32x8x4, 32x4x8, 32x2x4, 16x8x4, 16x4x8,
@@ -126,6 +126,8 @@ typedef struct {
   int smoother;        /* NRD_SMOOTH_RBGS (default) or NRD_SMOOTH_JACOBI, on every AMR
                           level and GMG grid */
   double omega;        /* damping of NRD_SMOOTH_JACOBI, 0 < omega <= 1 (default 6/7) */
+  double eta0;         /* Eisenstat-Walker forcing of the first Newton iteration,
+                          0 < eta0 <= eta_max (default 0.3) */
 } nrd_params;
 
 /* Statistics of one Newton solve (nrd_newton / nrd_step). */

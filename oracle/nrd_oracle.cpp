@@ -28,8 +28,8 @@
 //                          multigrid V-cycle on the coarsest AMR level.
 //   Sec. 5    regridding:  tau^c, tau^g error indicators.
 //
-// Readings where the paper is silent or garbled (each also listed in the
-// design notes):
+// Readings where the paper is silent or garbled (the CUDA path takes the
+// same readings):
 //   R1 limiter: default D_E = D_h/(1 + D_h g) with D_h = 2 D_r (Wilson form of
 //      Sec. 3.1); LIM_PAPER_LITERAL gives the printed 2 D_r/(1 + D_r g).
 //   R2 face D_T = k T_f^(5/2) with the arithmetic face T, not limited.
@@ -42,7 +42,8 @@
 //   R6 differencing parameter: b = 1, |<u,v>| compared, eps_mach = 2^-52,
 //      sign(0) = +1, eps halved (at most 10 times) until u + eps v > 0.
 //   R7 positivity cap: lambda = min(1, 0.9 min_{v_i<0} u_i/|v_i|).
-//   R8 Eisenstat-Walker forcing with eta_max = 0.9, gamma = 0.9, eta_0 = 0.9.
+//   R8 Eisenstat-Walker forcing with eta_max = 0.9, gamma = 0.9 and the
+//      safeguards of Kelley's choice; first forcing eta_0 = 0.3.
 //   R9 FAC: level error equations start from zero with homogeneous
 //      coarse-fine ghosts (coarse value 0); corrections are interpolated to
 //      every finer level; the composite residual is recomputed before every
@@ -159,7 +160,7 @@ struct Hier {
   double omega = 6.0 / 7.0;         // Jacobi damping
   double rtol = 1e-8, atol = 0.0;
   int max_newton = 20;
-  double eta_max = 0.9, ew_gamma = 0.9, u_min = 1e-6;
+  double eta_max = 0.9, ew_gamma = 0.9, eta0 = 0.3, u_min = 1e-6;
 
   // preconditioner state (frozen at the Newton iterate)
   bool pc_ready = false;
@@ -1146,7 +1147,7 @@ int newton(Hier& H, double* u, const double* b, double a0, double dt, Stats* st)
   double fn = std::sqrt(wdot(H, F.data(), F.data()));
   st->fnorm0 = fn;
   double stop = H.rtol * fn + H.atol;
-  double eta = H.eta_max;
+  double eta = H.eta0;
   int it = 0, kits = 0, status = 0;
   while (fn > stop && it < H.max_newton) {
     pc_setup(H, u, a0, dt);

@@ -5,8 +5,8 @@ with the CUDA library.
 
 The paper groups tagged cells into patches with the Berger-Rigoutsos
 algorithm and moves data to the new hierarchy by conservative linear
-refinement, without giving parameters.  The reading followed here (R18-R20
-of the design notes):
+refinement, without giving parameters.  The reading followed here (R18-R20,
+the same on the CUDA side):
 
 R18 clustering, level by level from the coarsest.  Tags of level l are those
     of the current hierarchy; a cell missing there inherits the tag of the

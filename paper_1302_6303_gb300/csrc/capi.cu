@@ -64,6 +64,8 @@ int check_params(const nrd_params* p, std::string& err) {
   if (p->graph != 0 && p->graph != 1) { err = "graph must be 0 or 1"; return NRD_EINVAL; }
   if (p->smoother != NRD_SMOOTH_RBGS && p->smoother != NRD_SMOOTH_JACOBI) { err = "bad smoother"; return NRD_EINVAL; }
   if (!(p->omega > 0.0 && p->omega <= 1.0)) { err = "omega must be in (0, 1]"; return NRD_EINVAL; }
+  if (!(p->eta_max > 0.0 && p->eta_max < 1.0)) { err = "eta_max must be in (0, 1)"; return NRD_EINVAL; }
+  if (!(p->eta0 > 0.0 && p->eta0 <= p->eta_max)) { err = "eta0 must be in (0, eta_max]"; return NRD_EINVAL; }
   bool ok = (p->tile_x == 0 && p->tile_y == 0 && p->tile_z == 0);
   for (int t = 0; t < kNumShapes && !ok; t++)
     ok = (p->tile_x == kShapes[t][0] && p->tile_y == kShapes[t][1] && p->tile_z == kShapes[t][2]);
@@ -231,6 +233,7 @@ int nrd_params_default(nrd_params* p) {
   p->graph = 1;
   p->smoother = NRD_SMOOTH_RBGS;
   p->omega = 6.0 / 7.0;
+  p->eta0 = 0.3;
   return NRD_OK;
 }
 

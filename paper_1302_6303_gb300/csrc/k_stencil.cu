@@ -476,8 +476,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
           }
           continue;
         }
-        // face slots: interior faces at dir N + (low-side cell), patch faces at
-        // 3N + their ghost index
+        // face slots: an interior face at dir N + the index of the cell on its
+        // high side (the face is that cell's low face: cell idx has its low x
+        // face at idx and its high x face at idx + 1); patch faces at 3N +
+        // their ghost index
         auto gslot = [&](int ff, int a, int b) {
           return 3L * N + P.goff + P.fo[ff] + a + P.n[((ff >> 1) + 1) % 3] * b;
         };

@@ -44,7 +44,7 @@ enum { NK_NAN = 1, NK_NEG = 2 };
 struct NkCtl {
   double a0, dt, beta;            // read by the stencil kernels (par)
   double fn, fn0, fold, stop, eta, tol, lam, min_lambda, gres, rn2;
-  double rtol, atol, eta_max, ew_gamma;
+  double rtol, atol, eta_max, ew_gamma, eta0;
   int j, total, it, krylov, flags, ticks;
   int max_newton, max_krylov;
   int cycles, restarts;           // executions of the cycle and restart bodies
@@ -63,8 +63,8 @@ struct SmallG {
 __device__ __forceinline__ bool tick(NkCtl* c) { return ++c->ticks < kMaxTicks; }
 
 __global__ void k_nk_params(NkCtl* c, double a0, double dt, double rtol, double atol,
-                            double eta_max, double ew_gamma, int max_newton, int max_krylov,
-                            double* dbeta) {
+                            double eta_max, double ew_gamma, double eta0, int max_newton,
+                            int max_krylov, double* dbeta) {
   c->a0 = a0;
   c->dt = dt;
   c->beta = dt / a0;
@@ -73,6 +73,7 @@ __global__ void k_nk_params(NkCtl* c, double a0, double dt, double rtol, double 
   c->atol = atol;
   c->eta_max = eta_max;
   c->ew_gamma = ew_gamma;
+  c->eta0 = eta0;
   c->max_newton = max_newton;
   c->max_krylov = max_krylov;
   c->ticks = 0;
@@ -83,7 +84,7 @@ __global__ void k_nk_init(NkCtl* c, const double* res, cudaGraphConditionalHandl
   c->fn = fn;
   c->fn0 = fn;
   c->stop = c->rtol * fn + c->atol;
-  c->eta = c->eta_max;
+  c->eta = c->eta0;
   c->it = 0;
   c->krylov = 0;
   c->cycles = 0;
@@ -654,7 +655,8 @@ int nk_graph_launch(nrd_ctx* c, double* u, const double* b, double a0, double dt
   }
   cudaMemcpyAsync(G->uw, u, n2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
   k_nk_params<<<1, 1, 0, s>>>(G->ctl, a0, dt, c->p.rtol, c->p.atol, c->p.eta_max, c->p.ew_gamma,
-                              c->p.max_newton, c->p.max_krylov, pc_beta_device(c->pc));
+                              c->p.eta0, c->p.max_newton, c->p.max_krylov,
+                              pc_beta_device(c->pc));
   if (cudaGraphLaunch(G->exec, s) != cudaSuccess) {
     c->err = "launch of the Newton graph failed";
     return NRD_ECUDA;

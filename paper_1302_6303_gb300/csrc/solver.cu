@@ -314,7 +314,7 @@ static int solver_newton_host(nrd_ctx* c, double* u, const double* b, double a0,
   }
   loc.fnorm0 = fn;
   const double stop = c->p.rtol * fn + c->p.atol;
-  double eta = c->p.eta_max;
+  double eta = c->p.eta0;
   int it = 0;
   while (fn > stop && it < c->p.max_newton) {
     if (!lin) {

@@ -47,7 +47,7 @@ class Params(ctypes.Structure):
         ("atol", ctypes.c_double), ("max_newton", ctypes.c_int), ("eta_max", ctypes.c_double),
         ("ew_gamma", ctypes.c_double), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
         ("tile_z", ctypes.c_int), ("graph", ctypes.c_int), ("smoother", ctypes.c_int),
-        ("omega", ctypes.c_double),
+        ("omega", ctypes.c_double), ("eta0", ctypes.c_double),
     ]
 
 
