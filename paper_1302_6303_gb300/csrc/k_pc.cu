@@ -99,36 +99,144 @@ __device__ __forceinline__ void box_row(const BoxK<P>& B, const P* A, const P* e
   of = o;
 }
 
-// one colour of a red-black Gauss-Seidel pass on a box; grid (tiles x,
-// tiles y, 2 x tiles z), the upper half of z for field 1.
-// ZERO: the correction starts from 0 (the pass writes 0 to the other colour);
-// ADD:  last pass of the level: u += e on both cells of the pair where the
-//       cell is not covered (level 0 inside the hierarchy vectors)
-template <class P, bool ZERO, bool ADD>
-__global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, const uint8_t* mask,
-                                                       P* u) {
-  const int ntz = gridDim.z >> 1;
-  const int fld = blockIdx.z >= ntz;
-  const int t = threadIdx.x;
-  const int j = blockIdx.y * VT + rb_j(t), k = (blockIdx.z - fld * ntz) * VT + rb_k(t);
-  if (j >= B.n1 || k >= B.n2) return;
-  const int ib = blockIdx.x * VT + rb_px(t);
-  const int par = (j + k + colour) & 1;          // box cells: colour = parity of i + j + k
-  const int i = ib + par, ip = ib + 1 - par;     // this colour, the other one
-  P* e = B.e + fld * B.vfs;
-  const P* A = B.A + fld * B.Afs;
-  const int row = B.n0 * (j + B.n1 * k);
-  P ev = P(0);
-  if (i < B.n0) {
-    P dg, of;
-    box_row<P, ZERO>(B, A, e, i, j, k, dg, of);
-    ev = (B.f[fld * B.vfs + row + i] + of) / dg;
-    e[row + i] = ev;
-    if (ADD && !(mask[row + i] & MASK_COVERED)) u[fld * B.vfs + row + i] += ev;
+// ---- one red-black Gauss-Seidel sweep on a box, both colours in one launch
+// The sweep reads the correction es (or zero) and writes ed (ed != es): first
+// every cell of colour c0 from the old values of its neighbours (which have
+// the other colour), then every cell of colour 1 - c0 from the new ones, the
+// same arithmetic per cell as two colour passes.  A CTA owns SX x SY columns
+// and marches a chunk of SZ z-planes: at step k it updates the first colour
+// on plane k over its columns and a one-column ring (the ring's new values
+// are what the second colour of its own columns reads), then the second
+// colour on plane k - 1.  Plane values that other threads read live in
+// shared memory (three rotating planes with a two-column ring of old
+// values); each thread keeps its own column's planes k-2 .. k+1 in
+// registers.  Nothing another CTA writes is read (es and ed differ), so
+// chunks and tiles are independent; a chunk also updates the first colour
+// on the plane on either side of it.  Each sweep then streams the
+// coefficients, the rhs and es once and writes ed once, where two colour
+// passes stream them twice.
+// ZERO: es = 0 (the first sweep of a level).  ADD: u += ed on uncovered cells
+// (the last sweep on level 0, in the hierarchy vectors).
+constexpr int SX = 32, SY = 16;
+constexpr int SWX = SX + 2, SWY = SY + 2;          // columns with the ring
+constexpr int SW_THREADS = 640;                    // >= SWX * SWY = 612
+constexpr int SPX = SX + 4, SPY = SY + 4;          // shared plane with a 2-column ring
+constexpr int SRING = SPX * SPY - SWX * SWY;       // 108 outer-ring cells
+
+// row (i, j, k) of I - beta div D grad on a box with the six neighbour
+// values given (the same operations in the same order as box_row)
+template <class P>
+__device__ __forceinline__ void box_row_nb(const BoxK<P>& B, const P* A, int i, int j, int k,
+                                           P xm, P xp, P ym, P yp, P zm, P zp, P& dg, P& of) {
+  const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
+  const int idx = i + n0 * (j + n1 * k);
+  const int s2 = n0 * n1;
+  P d = P(1), o = P(0), a;
+  if (i > 0) { a = A[idx]; d += a; o += a * xm; }
+  else d += A[B.gbase + B.fo[0] + j + n1 * k];
+  if (i < n0 - 1) { a = A[idx + 1]; d += a; o += a * xp; }
+  else d += A[B.gbase + B.fo[1] + j + n1 * k];
+  if (j > 0) { a = A[B.NA + idx]; d += a; o += a * ym; }
+  else d += A[B.gbase + B.fo[2] + k + n2 * i];
+  if (j < n1 - 1) { a = A[B.NA + idx + n0]; d += a; o += a * yp; }
+  else d += A[B.gbase + B.fo[3] + k + n2 * i];
+  if (k > 0) { a = A[2 * B.NA + idx]; d += a; o += a * zm; }
+  else d += A[B.gbase + B.fo[4] + i + n0 * j];
+  if (k < n2 - 1) { a = A[2 * B.NA + idx + s2]; d += a; o += a * zp; }
+  else d += A[B.gbase + B.fo[5] + i + n0 * j];
+  dg = d;
+  of = o;
+}
+
+// outer-ring cell q (0 .. SRING-1) of the shared plane -> (x, y) in plane
+// coordinates (0 .. SPX-1, 0 .. SPY-1): rows y = 0 and y = SPY-1, then
+// columns x = 0 and x = SPX-1 of the rows in between
+__device__ __forceinline__ void ring2_xy(int q, int& x, int& y) {
+  if (q < 2 * SPX) {
+    x = q % SPX;
+    y = (q < SPX) ? 0 : SPY - 1;
+  } else {
+    const int r = q - 2 * SPX;
+    x = (r < SPY - 2) ? 0 : SPX - 1;
+    y = 1 + ((r < SPY - 2) ? r : r - (SPY - 2));
   }
-  if (ip < B.n0) {
-    if (ZERO) e[row + ip] = P(0);
-    if (ADD && !(mask[row + ip] & MASK_COVERED)) u[fld * B.vfs + row + ip] += e[row + ip];
+}
+
+// grid (ceil(n0 / SX), ceil(n1 / SY), 2 x z-chunks), the upper half of z for
+// field 1; sz planes per chunk
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(SW_THREADS) k_bsweep(BoxK<P> B, int c0, int sz,
+                                                        const P* __restrict__ es,
+                                                        P* __restrict__ ed,
+                                                        const uint8_t* __restrict__ mask,
+                                                        P* __restrict__ u) {
+  __shared__ P S[3][SPY][SPX];
+  const int nzc = gridDim.z >> 1;
+  const int fld = blockIdx.z >= nzc;
+  const int z0 = (blockIdx.z - fld * nzc) * sz;
+  const int z1 = min(z0 + sz, B.n2);
+  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+  const int t = threadIdx.x;
+  const bool col = t < SWX * SWY;
+  const int ci = col ? t % SWX : 0, cj = col ? t / SWX : 0;   // column in the ring-1 region
+  const int i = x0 - 1 + ci, j = y0 - 1 + cj;
+  const bool inb = col && i >= 0 && i < B.n0 && j >= 0 && j < B.n1;
+  const bool own = inb && ci >= 1 && ci <= SX && cj >= 1 && cj <= SY;
+  const long fo = (long)fld * B.vfs;
+  const P* A = B.A + fld * B.Afs;
+  const P* f = B.f + fo;
+  const P* eo = ZERO ? nullptr : es + fo;
+  P* en = ed + fo;
+  // this thread's outer-ring cell (threads 0 .. SRING-1)
+  int rx = 0, ry = 0;
+  if (t < SRING) ring2_xy(t, rx, ry);
+  const int ri = x0 - 2 + rx, rj = y0 - 2 + ry;
+  const bool rin = t < SRING && ri >= 0 && ri < B.n0 && rj >= 0 && rj < B.n1;
+  auto old_at = [&](bool ok, int ii, int jj, int k) -> P {
+    if (ZERO || !ok || k < 0 || k >= B.n2) return P(0);
+    return eo[ii + B.n0 * (jj + B.n1 * k)];
+  };
+  const int kb = max(z0 - 1, 0);             // first plane of the first colour
+  const int ke = min(z1, B.n2 - 1);          // last plane of the first colour
+  P vm2 = P(0), vm1 = old_at(inb, i, j, kb - 1), v0 = old_at(inb, i, j, kb);
+  P r0 = old_at(rin, ri, rj, kb);
+  for (int k = kb; k <= z1; k++) {
+    P (*Sk)[SPX] = S[k % 3];
+    P (*Sm)[SPX] = S[(k + 2) % 3];           // plane k - 1
+    const P vp1 = old_at(inb, i, j, k + 1);
+    const P rp1 = old_at(rin, ri, rj, k + 1);
+    if (k <= ke) {
+      if (col) Sk[cj + 1][ci + 1] = v0;
+      if (t < SRING) Sk[ry][rx] = r0;
+    }
+    __syncthreads();
+    // first colour on plane k (own columns and the ring)
+    if (k <= ke && inb && ((i + j + k) & 1) == c0) {
+      P dg, of;
+      box_row_nb<P>(B, A, i, j, k, Sk[cj + 1][ci], Sk[cj + 1][ci + 2], Sk[cj][ci + 1],
+                    Sk[cj + 2][ci + 1], vm1, vp1, dg, of);
+      v0 = (f[i + B.n0 * (j + B.n1 * k)] + of) / dg;
+      Sk[cj + 1][ci + 1] = v0;
+    }
+    __syncthreads();
+    // second colour on plane k - 1 (own columns); both colours written there
+    const int km = k - 1;
+    if (km >= z0 && km < z1 && own) {
+      const int idx = i + B.n0 * (j + B.n1 * km);
+      P val = vm1;
+      if (((i + j + km) & 1) != c0) {
+        P dg, of;
+        box_row_nb<P>(B, A, i, j, km, Sm[cj + 1][ci], Sm[cj + 1][ci + 2], Sm[cj][ci + 1],
+                      Sm[cj + 2][ci + 1], vm2, v0, dg, of);
+        val = (f[idx] + of) / dg;
+      }
+      en[idx] = val;
+      if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] += val;
+    }
+    vm2 = vm1;
+    vm1 = v0;
+    v0 = vp1;
+    r0 = rp1;
   }
 }
 
@@ -1096,7 +1204,7 @@ dim3 tile_grid(int n0, int n1, int n2) {
 // from zero, the first sweep writes whichever buffer makes the last land in
 // e; from the current e, the sweeps alternate starting e -> scratch, and the
 // caller arranges an even count or a start in the scratch (see
-// jacobi_start_in_scratch)
+// start_in_scratch)
 template <class P>
 void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bool from_scratch,
                 const uint8_t* mask, P* addu, cudaStream_t s) {
@@ -1116,24 +1224,43 @@ void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bo
   }
 }
 
-// a nonzero start for `sweeps` Jacobi sweeps that must end in e: in the
-// scratch when the count is odd
-inline bool jacobi_start_in_scratch(int sweeps) { return (sweeps % 2) == 1; }
 
+// red-black sweeps on a box with k_bsweep, alternating between e and a
+// scratch vector of the same layout (as box_jacobi); c0 = first colour
+// (0: red first); zero: the first sweep starts from e = 0 and its target is
+// chosen so that the last sweep writes e; otherwise the sweeps start from e,
+// or from the scratch when from_scratch (the caller starts an odd count
+// there, so that the last sweep writes e); addu: the last sweep adds the
+// correction to u on uncovered cells (level 0)
 template <class P>
-void box_smooth(const BoxK<P>& V, int sweeps, bool red_first, bool zero, const uint8_t* mask,
-                P* addu, cudaStream_t s) {
-  const dim3 g = tile_grid(V.n0, V.n1, V.n2);
-  for (int sw = 0; sw < sweeps; sw++)
-    for (int pass = 0; pass < 2; pass++) {
-      const int colour = red_first ? pass : 1 - pass;
-      const bool Z = zero && sw == 0 && pass == 0;
-      const bool D = addu && sw == sweeps - 1 && pass == 1;
-      if (Z) k_bsmooth<P, true, false><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
-      else if (D) k_bsmooth<P, false, true><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
-      else k_bsmooth<P, false, false><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
+void box_sweeps(const BoxK<P>& V, P* scratch, int sweeps, int c0, bool zero, bool from_scratch,
+                const uint8_t* mask, P* addu, cudaStream_t s) {
+  // z-chunks: enough CTAs to fill the GPU several times over (the SX x SY
+  // column tiles alone do not on the coarse boxes), at least 2 planes each
+  const int ntx = (V.n0 + SX - 1) / SX, nty = (V.n1 + SY - 1) / SY;
+  const int want = std::max(1, (8 * 152 + 2 * ntx * nty - 1) / (2 * ntx * nty));
+  int sz = 32;
+  while (sz > 2 && (V.n2 + sz - 1) / sz < want) sz >>= 1;
+  const int nzc = (V.n2 + sz - 1) / sz;
+  const dim3 g(ntx, nty, 2 * nzc);
+  P* buf[2] = {V.e, scratch};
+  int cur = zero ? (((sweeps - 1) % 2 == 0) ? 0 : 1) : (from_scratch ? 1 : 0);
+  for (int sw = 0; sw < sweeps; sw++) {
+    const bool D = addu && sw == sweeps - 1;
+    if (zero && sw == 0) {
+      if (D) k_bsweep<P, true, true><<<g, SW_THREADS, 0, s>>>(V, c0, sz, nullptr, buf[cur], mask, addu);
+      else k_bsweep<P, true, false><<<g, SW_THREADS, 0, s>>>(V, c0, sz, nullptr, buf[cur], mask, addu);
+      continue;
     }
+    if (D) k_bsweep<P, false, true><<<g, SW_THREADS, 0, s>>>(V, c0, sz, buf[cur], buf[1 - cur], mask, addu);
+    else k_bsweep<P, false, false><<<g, SW_THREADS, 0, s>>>(V, c0, sz, buf[cur], buf[1 - cur], mask, addu);
+    cur = 1 - cur;
+  }
 }
+
+// a nonzero start for `sweeps` Gauss-Seidel or Jacobi sweeps that must end
+// in e: in the scratch when the count is odd
+inline bool start_in_scratch(int sweeps) { return (sweeps % 2) == 1; }
 
 // ---- the coarse end of the GMG V-cycle in one kernel
 // Levels tail_m .. nmg-1 are small (at most 8,192 cells per field): one CTA
@@ -1525,12 +1652,12 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   if (m == ps->nmg - 1) {
     if (ps->csw == 0) zero_e();   // no correction
     else if (jac) box_jacobi(V, omega, scratch, ps->csw, true, false, mask, addu, s);
-    else box_smooth(V, ps->csw, true, true, mask, addu, s);
+    else box_sweeps(V, scratch, ps->csw, 0, true, false, mask, addu, s);
     return;
   }
   if (ps->nu1 == 0) zero_e();
   else if (jac) box_jacobi(V, omega, scratch, ps->nu1, true, false, nullptr, (P*)nullptr, s);
-  else box_smooth(V, ps->nu1, true, true, nullptr, (P*)nullptr, s);
+  else box_sweeps(V, scratch, ps->nu1, 0, true, false, nullptr, (P*)nullptr, s);
   const BoxRaw& C = ps->box[m + 1];
   const dim3 gc = restrict_grid(C.n[0], C.n[1], C.n[2]);
   // after a red-first Gauss-Seidel sweep the black residuals are zero
@@ -1539,9 +1666,9 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   else
     k_brestrict<P, false><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);
   gmg_vcycle<P>(ps, H, m + 1, s);
-  // e + P e_c: into the scratch when an odd number of Jacobi sweeps follows,
-  // so that the last one writes e
-  const bool to_scratch = jac && ps->nu2 > 0 && jacobi_start_in_scratch(ps->nu2);
+  // e + P e_c: into the scratch when an odd number of sweeps follows, so
+  // that the last one writes e
+  const bool to_scratch = ps->nu2 > 0 && start_in_scratch(ps->nu2);
   k_bprolong<P><<<tile_grid(B.n[0], B.n[1], B.n[2]), FTHREADS, 0, s>>>(
       (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V, to_scratch ? scratch : V.e);
   if (ps->nu2 == 0) {
@@ -1549,7 +1676,7 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   } else if (jac) {
     box_jacobi(V, omega, scratch, ps->nu2, false, to_scratch, mask, addu, s);
   } else {
-    box_smooth(V, ps->nu2, false, false, mask, addu, s);
+    box_sweeps(V, scratch, ps->nu2, 1, false, to_scratch, mask, addu, s);
   }
 }
 
