@@ -102,26 +102,22 @@ __device__ __forceinline__ void box_row(const BoxK<P>& B, const P* A, const P* e
 // ---- one red-black Gauss-Seidel sweep on a box, both colours in one launch
 // The sweep reads the correction es (or zero) and writes ed (ed != es): first
 // every cell of colour c0 from the old values of its neighbours (which have
-// the other colour), then every cell of colour 1 - c0 from the new ones, the
-// same arithmetic per cell as two colour passes.  A CTA owns SX x SY columns
-// and marches a chunk of SZ z-planes: at step k it updates the first colour
-// on plane k over its columns and a one-column ring (the ring's new values
-// are what the second colour of its own columns reads), then the second
-// colour on plane k - 1.  Plane values that other threads read live in
-// shared memory (three rotating planes with a two-column ring of old
-// values); each thread keeps its own column's planes k-2 .. k+1 in
-// registers.  Nothing another CTA writes is read (es and ed differ), so
-// chunks and tiles are independent; a chunk also updates the first colour
-// on the plane on either side of it.  Each sweep then streams the
-// coefficients, the rhs and es once and writes ed once, where two colour
-// passes stream them twice.
+// the other colour), then every cell of colour 1 - c0 from the new ones: the
+// same arithmetic per cell as two colour passes.  A CTA owns a 32 x 8 x 8
+// tile.  It loads the old values of the tile and a two-cell ring into shared
+// memory, updates the first colour on the tile and a one-cell ring (the
+// values the tile's second colour reads), then the second colour on the
+// tile, and writes the tile.  Nothing another CTA writes is read (es and ed
+// differ), so tiles are independent; the ring work is repeated by the
+// neighbouring tiles, whose loads of the same data mostly hit L2.  Each
+// sweep then moves the coefficients, the rhs and es from DRAM about once and
+// writes ed once, where two colour passes move them twice.
 // ZERO: es = 0 (the first sweep of a level).  ADD: u += ed on uncovered cells
 // (the last sweep on level 0, in the hierarchy vectors).
-constexpr int SX = 32, SY = 16;
-constexpr int SWX = SX + 2, SWY = SY + 2;          // columns with the ring
-constexpr int SW_THREADS = 640;                    // >= SWX * SWY = 612
-constexpr int SPX = SX + 4, SPY = SY + 4;          // shared plane with a 2-column ring
-constexpr int SRING = SPX * SPY - SWX * SWY;       // 108 outer-ring cells
+constexpr int SX = 32, SY = 8, SZ = 8;
+constexpr int SW_THREADS = 512;
+constexpr int S2X = SX + 4, S2Y = SY + 4, S2Z = SZ + 4;     // tile + two-cell ring
+constexpr int S1X = SX + 2, S1Y = SY + 2, S1Z = SZ + 2;     // tile + one-cell ring
 
 // row (i, j, k) of I - beta div D grad on a box with the six neighbour
 // values given (the same operations in the same order as box_row)
@@ -148,95 +144,71 @@ __device__ __forceinline__ void box_row_nb(const BoxK<P>& B, const P* A, int i, 
   of = o;
 }
 
-// outer-ring cell q (0 .. SRING-1) of the shared plane -> (x, y) in plane
-// coordinates (0 .. SPX-1, 0 .. SPY-1): rows y = 0 and y = SPY-1, then
-// columns x = 0 and x = SPX-1 of the rows in between
-__device__ __forceinline__ void ring2_xy(int q, int& x, int& y) {
-  if (q < 2 * SPX) {
-    x = q % SPX;
-    y = (q < SPX) ? 0 : SPY - 1;
-  } else {
-    const int r = q - 2 * SPX;
-    x = (r < SPY - 2) ? 0 : SPX - 1;
-    y = 1 + ((r < SPY - 2) ? r : r - (SPY - 2));
-  }
-}
-
-// grid (ceil(n0 / SX), ceil(n1 / SY), 2 x z-chunks), the upper half of z for
-// field 1; sz planes per chunk
+// grid (ceil(n0 / SX), ceil(n1 / SY), 2 ceil(n2 / SZ)), the upper half of z
+// for field 1; the tile origin is a multiple of 2 on every axis, so the
+// colour of ring-frame cell (x, y, z) is (x + y + z + 1) mod 2
 template <class P, bool ZERO, bool ADD>
-__global__ void __launch_bounds__(SW_THREADS) k_bsweep(BoxK<P> B, int c0, int sz,
+__global__ void __launch_bounds__(SW_THREADS) k_bsweep(BoxK<P> B, int c0,
                                                         const P* __restrict__ es,
                                                         P* __restrict__ ed,
                                                         const uint8_t* __restrict__ mask,
                                                         P* __restrict__ u) {
-  __shared__ P S[3][SPY][SPX];
-  const int nzc = gridDim.z >> 1;
-  const int fld = blockIdx.z >= nzc;
-  const int z0 = (blockIdx.z - fld * nzc) * sz;
-  const int z1 = min(z0 + sz, B.n2);
-  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY;
+  __shared__ P S[S2Z][S2Y][S2X];
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, z0 = (blockIdx.z - fld * ntz) * SZ;
   const int t = threadIdx.x;
-  const bool col = t < SWX * SWY;
-  const int ci = col ? t % SWX : 0, cj = col ? t / SWX : 0;   // column in the ring-1 region
-  const int i = x0 - 1 + ci, j = y0 - 1 + cj;
-  const bool inb = col && i >= 0 && i < B.n0 && j >= 0 && j < B.n1;
-  const bool own = inb && ci >= 1 && ci <= SX && cj >= 1 && cj <= SY;
   const long fo = (long)fld * B.vfs;
   const P* A = B.A + fld * B.Afs;
   const P* f = B.f + fo;
-  const P* eo = ZERO ? nullptr : es + fo;
-  P* en = ed + fo;
-  // this thread's outer-ring cell (threads 0 .. SRING-1)
-  int rx = 0, ry = 0;
-  if (t < SRING) ring2_xy(t, rx, ry);
-  const int ri = x0 - 2 + rx, rj = y0 - 2 + ry;
-  const bool rin = t < SRING && ri >= 0 && ri < B.n0 && rj >= 0 && rj < B.n1;
-  auto old_at = [&](bool ok, int ii, int jj, int k) -> P {
-    if (ZERO || !ok || k < 0 || k >= B.n2) return P(0);
-    return eo[ii + B.n0 * (jj + B.n1 * k)];
-  };
-  const int kb = max(z0 - 1, 0);             // first plane of the first colour
-  const int ke = min(z1, B.n2 - 1);          // last plane of the first colour
-  P vm2 = P(0), vm1 = old_at(inb, i, j, kb - 1), v0 = old_at(inb, i, j, kb);
-  P r0 = old_at(rin, ri, rj, kb);
-  for (int k = kb; k <= z1; k++) {
-    P (*Sk)[SPX] = S[k % 3];
-    P (*Sm)[SPX] = S[(k + 2) % 3];           // plane k - 1
-    const P vp1 = old_at(inb, i, j, k + 1);
-    const P rp1 = old_at(rin, ri, rj, k + 1);
-    if (k <= ke) {
-      if (col) Sk[cj + 1][ci + 1] = v0;
-      if (t < SRING) Sk[ry][rx] = r0;
-    }
-    __syncthreads();
-    // first colour on plane k (own columns and the ring)
-    if (k <= ke && inb && ((i + j + k) & 1) == c0) {
-      P dg, of;
-      box_row_nb<P>(B, A, i, j, k, Sk[cj + 1][ci], Sk[cj + 1][ci + 2], Sk[cj][ci + 1],
-                    Sk[cj + 2][ci + 1], vm1, vp1, dg, of);
-      v0 = (f[i + B.n0 * (j + B.n1 * k)] + of) / dg;
-      Sk[cj + 1][ci + 1] = v0;
-    }
-    __syncthreads();
-    // second colour on plane k - 1 (own columns); both colours written there
-    const int km = k - 1;
-    if (km >= z0 && km < z1 && own) {
-      const int idx = i + B.n0 * (j + B.n1 * km);
-      P val = vm1;
-      if (((i + j + km) & 1) != c0) {
-        P dg, of;
-        box_row_nb<P>(B, A, i, j, km, Sm[cj + 1][ci], Sm[cj + 1][ci + 2], Sm[cj][ci + 1],
-                      Sm[cj + 2][ci + 1], vm2, v0, dg, of);
-        val = (f[idx] + of) / dg;
-      }
-      en[idx] = val;
-      if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] += val;
-    }
-    vm2 = vm1;
-    vm1 = v0;
-    v0 = vp1;
-    r0 = rp1;
+  const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
+  // old values on the tile and the two-cell ring (0 outside the box)
+  for (int q = t; q < S2X * S2Y * S2Z; q += SW_THREADS) {
+    const int x = q % S2X, r = q / S2X, y = r % S2Y, z = r / S2Y;
+    const int i = x0 - 2 + x, j = y0 - 2 + y, k = z0 - 2 + z;
+    P v = P(0);
+    if (!ZERO && i >= 0 && i < n0 && j >= 0 && j < n1 && k >= 0 && k < n2)
+      v = es[fo + i + n0 * (j + n1 * k)];
+    S[z][y][x] = v;
+  }
+  __syncthreads();
+  // first colour on the tile and the one-cell ring: 17 cells of the colour
+  // in each 34-cell row of the ring frame
+  for (int q = t; q < (S1X / 2) * S1Y * S1Z; q += SW_THREADS) {
+    const int row = q / (S1X / 2), y = row % S1Y, z = row / S1Y;
+    const int x = 2 * (q % (S1X / 2)) + ((c0 + 1 + y + z) & 1);
+    const int i = x0 - 1 + x, j = y0 - 1 + y, k = z0 - 1 + z;
+    if (i < 0 || i >= n0 || j < 0 || j >= n1 || k < 0 || k >= n2) continue;
+    P (*Sz)[S2X] = S[z + 1];
+    P dg, of;
+    box_row_nb<P>(B, A, i, j, k, Sz[y + 1][x], Sz[y + 1][x + 2], Sz[y][x + 1], Sz[y + 2][x + 1],
+                  S[z][y + 1][x + 1], S[z + 2][y + 1][x + 1], dg, of);
+    S[z + 1][y + 1][x + 1] = (f[i + n0 * (j + n1 * k)] + of) / dg;
+  }
+  __syncthreads();
+  // second colour on the tile: 16 cells of the colour in each 32-cell row
+  for (int q = t; q < (SX / 2) * SY * SZ; q += SW_THREADS) {
+    const int row = q / (SX / 2), yi = row % SY, zi = row / SY;
+    const int xi = 2 * (q % (SX / 2)) + ((c0 + 1 + yi + zi) & 1);
+    const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
+    if (i >= n0 || j >= n1 || k >= n2) continue;
+    const int x = xi + 1, y = yi + 1, z = zi + 1;    // one-ring frame
+    P (*Sz)[S2X] = S[z + 1];
+    P dg, of;
+    box_row_nb<P>(B, A, i, j, k, Sz[y + 1][x], Sz[y + 1][x + 2], Sz[y][x + 1], Sz[y + 2][x + 1],
+                  S[z][y + 1][x + 1], S[z + 2][y + 1][x + 1], dg, of);
+    S[z + 1][y + 1][x + 1] = (f[i + n0 * (j + n1 * k)] + of) / dg;
+  }
+  __syncthreads();
+  // the tile, both colours, in rows of 32
+  for (int q = t; q < SX * SY * SZ; q += SW_THREADS) {
+    const int xi = q % SX, r = q / SX, yi = r % SY, zi = r / SY;
+    const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
+    if (i >= n0 || j >= n1 || k >= n2) continue;
+    const int idx = i + n0 * (j + n1 * k);
+    const P v = S[zi + 2][yi + 2][xi + 2];
+    ed[fo + idx] = v;
+    if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] += v;
   }
 }
 
@@ -1235,25 +1207,18 @@ void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bo
 template <class P>
 void box_sweeps(const BoxK<P>& V, P* scratch, int sweeps, int c0, bool zero, bool from_scratch,
                 const uint8_t* mask, P* addu, cudaStream_t s) {
-  // z-chunks: enough CTAs to fill the GPU several times over (the SX x SY
-  // column tiles alone do not on the coarse boxes), at least 2 planes each
-  const int ntx = (V.n0 + SX - 1) / SX, nty = (V.n1 + SY - 1) / SY;
-  const int want = std::max(1, (8 * 152 + 2 * ntx * nty - 1) / (2 * ntx * nty));
-  int sz = 32;
-  while (sz > 2 && (V.n2 + sz - 1) / sz < want) sz >>= 1;
-  const int nzc = (V.n2 + sz - 1) / sz;
-  const dim3 g(ntx, nty, 2 * nzc);
+  const dim3 g((V.n0 + SX - 1) / SX, (V.n1 + SY - 1) / SY, 2 * ((V.n2 + SZ - 1) / SZ));
   P* buf[2] = {V.e, scratch};
   int cur = zero ? (((sweeps - 1) % 2 == 0) ? 0 : 1) : (from_scratch ? 1 : 0);
   for (int sw = 0; sw < sweeps; sw++) {
     const bool D = addu && sw == sweeps - 1;
     if (zero && sw == 0) {
-      if (D) k_bsweep<P, true, true><<<g, SW_THREADS, 0, s>>>(V, c0, sz, nullptr, buf[cur], mask, addu);
-      else k_bsweep<P, true, false><<<g, SW_THREADS, 0, s>>>(V, c0, sz, nullptr, buf[cur], mask, addu);
+      if (D) k_bsweep<P, true, true><<<g, SW_THREADS, 0, s>>>(V, c0, nullptr, buf[cur], mask, addu);
+      else k_bsweep<P, true, false><<<g, SW_THREADS, 0, s>>>(V, c0, nullptr, buf[cur], mask, addu);
       continue;
     }
-    if (D) k_bsweep<P, false, true><<<g, SW_THREADS, 0, s>>>(V, c0, sz, buf[cur], buf[1 - cur], mask, addu);
-    else k_bsweep<P, false, false><<<g, SW_THREADS, 0, s>>>(V, c0, sz, buf[cur], buf[1 - cur], mask, addu);
+    if (D) k_bsweep<P, false, true><<<g, SW_THREADS, 0, s>>>(V, c0, buf[cur], buf[1 - cur], mask, addu);
+    else k_bsweep<P, false, false><<<g, SW_THREADS, 0, s>>>(V, c0, buf[cur], buf[1 - cur], mask, addu);
     cur = 1 - cur;
   }
 }
