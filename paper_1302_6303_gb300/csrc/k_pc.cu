@@ -18,6 +18,8 @@
 #include <cstdio>
 
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include "nrd_internal.h"
 
@@ -99,91 +101,209 @@ __device__ __forceinline__ void box_row(const BoxK<P>& B, const P* A, const P* e
   of = o;
 }
 
+// one colour of a red-black Gauss-Seidel pass on a box; grid (tiles x,
+// tiles y, 2 x tiles z), the upper half of z for field 1.
+// ZERO: the correction starts from 0 (the pass writes 0 to the other colour);
+// ADD:  last pass of the level: u += e on both cells of the pair where the
+//       cell is not covered (level 0 inside the hierarchy vectors)
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, const uint8_t* mask,
+                                                       P* u) {
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int t = threadIdx.x;
+  const int j = blockIdx.y * VT + rb_j(t), k = (blockIdx.z - fld * ntz) * VT + rb_k(t);
+  if (j >= B.n1 || k >= B.n2) return;
+  const int ib = blockIdx.x * VT + rb_px(t);
+  const int par = (j + k + colour) & 1;          // box cells: colour = parity of i + j + k
+  const int i = ib + par, ip = ib + 1 - par;     // this colour, the other one
+  P* e = B.e + fld * B.vfs;
+  const P* A = B.A + fld * B.Afs;
+  const int row = B.n0 * (j + B.n1 * k);
+  P ev = P(0);
+  if (i < B.n0) {
+    P dg, of;
+    box_row<P, ZERO>(B, A, e, i, j, k, dg, of);
+    ev = (B.f[fld * B.vfs + row + i] + of) / dg;
+    e[row + i] = ev;
+    if (ADD && !(mask[row + i] & MASK_COVERED)) u[fld * B.vfs + row + i] += ev;
+  }
+  if (ip < B.n0) {
+    if (ZERO) e[row + ip] = P(0);
+    if (ADD && !(mask[row + ip] & MASK_COVERED)) u[fld * B.vfs + row + ip] += e[row + ip];
+  }
+}
+
 // ---- one red-black Gauss-Seidel sweep on a box, both colours in one launch
-// The sweep reads the correction es (or zero) and writes ed (ed != es): first
-// every cell of colour c0 from the old values of its neighbours (which have
-// the other colour), then every cell of colour 1 - c0 from the new ones: the
-// same arithmetic per cell as two colour passes.  A CTA owns a 32 x 8 x 8
-// tile.  It loads the old values of the tile and a two-cell ring into shared
-// memory, updates the first colour on the tile and a one-cell ring (the
-// values the tile's second colour reads), then the second colour on the
-// tile, and writes the tile.  Nothing another CTA writes is read (es and ed
-// differ), so tiles are independent; the ring work is repeated by the
-// neighbouring tiles, whose loads of the same data mostly hit L2.  Each
-// sweep then moves the coefficients, the rhs and es from DRAM about once and
-// writes ed once, where two colour passes move them twice.
-// ZERO: es = 0 (the first sweep of a level).  ADD: u += ed on uncovered cells
-// (the last sweep on level 0, in the hierarchy vectors).
+// (FP32 boxes whose arrays TMA can address).  The sweep reads the correction
+// es (or zero) and writes ed (ed != es): first every cell of colour c0 from
+// the old values of its neighbours (which have the other colour), then every
+// cell of colour 1 - c0 from the new ones, the same arithmetic per cell as
+// two colour passes of k_bsmooth.  A CTA owns a 32 x 8 x 8 tile.  One thread
+// starts five TMA box loads into shared memory: the old correction over the
+// tile and a two-cell ring, and the rhs and the three low-face coefficient
+// arrays over the tile and a one-cell ring (plus the high faces of the
+// ring); all threads wait on one mbarrier (bounded: a wait that runs out
+// sets err and the CTA stops after a second bounded wait for its copies).
+// Then the first colour is updated on the tile and the ring (the values the
+// tile's second colour reads), the second colour on the tile, and the tile
+// is written.  Nothing another CTA writes is read (es and ed differ), so
+// tiles are independent; the ring loads of neighbouring tiles mostly hit
+// L2.  A sweep thus moves the coefficients, the rhs and es from DRAM about
+// once and writes ed once, where two colour passes move them twice.
+// The boxes start 4 cells before the tile in x (TMA wants the innermost
+// coordinate at a 16-byte boundary) and are 40 wide; cells outside the
+// array read as zero and are never used (domain faces take the boundary
+// slot coefficient, read from global memory).
+// ZERO: es = 0 (the first sweep of a level; no load).  ADD: u += ed on
+// uncovered cells (the last sweep on level 0, in the hierarchy vectors).
 constexpr int SX = 32, SY = 8, SZ = 8;
 constexpr int SW_THREADS = 512;
-constexpr int S2X = SX + 4, S2Y = SY + 4, S2Z = SZ + 4;     // tile + two-cell ring
-constexpr int S1X = SX + 2, S1Y = SY + 2, S1Z = SZ + 2;     // tile + one-cell ring
+constexpr int TBX = 40;                                      // box width in x (from x0 - 4)
+constexpr int EBY = SY + 4, EBZ = SZ + 4;                    // correction box: two-cell ring
+constexpr int FBY = SY + 2, FBZ = SZ + 2;                    // rhs / coefficient boxes
+constexpr int E_BYTES = TBX * EBY * EBZ * 4;                 // 23040
+constexpr int F_BYTES = TBX * FBY * FBZ * 4;                 // 16000 (rhs, x faces)
+constexpr int AY_BYTES = TBX * (FBY + 1) * FBZ * 4;          // 17600 (y faces, one more row)
+constexpr int AZ_BYTES = TBX * FBY * (FBZ + 1) * 4;          // 17600 (z faces, one more plane)
+constexpr int up128(int b) { return (b + 127) / 128 * 128; }
+constexpr int OFF_F = up128(E_BYTES);
+constexpr int OFF_AX = OFF_F + up128(F_BYTES);
+constexpr int OFF_AY = OFF_AX + up128(F_BYTES);
+constexpr int OFF_AZ = OFF_AY + up128(AY_BYTES);
+constexpr int OFF_BAR = OFF_AZ + up128(AZ_BYTES);
+constexpr int SWEEP_SMEM = OFF_BAR + 16;
+constexpr long kTmaSpinLimit = 1L << 24;
 
-// row (i, j, k) of I - beta div D grad on a box with the six neighbour
-// values given (the same operations in the same order as box_row)
-template <class P>
-__device__ __forceinline__ void box_row_nb(const BoxK<P>& B, const P* A, int i, int j, int k,
-                                           P xm, P xp, P ym, P yp, P zm, P zp, P& dg, P& of) {
+struct SweepMaps {                 // per field: old correction, rhs, x/y/z low faces
+  CUtensorMap es[2], f[2], ax[2], ay[2], az[2];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                          int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4}], [%5];"
+      :
+      : "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
+// wait for phase 0 of the mbarrier, at most kTmaSpinLimit polls; false if
+// the wait ran out
+__device__ __forceinline__ bool mbar_wait0(uint32_t bar) {
+  for (long it = 0; it < kTmaSpinLimit; it++) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0; "
+        "selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(bar)
+        : "memory");
+    if (done) return true;
+    if (it > 64) __nanosleep(32);
+  }
+  return false;
+}
+
+// row (i, j, k) of I - beta div D grad with the six face coefficients and
+// neighbour values given; domain faces take the boundary slot (the same
+// operations in the same order as box_row)
+__device__ __forceinline__ void box_row_s(const BoxK<float>& B, const float* A, int i, int j,
+                                          int k, float axl, float axh, float ayl, float ayh,
+                                          float azl, float azh, float xm, float xp, float ym,
+                                          float yp, float zm, float zp, float& dg, float& of) {
   const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
-  const int idx = i + n0 * (j + n1 * k);
-  const int s2 = n0 * n1;
-  P d = P(1), o = P(0), a;
-  if (i > 0) { a = A[idx]; d += a; o += a * xm; }
+  float d = 1.0f, o = 0.0f;
+  if (i > 0) { d += axl; o += axl * xm; }
   else d += A[B.gbase + B.fo[0] + j + n1 * k];
-  if (i < n0 - 1) { a = A[idx + 1]; d += a; o += a * xp; }
+  if (i < n0 - 1) { d += axh; o += axh * xp; }
   else d += A[B.gbase + B.fo[1] + j + n1 * k];
-  if (j > 0) { a = A[B.NA + idx]; d += a; o += a * ym; }
+  if (j > 0) { d += ayl; o += ayl * ym; }
   else d += A[B.gbase + B.fo[2] + k + n2 * i];
-  if (j < n1 - 1) { a = A[B.NA + idx + n0]; d += a; o += a * yp; }
+  if (j < n1 - 1) { d += ayh; o += ayh * yp; }
   else d += A[B.gbase + B.fo[3] + k + n2 * i];
-  if (k > 0) { a = A[2 * B.NA + idx]; d += a; o += a * zm; }
+  if (k > 0) { d += azl; o += azl * zm; }
   else d += A[B.gbase + B.fo[4] + i + n0 * j];
-  if (k < n2 - 1) { a = A[2 * B.NA + idx + s2]; d += a; o += a * zp; }
+  if (k < n2 - 1) { d += azh; o += azh * zp; }
   else d += A[B.gbase + B.fo[5] + i + n0 * j];
   dg = d;
   of = o;
 }
 
 // grid (ceil(n0 / SX), ceil(n1 / SY), 2 ceil(n2 / SZ)), the upper half of z
-// for field 1; the tile origin is a multiple of 2 on every axis, so the
-// colour of ring-frame cell (x, y, z) is (x + y + z + 1) mod 2
-template <class P, bool ZERO, bool ADD>
-__global__ void __launch_bounds__(SW_THREADS) k_bsweep(BoxK<P> B, int c0,
-                                                        const P* __restrict__ es,
-                                                        P* __restrict__ ed,
-                                                        const uint8_t* __restrict__ mask,
-                                                        P* __restrict__ u) {
-  __shared__ P S[S2Z][S2Y][S2X];
+// for field 1; SWEEP_SMEM bytes of dynamic shared memory.  The tile origin
+// is even on every axis, so the colour of the cell at (x, y, z) in the
+// one-ring frame (origin one cell before the tile) is (x + y + z + 1) mod 2.
+template <bool ZERO, bool ADD>
+__global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant__ SweepMaps M,
+                                                           BoxK<float> B, int c0,
+                                                           float* __restrict__ ed,
+                                                           const uint8_t* __restrict__ mask,
+                                                           float* __restrict__ u,
+                                                           int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  float (*Se)[EBY][TBX] = reinterpret_cast<float (*)[EBY][TBX]>(smem);
+  float (*Sf)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(smem + OFF_F);
+  float (*Sx)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(smem + OFF_AX);
+  float (*Sy)[FBY + 1][TBX] = reinterpret_cast<float (*)[FBY + 1][TBX]>(smem + OFF_AY);
+  float (*Sz)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(smem + OFF_AZ);
+  const uint32_t bar = smem_u32(smem + OFF_BAR);
   const int ntz = gridDim.z >> 1;
   const int fld = blockIdx.z >= ntz;
   const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, z0 = (blockIdx.z - fld * ntz) * SZ;
   const int t = threadIdx.x;
-  const long fo = (long)fld * B.vfs;
-  const P* A = B.A + fld * B.Afs;
-  const P* f = B.f + fo;
   const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
-  // old values on the tile and the two-cell ring (0 outside the box)
-  for (int q = t; q < S2X * S2Y * S2Z; q += SW_THREADS) {
-    const int x = q % S2X, r = q / S2X, y = r % S2Y, z = r / S2Y;
-    const int i = x0 - 2 + x, j = y0 - 2 + y, k = z0 - 2 + z;
-    P v = P(0);
-    if (!ZERO && i >= 0 && i < n0 && j >= 0 && j < n1 && k >= 0 && k < n2)
-      v = es[fo + i + n0 * (j + n1 * k)];
-    S[z][y][x] = v;
+  const float* A = B.A + fld * B.Afs;
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
+  if (t == 0) {
+    const uint32_t bytes = (ZERO ? 0 : E_BYTES) + 2 * F_BYTES + AY_BYTES + AZ_BYTES;
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+    if (!ZERO) tma_load3(smem_u32(smem), &M.es[fld], x0 - 4, y0 - 2, z0 - 2, bar);
+    tma_load3(smem_u32(smem + OFF_F), &M.f[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(smem + OFF_AX), &M.ax[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(smem + OFF_AY), &M.ay[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(smem + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+  }
+  const bool late = !mbar_wait0(bar);
+  if (__syncthreads_or(late)) {
+    // the copies did not land in time: report, give them a second bounded
+    // wait (they write this CTA's shared memory), and stop
+    if (t == 0) atomicOr(err, 2);
+    mbar_wait0(bar);
+    return;
+  }
   // first colour on the tile and the one-cell ring: 17 cells of the colour
   // in each 34-cell row of the ring frame
-  for (int q = t; q < (S1X / 2) * S1Y * S1Z; q += SW_THREADS) {
-    const int row = q / (S1X / 2), y = row % S1Y, z = row / S1Y;
-    const int x = 2 * (q % (S1X / 2)) + ((c0 + 1 + y + z) & 1);
+  for (int q = t; q < 17 * FBY * FBZ; q += SW_THREADS) {
+    const int row = q / 17, y = row % FBY, z = row / FBY;
+    const int x = 2 * (q % 17) + ((c0 + 1 + y + z) & 1);
     const int i = x0 - 1 + x, j = y0 - 1 + y, k = z0 - 1 + z;
     if (i < 0 || i >= n0 || j < 0 || j >= n1 || k < 0 || k >= n2) continue;
-    P (*Sz)[S2X] = S[z + 1];
-    P dg, of;
-    box_row_nb<P>(B, A, i, j, k, Sz[y + 1][x], Sz[y + 1][x + 2], Sz[y][x + 1], Sz[y + 2][x + 1],
-                  S[z][y + 1][x + 1], S[z + 2][y + 1][x + 1], dg, of);
-    S[z + 1][y + 1][x + 1] = (f[i + n0 * (j + n1 * k)] + of) / dg;
+    const int xb = x + 3;                                   // column in the 40-wide boxes
+    float xm = 0.0f, xp = 0.0f, ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+    if (!ZERO) {
+      xm = Se[z + 1][y + 1][xb - 1];
+      xp = Se[z + 1][y + 1][xb + 1];
+      ym = Se[z + 1][y][xb];
+      yp = Se[z + 1][y + 2][xb];
+      zm = Se[z][y + 1][xb];
+      zp = Se[z + 2][y + 1][xb];
+    }
+    float dg, of;
+    box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
+              Sz[z][y][xb], Sz[z + 1][y][xb], xm, xp, ym, yp, zm, zp, dg, of);
+    Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
   }
   __syncthreads();
   // second colour on the tile: 16 cells of the colour in each 32-cell row
@@ -192,21 +312,23 @@ __global__ void __launch_bounds__(SW_THREADS) k_bsweep(BoxK<P> B, int c0,
     const int xi = 2 * (q % (SX / 2)) + ((c0 + 1 + yi + zi) & 1);
     const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
     if (i >= n0 || j >= n1 || k >= n2) continue;
-    const int x = xi + 1, y = yi + 1, z = zi + 1;    // one-ring frame
-    P (*Sz)[S2X] = S[z + 1];
-    P dg, of;
-    box_row_nb<P>(B, A, i, j, k, Sz[y + 1][x], Sz[y + 1][x + 2], Sz[y][x + 1], Sz[y + 2][x + 1],
-                  S[z][y + 1][x + 1], S[z + 2][y + 1][x + 1], dg, of);
-    S[z + 1][y + 1][x + 1] = (f[i + n0 * (j + n1 * k)] + of) / dg;
+    const int x = xi + 1, y = yi + 1, z = zi + 1, xb = x + 3;
+    float dg, of;
+    box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
+              Sz[z][y][xb], Sz[z + 1][y][xb], Se[z + 1][y + 1][xb - 1], Se[z + 1][y + 1][xb + 1],
+              Se[z + 1][y][xb], Se[z + 1][y + 2][xb], Se[z][y + 1][xb], Se[z + 2][y + 1][xb], dg,
+              of);
+    Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
   }
   __syncthreads();
   // the tile, both colours, in rows of 32
+  const long fo = (long)fld * B.vfs;
   for (int q = t; q < SX * SY * SZ; q += SW_THREADS) {
     const int xi = q % SX, r = q / SX, yi = r % SY, zi = r / SY;
     const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
     if (i >= n0 || j >= n1 || k >= n2) continue;
     const int idx = i + n0 * (j + n1 * k);
-    const P v = S[zi + 2][yi + 2][xi + 2];
+    const float v = Se[zi + 2][yi + 2][xi + 4];
     ed[fo + idx] = v;
     if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] += v;
   }
@@ -751,10 +873,19 @@ __global__ void k_p2_setup(const uint8_t* mask, int N, const double* Tk, const f
 }
 
 // y = P2^{-1} z per leaf cell (Sec. 4.2); covered cells get 0
+// (err set: a TMA wait of this V-cycle gave up, and y reads NaN)
 template <class P>
 __global__ void k_p2(int N, const P* zin, const P* p, double* y, const int* jd, long jstride,
-                     double* y2) {
+                     double* y2, const int* err) {
   if (jd) y += (long)(*jd) * jstride;   // y = column *jd of a basis (device index)
+  if (*err) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 2 * N; c += gridDim.x * blockDim.x) {
+      y[c] = nan;
+      if (y2) y2[c] = nan;
+    }
+    return;
+  }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
     const P sb = p[c], sbt = p[N + c], rd = p[2L * N + c];
     const P zE = zin[c], zT = zin[N + c];
@@ -771,7 +902,13 @@ __global__ void k_p2(int N, const P* zin, const P* p, double* y, const int* jd, 
 
 // y = V-cycle output in FP64; covered cells get 0
 template <class P>
-__global__ void k_out_cast(const uint8_t* mask, int N, const P* u, double* y) {
+__global__ void k_out_cast(const uint8_t* mask, int N, const P* u, double* y, const int* err) {
+  if (*err) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < 2 * N; c += gridDim.x * blockDim.x)
+      y[c] = nan;
+    return;
+  }
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
     bool cov = mask[c] & MASK_COVERED;
     y[c] = cov ? 0.0 : (double)u[c];
@@ -1132,6 +1269,14 @@ struct PcState {
   void* fj = nullptr;    // [2][N]
   void* bj[NRD_MAX_MG] = {nullptr};
   void* gwp = nullptr;   // [nterm] coarse-fine weights in precision P
+  // FP32 box levels whose arrays TMA can address run the one-launch
+  // red-black sweep (k_bsweep); their tensor maps: correction [buffer: e,
+  // scratch][field], rhs [field], low-face coefficients [axis][field]
+  bool tma_ok[NRD_MAX_MG] = {false};
+  CUtensorMap tm_e[NRD_MAX_MG][2][2];
+  CUtensorMap tm_f[NRD_MAX_MG][2];
+  CUtensorMap tm_a[NRD_MAX_MG][3][2];
+  int* d_err = nullptr;  // set when a TMA wait of the V-cycle gave up
 };
 
 namespace {
@@ -1197,28 +1342,38 @@ void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bo
 }
 
 
-// red-black sweeps on a box with k_bsweep, alternating between e and a
-// scratch vector of the same layout (as box_jacobi); c0 = first colour
-// (0: red first); zero: the first sweep starts from e = 0 and its target is
-// chosen so that the last sweep writes e; otherwise the sweeps start from e,
-// or from the scratch when from_scratch (the caller starts an odd count
-// there, so that the last sweep writes e); addu: the last sweep adds the
-// correction to u on uncovered cells (level 0)
-template <class P>
-void box_sweeps(const BoxK<P>& V, P* scratch, int sweeps, int c0, bool zero, bool from_scratch,
-                const uint8_t* mask, P* addu, cudaStream_t s) {
+// red-black sweeps on FP32 box level m with k_bsweep, alternating between
+// e and a scratch vector of the same layout (as box_jacobi); c0 = first
+// colour (0: red first); zero: the first sweep starts from e = 0 and its
+// target is chosen so that the last sweep writes e; otherwise the sweeps
+// start from e, or from the scratch when from_scratch (the caller starts an
+// odd count there, so that the last sweep writes e); addu: the last sweep
+// adds the correction to u on uncovered cells (level 0)
+void box_sweeps(const PcState* ps, int m, const BoxK<float>& V, float* scratch, int sweeps, int c0,
+                bool zero, bool from_scratch, const uint8_t* mask, float* addu, cudaStream_t s) {
   const dim3 g((V.n0 + SX - 1) / SX, (V.n1 + SY - 1) / SY, 2 * ((V.n2 + SZ - 1) / SZ));
-  P* buf[2] = {V.e, scratch};
+  float* buf[2] = {V.e, scratch};
+  SweepMaps M;
+  for (int fld = 0; fld < 2; fld++) {
+    M.f[fld] = ps->tm_f[m][fld];
+    M.ax[fld] = ps->tm_a[m][0][fld];
+    M.ay[fld] = ps->tm_a[m][1][fld];
+    M.az[fld] = ps->tm_a[m][2][fld];
+  }
+  auto src = [&](int b) {
+    for (int fld = 0; fld < 2; fld++) M.es[fld] = ps->tm_e[m][b][fld];
+  };
   int cur = zero ? (((sweeps - 1) % 2 == 0) ? 0 : 1) : (from_scratch ? 1 : 0);
   for (int sw = 0; sw < sweeps; sw++) {
     const bool D = addu && sw == sweeps - 1;
     if (zero && sw == 0) {
-      if (D) k_bsweep<P, true, true><<<g, SW_THREADS, 0, s>>>(V, c0, nullptr, buf[cur], mask, addu);
-      else k_bsweep<P, true, false><<<g, SW_THREADS, 0, s>>>(V, c0, nullptr, buf[cur], mask, addu);
+      if (D) k_bsweep<true, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[cur], mask, addu, ps->d_err);
+      else k_bsweep<true, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[cur], mask, addu, ps->d_err);
       continue;
     }
-    if (D) k_bsweep<P, false, true><<<g, SW_THREADS, 0, s>>>(V, c0, buf[cur], buf[1 - cur], mask, addu);
-    else k_bsweep<P, false, false><<<g, SW_THREADS, 0, s>>>(V, c0, buf[cur], buf[1 - cur], mask, addu);
+    src(cur);
+    if (D) k_bsweep<false, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[1 - cur], mask, addu, ps->d_err);
+    else k_bsweep<false, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[1 - cur], mask, addu, ps->d_err);
     cur = 1 - cur;
   }
 }
@@ -1226,6 +1381,44 @@ void box_sweeps(const BoxK<P>& V, P* scratch, int sweeps, int c0, bool zero, boo
 // a nonzero start for `sweeps` Gauss-Seidel or Jacobi sweeps that must end
 // in e: in the scratch when the count is odd
 inline bool start_in_scratch(int sweeps) { return (sweeps % 2) == 1; }
+
+// red-black sweeps on a box in place, two colour passes each (k_bsmooth)
+template <class P>
+void box_smooth(const BoxK<P>& V, int sweeps, bool red_first, bool zero, const uint8_t* mask,
+                P* addu, cudaStream_t s) {
+  const dim3 g = tile_grid(V.n0, V.n1, V.n2);
+  for (int sw = 0; sw < sweeps; sw++)
+    for (int pass = 0; pass < 2; pass++) {
+      const int colour = red_first ? pass : 1 - pass;
+      const bool Z = zero && sw == 0 && pass == 0;
+      const bool D = addu && sw == sweeps - 1 && pass == 1;
+      if (Z) k_bsmooth<P, true, false><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
+      else if (D) k_bsmooth<P, false, true><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
+      else k_bsmooth<P, false, false><<<g, VTHREADS, 0, s>>>(V, colour, mask, addu);
+    }
+}
+
+// does box level m smooth with the one-launch sweep (ping-pong buffers)?
+template <class P>
+bool fused_sweeps(const PcState* ps, int m) {
+  return sizeof(P) == 4 && ps->tma_ok[m];
+}
+
+// red-black sweeps on box level m: the one-launch TMA sweep where the level
+// allows it, else two colour passes in place (from_scratch is then false)
+template <class P>
+void rb_sweeps(const PcState* ps, int m, const BoxK<P>& V, P* scratch, int sweeps, int c0,
+               bool zero, bool from_scratch, const uint8_t* mask, P* addu, cudaStream_t s) {
+  if constexpr (sizeof(P) == 4) {
+    if (ps->tma_ok[m]) {
+      box_sweeps(ps, m, V, scratch, sweeps, c0, zero, from_scratch, mask, addu, s);
+      return;
+    }
+  }
+  box_smooth(V, sweeps, c0 == 0, zero, mask, addu, s);
+}
+
+
 
 // ---- the coarse end of the GMG V-cycle in one kernel
 // Levels tail_m .. nmg-1 are small (at most 8,192 cells per field): one CTA
@@ -1617,12 +1810,12 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   if (m == ps->nmg - 1) {
     if (ps->csw == 0) zero_e();   // no correction
     else if (jac) box_jacobi(V, omega, scratch, ps->csw, true, false, mask, addu, s);
-    else box_sweeps(V, scratch, ps->csw, 0, true, false, mask, addu, s);
+    else rb_sweeps<P>(ps, m, V, scratch, ps->csw, 0, true, false, mask, addu, s);
     return;
   }
   if (ps->nu1 == 0) zero_e();
   else if (jac) box_jacobi(V, omega, scratch, ps->nu1, true, false, nullptr, (P*)nullptr, s);
-  else box_sweeps(V, scratch, ps->nu1, 0, true, false, nullptr, (P*)nullptr, s);
+  else rb_sweeps<P>(ps, m, V, scratch, ps->nu1, 0, true, false, nullptr, (P*)nullptr, s);
   const BoxRaw& C = ps->box[m + 1];
   const dim3 gc = restrict_grid(C.n[0], C.n[1], C.n[2]);
   // after a red-first Gauss-Seidel sweep the black residuals are zero
@@ -1633,7 +1826,8 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   gmg_vcycle<P>(ps, H, m + 1, s);
   // e + P e_c: into the scratch when an odd number of sweeps follows, so
   // that the last one writes e
-  const bool to_scratch = ps->nu2 > 0 && start_in_scratch(ps->nu2);
+  const bool to_scratch =
+      (jac || fused_sweeps<P>(ps, m)) && ps->nu2 > 0 && start_in_scratch(ps->nu2);
   k_bprolong<P><<<tile_grid(B.n[0], B.n[1], B.n[2]), FTHREADS, 0, s>>>(
       (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V, to_scratch ? scratch : V.e);
   if (ps->nu2 == 0) {
@@ -1641,7 +1835,7 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   } else if (jac) {
     box_jacobi(V, omega, scratch, ps->nu2, false, to_scratch, mask, addu, s);
   } else {
-    box_sweeps(V, scratch, ps->nu2, 1, false, to_scratch, mask, addu, s);
+    rb_sweeps<P>(ps, m, V, scratch, ps->nu2, 1, false, to_scratch, mask, addu, s);
   }
 }
 
@@ -1784,9 +1978,10 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
     }
   }
   if (transposed)
-    k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y);
+    k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y, ps->d_err);
   else
-    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, (const P*)ps->p2, y, jd, jstride, y2);
+    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, (const P*)ps->p2, y, jd, jstride, y2,
+                                   ps->d_err);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }
 
@@ -1798,6 +1993,65 @@ void scale_all(PcState* ps, const Hier& H, SetupArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+// cuTensorMapEncodeTiled from the driver (through the runtime: no link to
+// libcuda); null when the driver does not offer it
+using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeFn tmap_encoder() {
+  static EncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(f);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// tensor map of an FP32 n0 x n1 x n2 array (x fastest) at base, with a
+// TBX x by x bz box; false when TMA cannot address it (base or row stride
+// not 16-byte aligned) or the encoding is refused
+bool tmap3(CUtensorMap* m, const float* base, const int n[3], int by, int bz) {
+  EncodeFn enc = tmap_encoder();
+  if (!enc || (reinterpret_cast<uintptr_t>(base) & 15) || (n[0] % 4) != 0) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)n[0], (cuuint64_t)n[1], (cuuint64_t)n[2]};
+  cuuint64_t strides[2] = {(cuuint64_t)n[0] * 4, (cuuint64_t)n[0] * n[1] * 4};
+  cuuint32_t box[3] = {(cuuint32_t)TBX, (cuuint32_t)by, (cuuint32_t)bz};
+  cuuint32_t es[3] = {1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box,
+             es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// tensor maps of FP32 box level m for k_bsweep (levels of at least 32 x 8 x 8
+// cells; the smaller ones keep the two-pass kernel)
+void setup_sweep_maps(PcState* ps, const Hier& H, int m) {
+  ps->tma_ok[m] = false;
+  if (ps->prec != NRD_PC_F32) return;
+  const BoxRaw B = (m == 0) ? level0_box(H) : ps->box[m];
+  if (B.n[0] < 32 || B.n[1] < 8 || B.n[2] < 8) return;
+  const long vfs = (m == 0) ? H.N : (long)B.n[0] * B.n[1] * B.n[2];
+  const float* e = (const float*)((m == 0) ? ps->fe : ps->be[m]);
+  const float* sc = (const float*)((m == 0) ? ps->fj : ps->bj[m]);
+  const float* f = (const float*)((m == 0) ? ps->fr : ps->bf[m]);
+  const float* A = (const float*)((m == 0) ? ps->A : ps->bA[m]);
+  bool ok = true;
+  for (int fld = 0; fld < 2 && ok; fld++) {
+    ok = tmap3(&ps->tm_e[m][0][fld], e + fld * vfs, B.n, SY + 4, SZ + 4) &&
+         tmap3(&ps->tm_e[m][1][fld], sc + fld * vfs, B.n, SY + 4, SZ + 4) &&
+         tmap3(&ps->tm_f[m][fld], f + fld * vfs, B.n, SY + 2, SZ + 2) &&
+         tmap3(&ps->tm_a[m][0][fld], A + fld * B.AF, B.n, SY + 2, SZ + 2) &&
+         tmap3(&ps->tm_a[m][1][fld], A + fld * B.AF + B.NA, B.n, SY + 3, SZ + 2) &&
+         tmap3(&ps->tm_a[m][2][fld], A + fld * B.AF + 2 * B.NA, B.n, SY + 2, SZ + 3);
+  }
+  ps->tma_ok[m] = ok;
+}
 
 int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err) {
   PcState* ps = new PcState();
@@ -1909,10 +2163,21 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
       cudaMemset(ps->bA[m], 0, 2 * B.AF * e);
     }
   }
+  if (ok) ok = cudaMalloc(&ps->d_err, sizeof(int)) == cudaSuccess &&
+               cudaMemset(ps->d_err, 0, sizeof(int)) == cudaSuccess;
   if (!ok) {
     pc_free(ps);
     err = "preconditioner allocation failed";
     return NRD_ENOMEM;
+  }
+  // the one-launch red-black sweep on the FP32 box levels TMA can address
+  // (attributes set here, outside any stream capture)
+  if (ps->prec == NRD_PC_F32) {
+    cudaFuncSetAttribute(k_bsweep<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
+    cudaFuncSetAttribute(k_bsweep<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
+    cudaFuncSetAttribute(k_bsweep<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
+    cudaFuncSetAttribute(k_bsweep<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
+    for (int m = 0; m < ps->nmg; m++) setup_sweep_maps(ps, H, m);
   }
   // the coarsest box levels whose data fit one CTA's shared memory run as
   // one kernel (the first such level with at most 8,192 cells per field),
@@ -1972,6 +2237,7 @@ void pc_free(PcState* ps) {
   auto F = [](void* p) { if (p) cudaFree(p); };
   F(ps->Craw); F(ps->A); F(ps->fu); F(ps->fr); F(ps->fe); F(ps->fp); F(ps->fj); F(ps->ff); F(ps->gh);
   F(ps->cf); F(ps->Tk); F(ps->bgt); F(ps->d_beta); F(ps->p2); F(ps->vt); F(ps->gsrc); F(ps->gwp);
+  F(ps->d_err);
   pc_drop_graphs(ps);
   if (ps->cap) cudaStreamDestroy(ps->cap);
   for (int m = 0; m < NRD_MAX_MG; m++) {
