@@ -171,8 +171,8 @@ constexpr int OFF_F = up128(E_BYTES);
 constexpr int OFF_AX = OFF_F + up128(F_BYTES);
 constexpr int OFF_AY = OFF_AX + up128(F_BYTES);
 constexpr int OFF_AZ = OFF_AY + up128(AY_BYTES);
-constexpr int OFF_BAR = OFF_AZ + up128(AZ_BYTES);
-constexpr int SWEEP_SMEM = OFF_BAR + 16;
+constexpr int STAGE_BYTES = OFF_AZ + up128(AZ_BYTES);      // one tile's boxes
+constexpr int SWEEP_SMEM = 2 * STAGE_BYTES + 16;            // two stages + two mbarriers
 constexpr long kTmaSpinLimit = 1L << 24;
 
 struct SweepMaps {                 // per field: old correction, rhs, x/y/z low faces
@@ -193,16 +193,16 @@ __device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, 
       : "memory");
 }
 
-// wait for phase 0 of the mbarrier, at most kTmaSpinLimit polls; false if
-// the wait ran out
-__device__ __forceinline__ bool mbar_wait0(uint32_t bar) {
+// wait for the phase of the given parity of the mbarrier to complete, at
+// most kTmaSpinLimit polls; false if the wait ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   for (long it = 0; it < kTmaSpinLimit; it++) {
     uint32_t done;
     asm volatile(
-        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0; "
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; "
         "selp.u32 %0, 1, 0, p; }"
         : "=r"(done)
-        : "r"(bar)
+        : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
     if (it > 64) __nanosleep(32);
@@ -235,102 +235,133 @@ __device__ __forceinline__ void box_row_s(const BoxK<float>& B, const float* A, 
   of = o;
 }
 
-// grid (ceil(n0 / SX), ceil(n1 / SY), 2 ceil(n2 / SZ)), the upper half of z
-// for field 1; SWEEP_SMEM bytes of dynamic shared memory.  The tile origin
-// is even on every axis, so the colour of the cell at (x, y, z) in the
-// one-ring frame (origin one cell before the tile) is (x + y + z + 1) mod 2.
+// Persistent: a grid of at most one CTA per SM walks the tiles (x fastest,
+// then y, z, field), two stages deep: while one tile is computed the TMA
+// loads of the next land in the other stage.  ntile = 2 ntx nty ntz; SWEEP_SMEM
+// bytes of dynamic shared memory.  The tile origin is even on every axis, so
+// the colour of the cell at (x, y, z) in the one-ring frame (origin one cell
+// before the tile) is (x + y + z + 1) mod 2.
+// ADD stores the correction into u: on level 0's uncovered cells the
+// composite solution is still zero when level 0 is corrected (the finer
+// levels' corrections touch only their own cells), so u += e there is u = e.
 template <bool ZERO, bool ADD>
-__global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant__ SweepMaps M,
-                                                           BoxK<float> B, int c0,
+__global__ void __launch_bounds__(SW_THREADS, 1) k_bsweep(const __grid_constant__ SweepMaps M,
+                                                           BoxK<float> B, int c0, int ntx,
+                                                           int nty, int ntz,
                                                            float* __restrict__ ed,
                                                            const uint8_t* __restrict__ mask,
                                                            float* __restrict__ u,
                                                            int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  float (*Se)[EBY][TBX] = reinterpret_cast<float (*)[EBY][TBX]>(smem);
-  float (*Sf)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(smem + OFF_F);
-  float (*Sx)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(smem + OFF_AX);
-  float (*Sy)[FBY + 1][TBX] = reinterpret_cast<float (*)[FBY + 1][TBX]>(smem + OFF_AY);
-  float (*Sz)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(smem + OFF_AZ);
-  const uint32_t bar = smem_u32(smem + OFF_BAR);
-  const int ntz = gridDim.z >> 1;
-  const int fld = blockIdx.z >= ntz;
-  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, z0 = (blockIdx.z - fld * ntz) * SZ;
+  const uint32_t bar0 = smem_u32(smem + 2 * STAGE_BYTES);
   const int t = threadIdx.x;
   const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
-  const float* A = B.A + fld * B.Afs;
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
-  if (t == 0) {
+  const int per_fld = ntx * nty * ntz, ntile = 2 * per_fld;
+  auto origin = [&](int q, int& fld, int& x0, int& y0, int& z0) {
+    fld = q / per_fld;
+    const int r = q - fld * per_fld;
+    x0 = (r % ntx) * SX;
+    y0 = ((r / ntx) % nty) * SY;
+    z0 = (r / (ntx * nty)) * SZ;
+  };
+  // thread 0: start the loads of tile q into stage st
+  auto issue = [&](int q, int st) {
+    int fld, x0, y0, z0;
+    origin(q, fld, x0, y0, z0);
+    unsigned char* base = smem + st * STAGE_BYTES;
+    const uint32_t bar = bar0 + 8 * st;
     const uint32_t bytes = (ZERO ? 0 : E_BYTES) + 2 * F_BYTES + AY_BYTES + AZ_BYTES;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
-    if (!ZERO) tma_load3(smem_u32(smem), &M.es[fld], x0 - 4, y0 - 2, z0 - 2, bar);
-    tma_load3(smem_u32(smem + OFF_F), &M.f[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-    tma_load3(smem_u32(smem + OFF_AX), &M.ax[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-    tma_load3(smem_u32(smem + OFF_AY), &M.ay[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-    tma_load3(smem_u32(smem + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    if (!ZERO) tma_load3(smem_u32(base), &M.es[fld], x0 - 4, y0 - 2, z0 - 2, bar);
+    tma_load3(smem_u32(base + OFF_F), &M.f[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(base + OFF_AX), &M.ax[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(base + OFF_AY), &M.ay[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(base + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+  };
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if ((int)blockIdx.x < ntile) issue(blockIdx.x, 0);
   }
-  const bool late = !mbar_wait0(bar);
-  if (__syncthreads_or(late)) {
-    // the copies did not land in time: report, give them a second bounded
-    // wait (they write this CTA's shared memory), and stop
-    if (t == 0) atomicOr(err, 2);
-    mbar_wait0(bar);
-    return;
-  }
-  // first colour on the tile and the one-cell ring: 17 cells of the colour
-  // in each 34-cell row of the ring frame
-  for (int q = t; q < 17 * FBY * FBZ; q += SW_THREADS) {
-    const int row = q / 17, y = row % FBY, z = row / FBY;
-    const int x = 2 * (q % 17) + ((c0 + 1 + y + z) & 1);
-    const int i = x0 - 1 + x, j = y0 - 1 + y, k = z0 - 1 + z;
-    if (i < 0 || i >= n0 || j < 0 || j >= n1 || k < 0 || k >= n2) continue;
-    const int xb = x + 3;                                   // column in the 40-wide boxes
-    float xm = 0.0f, xp = 0.0f, ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
-    if (!ZERO) {
-      xm = Se[z + 1][y + 1][xb - 1];
-      xp = Se[z + 1][y + 1][xb + 1];
-      ym = Se[z + 1][y][xb];
-      yp = Se[z + 1][y + 2][xb];
-      zm = Se[z][y + 1][xb];
-      zp = Se[z + 2][y + 1][xb];
+  __syncthreads();
+  int it = 0;
+  for (int q = blockIdx.x; q < ntile; q += gridDim.x, it++) {
+    const int st = it & 1;
+    // the next tile's loads go into the other stage, free since the end of
+    // the previous iteration
+    if (t == 0 && q + (int)gridDim.x < ntile) issue(q + gridDim.x, st ^ 1);
+    const bool late = !mbar_wait(bar0 + 8 * st, (it >> 1) & 1);
+    if (__syncthreads_or(late)) {
+      // the copies did not land in time: report, give every load in flight
+      // a second bounded wait (they write this CTA's shared memory), stop
+      if (t == 0) atomicOr(err, 2);
+      mbar_wait(bar0 + 8 * st, (it >> 1) & 1);
+      if (q + (int)gridDim.x < ntile) mbar_wait(bar0 + 8 * (st ^ 1), ((it + 1) >> 1) & 1);
+      return;
     }
-    float dg, of;
-    box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
-              Sz[z][y][xb], Sz[z + 1][y][xb], xm, xp, ym, yp, zm, zp, dg, of);
-    Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
-  }
-  __syncthreads();
-  // second colour on the tile: 16 cells of the colour in each 32-cell row
-  for (int q = t; q < (SX / 2) * SY * SZ; q += SW_THREADS) {
-    const int row = q / (SX / 2), yi = row % SY, zi = row / SY;
-    const int xi = 2 * (q % (SX / 2)) + ((c0 + 1 + yi + zi) & 1);
-    const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
-    if (i >= n0 || j >= n1 || k >= n2) continue;
-    const int x = xi + 1, y = yi + 1, z = zi + 1, xb = x + 3;
-    float dg, of;
-    box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
-              Sz[z][y][xb], Sz[z + 1][y][xb], Se[z + 1][y + 1][xb - 1], Se[z + 1][y + 1][xb + 1],
-              Se[z + 1][y][xb], Se[z + 1][y + 2][xb], Se[z][y + 1][xb], Se[z + 2][y + 1][xb], dg,
-              of);
-    Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
-  }
-  __syncthreads();
-  // the tile, both colours, in rows of 32
-  const long fo = (long)fld * B.vfs;
-  for (int q = t; q < SX * SY * SZ; q += SW_THREADS) {
-    const int xi = q % SX, r = q / SX, yi = r % SY, zi = r / SY;
-    const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
-    if (i >= n0 || j >= n1 || k >= n2) continue;
-    const int idx = i + n0 * (j + n1 * k);
-    const float v = Se[zi + 2][yi + 2][xi + 4];
-    ed[fo + idx] = v;
-    if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] += v;
+    unsigned char* base = smem + st * STAGE_BYTES;
+    float (*Se)[EBY][TBX] = reinterpret_cast<float (*)[EBY][TBX]>(base);
+    float (*Sf)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(base + OFF_F);
+    float (*Sx)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(base + OFF_AX);
+    float (*Sy)[FBY + 1][TBX] = reinterpret_cast<float (*)[FBY + 1][TBX]>(base + OFF_AY);
+    float (*Sz)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(base + OFF_AZ);
+    int fld, x0, y0, z0;
+    origin(q, fld, x0, y0, z0);
+    const float* A = B.A + fld * B.Afs;
+    // first colour on the tile and the one-cell ring: 17 cells of the colour
+    // in each 34-cell row of the ring frame
+    for (int p = t; p < 17 * FBY * FBZ; p += SW_THREADS) {
+      const int row = p / 17, y = row % FBY, z = row / FBY;
+      const int x = 2 * (p % 17) + ((c0 + 1 + y + z) & 1);
+      const int i = x0 - 1 + x, j = y0 - 1 + y, k = z0 - 1 + z;
+      if (i < 0 || i >= n0 || j < 0 || j >= n1 || k < 0 || k >= n2) continue;
+      const int xb = x + 3;                                 // column in the 40-wide boxes
+      float xm = 0.0f, xp = 0.0f, ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+      if (!ZERO) {
+        xm = Se[z + 1][y + 1][xb - 1];
+        xp = Se[z + 1][y + 1][xb + 1];
+        ym = Se[z + 1][y][xb];
+        yp = Se[z + 1][y + 2][xb];
+        zm = Se[z][y + 1][xb];
+        zp = Se[z + 2][y + 1][xb];
+      }
+      float dg, of;
+      box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
+                Sz[z][y][xb], Sz[z + 1][y][xb], xm, xp, ym, yp, zm, zp, dg, of);
+      Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
+    }
+    __syncthreads();
+    // second colour on the tile: 16 cells of the colour in each 32-cell row
+    for (int p = t; p < (SX / 2) * SY * SZ; p += SW_THREADS) {
+      const int row = p / (SX / 2), yi = row % SY, zi = row / SY;
+      const int xi = 2 * (p % (SX / 2)) + ((c0 + 1 + yi + zi) & 1);
+      const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
+      if (i >= n0 || j >= n1 || k >= n2) continue;
+      const int x = xi + 1, y = yi + 1, z = zi + 1, xb = x + 3;
+      float dg, of;
+      box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
+                Sz[z][y][xb], Sz[z + 1][y][xb], Se[z + 1][y + 1][xb - 1],
+                Se[z + 1][y + 1][xb + 1], Se[z + 1][y][xb], Se[z + 1][y + 2][xb],
+                Se[z][y + 1][xb], Se[z + 2][y + 1][xb], dg, of);
+      Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
+    }
+    __syncthreads();
+    // the tile, both colours, in rows of 32
+    const long fo = (long)fld * B.vfs;
+    for (int p = t; p < SX * SY * SZ; p += SW_THREADS) {
+      const int xi = p % SX, r = p / SX, yi = r % SY, zi = r / SY;
+      const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
+      if (i >= n0 || j >= n1 || k >= n2) continue;
+      const int idx = i + n0 * (j + n1 * k);
+      const float v = Se[zi + 2][yi + 2][xi + 4];
+      ed[fo + idx] = v;
+      if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] = v;
+    }
+    // every thread is done with this stage before its next loads are issued
+    __syncthreads();
   }
 }
 
@@ -1277,6 +1308,7 @@ struct PcState {
   CUtensorMap tm_f[NRD_MAX_MG][2];
   CUtensorMap tm_a[NRD_MAX_MG][3][2];
   int* d_err = nullptr;  // set when a TMA wait of the V-cycle gave up
+  int nsm = 152;         // SMs of the device (persistent sweep grid)
 };
 
 namespace {
@@ -1351,7 +1383,9 @@ void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bo
 // adds the correction to u on uncovered cells (level 0)
 void box_sweeps(const PcState* ps, int m, const BoxK<float>& V, float* scratch, int sweeps, int c0,
                 bool zero, bool from_scratch, const uint8_t* mask, float* addu, cudaStream_t s) {
-  const dim3 g((V.n0 + SX - 1) / SX, (V.n1 + SY - 1) / SY, 2 * ((V.n2 + SZ - 1) / SZ));
+  const int ntx = (V.n0 + SX - 1) / SX, nty = (V.n1 + SY - 1) / SY, ntz = (V.n2 + SZ - 1) / SZ;
+  const int ntile = 2 * ntx * nty * ntz;
+  const int g = std::min(ntile, ps->nsm);
   float* buf[2] = {V.e, scratch};
   SweepMaps M;
   for (int fld = 0; fld < 2; fld++) {
@@ -1367,13 +1401,13 @@ void box_sweeps(const PcState* ps, int m, const BoxK<float>& V, float* scratch, 
   for (int sw = 0; sw < sweeps; sw++) {
     const bool D = addu && sw == sweeps - 1;
     if (zero && sw == 0) {
-      if (D) k_bsweep<true, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[cur], mask, addu, ps->d_err);
-      else k_bsweep<true, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[cur], mask, addu, ps->d_err);
+      if (D) k_bsweep<true, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[cur], mask, addu, ps->d_err);
+      else k_bsweep<true, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[cur], mask, addu, ps->d_err);
       continue;
     }
     src(cur);
-    if (D) k_bsweep<false, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[1 - cur], mask, addu, ps->d_err);
-    else k_bsweep<false, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[1 - cur], mask, addu, ps->d_err);
+    if (D) k_bsweep<false, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[1 - cur], mask, addu, ps->d_err);
+    else k_bsweep<false, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[1 - cur], mask, addu, ps->d_err);
     cur = 1 - cur;
   }
 }
@@ -2173,6 +2207,9 @@ int pc_alloc(PcState** out, const Hier& H, const nrd_params& p, std::string& err
   // the one-launch red-black sweep on the FP32 box levels TMA can address
   // (attributes set here, outside any stream capture)
   if (ps->prec == NRD_PC_F32) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+      cudaDeviceGetAttribute(&ps->nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(k_bsweep<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
     cudaFuncSetAttribute(k_bsweep<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
     cudaFuncSetAttribute(k_bsweep<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SWEEP_SMEM);
