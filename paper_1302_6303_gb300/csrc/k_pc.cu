@@ -138,8 +138,9 @@ __global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, con
 // (FP32 boxes whose arrays TMA can address).  The sweep reads the correction
 // es (or zero) and writes ed (ed != es): first every cell of colour c0 from
 // the old values of its neighbours (which have the other colour), then every
-// cell of colour 1 - c0 from the new ones, the same arithmetic per cell as
-// two colour passes of k_bsmooth.  A CTA owns a 32 x 8 x 8 tile.  One thread
+// cell of colour 1 - c0 from the new ones, as two colour passes of
+// k_bsmooth do (the division as a multiplication by the reciprocal of the
+// diagonal, which is at least 1).  A CTA owns a 32 x 8 x 8 tile.  One thread
 // starts five TMA box loads into shared memory: the old correction over the
 // tile and a two-cell ring, and the rhs and the three low-face coefficient
 // arrays over the tile and a one-cell ring (plus the high faces of the
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, con
 // ZERO: es = 0 (the first sweep of a level; no load).  ADD: u += ed on
 // uncovered cells (the last sweep on level 0, in the hierarchy vectors).
 constexpr int SX = 32, SY = 8, SZ = 8;
-constexpr int SW_THREADS = 512;
+constexpr int SW_THREADS = 1024;
 constexpr int TBX = 40;                                      // box width in x (from x0 - 4)
 constexpr int EBY = SY + 4, EBZ = SZ + 4;                    // correction box: two-cell ring
 constexpr int FBY = SY + 2, FBZ = SZ + 2;                    // rhs / coefficient boxes
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_bsweep(const __grid_constant_
       float dg, of;
       box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
                 Sz[z][y][xb], Sz[z + 1][y][xb], xm, xp, ym, yp, zm, zp, dg, of);
-      Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
+      Se[z + 1][y + 1][xb] = __fdividef(Sf[z][y][xb] + of, dg);
     }
     __syncthreads();
     // second colour on the tile: 16 cells of the colour in each 32-cell row
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_bsweep(const __grid_constant_
                 Sz[z][y][xb], Sz[z + 1][y][xb], Se[z + 1][y + 1][xb - 1],
                 Se[z + 1][y + 1][xb + 1], Se[z + 1][y][xb], Se[z + 1][y + 2][xb],
                 Se[z][y + 1][xb], Se[z + 2][y + 1][xb], dg, of);
-      Se[z + 1][y + 1][xb] = (Sf[z][y][xb] + of) / dg;
+      Se[z + 1][y + 1][xb] = __fdividef(Sf[z][y][xb] + of, dg);
     }
     __syncthreads();
     // the tile, both colours, in rows of 32
