@@ -236,6 +236,48 @@ __device__ __forceinline__ void box_row_s(const BoxK<float>& B, const float* A, 
   of = o;
 }
 
+constexpr int EPL = EBY * TBX;          // plane strides of the boxes in shared memory
+constexpr int FPL = FBY * TBX;
+constexpr int YPL = (FBY + 1) * TBX;
+
+// one Gauss-Seidel update of cell (i, j, k) from the shared boxes: oe its
+// offset in the correction box, of in the rhs / x-face / z-face boxes, oy in
+// the y-face box.  CHECK: the cell may lie on a domain face (box_row_s);
+// else all six neighbours are in the box (the same operations in the same
+// order).  ZERO: the neighbours' old values are zero.
+template <bool CHECK, bool ZERO>
+__device__ __forceinline__ void rb_update(const BoxK<float>& B, const float* A, float* Se,
+                                          const float* Sf, const float* Sx, const float* Sy,
+                                          const float* Sz, int oe, int of, int oy, int i, int j,
+                                          int k) {
+  const float axl = Sx[of], axh = Sx[of + 1], ayl = Sy[oy], ayh = Sy[oy + TBX];
+  const float azl = Sz[of], azh = Sz[of + FPL];
+  float xm = 0.0f, xp = 0.0f, ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
+  if (!ZERO) {
+    xm = Se[oe - 1];
+    xp = Se[oe + 1];
+    ym = Se[oe - TBX];
+    yp = Se[oe + TBX];
+    zm = Se[oe - EPL];
+    zp = Se[oe + EPL];
+  }
+  float dg, o;
+  if (CHECK) {
+    box_row_s(B, A, i, j, k, axl, axh, ayl, ayh, azl, azh, xm, xp, ym, yp, zm, zp, dg, o);
+  } else {
+    float d = 1.0f;
+    o = 0.0f;
+    d += axl; o += axl * xm;
+    d += axh; o += axh * xp;
+    d += ayl; o += ayl * ym;
+    d += ayh; o += ayh * yp;
+    d += azl; o += azl * zm;
+    d += azh; o += azh * zp;
+    dg = d;
+  }
+  Se[oe] = __fdividef(Sf[of] + o, dg);
+}
+
 // Persistent: a grid of at most one CTA per SM walks the tiles (x fastest,
 // then y, z, field), two stages deep: while one tile is computed the TMA
 // loads of the next land in the other stage.  ntile = 2 ntx nty ntz; SWEEP_SMEM
@@ -288,6 +330,23 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_bsweep(const __grid_constant_
     if ((int)blockIdx.x < ntile) issue(blockIdx.x, 0);
   }
   __syncthreads();
+  // thread -> cells, the same for every tile (tile origins are even):
+  // first colour: column (x1, y1) of the 34 x 10 ring frame, planes
+  // [5 zh, 5 zh + 5) of it, those of the colour every other plane;
+  // second colour: column (x2, y2) of the tile, planes [4 zh, 4 zh + 4);
+  // write: column (x3, y3), planes z3, z3 + 1
+  const int c1 = t % (FBY * (SX + 2)), zh1 = t / (FBY * (SX + 2));
+  const bool c1ok = t < 2 * FBY * (SX + 2);
+  const int x1 = c1 % (SX + 2), y1 = c1 / (SX + 2);
+  const int z1s = 5 * zh1 + ((c0 + 1 + x1 + y1 + zh1) & 1), z1e = 5 * zh1 + 5;
+  const int oe1 = EPL + (y1 + 1) * TBX + x1 + 3, of1 = y1 * TBX + x1 + 3, oy1 = of1;
+  const bool c2ok = t < 2 * SX * SY;
+  const int x2 = t & (SX - 1), y2 = (t / SX) % SY, zh2 = t / (SX * SY);
+  const int z2s = 4 * zh2 + ((c0 + 1 + x2 + y2) & 1), z2e = 4 * zh2 + 4;
+  const int oe2 = 2 * EPL + (y2 + 2) * TBX + x2 + 4, of2 = FPL + (y2 + 1) * TBX + x2 + 4,
+            oy2 = YPL + (y2 + 1) * TBX + x2 + 4;
+  const int x3 = t & (SX - 1), y3 = (t / SX) % SY, z3 = 2 * (t / (SX * SY));
+  const int oe3 = (z3 + 2) * EPL + (y3 + 2) * TBX + x3 + 4;
   int it = 0;
   for (int q = blockIdx.x; q < ntile; q += gridDim.x, it++) {
     const int st = it & 1;
@@ -304,62 +363,66 @@ __global__ void __launch_bounds__(SW_THREADS, 1) k_bsweep(const __grid_constant_
       return;
     }
     unsigned char* base = smem + st * STAGE_BYTES;
-    float (*Se)[EBY][TBX] = reinterpret_cast<float (*)[EBY][TBX]>(base);
-    float (*Sf)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(base + OFF_F);
-    float (*Sx)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(base + OFF_AX);
-    float (*Sy)[FBY + 1][TBX] = reinterpret_cast<float (*)[FBY + 1][TBX]>(base + OFF_AY);
-    float (*Sz)[FBY][TBX] = reinterpret_cast<float (*)[FBY][TBX]>(base + OFF_AZ);
+    float* Se = reinterpret_cast<float*>(base);
+    const float* Sf = reinterpret_cast<const float*>(base + OFF_F);
+    const float* Sx = reinterpret_cast<const float*>(base + OFF_AX);
+    const float* Sy = reinterpret_cast<const float*>(base + OFF_AY);
+    const float* Sz = reinterpret_cast<const float*>(base + OFF_AZ);
     int fld, x0, y0, z0;
     origin(q, fld, x0, y0, z0);
     const float* A = B.A + fld * B.Afs;
-    // first colour on the tile and the one-cell ring: 17 cells of the colour
-    // in each 34-cell row of the ring frame
-    for (int p = t; p < 17 * FBY * FBZ; p += SW_THREADS) {
-      const int row = p / 17, y = row % FBY, z = row / FBY;
-      const int x = 2 * (p % 17) + ((c0 + 1 + y + z) & 1);
-      const int i = x0 - 1 + x, j = y0 - 1 + y, k = z0 - 1 + z;
-      if (i < 0 || i >= n0 || j < 0 || j >= n1 || k < 0 || k >= n2) continue;
-      const int xb = x + 3;                                 // column in the 40-wide boxes
-      float xm = 0.0f, xp = 0.0f, ym = 0.0f, yp = 0.0f, zm = 0.0f, zp = 0.0f;
-      if (!ZERO) {
-        xm = Se[z + 1][y + 1][xb - 1];
-        xp = Se[z + 1][y + 1][xb + 1];
-        ym = Se[z + 1][y][xb];
-        yp = Se[z + 1][y + 2][xb];
-        zm = Se[z][y + 1][xb];
-        zp = Se[z + 2][y + 1][xb];
+    // tiles whose cells and ring all have six in-box neighbours skip the
+    // boundary tests
+    const bool inner = x0 >= 2 && x0 + SX + 1 < n0 && y0 >= 2 && y0 + SY + 1 < n1 && z0 >= 2 &&
+                       z0 + SZ + 1 < n2;
+    // first colour on the tile and the one-cell ring: thread column (x1, y1)
+    // of the ring frame, z in its half, every other plane
+    if (c1ok) {
+      const int i = x0 - 1 + x1, j = y0 - 1 + y1;
+      if (inner) {
+        for (int z = z1s; z < z1e; z += 2)
+          rb_update<false, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
+                                 oy1 + z * YPL, i, j, z0 - 1 + z);
+      } else if (i >= 0 && i < n0 && j >= 0 && j < n1) {
+        for (int z = z1s; z < z1e; z += 2) {
+          const int k = z0 - 1 + z;
+          if (k >= 0 && k < n2)
+            rb_update<true, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
+                                  oy1 + z * YPL, i, j, k);
+        }
       }
-      float dg, of;
-      box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
-                Sz[z][y][xb], Sz[z + 1][y][xb], xm, xp, ym, yp, zm, zp, dg, of);
-      Se[z + 1][y + 1][xb] = __fdividef(Sf[z][y][xb] + of, dg);
     }
     __syncthreads();
-    // second colour on the tile: 16 cells of the colour in each 32-cell row
-    for (int p = t; p < (SX / 2) * SY * SZ; p += SW_THREADS) {
-      const int row = p / (SX / 2), yi = row % SY, zi = row / SY;
-      const int xi = 2 * (p % (SX / 2)) + ((c0 + 1 + yi + zi) & 1);
-      const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
-      if (i >= n0 || j >= n1 || k >= n2) continue;
-      const int x = xi + 1, y = yi + 1, z = zi + 1, xb = x + 3;
-      float dg, of;
-      box_row_s(B, A, i, j, k, Sx[z][y][xb], Sx[z][y][xb + 1], Sy[z][y][xb], Sy[z][y + 1][xb],
-                Sz[z][y][xb], Sz[z + 1][y][xb], Se[z + 1][y + 1][xb - 1],
-                Se[z + 1][y + 1][xb + 1], Se[z + 1][y][xb], Se[z + 1][y + 2][xb],
-                Se[z][y + 1][xb], Se[z + 2][y + 1][xb], dg, of);
-      Se[z + 1][y + 1][xb] = __fdividef(Sf[z][y][xb] + of, dg);
+    // second colour on the tile: thread column (x2, y2), z in its half
+    if (c2ok) {
+      const int i = x0 + x2, j = y0 + y2;
+      if (inner) {
+        for (int z = z2s; z < z2e; z += 2)
+          rb_update<false, false>(B, A, Se, Sf, Sx, Sy, Sz, oe2 + z * EPL, of2 + z * FPL,
+                                  oy2 + z * YPL, i, j, z0 + z);
+      } else if (i < n0 && j < n1) {
+        for (int z = z2s; z < z2e; z += 2)
+          if (z0 + z < n2)
+            rb_update<true, false>(B, A, Se, Sf, Sx, Sy, Sz, oe2 + z * EPL, of2 + z * FPL,
+                                   oy2 + z * YPL, i, j, z0 + z);
+      }
     }
     __syncthreads();
-    // the tile, both colours, in rows of 32
-    const long fo = (long)fld * B.vfs;
-    for (int p = t; p < SX * SY * SZ; p += SW_THREADS) {
-      const int xi = p % SX, r = p / SX, yi = r % SY, zi = r / SY;
-      const int i = x0 + xi, j = y0 + yi, k = z0 + zi;
-      if (i >= n0 || j >= n1 || k >= n2) continue;
-      const int idx = i + n0 * (j + n1 * k);
-      const float v = Se[zi + 2][yi + 2][xi + 4];
-      ed[fo + idx] = v;
-      if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] = v;
+    // the tile, both colours: rows of 32, two planes per thread
+    {
+      const long fo = (long)fld * B.vfs;
+      const int i = x0 + x3, j = y0 + y3;
+      if (i < n0 && j < n1) {
+#pragma unroll
+        for (int dz = 0; dz < 2; dz++) {
+          const int k = z0 + z3 + dz;
+          if (k >= n2) break;
+          const int idx = i + n0 * (j + n1 * k);
+          const float v = Se[oe3 + dz * EPL];
+          ed[fo + idx] = v;
+          if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] = v;
+        }
+      }
     }
     // every thread is done with this stage before its next loads are issued
     __syncthreads();
