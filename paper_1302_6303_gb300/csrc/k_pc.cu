@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, con
 // the old values of its neighbours (which have the other colour), then every
 // cell of colour 1 - c0 from the new ones, as two colour passes of
 // k_bsmooth do (the division as a multiplication by the reciprocal of the
-// diagonal, which is at least 1).  A CTA owns a 32 x 8 x 8 tile.  One thread
+// diagonal, which is at least 1).  A CTA owns a 32 x 8 x 4 tile.  One thread
 // starts five TMA box loads into shared memory: the old correction over the
 // tile and a two-cell ring, and the rhs and the three low-face coefficient
 // arrays over the tile and a one-cell ring (plus the high faces of the
@@ -158,15 +158,15 @@ __global__ void __launch_bounds__(VTHREADS) k_bsmooth(BoxK<P> B, int colour, con
 // slot coefficient, read from global memory).
 // ZERO: es = 0 (the first sweep of a level; no load).  ADD: u += ed on
 // uncovered cells (the last sweep on level 0, in the hierarchy vectors).
-constexpr int SX = 32, SY = 8, SZ = 8;
-constexpr int SW_THREADS = 512;
+constexpr int SX = 32, SY = 8, SZ = 4;
+constexpr int SW_THREADS = SX * SY;                          // one tile column per thread
 constexpr int TBX = 40;                                      // box width in x (from x0 - 4)
 constexpr int EBY = SY + 4, EBZ = SZ + 4;                    // correction box: two-cell ring
 constexpr int FBY = SY + 2, FBZ = SZ + 2;                    // rhs / coefficient boxes
-constexpr int E_BYTES = TBX * EBY * EBZ * 4;                 // 23040
-constexpr int F_BYTES = TBX * FBY * FBZ * 4;                 // 16000 (rhs, x faces)
-constexpr int AY_BYTES = TBX * (FBY + 1) * FBZ * 4;          // 17600 (y faces, one more row)
-constexpr int AZ_BYTES = TBX * FBY * (FBZ + 1) * 4;          // 17600 (z faces, one more plane)
+constexpr int E_BYTES = TBX * EBY * EBZ * 4;                 // correction
+constexpr int F_BYTES = TBX * FBY * FBZ * 4;                 // rhs, x faces
+constexpr int AY_BYTES = TBX * (FBY + 1) * FBZ * 4;          // y faces (one more row)
+constexpr int AZ_BYTES = TBX * FBY * (FBZ + 1) * 4;          // z faces (one more plane)
 constexpr int up128(int b) { return (b + 127) / 128 * 128; }
 constexpr int OFF_F = up128(E_BYTES);
 constexpr int OFF_AX = OFF_F + up128(F_BYTES);
@@ -278,15 +278,15 @@ __device__ __forceinline__ void rb_update(const BoxK<float>& B, const float* A, 
 }
 
 // Grid (ntx, nty, 2 ntz), one tile per CTA, the upper half of z for field 1;
-// SWEEP_SMEM bytes of dynamic shared memory, two CTAs per SM (one computes
-// while the other's loads land).  The tile origin is even on every axis, so
+// SWEEP_SMEM bytes of dynamic shared memory, four CTAs per SM (some compute
+// while the others' loads land).  The tile origin is even on every axis, so
 // the colour of the cell at (x, y, z) in the one-ring frame (origin one cell
 // before the tile) is (x + y + z + 1) mod 2.
 // ADD stores the correction into u: on level 0's uncovered cells the
 // composite solution is still zero when level 0 is corrected (the finer
 // levels' corrections touch only their own cells), so u += e there is u = e.
 template <bool ZERO, bool ADD>
-__global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant__ SweepMaps M,
+__global__ void __launch_bounds__(SW_THREADS, 4) k_bsweep(const __grid_constant__ SweepMaps M,
                                                            BoxK<float> B, int c0,
                                                            float* __restrict__ ed,
                                                            const uint8_t* __restrict__ mask,
@@ -312,21 +312,13 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant_
     tma_load3(smem_u32(smem + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
   }
   // thread -> cells (tile origins are even, so this is the same for every
-  // tile): first colour: column (x1, y1) of the 34 x 10 ring frame, all ten
-  // planes, those of the colour every other plane; second colour: column
-  // (x2, y2) of the tile, eight planes; write: column (x3, y3), planes
-  // z3 .. z3 + 3
-  const bool c1ok = t < FBY * (SX + 2);
-  const int x1 = t % (SX + 2), y1 = t / (SX + 2);
-  const int z1s = (c0 + 1 + x1 + y1) & 1;
-  const int oe1 = EPL + (y1 + 1) * TBX + x1 + 3, of1 = y1 * TBX + x1 + 3;
-  const bool c2ok = t < SX * SY;
-  const int x2 = t & (SX - 1), y2 = (t / SX) % SY;
+  // tile): first colour: columns t and t + SW_THREADS of the 34 x 10 ring
+  // frame, all planes, those of the colour every other plane; second colour
+  // and write: column (x2, y2) = t of the tile, all planes
+  const int x2 = t & (SX - 1), y2 = t / SX;
   const int z2s = (c0 + 1 + x2 + y2) & 1;
   const int oe2 = 2 * EPL + (y2 + 2) * TBX + x2 + 4, of2 = FPL + (y2 + 1) * TBX + x2 + 4,
             oy2 = YPL + (y2 + 1) * TBX + x2 + 4;
-  const int x3 = t & (SX - 1), y3 = (t / SX) % SY, z3 = 4 * (t / (SX * SY));
-  const int oe3 = (z3 + 2) * EPL + (y3 + 2) * TBX + x3 + 4;
   // everyone waits for the loads (the barrier's first phase); bounded
   __syncthreads();
   const bool late = !mbar_wait(bar, 0);
@@ -348,7 +340,10 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant_
   const bool inner = x0 >= 2 && x0 + SX + 1 < n0 && y0 >= 2 && y0 + SY + 1 < n1 && z0 >= 2 &&
                      z0 + SZ + 1 < n2;
   // first colour on the tile and the one-cell ring
-  if (c1ok) {
+  for (int c = t; c < FBY * (SX + 2); c += SW_THREADS) {
+    const int x1 = c % (SX + 2), y1 = c / (SX + 2);
+    const int z1s = (c0 + 1 + x1 + y1) & 1;
+    const int oe1 = EPL + (y1 + 1) * TBX + x1 + 3, of1 = y1 * TBX + x1 + 3;
     const int i = x0 - 1 + x1, j = y0 - 1 + y1;
     if (inner) {
 #pragma unroll
@@ -368,7 +363,7 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant_
   }
   __syncthreads();
   // second colour on the tile
-  if (c2ok) {
+  {
     const int i = x0 + x2, j = y0 + y2;
     if (inner) {
 #pragma unroll
@@ -385,16 +380,16 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant_
     }
   }
   __syncthreads();
-  // the tile, both colours: rows of 32, four planes per thread
+  // the tile, both colours: rows of 32, every plane
   const long fo = (long)fld * B.vfs;
-  const int i = x0 + x3, j = y0 + y3;
+  const int i = x0 + x2, j = y0 + y2;
   if (i < n0 && j < n1) {
 #pragma unroll
-    for (int dz = 0; dz < SZ / 2; dz++) {
-      const int k = z0 + z3 + dz;
+    for (int dz = 0; dz < SZ; dz++) {
+      const int k = z0 + dz;
       if (k >= n2) break;
       const int idx = i + n0 * (j + n1 * k);
-      const float v = Se[oe3 + dz * EPL];
+      const float v = Se[2 * EPL + (y2 + 2) * TBX + x2 + 4 + dz * EPL];
       ed[fo + idx] = v;
       if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] = v;
     }
