@@ -131,6 +131,77 @@ inline Dual fabs(Dual a) {
 using std::sqrt;
 using std::fabs;
 
+// Sparse forward mode: a value with its derivatives with respect to every
+// input of the residual (sorted (input, derivative) pairs).  Evaluating the
+// residual code once with every input seeded by its own index gives every
+// row of the Jacobian, with its sparsity, by the same chain rule as Dual.
+struct SDual {
+  double v;
+  std::vector<std::pair<long, double>> d;
+  SDual() : v(0) {}
+  SDual(double a) : v(a) {}
+};
+// ca * a + cb * b on sorted derivative lists
+inline std::vector<std::pair<long, double>> sd_comb(const std::vector<std::pair<long, double>>& a,
+                                                    double ca,
+                                                    const std::vector<std::pair<long, double>>& b,
+                                                    double cb) {
+  std::vector<std::pair<long, double>> o;
+  o.reserve(a.size() + b.size());
+  size_t i = 0, j = 0;
+  while (i < a.size() || j < b.size()) {
+    if (j == b.size() || (i < a.size() && a[i].first < b[j].first)) {
+      o.push_back({a[i].first, ca * a[i].second});
+      i++;
+    } else if (i == a.size() || b[j].first < a[i].first) {
+      o.push_back({b[j].first, cb * b[j].second});
+      j++;
+    } else {
+      o.push_back({a[i].first, ca * a[i].second + cb * b[j].second});
+      i++;
+      j++;
+    }
+  }
+  return o;
+}
+inline SDual sd_make(double v, std::vector<std::pair<long, double>> d) {
+  SDual r(v);
+  r.d = std::move(d);
+  return r;
+}
+inline SDual sd_scale(const SDual& a, double v, double c) {
+  SDual r(v);
+  r.d = a.d;
+  for (auto& e : r.d) e.second *= c;
+  return r;
+}
+inline SDual operator+(const SDual& a, const SDual& b) { return sd_make(a.v + b.v, sd_comb(a.d, 1.0, b.d, 1.0)); }
+inline SDual operator-(const SDual& a, const SDual& b) { return sd_make(a.v - b.v, sd_comb(a.d, 1.0, b.d, -1.0)); }
+inline SDual operator-(const SDual& a) { return sd_scale(a, -a.v, -1.0); }
+inline SDual operator*(const SDual& a, const SDual& b) { return sd_make(a.v * b.v, sd_comb(a.d, b.v, b.d, a.v)); }
+inline SDual operator/(const SDual& a, const SDual& b) {
+  return sd_make(a.v / b.v, sd_comb(a.d, 1.0 / b.v, b.d, -a.v / (b.v * b.v)));
+}
+inline SDual operator+(double a, const SDual& b) { return sd_scale(b, a + b.v, 1.0); }
+inline SDual operator+(const SDual& a, double b) { return sd_scale(a, a.v + b, 1.0); }
+inline SDual operator-(const SDual& a, double b) { return sd_scale(a, a.v - b, 1.0); }
+inline SDual operator-(double a, const SDual& b) { return sd_scale(b, a - b.v, -1.0); }
+inline SDual operator*(double a, const SDual& b) { return sd_scale(b, a * b.v, a); }
+inline SDual operator*(const SDual& a, double b) { return sd_scale(a, a.v * b, b); }
+inline SDual operator/(const SDual& a, double b) { return sd_scale(a, a.v / b, 1.0 / b); }
+inline SDual operator/(double a, const SDual& b) { return SDual(a) / b; }
+inline SDual& operator+=(SDual& a, const SDual& b) { a = a + b; return a; }
+inline SDual sqrt(const SDual& a) {
+  double s = std::sqrt(a.v);
+  return sd_scale(a, s, 1.0 / (2.0 * s));
+}
+// R14: derivative of |x| at 0 taken as 0.
+inline SDual fabs(const SDual& a) {
+  if (a.v > 0) return a;
+  if (a.v < 0) return -a;
+  return SDual(0.0);
+}
+
 // --------------------------------------------------------------- hierarchy
 struct Level {
   int n[3];
@@ -205,6 +276,7 @@ struct Hier {
 
 inline double cube(double a) { return a * a * a; }
 inline Dual cube(Dual a) { return a * a * a; }
+inline SDual cube(const SDual& a) { return a * a * a; }
 
 // Composite value of a field at an existing level-l cell: its own value when
 // it is a leaf, the mean of its 8 children when covered by level l+1.
@@ -1403,6 +1475,39 @@ void orc_jv_scale(orc_hier* h, const double* u, const double* v, double a0, doub
 void orc_vjp(orc_hier* h, const double* u, const double* w, double a0, double dt, double* JTw,
              double* dz, double* JTw_abs) {
   vjp_bruteforce(*reinterpret_cast<Hier*>(h), u, w, a0, dt, JTw, dz, JTw_abs);
+}
+
+// The Jacobian of F(u) = a0 u - b - dt f(u) with respect to u and z, every
+// entry the residual code reaches, as triplets: rows 0 .. 2N-1, columns
+// 0 .. 2N-1 for u and 2N + k for z_k.  Returns the number of entries, or
+// -(that number) when cap is too small (nothing written then).
+long orc_jacobian(orc_hier* h, const double* u, double a0, double dt, long cap, int* rows,
+                  int* cols, double* vals) {
+  const Hier& H = *reinterpret_cast<Hier*>(h);
+  const long N = H.N, n2 = 2 * N;
+  std::vector<SDual> ud(n2), zd(N), Fd(n2);
+  for (long i = 0; i < n2; i++) {
+    ud[i] = SDual(u[i]);
+    ud[i].d.push_back({i, 1.0});
+  }
+  for (long k = 0; k < N; k++) {
+    zd[k] = SDual(H.z[k]);
+    zd[k].d.push_back({n2 + k, 1.0});
+  }
+  std::vector<double> b0(n2, 0.0);
+  residual_t<SDual>(H, ud.data(), zd.data(), b0.data(), a0, dt, Fd.data(), nullptr);
+  long nnz = 0;
+  for (long r = 0; r < n2; r++) nnz += (long)Fd[r].d.size();
+  if (nnz > cap) return -nnz;
+  long q = 0;
+  for (long r = 0; r < n2; r++)
+    for (const auto& e : Fd[r].d) {
+      rows[q] = (int)r;
+      cols[q] = (int)e.first;
+      vals[q] = e.second;
+      q++;
+    }
+  return nnz;
 }
 
 // material in double precision (for finite-difference pins in z)

@@ -81,6 +81,8 @@ def _load():
         "orc_pc_apply": (None, [vp, _dp, _dp]),
         "orc_comp_apply": (None, [vp, ctypes.c_int, _dp, _dp]),
         "orc_level_apply": (None, [vp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+        "orc_jacobian": (ctypes.c_long, [vp, _dp, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                         _ip, _ip, _dp]),
         "orc_fac": (None, [vp, ctypes.c_int, _dp, _dp]),
         "orc_gmg": (None, [vp, ctypes.c_int, _dp, _dp]),
         "orc_average_down": (None, [vp, _dp]),
@@ -233,6 +235,28 @@ class Oracle:
         y = np.empty(self.N)
         _lib.orc_comp_apply(self._h, fld, _d(np.ascontiguousarray(x)), _d(y))
         return y
+
+    def jacobian(self, u, a0, dt):
+        """Sparse dF/du (2N x 2N) and dF/dz (2N x N) at u, every entry the
+        residual reaches (scipy CSR)."""
+        import scipy.sparse as sp
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        n2 = 2 * self.N
+        cap = 64 * n2
+        while True:
+            rows = np.empty(cap, dtype=np.int32)
+            cols = np.empty(cap, dtype=np.int32)
+            vals = np.empty(cap)
+            nnz = _lib.orc_jacobian(self._h, _d(u), a0, dt, cap, rows.ctypes.data_as(_ip),
+                                    cols.ctypes.data_as(_ip), _d(vals))
+            if nnz >= 0:
+                break
+            cap = -nnz
+        rows, cols, vals = rows[:nnz], cols[:nnz], vals[:nnz]
+        zc = cols >= n2
+        Ju = sp.csr_matrix((vals[~zc], (rows[~zc], cols[~zc])), shape=(n2, n2))
+        Jz = sp.csr_matrix((vals[zc], (rows[zc], cols[zc] - n2)), shape=(n2, self.N))
+        return Ju, Jz
 
     def level_apply(self, fld, lev, x):
         """The FAC level operator of level `lev` (homogeneous coarse-fine

@@ -773,3 +773,68 @@ def test_bdf2_error_estimate_exact_for_cubics(alpha):
     N = h.ncells
     ref = max(np.max(np.abs(est[:N] / (u1[:N] + 0.5))), np.max(np.abs(est[N:] / (u1[N:] + 0.25))))
     assert abs(m - ref) <= 1e-15 * ref
+
+
+# ------------------------------------------------ gradient through the steps
+def test_oracle_sparse_jacobian_matches_forward_and_transposed_products():
+    """The sparse forward-mode Jacobian reproduces the analytic Jv (pinned by
+    the dense central-difference Jacobians above) and the transposed
+    products by columns, in u and in z."""
+    for h in (W.tiny_amr(8, three_levels=True), W.boundary_amr(8)):
+        z = W.material_from_cubes(h, [((2, 2, 2), 3, 10.0)])
+        o = Oracle(h, z)
+        u = W.front_state(h, seed=3, noise=0.1)
+        Ju, Jz = o.jacobian(u, 1.3, 3e-3)
+        v = W.random_direction(h, 4)
+        Jv = o.jv_analytic(u, v, 1.3, 3e-3)
+        assert np.abs(Ju @ v - Jv).max() <= 1e-14 * np.abs(Jv).max()
+        w = W.random_direction(h, 5)
+        JTw, dz, _ = o.vjp(u, w, 1.3, 3e-3)
+        assert np.abs(Ju.T @ w - JTw).max() <= 1e-14 * np.abs(JTw).max()
+        assert np.abs(Jz.T @ w - dz).max() <= 1e-14 * np.abs(dz).max()
+
+
+def test_oracle_gradient_against_central_differences():
+    """The oracle's discrete adjoint through backward-Euler steps against
+    central differences of its own converged forward map J(z, E_0)."""
+    from oracle.gradient import be_gradient
+    from paper_1302_6303_gb300.adjoint import box_weights
+    h = W.Hierarchy((8, 8, 8), [[((0, 0, 0), (7, 7, 7))], [((0, 4, 4), (5, 9, 9))]])
+    z = W.material_from_cubes(h, [((2, 1, 1), 3, 10.0)])
+    N = h.ncells
+    u0 = W.front_state(h, seed=2, noise=0.0, front=0.3, width=0.1)
+    w = box_weights(h, ((2, 2, 2), (5, 5, 5)))
+    nsteps, dt = 3, 1e-3
+
+    def oracle(zz):
+        o = Oracle(h, None)
+        o.set_material_f64(zz)
+        o.set_solver(jv_mode=JV_ANALYTIC, nmg=2, rtol=1e-13, max_newton=30)
+        return o
+
+    zz = z.astype(np.float64)
+    J, dz, dE = be_gradient(oracle(zz), u0, nsteps, dt, w)
+
+    def J_of(zv, E):
+        o = oracle(zv)
+        u = np.concatenate([E, u0[N:]])
+        for _ in range(nsteps):
+            u, st = o.newton(u.copy(), u.copy(), 1.0, dt)
+            assert st["status"] == 0
+        return float(np.dot(w, u[:N]))
+
+    assert abs(J_of(zz, u0[:N]) - J) <= 1e-12 * abs(J)
+    for k in np.argsort(-np.abs(dz))[:3]:
+        hz = 1e-6 * zz[k]
+        zp, zm = zz.copy(), zz.copy()
+        zp[k] += hz
+        zm[k] -= hz
+        fd = (J_of(zp, u0[:N]) - J_of(zm, u0[:N])) / (2 * hz)
+        assert abs(fd - dz[k]) <= 1e-6 * np.abs(dz).max(), (k, fd, dz[k])
+    for k in np.argsort(-np.abs(dE))[:3]:
+        he = 1e-6 * u0[k]
+        Ep, Em = u0[:N].copy(), u0[:N].copy()
+        Ep[k] += he
+        Em[k] -= he
+        fd = (J_of(zz, Ep) - J_of(zz, Em)) / (2 * he)
+        assert abs(fd - dE[k]) <= 1e-6 * np.abs(dE).max(), (k, fd, dE[k])
