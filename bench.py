@@ -107,6 +107,10 @@ def parse():
                          "Newton loop runs host-driven so that a profiler sees every kernel "
                          "as its own launch (--profile-graph keeps the graph form)")
     ap.add_argument("--profile-graph", action="store_true")
+    ap.add_argument("--levels-table", type=float, default=0.0, metavar="T_END",
+                    help="iteration table of Sec. 6: the dynamic-AMR Marshak run at base 16^3 "
+                         "with at most 2, 3 and 4 levels to t = T_END (the paper's solver "
+                         "settings); prints one JSON line per depth and exits")
     ap.add_argument("--profile-pc", type=int, default=0, metavar="N",
                     help="short run for profilers: N preconditioner applies (cached graph) "
                          "on the workload after one set-up, 8x8x4 tiles, the workload's "
@@ -155,6 +159,50 @@ def profile_pc_run(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile_pc": True, "applies": args.profile_pc,
                       "us_per_apply": e0.elapsed_time(e1) * 1e3 / args.profile_pc}))
+    return 0
+
+
+def levels_table(args):
+    """Average Newton and GMRES iterations per time step of the dynamic-AMR
+    Marshak run (Sec. 6: three z = 10 blocks, Robin R = 1 at x = 0 and R = 0
+    at x = 1, E0 = 1e-5) at base 16^3 with at most 2, 3 and 4 levels, BDF2
+    with the PC.4.7 controller, regridding every 4 steps on the tau^c and
+    tau^g indicators, Newton rtol 1e-12 and atol 1e-10, at most 50 Krylov
+    iterations per Newton step, V(1,0) red-black Gauss-Seidel with smoothing
+    only on the coarsest level, FP32 V-cycle, analytic Jv."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd, workloads as W
+    from paper_1302_6303_gb300.amr import DynamicAmr, RegridPolicy
+    n0 = (16, 16, 16)
+    cubes = W.paper_blocks(n0)
+    h = W.Hierarchy(n0=n0, levels=[[((0, 0, 0), (15, 15, 15))]], bc_type=[1, 1, 0, 0, 0, 0],
+                    bc_R=[1.0, 0.0, 0, 0, 0, 0])
+    # the paper's 16b2l .. 16b4l averages (Sec. 6 iteration tables)
+    paper = {2: (2.99, 7.71), 3: (2.96, 7.21), 4: (2.64, 6.63)}
+    for L in (2, 3, 4):
+        params = nrd.default_params(nu1=1, nu2=0, nmg=1, coarse_sweeps=1, rtol=1e-12, atol=1e-10,
+                                    max_krylov=50, jv_mode=nrd.JV_ANALYTIC,
+                                    pc_precision=nrd.PC_F32)
+        pol = RegridPolicy(regrid_every=4, thr_c=0.2, thr_g=0.2, tag_bits=3, buffer=1,
+                           efficiency=0.7, min_side=4, max_side=16, max_levels=L)
+        run = DynamicAmr(h, lambda hh: W.material_from_cubes(hh, cubes), params=params,
+                         policy=pol, eps_t=5e-3, dt_max=5e-3)
+        t0 = time.perf_counter()
+        run.run(torch.from_numpy(W.initial_state(h)).cuda(), 1e-4, t_end=args.levels_table)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        hist = run.history
+        ns = len(hist)
+        print(json.dumps({
+            "levels": L, "t_end": args.levels_table, "steps": ns,
+            "newton_per_step": sum(r["newton"] for r in hist) / ns,
+            "gmres_per_step": sum(r["krylov"] for r in hist) / ns,
+            "regrids": len(run.events), "max_leaf_cells": max(r["nleaf"] for r in hist),
+            "levels_reached": max(r["nlevels"] for r in hist), "wall_s": wall,
+            "paper_16b%dl" % L: {"newton_per_step": paper[L][0], "gmres_per_step": paper[L][1],
+                                 "t_end": 1.0}}), flush=True)
     return 0
 
 
@@ -597,6 +645,8 @@ def main():
         return profile_run(args)
     if args.profile_pc:
         return profile_pc_run(args)
+    if args.levels_table > 0:
+        return levels_table(args)
     import torch
     import __graft_entry__ as g
     g.build()

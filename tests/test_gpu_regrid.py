@@ -276,3 +276,88 @@ def test_dynamic_amr_marshak_run(nrd):
     Lmax = L[leaf].max()
     front = np.abs(E - 0.5 * E.max())[leaf].argmin()
     assert L[leaf][front] == Lmax
+
+
+def test_amr2_bdf2_run_with_regrids_matches_oracle(nrd):
+    """The 2-level workload at base 16^3: 20 BDF2 steps (the first backward
+    Euler) of dt = 5e-4 with regridding every 5 steps (tags h|grad E|/E >
+    0.1, Berger-Rigoutsos with efficiency 0.7, fine boxes of 16-32 cells, a
+    one-cell buffer), each regrid followed by the warm-restart re-solve of
+    the last step (reading R20), on the GPU and in the oracle, compared per
+    cell after every step.  The tags are computed from the oracle's state on
+    both sides, so that no threshold decision rests on the last digits of
+    two converged solves; the GPU's tags and boxes must equal the oracle's."""
+    n0, dt, rtol = 16, 5e-4, 1e-10
+    h, cubes = W.config_amr2_cubes(n0, seed=0)
+    kw = dict(pc_precision=1, jv_mode=nrd.JV_ANALYTIC, rtol=rtol)
+
+    def pair(hh):
+        zz = W.material_from_cubes(hh, cubes)
+        c = ctx_for(nrd, hh, zz, **kw)
+        o = Oracle(hh, zz)
+        o.set_solver(nmg=auto_nmg(hh), jv_mode=O_AN, rtol=rtol)
+        return c, o
+
+    ctx, o = pair(h)
+    un_o = W.initial_state(h)
+    un_g = dev(un_o)
+    unm1_o, unm1_g = None, None
+    regrids = 0
+    for n in range(20):
+        if unm1_o is None:
+            a0, b, dtp = 1.0, un_o.copy(), 0.0
+        else:
+            a0, b, dtp = 1.5, 2.0 * un_o - 0.5 * unm1_o, dt   # BDF2, equal steps
+        u_g = un_g.clone()
+        st = ctx.step(u_g, un_g, unm1_g, dt, dtp)
+        u_o, sto = o.newton(un_o.copy(), b, a0, dt)
+        assert st["status"] == 0 and sto["status"] == 0, (n, st, sto)
+        rel = per_cell_rel(u_g.cpu().numpy(), u_o, o.leaf_mask())
+        assert rel <= 1e-8, (n, rel)
+        last = (un_o, unm1_o, un_g, unm1_g, a0, dtp, sto["fnorm0"])
+        unm1_o, un_o, unm1_g, un_g = un_o, u_o, un_g, u_g
+        if (n + 1) % 5 or n == 19:
+            continue
+        # regrid on the oracle's state
+        tags_o = o.tag(un_o, np.inf, np.inf, 0.1)
+        t_dev = ctx.tag(dev(un_o), float("inf"), float("inf"), 0.1)
+        assert np.array_equal(t_dev.cpu().numpy(), tags_o)
+        lev = as_lists(ctx.regrid_boxes(t_dev, 4, 1, 0.7, 16, 32, 2))
+        lev_o = as_lists(R.regrid_boxes(h, tags_o, tag_bits=4, buffer=1, efficiency=0.7,
+                                        min_side=16, max_side=32, max_levels=2))
+        assert lev == lev_o
+        if lev == as_lists(h.levels):
+            continue
+        regrids += 1
+        nh = W.Hierarchy(n0=h.n0, levels=lev, bc_type=h.bc_type, bc_R=h.bc_R)
+        cn, on = pair(nh)
+        p_un_o, p_unm1_o, p_un_g, p_unm1_g, pa0, pdtp, f0 = last
+        # transfer u_{n+1}, u_n, u_{n-1} of the last step on each side
+        vec_o = [un_o, p_un_o] + ([p_unm1_o] if p_unm1_o is not None else [])
+        vec_g = [un_g, p_un_g] + ([p_unm1_g] if p_unm1_g is not None else [])
+        mv_o = [R.transfer(h, nh, v) for v in vec_o]
+        mv_g = ctx.transfer_to(cn, torch.stack(vec_g))
+        for a, b_ in zip(mv_g.cpu().numpy(), mv_o):
+            assert per_cell_rel(a, b_, ~nh.covered_mask()) <= 1e-8
+        # warm restart: the last step solved again on the new hierarchy from
+        # the transferred solution, to the absolute residual the original
+        # step reached
+        atol = rtol * f0
+        cn.set_params(atol=atol)
+        on.set_solver(nmg=auto_nmg(nh), jv_mode=O_AN, rtol=0.0, atol=atol)
+        if len(mv_o) == 3:
+            b2 = 2.0 * mv_o[1] - 0.5 * mv_o[2]
+        else:
+            b2 = mv_o[1].copy()
+        u_g = mv_g[0].clone().contiguous()
+        st = cn.step(u_g, mv_g[1].contiguous(),
+                     mv_g[2].contiguous() if len(mv_o) == 3 else None, dt, pdtp)
+        u_o, sto = on.newton(mv_o[0].copy(), b2, pa0, dt)
+        assert st["status"] == 0 and sto["status"] == 0, (n, st, sto)
+        assert per_cell_rel(u_g.cpu().numpy(), u_o, on.leaf_mask()) <= 1e-8
+        cn.set_params(atol=0.0)
+        on.set_solver(nmg=auto_nmg(nh), jv_mode=O_AN, rtol=rtol)
+        h, ctx, o = nh, cn, on
+        un_o, unm1_o = u_o, mv_o[1]
+        un_g, unm1_g = u_g, mv_g[1].contiguous()
+    assert regrids >= 1
