@@ -68,12 +68,31 @@ WORKLOADS = {
     },
 }
 
-# Algorithmic work per leaf cell of the linearisation stencil, in FP64-pipe
-# instructions (the unit that bounds it on GB300, which issues 2 FP64
-# instructions per clock per SM): 3 faces x 45 (face flux, its 5 partials and
-# the two P1 coefficients incl. the refined reciprocal and reciprocal square
-# root; the FP32 narrowing of the coefficients runs on the integer pipe) + 34
-# per cell (balance, coupling and its partials, P2 data).
+# Algorithmic FP64 work per leaf cell, counted from the formulas of Sec. 3.2
+# and Sec. 4.2 (each add, subtract or multiply one operation; divisions and
+# square roots charged below at their measured cost):
+#  residual, per face (3 per cell): T_f 2, z_a^3 + z_b^3 1, 3(...) 1, T_f^3 2,
+#    E_a + E_b 1, its scaling 1, dE 1, 2 D_r 1, D_h g 1, 1 + D_h g 1,
+#    k T_f^2 sqrt(T_f) 2, the two fluxes 2 + 2 with dT 1: 19 ops, 3 divisions
+#    (D_r, g, D_E), 1 square root; per cell: z^3 2, the two divergences 16,
+#    T^3 2, T^4 1, T^4 - E 1, sigma (T^4 - E) 1, a0 u - b - dt (div +- coupling)
+#    5 + 5: 33 ops, 1 division (sigma): 90 ops, 10 divisions, 3 square roots.
+#  linearisation = residual + per face the five flux partials (dD_r/dT_f 1,
+#    dg/dE_a, dg/dE_b 5, dD_E/dD_h and dD_E/dg 2, the chain to T_f 2 and to
+#    E_a, E_b 2, dF_E 3 + 3 + 2, dD_T/dT_f 2, dF_T 3 + 3) and the two scaled
+#    P1 coefficients 2: 31 ops and 2 divisions (1/T_f, 1/(E_a + E_b)); per
+#    cell the coupling partials 7 ops and 1 division, the P2 data 4 ops and
+#    1 division: 194 ops, 18 divisions, 3 square roots.
+#  frozen Jv: per face 6 + 3 (the two tangent fluxes from the five partials),
+#    per cell the two divergences 16, the coupling tangent 3, a0 v - dt (...)
+#    6: 52 ops.
+LIN_OPS = (194, 18, 3)            # (ops, divisions, square roots) per leaf cell
+RES_OPS = (90, 10, 3)
+JV_OPS = (52, 0, 0)
+# FP64-pipe instructions per leaf cell of the kernels as written (the
+# refined reciprocal and reciprocal square root replace the divisions and
+# square roots; FP32 narrowing on the integer pipe): linearisation 3 faces x
+# 45 + 34 per cell
 LIN_INST_PER_CELL = 3 * 45 + 34
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
@@ -670,6 +689,7 @@ def main():
     wl = WORKLOADS[key]
     h, z, u0 = workload(key)
     rates = nrd.measure_peaks()
+    ops = nrd.measure_fp64_ops()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     ctx = make_ctx(nrd, h, z, torch, production=True, wl=wl)
     leaf = ctx.nleaf
@@ -710,27 +730,48 @@ def main():
     traffic = TRAFFIC.get(key, {})
     lin_ms, lin_n = kt["linearise"]
     t_lin = lin_ms / max(lin_n, 1) * 1e-3
-    ach = LIN_INST_PER_CELL * leaf / t_lin / 1e9
+    # FP64 work in flop-equivalents: ops at 1 flop, a division or square root
+    # at the flops of the FMAs the pipe could issue in its place (measured
+    # rates), against the measured FMA rate in flops (2 per FMA)
+    c_div = 2.0 * ops["fma_per_s"] / ops["div_per_s"]
+    c_sqrt = 2.0 * ops["fma_per_s"] / ops["sqrt_per_s"]
+    flop_peak = 2.0 * ops["fma_per_s"] / 1e9
+
+    def work(o):
+        return o[0] + c_div * o[1] + c_sqrt * o[2]
+
+    ach = work(LIN_OPS) * leaf / t_lin / 1e9
+    ach_inst = LIN_INST_PER_CELL * leaf / t_lin / 1e9
     roof = {"kernel": "k_stencil<ST_LINF> + k_stencil<ST_LINC> (residual + linearisation, "
                       "FP64: every face once, then the cells)", "bound": "alu",
-            "achieved": ach, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
-            "frac": ach / fp64_peak, "traffic": traffic.get("linearise"),
+            "achieved": ach, "peak": flop_peak, "unit": "GFLOP/s (FP64)",
+            "frac": ach / flop_peak, "traffic": traffic.get("linearise"),
             "per_launch_us": t_lin * 1e6, "launches": lin_n,
             "timing": "CUDA events around each linearisation (its face and cell launches) in "
                       "an instrumented repeat of the timed steps",
-            "peak_source": fp64_src,
-            "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
-                           % (LIN_INST_PER_CELL, leaf)}
+            "peak_source": "FP64 FMA rate measured in this run (nrd_measure_fp64_ops), 2 flops "
+                           "per FMA; MEASURED_PEAKS.json has no FP64 figure",
+            "algorithmic": "%d FP64 ops + %d divisions x %.1f + %d square roots x %.1f "
+                           "flop-equivalents (measured costs) = %.0f per leaf cell x %d leaf "
+                           "cells" % (LIN_OPS[0], LIN_OPS[1], c_div, LIN_OPS[2], c_sqrt,
+                                      work(LIN_OPS), leaf),
+            "fp64_instructions": {"per_cell": LIN_INST_PER_CELL, "achieved": ach_inst,
+                                  "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
+                                  "frac": ach_inst / fp64_peak},
+            "measured_fp64_ops": ops}
     jv_ms, jv_n = kt["jv"]
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
-    ach_jv = JV_INST_PER_CELL * leaf / t_jv / 1e9
+    ach_jv = work(JV_OPS) * leaf / t_jv / 1e9
+    ach_jv_inst = JV_INST_PER_CELL * leaf / t_jv / 1e9
     gbs_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
     roof_jv = {"kernel": "k_stencil<ST_JVF> (frozen-Jacobian Jv)", "bound": "alu",
-               "achieved": ach_jv, "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
-               "frac": ach_jv / fp64_peak, "traffic": traffic.get("jv"),
+               "achieved": ach_jv, "peak": flop_peak, "unit": "GFLOP/s (FP64)",
+               "frac": ach_jv / flop_peak, "traffic": traffic.get("jv"),
                "per_launch_us": t_jv * 1e6, "launches": jv_n,
-               "algorithmic": "%d FP64-pipe instructions per leaf cell x %d leaf cells"
-                              % (JV_INST_PER_CELL, leaf),
+               "algorithmic": "%d FP64 ops per leaf cell x %d leaf cells" % (JV_OPS[0], leaf),
+               "fp64_instructions": {"per_cell": JV_INST_PER_CELL, "achieved": ach_jv_inst,
+                                     "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
+                                     "frac": ach_jv_inst / fp64_peak},
                "hbm": {"achieved": gbs_jv, "peak": hbm_peak, "unit": "GB/s",
                        "frac": gbs_jv / hbm_peak, "peak_source": peak_src,
                        "algorithmic": "%d B per leaf cell" % JV_BYTES_PER_CELL}}

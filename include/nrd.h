@@ -403,6 +403,14 @@ int nrd_check_narrow(const double* x, int64_t n, float* out, cudaStream_t stream
 int nrd_measure_peaks(double* fp64_tflops_host, double* fp32_tflops_host, double* copy_gbs_host,
                       cudaStream_t stream);
 
+/* FP64 operation rates of the current device, for charging the divisions and
+ * square roots of a kernel's algorithmic work (the paper has no counterpart):
+ * rates_host[0] = fused multiply-adds per second, [1] = correctly rounded
+ * divisions per second, [2] = correctly rounded square roots per second, each
+ * from independent chains on every SM, the best of 3 runs timed with CUDA
+ * events.  Allocates and frees a small scratch array.  Synchronises. */
+int nrd_measure_fp64_ops(double* rates_host, cudaStream_t stream);
+
 /* ---------------------------------------------- time-step control (Sec. 3.4-3.5) */
 enum { NRD_DT_EPS = 0, NRD_DT_PC47 = 1 };
 

@@ -29,6 +29,7 @@ EXPORTED = [
     "nrd_jv", "nrd_linearise", "nrd_vjp", "nrd_adjoint_solve", "nrd_fd_eps", "nrd_dot", "nrd_precond_setup", "nrd_precond_apply", "nrd_newton",
     "nrd_step", "nrd_step_begin", "nrd_step_end", "nrd_tag", "nrd_regrid_boxes", "nrd_transfer", "nrd_time_derivative", "nrd_predict", "nrd_lte", "nrd_dt_control",
     "nrd_autotune", "nrd_autotune_sweeps", "nrd_wdot_noalloc", "nrd_measure_peaks",
+    "nrd_measure_fp64_ops",
     "nrd_check_fastmath", "nrd_check_narrow",
     "nrd_timing_enable",
     "nrd_timing_read",
@@ -117,6 +118,7 @@ def load(path: str = _LIBPATH):
         "nrd_dt_control": (c_int, [c_int, c_dbl, c_dbl, c_dbl, c_dbl, c_dbl, P(c_dbl)]),
         "nrd_wdot_noalloc": (c_int, [dp, dp, fp, ctypes.c_int64, dp, vp]),
         "nrd_measure_peaks": (c_int, [P(c_dbl), P(c_dbl), P(c_dbl), vp]),
+        "nrd_measure_fp64_ops": (c_int, [P(c_dbl), vp]),
         "nrd_check_fastmath": (c_int, [dp, ctypes.c_int64, dp, vp]),
         "nrd_check_narrow": (c_int, [dp, ctypes.c_int64, fp, vp]),
         "nrd_timing_enable": (c_int, [vp, c_int]),
@@ -161,6 +163,17 @@ def measure_peaks():
     if rc != OK:
         raise NrdError(rc, "nrd_measure_peaks failed")
     return {"fp64_tflops": a.value, "fp32_tflops": b.value, "copy_gbs": c.value}
+
+
+def measure_fp64_ops():
+    """FP64 FMA, division and square-root rates (operations per second) of
+    the current device."""
+    lib = load()
+    r = (ctypes.c_double * 3)()
+    rc = lib.nrd_measure_fp64_ops(r, _stream())
+    if rc != OK:
+        raise NrdError(rc, "nrd_measure_fp64_ops failed")
+    return {"fma_per_s": r[0], "div_per_s": r[1], "sqrt_per_s": r[2]}
 
 
 def check_fastmath(x):
