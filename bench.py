@@ -126,6 +126,13 @@ def parse():
                          "Newton loop runs host-driven so that a profiler sees every kernel "
                          "as its own launch (--profile-graph keeps the graph form)")
     ap.add_argument("--profile-graph", action="store_true")
+    ap.add_argument("--profile-stencils", action="store_true",
+                    help="short run for profilers: two rounds of linearisation, frozen Jv and "
+                         "residual, then one Newton step (graph form), 8x8x8 tiles, GMRES "
+                         "restart 2")
+    ap.add_argument("--grid", type=int, default=0, metavar="N",
+                    help="profile modes: the workload's layout at base N^3 (a smaller case of "
+                         "the same kernels for multi-pass profiler captures)")
     ap.add_argument("--levels-table", type=float, default=0.0, metavar="T_END",
                     help="iteration table of Sec. 6: the dynamic-AMR Marshak run at base 16^3 "
                          "with at most 2, 3 and 4 levels to t = T_END (the paper's solver "
@@ -158,7 +165,7 @@ def profile_pc_run(args):
     import __graft_entry__ as g
     g.build()
     from paper_1302_6303_gb300 import nrd
-    h, z, u0 = workload(args.workload)
+    h, z, u0 = workload(args.workload, args.grid or None)
     ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
     ctx.set_params(tile_x=8, tile_y=8, tile_z=4)
     if WORKLOADS[args.workload]["solver"] is None:
@@ -176,8 +183,30 @@ def profile_pc_run(args):
         ctx.precond_apply(w, out=y)
     e1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"profile_pc": True, "applies": args.profile_pc,
+    print(json.dumps({"profile_pc": True, "applies": args.profile_pc, "cells": h.ncells,
                       "us_per_apply": e0.elapsed_time(e1) * 1e3 / args.profile_pc}))
+    return 0
+
+
+def profile_stencils_run(args):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd, workloads as W
+    h, z, u0 = workload(args.workload, args.grid or None)
+    ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
+    ctx.set_params(tile_x=8, tile_y=8, tile_z=8, restart=2)
+    u = torch.from_numpy(W.front_state(h, seed=1, noise=0.0, front=0.1, width=0.05)).cuda()
+    v = torch.from_numpy(W.random_direction(h, 2)).cuda()
+    for _ in range(2):
+        ctx.linearise(u, u, 1.0, DT)
+        ctx.jv(u, v, 1.0, DT, mode=nrd.JV_FROZEN)
+        ctx.residual(u, u, 1.0, DT)
+    un = u.clone()
+    st = ctx.step(u, un, None, DT)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_stencils": True, "cells": h.ncells, "newton": st["newton_its"],
+                      "krylov": st["krylov_its"]}))
     return 0
 
 
@@ -664,6 +693,8 @@ def main():
         return profile_run(args)
     if args.profile_pc:
         return profile_pc_run(args)
+    if args.profile_stencils:
+        return profile_stencils_run(args)
     if args.levels_table > 0:
         return levels_table(args)
     import torch
