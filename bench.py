@@ -194,8 +194,12 @@ def profile_stencils_run(args):
     g.build()
     from paper_1302_6303_gb300 import nrd, workloads as W
     h, z, u0 = workload(args.workload, args.grid or None)
-    ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
-    ctx.set_params(tile_x=8, tile_y=8, tile_z=8, restart=2)
+    sv = dict(nu1=2, nu2=2, nmg=4, coarse_sweeps=4)
+    sv.update(WORKLOADS[args.workload]["solver"] or {})
+    ctx = nrd.Context(restart=2, rtol=1e-8, jv_mode=nrd.JV_ANALYTIC, pc_precision=nrd.PC_F32,
+                      tile_x=8, tile_y=8, tile_z=8, **sv)
+    ctx.set_hierarchy_from(h)
+    ctx.set_material(torch.from_numpy(z).cuda())
     u = torch.from_numpy(W.front_state(h, seed=1, noise=0.0, front=0.1, width=0.05)).cuda()
     v = torch.from_numpy(W.random_direction(h, 2)).cuda()
     for _ in range(2):
