@@ -89,24 +89,23 @@ WORKLOADS = {
 LIN_OPS = (194, 18, 3)            # (ops, divisions, square roots) per leaf cell
 RES_OPS = (90, 10, 3)
 JV_OPS = (52, 0, 0)
-# FP64-pipe instructions per leaf cell of the kernels as written (the
-# refined reciprocal and reciprocal square root replace the divisions and
-# square roots; FP32 narrowing on the integer pipe): linearisation 3 faces x
-# 45 + 34 per cell
-LIN_INST_PER_CELL = 3 * 45 + 34
 # frozen-Jacobian Jv: 3 faces x 5 partials x 8 B + v 16 B + cell partials
 # 16 B + Jv 16 B + mask 1 B
 JV_BYTES_PER_CELL = 169.0
-# and its FP64-pipe instructions per leaf cell, the bound that binds it on
-# GB300: 3 faces x 6 (the two tangent fluxes from the five partials) + 20 per
-# cell (two divergences, the coupling tangent, a0 v - dt (...) for both fields)
-JV_INST_PER_CELL = 3 * 6 + 20
 # DRAM bytes per launch group from an ncu capture of the current kernels,
 # per workload (None: not captured for this kernel version and workload)
+# (single256: captured on the same layout at 128^3, 2,097,152 cells, and
+# scaled by the cells, x8: these stencils stream their inputs once; the
+# linearisation's face and cell launches 57.7 + 377.6 + 187.9 + 63.8 MB,
+# the frozen Jv 321.9 + 55.5 MB)
 TRAFFIC = {
     "amr2_base64": {"linearise": None, "jv": None},
-    "single256": {"linearise": None, "jv": None},
+    "single256": {"linearise": 8 * (57.7 + 377.6 + 187.9 + 63.8) * 1e6,
+                  "jv": 8 * (321.9 + 55.5) * 1e6},
 }
+# FP64-pipe instructions per cell measured by ncu (sm__inst_executed_pipe_fp64,
+# same capture): linearisation 139.2 + 35.0, frozen Jv 40.4
+LIN_INST_NCU, JV_INST_NCU = 139.2 + 35.0, 40.4
 
 
 def parse():
@@ -784,7 +783,7 @@ def main():
 
     ach = flops(LIN_OPS) * leaf / t_lin / 1e9
     ach_c = charged(LIN_OPS) * leaf / t_lin / 1e9
-    ach_inst = LIN_INST_PER_CELL * leaf / t_lin / 1e9
+    ach_inst = LIN_INST_NCU * leaf / t_lin / 1e9
     roof = {"kernel": "k_stencil<ST_LINF> + k_stencil<ST_LINC> (residual + linearisation, "
                       "FP64: every face once, then the cells)", "bound": "alu",
             "achieved": ach, "peak": flop_peak, "unit": "GFLOP/s (FP64)",
@@ -800,21 +799,22 @@ def main():
             "division_charged": {"achieved": ach_c, "frac": ach_c / flop_peak,
                                  "per_cell": charged(LIN_OPS),
                                  "flops_per_division": c_div, "flops_per_sqrt": c_sqrt},
-            "fp64_instructions": {"per_cell": LIN_INST_PER_CELL, "achieved": ach_inst,
+            "fp64_instructions": {"per_cell": LIN_INST_NCU, "achieved": ach_inst,
                                   "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
-                                  "frac": ach_inst / fp64_peak},
+                                  "frac": ach_inst / fp64_peak,
+                                  "source": "ncu sm__inst_executed_pipe_fp64 per cell"},
             "measured_fp64_ops": ops}
     jv_ms, jv_n = kt["jv"]
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
     ach_jv = flops(JV_OPS) * leaf / t_jv / 1e9
-    ach_jv_inst = JV_INST_PER_CELL * leaf / t_jv / 1e9
+    ach_jv_inst = JV_INST_NCU * leaf / t_jv / 1e9
     gbs_jv = JV_BYTES_PER_CELL * leaf / t_jv / 1e9
     roof_jv = {"kernel": "k_stencil<ST_JVF> (frozen-Jacobian Jv)", "bound": "alu",
                "achieved": ach_jv, "peak": flop_peak, "unit": "GFLOP/s (FP64)",
                "frac": ach_jv / flop_peak, "traffic": traffic.get("jv"),
                "per_launch_us": t_jv * 1e6, "launches": jv_n,
                "algorithmic": "%d FP64 ops per leaf cell x %d leaf cells" % (JV_OPS[0], leaf),
-               "fp64_instructions": {"per_cell": JV_INST_PER_CELL, "achieved": ach_jv_inst,
+               "fp64_instructions": {"per_cell": JV_INST_NCU, "achieved": ach_jv_inst,
                                      "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
                                      "frac": ach_jv_inst / fp64_peak},
                "hbm": {"achieved": gbs_jv, "peak": hbm_peak, "unit": "GB/s",
