@@ -91,9 +91,12 @@ enum { NRD_LIM_WILSON = 0, NRD_LIM_PAPER_LITERAL = 1 };
  * (nrd_linearise) and applies them per Krylov iteration (NRD_JV_FROZEN). */
 enum { NRD_JV_FD = 0, NRD_JV_ANALYTIC = 1, NRD_JV_FROZEN = 2 };
 enum { NRD_PC_F64 = 0, NRD_PC_F32 = 1 };
-/* V-cycle smoothers (Sec. 4.3): red-black Gauss-Seidel (the paper's runs) or
- * damped point Jacobi, e <- e + omega ((f + off(e)) / diag - e) */
-enum { NRD_SMOOTH_RBGS = 0, NRD_SMOOTH_JACOBI = 1 };
+/* V-cycle smoothers (Sec. 4.3): red-black Gauss-Seidel (the paper's runs),
+ * damped point Jacobi, e <- e + omega ((f + off(e)) / diag - e), or block
+ * Gauss-Seidel with x-line blocks on the box levels (each line solved
+ * exactly, lines coloured by the parity of j + k; the patch levels then keep
+ * red-black point sweeps) */
+enum { NRD_SMOOTH_RBGS = 0, NRD_SMOOTH_JACOBI = 1, NRD_SMOOTH_LINE = 2 };
 
 /* Solver and model parameters.  nrd_params_default() fills the values used
  * by the paper (Sec. 3.1: k = 0.01; Sec. 4.1: u_min = 1e-6) and the
@@ -124,7 +127,7 @@ typedef struct {
                           The host-driven loop is also used while kernel timing is
                           on.  Both give the same iterates up to rounding. */
   int smoother;        /* NRD_SMOOTH_RBGS (default) or NRD_SMOOTH_JACOBI, on every AMR
-                          level and GMG grid */
+                          level and GMG grid, or NRD_SMOOTH_LINE */
   double omega;        /* damping of NRD_SMOOTH_JACOBI, 0 < omega <= 1 (default 6/7) */
   double eta0;         /* Eisenstat-Walker forcing of the first Newton iteration,
                           0 < eta0 <= eta_max (default 0.3) */

@@ -227,7 +227,8 @@ struct Hier {
   // solver settings
   int restart = 30, max_krylov = 300, jv_mode = JV_FD;
   int nu1 = 2, nu2 = 2, nmg = 4, coarse_sweeps = 4;
-  int smoother = 0;                 // 0 red-black Gauss-Seidel, 1 damped point Jacobi
+  int smoother = 0;                 // 0 red-black Gauss-Seidel, 1 damped point Jacobi,
+                                    // 2 block (x-line) Gauss-Seidel on the box levels
   double omega = 6.0 / 7.0;         // Jacobi damping
   double rtol = 1e-8, atol = 0.0;
   int max_newton = 20;
@@ -896,10 +897,83 @@ void jacobi(const Grid& G, std::vector<double>& e, const std::vector<double>& f,
   }
 }
 
+// Block Gauss-Seidel (Sec. 4.3 names it without saying what the blocks are;
+// reading R26): the blocks are the x-lines of a box level, each solved
+// exactly (a tridiagonal system: the line's cells coupled through their x
+// faces, the y- and z-neighbours taken at their current values), the lines
+// coloured by the parity of j + k, red lines first in pre-smoothing and
+// black lines first in post-smoothing.  A colour's lines do not couple, so
+// one colour is a block Jacobi pass and the two colours a block
+// Gauss-Seidel sweep.  The AMR patch levels keep point red-black sweeps.
+void xline_gs(const Grid& G, std::vector<double>& e, const std::vector<double>& f, int sweeps,
+              bool red_first) {
+  const Hier& H = *G.H;
+  const Hier::OpLevel& O = *G.O;
+  const double beta = H.beta;
+  const int n0 = O.n[0], n1 = O.n[1], n2 = O.n[2];
+  for (int sw = 0; sw < sweeps; sw++)
+    for (int pass = 0; pass < 2; pass++) {
+      int colour = red_first ? pass : 1 - pass;
+      ORC_PARALLEL_FOR
+      for (int k = 0; k < n2; k++)
+        for (int j = 0; j < n1; j++) {
+          if ((j + k) % 2 != colour) continue;
+          // the line's tridiagonal system: lo e_{i-1} + dg e_i + hi e_{i+1} = rhs
+          std::vector<double> lo(n0, 0.0), dg(n0, 1.0), hi(n0, 0.0), rhs(n0, 0.0);
+          for (int i = 0; i < n0; i++) {
+            int c[3] = {i, j, k};
+            double d = 1.0, of = 0.0;
+            for (int dd = 0; dd < 3; dd++) {
+              double h = O.h[dd];
+              for (int s = -1; s <= 1; s += 2) {
+                int g[3] = {c[0], c[1], c[2]};
+                g[dd] += s;
+                int face = 2 * dd + (s > 0 ? 1 : 0);
+                if (!G.in_domain(g)) {
+                  if (G.fld == 0 && H.bc_type[face] == BC_ROBIN) {
+                    double Db = O.Db[face][pidx(O.n, dd, c)];
+                    d += beta * 2.0 * Db / (h * (4.0 * Db + h));
+                  }
+                  continue;
+                }
+                int fc[3] = {c[0], c[1], c[2]};
+                if (s > 0) fc[dd] += 1;
+                double a = beta * O.C[dd][fidx(O.n, dd, fc[0], fc[1], fc[2])] / (h * h);
+                d += a;
+                if (dd == 0) {
+                  if (s < 0) lo[i] = -a; else hi[i] = -a;
+                } else {
+                  of += a * e[G.di(g)];
+                }
+              }
+            }
+            dg[i] = d;
+            rhs[i] = f[G.di(c)] + of;
+          }
+          // Thomas algorithm
+          std::vector<double> cp(n0), dp(n0);
+          cp[0] = hi[0] / dg[0];
+          dp[0] = rhs[0] / dg[0];
+          for (int i = 1; i < n0; i++) {
+            double m = dg[i] - lo[i] * cp[i - 1];
+            cp[i] = hi[i] / m;
+            dp[i] = (rhs[i] - lo[i] * dp[i - 1]) / m;
+          }
+          int cl[3] = {n0 - 1, j, k};
+          e[G.di(cl)] = dp[n0 - 1];
+          for (int i = n0 - 2; i >= 0; i--) {
+            int c[3] = {i, j, k}, c1[3] = {i + 1, j, k};
+            e[G.di(c)] = dp[i] - cp[i] * e[G.di(c1)];
+          }
+        }
+    }
+}
+
 // the smoother selected for the V-cycle
 void smooth(const Grid& G, std::vector<double>& e, const std::vector<double>& f, int sweeps,
             bool red_first) {
   if (G.H->smoother == 1) jacobi(G, e, f, sweeps, G.H->omega);
+  else if (G.H->smoother == 2 && G.O->amr < 0) xline_gs(G, e, f, sweeps, red_first);
   else rbgs(G, e, f, sweeps, red_first);
 }
 
@@ -1412,7 +1486,8 @@ void orc_set_solver(orc_hier* h, int restart, int max_krylov, int jv_mode, int n
   H->max_newton = max_newton;
 }
 
-// smoother of the V-cycle: 0 red-black Gauss-Seidel, 1 damped point Jacobi
+// smoother of the V-cycle: 0 red-black Gauss-Seidel, 1 damped point Jacobi,
+// 2 x-line block Gauss-Seidel on the box levels (R26)
 void orc_set_smoother(orc_hier* h, int kind, double omega) {
   Hier* H = reinterpret_cast<Hier*>(h);
   H->smoother = kind;

@@ -151,7 +151,8 @@ class Oracle:
                             rtol, atol, max_newton)
 
     def set_smoother(self, kind=0, omega=6.0 / 7.0):
-        """V-cycle smoother: 0 red-black Gauss-Seidel, 1 damped point Jacobi."""
+        """V-cycle smoother: 0 red-black Gauss-Seidel, 1 damped point Jacobi,
+        2 block (x-line) Gauss-Seidel on the box levels (reading R26)."""
         _lib.orc_set_smoother(self._h, kind, omega)
 
     def leaf_mask(self):

@@ -62,7 +62,8 @@ int check_params(const nrd_params* p, std::string& err) {
   if (!(p->rtol >= 0.0) || !(p->atol >= 0.0)) { err = "tolerances must be >= 0"; return NRD_EINVAL; }
   if (p->max_newton < 1) { err = "max_newton must be >= 1"; return NRD_EINVAL; }
   if (p->graph != 0 && p->graph != 1) { err = "graph must be 0 or 1"; return NRD_EINVAL; }
-  if (p->smoother != NRD_SMOOTH_RBGS && p->smoother != NRD_SMOOTH_JACOBI) { err = "bad smoother"; return NRD_EINVAL; }
+  if (p->smoother != NRD_SMOOTH_RBGS && p->smoother != NRD_SMOOTH_JACOBI &&
+      p->smoother != NRD_SMOOTH_LINE) { err = "bad smoother"; return NRD_EINVAL; }
   if (!(p->omega > 0.0 && p->omega <= 1.0)) { err = "omega must be in (0, 1]"; return NRD_EINVAL; }
   if (!(p->eta_max > 0.0 && p->eta_max < 1.0)) { err = "eta_max must be in (0, 1)"; return NRD_EINVAL; }
   if (!(p->eta0 > 0.0 && p->eta0 <= p->eta_max)) { err = "eta0 must be in (0, eta_max]"; return NRD_EINVAL; }

@@ -396,6 +396,63 @@ __global__ void __launch_bounds__(SW_THREADS, 4) k_bsweep(const __grid_constant_
   }
 }
 
+// ---- block (x-line) Gauss-Seidel on a box (Sec. 4.3 names block
+// Gauss-Seidel; the blocks are the box's x-lines, reading R26).  One colour
+// of lines per launch: each thread solves one x-line (j, k) with
+// (j + k) % 2 == colour exactly by the Thomas algorithm, the line's cells
+// coupled through their x faces and the y- and z-neighbours (lines of the
+// other colour) at their current values.  The forward elimination keeps c'
+// in cp (a scratch vector of the correction's layout) and d' in e; the back
+// substitution overwrites e.  Grid (lines / 128, 2 fields).
+// ZERO: the neighbours are 0 (the first pass of a level).  ADD: u += e on
+// uncovered cells (the last pass on level 0).
+template <class P, bool ZERO, bool ADD>
+__global__ void __launch_bounds__(128) k_bline(BoxK<P> B, int colour, P* cpbuf,
+                                                const uint8_t* mask, P* u) {
+  const int fld = blockIdx.y;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= B.n1 * B.n2) return;
+  const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
+  const int j = q % n1, k = q / n1;
+  if (((j + k) & 1) != colour) return;
+  P* e = B.e + fld * B.vfs;
+  P* cp = cpbuf + fld * B.vfs;
+  const P* f = B.f + fld * B.vfs;
+  const P* A = B.A + fld * B.Afs;
+  const int s2 = n0 * n1;
+  const int base = n0 * (j + n1 * k);
+  P cprev = P(0), dprev = P(0);
+  for (int i = 0; i < n0; i++) {
+    const int idx = base + i;
+    P d = P(1), lo = P(0), hi = P(0), of = P(0), a;
+    if (i > 0) { a = A[idx]; d += a; lo = -a; }
+    else d += A[B.gbase + B.fo[0] + j + n1 * k];
+    if (i < n0 - 1) { a = A[idx + 1]; d += a; hi = -a; }
+    else d += A[B.gbase + B.fo[1] + j + n1 * k];
+    if (j > 0) { a = A[B.NA + idx]; d += a; if (!ZERO) of += a * e[idx - n0]; }
+    else d += A[B.gbase + B.fo[2] + k + n2 * i];
+    if (j < n1 - 1) { a = A[B.NA + idx + n0]; d += a; if (!ZERO) of += a * e[idx + n0]; }
+    else d += A[B.gbase + B.fo[3] + k + n2 * i];
+    if (k > 0) { a = A[2 * B.NA + idx]; d += a; if (!ZERO) of += a * e[idx - s2]; }
+    else d += A[B.gbase + B.fo[4] + i + n0 * j];
+    if (k < n2 - 1) { a = A[2 * B.NA + idx + s2]; d += a; if (!ZERO) of += a * e[idx + s2]; }
+    else d += A[B.gbase + B.fo[5] + i + n0 * j];
+    const P m = d - lo * cprev;
+    cprev = hi / m;
+    dprev = (f[idx] + of - lo * dprev) / m;
+    cp[idx] = cprev;
+    e[idx] = dprev;
+  }
+  P x = dprev;
+  if (ADD && !(mask[base + n0 - 1] & MASK_COVERED)) u[fld * B.vfs + base + n0 - 1] += x;
+  for (int i = n0 - 2; i >= 0; i--) {
+    const int idx = base + i;
+    x = e[idx] - cp[idx] * x;
+    e[idx] = x;
+    if (ADD && !(mask[idx] & MASK_COVERED)) u[fld * B.vfs + idx] += x;
+  }
+}
+
 // one damped point Jacobi sweep on a box (Sec. 4.3): ed = es + omega
 // ((f + off(es)) / diag - es); ZERO: es = 0; ADD: u += ed on uncovered cells
 // (level 0).  One cell per thread; grid (tiles x, tiles y, 2 x tiles z).
@@ -1461,10 +1518,27 @@ void box_smooth(const BoxK<P>& V, int sweeps, bool red_first, bool zero, const u
     }
 }
 
+// block Gauss-Seidel sweeps on a box in place: two colours of x-lines each
+// (k_bline); c' in the scratch
+template <class P>
+void box_lines(const BoxK<P>& V, P* scratch, int sweeps, bool red_first, bool zero,
+               const uint8_t* mask, P* addu, cudaStream_t s) {
+  const dim3 g((V.n1 * V.n2 + 127) / 128, 2);
+  for (int sw = 0; sw < sweeps; sw++)
+    for (int pass = 0; pass < 2; pass++) {
+      const int colour = red_first ? pass : 1 - pass;
+      const bool Z = zero && sw == 0 && pass == 0;
+      const bool D = addu && sw == sweeps - 1 && pass == 1;
+      if (Z) k_bline<P, true, false><<<g, 128, 0, s>>>(V, colour, scratch, mask, addu);
+      else if (D) k_bline<P, false, true><<<g, 128, 0, s>>>(V, colour, scratch, mask, addu);
+      else k_bline<P, false, false><<<g, 128, 0, s>>>(V, colour, scratch, mask, addu);
+    }
+}
+
 // does box level m smooth with the one-launch sweep (ping-pong buffers)?
 template <class P>
 bool fused_sweeps(const PcState* ps, int m) {
-  return sizeof(P) == 4 && ps->tma_ok[m];
+  return sizeof(P) == 4 && ps->tma_ok[m] && ps->smoother == NRD_SMOOTH_RBGS;
 }
 
 // red-black sweeps on box level m: the one-launch TMA sweep where the level
@@ -1472,6 +1546,10 @@ bool fused_sweeps(const PcState* ps, int m) {
 template <class P>
 void rb_sweeps(const PcState* ps, int m, const BoxK<P>& V, P* scratch, int sweeps, int c0,
                bool zero, bool from_scratch, const uint8_t* mask, P* addu, cudaStream_t s) {
+  if (ps->smoother == NRD_SMOOTH_LINE) {
+    box_lines(V, scratch, sweeps, c0 == 0, zero, mask, addu, s);
+    return;
+  }
   if constexpr (sizeof(P) == 4) {
     if (ps->tma_ok[m]) {
       box_sweeps(ps, m, V, scratch, sweeps, c0, zero, from_scratch, mask, addu, s);
@@ -1850,7 +1928,7 @@ void add_level(PcState* ps, const Hier& H, int l, cudaStream_t s) {
 // pass also adds the correction to the composite solution.
 template <class P>
 void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
-  if (m > 0 && m == ps->tail_m) {
+  if (m > 0 && m == ps->tail_m && ps->smoother != NRD_SMOOTH_LINE) {
     run_tail<P>(ps, s);
     return;
   }
@@ -1881,8 +1959,8 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   else rb_sweeps<P>(ps, m, V, scratch, ps->nu1, 0, true, false, nullptr, (P*)nullptr, s);
   const BoxRaw& C = ps->box[m + 1];
   const dim3 gc = restrict_grid(C.n[0], C.n[1], C.n[2]);
-  // after a red-first Gauss-Seidel sweep the black residuals are zero
-  if (ps->nu1 > 0 && !jac)
+  // after a red-first point Gauss-Seidel sweep the black residuals are zero
+  if (ps->nu1 > 0 && !jac && ps->smoother != NRD_SMOOTH_LINE)
     k_brestrict<P, true><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);
   else
     k_brestrict<P, false><<<gc, VTHREADS, 0, s>>>(V, (P*)ps->bf[m + 1], C.n[0], C.n[1], C.n[2]);

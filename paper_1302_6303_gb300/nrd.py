@@ -20,7 +20,7 @@ BC_NEUMANN, BC_ROBIN = 0, 1
 LIM_WILSON, LIM_PAPER_LITERAL = 0, 1
 JV_FD, JV_ANALYTIC, JV_FROZEN = 0, 1, 2
 PC_F64, PC_F32 = 0, 1
-SMOOTH_RBGS, SMOOTH_JACOBI = 0, 1
+SMOOTH_RBGS, SMOOTH_JACOBI, SMOOTH_LINE = 0, 1, 2
 DT_EPS, DT_PC47 = 0, 1
 
 EXPORTED = [

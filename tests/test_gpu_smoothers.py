@@ -1,6 +1,7 @@
 """Smoother variants of the V-cycle (Sec. 4.3): the damped point Jacobi
-smoother on the GPU against the FP64 oracle, and the iteration counts of the
-smoothers and sweep schedules on one implicit step.
+smoother and block (x-line) Gauss-Seidel on the GPU against the FP64 oracle,
+and the iteration counts of the smoothers and sweep schedules on one
+implicit step.
 
 Tolerances as in test_gpu_parity: FP64 V-cycle 1e-11 of max |y| (same
 algorithm, different rounding), FP32 V-cycle 2e-4, converged step 1e-8
@@ -81,6 +82,55 @@ def test_jacobi_precond_apply(nrd, name, sched, prec, tol):
     assert err <= tol, err
 
 
+LINE_CASES = dict(CASES, single32=lambda: W.config_single_level(32, seed=1, cube_side=8),
+                  odd=lambda: (W.uniform((12, 10, 6)),
+                               W.material_from_cubes(W.uniform((12, 10, 6)),
+                                                     [((2, 1, 1), 4, 10.0)])))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+@pytest.mark.parametrize("sched", [(2, 2, 4), (1, 1, 2), (1, 3, 3)])
+@pytest.mark.parametrize("name", list(LINE_CASES))
+def test_line_gs_precond_apply(nrd, name, sched, prec, tol):
+    """Block Gauss-Seidel with x-line blocks (reading R26) on the GMG box
+    levels, point red-black sweeps on the patch levels: the V-cycle against
+    the oracle's; single levels (including a 32^3 box whose levels have TMA
+    maps, which this smoother does not use, and an odd-sized box) and
+    2- and 3-level hierarchies."""
+    h, z = LINE_CASES[name]()
+    nmg = 3 if min(h.n0) >= 16 else (2 if all(n % 2 == 0 for n in h.n0) else 1)
+    nu1, nu2, csw = sched
+    ctx, o = make(nrd, h, z, pc_precision=prec, nmg=nmg, nu1=nu1, nu2=nu2, coarse_sweeps=csw,
+                  smoother=nrd.SMOOTH_LINE)
+    o.set_solver(nmg=nmg, nu1=nu1, nu2=nu2, coarse_sweeps=csw)
+    o.set_smoother(2)
+    u = W.front_state(h, seed=2, noise=0.1)
+    a0, dt = 1.2, 5e-3
+    ctx.precond_setup(dev(u), a0, dt)
+    o.pc_setup(u, a0, dt)
+    w = W.random_direction(h, 5)
+    y = ctx.precond_apply(dev(w)).cpu().numpy()
+    yo = o.pc_apply(w)
+    err = np.abs(y - yo).max() / np.abs(yo).max()
+    assert err <= tol, err
+
+
+@pytest.mark.parametrize("name", ["single16", "amr2_16"])
+def test_line_gs_newton_step(nrd, name):
+    h, z = CASES[name]()
+    ctx, o = make(nrd, h, z, pc_precision=1, nmg=3, jv_mode=nrd.JV_ANALYTIC, rtol=1e-10,
+                  smoother=nrd.SMOOTH_LINE)
+    o.set_solver(nmg=3, jv_mode=O_AN, rtol=1e-10)
+    o.set_smoother(2)
+    u0 = W.front_state(h, seed=9, noise=0.0, front=0.1, width=0.05)
+    u = dev(u0)
+    st = ctx.step(u, dev(u0), None, 1e-3)
+    uo, sto = o.newton(u0.copy(), u0.copy(), 1.0, 1e-3)
+    assert st["status"] == 0 and sto["status"] == 0
+    rel = per_cell_rel(u.cpu().numpy(), uo, o.leaf_mask())
+    assert rel <= 1e-8, rel
+
+
 def test_jacobi_large_gmg_tail(nrd):
     """A base box deep enough for the one-CTA coarse end of the GMG V-cycle
     (FP32): Jacobi sweeps there from shared memory against the oracle."""
@@ -133,6 +183,8 @@ def test_smoother_iteration_counts(nrd, capsys):
                                               smoother=nrd.SMOOTH_JACOBI, omega=OMEGA)),
         ("Jacobi V(2,2), 4-level GMG", dict(nu1=2, nu2=2, nmg=4, coarse_sweeps=4,
                                               smoother=nrd.SMOOTH_JACOBI, omega=OMEGA)),
+        ("x-line block GS V(1,1), 4-level GMG", dict(nu1=1, nu2=1, nmg=4, coarse_sweeps=2,
+                                                     smoother=nrd.SMOOTH_LINE)),
     ]
     sols, rows = [], []
     for label, kw in variants:

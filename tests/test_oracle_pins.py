@@ -551,6 +551,74 @@ def test_fac_with_jacobi_converges_to_direct_solve(fld):
     assert errs[5] / errs[4] < 0.8
 
 
+@pytest.mark.parametrize("fld", [0, 1])
+def test_xline_block_gs_matches_dense_block_gs(fld):
+    """Block Gauss-Seidel (Sec. 4.3; reading R26: x-line blocks of a box
+    level solved exactly, lines coloured by j + k, red first in
+    pre-smoothing) against the same iteration written densely: A the
+    single-level operator from its columns, each block's rows solved with
+    numpy against the current values outside the block.  One and three
+    sweeps on the smoothing-only coarsest level (one GMG level), and a
+    single-line box, where one sweep is the exact solve."""
+    for n, sweeps in (((6, 4, 4), 1), ((6, 4, 4), 3), ((9, 1, 1), 1)):
+        h = W.uniform(n)
+        N = h.ncells
+        o, _ = _setup_pc(h, nmg=1, coarse_sweeps=sweeps)
+        o.set_smoother(2)
+        A = np.zeros((N, N))
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = 1.0
+            A[:, j] = o.comp_apply(fld, e)
+        f = np.random.default_rng(4).standard_normal(N)
+        L, I, J, K = h.cell_ijk()
+        x = np.zeros(N)
+        for _ in range(sweeps):
+            for colour in (0, 1):
+                for k in range(n[2]):
+                    for j in range(n[1]):
+                        if (j + k) % 2 != colour:
+                            continue
+                        blk = np.nonzero((J == j) & (K == k))[0]
+                        rest = np.setdiff1d(np.arange(N), blk)
+                        rhs = f[blk] - A[np.ix_(blk, rest)] @ x[rest]
+                        x[blk] = np.linalg.solve(A[np.ix_(blk, blk)], rhs)
+        y = o.gmg(fld, f)
+        assert np.abs(y - x).max() <= 1e-12 * np.abs(x).max()
+        if n[1] == 1:
+            assert np.abs(A @ y - f).max() <= 1e-12 * np.abs(f).max()
+
+
+@pytest.mark.parametrize("fld", [0, 1])
+def test_fac_with_block_gs_converges_to_direct_solve(fld):
+    """FAC with x-line block Gauss-Seidel on the GMG box levels (point
+    red-black sweeps on the patch levels) converges to the dense direct
+    solution of the composite operator."""
+    h = W.tiny_amr(8)
+    o, _ = _setup_pc(h, nmg=3, dt=0.2)
+    o.set_smoother(2)
+    leaf = o.leaf_mask()
+    idx = np.nonzero(leaf)[0]
+    N = h.ncells
+    A = np.zeros((idx.size, idx.size))
+    for jj, j in enumerate(idx):
+        e = np.zeros(N)
+        e[j] = 1.0
+        A[:, jj] = o.comp_apply(fld, e)[idx]
+    f = np.zeros(N)
+    f[idx] = np.random.default_rng(8).standard_normal(idx.size)
+    xd = np.linalg.solve(A, f[idx])
+    x = np.zeros(N)
+    errs = []
+    for _ in range(40):
+        r = f - o.comp_apply(fld, x)
+        r[~leaf] = 0.0
+        x += o.fac(fld, r)
+        errs.append(np.abs(x[idx] - xd).max())
+    assert errs[-1] <= 1e-10 * np.abs(xd).max()
+    assert errs[5] / errs[4] < 0.8
+
+
 def test_p2_solve_matches_printed_matrix():
     """y = P^{-1} w = P2^{-1} P1^{-1} w with P2 as printed in Sec. 4.2."""
     h = W.uniform(4)
