@@ -404,11 +404,11 @@ __global__ void __launch_bounds__(SW_THREADS, 4) k_bsweep(const __grid_constant_
 // other colour) at their current values.  The forward elimination keeps c'
 // in cp (a scratch vector of the correction's layout) and d' in e; the back
 // substitution overwrites e.  Grid (lines / 128, 2 fields).
-// ZERO: the neighbours are 0 (the first pass of a level).  ADD: u += e on
-// uncovered cells (the last pass on level 0).
-template <class P, bool ZERO, bool ADD>
-__global__ void __launch_bounds__(128) k_bline(BoxK<P> B, int colour, P* cpbuf,
-                                                const uint8_t* mask, P* u) {
+// ZERO: the neighbours are 0 (the first pass of a level).  (On level 0 the
+// caller adds the correction of both colours' lines to the composite
+// solution after the last pass.)
+template <class P, bool ZERO>
+__global__ void __launch_bounds__(128) k_bline(BoxK<P> B, int colour, P* cpbuf) {
   const int fld = blockIdx.y;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= B.n1 * B.n2) return;
@@ -444,12 +444,10 @@ __global__ void __launch_bounds__(128) k_bline(BoxK<P> B, int colour, P* cpbuf,
     e[idx] = dprev;
   }
   P x = dprev;
-  if (ADD && !(mask[base + n0 - 1] & MASK_COVERED)) u[fld * B.vfs + base + n0 - 1] += x;
   for (int i = n0 - 2; i >= 0; i--) {
     const int idx = base + i;
     x = e[idx] - cp[idx] * x;
     e[idx] = x;
-    if (ADD && !(mask[idx] & MASK_COVERED)) u[fld * B.vfs + idx] += x;
   }
 }
 
@@ -1528,11 +1526,14 @@ void box_lines(const BoxK<P>& V, P* scratch, int sweeps, bool red_first, bool ze
     for (int pass = 0; pass < 2; pass++) {
       const int colour = red_first ? pass : 1 - pass;
       const bool Z = zero && sw == 0 && pass == 0;
-      const bool D = addu && sw == sweeps - 1 && pass == 1;
-      if (Z) k_bline<P, true, false><<<g, 128, 0, s>>>(V, colour, scratch, mask, addu);
-      else if (D) k_bline<P, false, true><<<g, 128, 0, s>>>(V, colour, scratch, mask, addu);
-      else k_bline<P, false, false><<<g, 128, 0, s>>>(V, colour, scratch, mask, addu);
+      if (Z) k_bline<P, true><<<g, 128, 0, s>>>(V, colour, scratch);
+      else k_bline<P, false><<<g, 128, 0, s>>>(V, colour, scratch);
     }
+  // the correction of both colours' lines into the composite solution
+  if (addu) {
+    const int n = V.n0 * V.n1 * V.n2;
+    k_add_leaf<P><<<dim3(g1(n), 2), BS, 0, s>>>(mask, 0, n, (int)V.vfs, V.e, addu);
+  }
 }
 
 // does box level m smooth with the one-launch sweep (ping-pong buffers)?
