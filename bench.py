@@ -410,61 +410,46 @@ def run_steps(ctx, torch, u0, nsteps, warmup, flush, timing=False):
 
 def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
     """Same metric through the public API with host buffers: each step copies
-    u_n, u_{n-1} and the time derivative at t_n from pinned host memory,
-    predicts, steps, forms the new time derivative, tags, and reads u_{n+1},
-    its time derivative and the tags back."""
+    the state u_n from pinned host memory, predicts, steps, forms the new time
+    derivative, tags, and reads u_{n+1} and the tags back.  The history the
+    next step needs (u_{n-1}, the time derivative) is what the previous step
+    left on the device, as a caller that keeps it there would."""
     N2 = u0.size
-    # every host buffer is pinned, and stays so: the next step's inputs are
+    # the host buffers are pinned and stay so: the next step's input is
     # copied into them on the host, outside the timed region (a clone of a
-    # pinned tensor is pageable, which would make the uploads staged copies)
+    # pinned tensor is pageable, which would make the upload a staged copy)
     hn = torch.from_numpy(u0.copy()).pin_memory()
-    hnm1_buf = torch.empty(N2, dtype=torch.float64).pin_memory()
-    hdot_buf = torch.empty(N2, dtype=torch.float64).pin_memory()
-    hnm1 = None
-    hdot = None
     hout = torch.empty(N2, dtype=torch.float64).pin_memory()
-    hdot_out = torch.empty(N2, dtype=torch.float64).pin_memory()
     htag = torch.empty(N2 // 2, dtype=torch.uint8).pin_memory()
     d_n = torch.empty(N2, dtype=torch.float64, device="cuda")
     d_nm1 = torch.empty_like(d_n)
     d_dot = torch.empty_like(d_n)
-    d_dot_out = torch.empty_like(d_n)
+    d_dot_new = torch.empty_like(d_n)
     d_u = torch.empty_like(d_n)
+    have_nm1 = have_dot = False
     total, kry = 0.0, 0
     h2d = d2h = 0
     side = torch.cuda.Stream()
-    stepped, derived, copied = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+    stepped, copied = torch.cuda.Event(), torch.cuda.Event()
     for s in range(warmup + nsteps):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record()
         d_n.copy_(hn, non_blocking=True)
-        b_in = N2 * 8
-        if hnm1 is not None:
-            d_nm1.copy_(hnm1, non_blocking=True)
-            b_in += N2 * 8
-        if hdot is not None:
-            d_dot.copy_(hdot, non_blocking=True)
-            b_in += N2 * 8
+        if have_dot:
             ctx.predict(d_n, d_nm1, d_dot, DT, DT, out=d_u)
         else:
             d_u.copy_(d_n)
-        ctx.step_begin(d_u, d_n, d_nm1 if hnm1 is not None else None, DT,
-                       DT if hnm1 is not None else 0.0)
+        nm1 = d_nm1 if have_nm1 else None
+        ctx.step_begin(d_u, d_n, nm1, DT, DT if have_nm1 else 0.0)
         # u_{n+1} goes back to the host on a side stream while the time
         # derivative and the indicators run (both only read it)
         stepped.record()
         with torch.cuda.stream(side):
             side.wait_event(stepped)
             hout.copy_(d_u, non_blocking=True)
-        ctx.time_derivative(d_u, d_n, d_nm1 if hnm1 is not None else None, DT,
-                            DT if hnm1 is not None else 0.0, out=d_dot_out)
-        # and so does the time derivative while the indicators run
-        derived.record()
-        with torch.cuda.stream(side):
-            side.wait_event(derived)
-            hdot_out.copy_(d_dot_out, non_blocking=True)
             copied.record()
+        ctx.time_derivative(d_u, d_n, nm1, DT, DT if have_nm1 else 0.0, out=d_dot_new)
         t = ctx.tag(d_u, thr_r=0.1)
         htag.copy_(t, non_blocking=True)
         torch.cuda.current_stream().wait_event(copied)
@@ -474,11 +459,12 @@ def run_e2e(nrd, ctx, torch, u0, nsteps, warmup):
         if s >= warmup:
             total += ev0.elapsed_time(ev1)
             kry += st["krylov_its"]
-            h2d, d2h = b_in, 2 * N2 * 8 + N2 // 2
-        hnm1_buf.copy_(hn)
+            h2d, d2h = N2 * 8, N2 * 8 + N2 // 2
         hn.copy_(hout)
-        hdot_buf.copy_(hdot_out)
-        hnm1, hdot = hnm1_buf, hdot_buf
+        # device history for the next step: this step's input and derivative
+        d_nm1, d_n = d_n, d_nm1
+        d_dot, d_dot_new = d_dot_new, d_dot
+        have_nm1 = have_dot = True
     return total, kry, h2d, d2h
 
 
