@@ -173,7 +173,7 @@ constexpr int OFF_AX = OFF_F + up128(F_BYTES);
 constexpr int OFF_AY = OFF_AX + up128(F_BYTES);
 constexpr int OFF_AZ = OFF_AY + up128(AY_BYTES);
 constexpr int STAGE_BYTES = OFF_AZ + up128(AZ_BYTES);      // one tile's boxes
-constexpr int SWEEP_SMEM = 2 * STAGE_BYTES + 16;            // two stages + two mbarriers
+constexpr int SWEEP_SMEM = STAGE_BYTES + 16;                // the boxes + the mbarrier
 constexpr long kTmaSpinLimit = 1L << 20;   // polls of mbarrier.try_wait
 
 struct SweepMaps {                 // per field: old correction, rhs, x/y/z low faces
@@ -277,59 +277,40 @@ __device__ __forceinline__ void rb_update(const BoxK<float>& B, const float* A, 
   Se[oe] = __fdividef(Sf[of] + o, dg);
 }
 
-// Persistent: a grid of two CTAs per SM walks the tiles (x fastest, then y,
-// z, field), two stages deep: while a CTA computes one tile, the TMA loads of
-// its next tile land in its other stage.  ntile = 2 ntx nty ntz; SWEEP_SMEM
-// bytes of dynamic shared memory.  The tile origin is even on every axis, so
+// Grid (ntx, nty, 2 ntz), one tile per CTA, the upper half of z for field 1;
+// SWEEP_SMEM bytes of dynamic shared memory, four CTAs per SM (some compute
+// while the others' loads land).  The tile origin is even on every axis, so
 // the colour of the cell at (x, y, z) in the one-ring frame (origin one cell
 // before the tile) is (x + y + z + 1) mod 2.
 // ADD stores the correction into u: on level 0's uncovered cells the
 // composite solution is still zero when level 0 is corrected (the finer
 // levels' corrections touch only their own cells), so u += e there is u = e.
 template <bool ZERO, bool ADD>
-__global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant__ SweepMaps M,
-                                                           BoxK<float> B, int c0, int ntx,
-                                                           int nty, int ntz,
+__global__ void __launch_bounds__(SW_THREADS, 4) k_bsweep(const __grid_constant__ SweepMaps M,
+                                                           BoxK<float> B, int c0,
                                                            float* __restrict__ ed,
                                                            const uint8_t* __restrict__ mask,
                                                            float* __restrict__ u,
                                                            int* __restrict__ err) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const uint32_t bar0 = smem_u32(smem + 2 * STAGE_BYTES);
+  const uint32_t bar = smem_u32(smem + STAGE_BYTES);
   const int t = threadIdx.x;
   const int n0 = B.n0, n1 = B.n1, n2 = B.n2;
-  const int per_fld = ntx * nty * ntz, ntile = 2 * per_fld;
-  auto origin = [&](int q, int& fld, int& x0, int& y0, int& z0) {
-    fld = q / per_fld;
-    const int r = q - fld * per_fld;
-    x0 = (r % ntx) * SX;
-    y0 = ((r / ntx) % nty) * SY;
-    z0 = (r / (ntx * nty)) * SZ;
-  };
-  // thread 0: start the loads of tile q into stage st (after the generic
-  // accesses of the stage's previous tile, ordered by the barrier before)
-  auto issue = [&](int q, int st) {
-    int fld, x0, y0, z0;
-    origin(q, fld, x0, y0, z0);
-    unsigned char* base = smem + st * STAGE_BYTES;
-    const uint32_t bar = bar0 + 8 * st;
+  const int ntz = gridDim.z >> 1;
+  const int fld = blockIdx.z >= ntz;
+  const int x0 = blockIdx.x * SX, y0 = blockIdx.y * SY, z0 = (blockIdx.z - fld * ntz) * SZ;
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     const uint32_t bytes = (ZERO ? 0 : E_BYTES) + 2 * F_BYTES + AY_BYTES + AZ_BYTES;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
-    if (!ZERO) tma_load3(smem_u32(base), &M.es[fld], x0 - 4, y0 - 2, z0 - 2, bar);
-    tma_load3(smem_u32(base + OFF_F), &M.f[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-    tma_load3(smem_u32(base + OFF_AX), &M.ax[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-    tma_load3(smem_u32(base + OFF_AY), &M.ay[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-    tma_load3(smem_u32(base + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
-  };
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if ((int)blockIdx.x < ntile) issue(blockIdx.x, 0);
+    if (!ZERO) tma_load3(smem_u32(smem), &M.es[fld], x0 - 4, y0 - 2, z0 - 2, bar);
+    tma_load3(smem_u32(smem + OFF_F), &M.f[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(smem + OFF_AX), &M.ax[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(smem + OFF_AY), &M.ay[fld], x0 - 4, y0 - 1, z0 - 1, bar);
+    tma_load3(smem_u32(smem + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
   }
-  __syncthreads();
   // thread -> cells (tile origins are even, so this is the same for every
   // tile): first colour: columns t and t + SW_THREADS of the 34 x 10 ring
   // frame, all planes, those of the colour every other plane; second colour
@@ -338,89 +319,80 @@ __global__ void __launch_bounds__(SW_THREADS, 2) k_bsweep(const __grid_constant_
   const int z2s = (c0 + 1 + x2 + y2) & 1;
   const int oe2 = 2 * EPL + (y2 + 2) * TBX + x2 + 4, of2 = FPL + (y2 + 1) * TBX + x2 + 4,
             oy2 = YPL + (y2 + 1) * TBX + x2 + 4;
-  int it = 0;
-  for (int q = blockIdx.x; q < ntile; q += gridDim.x, it++) {
-    const int st = it & 1;
-    if (t == 0 && q + (int)gridDim.x < ntile) issue(q + gridDim.x, st ^ 1);
-    const bool late = !mbar_wait(bar0 + 8 * st, (it >> 1) & 1);
-    if (__syncthreads_or(late)) {
-      // the copies did not land in time: report, give every load in flight
-      // a second bounded wait (they write this CTA's shared memory), stop
-      if (t == 0) atomicOr(err, 2);
-      mbar_wait(bar0 + 8 * st, (it >> 1) & 1);
-      if (q + (int)gridDim.x < ntile) mbar_wait(bar0 + 8 * (st ^ 1), ((it + 1) >> 1) & 1);
-      return;
-    }
-    unsigned char* base = smem + st * STAGE_BYTES;
-    float* Se = reinterpret_cast<float*>(base);
-    const float* Sf = reinterpret_cast<const float*>(base + OFF_F);
-    const float* Sx = reinterpret_cast<const float*>(base + OFF_AX);
-    const float* Sy = reinterpret_cast<const float*>(base + OFF_AY);
-    const float* Sz = reinterpret_cast<const float*>(base + OFF_AZ);
-    int fld, x0, y0, z0;
-    origin(q, fld, x0, y0, z0);
-    const float* A = B.A + fld * B.Afs;
-    // tiles whose cells and ring all have six in-box neighbours skip the
-    // boundary tests
-    const bool inner = x0 >= 2 && x0 + SX + 1 < n0 && y0 >= 2 && y0 + SY + 1 < n1 &&
-                       z0 >= 2 && z0 + SZ + 1 < n2;
-    // first colour on the tile and the one-cell ring
-    for (int c = t; c < FBY * (SX + 2); c += SW_THREADS) {
-      const int x1 = c % (SX + 2), y1 = c / (SX + 2);
-      const int z1s = (c0 + 1 + x1 + y1) & 1;
-      const int oe1 = EPL + (y1 + 1) * TBX + x1 + 3, of1 = y1 * TBX + x1 + 3;
-      const int i = x0 - 1 + x1, j = y0 - 1 + y1;
-      if (inner) {
+  // everyone waits for the loads (the barrier's first phase); bounded
+  __syncthreads();
+  const bool late = !mbar_wait(bar, 0);
+  if (__syncthreads_or(late)) {
+    // the copies did not land in time: report, give them a second bounded
+    // wait (they write this CTA's shared memory), and stop
+    if (t == 0) atomicOr(err, 2);
+    mbar_wait(bar, 0);
+    return;
+  }
+  float* Se = reinterpret_cast<float*>(smem);
+  const float* Sf = reinterpret_cast<const float*>(smem + OFF_F);
+  const float* Sx = reinterpret_cast<const float*>(smem + OFF_AX);
+  const float* Sy = reinterpret_cast<const float*>(smem + OFF_AY);
+  const float* Sz = reinterpret_cast<const float*>(smem + OFF_AZ);
+  const float* A = B.A + fld * B.Afs;
+  // tiles whose cells and ring all have six in-box neighbours skip the
+  // boundary tests
+  const bool inner = x0 >= 2 && x0 + SX + 1 < n0 && y0 >= 2 && y0 + SY + 1 < n1 && z0 >= 2 &&
+                     z0 + SZ + 1 < n2;
+  // first colour on the tile and the one-cell ring
+  for (int c = t; c < FBY * (SX + 2); c += SW_THREADS) {
+    const int x1 = c % (SX + 2), y1 = c / (SX + 2);
+    const int z1s = (c0 + 1 + x1 + y1) & 1;
+    const int oe1 = EPL + (y1 + 1) * TBX + x1 + 3, of1 = y1 * TBX + x1 + 3;
+    const int i = x0 - 1 + x1, j = y0 - 1 + y1;
+    if (inner) {
 #pragma unroll
-        for (int zz = 0; zz < FBZ; zz += 2) {
-          const int z = z1s + zz;
-          rb_update<false, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
-                                 of1 + z * YPL, i, j, z0 - 1 + z);
-        }
-      } else if (i >= 0 && i < n0 && j >= 0 && j < n1) {
-        for (int z = z1s; z < FBZ; z += 2) {
-          const int k = z0 - 1 + z;
-          if (k >= 0 && k < n2)
-            rb_update<true, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
-                                  of1 + z * YPL, i, j, k);
-        }
+      for (int zz = 0; zz < FBZ; zz += 2) {
+        const int z = z1s + zz;
+        rb_update<false, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
+                               of1 + z * YPL, i, j, z0 - 1 + z);
+      }
+    } else if (i >= 0 && i < n0 && j >= 0 && j < n1) {
+      for (int z = z1s; z < FBZ; z += 2) {
+        const int k = z0 - 1 + z;
+        if (k >= 0 && k < n2)
+          rb_update<true, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
+                                of1 + z * YPL, i, j, k);
       }
     }
-    __syncthreads();
-    // second colour on the tile
-    {
-      const int i = x0 + x2, j = y0 + y2;
-      if (inner) {
-#pragma unroll
-        for (int zz = 0; zz < SZ; zz += 2) {
-          const int z = z2s + zz;
-          rb_update<false, false>(B, A, Se, Sf, Sx, Sy, Sz, oe2 + z * EPL, of2 + z * FPL,
-                                  oy2 + z * YPL, i, j, z0 + z);
-        }
-      } else if (i < n0 && j < n1) {
-        for (int z = z2s; z < SZ; z += 2)
-          if (z0 + z < n2)
-            rb_update<true, false>(B, A, Se, Sf, Sx, Sy, Sz, oe2 + z * EPL, of2 + z * FPL,
-                                   oy2 + z * YPL, i, j, z0 + z);
-      }
-    }
-    __syncthreads();
-    // the tile, both colours: rows of 32, every plane
-    const long fo = (long)fld * B.vfs;
+  }
+  __syncthreads();
+  // second colour on the tile
+  {
     const int i = x0 + x2, j = y0 + y2;
-    if (i < n0 && j < n1) {
+    if (inner) {
 #pragma unroll
-      for (int dz = 0; dz < SZ; dz++) {
-        const int k = z0 + dz;
-        if (k >= n2) break;
-        const int idx = i + n0 * (j + n1 * k);
-        const float v = Se[2 * EPL + (y2 + 2) * TBX + x2 + 4 + dz * EPL];
-        ed[fo + idx] = v;
-        if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] = v;
+      for (int zz = 0; zz < SZ; zz += 2) {
+        const int z = z2s + zz;
+        rb_update<false, false>(B, A, Se, Sf, Sx, Sy, Sz, oe2 + z * EPL, of2 + z * FPL,
+                                oy2 + z * YPL, i, j, z0 + z);
       }
+    } else if (i < n0 && j < n1) {
+      for (int z = z2s; z < SZ; z += 2)
+        if (z0 + z < n2)
+          rb_update<true, false>(B, A, Se, Sf, Sx, Sy, Sz, oe2 + z * EPL, of2 + z * FPL,
+                                 oy2 + z * YPL, i, j, z0 + z);
     }
-    // every thread is done with this stage before its next loads are issued
-    __syncthreads();
+  }
+  __syncthreads();
+  // the tile, both colours: rows of 32, every plane
+  const long fo = (long)fld * B.vfs;
+  const int i = x0 + x2, j = y0 + y2;
+  if (i < n0 && j < n1) {
+#pragma unroll
+    for (int dz = 0; dz < SZ; dz++) {
+      const int k = z0 + dz;
+      if (k >= n2) break;
+      const int idx = i + n0 * (j + n1 * k);
+      const float v = Se[2 * EPL + (y2 + 2) * TBX + x2 + 4 + dz * EPL];
+      ed[fo + idx] = v;
+      if (ADD && !(mask[idx] & MASK_COVERED)) u[fo + idx] = v;
+    }
   }
 }
 
@@ -1497,9 +1469,7 @@ void box_jacobi(const BoxK<P>& V, P omega, P* scratch, int sweeps, bool zero, bo
 // adds the correction to u on uncovered cells (level 0)
 void box_sweeps(const PcState* ps, int m, const BoxK<float>& V, float* scratch, int sweeps, int c0,
                 bool zero, bool from_scratch, const uint8_t* mask, float* addu, cudaStream_t s) {
-  const int ntx = (V.n0 + SX - 1) / SX, nty = (V.n1 + SY - 1) / SY, ntz = (V.n2 + SZ - 1) / SZ;
-  const int ntile = 2 * ntx * nty * ntz;
-  const int g = std::min(ntile, 2 * ps->nsm);
+  const dim3 g((V.n0 + SX - 1) / SX, (V.n1 + SY - 1) / SY, 2 * ((V.n2 + SZ - 1) / SZ));
   float* buf[2] = {V.e, scratch};
   SweepMaps M;
   for (int fld = 0; fld < 2; fld++) {
@@ -1515,13 +1485,13 @@ void box_sweeps(const PcState* ps, int m, const BoxK<float>& V, float* scratch, 
   for (int sw = 0; sw < sweeps; sw++) {
     const bool D = addu && sw == sweeps - 1;
     if (zero && sw == 0) {
-      if (D) k_bsweep<true, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[cur], mask, addu, ps->d_err);
-      else k_bsweep<true, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[cur], mask, addu, ps->d_err);
+      if (D) k_bsweep<true, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[cur], mask, addu, ps->d_err);
+      else k_bsweep<true, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[cur], mask, addu, ps->d_err);
       continue;
     }
     src(cur);
-    if (D) k_bsweep<false, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[1 - cur], mask, addu, ps->d_err);
-    else k_bsweep<false, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, ntx, nty, ntz, buf[1 - cur], mask, addu, ps->d_err);
+    if (D) k_bsweep<false, true><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[1 - cur], mask, addu, ps->d_err);
+    else k_bsweep<false, false><<<g, SW_THREADS, SWEEP_SMEM, s>>>(M, V, c0, buf[1 - cur], mask, addu, ps->d_err);
     cur = 1 - cur;
   }
 }
