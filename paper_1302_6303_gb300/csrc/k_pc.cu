@@ -312,8 +312,9 @@ __global__ void __launch_bounds__(SW_THREADS, 4) k_bsweep(const __grid_constant_
     tma_load3(smem_u32(smem + OFF_AZ), &M.az[fld], x0 - 4, y0 - 1, z0 - 1, bar);
   }
   // thread -> cells (tile origins are even, so this is the same for every
-  // tile): second colour and write: column (x2, y2) = t of the tile, all
-  // planes
+  // tile): first colour: columns t and t + SW_THREADS of the 34 x 10 ring
+  // frame, all planes, those of the colour every other plane; second colour
+  // and write: column (x2, y2) = t of the tile, all planes
   const int x2 = t & (SX - 1), y2 = t / SX;
   const int z2s = (c0 + 1 + x2 + y2) & 1;
   const int oe2 = 2 * EPL + (y2 + 2) * TBX + x2 + 4, of2 = FPL + (y2 + 1) * TBX + x2 + 4,
@@ -338,22 +339,26 @@ __global__ void __launch_bounds__(SW_THREADS, 4) k_bsweep(const __grid_constant_
   // boundary tests
   const bool inner = x0 >= 2 && x0 + SX + 1 < n0 && y0 >= 2 && y0 + SY + 1 < n1 && z0 >= 2 &&
                      z0 + SZ + 1 < n2;
-  // first colour on the tile and the one-cell ring: (column, plane pair)
-  // items, FBZ / 2 per column of the 34 x 10 ring frame, spread evenly over
-  // the threads
-  constexpr int NC1 = FBY * (SX + 2);
-  for (int q = t; q < NC1 * (FBZ / 2); q += SW_THREADS) {
-    const int c = q % NC1, zz = 2 * (q / NC1);
+  // first colour on the tile and the one-cell ring
+  for (int c = t; c < FBY * (SX + 2); c += SW_THREADS) {
     const int x1 = c % (SX + 2), y1 = c / (SX + 2);
-    const int z = ((c0 + 1 + x1 + y1) & 1) + zz;
+    const int z1s = (c0 + 1 + x1 + y1) & 1;
     const int oe1 = EPL + (y1 + 1) * TBX + x1 + 3, of1 = y1 * TBX + x1 + 3;
-    const int i = x0 - 1 + x1, j = y0 - 1 + y1, k = z0 - 1 + z;
+    const int i = x0 - 1 + x1, j = y0 - 1 + y1;
     if (inner) {
-      rb_update<false, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
-                             of1 + z * YPL, i, j, k);
-    } else if (i >= 0 && i < n0 && j >= 0 && j < n1 && k >= 0 && k < n2) {
-      rb_update<true, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
-                            of1 + z * YPL, i, j, k);
+#pragma unroll
+      for (int zz = 0; zz < FBZ; zz += 2) {
+        const int z = z1s + zz;
+        rb_update<false, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
+                               of1 + z * YPL, i, j, z0 - 1 + z);
+      }
+    } else if (i >= 0 && i < n0 && j >= 0 && j < n1) {
+      for (int z = z1s; z < FBZ; z += 2) {
+        const int k = z0 - 1 + z;
+        if (k >= 0 && k < n2)
+          rb_update<true, ZERO>(B, A, Se, Sf, Sx, Sy, Sz, oe1 + z * EPL, of1 + z * FPL,
+                                of1 + z * YPL, i, j, k);
+      }
     }
   }
   __syncthreads();
