@@ -501,7 +501,7 @@ def regrid_leg(nrd, ctx, torch, h, z, r):
     k_ms, _ = cn.timing_read()["transfer"]
     cn.timing_enable(False)
     No, Nn, nvec = ctx.N, cn.N, 2
-    alg = 2 * 16 * nvec * No + 40 * Nn + 2 * 16 * nvec * Nn
+    alg = 2 * 16 * nvec * No + 4 * Nn + 2 * 16 * nvec * Nn
     # warm restart: the last step solved again (backward-Euler form from the
     # transferred u_{n-1}) from the transferred u_n
     un = moved[0].contiguous()
@@ -513,8 +513,9 @@ def regrid_leg(nrd, ctx, torch, h, z, r):
             "leaf_cells_new": cn.nleaf, "transfer_ms_total": transfer_ms,
             "transfer_kernel_ms": k_ms, "transfer_vectors": nvec,
             "transfer_gbs": alg / (k_ms * 1e-3) / 1e9 if k_ms > 0 else None,
-            "transfer_bytes": "copy of the old vectors (read+write) + 40 B descriptor + one "
-                              "read and one write per new value",
+            "transfer_bytes": "copy of the old vectors (read+write) + 4 B source code per new "
+                              "cell + one read and one write per new value (the 44 B entries "
+                              "of reconstructed cells not counted)",
             "resolve_ms": e0.elapsed_time(e1), "resolve_newton": st["newton_its"],
             "resolve_krylov": st["krylov_its"], "fnorm_after_transfer": st["fnorm0"],
             "fnorm_resolved": st["fnorm"]}

@@ -51,7 +51,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         res = list(ex.map(lambda u: _compile(u, verbose_ptxas), UNITS))
     objs = [o for o, _ in res]
     tmp = OUT + ".tmp%d" % os.getpid()
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -25,7 +25,8 @@
 // recursion accepts them (lower part first).
 //
 // nrd_transfer: conservative limited-linear transfer of state vectors from an
-// old to a new hierarchy (device gather, descriptor built on the host).  The
+// old to a new hierarchy (device gather; the per-cell source list is built on
+// host threads).  The
 // old vectors are first made composite (covered cells := mean of their
 // children).  A new cell that exists on the same level of the old hierarchy
 // copies it; any other new cell evaluates, at its centre, the limited linear
@@ -38,8 +39,10 @@
 // so positivity is kept).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "nrd_internal.h"
@@ -54,56 +57,117 @@ struct IBox {
   int side(int d) const { return hi[d] - lo[d] + 1; }
 };
 
+// One axis of a box filter of a dense 0/1 field of n[0] x n[1] x n[2] cells:
+// v[c] := AND (MIN) or OR (!MIN) of v over the cells within r of c along
+// axis d that lie inside the field.  v is viewed as [outer][n[d]][inner],
+// and each output row along the contiguous inner index combines 2r + 1
+// input rows.
+template <bool MIN>
+void box_filter_t(std::vector<uint8_t>& v, const int n[3], int d, int r) {
+  const long inner = d == 0 ? 1 : (d == 1 ? (long)n[0] : (long)n[0] * n[1]);
+  const long outer = (long)v.size() / (inner * n[d]);
+  const int m = n[d];
+  std::vector<uint8_t> w(v.size());
+  auto op = [](uint8_t a, uint8_t b) -> uint8_t { return MIN ? (a & b) : (a | b); };
+  for (long o = 0; o < outer; o++) {
+    const uint8_t* vo = &v[o * m * inner];
+    uint8_t* wo = &w[o * m * inner];
+    if (inner == 1) {  // along the row: combine the row with its shifts
+      std::memcpy(wo, vo, m);
+      for (int s = 1; s <= r && s < m; s++) {
+        for (int x = 0; x + s < m; x++) wo[x] = op(wo[x], vo[x + s]);
+        for (int x = s; x < m; x++) wo[x] = op(wo[x], vo[x - s]);
+      }
+      continue;
+    }
+    for (int x = 0; x < m; x++) {
+      const int y0 = std::max(0, x - r), y1 = std::min(m - 1, x + r);
+      uint8_t* dst = wo + x * inner;
+      std::memcpy(dst, vo + y0 * inner, inner);
+      for (int y = y0 + 1; y <= y1; y++) {
+        const uint8_t* src = vo + y * inner;
+        for (long t = 0; t < inner; t++) dst[t] = op(dst[t], src[t]);
+      }
+    }
+  }
+  v.swap(w);
+}
+
+void box_filter(std::vector<uint8_t>& v, const int n[3], int d, int r, bool take_min) {
+  if (take_min)
+    box_filter_t<true>(v, n, d, r);
+  else
+    box_filter_t<false>(v, n, d, r);
+}
+
+// Counts over boxes in O(1): a summed-area table of a dense 0/1 field,
+// S(i, j, k) = number of set cells in [0, i) x [0, j) x [0, k).
+struct BoxSum {
+  int n[3];
+  std::vector<int> S;
+  BoxSum(const std::vector<uint8_t>& v, const int nn[3]) {
+    for (int d = 0; d < 3; d++) n[d] = nn[d];
+    const long sx = n[0] + 1, sxy = sx * (n[1] + 1);
+    S.assign(sxy * (n[2] + 1), 0);
+    for (int k = 0; k < n[2]; k++)
+      for (int j = 0; j < n[1]; j++) {
+        const uint8_t* row = &v[(long)n[0] * (j + (long)n[1] * k)];
+        int* o = &S[(k + 1) * sxy + (j + 1) * sx];
+        const int* dn = o - sx;        // (j, k + 1)
+        const int* bk = o - sxy;       // (j + 1, k)
+        const int* db = o - sx - sxy;  // (j, k)
+        int line = 0;                  // running sum along the row
+        for (int i = 0; i < n[0]; i++) {
+          line += row[i] ? 1 : 0;
+          o[i + 1] = line + dn[i + 1] + bk[i + 1] - db[i + 1];
+        }
+      }
+  }
+  long count(const int lo[3], const int hi[3]) const {
+    const long sx = n[0] + 1, sxy = sx * (n[1] + 1);
+    auto at = [&](int i, int j, int k) { return (long)S[k * sxy + j * sx + i]; };
+    const int a0 = lo[0], a1 = lo[1], a2 = lo[2], b0 = hi[0] + 1, b1 = hi[1] + 1, b2 = hi[2] + 1;
+    return at(b0, b1, b2) - at(a0, b1, b2) - at(b0, a1, b2) - at(b0, b1, a2) + at(a0, a1, b2) +
+           at(a0, b1, a2) + at(b0, a1, a2) - at(a0, a1, a2);
+  }
+};
+
 struct Clusterer {
-  const std::vector<uint8_t>& tag;   // dense level-l tags
-  const std::vector<uint8_t>& ok;    // dense: cell may hold the finer level
+  const BoxSum& tag;   // level-l tags
+  const BoxSum& ok;    // level-l cells that may hold the finer level
   int n[3];
   double eff;
   int max_side, min_side;            // in level-l cells
   std::vector<IBox>& out;
 
-  long at(int i, int j, int k) const { return i + (long)n[0] * (j + (long)n[1] * k); }
+  // sig[x] = tags in the plane lo[d] + x of the box, along axis d
+  void signature(const IBox& b, int d, std::vector<long>& sig) const {
+    sig.assign(b.side(d), 0);
+    int lo[3] = {b.lo[0], b.lo[1], b.lo[2]}, hi[3] = {b.hi[0], b.hi[1], b.hi[2]};
+    for (int x = 0; x < b.side(d); x++) {
+      lo[d] = hi[d] = b.lo[d] + x;
+      sig[x] = tag.count(lo, hi);
+    }
+  }
 
+  // the box cut down to the bounding box of its tags; false if it has none
   bool shrink(IBox& b, long& cnt) const {
-    int lo[3] = {b.hi[0], b.hi[1], b.hi[2]}, hi[3] = {b.lo[0], b.lo[1], b.lo[2]};
-    cnt = 0;
-    for (int k = b.lo[2]; k <= b.hi[2]; k++)
-      for (int j = b.lo[1]; j <= b.hi[1]; j++)
-        for (int i = b.lo[0]; i <= b.hi[0]; i++)
-          if (tag[at(i, j, k)]) {
-            cnt++;
-            const int c[3] = {i, j, k};
-            for (int d = 0; d < 3; d++) {
-              lo[d] = std::min(lo[d], c[d]);
-              hi[d] = std::max(hi[d], c[d]);
-            }
-          }
+    cnt = tag.count(b.lo, b.hi);
     if (!cnt) return false;
+    std::vector<long> sig;
     for (int d = 0; d < 3; d++) {
-      b.lo[d] = lo[d];
-      b.hi[d] = hi[d];
+      signature(b, d, sig);
+      int f = 0, l = b.side(d) - 1;
+      while (!sig[f]) f++;
+      while (!sig[l]) l--;
+      const int lo = b.lo[d];
+      b.lo[d] = lo + f;
+      b.hi[d] = lo + l;
     }
     return true;
   }
 
-  bool all_ok(const IBox& b) const {
-    for (int k = b.lo[2]; k <= b.hi[2]; k++)
-      for (int j = b.lo[1]; j <= b.hi[1]; j++)
-        for (int i = b.lo[0]; i <= b.hi[0]; i++)
-          if (!ok[at(i, j, k)]) return false;
-    return true;
-  }
-
-  void signature(const IBox& b, int d, std::vector<long>& sig) const {
-    sig.assign(b.side(d), 0);
-    for (int k = b.lo[2]; k <= b.hi[2]; k++)
-      for (int j = b.lo[1]; j <= b.hi[1]; j++)
-        for (int i = b.lo[0]; i <= b.hi[0]; i++)
-          if (tag[at(i, j, k)]) {
-            const int c[3] = {i, j, k};
-            sig[c[d] - b.lo[d]]++;
-          }
-  }
+  bool all_ok(const IBox& b) const { return ok.count(b.lo, b.hi) == b.vol(); }
 
   void run(IBox b) {
     long cnt;
@@ -181,10 +245,15 @@ struct Clusterer {
   }
 };
 
-struct TransferDesc {
-  int src;          // old cell (copy) or old coarse cell (reconstruction)
-  int nb[6];        // old neighbours of src on its level (-1: none), x-, x+, y-, ...
-  float off[3];     // (x - x_c) / h_c of the new cell centre per axis (exact in float)
+// A new cell that is not a copy of an old cell on its own level: the old
+// coarse cell src, its six neighbours on that level (-1: none; x-, x+, y-,
+// ...) and the new cell centre relative to src's, (x - x_c) / h_c per axis
+// (a multiple of 1/2^(l - lc + 1), exact in float).
+struct ReconDesc {
+  int cell;         // the new cell
+  int src;
+  int nb[6];
+  float off[3];
 };
 
 __device__ __forceinline__ double minmod(double a, double b) {
@@ -192,19 +261,30 @@ __device__ __forceinline__ double minmod(double a, double b) {
   return (fabs(a) < fabs(b)) ? a : b;
 }
 
-__global__ void k_transfer(const TransferDesc* __restrict__ d, int N, int Nold, int nvec,
-                           const double* __restrict__ uo, double* __restrict__ un) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-    const TransferDesc t = d[c];
+// Threads [0, N): new cells with code >= 0 copy old cell code for every
+// field.  Threads [N, N + nrec): the reconstruction entries.
+__global__ void k_transfer(const int* __restrict__ code, const ReconDesc* __restrict__ rec,
+                           int N, int nrec, int Nold, int nvec, const double* __restrict__ uo,
+                           double* __restrict__ un) {
+  const long total = (long)N + nrec;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < total;
+       t += (long)gridDim.x * blockDim.x) {
+    if (t < N) {
+      const int src = code[t];
+      if (src < 0) continue;
+      for (int f = 0; f < 2 * nvec; f++) un[(long)f * N + t] = uo[(long)f * Nold + src];
+      continue;
+    }
+    const ReconDesc r = rec[t - N];
     for (int f = 0; f < 2 * nvec; f++) {
       const double* u = uo + (long)f * Nold;
-      const double uc = u[t.src];
+      const double uc = u[r.src];
       double v = uc;
       for (int a = 0; a < 3; a++) {
-        const int im = t.nb[2 * a], ip = t.nb[2 * a + 1];
-        if (im >= 0 && ip >= 0) v += minmod(uc - u[im], u[ip] - uc) * (double)t.off[a];
+        const int im = r.nb[2 * a], ip = r.nb[2 * a + 1];
+        if (im >= 0 && ip >= 0) v += minmod(uc - u[im], u[ip] - uc) * (double)r.off[a];
       }
-      un[(long)f * N + c] = v;
+      un[(long)f * N + r.cell] = v;
     }
   }
 }
@@ -249,6 +329,10 @@ int nrd_regrid_boxes(nrd_ctx* c, const uint8_t* tags, int tag_bits, int buffer,
   for (int l = 0; l + 1 < max_levels; l++) {
     const int n[3] = {n0[0] << l, n0[1] << l, n0[2] << l};
     const long lsize = (long)n[0] * n[1] * n[2];
+    if ((long)(n[0] + 1) * (n[1] + 1) * (n[2] + 1) > (long)INT32_MAX) {
+      c->err = "nrd_regrid_boxes: a level is too large for int32 box counts";
+      return NRD_EINVAL;
+    }
     auto li = [&](int i, int j, int k) { return i + (long)n[0] * (j + (long)n[1] * k); };
     std::vector<uint8_t> in(lsize, 0), raw(lsize, 0), tg(lsize, 0), ok(lsize, 0);
     for (const IBox& b : levels[l])
@@ -263,36 +347,20 @@ int nrd_regrid_boxes(nrd_ctx* c, const uint8_t* tags, int tag_bits, int buffer,
             }
             raw[li(i, j, k)] = t > 0 ? 1 : 0;
           }
-    for (int k = 0; k < n[2]; k++)
-      for (int j = 0; j < n[1]; j++)
-        for (int i = 0; i < n[0]; i++) {
-          if (!in[li(i, j, k)]) continue;
-          bool nest = true;
-          for (int dk = -1; dk <= 1 && nest; dk++)
-            for (int dj = -1; dj <= 1 && nest; dj++)
-              for (int di = -1; di <= 1 && nest; di++) {
-                const int q[3] = {i + di, j + dj, k + dk};
-                if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= n[0] || q[1] >= n[1] ||
-                    q[2] >= n[2])
-                  continue;
-                if (!in[li(q[0], q[1], q[2])]) nest = false;
-              }
-          ok[li(i, j, k)] = nest ? 1 : 0;
-          if (!nest) continue;
-          bool hit = false;
-          for (int dk = -buffer; dk <= buffer && !hit; dk++)
-            for (int dj = -buffer; dj <= buffer && !hit; dj++)
-              for (int di = -buffer; di <= buffer && !hit; di++) {
-                const int q[3] = {i + di, j + dj, k + dk};
-                if (q[0] < 0 || q[1] < 0 || q[2] < 0 || q[0] >= n[0] || q[1] >= n[1] ||
-                    q[2] >= n[2])
-                  continue;
-                if (raw[li(q[0], q[1], q[2])]) hit = true;
-              }
-          tg[li(i, j, k)] = hit ? 1 : 0;
-        }
+    // ok: every neighbour of the 3x3x3 block inside the domain is in the new
+    // level (proper nesting); tg: a raw tag within `buffer` cells (inside the
+    // domain), on ok cells.  Both are box filters, done one axis at a time:
+    // the minimum of `in` over windows of 3 (outside the domain counts as
+    // in), the maximum of `raw` over windows of 2 buffer + 1 (outside counts
+    // as untagged).
+    ok = in;
+    for (int d = 0; d < 3; d++) box_filter(ok, n, d, 1, true);
+    std::vector<uint8_t> hit = raw;
+    for (int d = 0; d < 3; d++) box_filter(hit, n, d, buffer, false);
+    for (long q = 0; q < lsize; q++) tg[q] = (ok[q] && hit[q]) ? 1 : 0;
     std::vector<IBox> coarse;
-    Clusterer C{tg, ok, {n[0], n[1], n[2]}, efficiency, max_side / 2, min_side / 2, coarse};
+    const BoxSum tsum(tg, n), osum(ok, n);
+    Clusterer C{tsum, osum, {n[0], n[1], n[2]}, efficiency, max_side / 2, min_side / 2, coarse};
     C.run(IBox{{0, 0, 0}, {n[0] - 1, n[1] - 1, n[2] - 1}});
     if (coarse.empty()) break;
     levels.emplace_back();
@@ -352,27 +420,40 @@ int nrd_transfer(nrd_ctx* src, nrd_ctx* dst, const double* u_src, double* u_dst,
       if (q[d] < 0 || q[d] >= A.lev[l].n[d]) return -1;
     return A.lmap[l][q[0] + (long)A.lev[l].n[0] * (q[1] + (long)A.lev[l].n[1] * q[2])];
   };
-  std::vector<TransferDesc> desc(B.N);
-  for (const PatchDev& P : B.patches) {
-    const int l = P.level;
-    for (int k = 0; k < P.n[2]; k++)
-      for (int j = 0; j < P.n[1]; j++)
-        for (int i = 0; i < P.n[0]; i++) {
-          const int q[3] = {P.lo[0] + i, P.lo[1] + j, P.lo[2] + k};
-          TransferDesc t;
-          for (int f = 0; f < 6; f++) t.nb[f] = -1;
-          for (int d = 0; d < 3; d++) t.off[d] = 0.0f;
-          t.src = old_cell(l, q);
-          if (t.src < 0) {
+  // Per new cell: the old cell on the same level (a copy), else -1 and a
+  // reconstruction entry.  Patches are split over host threads; each thread
+  // keeps its own entries, concatenated afterwards.
+  std::vector<int> code(B.N);
+  const int np = (int)B.patches.size();
+  int nth = (int)std::min<long>(16, std::max<long>(1, (long)B.N / 65536));
+  nth = std::max(1, std::min(nth, (int)std::thread::hardware_concurrency()));
+  std::vector<std::vector<ReconDesc>> recs(nth);
+  std::vector<int> fail(nth, 0);
+  auto work = [&](int th) {
+    // patches of thread th: a contiguous range holding about 1/nth of the cells
+    const long lo_cell = (long)B.N * th / nth, hi_cell = (long)B.N * (th + 1) / nth;
+    for (int p = 0; p < np; p++) {
+      const PatchDev& P = B.patches[p];
+      if (P.off < lo_cell || P.off >= hi_cell) continue;
+      const int l = P.level;
+      for (int k = 0; k < P.n[2]; k++)
+        for (int j = 0; j < P.n[1]; j++)
+          for (int i = 0; i < P.n[0]; i++) {
+            const int q[3] = {P.lo[0] + i, P.lo[1] + j, P.lo[2] + k};
+            const int c = P.off + i + P.n[0] * (j + P.n[1] * k);
+            code[c] = old_cell(l, q);
+            if (code[c] >= 0) continue;
             int lc = std::min(l, A.L) - 1, cq[3] = {0, 0, 0};
             for (; lc >= 0; lc--) {
               for (int d = 0; d < 3; d++) cq[d] = q[d] >> (l - lc);
               if (old_cell(lc, cq) >= 0) break;
             }
             if (lc < 0) {
-              dst->err = "transfer: a new cell lies in no old cell";
-              return NRD_EINVAL;
+              fail[th] = 1;
+              return;
             }
+            ReconDesc t;
+            t.cell = c;
             t.src = old_cell(lc, cq);
             const int r = 1 << (l - lc);
             for (int d = 0; d < 3; d++) {
@@ -384,29 +465,53 @@ int nrd_transfer(nrd_ctx* src, nrd_ctx* dst, const double* u_src, double* u_dst,
                 t.nb[2 * d + sd] = old_cell(lc, nq);
               }
             }
+            recs[th].push_back(t);
           }
-          desc[P.off + i + P.n[0] * (j + P.n[1] * k)] = t;
-        }
+    }
+  };
+  if (nth == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int th = 0; th < nth; th++) pool.emplace_back(work, th);
+    for (auto& t : pool) t.join();
   }
+  for (int th = 0; th < nth; th++)
+    if (fail[th]) {
+      dst->err = "transfer: a new cell lies in no old cell";
+      return NRD_EINVAL;
+    }
+  size_t nrec = 0;
+  for (const auto& v : recs) nrec += v.size();
+  std::vector<ReconDesc> rec;
+  rec.reserve(nrec);
+  for (const auto& v : recs) rec.insert(rec.end(), v.begin(), v.end());
   const size_t No = (size_t)A.N, Nn = (size_t)B.N;
-  TransferDesc* d_desc = nullptr;
-  double* d_comp = nullptr;
-  if (cudaMalloc(&d_desc, Nn * sizeof(TransferDesc)) != cudaSuccess ||
-      cudaMalloc(&d_comp, 2 * No * nvec * sizeof(double)) != cudaSuccess) {
-    cudaFree(d_desc);
+  // one device buffer: the old vectors (made composite), the codes and the
+  // reconstruction entries
+  const size_t comp_bytes = 2 * No * nvec * sizeof(double);
+  const size_t code_bytes = (Nn * sizeof(int) + 15) / 16 * 16;
+  const size_t rec_bytes = nrec * sizeof(ReconDesc);
+  char* d_buf = nullptr;
+  if (cudaMalloc(&d_buf, comp_bytes + code_bytes + rec_bytes) != cudaSuccess) {
     dst->err = "allocation failed";
     return NRD_ENOMEM;
   }
-  cudaMemcpyAsync(d_desc, desc.data(), Nn * sizeof(TransferDesc), cudaMemcpyHostToDevice, s);
+  double* d_comp = (double*)d_buf;
+  int* d_code = (int*)(d_buf + comp_bytes);
+  ReconDesc* d_rec = (ReconDesc*)(d_buf + comp_bytes + code_bytes);
+  cudaMemcpyAsync(d_code, code.data(), Nn * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (nrec) cudaMemcpyAsync(d_rec, rec.data(), rec_bytes, cudaMemcpyHostToDevice, s);
   dst->timer.begin(NRD_TK_TRANSFER, s);
-  cudaMemcpyAsync(d_comp, u_src, 2 * No * nvec * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(d_comp, u_src, comp_bytes, cudaMemcpyDeviceToDevice, s);
   launch_average_down(A, d_comp, 2 * nvec, (int)No, s);
-  const int grid = (int)std::max(1L, std::min(152L * 8, ((long)Nn + 255) / 256));
-  k_transfer<<<grid, 256, 0, s>>>(d_desc, (int)Nn, (int)No, nvec, d_comp, u_dst);
+  const long work_items = (long)Nn + (long)nrec;
+  const int grid = (int)std::max(1L, std::min(152L * 8, (work_items + 255) / 256));
+  k_transfer<<<grid, 256, 0, s>>>(d_code, d_rec, (int)Nn, (int)nrec, (int)No, nvec, d_comp,
+                                  u_dst);
   dst->timer.end(NRD_TK_TRANSFER, s);
   const cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(d_desc);
-  cudaFree(d_comp);
+  cudaFree(d_buf);
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     dst->err = "transfer kernel failed";
     return NRD_ECUDA;
