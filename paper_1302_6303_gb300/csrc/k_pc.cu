@@ -2136,8 +2136,9 @@ void scale_all(PcState* ps, const Hier& H, SetupArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-// cuTensorMapEncodeTiled from the driver (through the runtime: no link to
-// libcuda); null when the driver does not offer it
+// cuTensorMapEncodeTiled of the CUDA driver API, found through the runtime's
+// entry-point query (no link to libcuda); null when the installed CUDA driver
+// does not offer it
 using EncodeFn = PFN_cuTensorMapEncodeTiled_v12000;
 EncodeFn tmap_encoder() {
   static EncodeFn fn = nullptr;
