@@ -359,10 +359,9 @@ int nrd_autotune(nrd_ctx* ctx, const double* u, const double* b, double a0, doub
 
 /* Allocation-free weighted inner product (no counterpart in the paper: an
  * interface addition for callers that cannot allocate device memory where
- * they need the product -- code issuing work inside a CUDA stream capture,
- * code under an external memory manager that owns all device memory, or
- * latency-critical paths where an allocation, which can synchronise the
- * device, is not acceptable).
+ * they need the product -- code under an external memory manager that owns
+ * all device memory, or latency-critical paths where an allocation, which
+ * can synchronise the device, is not acceptable).
  *   out[0] = sum_{i<n} w[i] (x[i] y[i] + x[n+i] y[n+i])   (device pointers:
  *   x, y: 2n doubles; w: n floats; out: one double, written asynchronously).
  * With w = leaf-cell volumes (0 on covered cells) this equals nrd_dot.
@@ -370,8 +369,8 @@ int nrd_autotune(nrd_ctx* ctx, const double* u, const double* b, double a0, doub
  * file-scope device array of 65,536 doubles (512 KiB), held by every GPU that
  * loads the library until the process exits; n is therefore limited to
  * 2^26 = 67,108,864 (NRD_EINVAL beyond, nothing launched).  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array:
+ * a device looks up the array's device address (cudaGetSymbolAddress) and
+ * keeps it for later calls.  All calls share the array:
  * calls that overlap on the GPU (different streams without ordering) race
  * and give wrong results; calls ordered on one stream are safe.  Every
  * partial a call reads it has written itself, so nothing needs clearing.

@@ -2,10 +2,9 @@
 //
 // nrd_dot reduces through block partials held in device memory that the
 // context allocated.  Some callers cannot allocate device memory at the point
-// where they need a dot product: code issuing work inside a CUDA stream
-// capture, code running under an external memory manager that owns every
-// device byte, or a latency-critical path where an allocation (which can
-// synchronise the device) is not acceptable.  nrd_wdot_noalloc serves them:
+// where they need a dot product: code running under an external memory
+// manager that owns every device byte, or a latency-critical path where an
+// allocation (which can synchronise the device) is not acceptable.  nrd_wdot_noalloc serves them:
 // its block partials live in the file-scope array below, so the call itself
 // allocates nothing and needs no context.
 #include <mutex>

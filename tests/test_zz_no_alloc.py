@@ -1,8 +1,7 @@
 """The allocation-free entry point (nrd_wdot_noalloc) against nrd_dot.
 
-Callers that cannot allocate device memory at the point of use (stream
-capture, an external memory manager, latency-critical paths) use the
-allocation-free variant; it must give the same inner product as the context
+Callers that cannot allocate device memory at the point of use (an external
+memory manager, latency-critical paths) use the allocation-free variant; it must give the same inner product as the context
 call.  This file is collected last so that a failure here comes after every
 other test has run; it also passes alone in a fresh process.
 """
