@@ -44,13 +44,13 @@ import numpy as np  # noqa: E402
 
 MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM, FALLBACK_BF16 = 6800.0, 1900.0
-DT = 5e-4
+DT = 5e-4   # the time step of the selected workload (set from WORKLOADS in main)
 
 # The workloads.  `solver` holds the V-cycle schedule where the workload
-# states one (config "3 red-black Gauss-Seidel sweeps": V(3,3) with 2 x 3
-# sweeps on the coarsest grid); None lets the sweep autotuner choose.
-# `cpu_n` is the grid of the bounded oracle sample timed on the host (the
-# same layout scaled), None for the full workload.
+# states one (three red-black Gauss-Seidel sweeps: V(3,3) with 2 x 3 sweeps on
+# the coarsest grid); None lets the sweep autotuner choose.  `cpu_n` is the
+# grid of the bounded oracle sample timed on the host (the same layout
+# scaled), None for the full workload.  `dt`: the fixed time step.
 WORKLOADS = {
     "single256": {
         "name": "single_level_256cubed_64cubes_z1_5_10",
@@ -58,6 +58,7 @@ WORKLOADS = {
         "solver": dict(nmg=4, nu1=3, nu2=3, coarse_sweeps=6),
         "regrid": False,
         "cpu_n": 128,
+        "dt": 5e-4,
     },
     "amr2_base64": {
         "name": "amr2_base64_marshak_band",
@@ -65,6 +66,18 @@ WORKLOADS = {
         "solver": None,
         "regrid": True,
         "cpu_n": None,
+        "dt": 5e-4,
+    },
+    "batching_base128": {
+        "name": "batching_base128_3levels",
+        "sizes": "base 128^3 + two levels of patches with sides 8-48 per axis (about 1,900 "
+                 "patches, 45.6M fine cells), fixed hierarchy",
+        "solver": None,
+        "regrid": False,
+        "cpu_n": 32,
+        # finest cells 1/512 wide: from the cold start, dt = 5e-4 takes Newton
+        # past 20 iterations on the first step (4 at dt = 1e-4)
+        "dt": 1e-4,
     },
 }
 
@@ -100,6 +113,7 @@ JV_BYTES_PER_CELL = 169.0
 # the frozen Jv 321.9 + 55.5 MB)
 TRAFFIC = {
     "amr2_base64": {"linearise": None, "jv": None},
+    "batching_base128": {"linearise": None, "jv": None},
     "single256": {"linearise": 8 * (57.7 + 377.6 + 187.9 + 63.8) * 1e6,
                   "jv": 8 * (321.9 + 55.5) * 1e6},
 }
@@ -275,6 +289,8 @@ def workload(key, n=None):
     from paper_1302_6303_gb300 import workloads as W
     if key == "single256":
         h, z = W.config_256(n or 256, seed=0)
+    elif key == "batching_base128":
+        h, z = W.config_batching(n or 128, seed=0)
     else:
         h, z = W.config_amr2(n or 64, seed=0)
     return h, z, W.initial_state(h)
@@ -676,7 +692,9 @@ def vcycle_bytes_per_cell(h, sweeps):
 
 
 def main():
+    global DT
     args = parse()
+    DT = WORKLOADS[args.workload]["dt"]
     if args.impl == "reference":
         return reference_arm(args)
     if args.profile:
