@@ -2111,13 +2111,13 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
   }
   gmg_vcycle<P>(ps, H, 0, s);
   prolong_finer<P>(ps, H, 0, s);
-  // up: level 1 to finest
-  for (int l = 1; l < H.L; l++) {
+  // up: level 1 to finest (without post-smoothing nothing reads the
+  // up-leg residuals: the correction is complete after the coarse solve's
+  // prolongation)
+  for (int l = 1; l < H.L && ps->nu2 > 0; l++) {
     composite_residual<P>(ps, H, l, s);
-    if (ps->nu2 > 0) {
-      level_smooth<P>(ps, H, l, ps->nu2, false, s);
-      prolong_finer<P>(ps, H, l, s);
-    }
+    level_smooth<P>(ps, H, l, ps->nu2, false, s);
+    prolong_finer<P>(ps, H, l, s);
   }
   if (transposed)
     k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y, ps->d_err);
