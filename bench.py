@@ -154,6 +154,9 @@ def parse():
                     help="short run for profilers: N preconditioner applies (cached graph) "
                          "on the workload after one set-up, 8x8x4 tiles, the workload's "
                          "schedule (else V(1,1)/2); prints the mean time per apply")
+    ap.add_argument("--pc-sweeps", default="", metavar="NU1,NU2,COARSE,SMOOTHER",
+                    help="V-cycle schedule of --profile-pc (smoother 0 red-black, 1 Jacobi, "
+                         "2 x-line); default: the workload's, else V(1,1) red-black, 2 coarse")
     return ap.parse_args()
 
 
@@ -181,7 +184,10 @@ def profile_pc_run(args):
     h, z, u0 = workload(args.workload, args.grid or None)
     ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
     ctx.set_params(tile_x=8, tile_y=8, tile_z=4)
-    if WORKLOADS[args.workload]["solver"] is None:
+    if args.pc_sweeps:
+        n1, n2, cs, sm = (int(x) for x in args.pc_sweeps.split(","))
+        ctx.set_params(nu1=n1, nu2=n2, coarse_sweeps=cs, smoother=sm)
+    elif WORKLOADS[args.workload]["solver"] is None:
         ctx.set_params(nu1=1, nu2=1, coarse_sweeps=2)
     u = torch.from_numpy(u0).cuda()
     ctx.precond_setup(u, 1.0, DT)

@@ -175,13 +175,21 @@ def test_tag(nrd, name):
                 assert near.all(), (bit, ind[diff, bit][~near][:5], thr[bit])
 
 
+# red-black schedules (nu1, nu2, coarse sweeps): V(2,2); V(1,0), where the
+# up-leg of the FAC cycle only prolongs (no post-smoothing, no residuals);
+# V(1,1); V(3,3), the 256^3 workload's
+RB_SCHED = [(2, 2, 4), (1, 0, 2), (1, 1, 2), (3, 3, 6)]
+
+
 @pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-4)])
+@pytest.mark.parametrize("sched", RB_SCHED)
 @pytest.mark.parametrize("name", ["single32", "tiny2", "tiny3", "boundary", "amr2_16"])
-def test_precond_apply(nrd, name, prec, tol):
+def test_precond_apply(nrd, name, sched, prec, tol):
     h, z = CASES[name]()
     nmg = 3 if h.n0[0] >= 16 else 2
-    ctx, o = make(nrd, h, z, pc_precision=prec, nmg=nmg, nu1=2, nu2=2, coarse_sweeps=4)
-    o.set_solver(nmg=nmg, nu1=2, nu2=2, coarse_sweeps=4)
+    nu1, nu2, csw = sched
+    ctx, o = make(nrd, h, z, pc_precision=prec, nmg=nmg, nu1=nu1, nu2=nu2, coarse_sweeps=csw)
+    o.set_solver(nmg=nmg, nu1=nu1, nu2=nu2, coarse_sweeps=csw)
     u = _state(h)
     a0, dt = 1.2, 5e-3
     ctx.precond_setup(dev(u), a0, dt)
