@@ -11,9 +11,12 @@ Workloads (``--workload``; the default is the largest single-GPU one):
 * ``amr2_base64``: 2-level AMR, base 64^3, refinement ratio 2, fine patches
   of 16^3-32^3 cells tiling the Marshak band x < 1/8, z = 10 in 20 seeded
   cubes of side 4-12 base cells on z = 1; sweep schedule from the autotuner.
+* ``batching_base128``: 3 levels, base 128^3, 1,913 patches with even sides
+  uniform in 8-48 cells per axis (45.6M cells), z = 10 in 64 seeded cubes;
+  sweep schedule from the autotuner; dt = 1e-4.
 
-Both: BDF2 steps (the first one backward Euler) with dt = 5e-4 from the
-initial state (Sec. 3.1), Newton rtol 1e-8.
+All: BDF2 steps (the first one backward Euler) with a fixed dt (5e-4 unless
+stated) from the initial state (Sec. 3.1), Newton rtol 1e-8.
 
 One benchmark step = one implicit time step through the public API: the
 generalised leapfrog predictor as the Newton initial guess (nrd_predict, Eq.
