@@ -123,6 +123,19 @@ TRAFFIC = {
 # FP64-pipe instructions per cell measured by ncu (sm__inst_executed_pipe_fp64,
 # same capture): linearisation 139.2 + 35.0, frozen Jv 40.4
 LIN_INST_NCU, JV_INST_NCU = 139.2 + 35.0, 40.4
+# Algorithmic DRAM bytes per leaf cell of the linearisation as laid out here:
+# face launch reads E, T, z^3 (24 B) and writes per face slot (3 per cell) the
+# 5 FP64 Jacobian partials, the 2 scaled FP32 P1 coefficients and the 2 FP64
+# face fluxes (3 x 64 = 192 B); the cell launch reads the 6 fluxes of its
+# low faces (48 B), u and b (32 B) and z^3 (8 B) and writes F (16 B), the 2
+# FP64 coupling partials (16 B) and the 3 FP32 P2 values (12 B).  The residual
+# alone moves 52 B per cell and the analytic Jv 52 B (E, T, v, z read, Jv
+# written); the frozen form stores the partials once per Newton iterate so
+# that each Krylov iteration reads them instead of recomputing them in FP64.
+# (ncu's DRAM bytes of a launch can fall below these counts: writes still held
+# in the 129 MB L2 when the launch ends are counted by a later one.)
+LIN_BYTES_PER_CELL = 24 + 192 + 48 + 32 + 8 + 16 + 16 + 12
+RES_BYTES_PER_CELL = 52.0
 
 
 def parse():
@@ -818,6 +831,16 @@ def main():
                                   "frac": ach_inst / fp64_peak,
                                   "source": "ncu sm__inst_executed_pipe_fp64 per cell"},
             "measured_fp64_ops": ops}
+    if traffic.get("linearise"):
+        tpc = traffic["linearise"] / leaf
+        roof["bytes"] = {"dram_per_cell": tpc, "algorithmic_per_cell": LIN_BYTES_PER_CELL,
+                         "ratio": tpc / LIN_BYTES_PER_CELL,
+                         "residual_only_per_cell": RES_BYTES_PER_CELL,
+                         "ratio_to_residual_only": tpc / RES_BYTES_PER_CELL,
+                         "why": "the linearisation also writes the frozen Jacobian partials, "
+                                "P1 coefficients, coupling partials and P2 data that the "
+                                "Krylov iterations and the V-cycle read (FP64 issue, not "
+                                "HBM, bounds these kernels)"}
     jv_ms, jv_n = kt["jv"]
     t_jv = jv_ms / max(jv_n, 1) * 1e-3
     ach_jv = flops(JV_OPS) * leaf / t_jv / 1e9
@@ -834,6 +857,15 @@ def main():
                "hbm": {"achieved": gbs_jv, "peak": hbm_peak, "unit": "GB/s",
                        "frac": gbs_jv / hbm_peak, "peak_source": peak_src,
                        "algorithmic": "%d B per leaf cell" % JV_BYTES_PER_CELL}}
+    if traffic.get("jv"):
+        tpc = traffic["jv"] / leaf
+        roof_jv["bytes"] = {"dram_per_cell": tpc, "algorithmic_per_cell": JV_BYTES_PER_CELL,
+                            "ratio": tpc / JV_BYTES_PER_CELL,
+                            "analytic_jv_per_cell": RES_BYTES_PER_CELL,
+                            "ratio_to_analytic": tpc / RES_BYTES_PER_CELL,
+                            "why": "reads the 5 stored FP64 partials per face instead of "
+                                   "re-deriving them from E, T and z (40 FP64 instructions "
+                                   "per cell instead of about 130)"}
     pc_ms, pc_n = kt["pc_apply"]
     t_pc = pc_ms / max(pc_n, 1) * 1e-3
     vb = vcycle_bytes_per_cell(h, sweeps)
