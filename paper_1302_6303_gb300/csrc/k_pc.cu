@@ -549,20 +549,56 @@ __device__ __forceinline__ P tri_interp(const P* src, int cn0, int cn1, int cn2,
 }
 
 // e(fine box) += trilinear interpolation of the coarse correction
-// out = e + P ec (out may be e itself)
+// out = e + P ec (out may be e itself).  One thread per coarse cell p and its
+// 2x2x2 children: the 27 coarse values around p are loaded once and shared
+// by the children, each of which sums its 8 terms in tri_interp's order and
+// with its weights (parent 3/4, the neighbour on the child's side 1/4 per
+// axis; the parent itself where that neighbour is outside the box), so the
+// result is bit-identical to tri_interp per fine cell.  grid (coarse x / 8,
+// y / 8, 2 fields x z / 4), 256 threads.
+constexpr int PX = 8, PY = 8, PZ = 4;
 template <class P>
-__global__ void __launch_bounds__(FTHREADS) k_bprolong(const P* ec, int cn0, int cn1, int cn2,
-                                                        BoxK<P> F, P* out) {
+__global__ void __launch_bounds__(PX * PY * PZ) k_bprolong(const P* ec, int cn0, int cn1,
+                                                            int cn2, BoxK<P> F, P* out) {
   const int ntz = gridDim.z >> 1;
   const int fld = blockIdx.z >= ntz;
   const int t = threadIdx.x;
-  const int i = blockIdx.x * VT + ft_i(t), j = blockIdx.y * VT + ft_j(t);
-  const int k = (blockIdx.z - fld * ntz) * VT + ft_k(t);
-  if (i >= F.n0 || j >= F.n1 || k >= F.n2) return;
-  const long fo = fld * F.vfs;
+  const int p0 = blockIdx.x * PX + t % PX, p1 = blockIdx.y * PY + (t / PX) % PY;
+  const int p2 = (blockIdx.z - fld * ntz) * PZ + t / (PX * PY);
+  if (p0 >= cn0 || p1 >= cn1 || p2 >= cn2) return;
   const P* src = ec + fld * ((long)cn0 * cn1 * cn2);
-  const int idx = i + F.n0 * (j + F.n1 * k);
-  out[fo + idx] = F.e[fo + idx] + tri_interp(src, cn0, cn1, cn2, i, j, k, (const int*)nullptr);
+  const long fo = fld * F.vfs;
+  // coarse coordinates of the low / centre / high neighbours per axis
+  const int cx[3] = {p0 > 0 ? p0 - 1 : p0, p0, p0 < cn0 - 1 ? p0 + 1 : p0};
+  const int cy[3] = {p1 > 0 ? p1 - 1 : p1, p1, p1 < cn1 - 1 ? p1 + 1 : p1};
+  const int cz[3] = {p2 > 0 ? p2 - 1 : p2, p2, p2 < cn2 - 1 ? p2 + 1 : p2};
+  P c[3][3][3];
+#pragma unroll
+  for (int z = 0; z < 3; z++)
+#pragma unroll
+    for (int y = 0; y < 3; y++)
+#pragma unroll
+      for (int x = 0; x < 3; x++) c[z][y][x] = src[cx[x] + cn0 * (cy[y] + cn1 * cz[z])];
+#pragma unroll
+  for (int sz = 0; sz < 2; sz++)
+#pragma unroll
+    for (int sy = 0; sy < 2; sy++)
+#pragma unroll
+      for (int sx = 0; sx < 2; sx++) {
+        const int i = 2 * p0 + sx, j = 2 * p1 + sy, k = 2 * p2 + sz;
+        if (i >= F.n0 || j >= F.n1 || k >= F.n2) continue;
+        P v = P(0);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          const int a = q & 1, b = (q >> 1) & 1, d = q >> 2;
+          const P w = (a ? P(0.25) : P(0.75)) * (b ? P(0.25) : P(0.75)) * (d ? P(0.25) : P(0.75));
+          // term a of axis x: the parent (centre) or the neighbour on the child's side
+          const int xs = a ? 2 * sx : 1, ys = b ? 2 * sy : 1, zs = d ? 2 * sz : 1;
+          v += w * c[zs][ys][xs];
+        }
+        const long idx = fo + i + F.n0 * (j + (long)F.n1 * k);
+        out[idx] = F.e[idx] + v;
+      }
 }
 
 // ------------------------------------------------- AMR (multi-patch) levels
@@ -2008,7 +2044,8 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   // that the last one writes e
   const bool to_scratch =
       (jac || fused_sweeps<P>(ps, m)) && ps->nu2 > 0 && start_in_scratch(ps->nu2);
-  k_bprolong<P><<<tile_grid(B.n[0], B.n[1], B.n[2]), FTHREADS, 0, s>>>(
+  k_bprolong<P><<<dim3((C.n[0] + PX - 1) / PX, (C.n[1] + PY - 1) / PY,
+                       2 * ((C.n[2] + PZ - 1) / PZ)), PX * PY * PZ, 0, s>>>(
       (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V, to_scratch ? scratch : V.e);
   if (ps->nu2 == 0) {
     if (m == 0) add_level<P>(ps, H, 0, s);
