@@ -998,8 +998,9 @@ __global__ void __launch_bounds__(FTHREADS) k_vprolong(int ntl, VLev<P> V, int t
     k_vprolong_tile<P, PV>(tt, V, t0, cmap, cn0, cn1, cn2, src, pv, u);
 }
 
-// V-cycle input: ff = fr = w (the residual of u = 0), u = 0; TR: w goes
-// through the transposed P2 solve first, P2^T = [[1 + sb, -sb], [-sbt, 1 + sbt]]
+// V-cycle input: fr = w (the residual of u = 0) and, with finer levels (ff
+// non-null), ff = w and u = 0; TR: w goes through the transposed P2 solve
+// first, P2^T = [[1 + sb, -sb], [-sbt, 1 + sbt]]
 template <class P, bool TR>
 __global__ void k_vc_init(int N, const double* w, const P* p, P* ff, P* fr, P* fu, const int* jd,
                           long jstride) {
@@ -1015,12 +1016,14 @@ __global__ void k_vc_init(int N, const double* w, const P* p, P* ff, P* fr, P* f
       xE = (P)w[c];
       xT = (P)w[N + c];
     }
-    ff[c] = xE;
-    ff[N + c] = xT;
+    if (ff) {   // the composite rhs and solution exist only with finer levels
+      ff[c] = xE;
+      ff[N + c] = xT;
+      fu[c] = P(0);
+      fu[N + c] = P(0);
+    }
     fr[c] = xE;
     fr[N + c] = xT;
-    fu[c] = P(0);
-    fu[N + c] = P(0);
   }
 }
 
@@ -2015,7 +2018,9 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
   const long vfs = (m == 0) ? H.N : nc;
   const BoxK<P> V = boxk<P>(B, A, e, f, vfs);
   const uint8_t* mask = (m == 0) ? H.d_mask : nullptr;
-  P* addu = (m == 0) ? (P*)ps->fu : nullptr;
+  // one level: the level-0 correction is the V-cycle's result (read from fe),
+  // no composite solution to add it to
+  P* addu = (m == 0 && H.L > 1) ? (P*)ps->fu : nullptr;
   auto zero_e = [&]() {
     for (int fld = 0; fld < 2; fld++)
       cudaMemsetAsync((char*)e + fld * vfs * (long)sizeof(P), 0, nc * sizeof(P), s);
@@ -2048,7 +2053,7 @@ void gmg_vcycle(PcState* ps, const Hier& H, int m, cudaStream_t s) {
                        2 * ((C.n[2] + PZ - 1) / PZ)), PX * PY * PZ, 0, s>>>(
       (const P*)ps->be[m + 1], C.n[0], C.n[1], C.n[2], V, to_scratch ? scratch : V.e);
   if (ps->nu2 == 0) {
-    if (m == 0) add_level<P>(ps, H, 0, s);
+    if (m == 0 && H.L > 1) add_level<P>(ps, H, 0, s);
   } else if (jac) {
     box_jacobi(V, omega, scratch, ps->nu2, false, to_scratch, mask, addu, s);
   } else {
@@ -2185,11 +2190,16 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
   // r = f (u = 0).  The covered cells' residual is not averaged down here:
   // the finest level has none, and every coarser level's covered cells are
   // re-averaged by the down-leg composite residual that precedes its smoothing
+  // one level: the V-cycle is the GMG cycle on level 0 alone, whose rhs is fr
+  // and whose correction (fe) is the result; the composite rhs ff and solution
+  // fu are neither written nor read
+  const bool one = H.L == 1;
+  P* ffp = one ? nullptr : (P*)ps->ff;
   if (transposed)
-    k_vc_init<P, true><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff, (P*)ps->fr,
+    k_vc_init<P, true><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, ffp, (P*)ps->fr,
                                               (P*)ps->fu, nullptr, 0);
   else
-    k_vc_init<P, false><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, (P*)ps->ff, (P*)ps->fr,
+    k_vc_init<P, false><<<g1(H.N), BS, 0, s>>>(H.N, w, (const P*)ps->p2, ffp, (P*)ps->fr,
                                                (P*)ps->fu, jd, jstride);
   // down: finest to level 1 (no sweeps: a zero correction)
   for (int l = H.L - 1; l >= 1; l--) {
@@ -2209,10 +2219,11 @@ int apply_t(PcState* ps, const Hier& H, const double* w, double* y, bool transpo
     level_smooth<P>(ps, H, l, ps->nu2, false, s);
     prolong_finer<P>(ps, H, l, s);
   }
+  const P* res = (const P*)(one ? ps->fe : ps->fu);
   if (transposed)
-    k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, (const P*)ps->fu, y, ps->d_err);
+    k_out_cast<P><<<g1(H.N), BS, 0, s>>>(H.d_mask, H.N, res, y, ps->d_err);
   else
-    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, (const P*)ps->fu, (const P*)ps->p2, y, jd, jstride, y2,
+    k_p2<P><<<g1(H.N), BS, 0, s>>>(H.N, res, (const P*)ps->p2, y, jd, jstride, y2,
                                    ps->d_err);
   return cudaGetLastError() == cudaSuccess ? NRD_OK : NRD_ECUDA;
 }
