@@ -170,6 +170,10 @@ def parse():
                     help="short run for profilers: N preconditioner applies (cached graph) "
                          "on the workload after one set-up, 8x8x4 tiles, the workload's "
                          "schedule (else V(1,1)/2); prints the mean time per apply")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time the differentiation workload instead: base 96^3 + 8 fine boxes, "
+                         "40 backward-Euler steps with checkpoints every 8, the gradient of "
+                         "the final-time energy in a box with respect to z and E_0")
     ap.add_argument("--pc-sweeps", default="", metavar="NU1,NU2,COARSE,SMOOTHER",
                     help="V-cycle schedule of --profile-pc (smoother 0 red-black, 1 Jacobi, "
                          "2 x-line); default: the workload's, else V(1,1) red-black, 2 coarse")
@@ -220,6 +224,74 @@ def profile_pc_run(args):
     torch.cuda.synchronize()
     print(json.dumps({"profile_pc": True, "applies": args.profile_pc, "cells": h.ncells,
                       "us_per_apply": e0.elapsed_time(e1) * 1e3 / args.profile_pc}))
+    return 0
+
+
+def adjoint_run(args):
+    """The differentiation workload (Sec. 6 geometry): forward = 40 backward-
+    Euler steps through ImplicitSteps (nrd_step, checkpoints every 8 steps),
+    backward = the discrete adjoint through the steps (per step nrd_linearise,
+    nrd_adjoint_solve with P^-T ~ P1^-1 P2^-T, nrd_vjp; each segment's states
+    recomputed from its checkpoint), both timed with CUDA events; forward
+    Newton rtol 1e-10, adjoint rtol 1e-10, analytic Jv, FP32 V-cycle."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_1302_6303_gb300 import nrd, workloads as W
+    from paper_1302_6303_gb300.adjoint import ImplicitSteps, StepRunner, box_weights
+    n0, nsteps, dt, ckpt = 96, 40, 2.5e-4, 8
+    h, z, fbox = W.config_adjoint(n0, seed=0, nbox=8)
+    u0 = W.front_state(h, seed=2, noise=0.0, front=0.5, width=0.05)
+    N = h.ncells
+    nmg = 1
+    while nmg < 4 and all(n % (1 << nmg) == 0 for n in h.n0):
+        nmg += 1
+    ctx = nrd.Context(nmg=nmg, jv_mode=nrd.JV_ANALYTIC, pc_precision=nrd.PC_F32, rtol=1e-10,
+                      atol=0.0, max_newton=30)
+    ctx.set_hierarchy_from(h)
+    ctx.set_material(torch.from_numpy(z).cuda())
+    wts = torch.from_numpy(box_weights(h, fbox)).cuda()
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    res = []
+    for rep in range(1 + max(1, args.steps // 10)):
+        runner = StepRunner(ctx, dev(u0[N:]), nsteps, dt, wts, ckpt_every=ckpt)
+        zt = dev(z.astype(np.float64)).requires_grad_(True)
+        Et = dev(u0[:N]).requires_grad_(True)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record()
+        J = ImplicitSteps.apply(zt, Et, runner)
+        e1.record()
+        nfwd = len(runner.stats)
+        J.backward()
+        e2.record()
+        torch.cuda.synchronize()
+        fst, bst, ast = runner.stats[:nfwd], runner.stats[nfwd:], runner.adjoint_stats
+        res.append({"forward_ms": e0.elapsed_time(e1), "backward_ms": e1.elapsed_time(e2),
+                    "forward_newton": sum(s["newton_its"] for s in fst),
+                    "forward_krylov": sum(s["krylov_its"] for s in fst),
+                    "recomputed_steps": len(bst),
+                    "recompute_krylov": sum(s["krylov_its"] for s in bst),
+                    "adjoint_krylov": sum(s["krylov_its"] for s in ast),
+                    "J": float(J.detach())})
+    r = res[-1]   # the first repetition also builds the graphs
+    leaf = ctx.nleaf
+    print(json.dumps({
+        "adjoint": True, "workload": "differentiation: base 96^3 + 8 fine boxes of 16-32 fine "
+        "cells near x = 0, 40 backward-Euler steps of dt = 2.5e-4, checkpoints every 8, "
+        "J = integral of E over the interior (n0/6)^3 box at the final time",
+        "cells": N, "leaf_cells": leaf, "repetitions": len(res), "timed": "the last one",
+        "forward_ms": r["forward_ms"], "backward_ms": r["backward_ms"],
+        "backward_over_forward": r["backward_ms"] / r["forward_ms"],
+        "forward_ms_per_step": r["forward_ms"] / nsteps,
+        "forward_newton_per_step": r["forward_newton"] / nsteps,
+        "forward_krylov_per_step": r["forward_krylov"] / nsteps,
+        "recomputed_steps": r["recomputed_steps"],
+        "adjoint_krylov_per_step": r["adjoint_krylov"] / nsteps,
+        "forward_mcells": leaf * r["forward_krylov"] / (r["forward_ms"] * 1e-3) / 1e6,
+        "gradient": "dJ/dz on the leaf cells and dJ/dE_0, checked against central differences "
+                    "and the oracle's gradient in tests/test_gpu_adjoint.py",
+        "J": r["J"], "all": res}))
     return 0
 
 
@@ -723,6 +795,8 @@ def main():
         return profile_run(args)
     if args.profile_pc:
         return profile_pc_run(args)
+    if args.adjoint:
+        return adjoint_run(args)
     if args.profile_stencils:
         return profile_stencils_run(args)
     if args.levels_table > 0:

@@ -29,7 +29,8 @@ class StepRunner:
         self.weights = weights          # (N,) float64: V_c on leaf cells of the box, else 0
         self.ckpt_every = ckpt_every
         self.adjoint_rtol = adjoint_rtol
-        self.stats = []
+        self.stats = []           # nrd_step stats of every forward step (recomputations too)
+        self.adjoint_stats = []   # nrd_adjoint_solve stats, one per step of the backward pass
 
     def step(self, un):
         u = un.clone()
@@ -81,7 +82,8 @@ class ImplicitSteps(torch.autograd.Function):
             for n in reversed(range(n0, n1)):
                 un, unp1 = states[n - n0], states[n - n0 + 1]
                 ctx.linearise(unp1, un, 1.0, r.dt)
-                lam, _ = ctx.adjoint_solve(g, 1.0, r.dt, rtol=r.adjoint_rtol)
+                lam, ast = ctx.adjoint_solve(g, 1.0, r.dt, rtol=r.adjoint_rtol)
+                r.adjoint_stats.append(ast)
                 _, dzn = ctx.vjp(lam, 1.0, r.dt)
                 dz -= dzn
                 g = lam
