@@ -133,12 +133,18 @@ def batching_full():
     return h, z
 
 
-def test_batching_full_size_elementwise(nrd, batching_full):
+# stencil tiles: 8x8x4 is the autotuner's pick in the recorded bench runs of
+# both full-size workloads; 8x8x8 is a second instantiation
+FULL_TILES = [(8, 8, 4), (8, 8, 8)]
+
+
+@pytest.mark.parametrize("tile", FULL_TILES)
+def test_batching_full_size_elementwise(nrd, batching_full, tile):
     """Base 128^3, 3 levels, ~2,000 patches (45.6M cells), in the launch
     configuration of the benchmark's stencils: residual and frozen Jv per
     cell against the oracle."""
     h, z = batching_full
-    ctx = nrd.Context(pc_precision=1, nmg=4, tile_x=8, tile_y=8, tile_z=8)
+    ctx = nrd.Context(pc_precision=1, nmg=4, tile_x=tile[0], tile_y=tile[1], tile_z=tile[2])
     ctx.set_hierarchy_from(h)
     ctx.set_material(dev(z))
     o = Oracle(h, z)
@@ -176,10 +182,13 @@ def test_batching_full_size_conservation(nrd, batching_full):
 
 def test_batching_full_size_newton_step(nrd, batching_full):
     """One graph-captured Newton step (analytic Jv, FP32 V-cycle, FGMRES) on
-    the full 3-level hierarchy; the oracle's residual accepts the result."""
+    the full 3-level hierarchy with the benchmark's settings (8x8x4 tiles,
+    point-Jacobi V(1,0) with 2 coarse sweeps); the oracle's residual accepts
+    the result."""
     h, z = batching_full
     ctx = nrd.Context(pc_precision=1, nmg=4, jv_mode=nrd.JV_ANALYTIC, rtol=1e-8,
-                      tile_x=8, tile_y=8, tile_z=8)
+                      tile_x=8, tile_y=8, tile_z=4, nu1=1, nu2=0, coarse_sweeps=2,
+                      smoother=nrd.SMOOTH_JACOBI)
     ctx.set_hierarchy_from(h)
     ctx.set_material(dev(z))
     o = Oracle(h, z)
@@ -188,9 +197,10 @@ def test_batching_full_size_newton_step(nrd, batching_full):
 
 
 # ------------------------------------------------------------- 256^3 single
-def test_256_full_size_elementwise(nrd):
+@pytest.mark.parametrize("tile", FULL_TILES)
+def test_256_full_size_elementwise(nrd, tile):
     h, z = W.config_256(256, seed=0)
-    ctx = nrd.Context(tile_x=8, tile_y=8, tile_z=8)
+    ctx = nrd.Context(tile_x=tile[0], tile_y=tile[1], tile_z=tile[2])
     ctx.set_hierarchy_from(h)
     ctx.set_material(dev(z))
     o = Oracle(h, z)
@@ -199,11 +209,12 @@ def test_256_full_size_elementwise(nrd):
 
 
 def test_256_full_size_newton_step(nrd):
-    """The benchmark's solver on the full 256^3 grid: the oracle's residual
-    accepts the GPU's converged step."""
+    """The benchmark's solver on the full 256^3 grid (8x8x4 tiles, FP32
+    V(3,3) with 6 coarse sweeps): the oracle's residual accepts the GPU's
+    converged step."""
     h, z = W.config_256(256, seed=0)
     ctx = nrd.Context(pc_precision=1, nmg=4, nu1=3, nu2=3, coarse_sweeps=6,
-                      jv_mode=nrd.JV_ANALYTIC, rtol=1e-8)
+                      jv_mode=nrd.JV_ANALYTIC, rtol=1e-8, tile_x=8, tile_y=8, tile_z=4)
     ctx.set_hierarchy_from(h)
     ctx.set_material(dev(z))
     o = Oracle(h, z)
