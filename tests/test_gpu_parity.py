@@ -239,20 +239,27 @@ def test_bdf2_step_matches_oracle(nrd):
 
 
 def test_full_size_residual_and_jv(nrd):
-    """The benchmark workload (64^3 base + a fine Marshak band, about 377k leaf
-    cells) in the benchmark's launch configuration: every cell checked."""
+    """The 2-level benchmark workload (64^3 base + fine patches over the
+    Marshak band, 491,520 leaf cells) in the benchmark's launch configuration
+    (8x8x4 stencil tiles; the linearisation's face and cell launches and the
+    frozen Jv the Krylov loop uses), and the residual-only and tangent
+    forms: every cell checked."""
     h, z = W.config_amr2(64, seed=0)
-    ctx, o = make(nrd, h, z)
+    ctx, o = make(nrd, h, z, tile_x=8, tile_y=8, tile_z=4)
     u = W.front_state(h, seed=3, noise=0.05)
     v = W.random_direction(h, 4)
     a0, dt = 1.0, 5e-4
-    F = ctx.residual(dev(u), dev(u), a0, dt).cpu().numpy()
     Fo = o.residual(u, u.copy(), a0, dt)
     S = o.residual_scale(u, u.copy(), a0, dt)
-    assert np.all(np.abs(F - Fo) <= 1e-12 * S + 1e-300)
-    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_ANALYTIC).cpu().numpy()
     Jo = o.jv_analytic(u, v, a0, dt)
     Sj = o.jv_scale(u, v, a0, dt)
+    F = ctx.residual(dev(u), dev(u), a0, dt).cpu().numpy()
+    assert np.all(np.abs(F - Fo) <= 1e-12 * S + 1e-300)
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_ANALYTIC).cpu().numpy()
+    assert np.all(np.abs(J - Jo) <= 1e-12 * Sj + 1e-300)
+    F = ctx.linearise(dev(u), dev(u), a0, dt).cpu().numpy()
+    assert np.all(np.abs(F - Fo) <= 1e-12 * S + 1e-300)
+    J = ctx.jv(dev(u), dev(v), a0, dt, mode=nrd.JV_FROZEN).cpu().numpy()
     assert np.all(np.abs(J - Jo) <= 1e-12 * Sj + 1e-300)
 
 
