@@ -969,7 +969,9 @@ def main():
         del ctxp
 
     barrier()
-    e_ms, e_kry, h2d, d2h = run_e2e(nrd, ctx, torch, u0, args.steps, 1)
+    # the same warm-up and timed steps as the device-resident line, so that
+    # the two time the same Newton and Krylov mix
+    e_ms, e_kry, h2d, d2h = run_e2e(nrd, ctx, torch, u0, args.steps, args.warmup)
     e_val, _ = replicas_value(dist, world, leaf * e_kry, e_ms, "cuda")
     e2e = {"value": e_val, "unit": "Mcell/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
