@@ -360,6 +360,8 @@ def levels_table(args):
             "gmres_per_step": sum(r["krylov"] for r in hist) / ns,
             "regrids": len(run.events), "max_leaf_cells": max(r["nleaf"] for r in hist),
             "levels_reached": max(r["nlevels"] for r in hist), "wall_s": wall,
+            "regrid_s": sum(e.regrid_s for e in run.events),
+            "resolve_s": sum(e.resolve_s for e in run.events),
             "paper_16b%dl" % L: {"newton_per_step": paper[L][0], "gmres_per_step": paper[L][1],
                                  "t_end": 1.0}}), flush=True)
     return 0

@@ -14,6 +14,7 @@ Host bookkeeping only; every vector operation runs in libnrd.so.
 """
 from __future__ import annotations
 
+import time
 from dataclasses import dataclass
 
 import numpy as np
@@ -49,6 +50,8 @@ class RegridEvent:
     fnorm_after: float
     newton: int
     krylov: int
+    regrid_s: float = 0.0             # tags, clustering, new context, transfer (wall)
+    resolve_s: float = 0.0            # the re-solve, including the new context's graph build
 
 
 class DynamicAmr:
@@ -167,7 +170,9 @@ class DynamicAmr:
             if self.policy.regrid_every > 0 and n % self.policy.regrid_every == 0:
                 h_un, h_unm1, h_dt, h_dtp, h_f0 = last
                 old_ncells = self.ctx.N
+                t_rg = time.perf_counter()
                 moved = self._regrid([un, h_un, h_unm1])
+                t_rg = time.perf_counter() - t_rg
                 if moved is not None:
                     un_new, h_un_new, h_unm1_new = moved
                     ctx = self.ctx
@@ -179,12 +184,14 @@ class DynamicAmr:
                     # transferred state is already converged and a purely
                     # relative test would ask for rounding noise.
                     u = un_new.clone()
+                    t_rs = time.perf_counter()
                     atol0 = ctx.params.atol
                     ctx.set_params(atol=max(atol0, ctx.params.rtol * h_f0))
                     try:
                         st = ctx.step(u, h_un_new, h_unm1_new, h_dt, h_dtp, check=False)
                     finally:
                         ctx.set_params(atol=atol0)
+                    t_rs = time.perf_counter() - t_rs
                     if st["status"] != nrd.OK:
                         raise RuntimeError("re-solve after regrid did not converge")
                     un, unm1 = u, h_un_new
@@ -194,5 +201,5 @@ class DynamicAmr:
                         step=n, t=t, ncells_old=old_ncells, ncells_new=ctx.N,
                         nboxes=[len(l) for l in self.hier.levels], fnorm_before=st["fnorm0"],
                         fnorm_after=st["fnorm"], newton=st["newton_its"],
-                        krylov=st["krylov_its"]))
+                        krylov=st["krylov_its"], regrid_s=t_rg, resolve_s=t_rs))
         return un

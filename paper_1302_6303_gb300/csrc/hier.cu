@@ -6,10 +6,32 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <thread>
 
 #include "nrd_internal.h"
 
 namespace {
+
+// The per-cell and per-patch loops below are independent across cells
+// (patches): they run over contiguous chunks on host threads, each chunk
+// with its own output lists, joined in chunk order, so every list is the
+// one a serial loop builds.
+int host_chunks(long n, long min_per_chunk) {
+  const long hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  return (int)std::max(1L, std::min(hw, n / std::max(1L, min_per_chunk)));
+}
+// fn(lo, hi, k) for chunk k = [n k / nch, n (k + 1) / nch)
+template <class F>
+void host_parallel(long n, int nch, const F& fn) {
+  if (nch <= 1) {
+    fn(0L, n, 0);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(nch);
+  for (int k = 0; k < nch; k++) th.emplace_back([&fn, n, nch, k] { fn(n * k / nch, n * (k + 1) / nch, k); });
+  for (auto& t : th) t.join();
+}
 
 struct Builder {
   Hier& H;
@@ -236,90 +258,123 @@ int hier_upload(Hier& H, std::string& err) {
   std::vector<uint8_t> mask(N, 0);
   std::vector<float> wvol(N, 0.0f);
   std::vector<int> cellijk(3 * (size_t)N);
+  const int nchc = host_chunks(N, 32768);
+  std::vector<int> leaf_k(nchc, 0);
+  host_parallel(N, nchc, [&](long lo, long hi, int k) {
+    int nl = 0;
+    for (long idx = lo; idx < hi; idx++) {
+      int c[3];
+      B.ijk_of((int)idx, c);
+      cellijk[3 * idx] = c[0];
+      cellijk[3 * idx + 1] = c[1];
+      cellijk[3 * idx + 2] = c[2];
+      int l = H.patches[H.cell_patch[idx]].level;
+      if (B.covered(l, c)) {
+        mask[idx] = MASK_COVERED;
+        continue;
+      }
+      nl++;
+      const double* h = H.lev[l].h;
+      wvol[idx] = (float)(h[0] * h[1] * h[2]);
+      for (int f = 0; f < 6; f++) {
+        int d = f / 2, s = (f % 2) ? 1 : -1;
+        int g[3] = {c[0], c[1], c[2]};
+        g[d] += s;
+        if (B.inside(l, g) && B.cell(l, g) >= 0 && B.covered(l, g))
+          mask[idx] |= (uint8_t)(2 << f);
+      }
+    }
+    leaf_k[k] = nl;
+  });
   int nleaf = 0;
-  for (int idx = 0; idx < N; idx++) {
-    int c[3];
-    B.ijk_of(idx, c);
-    cellijk[3 * idx] = c[0];
-    cellijk[3 * idx + 1] = c[1];
-    cellijk[3 * idx + 2] = c[2];
-  }
-  for (int idx = 0; idx < N; idx++) {
-    const int* c = &cellijk[3 * idx];
-    int l = H.patches[H.cell_patch[idx]].level;
-    if (B.covered(l, c)) {
-      mask[idx] = MASK_COVERED;
-      continue;
-    }
-    nleaf++;
-    const double* h = H.lev[l].h;
-    wvol[idx] = (float)(h[0] * h[1] * h[2]);
-    for (int f = 0; f < 6; f++) {
-      int d = f / 2, s = (f % 2) ? 1 : -1;
-      int g[3] = {c[0], c[1], c[2]};
-      g[d] += s;
-      if (B.inside(l, g) && B.cell(l, g) >= 0 && B.covered(l, g)) mask[idx] |= (uint8_t)(2 << f);
-    }
-  }
+  for (int v : leaf_k) nleaf += v;
   H.nleaf = nleaf;
   // ghosts
   std::vector<uint8_t> gtype(G), gface(G);
   std::vector<int> gcell(G), gzsrc(G), gt0(G + 1);
   std::vector<int> gidx;
   std::vector<double> gw;
-  for (int p = 0; p < (int)H.patches.size(); p++) {
-    const PatchDev& P = H.patches[p];
-    int l = P.level;
-    for (int f = 0; f < 6; f++) {
-      int d = f / 2, s = (f % 2) ? 1 : -1, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-      for (int b = 0; b < P.n[t2]; b++)
-        for (int a = 0; a < P.n[t1]; a++) {
-          int c[3];
-          c[d] = (s < 0) ? P.lo[d] : P.lo[d] + P.n[d] - 1;
-          c[t1] = P.lo[t1] + a;
-          c[t2] = P.lo[t2] + b;
-          int gi = P.goff + P.fo[f] + a + P.n[t1] * b;
-          int ic = B.cell(l, c);
-          int g[3] = {c[0], c[1], c[2]};
-          g[d] += s;
-          gface[gi] = (uint8_t)(f | (l << 3));
-          gcell[gi] = ic;
-          gt0[gi] = (int)gidx.size();
-          if (!B.inside(l, g)) {
-            gtype[gi] = (H.bc_type[f] == NRD_BC_ROBIN) ? GT_ROBIN : GT_NEUMANN;
-            gzsrc[gi] = ic;
-            continue;
-          }
-          int ig = B.cell(l, g);
-          if (ig >= 0) {
-            gtype[gi] = GT_SIBLING;
-            gzsrc[gi] = ig;
-            gidx.push_back(ig);
-            gw.push_back(1.0);
-            continue;
-          }
-          // coarse-fine: g = (x_c + 2 i)/3, i = (9 c00 + 3 c10 + 3 c01 + c11)/16
-          gtype[gi] = GT_CF;
-          int Pc[3] = {g[0] / 2, g[1] / 2, g[2] / 2};
-          const LevelInfo& C = H.lev[l - 1];
-          int o1 = (g[t1] % 2 == 0) ? -1 : 1, o2 = (g[t2] % 2 == 0) ? -1 : 1;
-          if (Pc[t1] + o1 < 0 || Pc[t1] + o1 >= C.n[t1]) o1 = 0;
-          if (Pc[t2] + o2 < 0 || Pc[t2] + o2 >= C.n[t2]) o2 = 0;
-          gzsrc[gi] = B.cell(l - 1, Pc);
-          gidx.push_back(ic);
-          gw.push_back(1.0 / 3.0);
-          const double wq[4] = {9.0, 3.0, 3.0, 1.0};
-          for (int q = 0; q < 4; q++) {
-            int cc[3] = {Pc[0], Pc[1], Pc[2]};
-            if (q == 1 || q == 3) cc[t1] += o1;
-            if (q == 2 || q == 3) cc[t2] += o2;
-            if (B.cell(l - 1, cc) < 0) {
-              err = "coarse-fine interpolation source missing (nesting)";
-              return NRD_EINVAL;
+  {
+    const int np = (int)H.patches.size();
+    const int nch = host_chunks(np, 8);
+    std::vector<std::vector<int>> gxk(nch);
+    std::vector<std::vector<double>> wxk(nch);
+    std::vector<int> bad(nch, 0);
+    host_parallel(np, nch, [&](long plo, long phi, int k) {
+      std::vector<int>& gx = gxk[k];
+      std::vector<double>& wx = wxk[k];
+      for (int p = (int)plo; p < (int)phi; p++) {
+        const PatchDev& P = H.patches[p];
+        int l = P.level;
+        for (int f = 0; f < 6; f++) {
+          int d = f / 2, s = (f % 2) ? 1 : -1, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          for (int b = 0; b < P.n[t2]; b++)
+            for (int a = 0; a < P.n[t1]; a++) {
+              int c[3];
+              c[d] = (s < 0) ? P.lo[d] : P.lo[d] + P.n[d] - 1;
+              c[t1] = P.lo[t1] + a;
+              c[t2] = P.lo[t2] + b;
+              int gi = P.goff + P.fo[f] + a + P.n[t1] * b;
+              int ic = B.cell(l, c);
+              int g[3] = {c[0], c[1], c[2]};
+              g[d] += s;
+              gface[gi] = (uint8_t)(f | (l << 3));
+              gcell[gi] = ic;
+              gt0[gi] = (int)gx.size();
+              if (!B.inside(l, g)) {
+                gtype[gi] = (H.bc_type[f] == NRD_BC_ROBIN) ? GT_ROBIN : GT_NEUMANN;
+                gzsrc[gi] = ic;
+                continue;
+              }
+              int ig = B.cell(l, g);
+              if (ig >= 0) {
+                gtype[gi] = GT_SIBLING;
+                gzsrc[gi] = ig;
+                gx.push_back(ig);
+                wx.push_back(1.0);
+                continue;
+              }
+              // coarse-fine: g = (x_c + 2 i)/3, i = (9 c00 + 3 c10 + 3 c01 + c11)/16
+              gtype[gi] = GT_CF;
+              int Pc[3] = {g[0] / 2, g[1] / 2, g[2] / 2};
+              const LevelInfo& C = H.lev[l - 1];
+              int o1 = (g[t1] % 2 == 0) ? -1 : 1, o2 = (g[t2] % 2 == 0) ? -1 : 1;
+              if (Pc[t1] + o1 < 0 || Pc[t1] + o1 >= C.n[t1]) o1 = 0;
+              if (Pc[t2] + o2 < 0 || Pc[t2] + o2 >= C.n[t2]) o2 = 0;
+              gzsrc[gi] = B.cell(l - 1, Pc);
+              gx.push_back(ic);
+              wx.push_back(1.0 / 3.0);
+              const double wq[4] = {9.0, 3.0, 3.0, 1.0};
+              for (int q = 0; q < 4; q++) {
+                int cc[3] = {Pc[0], Pc[1], Pc[2]};
+                if (q == 1 || q == 3) cc[t1] += o1;
+                if (q == 2 || q == 3) cc[t2] += o2;
+                if (B.cell(l - 1, cc) < 0) {
+                  bad[k] = 1;
+                  return;
+                }
+                B.expand(l - 1, cc, (2.0 / 3.0) * wq[q] / 16.0, gx, wx);
+              }
             }
-            B.expand(l - 1, cc, (2.0 / 3.0) * wq[q] / 16.0, gidx, gw);
-          }
         }
+      }
+    });
+    for (int k = 0; k < nch; k++)
+      if (bad[k]) {
+        err = "coarse-fine interpolation source missing (nesting)";
+        return NRD_EINVAL;
+      }
+    // chunk k's term offsets start at the terms of the chunks before it
+    for (int k = 0; k < nch; k++) {
+      const int base = (int)gidx.size();
+      const int plo = (int)((long)np * k / nch), phi = (int)((long)np * (k + 1) / nch);
+      if (plo < phi) {
+        const int g0 = H.patches[plo].goff;
+        const int g1 = (phi < np) ? H.patches[phi].goff : G;
+        for (int g = g0; g < g1; g++) gt0[g] += base;
+      }
+      gidx.insert(gidx.end(), gxk[k].begin(), gxk[k].end());
+      gw.insert(gw.end(), wxk[k].begin(), wxk[k].end());
     }
   }
   gt0[G] = (int)gidx.size();
@@ -400,48 +455,58 @@ int hier_upload(Hier& H, std::string& err) {
   std::vector<std::vector<int4>> cz_src(L);
   for (int l = 0; l + 1 < L; l++) {
     const LevelInfo& Lv = H.lev[l];
-    for (int idx = Lv.off; idx < Lv.off + Lv.ncell; idx++) {
-      const int* c = &cellijk[3 * idx];
-      for (int f = 0; f < 6; f++) {
-        int d = f / 2, s = (f % 2) ? 1 : -1, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
-        int g[3] = {c[0], c[1], c[2]};
-        g[d] += s;
+    const int nch = host_chunks(Lv.ncell, 4096);
+    std::vector<std::vector<int>> tk(nch);
+    std::vector<std::vector<int4>> sk(nch);
+    host_parallel(Lv.ncell, nch, [&](long lo, long hi, int k) {
+      for (long q = lo; q < hi; q++) {
+        const int idx = Lv.off + (int)q;
+        const int* c = &cellijk[3 * idx];
         const PatchDev& P = H.patches[H.cell_patch[idx]];
-        bool patch_bnd = (s < 0) ? (c[d] == P.lo[d]) : (c[d] == P.lo[d] + P.n[d] - 1);
-        if (!patch_bnd && s > 0) continue;  // interior faces listed once (as low faces)
-        bool cov_c = B.covered(l, c);
-        bool in = B.inside(l, g);
-        bool cov_g = in && B.cell(l, g) >= 0 && B.covered(l, g);
-        if (!cov_c && !cov_g) continue;
-        int tgt;
-        if (patch_bnd)
-          tgt = 3 * N + B.ghost_index(H.cell_patch[idx], f, c);
-        else
-          tgt = d * N + idx;
-        int src[4];
-        int n = 0;
-        for (int bb = 0; bb < 2; bb++)
-          for (int aa = 0; aa < 2; aa++) {
-            int qa[3], qb[3];
-            // fine cells on both sides of the coincident fine face
-            int plane = (s > 0) ? 2 * g[d] : 2 * c[d];   // fine index of the high-side cell
-            qb[d] = plane;
-            qa[d] = plane - 1;
-            qa[t1] = qb[t1] = 2 * c[t1] + aa;
-            qa[t2] = qb[t2] = 2 * c[t2] + bb;
-            if (!in) {
-              // physical face: Robin D_b lives in the boundary slot of the
-              // fine boundary cell
-              int* qc = (s > 0) ? qa : qb;
-              int iq = B.cell(l + 1, qc);
-              src[n++] = 3 * N + B.ghost_index(H.cell_patch[iq], f, qc);
-            } else {
-              src[n++] = B.face_addr(l + 1, d, qa, qb);
+        const bool cov_c = B.covered(l, c);
+        for (int f = 0; f < 6; f++) {
+          int d = f / 2, s = (f % 2) ? 1 : -1, t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+          int g[3] = {c[0], c[1], c[2]};
+          g[d] += s;
+          bool patch_bnd = (s < 0) ? (c[d] == P.lo[d]) : (c[d] == P.lo[d] + P.n[d] - 1);
+          if (!patch_bnd && s > 0) continue;  // interior faces listed once (as low faces)
+          bool in = B.inside(l, g);
+          bool cov_g = in && B.cell(l, g) >= 0 && B.covered(l, g);
+          if (!cov_c && !cov_g) continue;
+          int tgt;
+          if (patch_bnd)
+            tgt = 3 * N + B.ghost_index(H.cell_patch[idx], f, c);
+          else
+            tgt = d * N + idx;
+          int src[4];
+          int n = 0;
+          for (int bb = 0; bb < 2; bb++)
+            for (int aa = 0; aa < 2; aa++) {
+              int qa[3], qb[3];
+              // fine cells on both sides of the coincident fine face
+              int plane = (s > 0) ? 2 * g[d] : 2 * c[d];   // fine index of the high-side cell
+              qb[d] = plane;
+              qa[d] = plane - 1;
+              qa[t1] = qb[t1] = 2 * c[t1] + aa;
+              qa[t2] = qb[t2] = 2 * c[t2] + bb;
+              if (!in) {
+                // physical face: Robin D_b lives in the boundary slot of the
+                // fine boundary cell
+                int* qc = (s > 0) ? qa : qb;
+                int iq = B.cell(l + 1, qc);
+                src[n++] = 3 * N + B.ghost_index(H.cell_patch[iq], f, qc);
+              } else {
+                src[n++] = B.face_addr(l + 1, d, qa, qb);
+              }
             }
-          }
-        cz_tgt[l].push_back(tgt);
-        cz_src[l].push_back(make_int4(src[0], src[1], src[2], src[3]));
+          tk[k].push_back(tgt);
+          sk[k].push_back(make_int4(src[0], src[1], src[2], src[3]));
+        }
       }
+    });
+    for (int k = 0; k < nch; k++) {
+      cz_tgt[l].insert(cz_tgt[l].end(), tk[k].begin(), tk[k].end());
+      cz_src[l].insert(cz_src[l].end(), sk[k].begin(), sk[k].end());
     }
   }
   // covered lists for average-down
