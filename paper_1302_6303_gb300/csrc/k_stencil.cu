@@ -581,10 +581,16 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     // where the tile ends the patch, enumerated without gaps so that whole
     // warps skip what is not there)
     const int tzl = tile.k1 - tile.k0;
-    const int nlow = FACES ? TX * TY * tzl : 0;
-    const int nbx = (FACES && tile.i0 + TX == nx) ? TY * tzl : 0;
-    const int nby = (FACES && tile.j0 + TY == ny) ? TX * tzl : 0;
-    const int nbz = (FACES && tile.k1 == nz) ? TX * TY : 0;
+    // the tile's extent inside its patch (a tile at a patch's high end may be
+    // narrower than TX x TY): only its cells' faces are enumerated, so that
+    // no lane of a warp idles on a face outside the patch (an idle lane
+    // still costs its warp's FP64 issue slots)
+    const int ex = min(TX, nx - tile.i0), ey = min(TY, ny - tile.j0);
+    const bool full = (ex == TX && ey == TY);
+    const int nlow = FACES ? ex * ey * tzl : 0;
+    const int nbx = (FACES && tile.i0 + ex == nx) ? ey * tzl : 0;
+    const int nby = (FACES && tile.j0 + ey == ny) ? ex * tzl : 0;
+    const int nbz = (FACES && tile.k1 == nz) ? ex * ey : 0;
     const int nfaces = FACES ? 3 * nlow + nbx + nby + nbz : NFX + NFY + NFZ;
     for (int f = threadIdx.x; f < nfaces; f += blockDim.x) {
       int dir, fi, fj, fk, slot = 0;
@@ -595,14 +601,18 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         if (q < 3 * nlow) {
           dir = q / nlow;
           q -= dir * nlow;
-          fi = q % TX; fj = (q / TX) % TY; fk = q / (TX * TY);
+          if (full) {
+            fi = q % TX; fj = (q / TX) % TY; fk = q / (TX * TY);
+          } else {
+            fi = q % ex; fj = (q / ex) % ey; fk = q / (ex * ey);
+          }
         } else if ((q -= 3 * nlow) < nbx) {
-          dir = 0; fi = TX; fj = q % TY; fk = q / TY;
+          dir = 0; fi = ex; fj = q % ey; fk = q / ey;
         } else if ((q -= nbx) < nby) {
-          dir = 1; fj = TY; fi = q % TX; fk = q / TX;
+          dir = 1; fj = ey; fi = q % ex; fk = q / ex;
         } else {
           q -= nby;
-          dir = 2; fk = tzl; fi = q % TX; fj = q / TX;
+          dir = 2; fk = tzl; fi = q % ex; fj = q / ex;
         }
       } else if (f < NFX) {
         dir = 0; slot = f;
