@@ -325,7 +325,8 @@ int nrd_tag(nrd_ctx* ctx, const double* u, double thr_c, double thr_g, double th
  *   *nlevels_out levels, nboxes_out[max_levels] boxes per level (0 past the
  *   last), boxes_out[6*max_boxes] inclusive lo/hi per box in layout order
  *   (level 0 is the base box), *total_out the total box count (also set when
- *   it exceeds max_boxes, which returns NRD_EINVAL).  Synchronises. */
+ *   it exceeds max_boxes, which returns NRD_EINVAL, as does a level whose
+ *   index space has 2^31 cells or more).  Synchronises. */
 int nrd_regrid_boxes(nrd_ctx* ctx, const uint8_t* tags, int tag_bits, int buffer,
                      double efficiency, int min_side, int max_side, int max_levels,
                      int max_boxes, int* nlevels_out, int* nboxes_out, int* boxes_out,
@@ -341,11 +342,13 @@ int nrd_regrid_boxes(nrd_ctx* ctx, const uint8_t* tags, int tag_bits, int buffer
  * leaf sums of V u are conserved and no value leaves the range of the old
  * neighbours (E, T stay positive).
  *   u_src: device, nvec x 2*ncells(src) doubles;  u_dst: device,
- *   nvec x 2*ncells(dst) doubles (every cell written).  Allocates and frees a
- *   descriptor of 40 bytes per new cell and a copy of u_src.  Synchronises.
+ *   nvec x 2*ncells(dst) doubles (every cell written).  Allocates and frees
+ *   one device buffer: a copy of u_src, 4 bytes per new cell (the old cell it
+ *   copies, or -1) and 44 bytes per reconstructed cell (the source list is
+ *   built on host threads).  Synchronises.
  * Errors: NRD_ESTATE (a context without hierarchy), NRD_EINVAL (different
- * base grids, null pointers, nvec < 1), NRD_ENOMEM, NRD_ECUDA; the message is
- * stored in ctx_dst. */
+ * base grids, null pointers, nvec < 1, a new cell in no old cell),
+ * NRD_ENOMEM, NRD_ECUDA; the message is stored in ctx_dst. */
 int nrd_transfer(nrd_ctx* ctx_src, nrd_ctx* ctx_dst, const double* u_src, double* u_dst,
                  int nvec, cudaStream_t stream);
 
