@@ -905,7 +905,11 @@ def main():
             "fp64_instructions": {"per_cell": LIN_INST_NCU, "achieved": ach_inst,
                                   "peak": fp64_peak, "unit": "Ginst/s (FP64 pipe)",
                                   "frac": ach_inst / fp64_peak,
-                                  "source": "ncu sm__inst_executed_pipe_fp64 per cell"},
+                                  "source": "ncu sm__inst_executed_pipe_fp64 per cell" + (
+                                      "" if key == "single256" else
+                                      ", captured on the single-level layout at 128^3 and "
+                                      "applied to this workload (not captured here: patch "
+                                      "boundaries add faces)")},
             "measured_fp64_ops": ops}
     if traffic.get("linearise"):
         tpc = traffic["linearise"] / leaf
