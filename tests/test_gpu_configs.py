@@ -133,8 +133,8 @@ def batching_full():
     return h, z
 
 
-# stencil tiles: 8x8x4 is the autotuner's pick in the recorded bench runs of
-# both full-size workloads; 8x8x8 is a second instantiation
+# stencil tiles: the autotuner's picks in the recorded bench runs, 8x8x8 on the
+# 256^3 workload and 8x8x4 on the 3-level one (both checked on both)
 FULL_TILES = [(8, 8, 4), (8, 8, 8)]
 
 
@@ -209,12 +209,12 @@ def test_256_full_size_elementwise(nrd, tile):
 
 
 def test_256_full_size_newton_step(nrd):
-    """The benchmark's solver on the full 256^3 grid (8x8x4 tiles, FP32
+    """The benchmark's solver on the full 256^3 grid (8x8x8 tiles, FP32
     V(3,3) with 6 coarse sweeps): the oracle's residual accepts the GPU's
     converged step."""
     h, z = W.config_256(256, seed=0)
     ctx = nrd.Context(pc_precision=1, nmg=4, nu1=3, nu2=3, coarse_sweeps=6,
-                      jv_mode=nrd.JV_ANALYTIC, rtol=1e-8, tile_x=8, tile_y=8, tile_z=4)
+                      jv_mode=nrd.JV_ANALYTIC, rtol=1e-8, tile_x=8, tile_y=8, tile_z=8)
     ctx.set_hierarchy_from(h)
     ctx.set_material(dev(z))
     o = Oracle(h, z)
