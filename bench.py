@@ -53,7 +53,9 @@ DT = 5e-4   # the time step of the selected workload (set from WORKLOADS in main
 # states one (three red-black Gauss-Seidel sweeps: V(3,3) with 2 x 3 sweeps on
 # the coarsest grid); None lets the sweep autotuner choose.  `cpu_n` is the
 # grid of the bounded oracle sample timed on the host (the same layout
-# scaled), None for the full workload.  `dt`: the fixed time step.
+# scaled), None for the full workload.  `dt`: the fixed time step.  `tile`: the
+# stencil tile the autotuner picks for the workload in the recorded runs (used
+# by the profiling modes, which skip the autotuner).
 WORKLOADS = {
     "single256": {
         "name": "single_level_256cubed_64cubes_z1_5_10",
@@ -62,6 +64,7 @@ WORKLOADS = {
         "regrid": False,
         "cpu_n": 128,
         "dt": 5e-4,
+        "tile": (8, 8, 8),
     },
     "amr2_base64": {
         "name": "amr2_base64_marshak_band",
@@ -70,6 +73,7 @@ WORKLOADS = {
         "regrid": True,
         "cpu_n": None,
         "dt": 5e-4,
+        "tile": (8, 8, 4),
     },
     "batching_base128": {
         "name": "batching_base128_3levels",
@@ -81,6 +85,7 @@ WORKLOADS = {
         # finest cells 1/512 wide: from the cold start, dt = 5e-4 takes Newton
         # past 20 iterations on the first step (4 at dt = 1e-4)
         "dt": 1e-4,
+        "tile": (8, 8, 4),
     },
 }
 
@@ -112,13 +117,13 @@ JV_BYTES_PER_CELL = 169.0
 # per workload (None: not captured for this kernel version and workload)
 # (single256: captured on the same layout at 128^3, 2,097,152 cells, and
 # scaled by the cells, x8: these stencils stream their inputs once; the
-# linearisation's face and cell launches 57.7 + 377.6 + 187.9 + 63.8 MB,
-# the frozen Jv 321.9 + 55.5 MB)
+# linearisation's face and cell launches 58.1 + 394.5 + 187.8 + 64.9 MB,
+# the frozen Jv 322.0 + 55.6 MB)
 TRAFFIC = {
     "amr2_base64": {"linearise": None, "jv": None},
     "batching_base128": {"linearise": None, "jv": None},
-    "single256": {"linearise": 8 * (57.7 + 377.6 + 187.9 + 63.8) * 1e6,
-                  "jv": 8 * (321.9 + 55.5) * 1e6},
+    "single256": {"linearise": 8 * (58.1 + 394.5 + 187.8 + 64.9) * 1e6,
+                  "jv": 8 * (322.0 + 55.6) * 1e6},
 }
 # FP64-pipe instructions per cell measured by ncu (sm__inst_executed_pipe_fp64,
 # same capture): linearisation 139.2 + 35.0, frozen Jv 40.4
@@ -187,7 +192,8 @@ def profile_run(args):
     from paper_1302_6303_gb300 import nrd
     h, z, u0 = workload(args.workload)
     ctx = make_ctx(nrd, h, z, torch, production=True, wl=WORKLOADS[args.workload])
-    ctx.set_params(tile_x=8, tile_y=8, tile_z=4, graph=1 if args.profile_graph else 0)
+    tx, ty, tz = WORKLOADS[args.workload]["tile"]
+    ctx.set_params(tile_x=tx, tile_y=ty, tile_z=tz, graph=1 if args.profile_graph else 0)
     if WORKLOADS[args.workload]["solver"] is None:
         ctx.set_params(nu1=1, nu2=1, coarse_sweeps=2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
