@@ -27,9 +27,18 @@ void host_parallel(long n, int nch, const F& fn) {
     fn(0L, n, 0);
     return;
   }
+  // a chunk whose thread cannot be started (the system refuses it) runs here
   std::vector<std::thread> th;
   th.reserve(nch);
-  for (int k = 0; k < nch; k++) th.emplace_back([&fn, n, nch, k] { fn(n * k / nch, n * (k + 1) / nch, k); });
+  int started = 0;
+  try {
+    for (; started < nch; started++) {
+      const int k = started;
+      th.emplace_back([&fn, n, nch, k] { fn(n * k / nch, n * (k + 1) / nch, k); });
+    }
+  } catch (...) {
+  }
+  for (int k = started; k < nch; k++) fn(n * k / nch, n * (k + 1) / nch, k);
   for (auto& t : th) t.join();
 }
 

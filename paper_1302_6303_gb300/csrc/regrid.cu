@@ -472,8 +472,14 @@ int nrd_transfer(nrd_ctx* src, nrd_ctx* dst, const double* u_src, double* u_dst,
   if (nth == 1) {
     work(0);
   } else {
+    // a part whose thread cannot be started (the system refuses it) runs here
     std::vector<std::thread> pool;
-    for (int th = 0; th < nth; th++) pool.emplace_back(work, th);
+    int started = 0;
+    try {
+      for (; started < nth; started++) pool.emplace_back(work, started);
+    } catch (...) {
+    }
+    for (int th = started; th < nth; th++) work(th);
     for (auto& t : pool) t.join();
   }
   for (int th = 0; th < nth; th++)
