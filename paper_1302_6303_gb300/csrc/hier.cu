@@ -581,6 +581,7 @@ int hier_tiles(Hier& H, std::string& err) {
   const int kSplit = 3 * std::max(nsm, 1);   // about one wave of the linearisation stencil
   const int TX = H.tile_x, TY = H.tile_y, TZ = H.tile_z;
   std::vector<TileDev> full, covered;
+  H.ragged = false;
   for (int l = 0; l < H.L; l++) {
     LevelInfo& Lv = H.lev[l];
     Lv.t0 = 0;
@@ -598,6 +599,7 @@ int hier_tiles(Hier& H, std::string& err) {
                   if (!(H.hmask[P.off + i + P.n[0] * (j + P.n[1] * k)] & MASK_COVERED)) all = false;
             TileDev t{p, i0, j0, k0, k1, all ? 1 : 0};
             (all ? covered : full).push_back(t);
+            if (!all && (i0 + TX > P.n[0] || j0 + TY > P.n[1])) H.ragged = true;
           }
     }
   }

@@ -385,7 +385,14 @@ __device__ __forceinline__ void lin_cell_covered(const StencilIO& io, int N, int
   }
 }
 
-template <int MODE, int TX, int TY, int TZ>
+// CMP: the cell loops (and the fused forms' face loop) run over the cells of
+// a tile inside its patch only, with index arithmetic in the tile's runtime
+// extent; used where the hierarchy has tiles narrower than the tile shape
+// (patches whose sides are not multiples of it), so that no lane of a warp
+// idles on a cell outside its patch.  Without CMP the extents are the
+// compile-time shape (fewer registers: the form for hierarchies without
+// such tiles).
+template <int MODE, int TX, int TY, int TZ, bool CMP = false>
 __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
   constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
   constexpr int NH = HX * HY * HZ;
@@ -461,8 +468,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
       const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
       const double* pE = io.pef;
       const double* pT = io.pef + NS;
-      for (int c = threadIdx.x; c < NC; c += blockDim.x) {
-        const int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
+      const int cex = CMP ? min(TX, nx - tile.i0) : TX, cey = CMP ? min(TY, ny - tile.j0) : TY;
+      const int nce = CMP ? cex * cey * (tile.k1 - tile.k0) : NC;
+      for (int c = threadIdx.x; c < nce; c += blockDim.x) {
+        const int ci = c % cex, cj = (c / cex) % cey, ck = c / (cex * cey);
         const int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
         if (i >= nx || j >= ny || k >= tile.k1) continue;
         const int idx = P.off + i + nx * (j + ny * k);
@@ -591,7 +600,9 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     const int nbx = (FACES && tile.i0 + ex == nx) ? ey * tzl : 0;
     const int nby = (FACES && tile.j0 + ey == ny) ? ex * tzl : 0;
     const int nbz = (FACES && tile.k1 == nz) ? ex * ey : 0;
-    const int nfaces = FACES ? 3 * nlow + nbx + nby + nbz : NFX + NFY + NFZ;
+    const int nfxe = (ex + 1) * ey * tzl, nfye = ex * (ey + 1) * tzl;
+    const int nfaces = FACES ? 3 * nlow + nbx + nby + nbz
+                             : (CMP ? nfxe + nfye + ex * ey * (tzl + 1) : NFX + NFY + NFZ);
     for (int f = threadIdx.x; f < nfaces; f += blockDim.x) {
       int dir, fi, fj, fk, slot = 0;
       double* outE = nullptr;
@@ -613,6 +624,24 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
         } else {
           q -= nby;
           dir = 2; fk = tzl; fi = q % ex; fj = q / ex;
+        }
+      } else if (CMP) {
+        // the faces of the tile's cells inside the patch, each written to its
+        // full-tile slot (the cell loop reads them there)
+        int q = f;
+        if (q < nfxe) {
+          dir = 0; fi = q % (ex + 1); fj = (q / (ex + 1)) % ey; fk = q / ((ex + 1) * ey);
+          slot = fi + (TX + 1) * (fj + TY * fk);
+          outE = fxE; outT = fxT;
+        } else if ((q -= nfxe) < nfye) {
+          dir = 1; fi = q % ex; fj = (q / ex) % (ey + 1); fk = q / (ex * (ey + 1));
+          slot = fi + TX * (fj + (TY + 1) * fk);
+          outE = fyE; outT = fyT;
+        } else {
+          q -= nfye;
+          dir = 2; fi = q % ex; fj = (q / ex) % ey; fk = q / (ex * ey);
+          slot = fi + TX * (fj + TY * fk);
+          outE = fzE; outT = fzT;
         }
       } else if (f < NFX) {
         dir = 0; slot = f;
@@ -751,8 +780,10 @@ __global__ void __launch_bounds__(256) k_stencil(StArgs A) {
     if (FACES) continue;   // the cell launch forms the balance
     // ---- cell balance
     const double rhx = A.lh.rh[lvl][0], rhy = A.lh.rh[lvl][1], rhz = A.lh.rh[lvl][2];
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
-      int ci = c % TX, cj = (c / TX) % TY, ck = c / (TX * TY);
+    const int fex = CMP ? ex : TX, fey = CMP ? ey : TY;
+    const int nce = CMP ? ex * ey * tzl : NC;
+    for (int c = threadIdx.x; c < nce; c += blockDim.x) {
+      int ci = c % fex, cj = (c / fex) % fey, ck = c / (fex * fey);
       int i = tile.i0 + ci, j = tile.j0 + cj, k = tile.k0 + ck;
       if (i >= nx || j >= ny || k >= tile.k1) continue;
       int idx = P.off + i + nx * (j + ny * k);
@@ -1024,33 +1055,41 @@ size_t stencil_smem() {
   return d * sizeof(double);
 }
 
-template <int MODE, int TX, int TY, int TZ>
+template <int MODE, int TX, int TY, int TZ, bool CMP>
 void run_stencil(const StArgs& a, cudaStream_t s) {
   size_t sm = stencil_smem<MODE, TX, TY, TZ>();
   static bool init = false;
   if (!init) {
-    cudaFuncSetAttribute(k_stencil<MODE, TX, TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)sm);
+    cudaFuncSetAttribute(k_stencil<MODE, TX, TY, TZ, CMP>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     init = true;
   }
   // one tile per CTA: the block scheduler balances tiles of uneven cost
   int grid = a.ntiles;
   if (grid < 1) return;
-  k_stencil<MODE, TX, TY, TZ><<<grid, 256, sm, s>>>(a);
+  k_stencil<MODE, TX, TY, TZ, CMP><<<grid, 256, sm, s>>>(a);
 }
 
-template <int MODE>
+template <int MODE, bool CMP = false>
 void dispatch_tile(const StArgs& a, int tx, int ty, int tz, cudaStream_t s) {
-  if (tx == 32 && ty == 8 && tz == 4) run_stencil<MODE, 32, 8, 4>(a, s);
-  else if (tx == 32 && ty == 4 && tz == 8) run_stencil<MODE, 32, 4, 8>(a, s);
-  else if (tx == 32 && ty == 2 && tz == 4) run_stencil<MODE, 32, 2, 4>(a, s);
-  else if (tx == 16 && ty == 8 && tz == 4) run_stencil<MODE, 16, 8, 4>(a, s);
-  else if (tx == 16 && ty == 4 && tz == 8) run_stencil<MODE, 16, 4, 8>(a, s);
-  else if (tx == 16 && ty == 8 && tz == 8) run_stencil<MODE, 16, 8, 8>(a, s);
-  else if (tx == 16 && ty == 4 && tz == 4) run_stencil<MODE, 16, 4, 4>(a, s);
-  else if (tx == 8 && ty == 8 && tz == 8) run_stencil<MODE, 8, 8, 8>(a, s);
-  else if (tx == 8 && ty == 8 && tz == 4) run_stencil<MODE, 8, 8, 4>(a, s);
-  else run_stencil<MODE, 32, 4, 4>(a, s);
+  if (tx == 32 && ty == 8 && tz == 4) run_stencil<MODE, 32, 8, 4, CMP>(a, s);
+  else if (tx == 32 && ty == 4 && tz == 8) run_stencil<MODE, 32, 4, 8, CMP>(a, s);
+  else if (tx == 32 && ty == 2 && tz == 4) run_stencil<MODE, 32, 2, 4, CMP>(a, s);
+  else if (tx == 16 && ty == 8 && tz == 4) run_stencil<MODE, 16, 8, 4, CMP>(a, s);
+  else if (tx == 16 && ty == 4 && tz == 8) run_stencil<MODE, 16, 4, 8, CMP>(a, s);
+  else if (tx == 16 && ty == 8 && tz == 8) run_stencil<MODE, 16, 8, 8, CMP>(a, s);
+  else if (tx == 16 && ty == 4 && tz == 4) run_stencil<MODE, 16, 4, 4, CMP>(a, s);
+  else if (tx == 8 && ty == 8 && tz == 8) run_stencil<MODE, 8, 8, 8, CMP>(a, s);
+  else if (tx == 8 && ty == 8 && tz == 4) run_stencil<MODE, 8, 8, 4, CMP>(a, s);
+  else run_stencil<MODE, 32, 4, 4, CMP>(a, s);
+}
+
+// the compact-cell form where the hierarchy has ragged tiles, for the launches
+// of the Newton and Krylov loops (the cell launches and the frozen Jv)
+template <int MODE>
+void dispatch_tile_h(const Hier& H, const StArgs& a, cudaStream_t s) {
+  if (H.ragged) dispatch_tile<MODE, true>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else dispatch_tile<MODE, false>(a, H.tile_x, H.tile_y, H.tile_z, s);
 }
 
 }  // namespace
@@ -1113,15 +1152,15 @@ void launch_stencil(const Hier& H, const ModelParams& mp, const float* z, const 
   a.io = io;
   if (mode == ST_RESIDUAL && io.pef) {
     dispatch_tile<ST_RESF>(a, H.tile_x, H.tile_y, H.tile_z, s);
-    dispatch_tile<ST_RESC>(a, H.tile_x, H.tile_y, H.tile_z, s);
+    dispatch_tile_h<ST_RESC>(H, a, s);
   } else if (mode == ST_RESIDUAL) dispatch_tile<ST_RESIDUAL>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_JV) dispatch_tile<ST_JV>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_LIN && io.pef) {
     dispatch_tile<ST_LINF>(a, H.tile_x, H.tile_y, H.tile_z, s);
-    dispatch_tile<ST_LINC>(a, H.tile_x, H.tile_y, H.tile_z, s);
+    dispatch_tile_h<ST_LINC>(H, a, s);
   } else if (mode == ST_LIN) dispatch_tile<ST_LIN>(a, H.tile_x, H.tile_y, H.tile_z, s);
   else if (mode == ST_LINZ) dispatch_tile<ST_LINZ>(a, H.tile_x, H.tile_y, H.tile_z, s);
-  else if (mode == ST_JVF) dispatch_tile<ST_JVF>(a, H.tile_x, H.tile_y, H.tile_z, s);
+  else if (mode == ST_JVF) dispatch_tile_h<ST_JVF>(H, a, s);
   else dispatch_tile<ST_FD>(a, H.tile_x, H.tile_y, H.tile_z, s);
 }
 

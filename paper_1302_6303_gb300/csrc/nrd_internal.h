@@ -54,6 +54,7 @@ struct Hier {
   int bc_type[6];
   double bc_R[6];
   int tile_x = 32, tile_y = 4, tile_z = 4;
+  bool ragged = false;                    // a tile narrower than the tile shape in x or y
   std::vector<uint8_t> hmask;             // host copy of the cell masks
 
   // host copies
